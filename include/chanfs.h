@@ -1,0 +1,184 @@
+/*
+ * chanfs.h -- C ABI of libchanfs, a GB300-native (sm_103a) solver for the
+ * pressure-Poisson and wall-normal implicit-diffusion Helmholtz equations of
+ * incompressible channel flow on a staggered second-order finite-difference
+ * grid, after Diez, Peeters & Costa, "A pencil-distributed finite-difference
+ * solver for extreme-scale calculations of turbulent wall flows at high
+ * Reynolds number" (arXiv 2502.06296).
+ *
+ * Grid and storage
+ *   Nx x Ny x Nz cells; x and y periodic and uniform (dx = lx/Nx, dy = ly/Ny);
+ *   z bounded by two walls and arbitrarily stretched, given by the Nz cell
+ *   widths dz[k] (Sec. 2.1).  Every field is Nx*Ny*Nz contiguous doubles,
+ *   x fastest: f[x + Nx*(y + Ny*z)].  Cell-centred fields hold p, u, v; a
+ *   face-located field holds w at the top face of cell k in slot k, and slot
+ *   Nz-1 (the top wall) is written as 0 by the solver.
+ *
+ * Calls and memory
+ *   Field pointers are DEVICE pointers unless the name ends in _host.  They
+ *   belong to the caller, must be 16-byte aligned, and stay valid until the
+ *   work queued on `stream` has finished.  `stream` is a cudaStream_t passed
+ *   as void* (NULL = legacy default stream).  Solves are asynchronous; input
+ *   and output may be the same buffer (in place).  Plans own their tables and
+ *   workspace; one plan may be used from one host thread at a time.
+ *
+ * Errors
+ *   Every call returns a cfs_status.  Argument errors are detected on the host
+ *   and return before anything is queued.  A device-side failure (a bounded
+ *   wait that ran out) is recorded in the plan and reported by cfs_plan_check.
+ */
+#ifndef CHANFS_H
+#define CHANFS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CHANFS_VERSION 100 /* 1.0.0 */
+
+typedef struct cfs_plan* cfs_plan_t; /* opaque, owned by the library */
+
+typedef enum {
+  CFS_OK = 0,
+  CFS_EINVAL = -1,         /* bad argument (null pointer, bad size, bad enum) */
+  CFS_ENOMEM = -2,         /* device or host allocation failed */
+  CFS_EUNSUPPORTED = -3,   /* size outside what the kernels implement */
+  CFS_ECUDA = -4,          /* a CUDA runtime call failed */
+  CFS_ETIMEOUT = -5,       /* a device-side bounded wait ran out */
+  CFS_ENOTCONVERGED = -6   /* reserved for iterative refinement */
+} cfs_status;
+
+typedef enum { CFS_BC_NEUMANN = 0, CFS_BC_DIRICHLET = 1 } cfs_bc;   /* z walls */
+typedef enum { CFS_LOC_CENTER = 0, CFS_LOC_FACE = 1 } cfs_loc;      /* z location */
+typedef enum { CFS_F64 = 0 } cfs_dtype;                             /* arithmetic */
+
+/* Library version (CHANFS_VERSION of the build). */
+int cfs_version(void);
+
+/* Human-readable text for a cfs_status; never NULL. */
+const char* cfs_status_string(int status);
+
+/*
+ * cfs_plan_create -- set up a solver for one grid on the current CUDA device
+ * (Sec. 2.2.1 "Fourier-based synthesis", Eq. 12; App. A for the layout).
+ *   nx     cells along x; even, nx/2 = 2^a 3^b, 2 <= nx <= 4096.
+ *   ny     cells along y; 2^a 3^b, 1 <= ny <= 1024.
+ *   nz     cells along z; 3 <= nz <= 16384.
+ *   lx,ly  domain lengths (> 0); dx = lx/nx, dy = ly/ny.
+ *   dz     nz HOST doubles, the cell widths along z (all > 0); copied.
+ *   poisson_bc  z-wall condition of the Poisson equation (cfs_bc).
+ *   dtype  CFS_F64.
+ * At creation the plan computes, in FP64 and once (the time-invariant
+ * pre-processing of Sec. 2.2.4): the z metrics, the modified wavenumbers
+ * 2(cos(2 pi k/N) - 1)/h^2 re-ordered to the packed layout (App. A), the FFT
+ * twiddle tables and the LU factors of every (kx, ky) tridiagonal system of
+ * Eq. 12.  Returns CFS_EUNSUPPORTED for sizes outside the ranges above.
+ * On success *plan is set; on failure *plan is left NULL.
+ */
+int cfs_plan_create(cfs_plan_t* plan, int nx, int ny, int nz, double lx,
+                    double ly, const double* dz, int poisson_bc, int dtype);
+
+/* Release the plan and everything it owns.  Waits for the device. */
+int cfs_plan_destroy(cfs_plan_t plan);
+
+/* Device bytes held by the plan (tables, cached coefficients, staging). */
+int cfs_plan_device_bytes(cfs_plan_t plan, size_t* bytes);
+
+/*
+ * cfs_poisson_solve -- solve L p = f (Eq. 4 / Eq. 12): the staggered 7-point
+ * Laplacian, periodic in x and y, with the plan's z-wall condition.
+ *   f  device field (read), p  device field (written); f == p allowed.
+ * Steps (Sec. 2.2.3 without transposes): packed real FFT along x (App. A),
+ * complex FFT along y, one tridiagonal solve along z per (kx, ky), inverse y
+ * and x transforms.  With Neumann walls the dz-weighted mean of f is removed
+ * (compatibility) and p is returned with zero dz-weighted mean.
+ * No workspace beyond p is used.
+ */
+int cfs_poisson_solve(cfs_plan_t plan, const double* f, double* p,
+                      void* stream);
+
+/*
+ * cfs_helmholtz_prepare -- Step 1 of Algorithm 2 (Sec. 2.2.4) for the matrix
+ * I - c L_z with homogeneous Dirichlet walls at location `loc`: the reduction
+ * coefficients of each of `nparts` z-partitions and the factors of the
+ * reduced 2*nparts boundary system, computed on the host in FP64 and cached
+ * in the plan under (c, loc, nparts).  nparts = 0 picks a partition count.
+ *   c  the coefficient of Eq. 11 (gamma_k nu dt / 2, i.e. alpha nu dt), >= 0.
+ * Each partition needs 3..32 rows, at most 32 partitions of up to 16 rows or
+ * 12 partitions of up to 32 rows (registers), so a column has at most 512
+ * unknowns; otherwise EUNSUPPORTED.
+ * Calling it is optional: cfs_helmholtz_solve prepares on a cache miss.
+ */
+int cfs_helmholtz_prepare(cfs_plan_t plan, double c, int loc, int nparts);
+
+/*
+ * cfs_helmholtz_solve -- solve (I - c L_z) u = rhs in every (x, y) column
+ * (Eq. 11) by Steps 2-4 of Algorithm 2: runtime forward/backward reduction of
+ * the right-hand side only, the reduced boundary system, and reconstruction.
+ *   rhs  device field (read), u  device field (written); rhs == u allowed.
+ * Uses the coefficients cached by cfs_helmholtz_prepare (any nparts) or
+ * prepares with nparts = 0 on a miss.
+ */
+int cfs_helmholtz_solve(cfs_plan_t plan, double c, int loc, const double* rhs,
+                        double* u, void* stream);
+
+/*
+ * cfs_spectral_forward / cfs_spectral_inverse -- the transform stages of the
+ * Poisson solve on their own.  Forward: unnormalised DFT along x stored in
+ * the packed real format of App. A (pair j >= 1 of a line is X_j; pair 0 is
+ * X_0 + i X_{nx/2}), then an unnormalised complex DFT along y of each pair.
+ * Inverse: the exact inverse (normalised by 1/(nx ny)).  Both are nx*ny*nz
+ * doubles; in == out allowed.
+ */
+int cfs_spectral_forward(cfs_plan_t plan, const double* f, double* s,
+                         void* stream);
+int cfs_spectral_inverse(cfs_plan_t plan, const double* s, double* f,
+                         void* stream);
+
+/*
+ * cfs_poisson_stage -- one kernel of the Poisson solve on its own, for
+ * stage-by-stage testing and profiling.  `in` is read, `out` written (the
+ * y and z stages work in place on `out`, after copying `in` there when the
+ * two differ).  Stages, in the order cfs_poisson_solve runs them:
+ *   CFS_STAGE_X_FORWARD  packed real DFT along x (App. A), unnormalised
+ *   CFS_STAGE_Y_FORWARD  complex DFT along y of each packed pair, unnormalised
+ *   CFS_STAGE_Z_SOLVE    the tridiagonal solves of Eq. 12 on the spectrum,
+ *                        scaled by 2/(nx ny) to absorb the inverse transforms
+ *   CFS_STAGE_Y_INVERSE  unnormalised inverse complex DFT along y
+ *   CFS_STAGE_X_INVERSE  inverse real DFT along x, scaled by nx/2
+ */
+typedef enum {
+  CFS_STAGE_X_FORWARD = 0,
+  CFS_STAGE_Y_FORWARD = 1,
+  CFS_STAGE_Z_SOLVE = 2,
+  CFS_STAGE_Y_INVERSE = 3,
+  CFS_STAGE_X_INVERSE = 4
+} cfs_stage;
+int cfs_poisson_stage(cfs_plan_t plan, int stage, const double* in,
+                      double* out, void* stream);
+
+/*
+ * Host-buffer variants: f/p and rhs/u are HOST pointers (pinned memory gives
+ * full copy bandwidth; pageable memory works).  The plan stages the field in
+ * a device buffer it allocates on first use, copies in, solves and copies
+ * out on `stream`, then waits for the stream before returning.
+ */
+int cfs_poisson_solve_host(cfs_plan_t plan, const double* f, double* p,
+                           void* stream);
+int cfs_helmholtz_solve_host(cfs_plan_t plan, double c, int loc,
+                             const double* rhs, double* u, void* stream);
+
+/*
+ * cfs_plan_check -- wait for the device and report device-side failures
+ * recorded since the last check (then clear them).  *device_error (may be
+ * NULL) receives the raw failure bits.  Returns CFS_ETIMEOUT if a bounded
+ * wait inside a kernel ran out, CFS_ECUDA if the device reported an error.
+ */
+int cfs_plan_check(cfs_plan_t plan, int* device_error);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHANFS_H */

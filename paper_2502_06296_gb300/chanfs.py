@@ -1,0 +1,215 @@
+"""ctypes binding of libchanfs (include/chanfs.h): argument marshalling only.
+
+Every step of every solve runs in the library's CUDA kernels.  Fields are
+torch float64 tensors of shape (Nz, Ny, Nx) (x fastest), contiguous, on the
+plan's CUDA device; work is queued on torch's current stream unless a stream
+is given.  If the library has not been built this module raises: there is no
+CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libchanfs.so")
+
+NEUMANN, DIRICHLET = 0, 1
+CENTER, FACE = 0, 1
+F64 = 0
+
+X_FORWARD, Y_FORWARD, Z_SOLVE, Y_INVERSE, X_INVERSE = 0, 1, 2, 3, 4
+
+OK, EINVAL, ENOMEM, EUNSUPPORTED, ECUDA, ETIMEOUT, ENOTCONVERGED = 0, -1, -2, -3, -4, -5, -6
+
+_lib = None
+
+
+class ChanfsError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+def lib():
+    """Load libchanfs.so (built by __graft_entry__.build() / build.py)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; "
+                               f"g.build()'` first (there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, dp, i, d = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_double
+        sig = {
+            "cfs_version": ([], i),
+            "cfs_status_string": ([i], ctypes.c_char_p),
+            "cfs_plan_create": ([ctypes.POINTER(vp), i, i, i, d, d, dp, i, i], i),
+            "cfs_plan_destroy": ([vp], i),
+            "cfs_plan_device_bytes": ([vp, ctypes.POINTER(ctypes.c_size_t)], i),
+            "cfs_poisson_solve": ([vp, vp, vp, vp], i),
+            "cfs_helmholtz_prepare": ([vp, d, i, i], i),
+            "cfs_helmholtz_solve": ([vp, d, i, vp, vp, vp], i),
+            "cfs_spectral_forward": ([vp, vp, vp, vp], i),
+            "cfs_spectral_inverse": ([vp, vp, vp, vp], i),
+            "cfs_poisson_solve_host": ([vp, vp, vp, vp], i),
+            "cfs_helmholtz_solve_host": ([vp, d, i, vp, vp, vp], i),
+            "cfs_plan_check": ([vp, ctypes.POINTER(i)], i),
+            "cfs_poisson_stage": ([vp, i, vp, vp, vp], i),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    """Names of the C-ABI entry points declared in include/chanfs.h."""
+    hdr = os.path.join(os.path.dirname(HERE), "include", "chanfs.h")
+    import re
+    return sorted(set(re.findall(r"^\w[\w\s\*]*?\b(cfs_\w+)\s*\(", open(hdr).read(), re.M)))
+
+
+def status_string(status: int) -> str:
+    return lib().cfs_status_string(status).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise ChanfsError(rc, what)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """One grid: Nx x Ny x Nz cells, periodic x/y of lengths lx, ly, and the
+    z cell widths dz (host array).  See cfs_plan_create."""
+
+    def __init__(self, nx: int, ny: int, nz: int, lx: float, ly: float, dz, bc: int = NEUMANN,
+                 dtype: int = F64):
+        dz = np.ascontiguousarray(dz, dtype=np.float64)
+        if dz.size != nz:
+            raise ValueError("dz must have nz entries")
+        self.nx, self.ny, self.nz, self.lx, self.ly, self.bc = nx, ny, nz, lx, ly, bc
+        self.dz = dz.copy()
+        h = ctypes.c_void_p()
+        rc = lib().cfs_plan_create(ctypes.byref(h), nx, ny, nz, lx, ly,
+                                   dz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), bc, dtype)
+        _check(rc, "cfs_plan_create")
+        self._h = h
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cfs_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _field(self, t, name):
+        import torch
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda:
+            raise TypeError(f"{name} must be a float64 CUDA tensor")
+        if tuple(t.shape) != self.shape or not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous with shape {self.shape}")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def _out(self, like, out):
+        import torch
+        return torch.empty_like(like) if out is None else out
+
+    def device_bytes(self) -> int:
+        n = ctypes.c_size_t()
+        _check(lib().cfs_plan_device_bytes(self._h, ctypes.byref(n)), "cfs_plan_device_bytes")
+        return n.value
+
+    def poisson_solve(self, f, out=None, stream=None):
+        out = self._out(f, out)
+        _check(lib().cfs_poisson_solve(self._h, self._field(f, "f"), self._field(out, "out"),
+                                       _stream_ptr(stream)), "cfs_poisson_solve")
+        return out
+
+    def helmholtz_prepare(self, c: float, loc: int = CENTER, nparts: int = 0):
+        _check(lib().cfs_helmholtz_prepare(self._h, float(c), loc, nparts), "cfs_helmholtz_prepare")
+
+    def helmholtz_solve(self, c: float, rhs, loc: int = CENTER, out=None, stream=None):
+        out = self._out(rhs, out)
+        _check(lib().cfs_helmholtz_solve(self._h, float(c), loc, self._field(rhs, "rhs"),
+                                         self._field(out, "out"), _stream_ptr(stream)),
+               "cfs_helmholtz_solve")
+        return out
+
+    def spectral_forward(self, f, out=None, stream=None):
+        out = self._out(f, out)
+        _check(lib().cfs_spectral_forward(self._h, self._field(f, "f"), self._field(out, "out"),
+                                          _stream_ptr(stream)), "cfs_spectral_forward")
+        return out
+
+    def spectral_inverse(self, s, out=None, stream=None):
+        out = self._out(s, out)
+        _check(lib().cfs_spectral_inverse(self._h, self._field(s, "s"), self._field(out, "out"),
+                                          _stream_ptr(stream)), "cfs_spectral_inverse")
+        return out
+
+    def poisson_stage(self, stage: int, x, out=None, stream=None):
+        """Run one kernel of the Poisson solve (see cfs_poisson_stage)."""
+        out = self._out(x, out)
+        _check(lib().cfs_poisson_stage(self._h, stage, self._field(x, "in"), self._field(out, "out"),
+                                       _stream_ptr(stream)), "cfs_poisson_stage")
+        return out
+
+    def poisson_solve_host(self, f, out, stream=None):
+        """f, out: host buffers (numpy arrays or pinned CPU tensors) of the field shape."""
+        _check(lib().cfs_poisson_solve_host(self._h, _host_ptr(f, self.shape), _host_ptr(out, self.shape),
+                                            _stream_ptr(stream)), "cfs_poisson_solve_host")
+        return out
+
+    def helmholtz_solve_host(self, c: float, rhs, out, loc: int = CENTER, stream=None):
+        _check(lib().cfs_helmholtz_solve_host(self._h, float(c), loc, _host_ptr(rhs, self.shape),
+                                              _host_ptr(out, self.shape), _stream_ptr(stream)),
+               "cfs_helmholtz_solve_host")
+        return out
+
+    def check(self) -> int:
+        """Synchronise and return the device failure bits (raises on failure)."""
+        bits = ctypes.c_int(0)
+        rc = lib().cfs_plan_check(self._h, ctypes.byref(bits))
+        _check(rc, "cfs_plan_check")
+        return bits.value
+
+
+def _host_ptr(a, shape):
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or a.size != int(np.prod(shape)):
+            raise ValueError("host buffer must be a contiguous float64 array of the field size")
+        return ctypes.c_void_p(a.ctypes.data)
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or a.dtype != torch.float64 or not a.is_contiguous() or a.numel() != int(np.prod(shape)):
+            raise ValueError("host buffer must be a contiguous float64 CPU tensor of the field size")
+        return ctypes.c_void_p(a.data_ptr())
+    raise TypeError("host buffer must be a numpy array or a CPU tensor")

@@ -1,0 +1,521 @@
+// plan.cu -- the C ABI of libchanfs: plans, tables, pre-processing and the
+// orchestration of the Poisson and Helmholtz solves on the caller's stream.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "chanfs_internal.cuh"
+
+using namespace chanfs;
+
+// ----------------------------------------------------------------------------
+// FFT radix plans and twiddles
+// ----------------------------------------------------------------------------
+namespace chanfs {
+
+static const double kTwoPi = 6.283185307179586476925286766559;
+
+// exp(-2 pi i e / n) with exact reduction of e modulo n.
+static double2 root(long long e, long long n) {
+  long long r = e % n;
+  if (r < 0) r += n;
+  double a = kTwoPi * (double)r / (double)n;
+  return make_double2(cos(a), -sin(a));
+}
+
+bool make_fft_desc(int n, FftDesc* d, std::vector<double2>* tw) {
+  memset(d, 0, sizeof(*d));
+  d->n = n;
+  int rest = n;
+  std::vector<int> rad;
+  while (rest % 8 == 0) { rad.push_back(8); rest /= 8; }
+  if (rest % 4 == 0) { rad.push_back(4); rest /= 4; }
+  if (rest % 2 == 0) { rad.push_back(2); rest /= 2; }
+  while (rest % 3 == 0) { rad.push_back(3); rest /= 3; }
+  if (rest != 1 || (int)rad.size() > kMaxPasses) return false;
+  tw->clear();
+  int L = 1;
+  d->npass = (int)rad.size();
+  for (int p = 0; p < d->npass; ++p) {
+    const int R = rad[p];
+    d->radix[p] = R;
+    d->span[p] = L;
+    d->twoff[p] = (int)tw->size();
+    for (int k = 0; k < L; ++k)
+      for (int r = 1; r < R; ++r) tw->push_back(root((long long)r * k, (long long)L * R));
+    L *= R;
+  }
+  d->ntw = (int)tw->size();
+  if (tw->empty()) tw->push_back(make_double2(1.0, 0.0));  // keep a valid pointer
+  return true;
+}
+
+}  // namespace chanfs
+
+// ----------------------------------------------------------------------------
+// Helpers
+// ----------------------------------------------------------------------------
+static bool is_23_smooth(int n) {
+  if (n < 1) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
+
+template <typename T>
+static int dev_upload(T** dst, const T* src, size_t count, size_t* acc) {
+  if (cudaMalloc(dst, sizeof(T) * count) != cudaSuccess) return CFS_ENOMEM;
+  *acc += sizeof(T) * count;
+  if (src && cudaMemcpy(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice) != cudaSuccess)
+    return CFS_ECUDA;
+  return CFS_OK;
+}
+
+// z stencil of the staggered grid (Sec. 2.1, eta of Eq. 12), flux form:
+//   (L_z p)_k = [(p_{k+1}-p_k)/dzc_k - (p_k-p_{k-1})/dzc_{k-1}] / dzf_k,
+// centred unknowns with mirror ghosts at the walls (Neumann: p_{-1} = p_0;
+// Dirichlet: u_{-1} = -u_0, ghost one cell width away), or, for face-located
+// unknowns, the Nz-1 interior faces with w = 0 on both walls.
+static int z_stencil(const std::vector<double>& dzf, int bc, int loc, std::vector<double>& A,
+                     std::vector<double>& B, std::vector<double>& C) {
+  const int nz = (int)dzf.size();
+  std::vector<double> dzc(nz > 1 ? nz - 1 : 1);
+  for (int k = 0; k + 1 < nz; ++k) dzc[k] = 0.5 * (dzf[k] + dzf[k + 1]);
+  if (loc == CFS_LOC_CENTER) {
+    A.assign(nz, 0.0);
+    B.assign(nz, 0.0);
+    C.assign(nz, 0.0);
+    for (int k = 0; k < nz; ++k) {
+      const double lo = (k > 0) ? 1.0 / (dzf[k] * dzc[k - 1]) : 1.0 / (dzf[0] * dzf[0]);
+      const double hi = (k < nz - 1) ? 1.0 / (dzf[k] * dzc[k]) : 1.0 / (dzf[k] * dzf[k]);
+      double diag = -(lo + hi);
+      if (k == 0) diag += (bc == CFS_BC_NEUMANN) ? lo : -lo;
+      if (k == nz - 1) diag += (bc == CFS_BC_NEUMANN) ? hi : -hi;
+      A[k] = (k > 0) ? lo : 0.0;
+      C[k] = (k < nz - 1) ? hi : 0.0;
+      B[k] = diag;
+    }
+    return nz;
+  }
+  const int n = nz - 1;
+  A.assign(n, 0.0);
+  B.assign(n, 0.0);
+  C.assign(n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    const double lo = 1.0 / (dzc[j] * dzf[j]);
+    const double hi = 1.0 / (dzc[j] * dzf[j + 1]);
+    A[j] = (j > 0) ? lo : 0.0;
+    C[j] = (j < n - 1) ? hi : 0.0;
+    B[j] = -(lo + hi);
+  }
+  return n;
+}
+
+static int cuda_status(cudaError_t e) { return e == cudaSuccess ? CFS_OK : CFS_ECUDA; }
+
+// ----------------------------------------------------------------------------
+// Public ABI
+// ----------------------------------------------------------------------------
+extern "C" int cfs_version(void) { return CHANFS_VERSION; }
+
+extern "C" const char* cfs_status_string(int s) {
+  switch (s) {
+    case CFS_OK: return "ok";
+    case CFS_EINVAL: return "invalid argument";
+    case CFS_ENOMEM: return "out of memory";
+    case CFS_EUNSUPPORTED: return "unsupported size or option";
+    case CFS_ECUDA: return "CUDA runtime error";
+    case CFS_ETIMEOUT: return "device-side wait timed out";
+    case CFS_ENOTCONVERGED: return "not converged";
+    default: return "unknown status";
+  }
+}
+
+static void plan_free(cfs_plan* P) {
+  if (!P) return;
+  cudaFree(P->d_twx);
+  cudaFree(P->d_twy);
+  cudaFree(P->d_post);
+  cudaFree(P->d_fwd);
+  cudaFree(P->d_bwd);
+  cudaFree(P->d_dzf);
+  cudaFree(P->d_stage);
+  cudaFree(P->d_status);
+  for (auto& h : P->helm) {
+    cudaFree(h.d_rows);
+    cudaFree(h.d_red);
+  }
+  delete P;
+}
+
+extern "C" int cfs_plan_create(cfs_plan_t* out, int nx, int ny, int nz, double lx, double ly,
+                               const double* dz, int poisson_bc, int dtype) {
+  if (!out) return CFS_EINVAL;
+  *out = nullptr;
+  if (!dz || !(lx > 0) || !(ly > 0) || !isfinite(lx) || !isfinite(ly)) return CFS_EINVAL;
+  if (poisson_bc != CFS_BC_NEUMANN && poisson_bc != CFS_BC_DIRICHLET) return CFS_EINVAL;
+  if (dtype != CFS_F64) return CFS_EUNSUPPORTED;
+  if (nx < 2 || ny < 1 || nz < 3) return CFS_EINVAL;
+  if (nx % 2 != 0 || nx > kMaxNx || !is_23_smooth(nx / 2)) return CFS_EUNSUPPORTED;
+  if (ny > kMaxNy || !is_23_smooth(ny) || nz > kMaxNz) return CFS_EUNSUPPORTED;
+  for (int k = 0; k < nz; ++k)
+    if (!(dz[k] > 0) || !isfinite(dz[k])) return CFS_EINVAL;
+
+  cfs_plan* P = new (std::nothrow) cfs_plan();
+  if (!P) return CFS_ENOMEM;
+  cudaGetDevice(&P->device);
+  P->nx = nx;
+  P->ny = ny;
+  P->nz = nz;
+  P->M = nx / 2;
+  P->nky = ny / 2 + 1;
+  P->lx = lx;
+  P->ly = ly;
+  P->bc = poisson_bc;
+  P->dzf.assign(dz, dz + nz);
+  P->helm_clock = 0;
+  P->device_bytes = 0;
+
+  // y tile: columns per tile and TMA boxes (at most 256 rows per box)
+  P->nbox = (ny + 255) / 256;
+  if (ny % P->nbox != 0) {
+    plan_free(P);
+    return CFS_EUNSUPPORTED;
+  }
+  P->by = ny / P->nbox;
+  // 8 columns per tile when the tile is small (or when 4 would leave a box
+  // start off the 128-byte boundary TMA wants in shared memory), else 4
+  P->tk = (ny <= 256 || P->by % 2 != 0) ? 8 : 4;
+  if (P->tk > P->M) P->tk = P->M;
+  if (P->nbox > 1 && ((size_t)P->by * P->tk * sizeof(double2)) % 128 != 0) {
+    plan_free(P);
+    return CFS_EUNSUPPORTED;
+  }
+
+  std::vector<double2> twx, twy;
+  if (!make_fft_desc(P->M, &P->fx, &twx) || !make_fft_desc(ny, &P->fy, &twy)) {
+    plan_free(P);
+    return CFS_EUNSUPPORTED;
+  }
+  // real-FFT untangling factors 0.5 * W_nx^k, k = 0..M/2
+  std::vector<double2> post(P->M / 2 + 1);
+  for (int k = 0; k <= P->M / 2; ++k) {
+    double2 w = chanfs::root(k, nx);
+    post[k] = make_double2(0.5 * w.x, 0.5 * w.y);
+  }
+  // modified wavenumbers of Eq. 12 for kx = 0..M and ky = 0..ny/2
+  const double dx = lx / nx, dy = ly / ny;
+  std::vector<double> lamx(P->M + 1), lamy(P->nky);
+  for (int k = 0; k <= P->M; ++k) lamx[k] = 2.0 * (cos(kTwoPi * k / nx) - 1.0) / (dx * dx);
+  for (int k = 0; k < P->nky; ++k) lamy[k] = 2.0 * (cos(kTwoPi * k / ny) - 1.0) / (dy * dy);
+  std::vector<double> A, B, C;
+  z_stencil(P->dzf, poisson_bc, CFS_LOC_CENTER, A, B, C);
+
+  int rc = CFS_OK;
+  double *dA = nullptr, *dB = nullptr, *dC = nullptr, *dlx = nullptr, *dly = nullptr;
+  size_t scratch = 0;
+  const size_t nfac = (size_t)(P->M + 1) * P->nky * nz;
+  if (!rc) rc = dev_upload(&P->d_twx, twx.data(), twx.size(), &P->device_bytes);
+  if (!rc) rc = dev_upload(&P->d_twy, twy.data(), twy.size(), &P->device_bytes);
+  if (!rc) rc = dev_upload(&P->d_post, post.data(), post.size(), &P->device_bytes);
+  if (!rc) rc = dev_upload(&P->d_dzf, P->dzf.data(), (size_t)nz, &P->device_bytes);
+  if (!rc) rc = dev_upload<double2>(&P->d_fwd, nullptr, nfac, &P->device_bytes);
+  if (!rc) rc = dev_upload<double>(&P->d_bwd, nullptr, nfac, &P->device_bytes);
+  if (!rc) rc = dev_upload<int>(&P->d_status, nullptr, 1, &P->device_bytes);
+  if (!rc) rc = cuda_status(cudaMemset(P->d_status, 0, sizeof(int)));
+  if (!rc) rc = dev_upload(&dA, A.data(), A.size(), &scratch);
+  if (!rc) rc = dev_upload(&dB, B.data(), B.size(), &scratch);
+  if (!rc) rc = dev_upload(&dC, C.data(), C.size(), &scratch);
+  if (!rc) rc = dev_upload(&dlx, lamx.data(), lamx.size(), &scratch);
+  if (!rc) rc = dev_upload(&dly, lamy.data(), lamy.size(), &scratch);
+  if (!rc) rc = cuda_status(launch_thomas_factor(P, dA, dB, dC, dlx, dly, 0));
+  if (!rc) rc = cuda_status(cudaDeviceSynchronize());
+  cudaFree(dA);
+  cudaFree(dB);
+  cudaFree(dC);
+  cudaFree(dlx);
+  cudaFree(dly);
+  if (rc) {
+    plan_free(P);
+    return rc;
+  }
+  *out = P;
+  return CFS_OK;
+}
+
+extern "C" int cfs_plan_destroy(cfs_plan_t P) {
+  if (!P) return CFS_EINVAL;
+  cudaDeviceSynchronize();
+  plan_free(P);
+  return CFS_OK;
+}
+
+extern "C" int cfs_plan_device_bytes(cfs_plan_t P, size_t* bytes) {
+  if (!P || !bytes) return CFS_EINVAL;
+  *bytes = P->device_bytes;
+  return CFS_OK;
+}
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+extern "C" int cfs_spectral_forward(cfs_plan_t P, const double* f, double* s, void* stream) {
+  if (!P || !f || !s || !aligned16(f) || !aligned16(s)) return CFS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = launch_rfft_x(P, f, s, false, 1.0, st);
+  if (e == cudaSuccess) e = launch_fft_y(P, s, false, st);
+  return e == cudaErrorInvalidValue ? CFS_EINVAL : cuda_status(e);
+}
+
+extern "C" int cfs_spectral_inverse(cfs_plan_t P, const double* s, double* f, void* stream) {
+  if (!P || !f || !s || !aligned16(f) || !aligned16(s)) return CFS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the y pass works in place, so it runs on the output buffer
+  cudaError_t e = cudaSuccess;
+  if (s != f)
+    e = cudaMemcpyAsync(f, s, sizeof(double) * (size_t)P->nx * P->ny * P->nz,
+                        cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = launch_fft_y(P, f, true, st);
+  if (e == cudaSuccess) e = launch_rfft_x(P, f, f, true, 2.0 / ((double)P->nx * P->ny), st);
+  return e == cudaErrorInvalidValue ? CFS_EINVAL : cuda_status(e);
+}
+
+extern "C" int cfs_poisson_solve(cfs_plan_t P, const double* f, double* p, void* stream) {
+  if (!P || !f || !p || !aligned16(f) || !aligned16(p)) return CFS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = launch_rfft_x(P, f, p, false, 1.0, st);
+  if (e == cudaSuccess) e = launch_fft_y(P, p, false, st);
+  if (e == cudaSuccess) e = launch_thomas(P, p, st);
+  if (e == cudaSuccess) e = launch_fft_y(P, p, true, st);
+  if (e == cudaSuccess) e = launch_rfft_x(P, p, p, true, 1.0, st);
+  return e == cudaErrorInvalidValue ? CFS_EINVAL : cuda_status(e);
+}
+
+extern "C" int cfs_poisson_stage(cfs_plan_t P, int stage, const double* in, double* out,
+                                 void* stream) {
+  if (!P || !in || !out || !aligned16(in) || !aligned16(out)) return CFS_EINVAL;
+  if (stage < CFS_STAGE_X_FORWARD || stage > CFS_STAGE_X_INVERSE) return CFS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (stage == CFS_STAGE_X_FORWARD) {
+    e = launch_rfft_x(P, in, out, false, 1.0, st);
+  } else if (stage == CFS_STAGE_X_INVERSE) {
+    e = launch_rfft_x(P, in, out, true, 1.0, st);
+  } else {
+    if (in != out)
+      e = cudaMemcpyAsync(out, in, sizeof(double) * (size_t)P->nx * P->ny * P->nz,
+                          cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) {
+      if (stage == CFS_STAGE_Y_FORWARD) e = launch_fft_y(P, out, false, st);
+      else if (stage == CFS_STAGE_Y_INVERSE) e = launch_fft_y(P, out, true, st);
+      else e = launch_thomas(P, out, st);
+    }
+  }
+  return e == cudaErrorInvalidValue ? CFS_EINVAL : cuda_status(e);
+}
+
+// ----------------------------------------------------------------------------
+// Helmholtz: Algorithm 2, Step 1 on the host in FP64 (Sec. 2.2.4: the
+// coefficients are the same for every (x, y) column, so every GPU computes
+// them locally instead of communicating them).
+// ----------------------------------------------------------------------------
+static HelmCoef* helm_find(cfs_plan* P, double c, int loc, int nparts) {
+  for (auto& h : P->helm)
+    if (h.c == c && h.loc == loc && (nparts == 0 || h.nparts == nparts)) return &h;
+  return nullptr;
+}
+
+static int auto_parts(int n) {
+  // up to 16 rows per partition (the register-only variant of the kernel);
+  // larger partitions (17..32 rows, at most 12) are available on request
+  int p = (n + 15) / 16;
+  if (p > kPcrMaxParts) p = kPcrMaxParts;
+  if (p < 1) p = 1;
+  while (p > 1 && n / p < 3) --p;
+  return p;
+}
+
+static int helm_prepare(cfs_plan* P, double c, int loc, int nparts, HelmCoef** res) {
+  if (!(c >= 0) || !isfinite(c)) return CFS_EINVAL;
+  if (loc != CFS_LOC_CENTER && loc != CFS_LOC_FACE) return CFS_EINVAL;
+  if (nparts < 0 || nparts > kPcrMaxParts) return CFS_EUNSUPPORTED;
+  if (HelmCoef* h = helm_find(P, c, loc, nparts)) {
+    h->stamp = ++P->helm_clock;
+    *res = h;
+    return CFS_OK;
+  }
+  std::vector<double> A, B, C;
+  const int n = z_stencil(P->dzf, CFS_BC_DIRICHLET, loc, A, B, C);
+  for (int i = 0; i < n; ++i) {  // I - c L_z
+    A[i] = -c * A[i];
+    B[i] = 1.0 - c * B[i];
+    C[i] = -c * C[i];
+  }
+  const int np = nparts ? nparts : auto_parts(n);
+  HelmCoef h;
+  memset(&h, 0, sizeof(h));
+  h.c = c;
+  h.loc = loc;
+  h.nparts = np;
+  h.n = n;
+  h.mmax = 0;
+  for (int q = 0; q <= np; ++q) h.start[q] = (int)(((long long)q * n) / np);
+  for (int q = 0; q < np; ++q) {
+    const int m = h.start[q + 1] - h.start[q];
+    if (m < 3 || m > kPcrMaxRows) return CFS_EUNSUPPORTED;
+    h.mmax = std::max(h.mmax, m);
+  }
+  if (h.mmax > 16 && np > kPcrMaxPartsWide) return CFS_EUNSUPPORTED;
+  std::vector<double> rows(5 * (size_t)n, 0.0);
+  double* alpha = rows.data();
+  double* beta = alpha + n;
+  double* ib = beta + n;
+  double* ap = ib + n;
+  double* cpv = ap + n;
+  const int J = 2 * np;
+  std::vector<double> ra(J), rb(J), rc(J);
+  std::vector<double> a(n), b(n), cc(n);
+  for (int q = 0; q < np; ++q) {
+    const int o = h.start[q], m = h.start[q + 1] - o;
+    const double *Aq = &A[o], *Bq = &B[o], *Cq = &C[o];
+    double *aq = &a[o], *bq = &b[o], *cq = &cc[o];
+    // Step 1 of Algorithm 2
+    aq[1] = Aq[1];
+    bq[1] = Bq[1];
+    for (int i = 2; i <= m - 1; ++i) {
+      bq[i] = Bq[i] - Aq[i] * Cq[i - 1] / bq[i - 1];
+      aq[i] = -Aq[i] * aq[i - 1] / bq[i - 1];
+    }
+    cq[m - 1] = Cq[m - 1];
+    cq[m - 2] = Cq[m - 2];
+    for (int i = m - 3; i >= 1; --i) {
+      aq[i] = aq[i] - Cq[i] * aq[i + 1] / bq[i + 1];
+      cq[i] = -Cq[i] * cq[i + 1] / bq[i + 1];
+    }
+    aq[0] = Aq[0];
+    bq[0] = Bq[0] - Cq[0] * aq[1] / Bq[1];
+    cq[0] = -Cq[0] * cq[1] / Bq[1];
+    // run-time factors of Steps 2 and 4 (divisions done here, once)
+    for (int i = 0; i < m; ++i) {
+      alpha[o + i] = (i >= 2) ? Aq[i] / bq[i - 1] : 0.0;
+      beta[o + i] = (i <= m - 3) ? Cq[i] / bq[i + 1] : 0.0;
+      ib[o + i] = 1.0 / bq[i];
+      ap[o + i] = aq[i] / bq[i];
+      cpv[o + i] = cq[i] / bq[i];
+    }
+    // Step 3: the partition's two rows of the reduced boundary system
+    ra[2 * q] = aq[0];
+    rb[2 * q] = bq[0];
+    rc[2 * q] = cq[0];
+    ra[2 * q + 1] = aq[m - 1];
+    rb[2 * q + 1] = bq[m - 1];
+    rc[2 * q + 1] = cq[m - 1];
+  }
+  // LU of the reduced system (no pivoting: diagonally dominant)
+  std::vector<double> red(3 * (size_t)J);
+  double* rl = red.data();
+  double* rip = rl + J;
+  double* ripc = rip + J;
+  double piv = rb[0];
+  rl[0] = 0.0;
+  rip[0] = 1.0 / piv;
+  ripc[0] = rc[0] / piv;
+  for (int j = 1; j < J; ++j) {
+    rl[j] = ra[j] / piv;
+    piv = rb[j] - rl[j] * rc[j - 1];
+    rip[j] = 1.0 / piv;
+    ripc[j] = rc[j] / piv;
+  }
+  int rcode = dev_upload(&h.d_rows, rows.data(), rows.size(), &P->device_bytes);
+  if (!rcode) rcode = dev_upload(&h.d_red, red.data(), red.size(), &P->device_bytes);
+  if (rcode) {
+    cudaFree(h.d_rows);
+    cudaFree(h.d_red);
+    return rcode;
+  }
+  // bounded cache: evict the least recently used entry
+  const size_t kMaxEntries = 32;
+  if (P->helm.size() >= kMaxEntries) {
+    auto it = std::min_element(P->helm.begin(), P->helm.end(),
+                               [](const HelmCoef& x, const HelmCoef& y) { return x.stamp < y.stamp; });
+    cudaDeviceSynchronize();
+    cudaFree(it->d_rows);
+    cudaFree(it->d_red);
+    P->device_bytes -= sizeof(double) * (5 * (size_t)it->n + 6 * (size_t)it->nparts);
+    P->helm.erase(it);
+  }
+  h.stamp = ++P->helm_clock;
+  P->helm.push_back(h);
+  *res = &P->helm.back();
+  return CFS_OK;
+}
+
+extern "C" int cfs_helmholtz_prepare(cfs_plan_t P, double c, int loc, int nparts) {
+  if (!P) return CFS_EINVAL;
+  HelmCoef* h = nullptr;
+  return helm_prepare(P, c, loc, nparts, &h);
+}
+
+extern "C" int cfs_helmholtz_solve(cfs_plan_t P, double c, int loc, const double* rhs, double* u,
+                                   void* stream) {
+  if (!P || !rhs || !u || !aligned16(rhs) || !aligned16(u)) return CFS_EINVAL;
+  HelmCoef* h = nullptr;
+  int rc = helm_prepare(P, c, loc, 0, &h);
+  if (rc) return rc;
+  return cuda_status(launch_pcr(P, *h, rhs, u, (cudaStream_t)stream));
+}
+
+// ----------------------------------------------------------------------------
+// Host-buffer variants
+// ----------------------------------------------------------------------------
+static int ensure_stage(cfs_plan* P) {
+  if (P->d_stage) return CFS_OK;
+  const size_t bytes = sizeof(double) * (size_t)P->nx * P->ny * P->nz;
+  if (cudaMalloc(&P->d_stage, bytes) != cudaSuccess) return CFS_ENOMEM;
+  P->device_bytes += bytes;
+  return CFS_OK;
+}
+
+extern "C" int cfs_poisson_solve_host(cfs_plan_t P, const double* f, double* p, void* stream) {
+  if (!P || !f || !p) return CFS_EINVAL;
+  int rc = ensure_stage(P);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = sizeof(double) * (size_t)P->nx * P->ny * P->nz;
+  if (cudaMemcpyAsync(P->d_stage, f, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return CFS_ECUDA;
+  rc = cfs_poisson_solve(P, P->d_stage, P->d_stage, stream);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(p, P->d_stage, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return CFS_ECUDA;
+  return cuda_status(cudaStreamSynchronize(st));
+}
+
+extern "C" int cfs_helmholtz_solve_host(cfs_plan_t P, double c, int loc, const double* rhs,
+                                        double* u, void* stream) {
+  if (!P || !rhs || !u) return CFS_EINVAL;
+  int rc = ensure_stage(P);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = sizeof(double) * (size_t)P->nx * P->ny * P->nz;
+  if (cudaMemcpyAsync(P->d_stage, rhs, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return CFS_ECUDA;
+  rc = cfs_helmholtz_solve(P, c, loc, P->d_stage, P->d_stage, stream);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(u, P->d_stage, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return CFS_ECUDA;
+  return cuda_status(cudaStreamSynchronize(st));
+}
+
+extern "C" int cfs_plan_check(cfs_plan_t P, int* device_error) {
+  if (!P) return CFS_EINVAL;
+  cudaError_t e = cudaDeviceSynchronize();
+  int bits = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&bits, P->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && bits) e = cudaMemset(P->d_status, 0, sizeof(int));
+  if (device_error) *device_error = bits;
+  if (e != cudaSuccess) return CFS_ECUDA;
+  return (bits & kErrTmaTimeout) ? CFS_ETIMEOUT : CFS_OK;
+}

@@ -1,0 +1,272 @@
+"""GPU parity: every stage of the CUDA path, called through the C ABI, against
+the CPU oracle on the same seeded inputs, element by element.
+
+Tolerance: 1e-12 in the relative max-norm, max|gpu - oracle| / max|oracle|,
+the figure the FP64 path is specified to meet.  Both sides compute in FP64;
+they differ only in rounding order (and FMA use on the GPU).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2502_06296_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def chanfs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_06296_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2502_06296_gb300 import chanfs as c
+    c.lib()
+    return c
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def make_dz(nz, beta):
+    return synth.uniform_dz(nz) if beta is None else synth.tanh_dz(nz, beta)
+
+
+# sizes span several y tiles and a ragged tail (M not a multiple of the tile
+# width), odd complex lengths along x and y, ny = 1 and ny > 256 (two TMA boxes)
+SPECTRAL_SIZES = [(32, 32, 4), (48, 36, 3), (6, 9, 3), (18, 27, 3), (2, 1, 3), (8, 1, 5),
+                  (24, 384, 3), (64, 288, 3), (54, 12, 3), (512, 8, 3), (16, 486, 3)]
+
+
+@pytest.mark.parametrize("dims", SPECTRAL_SIZES)
+def test_spectral_forward_and_inverse(chanfs, dims):
+    nx, ny, nz = dims
+    f = synth.normal(100 + nx + ny, (nz, ny, nx))
+    with chanfs.Plan(nx, ny, nz, 1.0, 1.0, np.full(nz, 1.0)) as plan:
+        s = host(plan.spectral_forward(dev(f)))
+        ref = oracle.spectral_forward(f)  # complex (nz, ny, nx/2)
+        got = s.view(np.complex128).reshape(ref.shape)
+        assert rel(got, ref) < TOL
+        back = host(plan.spectral_inverse(dev(s)))
+        assert rel(back, f) < TOL
+        assert rel(back, oracle.spectral_inverse(ref)) < TOL
+        # in place
+        t = dev(f)
+        plan.spectral_forward(t, out=t)
+        assert rel(host(t).view(np.complex128).reshape(ref.shape), ref) < TOL
+        assert plan.check() == 0
+
+
+def _oracle_x_packed(f):
+    nz, ny, nx = f.shape
+    out = np.empty_like(f)
+    for z in range(nz):
+        for y in range(ny):
+            out[z, y] = oracle.rfft_packed(f[z, y])
+    return out
+
+
+def _oracle_y(c, sign):
+    """Oracle FFT along axis 1 of a complex (nz, ny, m) array."""
+    out = np.empty_like(c)
+    for z in range(c.shape[0]):
+        for j in range(c.shape[2]):
+            out[z, :, j] = oracle.fft(c[z, :, j], sign)
+    return out
+
+
+STAGE_SIZES = [(24, 384, 3), (32, 32, 4), (16, 486, 3), (64, 288, 3), (8, 48, 3)]
+
+
+@pytest.mark.parametrize("dims", STAGE_SIZES)
+def test_each_transform_stage(chanfs, dims):
+    """x and y transforms one kernel at a time, forward and inverse."""
+    nx, ny, nz = dims
+    m = nx // 2
+    f = synth.normal(11 + nx + ny, (nz, ny, nx))
+    with chanfs.Plan(nx, ny, nz, 1.0, 1.0, np.full(nz, 1.0)) as plan:
+        x = host(plan.poisson_stage(chanfs.X_FORWARD, dev(f)))
+        xref = _oracle_x_packed(f)
+        assert rel(x, xref) < TOL, ("x forward", rel(x, xref))
+        y = host(plan.poisson_stage(chanfs.Y_FORWARD, dev(xref)))
+        yref = _oracle_y(xref.view(np.complex128).reshape(nz, ny, m), -1)
+        assert rel(y.view(np.complex128).reshape(nz, ny, m), yref) < TOL, "y forward"
+        yi = host(plan.poisson_stage(chanfs.Y_INVERSE, dev(xref)))
+        yiref = _oracle_y(xref.view(np.complex128).reshape(nz, ny, m), 1)
+        assert rel(yi.view(np.complex128).reshape(nz, ny, m), yiref) < TOL, "y inverse"
+        xi = host(plan.poisson_stage(chanfs.X_INVERSE, dev(xref)))
+        assert rel(xi, f * m) < TOL, ("x inverse", rel(xi, f * m))
+        assert plan.check() == 0
+
+
+POISSON_CASES = [
+    ((32, 32, 32), None, 0),      # the small uniform workload
+    ((32, 32, 32), None, 1),
+    ((48, 36, 20), 1.8, 0),       # stretched, ragged y tiles
+    ((48, 36, 20), 1.8, 1),
+    ((6, 9, 5), 1.2, 0),          # odd complex lengths
+    ((2, 1, 3), None, 0),         # degenerate: one x pair, ny = 1, nz = 3
+    ((8, 1, 16), 1.5, 1),
+    ((64, 384, 12), 1.8, 0),      # two TMA boxes along y
+    ((96, 54, 33), 2.0, 0),
+]
+
+
+@pytest.mark.parametrize("dims,beta,bc", POISSON_CASES)
+def test_poisson_matches_oracle(chanfs, dims, beta, bc):
+    nx, ny, nz = dims
+    lx, ly = 2 * np.pi, np.pi
+    dz = make_dz(nz, beta)
+    f = synth.normal(7 * nx + ny + nz, (nz, ny, nx))
+    if bc == chanfs.NEUMANN:
+        f = synth.remove_weighted_mean(f, dz)
+    ref = oracle.poisson_solve(f, lx, ly, dz, bc)
+    with chanfs.Plan(nx, ny, nz, lx, ly, dz, bc) as plan:
+        p = host(plan.poisson_solve(dev(f)))
+        assert rel(p, ref) < TOL, rel(p, ref)
+        # in place gives the same bits
+        t = dev(f)
+        plan.poisson_solve(t, out=t)
+        assert np.array_equal(host(t), p)
+        assert plan.check() == 0
+
+
+def test_poisson_neumann_removes_incompatible_mean(chanfs):
+    nx, ny, nz = 16, 12, 10
+    dz = synth.tanh_dz(nz, 1.4)
+    f = synth.normal(3, (nz, ny, nx)) + 0.25  # not compatible
+    ref = oracle.poisson_solve(f, 1.0, 2.0, dz, 0)
+    with chanfs.Plan(nx, ny, nz, 1.0, 2.0, dz, 0) as plan:
+        p = host(plan.poisson_solve(dev(f)))
+    assert rel(p, ref) < TOL
+    w = np.repeat(dz, nx * ny)
+    assert abs(w @ p.ravel()) < 1e-13 * w.sum() * np.max(np.abs(p))
+
+
+def test_poisson_small_workload_residual(chanfs):
+    cfg = synth.SMALL
+    f = synth.small_rhs(cfg)
+    dz = synth.grid_dz(cfg)
+    with chanfs.Plan(cfg["nx"], cfg["ny"], cfg["nz"], cfg["lx"], cfg["ly"], dz, 0) as plan:
+        p = host(plan.poisson_solve(dev(f)))
+    r = f - oracle.apply_poisson(p, cfg["lx"], cfg["ly"], dz, 0)
+    assert np.max(np.abs(r)) / np.max(np.abs(f)) < 1e-12
+    assert abs(p.mean()) < 1e-14 * np.max(np.abs(p))
+
+
+HELM_CASES = [
+    # (nx, ny, nz, beta, loc, nparts)
+    (16, 12, 48, 1.8, 0, 0),
+    (16, 12, 48, 1.8, 1, 0),
+    (12, 9, 100, 1.5, 0, 7),      # uneven partitions, ragged column tile
+    (12, 9, 100, 1.5, 1, 11),
+    (8, 8, 384, 1.8, 0, 12),      # 32-row partitions
+    (8, 8, 384, 1.8, 1, 12),
+    (8, 8, 384, 1.8, 0, 24),
+    (4, 3, 3, None, 0, 1),        # smallest column
+    (6, 4, 4, None, 1, 1),        # face: 3 unknowns
+    (48, 36, 512, 2.0, 0, 32),    # 512 unknowns, 32 partitions
+]
+
+
+@pytest.mark.parametrize("nx,ny,nz,beta,loc,nparts", HELM_CASES)
+def test_helmholtz_matches_oracle(chanfs, nx, ny, nz, beta, loc, nparts):
+    dz = make_dz(nz, beta)
+    rhs = synth.normal(nx * nz + loc, (nz, ny, nx))
+    c = 9.615e-5
+    ref = oracle.helmholtz_solve(rhs, dz, c, loc, oracle.THOMAS)
+    n = nz if loc == 0 else nz - 1
+    with chanfs.Plan(nx, ny, nz, 1.0, 1.0, dz) as plan:
+        plan.helmholtz_prepare(c, loc, nparts)
+        u = host(plan.helmholtz_solve(c, dev(rhs), loc))
+        assert rel(u, ref) < TOL, rel(u, ref)
+        if nparts and n >= 3 * nparts:
+            ref2 = oracle.helmholtz_solve(rhs, dz, c, loc, oracle.ALG2, nparts)
+            assert rel(u, ref2) < TOL
+        t = dev(rhs)
+        plan.helmholtz_solve(c, t, loc, out=t)
+        assert np.array_equal(host(t), u)
+        assert plan.check() == 0
+
+
+def test_helmholtz_identity_and_strong_coefficient(chanfs):
+    nx, ny, nz = 12, 8, 64
+    dz = synth.tanh_dz(nz, 1.8)
+    rhs = synth.normal(5, (nz, ny, nx))
+    with chanfs.Plan(nx, ny, nz, 1.0, 1.0, dz) as plan:
+        for loc in (0, 1):
+            u = host(plan.helmholtz_solve(0.0, dev(rhs), loc))
+            ref = rhs.copy()
+            if loc == 1:
+                ref[-1] = 0.0
+            assert np.array_equal(u, ref)
+            c = 1e-2  # far from the identity: c / dz^2 ~ 1e4
+            u = host(plan.helmholtz_solve(c, dev(rhs), loc))
+            assert rel(u, oracle.helmholtz_solve(rhs, dz, c, loc)) < TOL
+
+
+def test_helmholtz_rejects_unsupported_partitions(chanfs):
+    with chanfs.Plan(8, 8, 40, 1.0, 1.0, np.full(40, 0.05)) as plan:
+        with pytest.raises(chanfs.ChanfsError):
+            plan.helmholtz_prepare(1e-3, 0, 20)   # 2 rows per partition
+        with pytest.raises(chanfs.ChanfsError):
+            plan.helmholtz_prepare(1e-3, 0, 1)    # 40 rows in one partition
+        with pytest.raises(chanfs.ChanfsError):
+            plan.helmholtz_prepare(-1.0, 0, 0)
+    with chanfs.Plan(8, 8, 600, 1.0, 1.0, np.full(600, 2 / 600)) as plan:
+        with pytest.raises(chanfs.ChanfsError):
+            plan.helmholtz_prepare(1e-3, 0, 0)    # 600 unknowns > 512
+
+
+def test_host_buffer_entry_points_match_device_path(chanfs):
+    nx, ny, nz = 32, 24, 16
+    dz = synth.tanh_dz(nz, 1.6)
+    f = synth.remove_weighted_mean(synth.normal(9, (nz, ny, nx)), dz)
+    with chanfs.Plan(nx, ny, nz, 3.0, 2.0, dz) as plan:
+        p_dev = host(plan.poisson_solve(dev(f)))
+        out = np.empty_like(f)
+        plan.poisson_solve_host(f, out)
+        assert np.array_equal(out, p_dev)
+        pinned_in = torch.from_numpy(f).pin_memory()
+        pinned_out = torch.empty_like(pinned_in).pin_memory()
+        plan.poisson_solve_host(pinned_in, pinned_out)
+        assert np.array_equal(pinned_out.numpy(), p_dev)
+        u_dev = host(plan.helmholtz_solve(1e-3, dev(f), 1))
+        plan.helmholtz_solve_host(1e-3, f, out, 1)
+        assert np.array_equal(out, u_dev)
+
+
+@pytest.mark.slow
+def test_channel_workload_full_size(chanfs):
+    """The benchmark's 512 x 384 x 384 channel step, in the launch
+    configuration the benchmark times: every element against the oracle."""
+    cfg = synth.CHANNEL
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    dz = synth.grid_dz(cfg)
+    f, rhs = synth.channel_fields(cfg)
+    c = synth.CHANNEL_C
+    with chanfs.Plan(nx, ny, nz, cfg["lx"], cfg["ly"], dz, chanfs.NEUMANN) as plan:
+        p = host(plan.poisson_solve(dev(f)))
+        us = [host(plan.helmholtz_solve(c, dev(r), loc)) for r, loc in zip(rhs, (0, 0, 1))]
+        assert plan.check() == 0
+    ref = oracle.poisson_solve(f, cfg["lx"], cfg["ly"], dz, 0)
+    assert rel(p, ref) < TOL, rel(p, ref)
+    res = f - oracle.apply_poisson(p, cfg["lx"], cfg["ly"], dz, 0)
+    assert np.max(np.abs(res)) / np.max(np.abs(f)) < 1e-12
+    for r, loc, u in zip(rhs, (0, 0, 1), us):
+        uref = oracle.helmholtz_solve(r, dz, c, loc)
+        assert rel(u, uref) < TOL
