@@ -1,0 +1,432 @@
+"""Benchmark: one channel-flow step (Poisson + three z-implicit Helmholtz
+solves, FP64) on the 512 x 384 x 384 tanh(1.8) grid, through the C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is the whole hot path over one synthetic input set already resident in
+HBM: packed x rFFT, y FFT, z Thomas, inverse y and x transforms (the five
+kernels of cfs_poisson_solve, launched stage by stage so that each kernel is
+timed by CUDA events inside the timed region), then three Algorithm 2 solves
+(u and v cell-centred, w face-located).  Every field (604 MB) is larger than
+L2, so no flush is needed between steps.
+
+Metric: ns per grid point per step (lower is better).  With N GPUs each rank
+runs its own replica of the step (the solves share nothing), and the value is
+the max-over-ranks time divided by all ranks' points.  Rank 0 prints one JSON
+line.  `--impl reference` times the CPU oracle on a bounded sample instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2502_06296_gb300 import synth  # noqa: E402
+
+METRIC = "Poisson+Helmholtz ns/grid-pt, % HBM peak; mixed vs FP64 at 1e-10; p99 latency"
+UNIT = "ns/grid-pt"
+CFG = synth.CHANNEL
+STAGES = ["x_forward", "y_forward", "z_thomas", "y_inverse", "x_inverse", "pcr_u", "pcr_v", "pcr_w"]
+KERNEL_OF_STAGE = {"x_forward": "rfft_x_kernel<false>", "y_forward": "fft_y_kernel<false>",
+                   "z_thomas": "thomas_kernel", "y_inverse": "fft_y_kernel<true>",
+                   "x_inverse": "rfft_x_kernel<true>", "pcr_u": "pcr_kernel<16>",
+                   "pcr_v": "pcr_kernel<16>", "pcr_w": "pcr_kernel<16>"}
+SOURCE_OF_STAGE = {"x_forward": "fft_x.cu", "x_inverse": "fft_x.cu", "y_forward": "fft_y.cu",
+                   "y_inverse": "fft_y.cu", "z_thomas": "thomas.cu", "pcr_u": "pcr.cu",
+                   "pcr_v": "pcr.cu", "pcr_w": "pcr.cu"}
+
+
+# ----------------------------------------------------------------------------
+# Algorithmic work per launch (5 N log2 N flops per complex FFT of length N,
+# half that for a real FFT; 16 bytes per point read + written)
+# ----------------------------------------------------------------------------
+
+def stage_work(stage: str, nx: int, ny: int, nz: int):
+    npts = nx * ny * nz
+    if stage.startswith("x_"):
+        flops = ny * nz * 2.5 * nx * np.log2(nx)
+    elif stage.startswith("y_"):
+        flops = (nx // 2) * nz * 5.0 * ny * np.log2(ny)
+    elif stage == "z_thomas":
+        flops = 5.0 * npts  # forward: 2 mul + 1 add, backward: 1 mul + 1 add
+    else:
+        flops = 9.0 * npts  # Algorithm 2: 2 + 2 (Step 2) + 5 (Step 4)
+    return float(flops), 16.0 * npts
+
+
+def fp64_peak_tflops(sm_count: int = 152, clock_mhz: float = 2070.0) -> float:
+    """Two FP64 FMA lanes per SM per clock (the GB300 rate: 1.25 TFLOP/s
+    nominal), counted as 2 flops each, at the maximum SM clock."""
+    return sm_count * 2 * 2 * clock_mhz * 1e6 / 1e12
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+def profiled_traffic(stage: str):
+    """Bytes per launch from the committed ncu summary of this stage's kernel,
+    or None if there is none or the kernel source changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", f"{stage}_channel_512x384x384.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    h = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
+    if not m or not h:
+        return None
+    src = os.path.join(ROOT, "paper_2502_06296_gb300", "csrc", SOURCE_OF_STAGE[stage])
+    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return float(m.group(1)) if cur == h.group(1) else None
+
+
+# ----------------------------------------------------------------------------
+# Clocks during the timed region
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+# ----------------------------------------------------------------------------
+# Distributed helpers (replicas only; the data path has no collective)
+# ----------------------------------------------------------------------------
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def reduce_max(value: float, device=None) -> float:
+    """Max over ranks of a host scalar (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(device=None):
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        if device is not None and dist.get_backend() == "nccl":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def aggregate(max_ms_total: float, steps: int, npts_per_rank: int, world: int) -> dict:
+    """Whole-job figures from the max-over-ranks elapsed time of `steps` steps."""
+    ms_per_step = max_ms_total / steps
+    ns_per_pt = ms_per_step * 1e6 / (npts_per_rank * world)
+    return {"ms_per_step": ms_per_step, "value": ns_per_pt}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample)
+# ----------------------------------------------------------------------------
+
+def oracle_sample_step(nz_sample: int):
+    """The channel step on the full x-y planes and nz_sample tanh(1.8) cells:
+    one Poisson and three Helmholtz solves by the CPU oracle.  Returns
+    (seconds, points)."""
+    import oracle
+    nx, ny = CFG["nx"], CFG["ny"]
+    dz = synth.tanh_dz(nz_sample, CFG["beta"])
+    shape = (nz_sample, ny, nx)
+    f = synth.remove_weighted_mean(synth.normal(CFG["seed"], shape), dz)
+    rhs = [synth.normal(CFG["seed"] + 1 + i, shape) for i in range(3)]
+    t0 = time.perf_counter()
+    oracle.poisson_solve(f, CFG["lx"], CFG["ly"], dz, oracle.NEUMANN)
+    for r, loc in zip(rhs, (oracle.CENTER, oracle.CENTER, oracle.FACE)):
+        oracle.helmholtz_solve(r, dz, synth.CHANNEL_C, loc, oracle.THOMAS)
+    return time.perf_counter() - t0, nx * ny * nz_sample
+
+
+def cpu_baseline(nz_sample: int = 96):
+    secs, npts = oracle_sample_step(nz_sample)
+    return {"value": secs * 1e9 / npts, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one step (Poisson + 3 Helmholtz) on {CFG['nx']}x{CFG['ny']}x{nz_sample} "
+                      f"(full x-y planes, {nz_sample} tanh(1.8) cells), single-threaded FP64 C, "
+                      f"{secs:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    nz_s = 24
+    for _ in range(args.warmup):
+        oracle_sample_step(nz_s)
+    tot, npts = 0.0, 0
+    for _ in range(args.steps):
+        s, n = oracle_sample_step(nz_s)
+        tot += s
+        npts = n
+    ns = tot * 1e9 / (npts * args.steps)
+    line = {"metric": METRIC, "value": ns, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot * 1e3 / args.steps, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": CFG["name"], "sample_nz": nz_s, "parallelism": "cpu_1core"},
+            "cpu_baseline": {"value": ns, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: Poisson + 3 Helmholtz on {CFG['nx']}x{CFG['ny']}x{nz_s}"},
+            "e2e": {"value": ns, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend="nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+
+    from paper_2502_06296_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2502_06296_gb300 import chanfs
+
+    cfg = dict(CFG)
+    if args.nz:  # reduced wall-normal size for profiling captures
+        cfg.update(nz=args.nz, name=f"channel_{CFG['nx']}x{CFG['ny']}x{args.nz}_tanh1.8")
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    npts = nx * ny * nz
+    dz = synth.grid_dz(cfg)
+    c = synth.CHANNEL_C
+    f_h, rhs_h = synth.channel_fields(cfg)
+    plan = chanfs.Plan(nx, ny, nz, CFG["lx"], CFG["ly"], dz, chanfs.NEUMANN)
+    for loc in (chanfs.CENTER, chanfs.FACE):
+        plan.helmholtz_prepare(c, loc, args.nparts)
+    f = torch.from_numpy(f_h).to(device)
+    rhs = [torch.from_numpy(r).to(device) for r in rhs_h]
+    p = torch.empty_like(f)
+    us = [torch.empty_like(f) for _ in range(3)]
+    locs = (chanfs.CENTER, chanfs.CENTER, chanfs.FACE)
+    stream = torch.cuda.current_stream(device)
+
+    # the stage sequence is cfs_poisson_solve's: check it gives the same bits
+    plan.poisson_solve(f, out=p)
+    ref_bits = p.clone()
+
+    def step(events=None):
+        def mark(i):
+            if events is not None:
+                events[i].record(stream)
+        mark(0)
+        plan.poisson_stage(chanfs.X_FORWARD, f, out=p)
+        mark(1)
+        plan.poisson_stage(chanfs.Y_FORWARD, p, out=p)
+        mark(2)
+        plan.poisson_stage(chanfs.Z_SOLVE, p, out=p)
+        mark(3)
+        plan.poisson_stage(chanfs.Y_INVERSE, p, out=p)
+        mark(4)
+        plan.poisson_stage(chanfs.X_INVERSE, p, out=p)
+        mark(5)
+        for i in range(3):
+            plan.helmholtz_solve(c, rhs[i], locs[i], out=us[i])
+            mark(6 + i)
+
+    step()
+    torch.cuda.synchronize()
+    assert torch.equal(p, ref_bits), "stage-by-stage step differs from cfs_poisson_solve"
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(9)] for _ in range(args.steps)]
+    barrier(device)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        start = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for k in range(args.steps):
+            step(events[k])
+        stop.record(stream)
+        torch.cuda.synchronize()
+    barrier(device)
+    elapsed_ms = start.elapsed_time(stop)
+    status = plan.check()
+    stage_ms = {s: [] for s in STAGES}
+    for ev in events:
+        for i, s in enumerate(STAGES):
+            stage_ms[s].append(ev[i].elapsed_time(ev[i + 1]))
+    max_ms = reduce_max(elapsed_ms, device)
+    agg = aggregate(max_ms, args.steps, npts, world)
+
+    # end to end through the host-buffer entry points: pinned host -> device,
+    # solve, device -> host, every step
+    f_pin = torch.from_numpy(f_h).pin_memory()
+    rhs_pin = [torch.from_numpy(r).pin_memory() for r in rhs_h]
+    out_pin = [torch.empty_like(f_pin).pin_memory() for _ in range(4)]
+
+    def e2e_step():
+        plan.poisson_solve_host(f_pin, out_pin[0])
+        for i in range(3):
+            plan.helmholtz_solve_host(c, rhs_pin[i], out_pin[1 + i], locs[i])
+
+    e2e_step()
+    e2e_steps = max(3, min(args.steps, 10))
+    barrier(device)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = reduce_max((time.perf_counter() - t0) * 1e3, device)
+    barrier(device)
+    e2e = aggregate(e2e_ms, e2e_steps, npts, world)
+    field_bytes = npts * 8
+
+    if rank != 0:
+        plan.close()
+        return 0
+
+    # roofline of the kernel with the largest time per step
+    mean_ms = {s: float(np.mean(v)) for s, v in stage_ms.items()}
+    per_kernel = {}
+    for s in STAGES:
+        k = KERNEL_OF_STAGE[s]
+        per_kernel.setdefault(k, 0.0)
+        per_kernel[k] += mean_ms[s]
+    dom_stage = max(STAGES, key=lambda s: mean_ms[s])
+    flops, nbytes = stage_work(dom_stage, nx, ny, nz)
+    dur_s = mean_ms[dom_stage] * 1e-3
+    peaks = read_peaks()
+    clock = clk.summary()
+    peak_tf = fp64_peak_tflops()
+    roof = {"bound": "alu", "achieved": flops / dur_s / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
+            "frac": flops / dur_s / 1e12 / peak_tf, "traffic": profiled_traffic(dom_stage),
+            "kernel": KERNEL_OF_STAGE[dom_stage], "stage": dom_stage,
+            "launch_ms": mean_ms[dom_stage], "flops_per_launch": flops,
+            "algorithmic_bytes_per_launch": nbytes,
+            "hbm_gbs": nbytes / dur_s / 1e9,
+            "hbm_frac": nbytes / dur_s / 1e9 / float(peaks.get("hbm_gbs", 6800.0)),
+            "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flops x 2070 MHz (1.26 TFLOP/s); "
+                           "HBM: MEASURED_PEAKS.json hbm_gbs"}
+    line = {
+        "metric": METRIC, "value": agg["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": agg["ms_per_step"], "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": cfg["name"], "nx": nx, "ny": ny, "nz": nz, "lx": CFG["lx"],
+                   "ly": CFG["ly"], "z_grid": "tanh(1.8) faces", "poisson_bc": "neumann",
+                   "helmholtz_c": c, "helmholtz": "u,v centred + w face, Dirichlet, Algorithm 2",
+                   "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (604 MB fields)",
+                   "pcr_partitions": args.nparts or "auto"},
+        "e2e": {"value": e2e["value"], "unit": UNIT, "h2d_bytes_per_step": 4 * field_bytes,
+                "d2h_bytes_per_step": 4 * field_bytes, "steps": e2e_steps,
+                "api": "cfs_poisson_solve_host + 3 x cfs_helmholtz_solve_host, pinned host buffers"},
+        "gpu_launches": 8 * args.steps,
+        "roofline": roof,
+        "stage_ms": {s: round(v, 4) for s, v in mean_ms.items()},
+        "kernel_ms_per_step": {k: round(v, 4) for k, v in per_kernel.items()},
+        "clocks": clock,
+        "device_status": status,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    else:
+        line["cpu_baseline"] = None
+    plan.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--nparts", type=int, default=0, help="PCR partitions (0 = library default)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nz", type=int, default=0,
+                    help="override the wall-normal size (profiling captures only)")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -472,3 +472,18 @@ def test_spectral_layout_against_numpy_fft2(dims):
     assert _rel(S[:, :, 1:], F[:, :, 1:M]) < 1e-12
     assert _rel(S[:, :, 0], F[:, :, 0] + 1j * F[:, :, M]) < 1e-12
     assert _rel(oracle.spectral_inverse(S), f) < 1e-13
+
+
+def test_oracle_reproduces_its_stored_fixture():
+    """tests/golden/poisson_small_oracle.json was written by
+    tests/golden/make_golden.py (oracle only): the oracle still gives it."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "poisson_small_oracle.json")
+    g = json.load(open(path))
+    cfg = synth.SMALL
+    p = oracle.poisson_solve(synth.small_rhs(cfg), cfg["lx"], cfg["ly"], synth.grid_dz(cfg), 0)
+    scale = g["max_abs_p"]
+    for s in g["samples"]:
+        assert abs(p[tuple(s["zyx"])] - s["p"]) < 1e-13 * scale
+    assert abs(np.max(np.abs(p)) - scale) < 1e-13 * scale
