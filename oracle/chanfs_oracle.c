@@ -705,9 +705,14 @@ int or_helmholtz_solve(int nx, int ny, int nz, const double* dzf, double c,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Spectral layout: App. A packing along x (even Nx: slot pair j of a line   */
-/* is X_j for j >= 1 and X_0 + i X_{Nx/2} for j = 0), then a complex DFT     */
-/* along y of each pair.  Pair j = 0 therefore holds F(0,ky) + i F(Nx/2,ky). */
+/* Spectral layout of the solver: App. A packing along x (even Nx: pair j of */
+/* a line is X_j for j >= 1 and X_0 + i X_{Nx/2} for j = 0), complex DFT     */
+/* along y of each pair, and for pair j = 0 the same packing idea once more  */
+/* along y (both F(0,ky) and F(Nx/2,ky) are DFTs of real sequences, so each  */
+/* is fixed by ky = 0..Ny/2):                                                */
+/*   slot ky, ky = 0 or 2ky = Ny:  F(0,ky) + i F(Nx/2,ky)  (both real)      */
+/*   slot ky, 0 < 2ky < Ny:        F(0,ky)                                  */
+/*   slot ky, 2ky > Ny:            F(Nx/2, Ny-ky)                           */
 /* Built here from the full 2-D DFT, i.e. the definition of the layout.     */
 /* ------------------------------------------------------------------------ */
 
@@ -725,7 +730,14 @@ int or_spectral_forward(int nx, int ny, int nz, const double* f, double* s) {
     for (int ky = 0; ky < ny; ++ky) {
       const cplx* row = F + (size_t)nx * ((size_t)ky + (size_t)ny * z);
       cplx* out = S + (size_t)M * ((size_t)ky + (size_t)ny * z);
-      out[0] = row[0] + I * row[M];
+      if (ky == 0 || 2 * ky == ny) {
+        out[0] = row[0] + I * row[M];
+      } else if (2 * ky < ny) {
+        out[0] = row[0];
+      } else {
+        const cplx* mirror = F + (size_t)nx * ((size_t)(ny - ky) + (size_t)ny * z);
+        out[0] = mirror[M];
+      }
       for (int j = 1; j < M; ++j) out[j] = row[j];
     }
   free(F);
@@ -744,9 +756,17 @@ int or_spectral_inverse(int nx, int ny, int nz, const double* s, double* f) {
       const cplx* in = S + (size_t)M * ((size_t)ky + (size_t)ny * z);
       const cplx* inm = S + (size_t)M * ((size_t)kym + (size_t)ny * z);
       cplx* row = F + (size_t)nx * ((size_t)ky + (size_t)ny * z);
-      /* untangle pair 0: F(0,ky) and F(M,ky) are DFTs of real sequences */
-      row[0] = 0.5 * (in[0] + conj(inm[0]));
-      row[M] = -0.5 * I * (in[0] - conj(inm[0]));
+      /* kx = 0 and kx = Nx/2 from the packed slots and Hermitian symmetry */
+      if (ky == 0 || 2 * ky == ny) {
+        row[0] = creal(in[0]);
+        row[M] = cimag(in[0]);
+      } else if (2 * ky < ny) {
+        row[0] = in[0];           /* slot ky holds F(0, ky) */
+        row[M] = inm[0];          /* slot Ny-ky holds F(M, ky) */
+      } else {
+        row[0] = conj(inm[0]);    /* F(0, ky) = conj F(0, Ny-ky) */
+        row[M] = conj(in[0]);     /* slot ky holds F(M, Ny-ky) */
+      }
       for (int j = 1; j < M; ++j) row[j] = in[j];
       /* Hermitian symmetry F(-kx,-ky) = conj F(kx,ky) for the other half */
       for (int j = 1; j < M; ++j) row[nx - j] = conj(inm[j]);

@@ -75,7 +75,8 @@ int or_helmholtz_solve(int nx, int ny, int nz, const double* dzf, double c,
                        double* u);
 
 /* Spectral layout used by the solver: App. A packing along x, complex DFT
- * along y (pair j of a packed x-line read as one complex number). */
+ * along y (pair j of a packed x-line read as one complex number), and pair 0
+ * (F(0,ky) + i F(Nx/2,ky)) stored untangled by the same packing along y. */
 int or_spectral_forward(int nx, int ny, int nz, const double* f, double* s);
 int or_spectral_inverse(int nx, int ny, int nz, const double* s, double* f);
 

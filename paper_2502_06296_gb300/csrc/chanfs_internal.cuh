@@ -89,6 +89,10 @@ struct cfs_plan {
   double2* d_fwd;    // (s/piv_k, A_k/piv_k)
   double* d_bwd;     // C_k/piv_k
   double* d_dzf;     // cell widths (weights of the Neumann mean)
+  // Neumann (0,0) column: wn = w/sum(w), gn = g/sum(w) with g = T'^{-T} w,
+  // hs = sc * T'^{-1} (0,1,..,1), T' the pinned operator; 3*nz doubles
+  double* d_sing;
+  double sing_cg, sing_sc;
   // Helmholtz cache
   std::vector<chanfs::HelmCoef> helm;
   unsigned long long helm_clock;
@@ -135,7 +139,28 @@ __device__ __forceinline__ double2 mul_mi(double2 a) {
   return INV ? make_double2(-a.y, a.x) : make_double2(a.y, -a.x);
 }
 
+// a + w x with fused multiply-adds (4 FP64 instructions); w is conjugated for
+// the inverse transform.
+template <bool INV>
+__device__ __forceinline__ double2 cfma(double2 w, double2 x, double2 a) {
+  if (INV)
+    return make_double2(fma(w.x, x.x, fma(w.y, x.y, a.x)), fma(w.x, x.y, fma(-w.y, x.x, a.y)));
+  return make_double2(fma(w.x, x.x, fma(-w.y, x.y, a.x)), fma(w.x, x.y, fma(w.y, x.x, a.y)));
+}
+template <bool INV>
+__device__ __forceinline__ double2 ctw(double2 x, double2 w) {
+  return INV ? cmulc(x, w) : cmul(x, w);
+}
+// 2a - s (2 FP64 instructions): the difference partner of s = a + t.
+__device__ __forceinline__ double2 ctwice_minus(double2 a, double2 s) {
+  return make_double2(fma(2.0, a.x, -s.x), fma(2.0, a.y, -s.y));
+}
+
 // Small DFTs in registers.  Forward kernel e^{-2 pi i / R}, inverse e^{+}.
+// The *_tw variants take the inputs before their Stockham twiddles w[r-1]
+// (r >= 1) and fold each twiddle product into the first butterfly level:
+//   (a + w x, a - w x) = (s, 2a - s) with s = a + w x by four FMAs,
+// 6 FP64 instructions per pair instead of 8.
 template <bool INV>
 __device__ __forceinline__ void dft2(double2& a, double2& b) {
   double2 t = a;
@@ -144,53 +169,122 @@ __device__ __forceinline__ void dft2(double2& a, double2& b) {
 }
 
 template <bool INV>
-__device__ __forceinline__ void dft3(double2& a, double2& b, double2& c) {
+__device__ __forceinline__ void dft2_tw(double2* v, const double2* w) {
+  double2 s = cfma<INV>(w[0], v[1], v[0]);
+  v[1] = ctwice_minus(v[0], s);
+  v[0] = s;
+}
+
+// y0 = a + s, y1,2 = (a - s/2) -/+ i (sqrt3/2) d  with s = b + c, d = b - c.
+template <bool INV>
+__device__ __forceinline__ void dft3_core(double2& a, double2& b, double2& c, double2 s, double2 d) {
   const double h = 0.8660254037844386467637231707529362;  // sqrt(3)/2
-  double2 s = cadd(b, c);
-  double2 d = csub(b, c);
   double2 t = make_double2(fma(-0.5, s.x, a.x), fma(-0.5, s.y, a.y));
   a = cadd(a, s);
-  // forward: y1 = t - i h d, y2 = t + i h d
-  double sx = INV ? -h : h;
+  const double sx = INV ? -h : h;
   b = make_double2(fma(sx, d.y, t.x), fma(-sx, d.x, t.y));
   c = make_double2(fma(-sx, d.y, t.x), fma(sx, d.x, t.y));
 }
 
 template <bool INV>
+__device__ __forceinline__ void dft3(double2& a, double2& b, double2& c) {
+  dft3_core<INV>(a, b, c, cadd(b, c), csub(b, c));
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft3_tw(double2* v, const double2* w) {
+  double2 b = ctw<INV>(v[1], w[0]);
+  double2 s = cfma<INV>(w[1], v[2], b);
+  double2 d = ctwice_minus(b, s);
+  dft3_core<INV>(v[0], v[1], v[2], s, d);
+}
+
+// Radix-4 second level from t0 = a0 + a2, t1 = a0 - a2, t2 = a1 + a3,
+// d = a1 - a3.
+template <bool INV>
+__device__ __forceinline__ void dft4_core(double2* y, double2 t0, double2 t1, double2 t2, double2 d) {
+  double2 t3 = mul_mi<INV>(d);
+  y[0] = cadd(t0, t2);
+  y[2] = csub(t0, t2);
+  y[1] = cadd(t1, t3);
+  y[3] = csub(t1, t3);
+}
+
+template <bool INV>
 __device__ __forceinline__ void dft4(double2& a0, double2& a1, double2& a2, double2& a3) {
-  double2 t0 = cadd(a0, a2), t1 = csub(a0, a2);
-  double2 t2 = cadd(a1, a3), t3 = mul_mi<INV>(csub(a1, a3));
-  a0 = cadd(t0, t2);
-  a2 = csub(t0, t2);
-  a1 = cadd(t1, t3);
-  a3 = csub(t1, t3);
+  double2 y[4];
+  dft4_core<INV>(y, cadd(a0, a2), csub(a0, a2), cadd(a1, a3), csub(a1, a3));
+  a0 = y[0]; a1 = y[1]; a2 = y[2]; a3 = y[3];
+}
+
+// DFT4 of (x0, w1 x1, w2 x2, w3 x3) given x0..x3 and w1..w3 (x0 untwiddled).
+template <bool INV>
+__device__ __forceinline__ void dft4_tw4(double2* y, double2 x0, double2 x1, double2 x2, double2 x3,
+                                         double2 w1, double2 w2, double2 w3) {
+  double2 t0 = cfma<INV>(w2, x2, x0);
+  double2 t1 = ctwice_minus(x0, t0);
+  double2 u = ctw<INV>(x1, w1);
+  double2 t2 = cfma<INV>(w3, x3, u);
+  dft4_core<INV>(y, t0, t1, t2, ctwice_minus(u, t2));
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4_tw(double2* v, const double2* w) {
+  double2 y[4];
+  dft4_tw4<INV>(y, v[0], v[1], v[2], v[3], w[0], w[1], w[2]);
+  v[0] = y[0]; v[1] = y[1]; v[2] = y[2]; v[3] = y[3];
+}
+
+// Radix-2 combination of the even (E) and odd (O) half-DFTs of a DFT8, with
+// the W8 factors folded into fused multiply-adds.
+template <bool INV>
+__device__ __forceinline__ void dft8_combine(double2* v, const double2* E, const double2* O) {
+  const double r = 0.7071067811865475244008443621048490;  // 1/sqrt(2)
+  v[0] = cadd(E[0], O[0]);
+  v[4] = csub(E[0], O[0]);
+  double2 m2 = mul_mi<INV>(O[2]);
+  v[2] = cadd(E[2], m2);
+  v[6] = csub(E[2], m2);
+  if (!INV) {
+    // W8 O = r (O.x + O.y, O.y - O.x);  W8^3 O = r (O.y - O.x, -(O.x + O.y))
+    double p1 = O[1].x + O[1].y, q1 = O[1].y - O[1].x;
+    v[1] = make_double2(fma(r, p1, E[1].x), fma(r, q1, E[1].y));
+    v[5] = make_double2(fma(-r, p1, E[1].x), fma(-r, q1, E[1].y));
+    double p3 = O[3].y - O[3].x, q3 = O[3].x + O[3].y;
+    v[3] = make_double2(fma(r, p3, E[3].x), fma(-r, q3, E[3].y));
+    v[7] = make_double2(fma(-r, p3, E[3].x), fma(r, q3, E[3].y));
+  } else {
+    // W8^-1 O = r (O.x - O.y, O.x + O.y);  W8^-3 O = r (-(O.x + O.y), O.x - O.y)
+    double p1 = O[1].x - O[1].y, q1 = O[1].x + O[1].y;
+    v[1] = make_double2(fma(r, p1, E[1].x), fma(r, q1, E[1].y));
+    v[5] = make_double2(fma(-r, p1, E[1].x), fma(-r, q1, E[1].y));
+    double q3 = O[3].x + O[3].y, p3 = O[3].x - O[3].y;
+    v[3] = make_double2(fma(-r, q3, E[3].x), fma(r, p3, E[3].y));
+    v[7] = make_double2(fma(r, q3, E[3].x), fma(-r, p3, E[3].y));
+  }
 }
 
 template <bool INV>
 __device__ __forceinline__ void dft8(double2* v) {
-  const double r = 0.7071067811865475244008443621048490;  // 1/sqrt(2)
-  double2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
-  double2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
-  dft4<INV>(e0, e1, e2, e3);
-  dft4<INV>(o0, o1, o2, o3);
-  // o1 *= W8^1, o2 *= W8^2 = -i, o3 *= W8^3 (forward); conjugates for inverse
-  double2 w1, w3;
-  if (!INV) {
-    w1 = make_double2((o1.x + o1.y) * r, (o1.y - o1.x) * r);
-    w3 = make_double2((o3.y - o3.x) * r, -(o3.x + o3.y) * r);
-  } else {
-    w1 = make_double2((o1.x - o1.y) * r, (o1.y + o1.x) * r);
-    w3 = make_double2(-(o3.x + o3.y) * r, (o3.x - o3.y) * r);
-  }
-  double2 w2 = mul_mi<INV>(o2);
-  v[0] = cadd(e0, o0);
-  v[4] = csub(e0, o0);
-  v[1] = cadd(e1, w1);
-  v[5] = csub(e1, w1);
-  v[2] = cadd(e2, w2);
-  v[6] = csub(e2, w2);
-  v[3] = cadd(e3, w3);
-  v[7] = csub(e3, w3);
+  double2 E[4], O[4];
+  dft4_core<INV>(E, cadd(v[0], v[4]), csub(v[0], v[4]), cadd(v[2], v[6]), csub(v[2], v[6]));
+  dft4_core<INV>(O, cadd(v[1], v[5]), csub(v[1], v[5]), cadd(v[3], v[7]), csub(v[3], v[7]));
+  dft8_combine<INV>(v, E, O);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft8_tw(double2* v, const double2* w) {
+  double2 E[4], O[4];
+  // even half: (v0, w2 v2, w4 v4, w6 v6)
+  dft4_tw4<INV>(E, v[0], v[2], v[4], v[6], w[1], w[3], w[5]);
+  // odd half: all four twiddled
+  double2 a = ctw<INV>(v[1], w[0]);
+  double2 t0 = cfma<INV>(w[4], v[5], a);
+  double2 t1 = ctwice_minus(a, t0);
+  double2 b = ctw<INV>(v[3], w[2]);
+  double2 t2 = cfma<INV>(w[6], v[7], b);
+  dft4_core<INV>(O, t0, t1, t2, ctwice_minus(b, t2));
+  dft8_combine<INV>(v, E, O);
 }
 
 template <int R, bool INV>
@@ -199,6 +293,14 @@ __device__ __forceinline__ void dft(double2* v) {
   else if constexpr (R == 3) dft3<INV>(v[0], v[1], v[2]);
   else if constexpr (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
   else if constexpr (R == 8) dft8<INV>(v);
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft_tw(double2* v, const double2* w) {
+  if constexpr (R == 2) dft2_tw<INV>(v, w);
+  else if constexpr (R == 3) dft3_tw<INV>(v, w);
+  else if constexpr (R == 4) dft4_tw<INV>(v, w);
+  else if constexpr (R == 8) dft8_tw<INV>(v, w);
 }
 
 // One Stockham radix-R butterfly: reads R points j + r*n/R of one batch from
@@ -214,11 +316,13 @@ __device__ __forceinline__ void stockham_bfly(const double2* __restrict__ in,
   for (int r = 0; r < R; ++r) v[r] = in[(j + r * q) * es];
   const int k = j % L;
   if (L > 1) {
-    const double2* w = tw + k * (R - 1);
+    double2 w[R - 1];
 #pragma unroll
-    for (int r = 1; r < R; ++r) v[r] = INV ? cmulc(v[r], w[r - 1]) : cmul(v[r], w[r - 1]);
+    for (int r = 0; r < R - 1; ++r) w[r] = tw[k * (R - 1) + r];
+    dft_tw<R, INV>(v, w);
+  } else {
+    dft<R, INV>(v);
   }
-  dft<R, INV>(v);
   const int o = (j - k) * R + k;
 #pragma unroll
   for (int r = 0; r < R; ++r) out[(o + r * L) * es] = v[r];

@@ -88,8 +88,31 @@ __global__ void __launch_bounds__(128) fft_y_kernel(const __grid_constant__ CUte
     if (threadIdx.x == 0) atomicOr(status, kErrTmaTimeout);
     return;  // no pass ran; nothing is stored
   }
+  const int ny = d.n;
+  // Column kx = 0 of the first tile is the packed pair F(0,ky) + i F(Nx/2,ky)
+  // (App. A).  Its y spectrum is stored untangled, App. A's packing applied
+  // once more along y: slot ky (0 < 2ky < Ny) holds F(0,ky), slot Ny-ky holds
+  // F(Nx/2,ky), and the self-conjugate slots (ky = 0, Ny/2) keep the real pair
+  // F(0,ky) + i F(Nx/2,ky).  Every slot is then one column of Eq. 12.
+  if (INV && blockIdx.x == 0) {  // re-tangle before the inverse transform
+    for (int ky = 1 + threadIdx.x; 2 * ky < ny; ky += blockDim.x) {
+      const double2 f0 = buf0[ky * tk], fm = buf0[(ny - ky) * tk];
+      buf0[ky * tk] = make_double2(f0.x - fm.y, f0.y + fm.x);         // F0 + i FM
+      buf0[(ny - ky) * tk] = make_double2(f0.x + fm.y, fm.x - f0.y);  // conj F0 + i conj FM
+    }
+    __syncthreads();
+  }
   // element (y, c) of the tile sits at y*tk + c: element stride tk, batch stride 1
   double2* res = stockham_smem<INV, true>(buf0, buf1, d, tk, tk, 1, tw);
+  if (!INV && blockIdx.x == 0) {  // untangle after the forward transform
+    for (int ky = 1 + threadIdx.x; 2 * ky < ny; ky += blockDim.x) {
+      const double2 z = res[ky * tk], zm = res[(ny - ky) * tk];
+      // F0 = (Z + conj Zm)/2,  FM = -i (Z - conj Zm)/2
+      res[ky * tk] = make_double2(0.5 * (z.x + zm.x), 0.5 * (z.y - zm.y));
+      res[(ny - ky) * tk] = make_double2(0.5 * (z.y + zm.y), 0.5 * (zm.x - z.x));
+    }
+    __syncthreads();
+  }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
   if (threadIdx.x == 0) {

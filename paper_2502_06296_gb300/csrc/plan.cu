@@ -116,6 +116,23 @@ static int z_stencil(const std::vector<double>& dzf, int bc, int loc, std::vecto
 
 static int cuda_status(cudaError_t e) { return e == cudaSuccess ? CFS_OK : CFS_ECUDA; }
 
+// Thomas algorithm on the host (FP64): a_k x_{k-1} + b_k x_k + c_k x_{k+1} = d_k.
+static void thomas_host(const std::vector<double>& a, const std::vector<double>& b,
+                        const std::vector<double>& c, const std::vector<double>& d,
+                        std::vector<double>& x) {
+  const int n = (int)b.size();
+  std::vector<double> cp(n), dp(n);
+  cp[0] = c[0] / b[0];
+  dp[0] = d[0] / b[0];
+  for (int k = 1; k < n; ++k) {
+    const double piv = b[k] - a[k] * cp[k - 1];
+    cp[k] = c[k] / piv;
+    dp[k] = (d[k] - a[k] * dp[k - 1]) / piv;
+  }
+  x[n - 1] = dp[n - 1];
+  for (int k = n - 2; k >= 0; --k) x[k] = dp[k] - cp[k] * x[k + 1];
+}
+
 // ----------------------------------------------------------------------------
 // Public ABI
 // ----------------------------------------------------------------------------
@@ -142,8 +159,10 @@ static void plan_free(cfs_plan* P) {
   cudaFree(P->d_fwd);
   cudaFree(P->d_bwd);
   cudaFree(P->d_dzf);
+  cudaFree(P->d_sing);
   cudaFree(P->d_stage);
   cudaFree(P->d_status);
+
   for (auto& h : P->helm) {
     cudaFree(h.d_rows);
     cudaFree(h.d_red);
@@ -214,6 +233,33 @@ extern "C" int cfs_plan_create(cfs_plan_t* out, int nx, int ny, int nz, double l
   std::vector<double> A, B, C;
   z_stencil(P->dzf, poisson_bc, CFS_LOC_CENTER, A, B, C);
 
+  // Neumann (0,0) column, pinned operator T' (row 0 -> identity):
+  // h = T'^{-1} (0,1,..,1) and g = T'^{-T} w by Thomas in FP64
+  std::vector<double> sing(3 * (size_t)nz, 0.0);
+  P->sing_sc = 2.0 / ((double)nx * (double)ny);  // the factor scale s
+  P->sing_cg = 0.0;
+  if (poisson_bc == CFS_BC_NEUMANN) {
+    std::vector<double> a(A), b(B), c(C), rhs(nz, 1.0), h(nz), g(nz);
+    b[0] = 1.0;
+    c[0] = 0.0;
+    rhs[0] = 0.0;
+    thomas_host(a, b, c, rhs, h);
+    // transpose: sub-diagonal c_{k-1}, super-diagonal a_{k+1}
+    std::vector<double> at(nz, 0.0), ct(nz, 0.0);
+    for (int k = 1; k < nz; ++k) at[k] = c[k - 1];
+    for (int k = 0; k + 1 < nz; ++k) ct[k] = a[k + 1];
+    thomas_host(at, b, ct, P->dzf, g);
+    double sw = 0.0;
+    for (int k = 0; k < nz; ++k) sw += P->dzf[k];
+    for (int k = 0; k < nz; ++k) {
+      sing[k] = P->dzf[k] / sw;
+      sing[nz + k] = g[k] / sw;
+      sing[2 * nz + k] = P->sing_sc * h[k];
+    }
+    for (int k = 1; k < nz; ++k) P->sing_cg += g[k];
+    P->sing_cg /= sw;
+  }
+
   int rc = CFS_OK;
   double *dA = nullptr, *dB = nullptr, *dC = nullptr, *dlx = nullptr, *dly = nullptr;
   size_t scratch = 0;
@@ -222,10 +268,12 @@ extern "C" int cfs_plan_create(cfs_plan_t* out, int nx, int ny, int nz, double l
   if (!rc) rc = dev_upload(&P->d_twy, twy.data(), twy.size(), &P->device_bytes);
   if (!rc) rc = dev_upload(&P->d_post, post.data(), post.size(), &P->device_bytes);
   if (!rc) rc = dev_upload(&P->d_dzf, P->dzf.data(), (size_t)nz, &P->device_bytes);
+  if (!rc) rc = dev_upload(&P->d_sing, sing.data(), sing.size(), &P->device_bytes);
   if (!rc) rc = dev_upload<double2>(&P->d_fwd, nullptr, nfac, &P->device_bytes);
   if (!rc) rc = dev_upload<double>(&P->d_bwd, nullptr, nfac, &P->device_bytes);
   if (!rc) rc = dev_upload<int>(&P->d_status, nullptr, 1, &P->device_bytes);
   if (!rc) rc = cuda_status(cudaMemset(P->d_status, 0, sizeof(int)));
+
   if (!rc) rc = dev_upload(&dA, A.data(), A.size(), &scratch);
   if (!rc) rc = dev_upload(&dB, B.data(), B.size(), &scratch);
   if (!rc) rc = dev_upload(&dC, C.data(), C.size(), &scratch);

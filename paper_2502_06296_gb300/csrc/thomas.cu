@@ -10,14 +10,14 @@
 //   backward x_k = g_k - (C_k/piv_k) x_{k+1}
 // i.e. 3 FP64 instructions per real unknown, no division at run time.
 //
-// One thread owns the column pair ky and Ny-ky of one kx (they share the
-// eigenvalue, hence the factors); consecutive threads take consecutive kx so
-// that every z-plane access is coalesced.  kx = 0 is the packed pair of App. A:
-// it holds F(0, ky) + i F(Nx/2, ky), which the thread untangles with the
-// Hermitian partner ky' = Ny - ky, solves with the two factor sets, and packs
-// back.  The singular Neumann column (0, 0) is pinned (row 0 -> F_0 = 0) after
-// removing the dz-weighted mean of its right-hand side, and the dz-weighted
-// mean of its solution is removed afterwards.
+// One thread per column of the spectrum; consecutive threads take consecutive
+// kx so that every z-plane access is coalesced.  Column kx = 0 arrives
+// untangled by the y transform (App. A's packing applied again along y), so
+// every slot is one column of Eq. 12; the two self-conjugate slots hold two
+// real columns with different eigenvalues in their real and imaginary parts.
+// The singular Neumann column (0, 0) is pinned (row 0 -> F_0 = 0); the
+// removal of the dz-weighted mean of its right-hand side and of its solution
+// is folded into the same two sweeps by linearity.
 #include "chanfs_internal.cuh"
 
 namespace chanfs {
@@ -26,107 +26,141 @@ struct ThomasArgs {
   double2* S;            // spectrum (Nz, Ny, M) complex
   const double2* fwd;    // (s/piv, A/piv) per (k, kyp, kx in [0, M])
   const double* bwd;     // C/piv
-  const double* dzf;     // weights of the Neumann mean
+  const double* sing;    // Neumann (0,0): wn | gn | hs, 3*nz (see below)
+  double sing_cg;        // g^T 1' / sum(w)
+  double sing_sc;        // the factor scale of the (0,0) column
   int M, ny, nz, nky;
+  int nblk_x;            // blocks along kx per ky
   int neumann;
 };
 
-__device__ __forceinline__ long long sidx(const ThomasArgs& a, int k, int ky, int j) {
-  return ((long long)k * a.ny + ky) * a.M + j;
-}
-__device__ __forceinline__ long long tidx(const ThomasArgs& a, int k, int kyp, int kx) {
-  return ((long long)k * a.nky + kyp) * (a.M + 1) + kx;
-}
+constexpr int kThomasBlock = 64;
+constexpr int kPrefetch = 3;
 
-// The (kx, ky) = (0, 0) pair under Neumann walls: P = 2 Re S is the singular
-// column, Q = 2 Im S is the regular column (Nx/2, 0).
-__device__ void thomas_singular(const ThomasArgs& a) {
-  double sw = 0.0, swp = 0.0;
-  for (int k = 0; k < a.nz; ++k) {
-    sw += a.dzf[k];
-    swp += a.dzf[k] * (2.0 * a.S[sidx(a, k, 0, 0)].x);
-  }
-  const double mu = swp / sw;
-  double gp = 0.0, gq = 0.0;
-  for (int k = 0; k < a.nz; ++k) {
-    double2 s = a.S[sidx(a, k, 0, 0)];
-    double p = (k == 0) ? 0.0 : 2.0 * s.x - mu;
-    double q = 2.0 * s.y;
-    double2 fp = a.fwd[tidx(a, k, 0, 0)], fq = a.fwd[tidx(a, k, 0, a.M)];
-    gp = fma(-fp.y, gp, fp.x * p);
-    gq = fma(-fq.y, gq, fq.x * q);
-    a.S[sidx(a, k, 0, 0)] = make_double2(gp, gq);
-  }
-  double xp = 0.0, xq = 0.0, swx = 0.0;
-  for (int k = a.nz - 1; k >= 0; --k) {
-    double2 g = a.S[sidx(a, k, 0, 0)];
-    xp = fma(-a.bwd[tidx(a, k, 0, 0)], xp, g.x);
-    xq = fma(-a.bwd[tidx(a, k, 0, a.M)], xq, g.y);
-    swx += a.dzf[k] * xp;
-    a.S[sidx(a, k, 0, 0)] = make_double2(xp, xq);
-  }
-  const double nu = swx / sw;
-  for (int k = 0; k < a.nz; ++k) a.S[sidx(a, k, 0, 0)].x -= nu;
-}
-
-__global__ void __launch_bounds__(128) thomas_kernel(ThomasArgs a) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int kyp = blockIdx.y;
+// One thread per spectrum column (kx = j in [0, M), slot ky in [0, Ny)),
+// consecutive threads on consecutive kx (every z-plane access of a warp is
+// one contiguous run).  A column is complex; its real and imaginary parts are
+// solved with factor sets tx and ty, which differ only for the two
+// self-conjugate slots of kx = 0 (a real F(0,ky) and a real F(Nx/2,ky) packed
+// together; see fft_y.cu).  Pointers step by a row stride and each thread
+// keeps the next kPrefetch rows in flight while the recurrence consumes the
+// current one (the sweep is sequential in k, and there are only a few warps
+// per SM, so this in-thread prefetch is what hides the memory latency).
+//
+// Neumann (0, 0) column (real part of slot (0, 0)): singular.  Its system is
+// pinned (row 0: F_0 = 0) and, by linearity, both projections are folded
+// into the same two sweeps:
+//   mu = sum_k wn_k E_k                   (dz-weighted mean of the rhs)
+//   x  = T'^{-1} E' - mu h - nu,  E' = (0, E_1, ..)
+//   nu = (g^T E' - mu g^T 1') / sum w     (dz-weighted mean of the solution)
+// with h = T'^{-1} (0, 1, .., 1) and g = T'^{-T} w precomputed by the plan.
+__global__ void __launch_bounds__(kThomasBlock, 11) thomas_kernel(ThomasArgs a) {
+  const int ky = blockIdx.x / a.nblk_x;
+  const int j = (blockIdx.x % a.nblk_x) * kThomasBlock + threadIdx.x;
   if (j >= a.M) return;
-  const int kyq = (a.ny - kyp) % a.ny;
-  const bool self = (kyq == kyp);
-  const bool j0 = (j == 0);
-  if (a.neumann && j0 && kyp == 0) {
-    thomas_singular(a);
-    return;
+  // factor sets of the real (tx) and imaginary (ty) parts
+  int kx_x = j, kx_y = j, kp_x, kp_y;
+  if (j > 0) {
+    kp_x = kp_y = min(ky, a.ny - ky);
+  } else if (2 * ky == 0 || 2 * ky == a.ny) {  // real pair F(0,ky) + i F(M,ky)
+    kp_x = kp_y = ky;
+    kx_y = a.M;
+  } else if (2 * ky < a.ny) {  // F(0, ky)
+    kp_x = kp_y = ky;
+  } else {  // F(M, Ny - ky)
+    kx_x = kx_y = a.M;
+    kp_x = kp_y = a.ny - ky;
   }
-  const int kxq = j0 ? a.M : j;  // factor set of the second column
-  double2 gp = make_double2(0.0, 0.0), gq = gp;
-  // forward sweep: g overwrites the right-hand side in place
-  for (int k = 0; k < a.nz; ++k) {
-    double2 u = a.S[sidx(a, k, kyp, j)];
-    double2 v = a.S[sidx(a, k, kyq, j)];
-    double2 P, Q;
-    if (j0) {  // untangle F(0,ky) (times 2) and F(M,ky) (times 2)
-      P = make_double2(u.x + v.x, u.y - v.y);
-      Q = make_double2(u.y + v.y, v.x - u.x);
-    } else {
-      P = u;
-      Q = v;
-    }
-    const double2 fp = a.fwd[tidx(a, k, kyp, j)];
-    const double2 fq = j0 ? a.fwd[tidx(a, k, kyp, kxq)] : fp;
-    gp = make_double2(fma(-fp.y, gp.x, fp.x * P.x), fma(-fp.y, gp.y, fp.x * P.y));
-    gq = make_double2(fma(-fq.y, gq.x, fq.x * Q.x), fma(-fq.y, gq.y, fq.x * Q.y));
-    if (j0 && self) {
-      a.S[sidx(a, k, kyp, 0)] = make_double2(gp.x, gq.x);  // both columns are real
-    } else {
-      a.S[sidx(a, k, kyp, j)] = gp;
-      a.S[sidx(a, k, kyq, j)] = gq;
+  const bool sing = a.neumann && j == 0 && ky == 0;
+  const int nz = a.nz;
+  const long long rs = (long long)a.ny * a.M;         // spectrum row stride
+  const long long rt = (long long)a.nky * (a.M + 1);  // factor row stride
+  double2* const s0 = a.S + (long long)ky * a.M + j;
+  const double2* const fx0 = a.fwd + (long long)kp_x * (a.M + 1) + kx_x;
+  const double2* const fy0 = a.fwd + (long long)kp_y * (a.M + 1) + kx_y;
+  const double* const bx0 = a.bwd + (long long)kp_x * (a.M + 1) + kx_x;
+  const double* const by0 = a.bwd + (long long)kp_y * (a.M + 1) + kx_y;
+
+  // forward: g_k = (s/piv_k) f_k - (A_k/piv_k) g_{k-1}, in place
+  double2 qu[kPrefetch], qx[kPrefetch], qy[kPrefetch];
+#pragma unroll
+  for (int i = 0; i < kPrefetch; ++i) {
+    if (i < nz) {
+      qu[i] = s0[i * rs];
+      qx[i] = fx0[i * rt];
+      qy[i] = fy0[i * rt];
     }
   }
-  // backward sweep
-  double2 xp = make_double2(0.0, 0.0), xq = xp;
-  for (int k = a.nz - 1; k >= 0; --k) {
-    double2 g1, g2;
-    if (j0 && self) {
-      double2 s = a.S[sidx(a, k, kyp, 0)];
-      g1 = make_double2(s.x, 0.0);
-      g2 = make_double2(s.y, 0.0);
-    } else {
-      g1 = a.S[sidx(a, k, kyp, j)];
-      g2 = a.S[sidx(a, k, kyq, j)];
+  const double2* pu = s0 + kPrefetch * rs;  // next rows to prefetch
+  const double2* px = fx0 + kPrefetch * rt;
+  const double2* py = fy0 + kPrefetch * rt;
+  double2* ps = s0;                          // row being written
+  double2 g = make_double2(0.0, 0.0);
+  double mu = 0.0, gam = 0.0;
+  for (int k = 0; k < nz; k += kPrefetch) {
+#pragma unroll
+    for (int i = 0; i < kPrefetch; ++i) {
+      if (k + i >= nz) break;
+      double2 u = qu[i];
+      const double2 fx = qx[i], fy = qy[i];
+      if (k + i + kPrefetch < nz) {
+        qu[i] = *pu;
+        qx[i] = *px;
+        qy[i] = *py;
+      }
+      pu += rs;
+      px += rt;
+      py += rt;
+      if (sing) {
+        mu = fma(a.sing[k + i], u.x, mu);
+        if (k + i > 0) gam = fma(a.sing[nz + k + i], u.x, gam);
+        else u.x = 0.0;  // pinned row
+      }
+      g = make_double2(fma(-fx.y, g.x, fx.x * u.x), fma(-fy.y, g.y, fy.x * u.y));
+      *ps = g;
+      ps += rs;
     }
-    const double bp = a.bwd[tidx(a, k, kyp, j)];
-    const double bq = j0 ? a.bwd[tidx(a, k, kyp, kxq)] : bp;
-    xp = make_double2(fma(-bp, xp.x, g1.x), fma(-bp, xp.y, g1.y));
-    xq = make_double2(fma(-bq, xq.x, g2.x), fma(-bq, xq.y, g2.y));
-    if (j0) {  // pack back: Z(ky) = P + i Q, Z(Ny-ky) = conj P + i conj Q
-      a.S[sidx(a, k, kyp, 0)] = make_double2(xp.x - xq.y, xp.y + xq.x);
-      if (!self) a.S[sidx(a, k, kyq, 0)] = make_double2(xp.x + xq.y, xq.x - xp.y);
-    } else {
-      a.S[sidx(a, k, kyp, j)] = xp;
-      a.S[sidx(a, k, kyq, j)] = xq;
+  }
+  const double nu = sing ? a.sing_sc * (gam - mu * a.sing_cg) : 0.0;
+
+  // backward: x_k = g_k - (C_k/piv_k) x_{k+1}, from the top wall down
+  double2 qg[kPrefetch];
+  double qbx[kPrefetch], qby[kPrefetch];
+  double2* const s1 = s0 + (long long)(nz - 1) * rs;
+  const double* const bx1 = bx0 + (long long)(nz - 1) * rt;
+  const double* const by1 = by0 + (long long)(nz - 1) * rt;
+#pragma unroll
+  for (int i = 0; i < kPrefetch; ++i) {
+    if (i < nz) {
+      qg[i] = s1[-i * rs];
+      qbx[i] = bx1[-i * rt];
+      qby[i] = by1[-i * rt];
+    }
+  }
+  const double2* pg = s1 - kPrefetch * rs;
+  const double* pbx = bx1 - kPrefetch * rt;
+  const double* pby = by1 - kPrefetch * rt;
+  ps = s1;
+  double2 x = make_double2(0.0, 0.0);
+  for (int r = 0; r < nz; r += kPrefetch) {
+#pragma unroll
+    for (int i = 0; i < kPrefetch; ++i) {
+      if (r + i >= nz) break;
+      const double2 gg = qg[i];
+      const double bx = qbx[i], by = qby[i];
+      if (r + i + kPrefetch < nz) {
+        qg[i] = *pg;
+        qbx[i] = *pbx;
+        qby[i] = *pby;
+      }
+      pg -= rs;
+      pbx -= rt;
+      pby -= rt;
+      x = make_double2(fma(-bx, x.x, gg.x), fma(-by, x.y, gg.y));
+      double2 out = x;
+      if (sing) out.x = fma(-mu, a.sing[2 * nz + (nz - 1 - r - i)], out.x) - nu;
+      *ps = out;
+      ps -= rs;
     }
   }
 }
@@ -136,22 +170,23 @@ cudaError_t launch_thomas(const cfs_plan* P, double* data, cudaStream_t st) {
   a.S = reinterpret_cast<double2*>(data);
   a.fwd = P->d_fwd;
   a.bwd = P->d_bwd;
-  a.dzf = P->d_dzf;
+  a.sing = P->d_sing;
+  a.sing_cg = P->sing_cg;
+  a.sing_sc = P->sing_sc;
   a.M = P->M;
   a.ny = P->ny;
   a.nz = P->nz;
   a.nky = P->nky;
+  a.nblk_x = (P->M + kThomasBlock - 1) / kThomasBlock;
   a.neumann = (P->bc == CFS_BC_NEUMANN);
-  dim3 grid((P->M + 127) / 128, P->nky);
-  thomas_kernel<<<grid, 128, 0, st>>>(a);
+  thomas_kernel<<<a.nblk_x * P->ny, kThomasBlock, 0, st>>>(a);
   return cudaGetLastError();
 }
 
 // ----------------------------------------------------------------------------
 // Plan-time factorisation, one thread per (kx, kyp), FP64 with true division.
-// The x-pair kx = 0 and kx = M (untangled from the packed column, which
-// doubles them) take s/2.  The Neumann (0, 0) system is pinned: row 0 becomes
-// F_0 = 0 (B_0 -> 1, C_0 -> 0).
+// The Neumann (0, 0) system is pinned: row 0 becomes F_0 = 0 (B_0 -> 1,
+// C_0 -> 0).
 // ----------------------------------------------------------------------------
 __global__ void thomas_factor_kernel(double2* fwd, double* bwd, const double* A, const double* B,
                                      const double* C, const double* lamx, const double* lamy,
@@ -160,7 +195,7 @@ __global__ void thomas_factor_kernel(double2* fwd, double* bwd, const double* A,
   const int kyp = blockIdx.y;
   if (kx > M) return;
   const double lam = lamx[kx] + lamy[kyp];
-  const double sc = (kx == 0 || kx == M) ? 0.5 * s : s;
+  const double sc = s;
   const bool pin = neumann && kx == 0 && kyp == 0;
   double piv = 1.0, cprev = 0.0;
   for (int k = 0; k < nz; ++k) {
