@@ -43,8 +43,8 @@ CFG = synth.CHANNEL
 STAGES = ["x_forward", "y_forward", "z_thomas", "y_inverse", "x_inverse", "pcr_u", "pcr_v", "pcr_w"]
 KERNEL_OF_STAGE = {"x_forward": "rfft_x_kernel<false>", "y_forward": "fft_y_kernel<false>",
                    "z_thomas": "thomas_kernel", "y_inverse": "fft_y_kernel<true>",
-                   "x_inverse": "rfft_x_kernel<true>", "pcr_u": "pcr_kernel<16>",
-                   "pcr_v": "pcr_kernel<16>", "pcr_w": "pcr_kernel<16>"}
+                   "x_inverse": "rfft_x_kernel<true>", "pcr_u": "pcr_kernel",
+                   "pcr_v": "pcr_kernel", "pcr_w": "pcr_kernel"}
 SOURCE_OF_STAGE = {"x_forward": "fft_x.cu", "x_inverse": "fft_x.cu", "y_forward": "fft_y.cu",
                    "y_inverse": "fft_y.cu", "z_thomas": "thomas.cu", "pcr_u": "pcr.cu",
                    "pcr_v": "pcr.cu", "pcr_w": "pcr.cu"}

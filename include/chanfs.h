@@ -106,9 +106,9 @@ int cfs_poisson_solve(cfs_plan_t plan, const double* f, double* p,
  * reduced 2*nparts boundary system, computed on the host in FP64 and cached
  * in the plan under (c, loc, nparts).  nparts = 0 picks a partition count.
  *   c  the coefficient of Eq. 11 (gamma_k nu dt / 2, i.e. alpha nu dt), >= 0.
- * Each partition needs 3..32 rows, at most 32 partitions of up to 16 rows or
- * 12 partitions of up to 32 rows (registers), so a column has at most 512
- * unknowns; otherwise EUNSUPPORTED.
+ * Each partition needs at least 3 rows; at most 64 partitions and 1024
+ * unknowns per column (a tile of 16 columns lives in shared memory);
+ * otherwise EUNSUPPORTED.
  * Calling it is optional: cfs_helmholtz_solve prepares on a cache miss.
  */
 int cfs_helmholtz_prepare(cfs_plan_t plan, double c, int loc, int nparts);

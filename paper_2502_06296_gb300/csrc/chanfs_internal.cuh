@@ -19,9 +19,8 @@ constexpr int kMaxPasses = 16;     // radix passes of one FFT
 constexpr int kMaxNx = 4096;       // x cells (complex length nx/2 <= 2048)
 constexpr int kMaxNy = 1024;       // y cells
 constexpr int kMaxNz = 16384;      // z cells
-constexpr int kPcrMaxParts = 32;   // warps of the PCR kernel
-constexpr int kPcrMaxRows = 32;    // rows held in registers per partition
-constexpr int kPcrMaxPartsWide = 12;  // warps when a partition has 17..32 rows
+constexpr int kPcrMaxParts = 64;   // z-partitions (half-warps) of the PCR kernel
+constexpr int kPcrMaxUnknowns = 1024;  // rows of a PCR tile in shared memory
 
 // Device status bits (plan->d_status)
 constexpr int kErrTmaTimeout = 1;
@@ -117,6 +116,7 @@ cudaError_t launch_thomas_factor(cfs_plan* P, const double* dA, const double* dB
                                  cudaStream_t st);
 cudaError_t launch_pcr(const cfs_plan* P, const HelmCoef& h, const double* rhs, double* u,
                        cudaStream_t st);
+size_t pcr_smem_bytes(int n, int nparts);
 
 // ----------------------------------------------------------------------------
 // Device helpers

@@ -1,44 +1,85 @@
 // pcr.cu -- z-implicit Helmholtz solve (I - c L_z) u = rhs (Eq. 11) by the
 // reworked parallel cyclic reduction of Algorithm 2, Steps 2-4.
 //
-// Mapping: a CTA has one warp per z-partition and 32 lanes = 32 consecutive
-// (x, y) columns, so every row access of a warp is one contiguous 256-byte
-// run.  Each thread keeps its partition's m <= MMAX rows in registers:
-//   Step 2: forward  d_i -= alpha_i d_{i-1}   (i = 2..m-1),
-//           backward d_i -= beta_i  d_{i+1}   (i = m-3..0),
-//   Step 3: the 2*nparts boundary unknowns of each column go to shared
-//           memory; warp 0 solves every column's reduced tridiagonal system
-//           (one lane per column) with the LU factors prepared on the host,
+// A CTA works on tiles of 16 consecutive (x, y) columns x all n rows.  The
+// Tensor Memory Accelerator copies a tile into shared memory (boxes of 16
+// doubles x <= 256 rows, 128-byte rows) and writes the result back, so the
+// kernel never stages data through registers.  Threads: one half-warp per
+// z-partition, one lane per column; each thread runs its partition's
+// recurrences in shared memory (conflict-free: a half-warp touches one
+// 128-byte row).
+//   Step 2: forward  d_i -= alpha_i d_{i-1}  (i = 2..m-1),
+//           backward d_i -= beta_i  d_{i+1}  (i = m-3..0),
+//   Step 3: the 2p boundary unknowns of each column go to a small array;
+//           16 lanes of warp 0 solve the reduced tridiagonal systems with the
+//           LU factors prepared on the host,
 //   Step 4: d_i = ib_i d_i - ap_i x_0 - cp_i x_{m-1}.
 // Only the right-hand side changes at run time (the point of Algorithm 2):
 // 5 FP64 instructions per unknown, no division.  The coefficients, identical
-// for every column, are staged once per CTA in shared memory and read as
-// warp-uniform broadcasts.  CTAs loop over column tiles.
+// for every column, are staged once per CTA and read as broadcasts.  CTAs are
+// persistent over tiles; several CTAs per SM overlap one CTA's serial phases
+// (copies, the reduced solve) with another's arithmetic.
 #include "chanfs_internal.cuh"
 
 namespace chanfs {
 
+constexpr int kPcrCols = 16;  // columns per tile (one half-warp)
+
 struct PcrArgs {
-  const double* rhs;
-  double* u;
-  long long ncols;  // Nx * Ny
-  int n;            // unknowns per column
+  double* u;           // output field (for the face wall row)
+  long long ncols;     // Nx * Ny
+  int n;               // unknowns per column
   int nparts;
-  int face;         // face-located field: slot nz-1 is the wall, written 0
+  int face;            // face-located field: slot nz-1 is the wall, written 0
   int nz;
+  int by, nbox;        // rows per TMA box, boxes per tile
   const double* rows;  // alpha | beta | ib | ap | cp  (5n)
-  const double* red;   // rl | rip | ripc            (3 * 2 nparts)
-  int start[kPcrMaxParts + 1];
+  const double* red;   // rl | rip | ripc             (3 * 2p)
 };
 
-// MMAX = 16: up to 32 warps at <= 64 registers; MMAX = 32: up to 12 warps.
-template <int MMAX>
-__global__ void __launch_bounds__(MMAX == 16 ? 1024 : 384) pcr_kernel(PcrArgs a) {
-  extern __shared__ __align__(16) double sm[];
+__device__ __forceinline__ void pcr_mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
+}
+
+__device__ __forceinline__ void pcr_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool pcr_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_u32(bar);
+  for (uint32_t it = 0; it < (1u << 24); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(1024) pcr_kernel(const __grid_constant__ CUtensorMap in_map,
+                                                   const __grid_constant__ CUtensorMap out_map,
+                                                   PcrArgs a, int* status) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int n = a.n, J = 2 * a.nparts;
-  double* s_rows = sm;             // 5n
-  double* s_red = s_rows + 5 * n;  // 3J
-  double* s_x = s_red + 3 * J;     // J x 32 boundary values
+  const int rows_alloc = a.nbox * a.by;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  double* T = reinterpret_cast<double*>(smem_raw + 128);  // tile [rows_alloc][16]
+  double* s_rows = T + rows_alloc * kPcrCols;               // 5n
+  double* s_red = s_rows + 5 * n;                           // 3J
+  double* s_x = s_red + 3 * J;                              // J x 16
+
+  if (threadIdx.x == 0) {
+    pcr_mbar_init(bar);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
   for (int e = threadIdx.x; e < 5 * n; e += blockDim.x) s_rows[e] = a.rows[e];
   for (int e = threadIdx.x; e < 3 * J; e += blockDim.x) s_red[e] = a.red[e];
   __syncthreads();
@@ -51,101 +92,164 @@ __global__ void __launch_bounds__(MMAX == 16 ? 1024 : 384) pcr_kernel(PcrArgs a)
   const double* rip = s_red + J;
   const double* ripc = s_red + 2 * J;
 
-  const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
-  const int s = a.start[q], m = a.start[q + 1] - s;
-  const long long ntiles = (a.ncols + 31) / 32;
+  const int c = threadIdx.x % kPcrCols;  // column within the tile
+  const int q = threadIdx.x / kPcrCols;  // partition
+  // partition q covers rows [q n / p, (q+1) n / p) (the rule the host used)
+  const int s = (int)(((long long)q * n) / a.nparts);
+  const int m = (int)(((long long)(q + 1) * n) / a.nparts) - s;
+  const long long ntiles = (a.ncols + kPcrCols - 1) / kPcrCols;
+  const uint32_t tile_bytes = (uint32_t)(a.nbox * a.by * kPcrCols * sizeof(double));
+  uint32_t phase = 0;
 
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long col = tile * 32 + lane;
-    const bool live = col < a.ncols;
-    double v[MMAX];
-#pragma unroll
-    for (int i = 0; i < MMAX; ++i)
-      v[i] = (live && i < m) ? a.rhs[(long long)(s + i) * a.ncols + col] : 0.0;
-    // Step 2, forward then backward reduction of d only
-#pragma unroll
-    for (int i = 2; i < MMAX; ++i)
-      if (i < m) v[i] = fma(-alpha[s + i], v[i - 1], v[i]);
-#pragma unroll
-    for (int i = MMAX - 3; i >= 0; --i)
-      if (i <= m - 3) v[i] = fma(-beta[s + i], v[i + 1], v[i]);
-    // v[m-1] without a run-time index (which would demote v to local memory)
-    unsigned long long lastbits = 0ull;
-#pragma unroll
-    for (int i = 2; i < MMAX; ++i)
-      lastbits |= (unsigned long long)__double_as_longlong(v[i]) &
-                  (0ull - (unsigned long long)(i == m - 1));
-    const double vlast = __longlong_as_double((long long)lastbits);
-    s_x[(2 * q) * 32 + lane] = v[0];
-    s_x[(2 * q + 1) * 32 + lane] = vlast;
+    const int col0 = (int)(tile * kPcrCols);
+    if (threadIdx.x == 0) {
+      pcr_expect_tx(bar, tile_bytes);
+      for (int b = 0; b < a.nbox; ++b) {
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(T + b * a.by * kPcrCols)),
+            "l"(reinterpret_cast<uint64_t>(&in_map)), "r"(smem_u32(bar)), "r"(col0), "r"(b * a.by)
+            : "memory");
+      }
+    }
+    const int ok = __syncthreads_and(pcr_wait(bar, phase) ? 1 : 0);
+    phase ^= 1u;
+    if (!ok) {
+      if (threadIdx.x == 0) atomicOr(status, kErrTmaTimeout);
+      return;
+    }
+    double* col = T + c;  // element (row r) at col[r * 16]
+    // Step 2: forward then backward reduction of d only
+    {
+      double prev = col[(s + 1) * kPcrCols];
+      for (int i = 2; i < m; ++i) {
+        const int r = s + i;
+        prev = fma(-alpha[r], prev, col[r * kPcrCols]);
+        col[r * kPcrCols] = prev;
+      }
+      double next = col[(s + m - 2) * kPcrCols];
+      for (int i = m - 3; i >= 0; --i) {
+        const int r = s + i;
+        next = fma(-beta[r], next, col[r * kPcrCols]);
+        col[r * kPcrCols] = next;
+      }
+      s_x[(2 * q) * kPcrCols + c] = col[s * kPcrCols];
+      s_x[(2 * q + 1) * kPcrCols + c] = col[(s + m - 1) * kPcrCols];
+    }
     __syncthreads();
-    // Step 3, reduced system [x_0^0, x_{m-1}^0, x_0^1, ...] per column
-    if (q == 0) {
-      double y = s_x[lane];
+    // Step 3: reduced system [x_0^0, x_{m-1}^0, x_0^1, ...], one lane per column
+    if (threadIdx.x < kPcrCols) {
+      double y = s_x[c];
       for (int jj = 1; jj < J; ++jj) {
-        y = fma(-rl[jj], y, s_x[jj * 32 + lane]);
-        s_x[jj * 32 + lane] = y;
+        y = fma(-rl[jj], y, s_x[jj * kPcrCols + c]);
+        s_x[jj * kPcrCols + c] = y;
       }
       double x = rip[J - 1] * y;
-      s_x[(J - 1) * 32 + lane] = x;
+      s_x[(J - 1) * kPcrCols + c] = x;
       for (int jj = J - 2; jj >= 0; --jj) {
-        x = fma(-ripc[jj], x, rip[jj] * s_x[jj * 32 + lane]);
-        s_x[jj * 32 + lane] = x;
+        x = fma(-ripc[jj], x, rip[jj] * s_x[jj * kPcrCols + c]);
+        s_x[jj * kPcrCols + c] = x;
       }
     }
     __syncthreads();
-    // Step 4, reconstruction
-    const double x0 = s_x[(2 * q) * 32 + lane];
-    const double xm = s_x[(2 * q + 1) * 32 + lane];
-    if (live) {
-      double* out = a.u + col;
-#pragma unroll
-      for (int i = 0; i < MMAX; ++i) {
-        if (i < m) {
-          double r;
-          if (i == 0) r = x0;
-          else if (i == m - 1) r = xm;
-          else r = fma(-cp[s + i], xm, fma(-ap[s + i], x0, ib[s + i] * v[i]));
-          out[(long long)(s + i) * a.ncols] = r;
-        }
+    // Step 4: reconstruction in place
+    {
+      const double x0 = s_x[(2 * q) * kPcrCols + c];
+      const double xm = s_x[(2 * q + 1) * kPcrCols + c];
+      col[s * kPcrCols] = x0;
+      col[(s + m - 1) * kPcrCols] = xm;
+      for (int i = 1; i <= m - 2; ++i) {
+        const int r = s + i;
+        col[r * kPcrCols] = fma(-cp[r], xm, fma(-ap[r], x0, ib[r] * col[r * kPcrCols]));
       }
-      if (a.face && q == a.nparts - 1) out[(long long)(a.nz - 1) * a.ncols] = 0.0;
     }
-    __syncthreads();  // s_x is reused by the next tile
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int b = 0; b < a.nbox; ++b) {
+        asm volatile(
+            "cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                reinterpret_cast<uint64_t>(&out_map)),
+            "r"(smem_u32(T + b * a.by * kPcrCols)), "r"(col0), "r"(b * a.by)
+            : "memory");
+      }
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // tile may be reused
+    }
+    if (a.face && threadIdx.x < kPcrCols && col0 + c < a.ncols)
+      a.u[(long long)(a.nz - 1) * a.ncols + col0 + c] = 0.0;
+    __syncthreads();
   }
 }
 
-template <int MMAX>
-static cudaError_t launch_pcr_t(const PcrArgs& a, cudaStream_t st) {
-  const size_t smem = sizeof(double) * (size_t)(5 * a.n + 3 * 2 * a.nparts + 2 * a.nparts * 32);
-  cudaFuncSetAttribute(pcr_kernel<MMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int dev = 0, nsm = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcr_kernel<MMAX>, 32 * a.nparts, smem);
-  if (per_sm < 1) per_sm = 1;
-  const long long ntiles = (a.ncols + 31) / 32;
-  long long grid = (long long)nsm * per_sm;
-  if (grid > ntiles) grid = ntiles;
-  pcr_kernel<MMAX><<<(unsigned)grid, 32 * a.nparts, smem, st>>>(a);
-  return cudaGetLastError();
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn pcr_encode() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &qr) == cudaSuccess &&
+        qr == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 2-D map over the first n rows of a field: ncols doubles per row.
+static bool pcr_map(CUtensorMap* map, const void* base, long long ncols, int n, int by) {
+  EncodeTiledFn enc = pcr_encode();
+  if (!enc) return false;
+  cuuint64_t gdim[2] = {(cuuint64_t)ncols, (cuuint64_t)n};
+  cuuint64_t gstride[1] = {(cuuint64_t)ncols * sizeof(double)};
+  cuuint32_t box[2] = {(cuuint32_t)kPcrCols, (cuuint32_t)by};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void*>(base), gdim, gstride, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+size_t pcr_smem_bytes(int n, int nparts) {
+  const int nbox = (n + 255) / 256;
+  const int by = (n + nbox - 1) / nbox;
+  return 128 + sizeof(double) * ((size_t)nbox * by * kPcrCols + 5 * (size_t)n + 6 * (size_t)nparts +
+                                 2 * (size_t)nparts * kPcrCols);
 }
 
 cudaError_t launch_pcr(const cfs_plan* P, const HelmCoef& h, const double* rhs, double* u,
                        cudaStream_t st) {
   PcrArgs a;
-  a.rhs = rhs;
   a.u = u;
   a.ncols = (long long)P->nx * P->ny;
   a.n = h.n;
   a.nparts = h.nparts;
   a.face = (h.loc == CFS_LOC_FACE);
   a.nz = P->nz;
+  a.nbox = (h.n + 255) / 256;
+  a.by = (h.n + a.nbox - 1) / a.nbox;
   a.rows = h.d_rows;
   a.red = h.d_red;
-  for (int i = 0; i <= kPcrMaxParts; ++i) a.start[i] = (i <= h.nparts) ? h.start[i] : h.n;
-  if (h.mmax <= 16) return launch_pcr_t<16>(a, st);
-  return launch_pcr_t<32>(a, st);
+  CUtensorMap in_map, out_map;
+  if (!pcr_map(&in_map, rhs, a.ncols, h.n, a.by) || !pcr_map(&out_map, u, a.ncols, h.n, a.by))
+    return cudaErrorInvalidValue;
+  const size_t smem = pcr_smem_bytes(h.n, h.nparts);
+  const int threads = kPcrCols * h.nparts;
+  cudaFuncSetAttribute(pcr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcr_kernel, threads, smem);
+  if (per_sm < 1) per_sm = 1;
+  const long long ntiles = (a.ncols + kPcrCols - 1) / kPcrCols;
+  long long grid = (long long)nsm * per_sm;
+  if (grid > ntiles) grid = ntiles;
+  pcr_kernel<<<(unsigned)grid, threads, smem, st>>>(in_map, out_map, a, P->d_status);
+  return cudaGetLastError();
 }
 
 }  // namespace chanfs

@@ -376,9 +376,8 @@ static HelmCoef* helm_find(cfs_plan* P, double c, int loc, int nparts) {
 }
 
 static int auto_parts(int n) {
-  // up to 16 rows per partition (the register-only variant of the kernel);
-  // larger partitions (17..32 rows, at most 12) are available on request
-  int p = (n + 15) / 16;
+  // about 32 rows per partition, at least 3
+  int p = (n + 31) / 32;
   if (p > kPcrMaxParts) p = kPcrMaxParts;
   if (p < 1) p = 1;
   while (p > 1 && n / p < 3) --p;
@@ -401,7 +400,9 @@ static int helm_prepare(cfs_plan* P, double c, int loc, int nparts, HelmCoef** r
     B[i] = 1.0 - c * B[i];
     C[i] = -c * C[i];
   }
+  if (n < 3 || n > kPcrMaxUnknowns) return CFS_EUNSUPPORTED;
   const int np = nparts ? nparts : auto_parts(n);
+  if (pcr_smem_bytes(n, np) > 227 * 1024) return CFS_EUNSUPPORTED;
   HelmCoef h;
   memset(&h, 0, sizeof(h));
   h.c = c;
@@ -412,10 +413,9 @@ static int helm_prepare(cfs_plan* P, double c, int loc, int nparts, HelmCoef** r
   for (int q = 0; q <= np; ++q) h.start[q] = (int)(((long long)q * n) / np);
   for (int q = 0; q < np; ++q) {
     const int m = h.start[q + 1] - h.start[q];
-    if (m < 3 || m > kPcrMaxRows) return CFS_EUNSUPPORTED;
+    if (m < 3) return CFS_EUNSUPPORTED;
     h.mmax = std::max(h.mmax, m);
   }
-  if (h.mmax > 16 && np > kPcrMaxPartsWide) return CFS_EUNSUPPORTED;
   std::vector<double> rows(5 * (size_t)n, 0.0);
   double* alpha = rows.data();
   double* beta = alpha + n;

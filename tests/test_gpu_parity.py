@@ -185,6 +185,9 @@ HELM_CASES = [
     (4, 3, 3, None, 0, 1),        # smallest column
     (6, 4, 4, None, 1, 1),        # face: 3 unknowns
     (48, 36, 512, 2.0, 0, 32),    # 512 unknowns, 32 partitions
+    (16, 12, 1024, 1.8, 0, 0),    # largest column, 4 TMA boxes
+    (16, 12, 700, 1.6, 1, 64),    # 64 partitions, ragged boxes
+    (6, 3, 40, 1.2, 0, 1),        # one partition: Algorithm 2 degenerates to Thomas
 ]
 
 
@@ -228,13 +231,14 @@ def test_helmholtz_rejects_unsupported_partitions(chanfs):
     with chanfs.Plan(8, 8, 40, 1.0, 1.0, np.full(40, 0.05)) as plan:
         with pytest.raises(chanfs.ChanfsError):
             plan.helmholtz_prepare(1e-3, 0, 20)   # 2 rows per partition
-        with pytest.raises(chanfs.ChanfsError):
-            plan.helmholtz_prepare(1e-3, 0, 1)    # 40 rows in one partition
+        plan.helmholtz_prepare(1e-3, 0, 1)        # one partition of 40 rows is fine
         with pytest.raises(chanfs.ChanfsError):
             plan.helmholtz_prepare(-1.0, 0, 0)
-    with chanfs.Plan(8, 8, 600, 1.0, 1.0, np.full(600, 2 / 600)) as plan:
+    with chanfs.Plan(8, 8, 1100, 1.0, 1.0, np.full(1100, 2 / 1100)) as plan:
         with pytest.raises(chanfs.ChanfsError):
-            plan.helmholtz_prepare(1e-3, 0, 0)    # 600 unknowns > 512
+            plan.helmholtz_prepare(1e-3, 0, 0)    # 1100 unknowns > 1024
+        with pytest.raises(chanfs.ChanfsError):
+            plan.helmholtz_prepare(1e-3, 0, 65)   # more than 64 partitions
 
 
 def test_host_buffer_entry_points_match_device_path(chanfs):
