@@ -52,7 +52,10 @@ typedef enum {
 
 typedef enum { CFS_BC_NEUMANN = 0, CFS_BC_DIRICHLET = 1 } cfs_bc;   /* z walls */
 typedef enum { CFS_LOC_CENTER = 0, CFS_LOC_FACE = 1 } cfs_loc;      /* z location */
-typedef enum { CFS_F64 = 0 } cfs_dtype;                             /* arithmetic */
+typedef enum {
+  CFS_F64 = 0,          /* FP64 transforms and sweeps */
+  CFS_F32_REFINED = 1   /* FP32 transforms and sweeps + FP64 iterative refinement */
+} cfs_dtype;
 
 /* Library version (CHANFS_VERSION of the build). */
 int cfs_version(void);
@@ -69,7 +72,10 @@ const char* cfs_status_string(int status);
  *   lx,ly  domain lengths (> 0); dx = lx/nx, dy = ly/ny.
  *   dz     nz HOST doubles, the cell widths along z (all > 0); copied.
  *   poisson_bc  z-wall condition of the Poisson equation (cfs_bc).
- *   dtype  CFS_F64.
+ *   dtype  CFS_F64, or CFS_F32_REFINED: solves run FP32 transforms and
+ *          sweeps and recover FP64 accuracy by iterative refinement (see
+ *          cfs_plan_set_refinement); the plan then also holds FP32 tables and
+ *          one FP32 work field, and nx must be a multiple of 4.
  * At creation the plan computes, in FP64 and once (the time-invariant
  * pre-processing of Sec. 2.2.4): the z metrics, the modified wavenumbers
  * 2(cos(2 pi k/N) - 1)/h^2 re-ordered to the packed layout (App. A), the FFT
@@ -169,6 +175,23 @@ int cfs_poisson_solve_host(cfs_plan_t plan, const double* f, double* p,
                            void* stream);
 int cfs_helmholtz_solve_host(cfs_plan_t plan, double c, int loc,
                              const double* rhs, double* u, void* stream);
+
+/*
+ * Iterative refinement (plans created with CFS_F32_REFINED).  A solve starts
+ * from x = 0 and repeats { delta = FP32 solve of r; x += delta in FP64;
+ * r = b - A x in FP64 } until ||r||_inf <= tol ||b||_inf or `maxit` FP32
+ * solves were done (defaults: tol = 1e-10, maxit = 4).  A is the staggered
+ * 7-point Laplacian (Poisson; b is the right-hand side minus its dz-weighted
+ * mean for Neumann walls) or I - c L_z (Helmholtz).  FP64 is used for the
+ * residual, the accumulation, the coefficient pre-processing and the z sweep
+ * of the near-singular low-wavenumber columns.  Each iteration reads the
+ * residual norm back, so refined solves synchronise `stream`; when the
+ * target is missed the solve returns CFS_ENOTCONVERGED with its best x.
+ * cfs_last_info reports the FP32 solves done and the final relative residual
+ * of the last refined solve.
+ */
+int cfs_plan_set_refinement(cfs_plan_t plan, double tol, int maxit);
+int cfs_last_info(cfs_plan_t plan, int* iters, double* rel_residual);
 
 /*
  * cfs_plan_check -- wait for the device and report device-side failures

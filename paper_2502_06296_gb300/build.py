@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "libchanfs.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
          "-Xcompiler", "-Wall"]
-SOURCES = ["plan.cu", "fft_x.cu", "fft_y.cu", "thomas.cu", "pcr.cu"]
+SOURCES = ["plan.cu", "fft_x.cu", "fft_y.cu", "thomas.cu", "pcr.cu", "refine.cu"]
 
 
 def _nvcc() -> str:
@@ -63,7 +63,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             for s, err in ex.map(compile_one, jobs):
                 logs.append(f"== {os.path.basename(s)}\n{err}")
-        with open(os.path.join(BUILD, "ptxas.log"), "a") as fh:
+        with open(os.path.join(BUILD, "ptxas.log"), "w") as fh:
             fh.write("\n".join(logs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"

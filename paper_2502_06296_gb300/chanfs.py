@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libchanfs.so")
 
 NEUMANN, DIRICHLET = 0, 1
 CENTER, FACE = 0, 1
-F64 = 0
+F64, F32_REFINED = 0, 1
 
 X_FORWARD, Y_FORWARD, Z_SOLVE, Y_INVERSE, X_INVERSE = 0, 1, 2, 3, 4
 
@@ -58,6 +58,8 @@ def lib():
             "cfs_helmholtz_solve_host": ([vp, d, i, vp, vp, vp], i),
             "cfs_plan_check": ([vp, ctypes.POINTER(i)], i),
             "cfs_poisson_stage": ([vp, i, vp, vp, vp], i),
+            "cfs_plan_set_refinement": ([vp, d, i], i),
+            "cfs_last_info": ([vp, ctypes.POINTER(i), ctypes.POINTER(d)], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -98,6 +100,7 @@ class Plan:
 
     def __init__(self, nx: int, ny: int, nz: int, lx: float, ly: float, dz, bc: int = NEUMANN,
                  dtype: int = F64):
+        self.dtype = dtype
         dz = np.ascontiguousarray(dz, dtype=np.float64)
         if dz.size != nz:
             raise ValueError("dz must have nz entries")
@@ -193,6 +196,16 @@ class Plan:
                                               _host_ptr(out, self.shape), _stream_ptr(stream)),
                "cfs_helmholtz_solve_host")
         return out
+
+    def set_refinement(self, tol: float = 1e-10, maxit: int = 4):
+        """Refined plans: stop at ||r||_inf <= tol ||b||_inf or after maxit FP32 solves."""
+        _check(lib().cfs_plan_set_refinement(self._h, float(tol), int(maxit)), "cfs_plan_set_refinement")
+
+    def last_info(self):
+        """(FP32 solves, final relative residual) of the last refined solve."""
+        it, rho = ctypes.c_int(0), ctypes.c_double(0.0)
+        _check(lib().cfs_last_info(self._h, ctypes.byref(it), ctypes.byref(rho)), "cfs_last_info")
+        return it.value, rho.value
 
     def check(self) -> int:
         """Synchronise and return the device failure bits (raises on failure)."""

@@ -3,66 +3,74 @@
 // imaginary slot of X_0).
 //
 // A line of nx = 2M reals is read as M complex numbers z_n = x_{2n} + i x_{2n+1}
-// with 128-bit loads, transformed by an M-point complex Stockham FFT in shared
-// memory, and untangled into the half spectrum:
+// with 128-bit (FP64) or 64-bit (FP32) loads, transformed by an M-point complex
+// Stockham FFT in shared memory, and untangled into the half spectrum:
 //   X_k = E/2 - i (W^k/2) O,  X_{M-k} = conj(E/2 + i (W^k/2) O) ... (forward)
 // with E = Z_k + conj Z_{M-k}, O = Z_k - conj Z_{M-k}, W = exp(-2 pi i/nx).
 // The inverse runs the same steps backwards.  Consecutive lines (y, z) are
 // contiguous, so a CTA's block of `lb` lines is one contiguous span.
 // in and out may alias (the inverse runs in place): no __restrict__ on them.
-#include "chanfs_internal.cuh"
+//
+// C = double2 is the FP64 solve.  C = float2 is the inner solve of iterative
+// refinement; its inverse can write the FP64 result directly (OUT_SET) or add
+// it to an FP64 field (OUT_ADD), the correction step p += delta.
+#include "chanfs_fft.cuh"
 
 namespace chanfs {
 
-template <bool INV>
-__global__ void __launch_bounds__(128) rfft_x_kernel(const double2* in,
-                                                     double2* out, long long nlines,
-                                                     FftDesc d, const double2* __restrict__ twg,
-                                                     const double2* __restrict__ postg, int lb,
+enum { OUT_SAME = 0, OUT_SET = 1, OUT_ADD = 2 };
+
+template <bool INV, class C, int OUT>
+__global__ void __launch_bounds__(128) rfft_x_kernel(const C* in, void* outv, long long nlines,
+                                                     FftDesc d, const C* __restrict__ twg,
+                                                     const C* __restrict__ postg, int lb,
                                                      double scale, int scaled) {
+  using T = typename cscal<C>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int M = d.n;
   const int bs = M;  // batch stride (complex)
-  double2* buf0 = reinterpret_cast<double2*>(smem_raw);
-  double2* buf1 = buf0 + lb * bs;
-  double2* tw = buf1 + lb * bs;
-  double2* post = tw + d.ntw;
+  C* buf0 = reinterpret_cast<C*>(smem_raw);
+  C* buf1 = buf0 + lb * bs;
+  C* tw = buf1 + lb * bs;
+  C* post = tw + d.ntw;
   const int npost = M / 2 + 1;
 
   for (int e = threadIdx.x; e < d.ntw; e += blockDim.x) tw[e] = twg[e];
   for (int e = threadIdx.x; e < npost; e += blockDim.x) post[e] = postg[e];
 
   const long long line0 = (long long)blockIdx.x * lb;
-  const double2 zero = make_double2(0.0, 0.0);
+  const C zero = mkc<C>(T(0), T(0));
+  const T h = T(0.5);
 
   if (!INV) {
+    C* out = reinterpret_cast<C*>(outv);
     // contiguous span of lb*M complex values
-    const double2* src = in + line0 * M;
+    const C* src = in + line0 * M;
     for (int e = threadIdx.x; e < lb * M; e += blockDim.x) {
       int l = e / M;
       buf0[e] = (line0 + l < nlines) ? src[e] : zero;
     }
     __syncthreads();
-    double2* Z = stockham_smem<false, false>(buf0, buf1, d, lb, 1, bs, tw);
+    C* Z = stockham_smem<false, false>(buf0, buf1, d, lb, 1, bs, tw);
     // untangle the half-length spectrum into the packed real spectrum
     for (int e = threadIdx.x; e < lb * npost; e += blockDim.x) {
       int l = e / npost, k = e % npost;
       long long line = line0 + l;
       if (line >= nlines) continue;
-      const double2* z = Z + l * bs;
-      double2* o = out + line * M;
+      const C* z = Z + l * bs;
+      C* o = out + line * M;
       if (k == 0) {
-        double2 z0 = z[0];
-        o[0] = make_double2(z0.x + z0.y, z0.x - z0.y);  // (X_0, X_M)
+        C z0 = z[0];
+        o[0] = mkc<C>(z0.x + z0.y, z0.x - z0.y);  // (X_0, X_M)
         continue;
       }
-      double2 zk = z[k], zm = z[M - k];
-      double2 E = make_double2(zk.x + zm.x, zk.y - zm.y);
-      double2 O = make_double2(zk.x - zm.x, zk.y + zm.y);
-      double2 u = cmul(O, post[k]);           // (W^k/2) O
-      double2 t = make_double2(u.y, -u.x);    // -i (W^k/2) O
-      o[k] = make_double2(fma(0.5, E.x, t.x), fma(0.5, E.y, t.y));
-      if (M - k != k) o[M - k] = make_double2(fma(0.5, E.x, -t.x), fma(-0.5, E.y, t.y));
+      C zk = z[k], zm = z[M - k];
+      C E = mkc<C>(zk.x + zm.x, zk.y - zm.y);
+      C O = mkc<C>(zk.x - zm.x, zk.y + zm.y);
+      C u = cmul(O, post[k]);          // (W^k/2) O
+      C t = mkc<C>(u.y, -u.x);         // -i (W^k/2) O
+      o[k] = mkc<C>(fma(h, E.x, t.x), fma(h, E.y, t.y));
+      if (M - k != k) o[M - k] = mkc<C>(fma(h, E.x, -t.x), fma(-h, E.y, t.y));
     }
   } else {
     __syncthreads();  // the untangling factors are read right away
@@ -70,68 +78,101 @@ __global__ void __launch_bounds__(128) rfft_x_kernel(const double2* in,
     for (int e = threadIdx.x; e < lb * npost; e += blockDim.x) {
       int l = e / npost, k = e % npost;
       long long line = line0 + l;
-      double2* z = buf0 + l * bs;
+      C* z = buf0 + l * bs;
       if (line >= nlines) {
         z[k] = zero;
         if (k > 0) z[M - k] = zero;
         continue;
       }
-      const double2* x = in + line * M;
-      double2 zk, zm;
+      const C* x = in + line * M;
+      C zk, zm;
       if (k == 0) {
-        double2 x0 = x[0];  // (X_0, X_M)
-        zk = make_double2(0.5 * (x0.x + x0.y), 0.5 * (x0.x - x0.y));
+        C x0 = x[0];  // (X_0, X_M)
+        zk = mkc<C>(h * (x0.x + x0.y), h * (x0.x - x0.y));
         zm = zk;
       } else {
-        double2 xk = x[k], xm = x[M - k];
-        double2 E = make_double2(xk.x + xm.x, xk.y - xm.y);
-        double2 T = make_double2(xk.x - xm.x, xk.y + xm.y);
-        double2 u = cmulc(T, post[k]);  // conj(W^k/2) T
-        zk = make_double2(fma(0.5, E.x, -u.y), fma(0.5, E.y, u.x));
-        zm = make_double2(fma(0.5, E.x, u.y), fma(-0.5, E.y, u.x));
+        C xk = x[k], xm = x[M - k];
+        C E = mkc<C>(xk.x + xm.x, xk.y - xm.y);
+        C Tt = mkc<C>(xk.x - xm.x, xk.y + xm.y);
+        C u = cmulc(Tt, post[k]);  // conj(W^k/2) T
+        zk = mkc<C>(fma(h, E.x, -u.y), fma(h, E.y, u.x));
+        zm = mkc<C>(fma(h, E.x, u.y), fma(-h, E.y, u.x));
       }
       if (scaled) {
-        zk.x *= scale; zk.y *= scale;
-        zm.x *= scale; zm.y *= scale;
+        const T sc = T(scale);
+        zk.x *= sc; zk.y *= sc;
+        zm.x *= sc; zm.y *= sc;
       }
       z[k] = zk;
       if (k > 0 && M - k != k) z[M - k] = zm;
     }
     __syncthreads();
-    double2* res = stockham_smem<true, false>(buf0, buf1, d, lb, 1, bs, tw);
-    double2* dst = out + line0 * M;
-    for (int e = threadIdx.x; e < lb * M; e += blockDim.x) {
-      int l = e / M;
-      if (line0 + l < nlines) dst[e] = res[e];
+    C* res = stockham_smem<true, false>(buf0, buf1, d, lb, 1, bs, tw);
+    if (OUT == OUT_SAME) {
+      C* dst = reinterpret_cast<C*>(outv) + line0 * M;
+      for (int e = threadIdx.x; e < lb * M; e += blockDim.x) {
+        int l = e / M;
+        if (line0 + l < nlines) dst[e] = res[e];
+      }
+    } else {
+      double2* dst = reinterpret_cast<double2*>(outv) + line0 * M;
+      for (int e = threadIdx.x; e < lb * M; e += blockDim.x) {
+        int l = e / M;
+        if (line0 + l < nlines) {
+          const C r = res[e];
+          if (OUT == OUT_SET) {
+            dst[e] = make_double2((double)r.x, (double)r.y);
+          } else {
+            double2 p = dst[e];
+            dst[e] = make_double2(p.x + (double)r.x, p.y + (double)r.y);
+          }
+        }
+      }
     }
   }
 }
 
-static int x_lines_per_cta(int M) { return M >= 1024 ? 1 : 1024 / M; }
+static int x_lines_per_cta(int M, size_t csize) {
+  // about 16 KB of complex data per buffer
+  const int target = (int)(16384 / csize);
+  return M >= target ? 1 : target / M;
+}
 
-static size_t x_smem_bytes(const cfs_plan* P, int lb) {
-  return sizeof(double2) * (size_t)(2 * lb * P->M + P->fx.ntw + P->M / 2 + 1);
+template <class C, int OUT>
+static cudaError_t launch_x(const cfs_plan* P, const void* in, void* out, bool inverse,
+                            double scale, const C* tw, const C* post, cudaStream_t st) {
+  const long long nlines = (long long)P->ny * P->nz;
+  const int lb = x_lines_per_cta(P->M, sizeof(C));
+  const long long grid = (nlines + lb - 1) / lb;
+  const size_t smem = sizeof(C) * (size_t)(2 * lb * P->M + P->fx.ntw + P->M / 2 + 1);
+  const int scaled = (scale != 1.0);
+  const C* cin = reinterpret_cast<const C*>(in);
+  if (!inverse) {
+    auto k = rfft_x_kernel<false, C, OUT_SAME>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<(unsigned)grid, 128, smem, st>>>(cin, out, nlines, P->fx, tw, post, lb, scale, scaled);
+  } else {
+    auto k = rfft_x_kernel<true, C, OUT>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<(unsigned)grid, 128, smem, st>>>(cin, out, nlines, P->fx, tw, post, lb, scale, scaled);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_rfft_x(const cfs_plan* P, const double* in, double* out, bool inverse,
                           double scale, cudaStream_t st) {
-  const long long nlines = (long long)P->ny * P->nz;
-  const int lb = x_lines_per_cta(P->M);
-  const long long grid = (nlines + lb - 1) / lb;
-  const size_t smem = x_smem_bytes(P, lb);
-  const int scaled = (scale != 1.0);
-  if (!inverse) {
-    cudaFuncSetAttribute(rfft_x_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    rfft_x_kernel<false><<<(unsigned)grid, 128, smem, st>>>(
-        reinterpret_cast<const double2*>(in), reinterpret_cast<double2*>(out), nlines, P->fx,
-        P->d_twx, P->d_post, lb, scale, scaled);
-  } else {
-    cudaFuncSetAttribute(rfft_x_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    rfft_x_kernel<true><<<(unsigned)grid, 128, smem, st>>>(
-        reinterpret_cast<const double2*>(in), reinterpret_cast<double2*>(out), nlines, P->fx,
-        P->d_twx, P->d_post, lb, scale, scaled);
-  }
-  return cudaGetLastError();
+  return launch_x<double2, OUT_SAME>(P, in, out, inverse, scale, P->d_twx, P->d_post, st);
+}
+
+cudaError_t launch_rfft_x32(const cfs_plan* P, const float* in, float* out, bool inverse,
+                            cudaStream_t st) {
+  return launch_x<float2, OUT_SAME>(P, in, out, inverse, 1.0, P->d_twx32, P->d_post32, st);
+}
+
+cudaError_t launch_rfft_x32_to64(const cfs_plan* P, const float* in, double* out, bool add,
+                                 cudaStream_t st) {
+  if (add) return launch_x<float2, OUT_ADD>(P, in, out, true, 1.0, P->d_twx32, P->d_post32, st);
+  return launch_x<float2, OUT_SET>(P, in, out, true, 1.0, P->d_twx32, P->d_post32, st);
 }
 
 }  // namespace chanfs

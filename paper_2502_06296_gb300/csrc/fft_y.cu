@@ -9,7 +9,7 @@
 // Stockham passes with the columns as batches, and written back by TMA.
 // Out-of-range columns of a ragged last tile are zero-filled on load and
 // clipped on store by the TMA unit.
-#include "chanfs_internal.cuh"
+#include "chanfs_fft.cuh"
 
 namespace chanfs {
 
@@ -58,16 +58,17 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void*
       : "memory");
 }
 
-template <bool INV>
+template <bool INV, class C>
 __global__ void __launch_bounds__(128) fft_y_kernel(const __grid_constant__ CUtensorMap map,
-                                                    FftDesc d, const double2* __restrict__ twg,
+                                                    FftDesc d, const C* __restrict__ twg,
                                                     int tk, int by, int nbox, int* status) {
+  using T = typename cscal<C>::T;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-  double2* buf0 = reinterpret_cast<double2*>(smem_raw + 128);
-  double2* buf1 = buf0 + tk * d.n;
-  double2* tw = buf1 + tk * d.n;
-  const int x0 = 2 * tk * blockIdx.x;  // in doubles: 16-byte aligned coordinate
+  C* buf0 = reinterpret_cast<C*>(smem_raw + 128);
+  C* buf1 = buf0 + tk * d.n;
+  C* tw = buf1 + tk * d.n;
+  const int x0 = 2 * tk * blockIdx.x;  // in reals: a 16-byte aligned coordinate
   const int z = blockIdx.y;
 
   if (threadIdx.x == 0) {
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(128) fft_y_kernel(const __grid_constant__ CUte
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    mbar_expect_tx(bar, (uint32_t)(nbox * by * tk * sizeof(double2)));
+    mbar_expect_tx(bar, (uint32_t)(nbox * by * tk * sizeof(C)));
     for (int b = 0; b < nbox; ++b) tma_load_3d(buf0 + b * by * tk, &map, bar, x0, b * by, z);
   }
   for (int e = threadIdx.x; e < d.ntw; e += blockDim.x) tw[e] = twg[e];
@@ -96,20 +97,21 @@ __global__ void __launch_bounds__(128) fft_y_kernel(const __grid_constant__ CUte
   // F(0,ky) + i F(Nx/2,ky).  Every slot is then one column of Eq. 12.
   if (INV && blockIdx.x == 0) {  // re-tangle before the inverse transform
     for (int ky = 1 + threadIdx.x; 2 * ky < ny; ky += blockDim.x) {
-      const double2 f0 = buf0[ky * tk], fm = buf0[(ny - ky) * tk];
-      buf0[ky * tk] = make_double2(f0.x - fm.y, f0.y + fm.x);         // F0 + i FM
-      buf0[(ny - ky) * tk] = make_double2(f0.x + fm.y, fm.x - f0.y);  // conj F0 + i conj FM
+      const C f0 = buf0[ky * tk], fm = buf0[(ny - ky) * tk];
+      buf0[ky * tk] = mkc<C>(f0.x - fm.y, f0.y + fm.x);         // F0 + i FM
+      buf0[(ny - ky) * tk] = mkc<C>(f0.x + fm.y, fm.x - f0.y);  // conj F0 + i conj FM
     }
     __syncthreads();
   }
   // element (y, c) of the tile sits at y*tk + c: element stride tk, batch stride 1
-  double2* res = stockham_smem<INV, true>(buf0, buf1, d, tk, tk, 1, tw);
+  C* res = stockham_smem<INV, true>(buf0, buf1, d, tk, tk, 1, tw);
   if (!INV && blockIdx.x == 0) {  // untangle after the forward transform
     for (int ky = 1 + threadIdx.x; 2 * ky < ny; ky += blockDim.x) {
-      const double2 z = res[ky * tk], zm = res[(ny - ky) * tk];
+      const C zz = res[ky * tk], zm = res[(ny - ky) * tk];
       // F0 = (Z + conj Zm)/2,  FM = -i (Z - conj Zm)/2
-      res[ky * tk] = make_double2(0.5 * (z.x + zm.x), 0.5 * (z.y - zm.y));
-      res[(ny - ky) * tk] = make_double2(0.5 * (z.y + zm.y), 0.5 * (zm.x - z.x));
+      const T h = T(0.5);
+      res[ky * tk] = mkc<C>(h * (zz.x + zm.x), h * (zz.y - zm.y));
+      res[(ny - ky) * tk] = mkc<C>(h * (zz.y + zm.y), h * (zm.x - zz.x));
     }
     __syncthreads();
   }
@@ -140,32 +142,45 @@ static EncodeTiledFn get_encode() {
   return fn;
 }
 
-cudaError_t launch_fft_y(const cfs_plan* P, double* data, bool inverse, cudaStream_t st) {
+template <class C>
+static cudaError_t launch_y(const cfs_plan* P, void* data, bool inverse, int tk, const C* tw,
+                            cudaStream_t st) {
   if (P->ny == 1) return cudaSuccess;  // length-1 transform is the identity
   EncodeTiledFn enc = get_encode();
   if (!enc) return cudaErrorNotSupported;
+  using T = typename cscal<C>::T;
   CUtensorMap map;
   cuuint64_t gdim[3] = {(cuuint64_t)(2 * P->M), (cuuint64_t)P->ny, (cuuint64_t)P->nz};
-  cuuint64_t gstride[2] = {(cuuint64_t)(2 * P->M) * sizeof(double),
-                           (cuuint64_t)(2 * P->M) * P->ny * sizeof(double)};
-  cuuint32_t box[3] = {(cuuint32_t)(2 * P->tk), (cuuint32_t)P->by, 1};
+  cuuint64_t gstride[2] = {(cuuint64_t)(2 * P->M) * sizeof(T),
+                           (cuuint64_t)(2 * P->M) * P->ny * sizeof(T)};
+  cuuint32_t box[3] = {(cuuint32_t)(2 * tk), (cuuint32_t)P->by, 1};
   cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, data, gdim, gstride, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  const CUtensorMapDataType dt =
+      sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  CUresult r = enc(&map, dt, 3, data, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  const size_t smem = 128 + sizeof(double2) * (size_t)(2 * P->tk * P->ny + P->fy.ntw);
-  dim3 grid((P->M + P->tk - 1) / P->tk, P->nz);
+  const size_t smem = 128 + sizeof(C) * (size_t)(2 * tk * P->ny + P->fy.ntw);
+  dim3 grid((P->M + tk - 1) / tk, P->nz);
   if (!inverse) {
-    cudaFuncSetAttribute(fft_y_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    fft_y_kernel<false><<<grid, 128, smem, st>>>(map, P->fy, P->d_twy, P->tk, P->by, P->nbox,
-                                                 P->d_status);
+    auto k = fft_y_kernel<false, C>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<grid, 128, smem, st>>>(map, P->fy, tw, tk, P->by, P->nbox, P->d_status);
   } else {
-    cudaFuncSetAttribute(fft_y_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    fft_y_kernel<true><<<grid, 128, smem, st>>>(map, P->fy, P->d_twy, P->tk, P->by, P->nbox,
-                                                P->d_status);
+    auto k = fft_y_kernel<true, C>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<grid, 128, smem, st>>>(map, P->fy, tw, tk, P->by, P->nbox, P->d_status);
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_fft_y(const cfs_plan* P, double* data, bool inverse, cudaStream_t st) {
+  return launch_y<double2>(P, data, inverse, P->tk, P->d_twy, st);
+}
+
+cudaError_t launch_fft_y32(const cfs_plan* P, float* data, bool inverse, cudaStream_t st) {
+  return launch_y<float2>(P, data, inverse, P->tk32, P->d_twy32, st);
 }
 
 }  // namespace chanfs

@@ -25,16 +25,17 @@ namespace chanfs {
 
 constexpr int kPcrCols = 16;  // columns per tile (one half-warp)
 
+template <class R>
 struct PcrArgs {
-  double* u;           // output field (for the face wall row)
+  R* u;                // output field (for the face wall row)
   long long ncols;     // Nx * Ny
   int n;               // unknowns per column
   int nparts;
   int face;            // face-located field: slot nz-1 is the wall, written 0
   int nz;
   int by, nbox;        // rows per TMA box, boxes per tile
-  const double* rows;  // alpha | beta | ib | ap | cp  (5n)
-  const double* red;   // rl | rip | ripc             (3 * 2p)
+  const R* rows;       // alpha | beta | ib | ap | cp  (5n)
+  const R* red;        // rl | rip | ripc             (3 * 2p)
 };
 
 __device__ __forceinline__ void pcr_mbar_init(uint64_t* bar) {
@@ -63,17 +64,18 @@ __device__ __forceinline__ bool pcr_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
+template <class R>
 __global__ void __launch_bounds__(1024) pcr_kernel(const __grid_constant__ CUtensorMap in_map,
                                                    const __grid_constant__ CUtensorMap out_map,
-                                                   PcrArgs a, int* status) {
+                                                   PcrArgs<R> a, int* status) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int n = a.n, J = 2 * a.nparts;
   const int rows_alloc = a.nbox * a.by;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-  double* T = reinterpret_cast<double*>(smem_raw + 128);  // tile [rows_alloc][16]
-  double* s_rows = T + rows_alloc * kPcrCols;               // 5n
-  double* s_red = s_rows + 5 * n;                           // 3J
-  double* s_x = s_red + 3 * J;                              // J x 16
+  R* T = reinterpret_cast<R*>(smem_raw + 128);  // tile [rows_alloc][16]
+  R* s_rows = T + rows_alloc * kPcrCols;               // 5n
+  R* s_red = s_rows + 5 * n;                           // 3J
+  R* s_x = s_red + 3 * J;                              // J x 16
 
   if (threadIdx.x == 0) {
     pcr_mbar_init(bar);
@@ -83,14 +85,14 @@ __global__ void __launch_bounds__(1024) pcr_kernel(const __grid_constant__ CUten
   for (int e = threadIdx.x; e < 5 * n; e += blockDim.x) s_rows[e] = a.rows[e];
   for (int e = threadIdx.x; e < 3 * J; e += blockDim.x) s_red[e] = a.red[e];
   __syncthreads();
-  const double* alpha = s_rows;
-  const double* beta = s_rows + n;
-  const double* ib = s_rows + 2 * n;
-  const double* ap = s_rows + 3 * n;
-  const double* cp = s_rows + 4 * n;
-  const double* rl = s_red;
-  const double* rip = s_red + J;
-  const double* ripc = s_red + 2 * J;
+  const R* alpha = s_rows;
+  const R* beta = s_rows + n;
+  const R* ib = s_rows + 2 * n;
+  const R* ap = s_rows + 3 * n;
+  const R* cp = s_rows + 4 * n;
+  const R* rl = s_red;
+  const R* rip = s_red + J;
+  const R* ripc = s_red + 2 * J;
 
   const int c = threadIdx.x % kPcrCols;  // column within the tile
   const int q = threadIdx.x / kPcrCols;  // partition
@@ -98,7 +100,7 @@ __global__ void __launch_bounds__(1024) pcr_kernel(const __grid_constant__ CUten
   const int s = (int)(((long long)q * n) / a.nparts);
   const int m = (int)(((long long)(q + 1) * n) / a.nparts) - s;
   const long long ntiles = (a.ncols + kPcrCols - 1) / kPcrCols;
-  const uint32_t tile_bytes = (uint32_t)(a.nbox * a.by * kPcrCols * sizeof(double));
+  const uint32_t tile_bytes = (uint32_t)(a.nbox * a.by * kPcrCols * sizeof(R));
   uint32_t phase = 0;
 
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -119,16 +121,16 @@ __global__ void __launch_bounds__(1024) pcr_kernel(const __grid_constant__ CUten
       if (threadIdx.x == 0) atomicOr(status, kErrTmaTimeout);
       return;
     }
-    double* col = T + c;  // element (row r) at col[r * 16]
+    R* col = T + c;  // element (row r) at col[r * 16]
     // Step 2: forward then backward reduction of d only
     {
-      double prev = col[(s + 1) * kPcrCols];
+      R prev = col[(s + 1) * kPcrCols];
       for (int i = 2; i < m; ++i) {
         const int r = s + i;
         prev = fma(-alpha[r], prev, col[r * kPcrCols]);
         col[r * kPcrCols] = prev;
       }
-      double next = col[(s + m - 2) * kPcrCols];
+      R next = col[(s + m - 2) * kPcrCols];
       for (int i = m - 3; i >= 0; --i) {
         const int r = s + i;
         next = fma(-beta[r], next, col[r * kPcrCols]);
@@ -140,12 +142,12 @@ __global__ void __launch_bounds__(1024) pcr_kernel(const __grid_constant__ CUten
     __syncthreads();
     // Step 3: reduced system [x_0^0, x_{m-1}^0, x_0^1, ...], one lane per column
     if (threadIdx.x < kPcrCols) {
-      double y = s_x[c];
+      R y = s_x[c];
       for (int jj = 1; jj < J; ++jj) {
         y = fma(-rl[jj], y, s_x[jj * kPcrCols + c]);
         s_x[jj * kPcrCols + c] = y;
       }
-      double x = rip[J - 1] * y;
+      R x = rip[J - 1] * y;
       s_x[(J - 1) * kPcrCols + c] = x;
       for (int jj = J - 2; jj >= 0; --jj) {
         x = fma(-ripc[jj], x, rip[jj] * s_x[jj * kPcrCols + c]);
@@ -155,8 +157,8 @@ __global__ void __launch_bounds__(1024) pcr_kernel(const __grid_constant__ CUten
     __syncthreads();
     // Step 4: reconstruction in place
     {
-      const double x0 = s_x[(2 * q) * kPcrCols + c];
-      const double xm = s_x[(2 * q + 1) * kPcrCols + c];
+      const R x0 = s_x[(2 * q) * kPcrCols + c];
+      const R xm = s_x[(2 * q + 1) * kPcrCols + c];
       col[s * kPcrCols] = x0;
       col[(s + m - 1) * kPcrCols] = xm;
       for (int i = 1; i <= m - 2; ++i) {
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(1024) pcr_kernel(const __grid_constant__ CUten
       asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // tile may be reused
     }
     if (a.face && threadIdx.x < kPcrCols && col0 + c < a.ncols)
-      a.u[(long long)(a.nz - 1) * a.ncols + col0 + c] = 0.0;
+      a.u[(long long)(a.nz - 1) * a.ncols + col0 + c] = R(0);
     __syncthreads();
   }
 }
@@ -201,55 +203,81 @@ static EncodeTiledFn pcr_encode() {
   return fn;
 }
 
-// 2-D map over the first n rows of a field: ncols doubles per row.
+// 2-D map over the first n rows of a field: ncols reals per row.
+template <class R>
 static bool pcr_map(CUtensorMap* map, const void* base, long long ncols, int n, int by) {
   EncodeTiledFn enc = pcr_encode();
   if (!enc) return false;
   cuuint64_t gdim[2] = {(cuuint64_t)ncols, (cuuint64_t)n};
-  cuuint64_t gstride[1] = {(cuuint64_t)ncols * sizeof(double)};
+  cuuint64_t gstride[1] = {(cuuint64_t)ncols * sizeof(R)};
   cuuint32_t box[2] = {(cuuint32_t)kPcrCols, (cuuint32_t)by};
   cuuint32_t estr[2] = {1, 1};
-  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void*>(base), gdim, gstride, box,
-             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+  const CUtensorMapDataType dt =
+      sizeof(R) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  return enc(map, dt, 2, const_cast<void*>(base), gdim, gstride, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-size_t pcr_smem_bytes(int n, int nparts) {
-  const int nbox = (n + 255) / 256;
-  const int by = (n + nbox - 1) / nbox;
-  return 128 + sizeof(double) * ((size_t)nbox * by * kPcrCols + 5 * (size_t)n + 6 * (size_t)nparts +
-                                 2 * (size_t)nparts * kPcrCols);
+// Rows per TMA box: at most 256; even for FP32 so that every box starts on a
+// 128-byte boundary of the shared tile (16 floats = 64 bytes per row).
+static void pcr_boxes(int n, size_t rsize, int* nbox, int* by) {
+  *nbox = (n + 255) / 256;
+  *by = (n + *nbox - 1) / *nbox;
+  if (rsize == 4 && (*by % 2)) ++*by;
 }
 
-cudaError_t launch_pcr(const cfs_plan* P, const HelmCoef& h, const double* rhs, double* u,
-                       cudaStream_t st) {
-  PcrArgs a;
+template <class R>
+static size_t pcr_smem_t(int n, int nparts) {
+  int nbox, by;
+  pcr_boxes(n, sizeof(R), &nbox, &by);
+  return 128 + sizeof(R) * ((size_t)nbox * by * kPcrCols + 5 * (size_t)n + 6 * (size_t)nparts +
+                            2 * (size_t)nparts * kPcrCols);
+}
+
+size_t pcr_smem_bytes(int n, int nparts) { return pcr_smem_t<double>(n, nparts); }
+
+template <class R>
+static cudaError_t launch_pcr_t(const cfs_plan* P, const HelmCoef& h, const R* rows, const R* red,
+                                const R* rhs, R* u, cudaStream_t st) {
+  PcrArgs<R> a;
   a.u = u;
   a.ncols = (long long)P->nx * P->ny;
   a.n = h.n;
   a.nparts = h.nparts;
   a.face = (h.loc == CFS_LOC_FACE);
   a.nz = P->nz;
-  a.nbox = (h.n + 255) / 256;
-  a.by = (h.n + a.nbox - 1) / a.nbox;
-  a.rows = h.d_rows;
-  a.red = h.d_red;
+  pcr_boxes(h.n, sizeof(R), &a.nbox, &a.by);
+  a.rows = rows;
+  a.red = red;
   CUtensorMap in_map, out_map;
-  if (!pcr_map(&in_map, rhs, a.ncols, h.n, a.by) || !pcr_map(&out_map, u, a.ncols, h.n, a.by))
+  if (!pcr_map<R>(&in_map, rhs, a.ncols, h.n, a.by) || !pcr_map<R>(&out_map, u, a.ncols, h.n, a.by))
     return cudaErrorInvalidValue;
-  const size_t smem = pcr_smem_bytes(h.n, h.nparts);
+  const size_t smem = pcr_smem_t<R>(h.n, h.nparts);
   const int threads = kPcrCols * h.nparts;
-  cudaFuncSetAttribute(pcr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = pcr_kernel<R>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int dev = 0, nsm = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcr_kernel, threads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
   if (per_sm < 1) per_sm = 1;
   const long long ntiles = (a.ncols + kPcrCols - 1) / kPcrCols;
   long long grid = (long long)nsm * per_sm;
   if (grid > ntiles) grid = ntiles;
-  pcr_kernel<<<(unsigned)grid, threads, smem, st>>>(in_map, out_map, a, P->d_status);
+  kern<<<(unsigned)grid, threads, smem, st>>>(in_map, out_map, a, P->d_status);
   return cudaGetLastError();
+}
+
+cudaError_t launch_pcr(const cfs_plan* P, const HelmCoef& h, const double* rhs, double* u,
+                       cudaStream_t st) {
+  return launch_pcr_t<double>(P, h, h.d_rows, h.d_red, rhs, u, st);
+}
+
+cudaError_t launch_pcr32(const cfs_plan* P, const HelmCoef& h, const float* rhs, float* u,
+                         cudaStream_t st) {
+  if (!h.d_rows32) return cudaErrorInvalidValue;
+  return launch_pcr_t<float>(P, h, h.d_rows32, h.d_red32, rhs, u, st);
 }
 
 }  // namespace chanfs

@@ -162,10 +162,21 @@ static void plan_free(cfs_plan* P) {
   cudaFree(P->d_sing);
   cudaFree(P->d_stage);
   cudaFree(P->d_status);
+  cudaFree(P->d_twx32);
+  cudaFree(P->d_twy32);
+  cudaFree(P->d_post32);
+  cudaFree(P->d_fwd32);
+  cudaFree(P->d_bwd32);
+  cudaFree(P->d_r32);
+  cudaFree(P->d_red);
+  cudaFree(P->d_zop);
 
   for (auto& h : P->helm) {
     cudaFree(h.d_rows);
     cudaFree(h.d_red);
+    cudaFree(h.d_rows32);
+    cudaFree(h.d_red32);
+    cudaFree(h.d_abc);
   }
   delete P;
 }
@@ -176,7 +187,9 @@ extern "C" int cfs_plan_create(cfs_plan_t* out, int nx, int ny, int nz, double l
   *out = nullptr;
   if (!dz || !(lx > 0) || !(ly > 0) || !isfinite(lx) || !isfinite(ly)) return CFS_EINVAL;
   if (poisson_bc != CFS_BC_NEUMANN && poisson_bc != CFS_BC_DIRICHLET) return CFS_EINVAL;
-  if (dtype != CFS_F64) return CFS_EUNSUPPORTED;
+  if (dtype != CFS_F64 && dtype != CFS_F32_REFINED) return CFS_EUNSUPPORTED;
+  // FP32 rows must be whole 16-byte units for the TMA copies
+  if (dtype == CFS_F32_REFINED && nx % 4 != 0) return CFS_EUNSUPPORTED;
   if (nx < 2 || ny < 1 || nz < 3) return CFS_EINVAL;
   if (nx % 2 != 0 || nx > kMaxNx || !is_23_smooth(nx / 2)) return CFS_EUNSUPPORTED;
   if (ny > kMaxNy || !is_23_smooth(ny) || nz > kMaxNz) return CFS_EUNSUPPORTED;
@@ -197,6 +210,12 @@ extern "C" int cfs_plan_create(cfs_plan_t* out, int nx, int ny, int nz, double l
   P->dzf.assign(dz, dz + nz);
   P->helm_clock = 0;
   P->device_bytes = 0;
+  P->dtype = dtype;
+  P->tol = 1e-10;
+  P->maxit = 4;
+  P->last_iters = 0;
+  P->last_rho = 0.0;
+  const bool refined = (dtype == CFS_F32_REFINED);
 
   // y tile: columns per tile and TMA boxes (at most 256 rows per box)
   P->nbox = (ny + 255) / 256;
@@ -210,6 +229,14 @@ extern "C" int cfs_plan_create(cfs_plan_t* out, int nx, int ny, int nz, double l
   P->tk = (ny <= 256 || P->by % 2 != 0) ? 8 : 4;
   if (P->tk > P->M) P->tk = P->M;
   if (P->nbox > 1 && ((size_t)P->by * P->tk * sizeof(double2)) % 128 != 0) {
+    plan_free(P);
+    return CFS_EUNSUPPORTED;
+  }
+  // FP32 tiles: twice the columns in the same bytes; an even count keeps the
+  // 16-byte TMA box rows
+  P->tk32 = (P->by % 2 != 0) ? 16 : 2 * P->tk;
+  if (P->tk32 > P->M) P->tk32 = P->M + (P->M & 1);
+  if (refined && P->nbox > 1 && ((size_t)P->by * P->tk32 * sizeof(float2)) % 128 != 0) {
     plan_free(P);
     return CFS_EUNSUPPORTED;
   }
@@ -260,6 +287,27 @@ extern "C" int cfs_plan_create(cfs_plan_t* out, int nx, int ny, int nz, double l
     P->sing_cg /= sw;
   }
 
+  // Refinement: the Poisson operator's z rows with the x/y diagonal folded in
+  // (residual kernel), and the columns kept in FP64 by the FP32 z sweep: those
+  // whose eigenvalue shift |lx + ly| is below 1e-3 of the largest z
+  // eigenvalue, where an FP32 sweep would lose more than ~4 digits.
+  std::vector<double> zop(3 * (size_t)nz);
+  for (int k = 0; k < nz; ++k) {
+    zop[k] = A[k];
+    zop[nz + k] = B[k] - 2.0 / (dx * dx) - 2.0 / (dy * dy);
+    zop[2 * nz + k] = C[k];
+  }
+  P->kx64 = P->ky64 = 0;
+  if (refined) {
+    double zmax = 0.0;
+    for (int k = 0; k < nz; ++k) zmax = std::max(zmax, fabs(A[k]) + fabs(B[k]) + fabs(C[k]));
+    const double thr = 1e-3 * zmax;
+    while (P->kx64 <= P->M && fabs(lamx[P->kx64]) < thr) ++P->kx64;
+    while (P->ky64 < P->nky && fabs(lamy[P->ky64]) < thr) ++P->ky64;
+    P->kx64 = std::max(P->kx64, 1);
+    P->ky64 = std::max(P->ky64, 1);
+  }
+
   int rc = CFS_OK;
   double *dA = nullptr, *dB = nullptr, *dC = nullptr, *dlx = nullptr, *dly = nullptr;
   size_t scratch = 0;
@@ -273,6 +321,22 @@ extern "C" int cfs_plan_create(cfs_plan_t* out, int nx, int ny, int nz, double l
   if (!rc) rc = dev_upload<double>(&P->d_bwd, nullptr, nfac, &P->device_bytes);
   if (!rc) rc = dev_upload<int>(&P->d_status, nullptr, 1, &P->device_bytes);
   if (!rc) rc = cuda_status(cudaMemset(P->d_status, 0, sizeof(int)));
+  if (!rc && refined) {
+    auto f32 = [](const std::vector<double2>& v) {
+      std::vector<float2> o(v.size());
+      for (size_t i = 0; i < v.size(); ++i) o[i] = make_float2((float)v[i].x, (float)v[i].y);
+      return o;
+    };
+    const std::vector<float2> twx32 = f32(twx), twy32 = f32(twy), post32 = f32(post);
+    rc = dev_upload(&P->d_twx32, twx32.data(), twx32.size(), &P->device_bytes);
+    if (!rc) rc = dev_upload(&P->d_twy32, twy32.data(), twy32.size(), &P->device_bytes);
+    if (!rc) rc = dev_upload(&P->d_post32, post32.data(), post32.size(), &P->device_bytes);
+    if (!rc) rc = dev_upload<float2>(&P->d_fwd32, nullptr, nfac, &P->device_bytes);
+    if (!rc) rc = dev_upload<float>(&P->d_bwd32, nullptr, nfac, &P->device_bytes);
+    if (!rc) rc = dev_upload<float>(&P->d_r32, nullptr, (size_t)nx * ny * nz, &P->device_bytes);
+    if (!rc) rc = dev_upload<double>(&P->d_red, nullptr, (size_t)nz + 8, &P->device_bytes);
+    if (!rc) rc = dev_upload(&P->d_zop, zop.data(), zop.size(), &P->device_bytes);
+  }
 
   if (!rc) rc = dev_upload(&dA, A.data(), A.size(), &scratch);
   if (!rc) rc = dev_upload(&dB, B.data(), B.size(), &scratch);
@@ -330,9 +394,22 @@ extern "C" int cfs_spectral_inverse(cfs_plan_t P, const double* s, double* f, vo
   return e == cudaErrorInvalidValue ? CFS_EINVAL : cuda_status(e);
 }
 
+static int ensure_stage(cfs_plan* P);
+
 extern "C" int cfs_poisson_solve(cfs_plan_t P, const double* f, double* p, void* stream) {
   if (!P || !f || !p || !aligned16(f) || !aligned16(p)) return CFS_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
+  if (P->dtype == CFS_F32_REFINED) {
+    if (f == p) {  // the residual needs f for every iteration
+      int rc = ensure_stage(P);
+      if (rc) return rc;
+      if (cudaMemcpyAsync(P->d_stage, f, sizeof(double) * (size_t)P->nx * P->ny * P->nz,
+                          cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return CFS_ECUDA;
+      f = P->d_stage;
+    }
+    return refine_poisson(P, f, p, st);
+  }
   cudaError_t e = launch_rfft_x(P, f, p, false, 1.0, st);
   if (e == cudaSuccess) e = launch_fft_y(P, p, false, st);
   if (e == cudaSuccess) e = launch_thomas(P, p, st);
@@ -478,9 +555,25 @@ static int helm_prepare(cfs_plan* P, double c, int loc, int nparts, HelmCoef** r
   }
   int rcode = dev_upload(&h.d_rows, rows.data(), rows.size(), &P->device_bytes);
   if (!rcode) rcode = dev_upload(&h.d_red, red.data(), red.size(), &P->device_bytes);
+  if (!rcode && P->dtype == CFS_F32_REFINED) {
+    // FP32 copies for the inner solves; the FP64 rows of I - c L_z for the residual
+    std::vector<float> rows32(rows.begin(), rows.end()), red32(red.begin(), red.end());
+    std::vector<double> abc(3 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+      abc[i] = A[i];
+      abc[n + i] = B[i];
+      abc[2 * n + i] = C[i];
+    }
+    rcode = dev_upload(&h.d_rows32, rows32.data(), rows32.size(), &P->device_bytes);
+    if (!rcode) rcode = dev_upload(&h.d_red32, red32.data(), red32.size(), &P->device_bytes);
+    if (!rcode) rcode = dev_upload(&h.d_abc, abc.data(), abc.size(), &P->device_bytes);
+  }
   if (rcode) {
     cudaFree(h.d_rows);
     cudaFree(h.d_red);
+    cudaFree(h.d_rows32);
+    cudaFree(h.d_red32);
+    cudaFree(h.d_abc);
     return rcode;
   }
   // bounded cache: evict the least recently used entry
@@ -491,6 +584,9 @@ static int helm_prepare(cfs_plan* P, double c, int loc, int nparts, HelmCoef** r
     cudaDeviceSynchronize();
     cudaFree(it->d_rows);
     cudaFree(it->d_red);
+    cudaFree(it->d_rows32);
+    cudaFree(it->d_red32);
+    cudaFree(it->d_abc);
     P->device_bytes -= sizeof(double) * (5 * (size_t)it->n + 6 * (size_t)it->nparts);
     P->helm.erase(it);
   }
@@ -512,7 +608,33 @@ extern "C" int cfs_helmholtz_solve(cfs_plan_t P, double c, int loc, const double
   HelmCoef* h = nullptr;
   int rc = helm_prepare(P, c, loc, 0, &h);
   if (rc) return rc;
-  return cuda_status(launch_pcr(P, *h, rhs, u, (cudaStream_t)stream));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (P->dtype == CFS_F32_REFINED) {
+    if (rhs == u) {
+      rc = ensure_stage(P);
+      if (rc) return rc;
+      if (cudaMemcpyAsync(P->d_stage, rhs, sizeof(double) * (size_t)P->nx * P->ny * P->nz,
+                          cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return CFS_ECUDA;
+      rhs = P->d_stage;
+    }
+    return refine_helmholtz(P, *h, rhs, u, st);
+  }
+  return cuda_status(launch_pcr(P, *h, rhs, u, st));
+}
+
+extern "C" int cfs_plan_set_refinement(cfs_plan_t P, double tol, int maxit) {
+  if (!P || !(tol > 0) || !isfinite(tol) || maxit < 1 || maxit > 64) return CFS_EINVAL;
+  P->tol = tol;
+  P->maxit = maxit;
+  return CFS_OK;
+}
+
+extern "C" int cfs_last_info(cfs_plan_t P, int* iters, double* rel_residual) {
+  if (!P) return CFS_EINVAL;
+  if (iters) *iters = P->last_iters;
+  if (rel_residual) *rel_residual = P->last_rho;
+  return CFS_OK;
 }
 
 // ----------------------------------------------------------------------------

@@ -1,0 +1,282 @@
+// refine.cu -- FP32 solves with FP64 iterative refinement.
+//
+// The FP32 transforms and sweeps are memory-bound on GB300, where FP64 runs
+// at 1/64 of the FP32 rate.  Accuracy is won back by classical iterative
+// refinement: p_0 = 0, r_0 = f; repeat { delta = solve32(r); p += delta (FP64);
+// r = f - L p (FP64, the staggered 7-point operator) } until
+// ||r||_inf <= tol ||f||_inf or the iteration budget is spent.  FP64 is used
+// only for the residual, the accumulation, the near-singular low-wavenumber
+// columns of the z sweep and the pre-processing of the coefficients.
+//
+// The correction p += delta is fused into the FP32 inverse x transform
+// (fft_x.cu, OUT_ADD); the residual kernels write the next FP32 right-hand
+// side and the max-norm of the residual in one pass.
+#include <math.h>
+#include <string.h>
+
+#include "chanfs_internal.cuh"
+
+namespace chanfs {
+
+constexpr int kResBlock = 128;
+
+__device__ __forceinline__ void block_max_to(float v, unsigned int* out) {
+  // non-negative floats order like their bit patterns
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __shared__ float wmax[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) wmax[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = (lane < (int)(blockDim.x >> 5)) ? wmax[lane] : 0.0f;
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) atomicMax(out, __float_as_uint(v));
+  }
+}
+
+// Neumann compatibility: the dz-weighted mean of f, reduced in a fixed order
+// (one block per z plane, then one block over the planes) so that results
+// are bit-reproducible.
+__global__ void plane_sum_kernel(const double* __restrict__ f, long long nxy, const double* dzf,
+                                 double* partial) {
+  __shared__ double sh[256];
+  const double* plane = f + (long long)blockIdx.x * nxy;
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < nxy; i += blockDim.x) s += plane[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = dzf[blockIdx.x] * sh[0];
+}
+
+__global__ void mean_final_kernel(const double* partial, int nz, const double* dzf, long long nxy,
+                                  double* mean) {
+  __shared__ double sh[256], shw[256];
+  double s = 0.0, w = 0.0;
+  for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+    s += partial[k];
+    w += dzf[k];
+  }
+  sh[threadIdx.x] = s;
+  shw[threadIdx.x] = w;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      sh[threadIdx.x] += sh[threadIdx.x + o];
+      shw[threadIdx.x] += shw[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *mean = sh[0] / (shw[0] * (double)nxy);
+}
+
+// r = (f - mean) - L p, written as FP32, and max |r|.  One thread per (x, y)
+// column marching up in z with p_{k-1}, p_k, p_{k+1} in registers; the x and
+// y neighbours of a plane are shared through L1.  p == nullptr: r = f - mean.
+// zop = [A_k | B_k - 2/dx^2 - 2/dy^2 | C_k]; FP64: 9 instructions per point.
+__global__ void __launch_bounds__(kResBlock) poisson_residual_kernel(
+    const double* __restrict__ f, const double* __restrict__ p, const double* __restrict__ zop,
+    const double* __restrict__ mean, float* __restrict__ r32, unsigned int* rmax, int nx, int ny,
+    int nz, double idx2, double idy2) {
+  const long long nxy = (long long)nx * ny;
+  const long long col = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float vmax = 0.0f;
+  if (col < nxy) {
+    const double mu = mean ? *mean : 0.0;
+    const int i = (int)(col % nx), j = (int)(col / nx);
+    const long long ip = (i + 1 == nx) ? col - i : col + 1;
+    const long long im = (i == 0) ? col + nx - 1 : col - 1;
+    const long long jp = (j + 1 == ny) ? col - (long long)j * nx : col + nx;
+    const long long jm = (j == 0) ? col + (long long)(ny - 1) * nx : col - nx;
+    double pkm = 0.0, pk = p ? p[col] : 0.0;
+    for (int k = 0; k < nz; ++k) {
+      const long long o = (long long)k * nxy;
+      const double pkp = (p && k + 1 < nz) ? p[o + nxy + col] : 0.0;
+      double r = f[o + col] - mu;
+      if (p) {
+        const double sx = p[o + ip] + p[o + im];
+        const double sy = p[o + jp] + p[o + jm];
+        double t = zop[nz + k] * pk;
+        t = fma(idx2, sx, t);
+        t = fma(idy2, sy, t);
+        t = fma(zop[k], pkm, t);
+        t = fma(zop[2 * nz + k], pkp, t);
+        r -= t;
+      }
+      const float rf = (float)r;
+      r32[o + col] = rf;
+      vmax = fmaxf(vmax, fabsf(rf));
+      pkm = pk;
+      pk = pkp;
+    }
+  }
+  block_max_to(vmax, rmax);
+}
+
+// Helmholtz: u (+)= delta, then r = rhs - (I - c L_z) u, as FP32, and max |r|.
+// mode 0: u is not read (r = rhs); 1: u = delta; 2: u += delta.  delta is read
+// from r32 and overwritten by the new residual.  One thread per column,
+// marching up in z one row behind the update so that u_{k+1} is final when
+// row k is evaluated.  abc = [A' | B' | C'] of I - c L_z (n rows); the wall
+// row of a face field (n < nz) keeps r = 0.  FP64: 5 instructions per point.
+__global__ void __launch_bounds__(kResBlock) helm_residual_kernel(
+    const double* __restrict__ rhs, double* __restrict__ u, float* __restrict__ r32,
+    const double* __restrict__ abc, unsigned int* rmax, long long ncols, int n, int nz, int mode) {
+  const long long col = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float vmax = 0.0f;
+  if (col < ncols) {
+    auto update = [&](int k) -> double {
+      const long long o = (long long)k * ncols + col;
+      if (mode == 0) return 0.0;
+      const double d = (double)r32[o];
+      const double v = (mode == 1) ? d : u[o] + d;
+      u[o] = v;
+      return v;
+    };
+    double um = 0.0, uk = update(0);
+    for (int k = 0; k < n; ++k) {
+      const double up = (k + 1 < n) ? update(k + 1) : 0.0;
+      const long long o = (long long)k * ncols + col;
+      double t = abc[n + k] * uk;
+      t = fma(abc[k], um, t);
+      t = fma(abc[2 * n + k], up, t);
+      const float rf = (float)(rhs[o] - t);
+      r32[o] = rf;
+      vmax = fmaxf(vmax, fabsf(rf));
+      um = uk;
+      uk = up;
+    }
+    if (n < nz) {
+      const long long o = (long long)(nz - 1) * ncols + col;
+      r32[o] = 0.0f;
+      if (mode == 1) u[o] = 0.0;
+    }
+  }
+  block_max_to(vmax, rmax);
+}
+
+// p -= mean (the dz-weighted mean computed by the two kernels above).
+__global__ void subtract_mean_kernel(double* __restrict__ p, long long n,
+                                     const double* __restrict__ mean) {
+  const double mu = *mean;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    p[i] -= mu;
+}
+
+static int cuda_rc(cudaError_t e) { return e == cudaSuccess ? CFS_OK : CFS_ECUDA; }
+
+// Reads back the max-norm word (one synchronisation of st).
+static int read_max(cfs_plan* P, cudaStream_t st, float* out) {
+  unsigned int bits = 0;
+  cudaError_t e = cudaMemcpyAsync(&bits, P->d_red, sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return CFS_ECUDA;
+  memcpy(out, &bits, sizeof(float));
+  return CFS_OK;
+}
+
+static unsigned int* max_word(cfs_plan* P) { return reinterpret_cast<unsigned int*>(P->d_red); }
+
+int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st) {
+  const long long nxy = (long long)P->nx * P->ny;
+  const double dx = P->lx / P->nx, dy = P->ly / P->ny;
+  const double idx2 = 1.0 / (dx * dx), idy2 = 1.0 / (dy * dy);
+  const unsigned grid = (unsigned)((nxy + kResBlock - 1) / kResBlock);
+  double* mean = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (P->bc == CFS_BC_NEUMANN) {  // remove the dz-weighted mean of f (compatibility)
+    mean = P->d_red + 1;
+    plane_sum_kernel<<<P->nz, 256, 0, st>>>(f, nxy, P->d_dzf, P->d_red + 2);
+    mean_final_kernel<<<1, 256, 0, st>>>(P->d_red + 2, P->nz, P->d_dzf, nxy, mean);
+    e = cudaGetLastError();
+  }
+  // r_0 = f - mean and the reference norm ||f - mean||_inf
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->d_red, 0, sizeof(unsigned int), st);
+  if (e == cudaSuccess) {
+    poisson_residual_kernel<<<grid, kResBlock, 0, st>>>(f, nullptr, P->d_zop, mean, P->d_r32,
+                                                        max_word(P), P->nx, P->ny, P->nz, idx2, idy2);
+    e = cudaGetLastError();
+  }
+  float fmax = 0.0f;
+  int rc = cuda_rc(e);
+  if (!rc) rc = read_max(P, st, &fmax);
+  if (rc) return rc;
+  P->last_iters = 0;
+  P->last_rho = 0.0;
+  if (fmax == 0.0f) {  // zero right-hand side: zero solution
+    return cuda_rc(cudaMemsetAsync(p, 0, sizeof(double) * (size_t)nxy * P->nz, st));
+  }
+  for (int it = 0; it < P->maxit; ++it) {
+    // delta = solve32(r), in place in r32; p (+)= delta fused into the last pass
+    e = launch_rfft_x32(P, P->d_r32, P->d_r32, false, st);
+    if (e == cudaSuccess) e = launch_fft_y32(P, P->d_r32, false, st);
+    if (e == cudaSuccess) e = launch_thomas32(P, P->d_r32, st);
+    if (e == cudaSuccess) e = launch_fft_y32(P, P->d_r32, true, st);
+    if (e == cudaSuccess) e = launch_rfft_x32_to64(P, P->d_r32, p, it > 0, st);
+    // r = f - mean - L p
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->d_red, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess) {
+      poisson_residual_kernel<<<grid, kResBlock, 0, st>>>(f, p, P->d_zop, mean, P->d_r32,
+                                                          max_word(P), P->nx, P->ny, P->nz, idx2,
+                                                          idy2);
+      e = cudaGetLastError();
+    }
+    float rmax = 0.0f;
+    rc = cuda_rc(e);
+    if (!rc) rc = read_max(P, st, &rmax);
+    if (rc) return rc;
+    P->last_iters = it + 1;
+    P->last_rho = (double)rmax / (double)fmax;
+    if (P->last_rho <= P->tol) break;
+  }
+  if (P->bc == CFS_BC_NEUMANN) {
+    // The residual cannot see a constant, so the FP32 rounding of each
+    // correction's mean accumulates unchecked; restore the zero dz-weighted
+    // mean of p in FP64.
+    plane_sum_kernel<<<P->nz, 256, 0, st>>>(p, nxy, P->d_dzf, P->d_red + 2);
+    mean_final_kernel<<<1, 256, 0, st>>>(P->d_red + 2, P->nz, P->d_dzf, nxy, P->d_red + 1);
+    subtract_mean_kernel<<<1216, 256, 0, st>>>(p, nxy * P->nz, P->d_red + 1);
+    rc = cuda_rc(cudaGetLastError());
+    if (rc) return rc;
+  }
+  return (P->last_rho <= P->tol) ? CFS_OK : CFS_ENOTCONVERGED;
+}
+
+int refine_helmholtz(cfs_plan* P, const HelmCoef& h, const double* rhs, double* u,
+                     cudaStream_t st) {
+  const long long ncols = (long long)P->nx * P->ny;
+  const unsigned grid = (unsigned)((ncols + kResBlock - 1) / kResBlock);
+  auto residual = [&](int mode) -> cudaError_t {
+    cudaError_t e = cudaMemsetAsync(P->d_red, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    helm_residual_kernel<<<grid, kResBlock, 0, st>>>(rhs, u, P->d_r32, h.d_abc, max_word(P), ncols,
+                                                     h.n, P->nz, mode);
+    return cudaGetLastError();
+  };
+  float fmax = 0.0f;
+  int rc = cuda_rc(residual(0));  // r_0 = rhs
+  if (!rc) rc = read_max(P, st, &fmax);
+  if (rc) return rc;
+  P->last_iters = 0;
+  P->last_rho = 0.0;
+  if (fmax == 0.0f)
+    return cuda_rc(cudaMemsetAsync(u, 0, sizeof(double) * (size_t)ncols * P->nz, st));
+  for (int it = 0; it < P->maxit; ++it) {
+    cudaError_t e = launch_pcr32(P, h, P->d_r32, P->d_r32, st);
+    if (e == cudaSuccess) e = residual(it == 0 ? 1 : 2);
+    float rmax = 0.0f;
+    rc = cuda_rc(e);
+    if (!rc) rc = read_max(P, st, &rmax);
+    if (rc) return rc;
+    P->last_iters = it + 1;
+    P->last_rho = (double)rmax / (double)fmax;
+    if (P->last_rho <= P->tol) return CFS_OK;
+  }
+  return CFS_ENOTCONVERGED;
+}
+
+}  // namespace chanfs

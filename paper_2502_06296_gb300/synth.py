@@ -86,6 +86,10 @@ SMALL = dict(name="poisson_uniform_32x32x32", nx=32, ny=32, nz=32, lx=2 * np.pi,
              beta=None, seed=20250206)
 CHANNEL = dict(name="channel_512x384x384_tanh1.8", nx=512, ny=384, nz=384, lx=12.8, ly=6.4,
                beta=1.8, seed=2502063)
+# The precision workload: the 32^3 physics (uniform grid, 2 pi x pi x 2,
+# Neumann walls, uniform[-1, 1] right-hand side minus its mean) at 1024 x 768 x 512.
+PRECISION = dict(name="poisson_uniform_1024x768x512", nx=1024, ny=768, nz=512, lx=2 * np.pi,
+                 ly=np.pi, beta=None, seed=20250207)
 # Helmholtz coefficient of Eq. (11): alpha * nu * dt with alpha = 0.5, nu = 1/5200, dt = 1e-4.
 CHANNEL_C = 0.5 * (1.0 / 5200.0) * 1e-4
 
@@ -107,3 +111,10 @@ def channel_fields(cfg=CHANNEL):
     f = remove_weighted_mean(normal(cfg["seed"], shape), dz)
     rhs = [normal(cfg["seed"] + 1 + i, shape) for i in range(3)]
     return f, rhs
+
+
+def precision_rhs(cfg=PRECISION) -> np.ndarray:
+    """Uniform[-1, 1] with its mean removed, as for the 32^3 workload."""
+    f = uniform(cfg["seed"], (cfg["nz"], cfg["ny"], cfg["nx"]))
+    f -= f.mean()
+    return f

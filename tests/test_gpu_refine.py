@@ -1,0 +1,158 @@
+"""GPU: FP32 solves with FP64 iterative refinement (plans created with
+CFS_F32_REFINED), against the FP64 CPU oracle.
+
+Accuracy bar: relative max-norm error <= 1e-10 against the oracle's FP64
+solution, and the reported relative residual <= 1e-10, within at most four
+FP32 solves.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2502_06296_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def chanfs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_06296_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2502_06296_gb300 import chanfs as c
+    c.lib()
+    return c
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+POISSON = [
+    ((32, 32, 32), None, 0, "uniform"),
+    ((64, 48, 64), 1.8, 0, "normal"),
+    ((64, 48, 64), 1.8, 1, "normal"),
+    ((48, 36, 40), 2.0, 0, "uniform"),
+    ((12, 9, 5), 1.2, 0, "normal"),     # odd complex length along y
+    ((128, 96, 96), 1.8, 0, "normal"),
+    ((96, 384, 24), 1.5, 0, "normal"),   # two TMA boxes along y
+]
+
+
+@pytest.mark.parametrize("dims,beta,bc,dist", POISSON)
+def test_refined_poisson_matches_fp64_oracle(chanfs, dims, beta, bc, dist):
+    nx, ny, nz = dims
+    lx, ly = 12.8, 6.4
+    dz = synth.uniform_dz(nz) if beta is None else synth.tanh_dz(nz, beta)
+    seed = 100 + nx + nz
+    f = synth.uniform(seed, (nz, ny, nx)) if dist == "uniform" else synth.normal(seed, (nz, ny, nx))
+    if bc == 0:
+        f = synth.remove_weighted_mean(f, dz)
+    ref = oracle.poisson_solve(f, lx, ly, dz, bc)
+    with chanfs.Plan(nx, ny, nz, lx, ly, dz, bc, chanfs.F32_REFINED) as plan:
+        p = host(plan.poisson_solve(dev(f)))
+        iters, rho = plan.last_info()
+        assert rho <= TOL and 1 <= iters <= 4, (iters, rho)
+        assert rel(p, ref) < TOL, rel(p, ref)
+        # the residual as the oracle computes it
+        r = f - oracle.apply_poisson(p, lx, ly, dz, bc)
+        if bc == 0:
+            r -= (np.repeat(dz, nx * ny) @ r.ravel()) / (dz.sum() * nx * ny)
+        assert np.max(np.abs(r)) / np.max(np.abs(f)) < 2 * TOL
+        # in place
+        t = dev(f)
+        plan.poisson_solve(t, out=t)
+        assert np.array_equal(host(t), p)
+        assert plan.check() == 0
+
+
+def test_refined_poisson_reports_nonconvergence(chanfs):
+    nx, ny, nz = 64, 48, 64
+    dz = synth.tanh_dz(nz, 1.8)
+    f = synth.remove_weighted_mean(synth.normal(5, (nz, ny, nx)), dz)
+    with chanfs.Plan(nx, ny, nz, 12.8, 6.4, dz, 0, chanfs.F32_REFINED) as plan:
+        plan.set_refinement(1e-14, 1)
+        with pytest.raises(chanfs.ChanfsError) as err:
+            plan.poisson_solve(dev(f))
+        assert err.value.status == chanfs.ENOTCONVERGED
+        iters, rho = plan.last_info()
+        assert iters == 1 and 1e-14 < rho < 1e-2
+        plan.set_refinement(1e-10, 4)
+        plan.poisson_solve(dev(f))
+        assert plan.last_info()[1] <= 1e-10
+
+
+def test_refined_plan_needs_nx_multiple_of_4(chanfs):
+    with pytest.raises(chanfs.ChanfsError) as err:
+        chanfs.Plan(6, 9, 5, 1.0, 1.0, np.full(5, 0.4), 0, chanfs.F32_REFINED)
+    assert err.value.status == chanfs.EUNSUPPORTED
+
+
+def test_refined_zero_rhs_gives_zero(chanfs):
+    with chanfs.Plan(16, 12, 10, 1.0, 1.0, np.full(10, 0.2), 0, chanfs.F32_REFINED) as plan:
+        p = host(plan.poisson_solve(torch.zeros(10, 12, 16, dtype=torch.float64, device="cuda")))
+        assert np.all(p == 0.0)
+
+
+HELM = [
+    (16, 12, 48, 1.8, 0, 9.615e-5),
+    (16, 12, 48, 1.8, 1, 9.615e-5),
+    (32, 24, 384, 1.8, 0, 9.615e-9),
+    (32, 24, 384, 1.8, 1, 9.615e-9),
+    (12, 9, 100, 1.5, 0, 1e-2),   # far from the identity
+]
+
+
+@pytest.mark.parametrize("nx,ny,nz,beta,loc,c", HELM)
+def test_refined_helmholtz_matches_fp64_oracle(chanfs, nx, ny, nz, beta, loc, c):
+    dz = synth.tanh_dz(nz, beta)
+    rhs = synth.normal(nx + nz + loc, (nz, ny, nx))
+    ref = oracle.helmholtz_solve(rhs, dz, c, loc)
+    with chanfs.Plan(nx, ny, nz, 1.0, 1.0, dz, 0, chanfs.F32_REFINED) as plan:
+        u = host(plan.helmholtz_solve(c, dev(rhs), loc))
+        iters, rho = plan.last_info()
+        assert rho <= TOL and 1 <= iters <= 4, (iters, rho)
+        assert rel(u, ref) < TOL, rel(u, ref)
+        if loc == 1:
+            assert np.all(u[-1] == 0.0)
+        t = dev(rhs)
+        plan.helmholtz_solve(c, t, loc, out=t)
+        assert np.array_equal(host(t), u)
+
+
+@pytest.mark.slow
+def test_refined_precision_workload_full_size(chanfs):
+    """The 1024 x 768 x 512 uniform precision workload: the refined solve
+    meets the residual target (checked with the oracle's operator) and agrees
+    with the FP64 GPU solve of the same right-hand side."""
+    cfg = synth.PRECISION
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    dz = synth.grid_dz(cfg)
+    f = synth.precision_rhs(cfg)
+    fd = dev(f)
+    with chanfs.Plan(nx, ny, nz, cfg["lx"], cfg["ly"], dz, 0, chanfs.F32_REFINED) as plan:
+        p = plan.poisson_solve(fd)
+        iters, rho = plan.last_info()
+        assert rho <= TOL and iters <= 4, (iters, rho)
+    with chanfs.Plan(nx, ny, nz, cfg["lx"], cfg["ly"], dz, 0, chanfs.F64) as plan:
+        p64 = plan.poisson_solve(fd)
+    torch.cuda.synchronize()
+    err = float((p - p64).abs().max() / p64.abs().max())
+    assert err < TOL, err
+    ph = host(p)
+    r = f - oracle.apply_poisson(ph, cfg["lx"], cfg["ly"], dz, 0)
+    assert np.max(np.abs(r)) / np.max(np.abs(f)) < 2 * TOL
