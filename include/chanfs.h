@@ -177,6 +177,32 @@ int cfs_helmholtz_solve_host(cfs_plan_t plan, double c, int loc,
                              const double* rhs, double* u, void* stream);
 
 /*
+ * cfs_helmholtz_solve_noalloc -- the solve of cfs_helmholtz_solve without a
+ * plan and without allocating any memory.  The paper has no counterpart; it
+ * exists for callers that cannot allocate device memory where they solve:
+ * cudaMalloc and cudaFree synchronise the whole device, stalling every other
+ * stream in flight, and applications that reserve the device memory up front
+ * for their own pool have none left to give.
+ *   nx, ny, nz, dz  grid as for cfs_plan_create (dz on the HOST); nx*ny even.
+ *   c, loc          as for cfs_helmholtz_solve; nparts as for
+ *                   cfs_helmholtz_prepare (0 = same choice as the plan).
+ *   rhs, u          device fields as for cfs_helmholtz_solve (rhs == u allowed).
+ * The Algorithm 2 coefficients are computed on the host and copied into a
+ * fixed device array inside the library, sized for at most 1024 unknowns
+ * per column and 64 partitions (about 44 KB, held by every GPU that loads
+ * the library until the process exits); larger sizes return
+ * CFS_EUNSUPPORTED.  The first call on a device looks up that array's
+ * address (cudaGetSymbolAddress), so make it before any stream capture.
+ * Every call overwrites the whole coefficient set and clears the array's
+ * status word; there is one array per device, so calls whose work overlaps
+ * on the GPU (other streams, other host threads) race.  The call waits for
+ * its small coefficient copy, then queues the solve on `stream` and returns.
+ */
+int cfs_helmholtz_solve_noalloc(int nx, int ny, int nz, const double* dz,
+                                double c, int loc, int nparts,
+                                const double* rhs, double* u, void* stream);
+
+/*
  * Iterative refinement (plans created with CFS_F32_REFINED).  A solve starts
  * from x = 0 and repeats { delta = FP32 solve of r; x += delta in FP64;
  * r = b - A x in FP64 } until ||r||_inf <= tol ||b||_inf or `maxit` FP32

@@ -59,6 +59,7 @@ def lib():
             "cfs_plan_check": ([vp, ctypes.POINTER(i)], i),
             "cfs_poisson_stage": ([vp, i, vp, vp, vp], i),
             "cfs_plan_set_refinement": ([vp, d, i], i),
+            "cfs_helmholtz_solve_noalloc": ([i, i, i, dp, d, i, i, vp, vp, vp], i),
             "cfs_last_info": ([vp, ctypes.POINTER(i), ctypes.POINTER(d)], i),
         }
         for name, (args, res) in sig.items():
@@ -213,6 +214,26 @@ class Plan:
         rc = lib().cfs_plan_check(self._h, ctypes.byref(bits))
         _check(rc, "cfs_plan_check")
         return bits.value
+
+
+def helmholtz_solve_noalloc(dz, c: float, rhs, loc: int = CENTER, nparts: int = 0, out=None,
+                            stream=None):
+    """cfs_helmholtz_solve_noalloc: the Helmholtz solve without a plan and
+    without device allocation by the library (see include/chanfs.h)."""
+    import torch
+    dz = np.ascontiguousarray(dz, dtype=np.float64)
+    nz, ny, nx = rhs.shape
+    if dz.size != nz:
+        raise ValueError("dz must have nz entries")
+    out = torch.empty_like(rhs) if out is None else out
+    for t, name in ((rhs, "rhs"), (out, "out")):
+        if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous() or t.shape != rhs.shape:
+            raise TypeError(f"{name} must be a contiguous float64 CUDA tensor of the rhs shape")
+    _check(lib().cfs_helmholtz_solve_noalloc(nx, ny, nz, dz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                             float(c), loc, nparts, ctypes.c_void_p(rhs.data_ptr()),
+                                             ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+           "cfs_helmholtz_solve_noalloc")
+    return out
 
 
 def _host_ptr(a, shape):

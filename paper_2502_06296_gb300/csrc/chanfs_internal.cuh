@@ -142,6 +142,9 @@ cudaError_t launch_thomas_factor(cfs_plan* P, const double* dA, const double* dB
 cudaError_t launch_pcr(const cfs_plan* P, const HelmCoef& h, const double* rhs, double* u,
                        cudaStream_t st);
 size_t pcr_smem_bytes(int n, int nparts);
+cudaError_t launch_pcr_raw(long long ncols, int nz, int n, int nparts, int loc, const double* rows,
+                           const double* red, const double* rhs, double* u, int* status,
+                           cudaStream_t st);
 cudaError_t launch_pcr32(const cfs_plan* P, const HelmCoef& h, const float* rhs, float* u,
                          cudaStream_t st);
 // Iterative refinement drivers (refine.cu): FP32 inner solves, FP64 residual

@@ -281,3 +281,43 @@ cudaError_t launch_pcr32(const cfs_plan* P, const HelmCoef& h, const float* rhs,
 }
 
 }  // namespace chanfs
+
+namespace chanfs {
+
+// Launches the FP64 Algorithm 2 kernel on coefficient arrays given by raw
+// device pointers (used by the allocation-free entry point).
+cudaError_t launch_pcr_raw(long long ncols, int nz, int n, int nparts, int loc, const double* rows,
+                           const double* red, const double* rhs, double* u, int* status,
+                           cudaStream_t st) {
+  PcrArgs<double> a;
+  a.u = u;
+  a.ncols = ncols;
+  a.n = n;
+  a.nparts = nparts;
+  a.face = (loc == CFS_LOC_FACE);
+  a.nz = nz;
+  pcr_boxes(n, sizeof(double), &a.nbox, &a.by);
+  a.rows = rows;
+  a.red = red;
+  CUtensorMap in_map, out_map;
+  if (!pcr_map<double>(&in_map, rhs, ncols, n, a.by) ||
+      !pcr_map<double>(&out_map, u, ncols, n, a.by))
+    return cudaErrorInvalidValue;
+  const size_t smem = pcr_smem_t<double>(n, nparts);
+  const int threads = kPcrCols * nparts;
+  auto kern = pcr_kernel<double>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+  if (per_sm < 1) per_sm = 1;
+  const long long ntiles = (ncols + kPcrCols - 1) / kPcrCols;
+  long long grid = (long long)nsm * per_sm;
+  if (grid > ntiles) grid = ntiles;
+  kern<<<(unsigned)grid, threads, smem, st>>>(in_map, out_map, a, status);
+  return cudaGetLastError();
+}
+
+}  // namespace chanfs
