@@ -14,6 +14,10 @@ Metric: ns per grid point per step (lower is better).  With N GPUs each rank
 runs its own replica of the step (the solves share nothing), and the value is
 the max-over-ranks time divided by all ranks' points.  Rank 0 prints one JSON
 line.  `--impl reference` times the CPU oracle on a bounded sample instead.
+
+After the timed steps, the line's "mixed" object compares FP32 solves with
+FP64 iterative refinement (tolerance 1e-10) against the FP64 solve on the
+1024 x 768 x 512 uniform workload (`--no-mixed` skips it).
 """
 
 from __future__ import annotations
@@ -247,8 +251,67 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------
+# FP32 solves + FP64 refinement against the FP64 solve (1024 x 768 x 512)
+# ----------------------------------------------------------------------------
+
+def run_mixed(chanfs, torch, device, reps: int = 5, warmup: int = 3):
+    """Poisson solve of the 1024 x 768 x 512 uniform workload by an FP64 plan
+    and by a CFS_F32_REFINED plan (tolerance 1e-10, at most 4 FP32 solves),
+    each timed by CUDA events over `reps` solves after `warmup`; the refined
+    result is compared with the FP64 one.  Fields are 3.2 GB (larger than L2)."""
+    cfg = synth.PRECISION
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    npts = nx * ny * nz
+    dz = synth.grid_dz(cfg)
+    f = torch.from_numpy(synth.precision_rhs(cfg)).to(device)
+    stream = torch.cuda.current_stream(device)
+    out, res = {}, {}
+    for name, dtype in (("f64", chanfs.F64), ("f32_refined", chanfs.F32_REFINED)):
+        with chanfs.Plan(nx, ny, nz, cfg["lx"], cfg["ly"], dz, chanfs.NEUMANN, dtype) as plan:
+            p = torch.empty_like(f)
+            for _ in range(warmup):
+                plan.poisson_solve(f, out=p)
+            torch.cuda.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+            iters = []
+            ev[0].record(stream)
+            for r in range(reps):
+                plan.poisson_solve(f, out=p)
+                ev[r + 1].record(stream)
+                if dtype == chanfs.F32_REFINED:
+                    iters.append(plan.last_info())
+            torch.cuda.synchronize()
+            ms = [ev[r].elapsed_time(ev[r + 1]) for r in range(reps)]
+            entry = {"ms": round(statistics.median(ms), 4),
+                     "ns_per_pt": statistics.median(ms) * 1e6 / npts,
+                     "device_status": plan.check()}
+            if iters:
+                entry["fp32_solves"] = max(i for i, _ in iters)
+                entry["rel_residual"] = max(r for _, r in iters)
+            out[name] = entry
+            res[name] = p
+    err = float((res["f32_refined"] - res["f64"]).abs().max() / res["f64"].abs().max())
+    out.update({"workload": cfg["name"], "tol": 1e-10, "rel_err_vs_f64": err,
+                "speedup": out["f64"]["ms"] / out["f32_refined"]["ms"], "reps": reps,
+                "timing": "median of CUDA-event times of single solves on the launching stream; "
+                          "refined solves include their host reads of the residual norm"})
+    return out
+
+
+# ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
+
+def run_mixed_only(args):
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2502_06296_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2502_06296_gb300 import chanfs
+    mixed = run_mixed(chanfs, torch, torch.device("cuda", 0), reps=args.steps, warmup=args.warmup)
+    print(json.dumps({"mixed": mixed}), flush=True)
+    return 0
+
 
 def run_ours(args):
     import torch
@@ -401,11 +464,14 @@ def run_ours(args):
         "clocks": clock,
         "device_status": status,
     }
+    plan.close()
+    del f, rhs, p, us, ref_bits
+    if not args.no_mixed:
+        line["mixed"] = run_mixed(chanfs, torch, device)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     else:
         line["cpu_baseline"] = None
-    plan.close()
     print(json.dumps(line), flush=True)
     return 0
 
@@ -418,6 +484,10 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--nparts", type=int, default=0, help="PCR partitions (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the FP32-refined vs FP64 solve of the 1024x768x512 workload")
+    ap.add_argument("--mixed-only", action="store_true",
+                    help="run only the FP32-refined vs FP64 comparison and print its object")
     ap.add_argument("--nz", type=int, default=0,
                     help="override the wall-normal size (profiling captures only)")
     args = ap.parse_args(argv)
@@ -425,6 +495,8 @@ def main(argv=None):
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.mixed_only:
+        return run_mixed_only(args)
     return run_ours(args)
 
 
