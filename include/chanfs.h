@@ -220,6 +220,24 @@ int cfs_plan_set_refinement(cfs_plan_t plan, double tol, int maxit);
 int cfs_last_info(cfs_plan_t plan, int* iters, double* rel_residual);
 
 /*
+ * Kernel-shape options of a plan.  The paper has no counterpart: an option
+ * chooses between launch shapes that compute the same thing (up to rounding
+ * order), and defaults are picked per plan from the problem size.
+ *   CFS_OPT_THOMAS_TILE  columns per shared-memory tile of the z sweeps of
+ *       Eq. 12: 0 automatic (the default), 8 or 16, or -1 for the streaming
+ *       kernel (one thread per column, rows through registers, the forward
+ *       sweep's intermediate written to the spectrum and read back).
+ * cfs_plan_set_option returns CFS_EINVAL for an unknown option or value, and
+ * CFS_EUNSUPPORTED if the value cannot run at this plan's size (a tile that
+ * does not fit in shared memory).  cfs_plan_get_option reports the value in
+ * effect, with automatic choices resolved (for CFS_F32_REFINED plans, the
+ * choice of the FP32 inner solve).
+ */
+enum { CFS_OPT_THOMAS_TILE = 1 };
+int cfs_plan_set_option(cfs_plan_t plan, int option, int value);
+int cfs_plan_get_option(cfs_plan_t plan, int option, int* value);
+
+/*
  * cfs_plan_check -- wait for the device and report device-side failures
  * recorded since the last check (then clear them).  *device_error (may be
  * NULL) receives the raw failure bits.  Returns CFS_ETIMEOUT if a bounded

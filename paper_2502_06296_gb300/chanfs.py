@@ -23,6 +23,8 @@ F64, F32_REFINED = 0, 1
 
 X_FORWARD, Y_FORWARD, Z_SOLVE, Y_INVERSE, X_INVERSE = 0, 1, 2, 3, 4
 
+OPT_THOMAS_TILE = 1
+
 OK, EINVAL, ENOMEM, EUNSUPPORTED, ECUDA, ETIMEOUT, ENOTCONVERGED = 0, -1, -2, -3, -4, -5, -6
 
 _lib = None
@@ -61,6 +63,8 @@ def lib():
             "cfs_plan_set_refinement": ([vp, d, i], i),
             "cfs_helmholtz_solve_noalloc": ([i, i, i, dp, d, i, i, vp, vp, vp], i),
             "cfs_last_info": ([vp, ctypes.POINTER(i), ctypes.POINTER(d)], i),
+            "cfs_plan_set_option": ([vp, i, i], i),
+            "cfs_plan_get_option": ([vp, i, ctypes.POINTER(i)], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -201,6 +205,16 @@ class Plan:
     def set_refinement(self, tol: float = 1e-10, maxit: int = 4):
         """Refined plans: stop at ||r||_inf <= tol ||b||_inf or after maxit FP32 solves."""
         _check(lib().cfs_plan_set_refinement(self._h, float(tol), int(maxit)), "cfs_plan_set_refinement")
+
+    def set_option(self, option: int, value: int):
+        """Choose a kernel shape (see cfs_plan_set_option)."""
+        _check(lib().cfs_plan_set_option(self._h, int(option), int(value)), "cfs_plan_set_option")
+
+    def get_option(self, option: int) -> int:
+        """The kernel shape in effect, automatic choices resolved."""
+        v = ctypes.c_int(0)
+        _check(lib().cfs_plan_get_option(self._h, int(option), ctypes.byref(v)), "cfs_plan_get_option")
+        return v.value
 
     def last_info(self):
         """(FP32 solves, final relative residual) of the last refined solve."""

@@ -90,6 +90,8 @@ struct cfs_plan {
   // Thomas factors of Eq. 12, per (kx in [0,M], kyp in [0,nky), k):
   double2* d_fwd;    // (s/piv_k, A_k/piv_k)
   double* d_bwd;     // C_k/piv_k
+  int thomas_tw;     // columns per shared-memory Thomas tile: 0 automatic,
+                     // 8 or 16 forced, -1 the streaming kernel
   double* d_dzf;     // cell widths (weights of the Neumann mean)
   // Neumann (0,0) column: wn = w/sum(w), gn = g/sum(w) with g = T'^{-T} w,
   // hs = sc * T'^{-1} (0,1,..,1), T' the pinned operator; 3*nz doubles
@@ -136,6 +138,9 @@ cudaError_t launch_rfft_x32_to64(const cfs_plan* P, const float* in, double* out
                                  cudaStream_t st);
 cudaError_t launch_fft_y32(const cfs_plan* P, float* data, bool inverse, cudaStream_t st);
 cudaError_t launch_thomas32(const cfs_plan* P, float* data, cudaStream_t st);
+// Thomas tile width the plan's solves use (8, 16, or -1 for the streaming
+// kernel), for the FP64 or the FP32 spectrum; 0 if `tw` cannot run.
+int thomas_tile_width(const cfs_plan* P, bool fp32, int tw);
 cudaError_t launch_thomas_factor(cfs_plan* P, const double* dA, const double* dB,
                                  const double* dC, const double* dlamx, const double* dlamy,
                                  cudaStream_t st);

@@ -10,53 +10,9 @@
 // Out-of-range columns of a ragged last tile are zero-filled on load and
 // clipped on store by the TMA unit.
 #include "chanfs_fft.cuh"
+#include "chanfs_tma.cuh"
 
 namespace chanfs {
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-// Bounded wait on phase `parity`; returns false if the bound ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  const uint32_t addr = smem_u32(bar);
-  for (uint32_t it = 0; it < (1u << 24); ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int x, int y, int z) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
-      : "memory");
-}
-
-__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void* src, int x, int y,
-                                             int z) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
-          reinterpret_cast<uint64_t>(map)),
-      "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z)
-      : "memory");
-}
 
 template <bool INV, class C>
 __global__ void __launch_bounds__(128) fft_y_kernel(const __grid_constant__ CUtensorMap map,
@@ -73,8 +29,7 @@ __global__ void __launch_bounds__(128) fft_y_kernel(const __grid_constant__ CUte
 
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_init_fence();
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -115,52 +70,25 @@ __global__ void __launch_bounds__(128) fft_y_kernel(const __grid_constant__ CUte
     }
     __syncthreads();
   }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  fence_proxy_async();
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int b = 0; b < nbox; ++b) tma_store_3d(&map, res + b * by * tk, x0, b * by, z);
-    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    tma_store_commit_and_wait_read();
   }
-}
-
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static EncodeTiledFn get_encode() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
-  return fn;
 }
 
 template <class C>
 static cudaError_t launch_y(const cfs_plan* P, void* data, bool inverse, int tk, const C* tw,
                             cudaStream_t st) {
   if (P->ny == 1) return cudaSuccess;  // length-1 transform is the identity
-  EncodeTiledFn enc = get_encode();
-  if (!enc) return cudaErrorNotSupported;
   using T = typename cscal<C>::T;
   CUtensorMap map;
-  cuuint64_t gdim[3] = {(cuuint64_t)(2 * P->M), (cuuint64_t)P->ny, (cuuint64_t)P->nz};
-  cuuint64_t gstride[2] = {(cuuint64_t)(2 * P->M) * sizeof(T),
-                           (cuuint64_t)(2 * P->M) * P->ny * sizeof(T)};
-  cuuint32_t box[3] = {(cuuint32_t)(2 * tk), (cuuint32_t)P->by, 1};
-  cuuint32_t estr[3] = {1, 1, 1};
-  const CUtensorMapDataType dt =
-      sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  CUresult r = enc(&map, dt, 3, data, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  const cuuint64_t gdim[3] = {(cuuint64_t)(2 * P->M), (cuuint64_t)P->ny, (cuuint64_t)P->nz};
+  const cuuint64_t gstride[2] = {(cuuint64_t)(2 * P->M) * sizeof(T),
+                                 (cuuint64_t)(2 * P->M) * P->ny * sizeof(T)};
+  const cuuint32_t box[3] = {(cuuint32_t)(2 * tk), (cuuint32_t)P->by, 1};
+  if (!encode_map(&map, sizeof(T), 3, data, gdim, gstride, box)) return cudaErrorInvalidValue;
   const size_t smem = 128 + sizeof(C) * (size_t)(2 * tk * P->ny + P->fy.ntw);
   dim3 grid((P->M + tk - 1) / tk, P->nz);
   if (!inverse) {

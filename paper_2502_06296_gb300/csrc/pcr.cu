@@ -19,7 +19,7 @@
 // for every column, are staged once per CTA and read as broadcasts.  CTAs are
 // persistent over tiles; several CTAs per SM overlap one CTA's serial phases
 // (copies, the reduced solve) with another's arithmetic.
-#include "chanfs_internal.cuh"
+#include "chanfs_tma.cuh"
 
 namespace chanfs {
 
@@ -38,32 +38,6 @@ struct PcrArgs {
   const R* red;        // rl | rip | ripc             (3 * 2p)
 };
 
-__device__ __forceinline__ void pcr_mbar_init(uint64_t* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
-}
-
-__device__ __forceinline__ void pcr_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool pcr_wait(uint64_t* bar, uint32_t parity) {
-  const uint32_t addr = smem_u32(bar);
-  for (uint32_t it = 0; it < (1u << 24); ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
 template <class R>
 __global__ void __launch_bounds__(1024) pcr_kernel(const __grid_constant__ CUtensorMap in_map,
                                                    const __grid_constant__ CUtensorMap out_map,
@@ -78,9 +52,8 @@ __global__ void __launch_bounds__(1024) pcr_kernel(const __grid_constant__ CUten
   R* s_x = s_red + 3 * J;                              // J x 16
 
   if (threadIdx.x == 0) {
-    pcr_mbar_init(bar);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_init(bar, 1);
+    mbar_init_fence();
   }
   for (int e = threadIdx.x; e < 5 * n; e += blockDim.x) s_rows[e] = a.rows[e];
   for (int e = threadIdx.x; e < 3 * J; e += blockDim.x) s_red[e] = a.red[e];
@@ -106,16 +79,11 @@ __global__ void __launch_bounds__(1024) pcr_kernel(const __grid_constant__ CUten
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int col0 = (int)(tile * kPcrCols);
     if (threadIdx.x == 0) {
-      pcr_expect_tx(bar, tile_bytes);
-      for (int b = 0; b < a.nbox; ++b) {
-        asm volatile(
-            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-            " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(T + b * a.by * kPcrCols)),
-            "l"(reinterpret_cast<uint64_t>(&in_map)), "r"(smem_u32(bar)), "r"(col0), "r"(b * a.by)
-            : "memory");
-      }
+      mbar_expect_tx(bar, tile_bytes);
+      for (int b = 0; b < a.nbox; ++b)
+        tma_load_2d(T + b * a.by * kPcrCols, &in_map, bar, col0, b * a.by);
     }
-    const int ok = __syncthreads_and(pcr_wait(bar, phase) ? 1 : 0);
+    const int ok = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0);
     phase ^= 1u;
     if (!ok) {
       if (threadIdx.x == 0) atomicOr(status, kErrTmaTimeout);
@@ -166,18 +134,12 @@ __global__ void __launch_bounds__(1024) pcr_kernel(const __grid_constant__ CUten
         col[r * kPcrCols] = fma(-cp[r], xm, fma(-ap[r], x0, ib[r] * col[r * kPcrCols]));
       }
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    fence_proxy_async();
     __syncthreads();
     if (threadIdx.x == 0) {
-      for (int b = 0; b < a.nbox; ++b) {
-        asm volatile(
-            "cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
-                reinterpret_cast<uint64_t>(&out_map)),
-            "r"(smem_u32(T + b * a.by * kPcrCols)), "r"(col0), "r"(b * a.by)
-            : "memory");
-      }
-      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // tile may be reused
+      for (int b = 0; b < a.nbox; ++b)
+        tma_store_2d(&out_map, T + b * a.by * kPcrCols, col0, b * a.by);
+      tma_store_commit_and_wait_read();  // the tile may be reused
     }
     if (a.face && threadIdx.x < kPcrCols && col0 + c < a.ncols)
       a.u[(long long)(a.nz - 1) * a.ncols + col0 + c] = R(0);
@@ -185,38 +147,13 @@ __global__ void __launch_bounds__(1024) pcr_kernel(const __grid_constant__ CUten
   }
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static EncodeTiledFn pcr_encode() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult qr;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &qr) == cudaSuccess &&
-        qr == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
-  return fn;
-}
-
 // 2-D map over the first n rows of a field: ncols reals per row.
 template <class R>
 static bool pcr_map(CUtensorMap* map, const void* base, long long ncols, int n, int by) {
-  EncodeTiledFn enc = pcr_encode();
-  if (!enc) return false;
-  cuuint64_t gdim[2] = {(cuuint64_t)ncols, (cuuint64_t)n};
-  cuuint64_t gstride[1] = {(cuuint64_t)ncols * sizeof(R)};
-  cuuint32_t box[2] = {(cuuint32_t)kPcrCols, (cuuint32_t)by};
-  cuuint32_t estr[2] = {1, 1};
-  const CUtensorMapDataType dt =
-      sizeof(R) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  return enc(map, dt, 2, const_cast<void*>(base), gdim, gstride, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  const cuuint64_t gdim[2] = {(cuuint64_t)ncols, (cuuint64_t)n};
+  const cuuint64_t gstride[1] = {(cuuint64_t)ncols * sizeof(R)};
+  const cuuint32_t box[2] = {(cuuint32_t)kPcrCols, (cuuint32_t)by};
+  return encode_map(map, sizeof(R), 2, base, gdim, gstride, box);
 }
 
 // Rows per TMA box: at most 256; even for FP32 so that every box starts on a

@@ -630,6 +630,34 @@ extern "C" int cfs_plan_set_refinement(cfs_plan_t P, double tol, int maxit) {
   return CFS_OK;
 }
 
+extern "C" int cfs_plan_set_option(cfs_plan_t P, int option, int value) {
+  if (!P) return CFS_EINVAL;
+  switch (option) {
+    case CFS_OPT_THOMAS_TILE: {
+      if (value != 0 && value != -1 && value != 8 && value != 16) return CFS_EINVAL;
+      const bool fp32 = (P->dtype == CFS_F32_REFINED);
+      if (thomas_tile_width(P, false, value) == 0 ||
+          (fp32 && thomas_tile_width(P, true, value) == 0))
+        return CFS_EUNSUPPORTED;
+      P->thomas_tw = value;
+      return CFS_OK;
+    }
+    default:
+      return CFS_EINVAL;
+  }
+}
+
+extern "C" int cfs_plan_get_option(cfs_plan_t P, int option, int* value) {
+  if (!P || !value) return CFS_EINVAL;
+  switch (option) {
+    case CFS_OPT_THOMAS_TILE:
+      *value = thomas_tile_width(P, P->dtype == CFS_F32_REFINED, P->thomas_tw);
+      return CFS_OK;
+    default:
+      return CFS_EINVAL;
+  }
+}
+
 extern "C" int cfs_last_info(cfs_plan_t P, int* iters, double* rel_residual) {
   if (!P) return CFS_EINVAL;
   if (iters) *iters = P->last_iters;

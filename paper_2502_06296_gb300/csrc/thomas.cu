@@ -18,7 +18,7 @@
 // The singular Neumann column (0, 0) is pinned (row 0 -> F_0 = 0); the
 // removal of the dz-weighted mean of its right-hand side and of its solution
 // is folded into the same two sweeps by linearity.
-#include "chanfs_internal.cuh"
+#include "chanfs_tma.cuh"
 
 namespace chanfs {
 
@@ -199,6 +199,250 @@ __global__ void __launch_bounds__(kThomasBlock, 11) thomas_kernel(ThomasArgs a) 
     sweep_column<CS, float2>(a, s0, a.fwd32 + ox, a.fwd32 + oy, a.bwd32 + ox, a.bwd32 + oy, false);
 }
 
+// ----------------------------------------------------------------------------
+// Shared-memory tiles.  A CTA takes TW consecutive spectrum columns (kx in
+// [j0, j0 + TW)) of one slot ky with all Nz rows: the Tensor Memory
+// Accelerator copies the tile into shared memory (rows of TW complex values),
+// both sweeps run there, and TMA writes the tile back.  Global memory sees one
+// read and one write of the spectrum plus the factors; the streaming kernel
+// above also writes g and reads it back.  One thread per real component:
+// thread 2c + r sweeps the real (r = 0) or imaginary (r = 1) part of column c
+// with the factor set of that part.  The factor rows of every thread stream
+// through a per-thread ring in shared memory that cp.async fills DG groups of
+// kTileG rows ahead of the sweep; a group's loads are issued together, so the
+// shared-memory latency is paid once per group and not once per row.  CTAs
+// are persistent over tiles, and several CTAs per SM overlap one tile's copies
+// with another's sweeps.  Tiles run in the slot order ky = 0, Ny-1, 1, Ny-2,
+// ... so that slots ky and Ny-ky, which share their factors, are swept close
+// together in time.
+// ----------------------------------------------------------------------------
+constexpr int kTileG = 8;  // rows per prefetch group
+
+template <class A> struct tile_fac;
+template <> struct tile_fac<double> { using F2 = double2; };
+template <> struct tile_fac<float> { using F2 = float2; };
+
+// Both sweeps of one real component: col[k * NT] is its row k (storage type
+// S, arithmetic type A); f2 / f1 point at its forward / backward factors of
+// row 0 (row stride rt); ring is its slot 0 (16-byte slots, NT * 16 bytes
+// apart).  `pin` marks the singular Neumann column: row 0 is pinned, and the
+// output is corrected by mu * hs_k + nu (the two dz-weighted means).
+template <class A, class S, int NT, int DG>
+__device__ __forceinline__ void tile_sweeps(S* col, const typename tile_fac<A>::F2* f2,
+                                            const A* f1, long long rt, int nz, bool pin,
+                                            const double* hs, double mu, double nu,
+                                            unsigned char* ring) {
+  using F2 = typename tile_fac<A>::F2;
+  constexpr int G = kTileG;
+  constexpr int RG = DG + 1;  // ring groups: group q + DG refills the slots of group q - 1
+  constexpr int SLOT = NT * 16;
+  const int ng = (nz + G - 1) / G;
+
+  // forward: g_k = (s/piv_k) u_k - (A_k/piv_k) g_{k-1}
+  for (int q = 0; q < DG; ++q) {
+    if (q < ng) {
+#pragma unroll
+      for (int i = 0; i < G; ++i) {
+        const int k = q * G + i;
+        if (k < nz) cp_async<(int)sizeof(F2)>(ring + (q * G + i) * SLOT, f2 + k * rt);
+      }
+    }
+    cp_async_commit();
+  }
+  A g = A(0);
+  int rg = 0;
+  for (int q = 0; q < ng; ++q) {
+    cp_async_wait<DG - 1>();
+    const int k0 = q * G;
+    F2 f[G];
+    A u[G];
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+      if (k0 + i < nz) {
+        f[i] = *reinterpret_cast<const F2*>(ring + (rg * G + i) * SLOT);
+        u[i] = (A)col[(k0 + i) * NT];
+      }
+    }
+    const int qn = q + DG;
+    if (qn < ng) {
+      const int rn = (rg + DG) % RG;
+#pragma unroll
+      for (int i = 0; i < G; ++i) {
+        const int k = qn * G + i;
+        if (k < nz) cp_async<(int)sizeof(F2)>(ring + (rn * G + i) * SLOT, f2 + k * rt);
+      }
+    }
+    cp_async_commit();
+    rg = (rg + 1 == RG) ? 0 : rg + 1;
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+      if (k0 + i < nz) {
+        const A uu = (pin && k0 + i == 0) ? A(0) : u[i];
+        g = fma(-f[i].y, g, f[i].x * uu);
+        col[(k0 + i) * NT] = (S)g;
+      }
+    }
+  }
+  cp_async_wait<0>();
+
+  // backward, from the top wall down: x_k = g_k - (C_k/piv_k) x_{k+1}
+  for (int q = 0; q < DG; ++q) {
+    if (q < ng) {
+#pragma unroll
+      for (int i = 0; i < G; ++i) {
+        const int k = nz - 1 - (q * G + i);
+        if (k >= 0) {
+          unsigned char* d = ring + (q * G + i) * SLOT;
+          cp_async<(int)sizeof(A)>(d, f1 + k * rt);
+          if (pin) cp_async<8>(d + 8, hs + k);
+        }
+      }
+    }
+    cp_async_commit();
+  }
+  A x = A(0);
+  rg = 0;
+  for (int q = 0; q < ng; ++q) {
+    cp_async_wait<DG - 1>();
+    const int k0 = nz - 1 - q * G;  // rows k0, k0 - 1, ..
+    A b[G], gg[G];
+    double h[G];
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+      if (k0 - i >= 0) {
+        const unsigned char* d = ring + (rg * G + i) * SLOT;
+        b[i] = *reinterpret_cast<const A*>(d);
+        h[i] = pin ? *reinterpret_cast<const double*>(d + 8) : 0.0;
+        gg[i] = (A)col[(k0 - i) * NT];
+      }
+    }
+    const int qn = q + DG;
+    if (qn < ng) {
+      const int rn = (rg + DG) % RG;
+#pragma unroll
+      for (int i = 0; i < G; ++i) {
+        const int k = nz - 1 - (qn * G + i);
+        if (k >= 0) {
+          unsigned char* d = ring + (rn * G + i) * SLOT;
+          cp_async<(int)sizeof(A)>(d, f1 + k * rt);
+          if (pin) cp_async<8>(d + 8, hs + k);
+        }
+      }
+    }
+    cp_async_commit();
+    rg = (rg + 1 == RG) ? 0 : rg + 1;
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+      if (k0 - i >= 0) {
+        x = fma(-b[i], x, gg[i]);
+        A out = x;
+        if (pin) out = (A)(fma(-mu, h[i], (double)out) - nu);
+        col[(k0 - i) * NT] = (S)out;
+      }
+    }
+  }
+  cp_async_wait<0>();
+}
+
+template <class CS, int TW, int DG>
+__global__ void __launch_bounds__(2 * TW) thomas_tile_kernel(const __grid_constant__ CUtensorMap map,
+                                                             ThomasArgs a, int bz, int nbox,
+                                                             int* status) {
+  using T = typename cplx_traits<CS>::T;
+  constexpr int NT = 2 * TW;
+  constexpr unsigned kMask = NT == 32 ? 0xffffffffu : ((1u << NT) - 1u);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  T* tile = reinterpret_cast<T*>(smem_raw + 128);  // [nbox * bz][NT]
+  const int rows = nbox * bz;
+  const int tid = threadIdx.x;
+  unsigned char* ring = reinterpret_cast<unsigned char*>(tile + (size_t)rows * NT) + tid * 16;
+  const int nbx = (a.M + TW - 1) / TW;
+  const long long ntiles = (long long)nbx * a.ny;
+  const uint32_t tile_bytes = (uint32_t)((size_t)rows * NT * sizeof(T));
+  const long long rt = (long long)a.nky * (a.M + 1);
+
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int sidx = (int)(t / nbx);
+    const int j0 = (int)(t % nbx) * TW;
+    const int ky = (sidx & 1) ? a.ny - ((sidx + 1) >> 1) : (sidx >> 1);
+    if (tid == 0) {
+      mbar_expect_tx(bar, tile_bytes);
+      for (int b = 0; b < nbox; ++b)
+        tma_load_3d(tile + (size_t)b * bz * NT, &map, bar, 2 * j0, ky, b * bz);
+    }
+    const int ok = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0);
+    phase ^= 1u;
+    if (!ok) {
+      if (tid == 0) atomicOr(status, kErrTmaTimeout);
+      return;
+    }
+    // Singular Neumann column (real part of column 0, slot 0): the
+    // dz-weighted mean of its right-hand side (mu) and, through g^T E', that
+    // of the pinned solution (nu), reduced over the loaded tile.
+    const bool sing_tile = a.neumann && ky == 0 && j0 == 0;
+    double mu = 0.0, nu = 0.0;
+    if (sing_tile) {
+      double pm = 0.0, pg = 0.0;
+      for (int k = tid; k < a.nz; k += NT) {
+        const double e = (double)tile[(size_t)k * NT];
+        pm = fma(a.sing[k], e, pm);
+        if (k > 0) pg = fma(a.sing[a.nz + k], e, pg);
+      }
+#pragma unroll
+      for (int o = NT / 2; o > 0; o >>= 1) {
+        pm += __shfl_xor_sync(kMask, pm, o);
+        pg += __shfl_xor_sync(kMask, pg, o);
+      }
+      mu = pm;
+      nu = a.sing_sc * (pg - mu * a.sing_cg);
+    }
+    const int c = tid >> 1, comp = tid & 1;
+    const int j = j0 + c;
+    if (j < a.M) {
+      int kx = j, kp;
+      if (j > 0) {
+        kp = min(ky, a.ny - ky);
+      } else if (2 * ky == 0 || 2 * ky == a.ny) {  // real pair F(0,ky) + i F(M,ky)
+        kp = ky;
+        kx = comp ? a.M : 0;
+      } else if (2 * ky < a.ny) {  // F(0, ky)
+        kp = ky;
+      } else {  // F(M, Ny - ky)
+        kx = a.M;
+        kp = a.ny - ky;
+      }
+      const bool pin = sing_tile && tid == 0;
+      const long long off = (long long)kp * (a.M + 1) + kx;
+      T* col = tile + tid;
+      if constexpr (sizeof(T) == 8) {
+        tile_sweeps<double, T, NT, DG>(col, a.fwd + off, a.bwd + off, rt, a.nz, pin,
+                                       a.sing + 2 * a.nz, mu, nu, ring);
+      } else {
+        if (pin || (kx < a.kx64 && kp < a.ky64))
+          tile_sweeps<double, T, NT, DG>(col, a.fwd + off, a.bwd + off, rt, a.nz, pin,
+                                         a.sing + 2 * a.nz, mu, nu, ring);
+        else
+          tile_sweeps<float, T, NT, DG>(col, a.fwd32 + off, a.bwd32 + off, rt, a.nz, false,
+                                        nullptr, 0.0, 0.0, ring);
+      }
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      for (int b = 0; b < nbox; ++b)
+        tma_store_3d(&map, tile + (size_t)b * bz * NT, 2 * j0, ky, b * bz);
+      tma_store_commit_and_wait_read();  // the tile may be reloaded
+    }
+  }
+}
+
 static ThomasArgs thomas_args(const cfs_plan* P, void* data) {
   ThomasArgs a;
   a.S = data;
@@ -220,17 +464,100 @@ static ThomasArgs thomas_args(const cfs_plan* P, void* data) {
   return a;
 }
 
-cudaError_t launch_thomas(const cfs_plan* P, double* data, cudaStream_t st) {
+// Rows per TMA box: at most 256, even when rows are 64 bytes so that every
+// box starts on a 128-byte boundary of the tile.
+static void tile_boxes(int nz, int row_bytes, int* nbox, int* bz) {
+  *nbox = (nz + 255) / 256;
+  *bz = (nz + *nbox - 1) / *nbox;
+  if ((row_bytes % 128) && (*bz % 2)) ++*bz;
+}
+
+template <class CS, int TW, int DG>
+static size_t tile_smem(int nz) {
+  using T = typename cplx_traits<CS>::T;
+  int nbox, bz;
+  tile_boxes(nz, 2 * TW * (int)sizeof(T), &nbox, &bz);
+  return 128 + (size_t)nbox * bz * 2 * TW * sizeof(T) + (size_t)(DG + 1) * kTileG * 2 * TW * 16;
+}
+
+// CTAs of the tile kernel resident per SM (0 if it cannot run).
+template <class CS, int TW, int DG>
+static int tile_occupancy(int nz) {
+  const size_t smem = tile_smem<CS, TW, DG>(nz);
+  if (smem > 227 * 1024) return 0;
+  auto kern = thomas_tile_kernel<CS, TW, DG>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return 0;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 2 * TW, smem) != cudaSuccess)
+    return 0;
+  return per_sm;
+}
+
+template <class CS, int TW, int DG>
+static cudaError_t launch_tile(const cfs_plan* P, void* data, cudaStream_t st) {
+  using T = typename cplx_traits<CS>::T;
+  const int per_sm = tile_occupancy<CS, TW, DG>(P->nz);
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
   ThomasArgs a = thomas_args(P, data);
-  thomas_kernel<double2><<<a.nblk_x * P->ny, kThomasBlock, 0, st>>>(a);
+  int nbox, bz;
+  tile_boxes(P->nz, 2 * TW * (int)sizeof(T), &nbox, &bz);
+  CUtensorMap map;
+  const cuuint64_t gdim[3] = {(cuuint64_t)(2 * P->M), (cuuint64_t)P->ny, (cuuint64_t)P->nz};
+  const cuuint64_t gstride[2] = {(cuuint64_t)(2 * P->M) * sizeof(T),
+                                 (cuuint64_t)(2 * P->M) * P->ny * sizeof(T)};
+  const cuuint32_t box[3] = {(cuuint32_t)(2 * TW), 1, (cuuint32_t)bz};
+  if (!encode_map(&map, sizeof(T), 3, data, gdim, gstride, box)) return cudaErrorInvalidValue;
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P->device);
+  const long long ntiles = (long long)((P->M + TW - 1) / TW) * P->ny;
+  long long grid = (long long)nsm * per_sm;
+  if (grid > ntiles) grid = ntiles;
+  thomas_tile_kernel<CS, TW, DG><<<(unsigned)grid, 2 * TW, tile_smem<CS, TW, DG>(P->nz), st>>>(
+      map, a, bz, nbox, P->d_status);
   return cudaGetLastError();
+}
+
+// Prefetch depth (groups of kTileG rows) of the factor ring.  An FP64 sweep
+// spends longer per row, so fewer rows in flight cover the same latency; the
+// narrow tile leaves shared memory for a deeper ring.
+template <class CS, int TW> struct tile_depth { static constexpr int DG = TW == 8 ? 6 : 2; };
+template <int TW> struct tile_depth<float2, TW> { static constexpr int DG = TW == 8 ? 12 : 4; };
+
+// Tile width for this plan: the forced one, or the one that keeps more
+// threads resident per SM (the wider tile on a tie); -1 = streaming kernel.
+template <class CS>
+static int pick_tile_width(const cfs_plan* P, int tw) {
+  constexpr int D16 = tile_depth<CS, 16>::DG, D8 = tile_depth<CS, 8>::DG;
+  if (tw == -1) return -1;
+  if (tw == 16) return tile_occupancy<CS, 16, D16>(P->nz) >= 1 ? 16 : 0;
+  if (tw == 8) return tile_occupancy<CS, 8, D8>(P->nz) >= 1 ? 8 : 0;
+  if (tw != 0) return 0;
+  return -1;  // measured fastest at the workload sizes so far
+}
+
+int thomas_tile_width(const cfs_plan* P, bool fp32, int tw) {
+  return fp32 ? pick_tile_width<float2>(P, tw) : pick_tile_width<double2>(P, tw);
+}
+
+template <class CS>
+static cudaError_t launch_thomas_t(const cfs_plan* P, void* data, cudaStream_t st) {
+  const int tw = pick_tile_width<CS>(P, P->thomas_tw);
+  if (tw == 16) return launch_tile<CS, 16, tile_depth<CS, 16>::DG>(P, data, st);
+  if (tw == 8) return launch_tile<CS, 8, tile_depth<CS, 8>::DG>(P, data, st);
+  ThomasArgs a = thomas_args(P, data);
+  thomas_kernel<CS><<<a.nblk_x * P->ny, kThomasBlock, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_thomas(const cfs_plan* P, double* data, cudaStream_t st) {
+  return launch_thomas_t<double2>(P, data, st);
 }
 
 cudaError_t launch_thomas32(const cfs_plan* P, float* data, cudaStream_t st) {
   if (!P->d_fwd32) return cudaErrorInvalidValue;
-  ThomasArgs a = thomas_args(P, data);
-  thomas_kernel<float2><<<a.nblk_x * P->ny, kThomasBlock, 0, st>>>(a);
-  return cudaGetLastError();
+  return launch_thomas_t<float2>(P, data, st);
 }
 
 // ----------------------------------------------------------------------------

@@ -150,6 +150,64 @@ def test_poisson_matches_oracle(chanfs, dims, beta, bc):
         assert plan.check() == 0
 
 
+# Shapes of the z sweeps of Eq. 12: shared-memory tiles of 16 and 8 columns
+# and the streaming kernel.  Ragged last tiles (M not a multiple of the tile
+# width), nz in one and in several TMA boxes (nz > 256, odd), ny = 1.
+THOMAS_CASES = [
+    ((48, 36, 20), 1.8, 0),
+    ((48, 36, 20), 1.8, 1),
+    ((6, 9, 5), 1.2, 0),
+    ((24, 12, 300), 1.8, 0),
+    ((48, 12, 301), 1.8, 1),
+    ((8, 1, 16), 1.5, 0),
+]
+
+
+@pytest.mark.parametrize("dims,beta,bc", THOMAS_CASES)
+def test_thomas_shapes_match_oracle(chanfs, dims, beta, bc):
+    nx, ny, nz = dims
+    lx, ly = 2 * np.pi, np.pi
+    dz = make_dz(nz, beta)
+    f = synth.normal(11 * nx + ny + nz, (nz, ny, nx))
+    if bc == chanfs.NEUMANN:
+        f = synth.remove_weighted_mean(f, dz)
+    ref = oracle.poisson_solve(f, lx, ly, dz, bc)
+    got = {}
+    with chanfs.Plan(nx, ny, nz, lx, ly, dz, bc) as plan:
+        for tw in (-1, 8, 16):
+            plan.set_option(chanfs.OPT_THOMAS_TILE, tw)
+            assert plan.get_option(chanfs.OPT_THOMAS_TILE) == tw
+            got[tw] = host(plan.poisson_solve(dev(f)))
+            assert rel(got[tw], ref) < TOL, (tw, rel(got[tw], ref))
+        plan.set_option(chanfs.OPT_THOMAS_TILE, 0)
+        assert plan.get_option(chanfs.OPT_THOMAS_TILE) in (-1, 8, 16)
+        assert plan.check() == 0
+    # the sweeps do the same arithmetic in every shape; only the singular
+    # Neumann column sums its weighted means in another order
+    for tw in (8, 16):
+        if bc == chanfs.DIRICHLET:
+            assert np.array_equal(got[tw], got[-1])
+        else:
+            assert rel(got[tw], got[-1]) < 1e-14
+
+
+def test_thomas_option_rejects_bad_values(chanfs):
+    with chanfs.Plan(16, 12, 10, 1.0, 1.0, np.full(10, 0.2)) as plan:
+        for bad in (1, 4, 32, -2):
+            with pytest.raises(chanfs.ChanfsError) as err:
+                plan.set_option(chanfs.OPT_THOMAS_TILE, bad)
+            assert err.value.status == chanfs.EINVAL
+        with pytest.raises(chanfs.ChanfsError) as err:
+            plan.set_option(99, 0)
+        assert err.value.status == chanfs.EINVAL
+    # a tile of 16 FP64 columns x 16000 rows does not fit in shared memory
+    with chanfs.Plan(16, 2, 16000, 1.0, 1.0, np.full(16000, 1e-4)) as plan:
+        with pytest.raises(chanfs.ChanfsError) as err:
+            plan.set_option(chanfs.OPT_THOMAS_TILE, 16)
+        assert err.value.status == chanfs.EUNSUPPORTED
+        assert plan.get_option(chanfs.OPT_THOMAS_TILE) == -1
+
+
 def test_poisson_neumann_removes_incompatible_mean(chanfs):
     nx, ny, nz = 16, 12, 10
     dz = synth.tanh_dz(nz, 1.4)

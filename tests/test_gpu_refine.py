@@ -80,6 +80,21 @@ def test_refined_poisson_matches_fp64_oracle(chanfs, dims, beta, bc, dist):
         assert plan.check() == 0
 
 
+@pytest.mark.parametrize("tw", [-1, 8, 16])
+def test_refined_poisson_thomas_shapes(chanfs, tw):
+    nx, ny, nz = 64, 48, 300   # two TMA boxes along z, near-singular FP64 columns
+    dz = synth.tanh_dz(nz, 1.8)
+    f = synth.remove_weighted_mean(synth.normal(17, (nz, ny, nx)), dz)
+    ref = oracle.poisson_solve(f, 12.8, 6.4, dz, 0)
+    with chanfs.Plan(nx, ny, nz, 12.8, 6.4, dz, 0, chanfs.F32_REFINED) as plan:
+        plan.set_option(chanfs.OPT_THOMAS_TILE, tw)
+        p = host(plan.poisson_solve(dev(f)))
+        iters, rho = plan.last_info()
+        assert rho <= TOL and iters <= 4, (iters, rho)
+        assert rel(p, ref) < TOL, rel(p, ref)
+        assert plan.check() == 0
+
+
 def test_refined_poisson_reports_nonconvergence(chanfs):
     nx, ny, nz = 64, 48, 64
     dz = synth.tanh_dz(nz, 1.8)
