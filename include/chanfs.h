@@ -220,6 +220,38 @@ int cfs_plan_set_refinement(cfs_plan_t plan, double tol, int maxit);
 int cfs_last_info(cfs_plan_t plan, int* iters, double* rel_residual);
 
 /*
+ * Grouped solves.  The paper has no counterpart (it spreads one box over many
+ * GPUs; a group puts many independent boxes on one).  A group is built from
+ * up to 4096 CFS_F32_REFINED plans of the current device, of any sizes, z
+ * grids, walls and refinement settings.  Every stage of the refined Poisson
+ * solve (FP32 transforms and z sweeps, FP64 residual, means and correction) is
+ * then one kernel launch for all boxes, and the host waits once per
+ * refinement iteration for the whole group instead of once per box.  Each box
+ * follows its own refined solve exactly, stopping test included, so its
+ * result is bit-identical to cfs_poisson_solve on its plan.
+ *   cfs_group_create   plans: nplans distinct plan handles (not owned: keep
+ *                      them alive while the group exists).  CFS_EUNSUPPORTED
+ *                      if a plan is not CFS_F32_REFINED or lives on another
+ *                      device.
+ *   cfs_group_poisson_solve  f, p: host arrays of nplans device pointers,
+ *                      box b sized as plan b's fields; f[b] != p[b] (the
+ *                      right-hand side is read again after p is first
+ *                      written).  The solve uses the plans' work fields:
+ *                      solves on the same plans, grouped or not, must not
+ *                      overlap on the device.  Returns CFS_ENOTCONVERGED if a
+ *                      box missed its tolerance (every box is still written).
+ *   cfs_group_last_info  per box: FP32 solves used and final relative
+ *                      residual of the last grouped solve (arrays of nplans).
+ */
+typedef struct cfs_group* cfs_group_t;
+int cfs_group_create(cfs_group_t* group, int nplans, const cfs_plan_t* plans);
+int cfs_group_destroy(cfs_group_t group);
+int cfs_group_size(cfs_group_t group, int* nplans);
+int cfs_group_poisson_solve(cfs_group_t group, const double* const* f, double* const* p,
+                            void* stream);
+int cfs_group_last_info(cfs_group_t group, int* iters, double* rel_residual);
+
+/*
  * Kernel-shape options of a plan.  The paper has no counterpart: an option
  * chooses between launch shapes that compute the same thing (up to rounding
  * order), and defaults are picked per plan from the problem size.

@@ -63,6 +63,11 @@ def lib():
             "cfs_plan_set_refinement": ([vp, d, i], i),
             "cfs_helmholtz_solve_noalloc": ([i, i, i, dp, d, i, i, vp, vp, vp], i),
             "cfs_last_info": ([vp, ctypes.POINTER(i), ctypes.POINTER(d)], i),
+            "cfs_group_create": ([ctypes.POINTER(vp), i, ctypes.POINTER(vp)], i),
+            "cfs_group_destroy": ([vp], i),
+            "cfs_group_size": ([vp, ctypes.POINTER(i)], i),
+            "cfs_group_poisson_solve": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp], i),
+            "cfs_group_last_info": ([vp, ctypes.POINTER(i), ctypes.POINTER(d)], i),
             "cfs_plan_set_option": ([vp, i, i], i),
             "cfs_plan_get_option": ([vp, i, ctypes.POINTER(i)], i),
         }
@@ -248,6 +253,57 @@ def helmholtz_solve_noalloc(dz, c: float, rhs, loc: int = CENTER, nparts: int = 
                                              ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
            "cfs_helmholtz_solve_noalloc")
     return out
+
+
+class Group:
+    """Several CFS_F32_REFINED plans solved together, one launch per stage for
+    all boxes (see cfs_group_create).  The plans must outlive the group."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        n = len(self.plans)
+        arr = (ctypes.c_void_p * n)(*[p._h for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(lib().cfs_group_create(ctypes.byref(h), n, arr), "cfs_group_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cfs_group_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def poisson_solve(self, fs, outs=None, stream=None):
+        """fs: one float64 CUDA tensor per plan; returns the solutions."""
+        import torch
+        if len(fs) != len(self.plans):
+            raise ValueError("one right-hand side per plan")
+        outs = [torch.empty_like(f) for f in fs] if outs is None else list(outs)
+        n = len(self.plans)
+        fp = (ctypes.c_void_p * n)(*[p._field(f, "f").value for p, f in zip(self.plans, fs)])
+        pp = (ctypes.c_void_p * n)(*[p._field(o, "out").value for p, o in zip(self.plans, outs)])
+        _check(lib().cfs_group_poisson_solve(self._h, fp, pp, _stream_ptr(stream)),
+               "cfs_group_poisson_solve")
+        return outs
+
+    def last_info(self):
+        """Per plan: (FP32 solves, final relative residual) of the last solve."""
+        n = len(self.plans)
+        it = (ctypes.c_int * n)()
+        rho = (ctypes.c_double * n)()
+        _check(lib().cfs_group_last_info(self._h, it, rho), "cfs_group_last_info")
+        return list(zip(list(it), list(rho)))
 
 
 def _host_ptr(a, shape):

@@ -1,0 +1,127 @@
+// chanfs_group.cuh -- grouped launches: one kernel launch covers one stage of
+// the solves of several plans (boxes of different sizes).
+//
+// Box b owns the blocks [start[b], start[b+1]) of a grouped grid; each box
+// carries its own argument record, so boxes with different grids, tables and
+// coefficients share one launch.  A per-box `active` word (may be null) lets
+// iterative refinement drop boxes that have converged: their blocks return at
+// once.  The field pointers that change from call to call (right-hand side
+// and solution) sit in a small per-call table, GroupIo, read by the kernels
+// that touch them.
+#pragma once
+
+#include "chanfs_internal.cuh"
+
+namespace chanfs {
+
+// Output modes of the FP32 inverse x transform: in place, FP64 result written
+// to the solution, or added to it (the correction step p += delta).
+enum { OUT_SAME = 0, OUT_SET = 1, OUT_ADD = 2 };
+
+struct GroupMap {
+  const int* start;   // nbox + 1 block offsets
+  const int* active;  // nbox flags, or nullptr (every box runs)
+  int nbox;
+};
+
+struct GroupIo {
+  const double* f;  // right-hand side
+  double* p;        // solution
+};
+
+// Arguments of one box, per grouped kernel.
+struct XBox {  // packed real FFT along x (fft_x.cu)
+  FftDesc d;
+  const void* in;
+  void* out;
+  const void* tw;
+  const void* post;
+  long long nlines;
+  int lb;
+};
+
+struct YBox {  // FFT along y on TMA tiles (fft_y.cu); the map is 64-byte aligned
+  CUtensorMap map;
+  FftDesc d;
+  const void* tw;
+  int tk, by, nbox, ntx;
+  int* status;
+};
+
+struct ThomasArgs {  // z sweeps of Eq. 12 (thomas.cu)
+  void* S;               // spectrum (Nz, Ny, M) complex, double2 or float2
+  const double2* fwd;    // FP64 factors (s/piv, A/piv) per (k, kyp, kx in [0, M])
+  const double* bwd;     // FP64 C/piv
+  const float2* fwd32;   // FP32 copies (refined plans only)
+  const float* bwd32;
+  const double* sing;    // Neumann (0,0): wn | gn | hs, 3*nz (see below)
+  double sing_cg;        // g^T 1' / sum(w)
+  double sing_sc;        // the factor scale of the (0,0) column
+  int M, ny, nz, nky;
+  int nblk_x;            // blocks along kx per ky
+  int neumann;
+  int kx64, ky64;        // FP32 spectra: columns kx < kx64, |ky| < ky64 in FP64
+};
+
+struct ResBox {  // refinement residual and norms (refine.cu)
+  const double* zop;   // Poisson: A_k | B_k - 2/dx^2 - 2/dy^2 | C_k
+  const double* abc;   // Helmholtz: A' | B' | C'
+  const double* dzf;   // cell widths
+  double* partial;     // nz plane sums
+  double* mean;        // dz-weighted mean
+  float* r32;          // FP32 residual / correction
+  unsigned int* rmax;  // max |r| (float bits)
+  int nx, ny, nz, n;   // n = Helmholtz unknowns per column
+  double idx2, idy2;
+  int neumann;
+};
+
+// Blocks of the grouped mean subtraction for a field of n points.
+inline __host__ __device__ long long group_sub_blocks(long long n) {
+  const long long b = (n + 255) / 256;
+  return b < 1216 ? b : 1216;
+}
+
+#ifdef __CUDACC__
+
+// Box and box-local block of this block; false if the box is masked out.
+__device__ __forceinline__ bool group_block(const GroupMap& g, int* box, int* blk) {
+  const int b0 = (int)blockIdx.x;
+  int lo = 0, hi = g.nbox;  // start[lo] <= b0 < start[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(g.start + mid) <= b0) lo = mid;
+    else hi = mid;
+  }
+  *box = lo;
+  *blk = b0 - __ldg(g.start + lo);
+  if (!g.active) return true;
+  return *(volatile const int*)(g.active + lo) != 0;
+}
+
+#endif  // __CUDACC__
+
+// Grouped launchers (one per translation unit).  `total` = start[nbox];
+// `smem` = the largest dynamic shared memory any box needs.
+cudaError_t launch_rfft_x_group32(const XBox* boxes, GroupMap g, int total, size_t smem,
+                                  bool inverse, int out_mode, const GroupIo* io,
+                                  cudaStream_t st);
+cudaError_t launch_fft_y_group32(const YBox* boxes, GroupMap g, int total, size_t smem,
+                                 bool inverse, cudaStream_t st);
+cudaError_t launch_thomas_group32(const ThomasArgs* boxes, GroupMap g, int total,
+                                  cudaStream_t st);
+// Grouped refinement kernels (refine.cu), launched by group.cu.
+cudaError_t launch_group_refine_stage(int stage, const ResBox* boxes, GroupMap g, int total,
+                                      const GroupIo* io, int flag, cudaStream_t st);
+cudaError_t launch_group_update(const ResBox* boxes, int nbox, const float* fmax,
+                                const double* tol, const int* maxit, int it, int* active,
+                                int* iters, double* rho, int* nactive, cudaStream_t st);
+cudaError_t launch_group_fmax(const ResBox* boxes, int nbox, float* fmax, cudaStream_t st);
+enum { GSTAGE_PLANE_SUM = 0, GSTAGE_MEAN_FINAL = 1, GSTAGE_RESIDUAL = 2, GSTAGE_SUBTRACT = 3 };
+
+// Host-side descriptions of one plan's box for the grouped kernels.
+size_t x_group_box(const cfs_plan* P, bool inverse, XBox* box, int* blocks);
+size_t y_group_box(const cfs_plan* P, YBox* box, int* blocks);
+size_t thomas_group_box(const cfs_plan* P, ThomasArgs* box, int* blocks);
+
+}  // namespace chanfs

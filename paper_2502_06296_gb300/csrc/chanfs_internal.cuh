@@ -22,6 +22,8 @@ constexpr int kMaxNz = 16384;      // z cells
 constexpr int kPcrMaxParts = 64;   // z-partitions (half-warps) of the PCR kernel
 constexpr int kPcrMaxUnknowns = 1024;  // rows of a PCR tile in shared memory
 
+constexpr int kMaxGroup = 4096;     // plans of one grouped solve
+
 // Device status bits (plan->d_status)
 constexpr int kErrTmaTimeout = 1;
 

@@ -15,16 +15,16 @@
 // refinement; its inverse can write the FP64 result directly (OUT_SET) or add
 // it to an FP64 field (OUT_ADD), the correction step p += delta.
 #include "chanfs_fft.cuh"
+#include "chanfs_group.cuh"
 
 namespace chanfs {
 
-enum { OUT_SAME = 0, OUT_SET = 1, OUT_ADD = 2 };
-
+// Block `blk` of the transform: lines [blk * lb, blk * lb + lb).
 template <bool INV, class C, int OUT>
-__global__ void __launch_bounds__(128) rfft_x_kernel(const C* in, void* outv, long long nlines,
-                                                     FftDesc d, const C* __restrict__ twg,
-                                                     const C* __restrict__ postg, int lb,
-                                                     double scale, int scaled) {
+__device__ __forceinline__ void rfft_x_body(const C* in, void* outv, long long nlines,
+                                            const FftDesc& d, const C* __restrict__ twg,
+                                            const C* __restrict__ postg, int lb, double scale,
+                                            int scaled, long long blk) {
   using T = typename cscal<C>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int M = d.n;
@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(128) rfft_x_kernel(const C* in, void* outv, lo
   for (int e = threadIdx.x; e < d.ntw; e += blockDim.x) tw[e] = twg[e];
   for (int e = threadIdx.x; e < npost; e += blockDim.x) post[e] = postg[e];
 
-  const long long line0 = (long long)blockIdx.x * lb;
+  const long long line0 = blk * lb;
   const C zero = mkc<C>(T(0), T(0));
   const T h = T(0.5);
 
@@ -132,6 +132,28 @@ __global__ void __launch_bounds__(128) rfft_x_kernel(const C* in, void* outv, lo
   }
 }
 
+template <bool INV, class C, int OUT>
+__global__ void __launch_bounds__(128) rfft_x_kernel(const C* in, void* outv, long long nlines,
+                                                     FftDesc d, const C* __restrict__ twg,
+                                                     const C* __restrict__ postg, int lb,
+                                                     double scale, int scaled) {
+  rfft_x_body<INV, C, OUT>(in, outv, nlines, d, twg, postg, lb, scale, scaled, blockIdx.x);
+}
+
+// One launch for several boxes (FP32 inner solves of grouped refinement):
+// the inverse's FP64 output goes to each box's solution in `io`.
+template <bool INV, int OUT>
+__global__ void __launch_bounds__(128) rfft_x_group_kernel(const XBox* boxes, GroupMap g,
+                                                           const GroupIo* io) {
+  int b, blk;
+  if (!group_block(g, &b, &blk)) return;
+  const XBox& x = boxes[b];
+  void* out = (OUT == OUT_SAME) ? x.out : static_cast<void*>(io[b].p);
+  rfft_x_body<INV, float2, OUT>(static_cast<const float2*>(x.in), out, x.nlines, x.d,
+                                static_cast<const float2*>(x.tw),
+                                static_cast<const float2*>(x.post), x.lb, 1.0, 0, blk);
+}
+
 static int x_lines_per_cta(int M, size_t csize) {
   // about 16 KB of complex data per buffer
   const int target = (int)(16384 / csize);
@@ -173,6 +195,39 @@ cudaError_t launch_rfft_x32_to64(const cfs_plan* P, const float* in, double* out
                                  cudaStream_t st) {
   if (add) return launch_x<float2, OUT_ADD>(P, in, out, true, 1.0, P->d_twx32, P->d_post32, st);
   return launch_x<float2, OUT_SET>(P, in, out, true, 1.0, P->d_twx32, P->d_post32, st);
+}
+
+size_t x_group_box(const cfs_plan* P, bool inverse, XBox* box, int* blocks) {
+  const int lb = x_lines_per_cta(P->M, sizeof(float2));
+  box->d = P->fx;
+  box->in = P->d_r32;
+  box->out = inverse ? nullptr : P->d_r32;
+  box->tw = P->d_twx32;
+  box->post = P->d_post32;
+  box->nlines = (long long)P->ny * P->nz;
+  box->lb = lb;
+  *blocks = (int)((box->nlines + lb - 1) / lb);
+  return sizeof(float2) * (size_t)(2 * lb * P->M + P->fx.ntw + P->M / 2 + 1);
+}
+
+cudaError_t launch_rfft_x_group32(const XBox* boxes, GroupMap g, int total, size_t smem,
+                                  bool inverse, int out_mode, const GroupIo* io,
+                                  cudaStream_t st) {
+  if (total <= 0) return cudaSuccess;
+  if (!inverse) {
+    auto k = rfft_x_group_kernel<false, OUT_SAME>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<total, 128, smem, st>>>(boxes, g, io);
+  } else if (out_mode == OUT_ADD) {
+    auto k = rfft_x_group_kernel<true, OUT_ADD>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<total, 128, smem, st>>>(boxes, g, io);
+  } else {
+    auto k = rfft_x_group_kernel<true, OUT_SET>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<total, 128, smem, st>>>(boxes, g, io);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace chanfs

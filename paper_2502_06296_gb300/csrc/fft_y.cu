@@ -11,21 +11,22 @@
 // clipped on store by the TMA unit.
 #include "chanfs_fft.cuh"
 #include "chanfs_tma.cuh"
+#include "chanfs_group.cuh"
 
 namespace chanfs {
 
+// Tile bx (columns [bx * tk, bx * tk + tk)) of z plane z.
 template <bool INV, class C>
-__global__ void __launch_bounds__(128) fft_y_kernel(const __grid_constant__ CUtensorMap map,
-                                                    FftDesc d, const C* __restrict__ twg,
-                                                    int tk, int by, int nbox, int* status) {
+__device__ __forceinline__ void fft_y_body(const CUtensorMap* map, const FftDesc& d,
+                                           const C* __restrict__ twg, int tk, int by, int nbox,
+                                           int* status, int bx, int z) {
   using T = typename cscal<C>::T;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
   C* buf0 = reinterpret_cast<C*>(smem_raw + 128);
   C* buf1 = buf0 + tk * d.n;
   C* tw = buf1 + tk * d.n;
-  const int x0 = 2 * tk * blockIdx.x;  // in reals: a 16-byte aligned coordinate
-  const int z = blockIdx.y;
+  const int x0 = 2 * tk * bx;  // in reals: a 16-byte aligned coordinate
 
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
@@ -34,7 +35,7 @@ __global__ void __launch_bounds__(128) fft_y_kernel(const __grid_constant__ CUte
   __syncthreads();
   if (threadIdx.x == 0) {
     mbar_expect_tx(bar, (uint32_t)(nbox * by * tk * sizeof(C)));
-    for (int b = 0; b < nbox; ++b) tma_load_3d(buf0 + b * by * tk, &map, bar, x0, b * by, z);
+    for (int b = 0; b < nbox; ++b) tma_load_3d(buf0 + b * by * tk, map, bar, x0, b * by, z);
   }
   for (int e = threadIdx.x; e < d.ntw; e += blockDim.x) tw[e] = twg[e];
   // every thread waits (bounded); the CTA then agrees on one outcome, which
@@ -50,7 +51,7 @@ __global__ void __launch_bounds__(128) fft_y_kernel(const __grid_constant__ CUte
   // once more along y: slot ky (0 < 2ky < Ny) holds F(0,ky), slot Ny-ky holds
   // F(Nx/2,ky), and the self-conjugate slots (ky = 0, Ny/2) keep the real pair
   // F(0,ky) + i F(Nx/2,ky).  Every slot is then one column of Eq. 12.
-  if (INV && blockIdx.x == 0) {  // re-tangle before the inverse transform
+  if (INV && bx == 0) {  // re-tangle before the inverse transform
     for (int ky = 1 + threadIdx.x; 2 * ky < ny; ky += blockDim.x) {
       const C f0 = buf0[ky * tk], fm = buf0[(ny - ky) * tk];
       buf0[ky * tk] = mkc<C>(f0.x - fm.y, f0.y + fm.x);         // F0 + i FM
@@ -60,7 +61,7 @@ __global__ void __launch_bounds__(128) fft_y_kernel(const __grid_constant__ CUte
   }
   // element (y, c) of the tile sits at y*tk + c: element stride tk, batch stride 1
   C* res = stockham_smem<INV, true>(buf0, buf1, d, tk, tk, 1, tw);
-  if (!INV && blockIdx.x == 0) {  // untangle after the forward transform
+  if (!INV && bx == 0) {  // untangle after the forward transform
     for (int ky = 1 + threadIdx.x; 2 * ky < ny; ky += blockDim.x) {
       const C zz = res[ky * tk], zm = res[(ny - ky) * tk];
       // F0 = (Z + conj Zm)/2,  FM = -i (Z - conj Zm)/2
@@ -73,9 +74,26 @@ __global__ void __launch_bounds__(128) fft_y_kernel(const __grid_constant__ CUte
   fence_proxy_async();
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int b = 0; b < nbox; ++b) tma_store_3d(&map, res + b * by * tk, x0, b * by, z);
+    for (int b = 0; b < nbox; ++b) tma_store_3d(map, res + b * by * tk, x0, b * by, z);
     tma_store_commit_and_wait_read();
   }
+}
+
+template <bool INV, class C>
+__global__ void __launch_bounds__(128) fft_y_kernel(const __grid_constant__ CUtensorMap map,
+                                                    FftDesc d, const C* __restrict__ twg,
+                                                    int tk, int by, int nbox, int* status) {
+  fft_y_body<INV, C>(&map, d, twg, tk, by, nbox, status, blockIdx.x, blockIdx.y);
+}
+
+// One launch for several boxes (FP32 inner solves of grouped refinement).
+template <bool INV>
+__global__ void __launch_bounds__(128) fft_y_group_kernel(const YBox* boxes, GroupMap g) {
+  int b, blk;
+  if (!group_block(g, &b, &blk)) return;
+  const YBox& y = boxes[b];
+  fft_y_body<INV, float2>(&y.map, y.d, static_cast<const float2*>(y.tw), y.tk, y.by, y.nbox,
+                          y.status, blk % y.ntx, blk / y.ntx);
 }
 
 template <class C>
@@ -109,6 +127,39 @@ cudaError_t launch_fft_y(const cfs_plan* P, double* data, bool inverse, cudaStre
 
 cudaError_t launch_fft_y32(const cfs_plan* P, float* data, bool inverse, cudaStream_t st) {
   return launch_y<float2>(P, data, inverse, P->tk32, P->d_twy32, st);
+}
+
+size_t y_group_box(const cfs_plan* P, YBox* box, int* blocks) {
+  const int tk = P->tk32;
+  const cuuint64_t gdim[3] = {(cuuint64_t)(2 * P->M), (cuuint64_t)P->ny, (cuuint64_t)P->nz};
+  const cuuint64_t gstride[2] = {(cuuint64_t)(2 * P->M) * sizeof(float),
+                                 (cuuint64_t)(2 * P->M) * P->ny * sizeof(float)};
+  const cuuint32_t bx[3] = {(cuuint32_t)(2 * tk), (cuuint32_t)P->by, 1};
+  if (!encode_map(&box->map, sizeof(float), 3, P->d_r32, gdim, gstride, bx)) return 0;
+  box->d = P->fy;
+  box->tw = P->d_twy32;
+  box->tk = tk;
+  box->by = P->by;
+  box->nbox = P->nbox;
+  box->ntx = (P->M + tk - 1) / tk;
+  box->status = P->d_status;
+  *blocks = (P->ny == 1) ? 0 : box->ntx * P->nz;  // a length-1 transform is the identity
+  return 128 + sizeof(float2) * (size_t)(2 * tk * P->ny + P->fy.ntw);
+}
+
+cudaError_t launch_fft_y_group32(const YBox* boxes, GroupMap g, int total, size_t smem,
+                                 bool inverse, cudaStream_t st) {
+  if (total <= 0) return cudaSuccess;
+  if (!inverse) {
+    auto k = fft_y_group_kernel<false>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<total, 128, smem, st>>>(boxes, g);
+  } else {
+    auto k = fft_y_group_kernel<true>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<total, 128, smem, st>>>(boxes, g);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace chanfs

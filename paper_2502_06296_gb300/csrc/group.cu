@@ -1,0 +1,338 @@
+// group.cu -- grouped refined solves: the Poisson solves of several plans
+// (boxes of different sizes, grids and walls) run together, every stage of
+// the FP32 inner solve and of the FP64 refinement launched once for all boxes.
+//
+// Each box follows exactly the iteration of its own refined solve (the same
+// kernels' arithmetic and block partition, the same stopping rule on its own
+// tolerance and FP32-solve budget), so a box's result does not depend on the
+// group it is solved in.  Boxes that converge drop out of the later stages
+// through a device-side mask; the host reads one word per iteration (are any
+// boxes still iterating?) instead of one per box.
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "chanfs_group.cuh"
+
+using namespace chanfs;
+
+namespace {
+
+template <class T>
+cudaError_t upload(T** dst, const std::vector<T>& src) {
+  if (src.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc(dst, sizeof(T) * src.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+  return e;
+}
+
+// Block offsets of a grouped launch from per-box block counts.
+std::vector<int> offsets(const std::vector<int>& blocks, int* total) {
+  std::vector<int> start(blocks.size() + 1, 0);
+  for (size_t b = 0; b < blocks.size(); ++b) start[b + 1] = start[b] + blocks[b];
+  *total = start.back();
+  return start;
+}
+
+}  // namespace
+
+struct cfs_group {
+  int nbox = 0;
+  int device = 0;
+  std::vector<cfs_plan*> plans;
+  std::vector<int> neumann;
+  // per-kernel descriptors and block offsets
+  XBox* d_xf = nullptr;
+  XBox* d_xi = nullptr;
+  YBox* d_y = nullptr;
+  ThomasArgs* d_th = nullptr;
+  ResBox* d_res = nullptr;
+  int *d_sx = nullptr, *d_sy = nullptr, *d_sth = nullptr, *d_sres = nullptr;
+  int *d_splane = nullptr, *d_sone = nullptr, *d_ssub = nullptr;
+  int tx = 0, ty = 0, tth = 0, tres = 0, tplane = 0, tone = 0, tsub = 0;
+  size_t smem_x = 0, smem_y = 0;
+  // refinement state
+  int* d_active = nullptr;  // boxes still iterating
+  int* d_mean = nullptr;    // boxes whose mean is removed (Neumann, nonzero rhs)
+  float* d_fmax = nullptr;
+  double* d_tol = nullptr;
+  int* d_maxit = nullptr;
+  int* d_iters = nullptr;
+  double* d_rho = nullptr;
+  int* d_nactive = nullptr;
+  GroupIo* d_io = nullptr;
+  GroupIo* h_io = nullptr;  // pinned staging of the per-call pointers
+  cudaEvent_t io_copied = nullptr;
+  std::vector<int> last_iters;
+  std::vector<double> last_rho;
+};
+
+static void group_free(cfs_group* G) {
+  void* ptrs[] = {G->d_xf,  G->d_xi,   G->d_y,     G->d_th,   G->d_res,   G->d_sx,
+                  G->d_sy,  G->d_sth,  G->d_sres,  G->d_splane, G->d_sone, G->d_ssub,
+                  G->d_active, G->d_mean, G->d_fmax, G->d_tol, G->d_maxit, G->d_iters,
+                  G->d_rho, G->d_nactive, G->d_io};
+  for (void* p : ptrs) cudaFree(p);
+  if (G->h_io) cudaFreeHost(G->h_io);
+  if (G->io_copied) cudaEventDestroy(G->io_copied);
+  delete G;
+}
+
+extern "C" int cfs_group_create(cfs_group_t* out, int nplans, const cfs_plan_t* plans) {
+  if (!out) return CFS_EINVAL;
+  *out = nullptr;
+  if (nplans < 1 || nplans > kMaxGroup || !plans) return CFS_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CFS_ECUDA;
+  for (int b = 0; b < nplans; ++b) {
+    if (!plans[b]) return CFS_EINVAL;
+    if (plans[b]->dtype != CFS_F32_REFINED || plans[b]->device != dev) return CFS_EUNSUPPORTED;
+    for (int c = 0; c < b; ++c)
+      if (plans[c] == plans[b]) return CFS_EINVAL;  // boxes share the plan's work field
+  }
+  cfs_group* G = new (std::nothrow) cfs_group();
+  if (!G) return CFS_ENOMEM;
+  G->nbox = nplans;
+  G->device = dev;
+  std::vector<XBox> xf(nplans), xi(nplans);
+  std::vector<YBox> y(nplans);
+  std::vector<ThomasArgs> th(nplans);
+  std::vector<ResBox> res(nplans);
+  std::vector<int> bx(nplans), by(nplans), bth(nplans), bres(nplans), bplane(nplans),
+      bone(nplans, 1), bsub(nplans), maxit(nplans);
+  std::vector<double> tol(nplans);
+  int rc = CFS_OK;
+  for (int b = 0; b < nplans && !rc; ++b) {
+    cfs_plan* P = plans[b];
+    G->plans.push_back(P);
+    G->neumann.push_back(P->bc == CFS_BC_NEUMANN);
+    G->smem_x = std::max(G->smem_x, x_group_box(P, false, &xf[b], &bx[b]));
+    x_group_box(P, true, &xi[b], &bx[b]);
+    const size_t sy = y_group_box(P, &y[b], &by[b]);
+    if (!sy) rc = CFS_ECUDA;
+    G->smem_y = std::max(G->smem_y, sy);
+    thomas_group_box(P, &th[b], &bth[b]);
+    const long long nxy = (long long)P->nx * P->ny;
+    ResBox& r = res[b];
+    memset(&r, 0, sizeof(r));
+    r.zop = P->d_zop;
+    r.dzf = P->d_dzf;
+    r.partial = P->d_red + 2;
+    r.mean = P->d_red + 1;
+    r.r32 = P->d_r32;
+    r.rmax = reinterpret_cast<unsigned int*>(P->d_red);
+    r.nx = P->nx;
+    r.ny = P->ny;
+    r.nz = P->nz;
+    r.n = P->nz;
+    const double dx = P->lx / P->nx, dy = P->ly / P->ny;
+    r.idx2 = 1.0 / (dx * dx);
+    r.idy2 = 1.0 / (dy * dy);
+    r.neumann = (P->bc == CFS_BC_NEUMANN);
+    bres[b] = (int)((nxy + 127) / 128);
+    bplane[b] = P->nz;
+    bsub[b] = (int)group_sub_blocks(nxy * P->nz);
+    tol[b] = P->tol;
+    maxit[b] = P->maxit;
+  }
+  cudaError_t e = rc ? cudaErrorInvalidValue : cudaSuccess;
+  std::vector<int> sx = offsets(bx, &G->tx), sy = offsets(by, &G->ty), sth = offsets(bth, &G->tth),
+                   sres = offsets(bres, &G->tres), splane = offsets(bplane, &G->tplane),
+                   sone = offsets(bone, &G->tone), ssub = offsets(bsub, &G->tsub);
+  if (e == cudaSuccess) e = upload(&G->d_xf, xf);
+  if (e == cudaSuccess) e = upload(&G->d_xi, xi);
+  if (e == cudaSuccess) e = upload(&G->d_y, y);
+  if (e == cudaSuccess) e = upload(&G->d_th, th);
+  if (e == cudaSuccess) e = upload(&G->d_res, res);
+  if (e == cudaSuccess) e = upload(&G->d_sx, sx);
+  if (e == cudaSuccess) e = upload(&G->d_sy, sy);
+  if (e == cudaSuccess) e = upload(&G->d_sth, sth);
+  if (e == cudaSuccess) e = upload(&G->d_sres, sres);
+  if (e == cudaSuccess) e = upload(&G->d_splane, splane);
+  if (e == cudaSuccess) e = upload(&G->d_sone, sone);
+  if (e == cudaSuccess) e = upload(&G->d_ssub, ssub);
+  if (e == cudaSuccess) e = upload(&G->d_tol, tol);
+  if (e == cudaSuccess) e = upload(&G->d_maxit, maxit);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_active, sizeof(int) * nplans);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_mean, sizeof(int) * nplans);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_fmax, sizeof(float) * nplans);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_iters, sizeof(int) * nplans);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_rho, sizeof(double) * nplans);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_nactive, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_io, sizeof(GroupIo) * nplans);
+  if (e == cudaSuccess) e = cudaMallocHost(&G->h_io, sizeof(GroupIo) * nplans);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G->io_copied, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    group_free(G);
+    return rc ? rc : (e == cudaErrorMemoryAllocation ? CFS_ENOMEM : CFS_ECUDA);
+  }
+  G->last_iters.assign(nplans, 0);
+  G->last_rho.assign(nplans, 0.0);
+  *out = G;
+  return CFS_OK;
+}
+
+extern "C" int cfs_group_destroy(cfs_group_t G) {
+  if (!G) return CFS_EINVAL;
+  cudaDeviceSynchronize();
+  group_free(G);
+  return CFS_OK;
+}
+
+static int rc_of(cudaError_t e) { return e == cudaSuccess ? CFS_OK : CFS_ECUDA; }
+
+extern "C" int cfs_group_poisson_solve(cfs_group_t G, const double* const* f, double* const* p,
+                                       void* stream) {
+  if (!G || !f || !p) return CFS_EINVAL;
+  const int nb = G->nbox;
+  for (int b = 0; b < nb; ++b)
+    if (!f[b] || !p[b] || static_cast<const void*>(f[b]) == static_cast<const void*>(p[b]))
+      return CFS_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the staging buffer of the previous call must have been copied
+  cudaError_t e = cudaEventSynchronize(G->io_copied);
+  for (int b = 0; b < nb && e == cudaSuccess; ++b) G->h_io[b] = GroupIo{f[b], p[b]};
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(G->d_io, G->h_io, sizeof(GroupIo) * nb, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaEventRecord(G->io_copied, st);
+  if (e != cudaSuccess) return CFS_ECUDA;
+
+  // the plans' current refinement settings
+  std::vector<double> tol(nb);
+  std::vector<int> maxits(nb);
+  for (int b = 0; b < nb; ++b) {
+    tol[b] = G->plans[b]->tol;
+    maxits[b] = G->plans[b]->maxit;
+  }
+  e = cudaMemcpyAsync(G->d_tol, tol.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(G->d_maxit, maxits.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return CFS_ECUDA;
+
+  std::vector<int> on(nb), mean_on(nb);
+  for (int b = 0; b < nb; ++b) mean_on[b] = G->neumann[b];
+  const GroupMap all{nullptr, nullptr, nb};
+  GroupMap g = all;
+  // remove the dz-weighted mean of f (Neumann boxes)
+  e = cudaMemcpyAsync(G->d_mean, mean_on.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    g.start = G->d_splane;
+    g.active = G->d_mean;
+    e = launch_group_refine_stage(GSTAGE_PLANE_SUM, G->d_res, g, G->tplane, G->d_io, 0, st);
+  }
+  if (e == cudaSuccess) {
+    g.start = G->d_sone;
+    e = launch_group_refine_stage(GSTAGE_MEAN_FINAL, G->d_res, g, G->tone, G->d_io, 0, st);
+  }
+  // r_0 = f - mean and its max-norm (the reference of each box)
+  if (e == cudaSuccess) {
+    g.start = G->d_sres;
+    g.active = nullptr;
+    e = launch_group_refine_stage(GSTAGE_RESIDUAL, G->d_res, g, G->tres, G->d_io, 0, st);
+  }
+  if (e == cudaSuccess) e = launch_group_fmax(G->d_res, nb, G->d_fmax, st);
+  std::vector<float> fmax(nb);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(fmax.data(), G->d_fmax, sizeof(float) * nb, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return CFS_ECUDA;
+  int nactive = 0;
+  for (int b = 0; b < nb; ++b) {
+    cfs_plan* P = G->plans[b];
+    on[b] = fmax[b] != 0.0f;
+    mean_on[b] = on[b] && G->neumann[b];
+    nactive += on[b];
+    G->last_iters[b] = 0;
+    G->last_rho[b] = 0.0;
+    if (!on[b])  // zero right-hand side: zero solution
+      e = cudaMemsetAsync(p[b], 0, sizeof(double) * (size_t)P->nx * P->ny * P->nz, st);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(G->d_active, on.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(G->d_mean, mean_on.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st);
+  int maxit = 0;
+  for (int b = 0; b < nb; ++b) maxit = std::max(maxit, G->plans[b]->maxit);
+  g.active = G->d_active;
+  for (int it = 0; it < maxit && nactive > 0 && e == cudaSuccess; ++it) {
+    g.start = G->d_sx;
+    e = launch_rfft_x_group32(G->d_xf, g, G->tx, G->smem_x, false, OUT_SAME, G->d_io, st);
+    if (e == cudaSuccess) {
+      g.start = G->d_sy;
+      e = launch_fft_y_group32(G->d_y, g, G->ty, G->smem_y, false, st);
+    }
+    if (e == cudaSuccess) {
+      g.start = G->d_sth;
+      e = launch_thomas_group32(G->d_th, g, G->tth, st);
+    }
+    if (e == cudaSuccess) {
+      g.start = G->d_sy;
+      e = launch_fft_y_group32(G->d_y, g, G->ty, G->smem_y, true, st);
+    }
+    if (e == cudaSuccess) {
+      g.start = G->d_sx;
+      e = launch_rfft_x_group32(G->d_xi, g, G->tx, G->smem_x, true, it > 0 ? OUT_ADD : OUT_SET,
+                                G->d_io, st);
+    }
+    if (e == cudaSuccess) {
+      g.start = G->d_sres;
+      e = launch_group_refine_stage(GSTAGE_RESIDUAL, G->d_res, g, G->tres, G->d_io, 1, st);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(G->d_nactive, 0, sizeof(int), st);
+    if (e == cudaSuccess)
+      e = launch_group_update(G->d_res, nb, G->d_fmax, G->d_tol, G->d_maxit, it, G->d_active,
+                              G->d_iters, G->d_rho, G->d_nactive, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&nactive, G->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  // restore the zero dz-weighted mean of p (Neumann boxes), as the single solve does
+  g.active = G->d_mean;
+  if (e == cudaSuccess) {
+    g.start = G->d_splane;
+    e = launch_group_refine_stage(GSTAGE_PLANE_SUM, G->d_res, g, G->tplane, G->d_io, 1, st);
+  }
+  if (e == cudaSuccess) {
+    g.start = G->d_sone;
+    e = launch_group_refine_stage(GSTAGE_MEAN_FINAL, G->d_res, g, G->tone, G->d_io, 0, st);
+  }
+  if (e == cudaSuccess) {
+    g.start = G->d_ssub;
+    e = launch_group_refine_stage(GSTAGE_SUBTRACT, G->d_res, g, G->tsub, G->d_io, 0, st);
+  }
+  std::vector<int> iters(nb);
+  std::vector<double> rho(nb);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(iters.data(), G->d_iters, sizeof(int) * nb, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(rho.data(), G->d_rho, sizeof(double) * nb, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return rc_of(e);
+  int rc = CFS_OK;
+  for (int b = 0; b < nb; ++b) {
+    if (!on[b]) continue;
+    G->last_iters[b] = iters[b];
+    G->last_rho[b] = rho[b];
+    G->plans[b]->last_iters = iters[b];
+    G->plans[b]->last_rho = rho[b];
+    if (!(rho[b] <= G->plans[b]->tol)) rc = CFS_ENOTCONVERGED;
+  }
+  return rc;
+}
+
+extern "C" int cfs_group_last_info(cfs_group_t G, int* iters, double* rel_residual) {
+  if (!G) return CFS_EINVAL;
+  for (int b = 0; b < G->nbox; ++b) {
+    if (iters) iters[b] = G->last_iters[b];
+    if (rel_residual) rel_residual[b] = G->last_rho[b];
+  }
+  return CFS_OK;
+}
+
+extern "C" int cfs_group_size(cfs_group_t G, int* nplans) {
+  if (!G || !nplans) return CFS_EINVAL;
+  *nplans = G->nbox;
+  return CFS_OK;
+}

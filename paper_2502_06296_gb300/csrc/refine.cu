@@ -14,7 +14,7 @@
 #include <math.h>
 #include <string.h>
 
-#include "chanfs_internal.cuh"
+#include "chanfs_group.cuh"
 
 namespace chanfs {
 
@@ -37,10 +37,10 @@ __device__ __forceinline__ void block_max_to(float v, unsigned int* out) {
 // Neumann compatibility: the dz-weighted mean of f, reduced in a fixed order
 // (one block per z plane, then one block over the planes) so that results
 // are bit-reproducible.
-__global__ void plane_sum_kernel(const double* __restrict__ f, long long nxy, const double* dzf,
-                                 double* partial) {
+__device__ __forceinline__ void plane_sum_body(const double* __restrict__ f, long long nxy,
+                                               const double* dzf, double* partial, int k) {
   __shared__ double sh[256];
-  const double* plane = f + (long long)blockIdx.x * nxy;
+  const double* plane = f + (long long)k * nxy;
   double s = 0.0;
   for (long long i = threadIdx.x; i < nxy; i += blockDim.x) s += plane[i];
   sh[threadIdx.x] = s;
@@ -49,11 +49,16 @@ __global__ void plane_sum_kernel(const double* __restrict__ f, long long nxy, co
     if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) partial[blockIdx.x] = dzf[blockIdx.x] * sh[0];
+  if (threadIdx.x == 0) partial[k] = dzf[k] * sh[0];
 }
 
-__global__ void mean_final_kernel(const double* partial, int nz, const double* dzf, long long nxy,
-                                  double* mean) {
+__global__ void plane_sum_kernel(const double* __restrict__ f, long long nxy, const double* dzf,
+                                 double* partial) {
+  plane_sum_body(f, nxy, dzf, partial, blockIdx.x);
+}
+
+__device__ __forceinline__ void mean_final_body(const double* partial, int nz, const double* dzf,
+                                                long long nxy, double* mean) {
   __shared__ double sh[256], shw[256];
   double s = 0.0, w = 0.0;
   for (int k = threadIdx.x; k < nz; k += blockDim.x) {
@@ -73,16 +78,21 @@ __global__ void mean_final_kernel(const double* partial, int nz, const double* d
   if (threadIdx.x == 0) *mean = sh[0] / (shw[0] * (double)nxy);
 }
 
+__global__ void mean_final_kernel(const double* partial, int nz, const double* dzf, long long nxy,
+                                  double* mean) {
+  mean_final_body(partial, nz, dzf, nxy, mean);
+}
+
 // r = (f - mean) - L p, written as FP32, and max |r|.  One thread per (x, y)
 // column marching up in z with p_{k-1}, p_k, p_{k+1} in registers; the x and
 // y neighbours of a plane are shared through L1.  p == nullptr: r = f - mean.
 // zop = [A_k | B_k - 2/dx^2 - 2/dy^2 | C_k]; FP64: 9 instructions per point.
-__global__ void __launch_bounds__(kResBlock) poisson_residual_kernel(
+__device__ __forceinline__ void poisson_residual_body(
     const double* __restrict__ f, const double* __restrict__ p, const double* __restrict__ zop,
     const double* __restrict__ mean, float* __restrict__ r32, unsigned int* rmax, int nx, int ny,
-    int nz, double idx2, double idy2) {
+    int nz, double idx2, double idy2, long long blk) {
   const long long nxy = (long long)nx * ny;
-  const long long col = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long col = blk * blockDim.x + threadIdx.x;
   float vmax = 0.0f;
   if (col < nxy) {
     const double mu = mean ? *mean : 0.0;
@@ -114,6 +124,13 @@ __global__ void __launch_bounds__(kResBlock) poisson_residual_kernel(
     }
   }
   block_max_to(vmax, rmax);
+}
+
+__global__ void __launch_bounds__(kResBlock) poisson_residual_kernel(
+    const double* __restrict__ f, const double* __restrict__ p, const double* __restrict__ zop,
+    const double* __restrict__ mean, float* __restrict__ r32, unsigned int* rmax, int nx, int ny,
+    int nz, double idx2, double idy2) {
+  poisson_residual_body(f, p, zop, mean, r32, rmax, nx, ny, nz, idx2, idy2, blockIdx.x);
 }
 
 // Helmholtz: u (+)= delta, then r = rhs - (I - c L_z) u, as FP32, and max |r|.
@@ -159,12 +176,115 @@ __global__ void __launch_bounds__(kResBlock) helm_residual_kernel(
 }
 
 // p -= mean (the dz-weighted mean computed by the two kernels above).
+__device__ __forceinline__ void subtract_mean_body(double* __restrict__ p, long long n,
+                                                   const double* __restrict__ mean, long long blk,
+                                                   long long nblk) {
+  const double mu = *mean;
+  for (long long i = blk * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) p[i] -= mu;
+}
+
 __global__ void subtract_mean_kernel(double* __restrict__ p, long long n,
                                      const double* __restrict__ mean) {
-  const double mu = *mean;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    p[i] -= mu;
+  subtract_mean_body(p, n, mean, blockIdx.x, gridDim.x);
+}
+
+// ----------------------------------------------------------------------------
+// Grouped forms: one launch per stage for every box of a group (the same
+// per-box arithmetic and block partition as the single-plan kernels).
+// ----------------------------------------------------------------------------
+
+__global__ void plane_sum_group_kernel(const ResBox* boxes, GroupMap g, const GroupIo* io,
+                                       int of_solution) {
+  int b, blk;
+  if (!group_block(g, &b, &blk)) return;
+  const ResBox& r = boxes[b];
+  const double* src = of_solution ? io[b].p : io[b].f;
+  plane_sum_body(src, (long long)r.nx * r.ny, r.dzf, r.partial, blk);
+}
+
+__global__ void mean_final_group_kernel(const ResBox* boxes, GroupMap g) {
+  int b, blk;
+  if (!group_block(g, &b, &blk)) return;
+  const ResBox& r = boxes[b];
+  mean_final_body(r.partial, r.nz, r.dzf, (long long)r.nx * r.ny, r.mean);
+}
+
+__global__ void __launch_bounds__(kResBlock) poisson_residual_group_kernel(const ResBox* boxes,
+                                                                           GroupMap g,
+                                                                           const GroupIo* io,
+                                                                           int with_p) {
+  int b, blk;
+  if (!group_block(g, &b, &blk)) return;
+  const ResBox& r = boxes[b];
+  poisson_residual_body(io[b].f, with_p ? io[b].p : nullptr, r.zop, r.neumann ? r.mean : nullptr,
+                        r.r32, r.rmax, r.nx, r.ny, r.nz, r.idx2, r.idy2, blk);
+}
+
+__global__ void subtract_mean_group_kernel(const ResBox* boxes, GroupMap g, const GroupIo* io) {
+  int b, blk;
+  if (!group_block(g, &b, &blk)) return;
+  const ResBox& r = boxes[b];
+  const long long n = (long long)r.nx * r.ny * r.nz;
+  subtract_mean_body(io[b].p, n, r.mean, blk, group_sub_blocks(n));
+}
+
+// After a residual: each active box takes its relative residual and leaves
+// the iteration once it meets its tolerance or has used its FP32 solves.
+// One thread per box; `nactive` counts the boxes still iterating.
+__global__ void group_update_kernel(const ResBox* boxes, int nbox, const float* fmax,
+                                    const double* tol, const int* maxit, int it, int* active,
+                                    int* iters, double* rho, int* nactive) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbox || !active[b]) return;
+  unsigned int* w = boxes[b].rmax;
+  const float rmax = __uint_as_float(*w);
+  *w = 0u;
+  rho[b] = (double)rmax / (double)fmax[b];
+  iters[b] = it + 1;
+  if (rho[b] <= tol[b] || it + 1 >= maxit[b]) active[b] = 0;
+  else atomicAdd(nactive, 1);
+}
+
+// The first residual's max |f - mean| of each box (the reference norm).
+__global__ void group_fmax_kernel(const ResBox* boxes, int nbox, float* fmax) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbox) return;
+  unsigned int* w = boxes[b].rmax;
+  fmax[b] = __uint_as_float(*w);
+  *w = 0u;
+}
+
+cudaError_t launch_group_refine_stage(int stage, const ResBox* boxes, GroupMap g, int total,
+                                      const GroupIo* io, int flag, cudaStream_t st) {
+  if (total <= 0) return cudaSuccess;
+  switch (stage) {
+    case GSTAGE_PLANE_SUM:
+      plane_sum_group_kernel<<<total, 256, 0, st>>>(boxes, g, io, flag);
+      break;
+    case GSTAGE_MEAN_FINAL:
+      mean_final_group_kernel<<<total, 256, 0, st>>>(boxes, g);
+      break;
+    case GSTAGE_RESIDUAL:
+      poisson_residual_group_kernel<<<total, kResBlock, 0, st>>>(boxes, g, io, flag);
+      break;
+    default:
+      subtract_mean_group_kernel<<<total, 256, 0, st>>>(boxes, g, io);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group_update(const ResBox* boxes, int nbox, const float* fmax,
+                                const double* tol, const int* maxit, int it, int* active,
+                                int* iters, double* rho, int* nactive, cudaStream_t st) {
+  group_update_kernel<<<(nbox + 127) / 128, 128, 0, st>>>(boxes, nbox, fmax, tol, maxit, it,
+                                                          active, iters, rho, nactive);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group_fmax(const ResBox* boxes, int nbox, float* fmax, cudaStream_t st) {
+  group_fmax_kernel<<<(nbox + 127) / 128, 128, 0, st>>>(boxes, nbox, fmax);
+  return cudaGetLastError();
 }
 
 static int cuda_rc(cudaError_t e) { return e == cudaSuccess ? CFS_OK : CFS_ECUDA; }

@@ -19,23 +19,10 @@
 // removal of the dz-weighted mean of its right-hand side and of its solution
 // is folded into the same two sweeps by linearity.
 #include "chanfs_tma.cuh"
+#include "chanfs_group.cuh"
 
 namespace chanfs {
 
-struct ThomasArgs {
-  void* S;               // spectrum (Nz, Ny, M) complex, double2 or float2
-  const double2* fwd;    // FP64 factors (s/piv, A/piv) per (k, kyp, kx in [0, M])
-  const double* bwd;     // FP64 C/piv
-  const float2* fwd32;   // FP32 copies (refined plans only)
-  const float* bwd32;
-  const double* sing;    // Neumann (0,0): wn | gn | hs, 3*nz (see below)
-  double sing_cg;        // g^T 1' / sum(w)
-  double sing_sc;        // the factor scale of the (0,0) column
-  int M, ny, nz, nky;
-  int nblk_x;            // blocks along kx per ky
-  int neumann;
-  int kx64, ky64;        // FP32 spectra: columns kx < kx64, |ky| < ky64 in FP64
-};
 
 constexpr int kThomasBlock = 64;
 constexpr int kPrefetch = 3;
@@ -170,9 +157,9 @@ __device__ __forceinline__ void sweep_column(const ThomasArgs& a, CS* const s0, 
 // Neumann (0,0) one included -- are still solved in FP64 arithmetic with the
 // FP64 factors, the rest in FP32.
 template <class CS>
-__global__ void __launch_bounds__(kThomasBlock, 11) thomas_kernel(ThomasArgs a) {
-  const int ky = blockIdx.x / a.nblk_x;
-  const int j = (blockIdx.x % a.nblk_x) * kThomasBlock + threadIdx.x;
+__device__ __forceinline__ void thomas_body(const ThomasArgs& a, int blk) {
+  const int ky = blk / a.nblk_x;
+  const int j = (blk % a.nblk_x) * kThomasBlock + threadIdx.x;
   if (j >= a.M) return;
   // factor sets of the real (x) and imaginary (y) parts
   int kx_x = j, kx_y = j, kp_x, kp_y;
@@ -197,6 +184,19 @@ __global__ void __launch_bounds__(kThomasBlock, 11) thomas_kernel(ThomasArgs a) 
     sweep_column<CS, double2>(a, s0, a.fwd + ox, a.fwd + oy, a.bwd + ox, a.bwd + oy, sing);
   else
     sweep_column<CS, float2>(a, s0, a.fwd32 + ox, a.fwd32 + oy, a.bwd32 + ox, a.bwd32 + oy, false);
+}
+
+template <class CS>
+__global__ void __launch_bounds__(kThomasBlock, 11) thomas_kernel(ThomasArgs a) {
+  thomas_body<CS>(a, blockIdx.x);
+}
+
+// One launch for several boxes (FP32 inner solves of grouped refinement).
+__global__ void __launch_bounds__(kThomasBlock, 11) thomas_group_kernel(const ThomasArgs* boxes,
+                                                                        GroupMap g) {
+  int b, blk;
+  if (!group_block(g, &b, &blk)) return;
+  thomas_body<float2>(boxes[b], blk);
 }
 
 // ----------------------------------------------------------------------------
@@ -607,6 +607,19 @@ cudaError_t launch_thomas_factor(cfs_plan* P, const double* dA, const double* dB
   thomas_factor_kernel<<<grid, 128, 0, st>>>(P->d_fwd, P->d_bwd, P->d_fwd32, P->d_bwd32, dA, dB,
                                              dC, dlamx, dlamy, P->M, P->nky, P->nz, s,
                                              P->bc == CFS_BC_NEUMANN);
+  return cudaGetLastError();
+}
+
+size_t thomas_group_box(const cfs_plan* P, ThomasArgs* box, int* blocks) {
+  *box = thomas_args(P, P->d_r32);
+  *blocks = box->nblk_x * P->ny;
+  return 0;
+}
+
+cudaError_t launch_thomas_group32(const ThomasArgs* boxes, GroupMap g, int total,
+                                  cudaStream_t st) {
+  if (total <= 0) return cudaSuccess;
+  thomas_group_kernel<<<total, kThomasBlock, 0, st>>>(boxes, g);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,136 @@
+"""GPU: grouped refined Poisson solves (one launch per stage for many boxes).
+
+Every box of a group must give the same bits as the refined solve of its own
+plan, alone, and agree with the FP64 CPU oracle to 1e-10 in the relative
+max-norm; its result must not depend on the other boxes of the group.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2502_06296_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def chanfs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_06296_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2502_06296_gb300 import chanfs as c
+    c.lib()
+    return c
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+# boxes of different sizes, stretchings and walls (sizes from the ensemble's
+# menus, reduced in z so that the oracle stays quick)
+BOXES = [
+    (128, 96, 24, 1.2, 0), (64, 48, 32, 2.2, 1), (32, 24, 16, None, 0), (96, 64, 20, 1.8, 0),
+    (16, 12, 40, 1.5, 1), (48, 36, 12, 1.6, 0),
+]
+
+
+def make_box(chanfs, i, spec):
+    nx, ny, nz, beta, bc = spec
+    dz = synth.uniform_dz(nz) if beta is None else synth.tanh_dz(nz, beta)
+    f = synth.normal(500 + i, (nz, ny, nx))
+    if bc == chanfs.NEUMANN:
+        f = synth.remove_weighted_mean(f, dz)
+    plan = chanfs.Plan(nx, ny, nz, 12.8, 6.4, dz, bc, chanfs.F32_REFINED)
+    return plan, f, dz
+
+
+def test_group_matches_single_solves_and_oracle(chanfs):
+    boxes = [make_box(chanfs, i, s) for i, s in enumerate(BOXES)]
+    plans = [b[0] for b in boxes]
+    fs = [dev(b[1]) for b in boxes]
+    alone = [host(p.poisson_solve(f)) for p, f in zip(plans, fs)]
+    alone_info = [p.last_info() for p in plans]
+    with chanfs.Group(plans) as g:
+        outs = g.poisson_solve(fs)
+        info = g.last_info()
+        got = [host(o) for o in outs]
+        # twice in a row: the group leaves nothing behind
+        again = [host(o) for o in g.poisson_solve(fs)]
+    for i, (plan, f, dz) in enumerate(boxes):
+        nx, ny, nz, beta, bc = BOXES[i]
+        assert np.array_equal(got[i], alone[i]), i
+        assert np.array_equal(again[i], alone[i]), i
+        assert info[i] == alone_info[i], (i, info[i], alone_info[i])
+        assert info[i][1] <= TOL and 1 <= info[i][0] <= 4
+        ref = oracle.poisson_solve(f, 12.8, 6.4, dz, bc)
+        assert rel(got[i], ref) < TOL, (i, rel(got[i], ref))
+        assert plan.check() == 0
+    for p in plans:
+        p.close()
+
+
+def test_box_result_does_not_depend_on_the_group(chanfs):
+    boxes = [make_box(chanfs, i, s) for i, s in enumerate(BOXES)]
+    plans = [b[0] for b in boxes]
+    fs = [dev(b[1]) for b in boxes]
+    with chanfs.Group(plans) as g:
+        full = [host(o) for o in g.poisson_solve(fs)]
+    with chanfs.Group(plans[2:4]) as g:
+        part = [host(o) for o in g.poisson_solve(fs[2:4])]
+    with chanfs.Group(plans[::-1]) as g:
+        rev = [host(o) for o in g.poisson_solve(fs[::-1])][::-1]
+    for i in (2, 3):
+        assert np.array_equal(part[i - 2], full[i])
+    for i in range(len(plans)):
+        assert np.array_equal(rev[i], full[i])
+    for p in plans:
+        p.close()
+
+
+def test_group_zero_rhs_and_nonconvergence(chanfs):
+    a, fa, _ = make_box(chanfs, 0, (32, 24, 16, 1.5, 0))
+    b, fb, _ = make_box(chanfs, 1, (16, 12, 20, 1.8, 1))
+    b.set_refinement(1e-14, 1)  # cannot be met with one FP32 solve
+    with chanfs.Group([a, b]) as g:
+        zero = torch.zeros(16, 24, 32, dtype=torch.float64, device="cuda")
+        with pytest.raises(chanfs.ChanfsError) as err:
+            g.poisson_solve([zero, dev(fb)])
+        assert err.value.status == chanfs.ENOTCONVERGED
+        info = g.last_info()
+    assert info[0] == (0, 0.0)
+    assert info[1][0] == 1 and info[1][1] > 1e-14
+    a.close()
+    b.close()
+
+
+def test_group_rejects_bad_arguments(chanfs):
+    p64 = chanfs.Plan(16, 12, 10, 1.0, 1.0, np.full(10, 0.2))
+    p32 = chanfs.Plan(16, 12, 10, 1.0, 1.0, np.full(10, 0.2), 0, chanfs.F32_REFINED)
+    with pytest.raises(chanfs.ChanfsError) as err:
+        chanfs.Group([p32, p64])
+    assert err.value.status == chanfs.EUNSUPPORTED
+    with pytest.raises(chanfs.ChanfsError) as err:
+        chanfs.Group([p32, p32])
+    assert err.value.status == chanfs.EINVAL
+    with chanfs.Group([p32]) as g:
+        t = torch.zeros(10, 12, 16, dtype=torch.float64, device="cuda")
+        with pytest.raises(chanfs.ChanfsError) as err:
+            g.poisson_solve([t], [t])
+        assert err.value.status == chanfs.EINVAL
+    p64.close()
+    p32.close()
