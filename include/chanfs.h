@@ -249,6 +249,12 @@ int cfs_group_destroy(cfs_group_t group);
 int cfs_group_size(cfs_group_t group, int* nplans);
 int cfs_group_poisson_solve(cfs_group_t group, const double* const* f, double* const* p,
                             void* stream);
+/* The z-implicit Helmholtz solves (I - c[b] L_z) u[b] = rhs[b] of the boxes
+ * (Eq. 11, Algorithm 2 for the FP32 inner solves), grouped in the same way:
+ * c, loc: host arrays of nplans coefficients and field locations (see
+ * cfs_helmholtz_solve); rhs[b] != u[b]. */
+int cfs_group_helmholtz_solve(cfs_group_t group, const double* c, const int* loc,
+                              const double* const* rhs, double* const* u, void* stream);
 int cfs_group_last_info(cfs_group_t group, int* iters, double* rel_residual);
 
 /*

@@ -68,6 +68,8 @@ def lib():
             "cfs_group_size": ([vp, ctypes.POINTER(i)], i),
             "cfs_group_poisson_solve": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp], i),
             "cfs_group_last_info": ([vp, ctypes.POINTER(i), ctypes.POINTER(d)], i),
+            "cfs_group_helmholtz_solve": ([vp, dp, ctypes.POINTER(i), ctypes.POINTER(vp),
+                                           ctypes.POINTER(vp), vp], i),
             "cfs_plan_set_option": ([vp, i, i], i),
             "cfs_plan_get_option": ([vp, i, ctypes.POINTER(i)], i),
         }
@@ -295,6 +297,22 @@ class Group:
         pp = (ctypes.c_void_p * n)(*[p._field(o, "out").value for p, o in zip(self.plans, outs)])
         _check(lib().cfs_group_poisson_solve(self._h, fp, pp, _stream_ptr(stream)),
                "cfs_group_poisson_solve")
+        return outs
+
+    def helmholtz_solve(self, cs, rhss, locs=None, outs=None, stream=None):
+        """(I - c L_z) u = rhs per box: cs, locs per plan; returns the solutions."""
+        import torch
+        n = len(self.plans)
+        if len(cs) != n or len(rhss) != n:
+            raise ValueError("one coefficient and one right-hand side per plan")
+        locs = [CENTER] * n if locs is None else list(locs)
+        outs = [torch.empty_like(r) for r in rhss] if outs is None else list(outs)
+        ca = (ctypes.c_double * n)(*[float(c) for c in cs])
+        la = (ctypes.c_int * n)(*[int(x) for x in locs])
+        fp = (ctypes.c_void_p * n)(*[p._field(r, "rhs").value for p, r in zip(self.plans, rhss)])
+        pp = (ctypes.c_void_p * n)(*[p._field(o, "out").value for p, o in zip(self.plans, outs)])
+        _check(lib().cfs_group_helmholtz_solve(self._h, ca, la, fp, pp, _stream_ptr(stream)),
+               "cfs_group_helmholtz_solve")
         return outs
 
     def last_info(self):

@@ -82,6 +82,27 @@ inline __host__ __device__ long long group_sub_blocks(long long n) {
   return b < 1216 ? b : 1216;
 }
 
+template <class R>
+struct PcrArgs {  // Algorithm 2 runtime (pcr.cu)
+  R* u;                // output field (for the face wall row)
+  long long ncols;     // Nx * Ny
+  int n;               // unknowns per column
+  int nparts;
+  int face;            // face-located field: slot nz-1 is the wall, written 0
+  int nz;
+  int by, nbox;        // rows per TMA box, boxes per tile
+  const R* rows;       // alpha | beta | ib | ap | cp  (5n)
+  const R* red;        // rl | rip | ripc             (3 * 2p)
+};
+
+struct PcrBox {  // one field of a grouped Algorithm 2 launch; maps 64-byte aligned
+  CUtensorMap in_map;
+  CUtensorMap out_map;
+  PcrArgs<float> a;
+  int* status;
+  int blocks;  // blocks of this box (they stride over its tiles)
+};
+
 #ifdef __CUDACC__
 
 // Box and box-local block of this block; false if the box is masked out.
@@ -110,6 +131,11 @@ cudaError_t launch_fft_y_group32(const YBox* boxes, GroupMap g, int total, size_
                                  bool inverse, cudaStream_t st);
 cudaError_t launch_thomas_group32(const ThomasArgs* boxes, GroupMap g, int total,
                                   cudaStream_t st);
+cudaError_t launch_pcr_group32(const PcrBox* boxes, GroupMap g, int total, int threads,
+                               size_t smem, cudaStream_t st);
+size_t pcr_group_box(const cfs_plan* P, const HelmCoef& h, PcrBox* box, int* blocks,
+                     int* threads);
+
 // Grouped refinement kernels (refine.cu), launched by group.cu.
 cudaError_t launch_group_refine_stage(int stage, const ResBox* boxes, GroupMap g, int total,
                                       const GroupIo* io, int flag, cudaStream_t st);
@@ -117,7 +143,13 @@ cudaError_t launch_group_update(const ResBox* boxes, int nbox, const float* fmax
                                 const double* tol, const int* maxit, int it, int* active,
                                 int* iters, double* rho, int* nactive, cudaStream_t st);
 cudaError_t launch_group_fmax(const ResBox* boxes, int nbox, float* fmax, cudaStream_t st);
-enum { GSTAGE_PLANE_SUM = 0, GSTAGE_MEAN_FINAL = 1, GSTAGE_RESIDUAL = 2, GSTAGE_SUBTRACT = 3 };
+enum {
+  GSTAGE_PLANE_SUM = 0,
+  GSTAGE_MEAN_FINAL = 1,
+  GSTAGE_RESIDUAL = 2,
+  GSTAGE_SUBTRACT = 3,
+  GSTAGE_HELM_RESIDUAL = 4  // flag = mode of helm_residual_kernel
+};
 
 // Host-side descriptions of one plan's box for the grouped kernels.
 size_t x_group_box(const cfs_plan* P, bool inverse, XBox* box, int* blocks);

@@ -154,6 +154,9 @@ cudaError_t launch_pcr_raw(long long ncols, int nz, int n, int nparts, int loc, 
                            cudaStream_t st);
 cudaError_t launch_pcr32(const cfs_plan* P, const HelmCoef& h, const float* rhs, float* u,
                          cudaStream_t st);
+// Algorithm 2, Step 1 for (c, loc) on the plan, from its cache or computed
+// and cached (plan.cu); nparts = 0 takes a cached set of any partition count.
+int plan_helm_prepare(cfs_plan* P, double c, int loc, int nparts, HelmCoef** out);
 // Iterative refinement drivers (refine.cu): FP32 inner solves, FP64 residual
 // and accumulation.  They synchronise `st` once per iteration.
 int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st);

@@ -64,7 +64,14 @@ struct cfs_group {
   int* d_nactive = nullptr;
   GroupIo* d_io = nullptr;
   GroupIo* h_io = nullptr;  // pinned staging of the per-call pointers
+  // Helmholtz: per-call Algorithm 2 and residual descriptors (c, loc vary)
+  PcrBox* d_pcr = nullptr;
+  PcrBox* h_pcr = nullptr;
+  ResBox* d_hres = nullptr;
+  ResBox* h_hres = nullptr;
+  int* d_spcr = nullptr;
   cudaEvent_t io_copied = nullptr;
+  std::vector<ResBox> res;  // host copy of d_res
   std::vector<int> last_iters;
   std::vector<double> last_rho;
 };
@@ -73,9 +80,11 @@ static void group_free(cfs_group* G) {
   void* ptrs[] = {G->d_xf,  G->d_xi,   G->d_y,     G->d_th,   G->d_res,   G->d_sx,
                   G->d_sy,  G->d_sth,  G->d_sres,  G->d_splane, G->d_sone, G->d_ssub,
                   G->d_active, G->d_mean, G->d_fmax, G->d_tol, G->d_maxit, G->d_iters,
-                  G->d_rho, G->d_nactive, G->d_io};
+                  G->d_rho, G->d_nactive, G->d_io, G->d_pcr, G->d_hres, G->d_spcr};
   for (void* p : ptrs) cudaFree(p);
   if (G->h_io) cudaFreeHost(G->h_io);
+  if (G->h_pcr) cudaFreeHost(G->h_pcr);
+  if (G->h_hres) cudaFreeHost(G->h_hres);
   if (G->io_copied) cudaEventDestroy(G->io_copied);
   delete G;
 }
@@ -163,11 +172,17 @@ extern "C" int cfs_group_create(cfs_group_t* out, int nplans, const cfs_plan_t* 
   if (e == cudaSuccess) e = cudaMalloc(&G->d_nactive, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&G->d_io, sizeof(GroupIo) * nplans);
   if (e == cudaSuccess) e = cudaMallocHost(&G->h_io, sizeof(GroupIo) * nplans);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_pcr, sizeof(PcrBox) * nplans);
+  if (e == cudaSuccess) e = cudaMallocHost(&G->h_pcr, sizeof(PcrBox) * nplans);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_hres, sizeof(ResBox) * nplans);
+  if (e == cudaSuccess) e = cudaMallocHost(&G->h_hres, sizeof(ResBox) * nplans);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_spcr, sizeof(int) * (nplans + 1));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G->io_copied, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     group_free(G);
     return rc ? rc : (e == cudaErrorMemoryAllocation ? CFS_ENOMEM : CFS_ECUDA);
   }
+  G->res = res;
   G->last_iters.assign(nplans, 0);
   G->last_rho.assign(nplans, 0.0);
   *out = G;
@@ -301,6 +316,116 @@ extern "C" int cfs_group_poisson_solve(cfs_group_t G, const double* const* f, do
   if (e == cudaSuccess) {
     g.start = G->d_ssub;
     e = launch_group_refine_stage(GSTAGE_SUBTRACT, G->d_res, g, G->tsub, G->d_io, 0, st);
+  }
+  std::vector<int> iters(nb);
+  std::vector<double> rho(nb);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(iters.data(), G->d_iters, sizeof(int) * nb, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(rho.data(), G->d_rho, sizeof(double) * nb, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return rc_of(e);
+  int rc = CFS_OK;
+  for (int b = 0; b < nb; ++b) {
+    if (!on[b]) continue;
+    G->last_iters[b] = iters[b];
+    G->last_rho[b] = rho[b];
+    G->plans[b]->last_iters = iters[b];
+    G->plans[b]->last_rho = rho[b];
+    if (!(rho[b] <= G->plans[b]->tol)) rc = CFS_ENOTCONVERGED;
+  }
+  return rc;
+}
+
+extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const int* loc,
+                                         const double* const* rhs, double* const* u,
+                                         void* stream) {
+  if (!G || !c || !loc || !rhs || !u) return CFS_EINVAL;
+  const int nb = G->nbox;
+  for (int b = 0; b < nb; ++b)
+    if (!rhs[b] || !u[b] || static_cast<const void*>(rhs[b]) == static_cast<const void*>(u[b]))
+      return CFS_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaEventSynchronize(G->io_copied);  // staging of the previous call is free
+  if (e != cudaSuccess) return CFS_ECUDA;
+  // Algorithm 2, Step 1 of every box (host, cached per plan), and the
+  // per-call descriptors
+  std::vector<int> blocks(nb), on(nb);
+  std::vector<double> tol(nb);
+  std::vector<int> maxits(nb);
+  int threads = 0;
+  size_t smem = 0;
+  for (int b = 0; b < nb; ++b) {
+    cfs_plan* P = G->plans[b];
+    HelmCoef* h = nullptr;
+    int rc = plan_helm_prepare(P, c[b], loc[b], 0, &h);
+    if (rc) return rc;
+    int th = 0;
+    const size_t sm = pcr_group_box(P, *h, &G->h_pcr[b], &blocks[b], &th);
+    if (!sm) return CFS_ECUDA;
+    threads = std::max(threads, th);
+    smem = std::max(smem, sm);
+    G->h_hres[b] = G->res[b];
+    G->h_hres[b].abc = h->d_abc;
+    G->h_hres[b].n = h->n;
+    G->h_io[b] = GroupIo{rhs[b], u[b]};
+    tol[b] = P->tol;
+    maxits[b] = P->maxit;
+  }
+  int tpcr = 0;
+  std::vector<int> spcr = offsets(blocks, &tpcr);
+  e = cudaMemcpyAsync(G->d_pcr, G->h_pcr, sizeof(PcrBox) * nb, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(G->d_hres, G->h_hres, sizeof(ResBox) * nb, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(G->d_io, G->h_io, sizeof(GroupIo) * nb, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaEventRecord(G->io_copied, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(G->d_spcr, spcr.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice,
+                        st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(G->d_tol, tol.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(G->d_maxit, maxits.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st);
+  // r_0 = rhs and its max-norm
+  GroupMap g{G->d_sres, nullptr, nb};
+  if (e == cudaSuccess)
+    e = launch_group_refine_stage(GSTAGE_HELM_RESIDUAL, G->d_hres, g, G->tres, G->d_io, 0, st);
+  if (e == cudaSuccess) e = launch_group_fmax(G->d_hres, nb, G->d_fmax, st);
+  std::vector<float> fmax(nb);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(fmax.data(), G->d_fmax, sizeof(float) * nb, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return CFS_ECUDA;
+  int nactive = 0, maxit = 0;
+  for (int b = 0; b < nb; ++b) {
+    cfs_plan* P = G->plans[b];
+    on[b] = fmax[b] != 0.0f;
+    nactive += on[b];
+    maxit = std::max(maxit, P->maxit);
+    G->last_iters[b] = 0;
+    G->last_rho[b] = 0.0;
+    if (!on[b])  // zero right-hand side: zero solution
+      e = cudaMemsetAsync(u[b], 0, sizeof(double) * (size_t)P->nx * P->ny * P->nz, st);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(G->d_active, on.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st);
+  g.active = G->d_active;
+  for (int it = 0; it < maxit && nactive > 0 && e == cudaSuccess; ++it) {
+    g.start = G->d_spcr;
+    e = launch_pcr_group32(G->d_pcr, g, tpcr, threads, smem, st);
+    if (e == cudaSuccess) {
+      g.start = G->d_sres;
+      e = launch_group_refine_stage(GSTAGE_HELM_RESIDUAL, G->d_hres, g, G->tres, G->d_io,
+                                    it == 0 ? 1 : 2, st);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(G->d_nactive, 0, sizeof(int), st);
+    if (e == cudaSuccess)
+      e = launch_group_update(G->d_hres, nb, G->d_fmax, G->d_tol, G->d_maxit, it, G->d_active,
+                              G->d_iters, G->d_rho, G->d_nactive, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&nactive, G->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   }
   std::vector<int> iters(nb);
   std::vector<double> rho(nb);

@@ -20,28 +20,20 @@
 // persistent over tiles; several CTAs per SM overlap one CTA's serial phases
 // (copies, the reduced solve) with another's arithmetic.
 #include "chanfs_tma.cuh"
+#include "chanfs_group.cuh"
 
 namespace chanfs {
 
 constexpr int kPcrCols = 16;  // columns per tile (one half-warp)
 
-template <class R>
-struct PcrArgs {
-  R* u;                // output field (for the face wall row)
-  long long ncols;     // Nx * Ny
-  int n;               // unknowns per column
-  int nparts;
-  int face;            // face-located field: slot nz-1 is the wall, written 0
-  int nz;
-  int by, nbox;        // rows per TMA box, boxes per tile
-  const R* rows;       // alpha | beta | ib | ap | cp  (5n)
-  const R* red;        // rl | rip | ripc             (3 * 2p)
-};
 
+// Tiles tile0, tile0 + tstride, ... of one field.  Threads beyond the
+// field's 16 * nparts (a grouped launch sized for its widest box) only take
+// part in the barriers.
 template <class R>
-__global__ void __launch_bounds__(1024) pcr_kernel(const __grid_constant__ CUtensorMap in_map,
-                                                   const __grid_constant__ CUtensorMap out_map,
-                                                   PcrArgs<R> a, int* status) {
+__device__ __forceinline__ void pcr_body(const CUtensorMap* in_map, const CUtensorMap* out_map,
+                                         const PcrArgs<R>& a, int* status, long long tile0,
+                                         long long tstride) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int n = a.n, J = 2 * a.nparts;
   const int rows_alloc = a.nbox * a.by;
@@ -69,6 +61,7 @@ __global__ void __launch_bounds__(1024) pcr_kernel(const __grid_constant__ CUten
 
   const int c = threadIdx.x % kPcrCols;  // column within the tile
   const int q = threadIdx.x / kPcrCols;  // partition
+  const bool part = q < a.nparts;
   // partition q covers rows [q n / p, (q+1) n / p) (the rule the host used)
   const int s = (int)(((long long)q * n) / a.nparts);
   const int m = (int)(((long long)(q + 1) * n) / a.nparts) - s;
@@ -76,12 +69,12 @@ __global__ void __launch_bounds__(1024) pcr_kernel(const __grid_constant__ CUten
   const uint32_t tile_bytes = (uint32_t)(a.nbox * a.by * kPcrCols * sizeof(R));
   uint32_t phase = 0;
 
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (long long tile = tile0; tile < ntiles; tile += tstride) {
     const int col0 = (int)(tile * kPcrCols);
     if (threadIdx.x == 0) {
       mbar_expect_tx(bar, tile_bytes);
       for (int b = 0; b < a.nbox; ++b)
-        tma_load_2d(T + b * a.by * kPcrCols, &in_map, bar, col0, b * a.by);
+        tma_load_2d(T + b * a.by * kPcrCols, in_map, bar, col0, b * a.by);
     }
     const int ok = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0);
     phase ^= 1u;
@@ -91,7 +84,7 @@ __global__ void __launch_bounds__(1024) pcr_kernel(const __grid_constant__ CUten
     }
     R* col = T + c;  // element (row r) at col[r * 16]
     // Step 2: forward then backward reduction of d only
-    {
+    if (part) {
       R prev = col[(s + 1) * kPcrCols];
       for (int i = 2; i < m; ++i) {
         const int r = s + i;
@@ -124,7 +117,7 @@ __global__ void __launch_bounds__(1024) pcr_kernel(const __grid_constant__ CUten
     }
     __syncthreads();
     // Step 4: reconstruction in place
-    {
+    if (part) {
       const R x0 = s_x[(2 * q) * kPcrCols + c];
       const R xm = s_x[(2 * q + 1) * kPcrCols + c];
       col[s * kPcrCols] = x0;
@@ -138,13 +131,29 @@ __global__ void __launch_bounds__(1024) pcr_kernel(const __grid_constant__ CUten
     __syncthreads();
     if (threadIdx.x == 0) {
       for (int b = 0; b < a.nbox; ++b)
-        tma_store_2d(&out_map, T + b * a.by * kPcrCols, col0, b * a.by);
+        tma_store_2d(out_map, T + b * a.by * kPcrCols, col0, b * a.by);
       tma_store_commit_and_wait_read();  // the tile may be reused
     }
     if (a.face && threadIdx.x < kPcrCols && col0 + c < a.ncols)
       a.u[(long long)(a.nz - 1) * a.ncols + col0 + c] = R(0);
     __syncthreads();
   }
+}
+
+template <class R>
+__global__ void __launch_bounds__(1024) pcr_kernel(const __grid_constant__ CUtensorMap in_map,
+                                                   const __grid_constant__ CUtensorMap out_map,
+                                                   PcrArgs<R> a, int* status) {
+  pcr_body<R>(&in_map, &out_map, a, status, blockIdx.x, gridDim.x);
+}
+
+// One launch for several boxes (FP32 inner solves of grouped refinement): the
+// blocks of box b stride over its tiles.
+__global__ void __launch_bounds__(1024) pcr_group_kernel(const PcrBox* boxes, GroupMap g) {
+  int b, blk;
+  if (!group_block(g, &b, &blk)) return;
+  const PcrBox& x = boxes[b];
+  pcr_body<float>(&x.in_map, &x.out_map, x.a, x.status, blk, x.blocks);
 }
 
 // 2-D map over the first n rows of a field: ncols reals per row.
@@ -215,6 +224,41 @@ cudaError_t launch_pcr32(const cfs_plan* P, const HelmCoef& h, const float* rhs,
                          cudaStream_t st) {
   if (!h.d_rows32) return cudaErrorInvalidValue;
   return launch_pcr_t<float>(P, h, h.d_rows32, h.d_red32, rhs, u, st);
+}
+
+// Tiles per block of a grouped launch: enough to amortise the staging of the
+// coefficients, few enough to spread a small box over many SMs.
+constexpr int kPcrGroupTiles = 8;
+
+size_t pcr_group_box(const cfs_plan* P, const HelmCoef& h, PcrBox* box, int* blocks,
+                     int* threads) {
+  PcrArgs<float>& a = box->a;
+  a.u = P->d_r32;
+  a.ncols = (long long)P->nx * P->ny;
+  a.n = h.n;
+  a.nparts = h.nparts;
+  a.face = (h.loc == CFS_LOC_FACE);
+  a.nz = P->nz;
+  pcr_boxes(h.n, sizeof(float), &a.nbox, &a.by);
+  a.rows = h.d_rows32;
+  a.red = h.d_red32;
+  if (!pcr_map<float>(&box->in_map, P->d_r32, a.ncols, h.n, a.by) ||
+      !pcr_map<float>(&box->out_map, P->d_r32, a.ncols, h.n, a.by))
+    return 0;
+  const long long ntiles = (a.ncols + kPcrCols - 1) / kPcrCols;
+  box->blocks = (int)((ntiles + kPcrGroupTiles - 1) / kPcrGroupTiles);
+  box->status = P->d_status;
+  *blocks = box->blocks;
+  *threads = kPcrCols * h.nparts;
+  return pcr_smem_t<float>(h.n, h.nparts);
+}
+
+cudaError_t launch_pcr_group32(const PcrBox* boxes, GroupMap g, int total, int threads,
+                               size_t smem, cudaStream_t st) {
+  if (total <= 0) return cudaSuccess;
+  cudaFuncSetAttribute(pcr_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  pcr_group_kernel<<<total, threads, smem, st>>>(boxes, g);
+  return cudaGetLastError();
 }
 
 }  // namespace chanfs

@@ -596,6 +596,10 @@ static int helm_prepare(cfs_plan* P, double c, int loc, int nparts, HelmCoef** r
   return CFS_OK;
 }
 
+int chanfs::plan_helm_prepare(cfs_plan* P, double c, int loc, int nparts, HelmCoef** out) {
+  return helm_prepare(P, c, loc, nparts, out);
+}
+
 extern "C" int cfs_helmholtz_prepare(cfs_plan_t P, double c, int loc, int nparts) {
   if (!P) return CFS_EINVAL;
   HelmCoef* h = nullptr;

@@ -139,10 +139,12 @@ __global__ void __launch_bounds__(kResBlock) poisson_residual_kernel(
 // marching up in z one row behind the update so that u_{k+1} is final when
 // row k is evaluated.  abc = [A' | B' | C'] of I - c L_z (n rows); the wall
 // row of a face field (n < nz) keeps r = 0.  FP64: 5 instructions per point.
-__global__ void __launch_bounds__(kResBlock) helm_residual_kernel(
-    const double* __restrict__ rhs, double* __restrict__ u, float* __restrict__ r32,
-    const double* __restrict__ abc, unsigned int* rmax, long long ncols, int n, int nz, int mode) {
-  const long long col = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void helm_residual_body(const double* __restrict__ rhs,
+                                                   double* __restrict__ u, float* __restrict__ r32,
+                                                   const double* __restrict__ abc,
+                                                   unsigned int* rmax, long long ncols, int n,
+                                                   int nz, int mode, long long blk) {
+  const long long col = blk * blockDim.x + threadIdx.x;
   float vmax = 0.0f;
   if (col < ncols) {
     auto update = [&](int k) -> double {
@@ -173,6 +175,12 @@ __global__ void __launch_bounds__(kResBlock) helm_residual_kernel(
     }
   }
   block_max_to(vmax, rmax);
+}
+
+__global__ void __launch_bounds__(kResBlock) helm_residual_kernel(
+    const double* __restrict__ rhs, double* __restrict__ u, float* __restrict__ r32,
+    const double* __restrict__ abc, unsigned int* rmax, long long ncols, int n, int nz, int mode) {
+  helm_residual_body(rhs, u, r32, abc, rmax, ncols, n, nz, mode, blockIdx.x);
 }
 
 // p -= mean (the dz-weighted mean computed by the two kernels above).
@@ -218,6 +226,17 @@ __global__ void __launch_bounds__(kResBlock) poisson_residual_group_kernel(const
   const ResBox& r = boxes[b];
   poisson_residual_body(io[b].f, with_p ? io[b].p : nullptr, r.zop, r.neumann ? r.mean : nullptr,
                         r.r32, r.rmax, r.nx, r.ny, r.nz, r.idx2, r.idy2, blk);
+}
+
+__global__ void __launch_bounds__(kResBlock) helm_residual_group_kernel(const ResBox* boxes,
+                                                                        GroupMap g,
+                                                                        const GroupIo* io,
+                                                                        int mode) {
+  int b, blk;
+  if (!group_block(g, &b, &blk)) return;
+  const ResBox& r = boxes[b];
+  helm_residual_body(io[b].f, io[b].p, r.r32, r.abc, r.rmax, (long long)r.nx * r.ny, r.n, r.nz,
+                     mode, blk);
 }
 
 __global__ void subtract_mean_group_kernel(const ResBox* boxes, GroupMap g, const GroupIo* io) {
@@ -266,6 +285,9 @@ cudaError_t launch_group_refine_stage(int stage, const ResBox* boxes, GroupMap g
       break;
     case GSTAGE_RESIDUAL:
       poisson_residual_group_kernel<<<total, kResBlock, 0, st>>>(boxes, g, io, flag);
+      break;
+    case GSTAGE_HELM_RESIDUAL:
+      helm_residual_group_kernel<<<total, kResBlock, 0, st>>>(boxes, g, io, flag);
       break;
     default:
       subtract_mean_group_kernel<<<total, 256, 0, st>>>(boxes, g, io);

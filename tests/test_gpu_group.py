@@ -134,3 +134,29 @@ def test_group_rejects_bad_arguments(chanfs):
         assert err.value.status == chanfs.EINVAL
     p64.close()
     p32.close()
+
+
+def test_group_helmholtz_matches_single_solves_and_oracle(chanfs):
+    boxes = [make_box(chanfs, i, s) for i, s in enumerate(BOXES)]
+    plans = [b[0] for b in boxes]
+    cs = [1e-6, 3e-5, 1e-4, 9.6e-9, 2e-5, 1e-2]
+    locs = [chanfs.CENTER, chanfs.FACE, chanfs.CENTER, chanfs.FACE, chanfs.CENTER, chanfs.FACE]
+    rhs = [synth.normal(700 + i, b[1].shape) for i, b in enumerate(boxes)]
+    rd = [dev(r) for r in rhs]
+    alone = [host(p.helmholtz_solve(c, r, loc)) for p, c, r, loc in zip(plans, cs, rd, locs)]
+    alone_info = [p.last_info() for p in plans]
+    with chanfs.Group(plans) as g:
+        got = [host(o) for o in g.helmholtz_solve(cs, rd, locs)]
+        info = g.last_info()
+        # a Poisson solve in between does not disturb the next Helmholtz solve
+        g.poisson_solve([dev(b[1]) for b in boxes])
+        again = [host(o) for o in g.helmholtz_solve(cs, rd, locs)]
+    for i, (plan, f, dz) in enumerate(boxes):
+        assert np.array_equal(got[i], alone[i]), i
+        assert np.array_equal(again[i], alone[i]), i
+        assert info[i] == alone_info[i], (i, info[i], alone_info[i])
+        ref = oracle.helmholtz_solve(rhs[i], dz, cs[i], locs[i])
+        assert rel(got[i], ref) < TOL, (i, rel(got[i], ref))
+        assert plan.check() == 0
+    for p in plans:
+        p.close()
