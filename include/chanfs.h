@@ -265,15 +265,32 @@ int cfs_group_last_info(cfs_group_t group, int* iters, double* rel_residual);
  *       Eq. 12: 0 automatic (the default), 8 or 16, or -1 for the streaming
  *       kernel (one thread per column, rows through registers, the forward
  *       sweep's intermediate written to the spectrum and read back).
+ *   CFS_OPT_X_LINES  x-lines per CTA of the x transforms: 0 automatic (about
+ *       16 KB of data per buffer) or 1..64.
+ *   CFS_OPT_Y_TILE  complex columns per y-transform tile (of the precision the
+ *       solves transform in): 0 automatic or 1..32 (even for refined plans).
+ *   CFS_OPT_PCR_PARTS  z-partitions of Algorithm 2 for Helmholtz sets that
+ *       are prepared without an explicit count: 0 automatic (about 32 rows
+ *       per partition) or 1..64, each partition at least 3 rows.
  * cfs_plan_set_option returns CFS_EINVAL for an unknown option or value, and
  * CFS_EUNSUPPORTED if the value cannot run at this plan's size (a tile that
  * does not fit in shared memory).  cfs_plan_get_option reports the value in
  * effect, with automatic choices resolved (for CFS_F32_REFINED plans, the
  * choice of the FP32 inner solve).
  */
-enum { CFS_OPT_THOMAS_TILE = 1 };
+enum { CFS_OPT_THOMAS_TILE = 1, CFS_OPT_X_LINES = 2, CFS_OPT_Y_TILE = 3, CFS_OPT_PCR_PARTS = 4 };
 int cfs_plan_set_option(cfs_plan_t plan, int option, int value);
 int cfs_plan_get_option(cfs_plan_t plan, int option, int* value);
+
+/*
+ * cfs_plan_autotune -- choose the options above for this plan by timing the
+ * candidates of each on the GPU (CUDA events on `stream`, the plan's own work
+ * fields as scratch) and set the fastest.  Results are kept per process for
+ * the plan's (nx, ny, nz, dtype), so later plans of that size take them
+ * without timing.  The paper has no counterpart.  Solves on the plan must not
+ * run meanwhile; the plan's cached Helmholtz sets are kept.
+ */
+int cfs_plan_autotune(cfs_plan_t plan, void* stream);
 
 /*
  * cfs_plan_check -- wait for the device and report device-side failures

@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "libchanfs.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
          "-Xcompiler", "-Wall"]
-SOURCES = ["plan.cu", "fft_x.cu", "fft_y.cu", "thomas.cu", "pcr.cu", "refine.cu", "group.cu", "noalloc.cu"]
+SOURCES = ["plan.cu", "fft_x.cu", "fft_y.cu", "thomas.cu", "pcr.cu", "refine.cu", "group.cu", "tune.cu", "noalloc.cu"]
 
 
 def _nvcc() -> str:

@@ -23,7 +23,7 @@ F64, F32_REFINED = 0, 1
 
 X_FORWARD, Y_FORWARD, Z_SOLVE, Y_INVERSE, X_INVERSE = 0, 1, 2, 3, 4
 
-OPT_THOMAS_TILE = 1
+OPT_THOMAS_TILE, OPT_X_LINES, OPT_Y_TILE, OPT_PCR_PARTS = 1, 2, 3, 4
 
 OK, EINVAL, ENOMEM, EUNSUPPORTED, ECUDA, ETIMEOUT, ENOTCONVERGED = 0, -1, -2, -3, -4, -5, -6
 
@@ -71,6 +71,7 @@ def lib():
             "cfs_group_helmholtz_solve": ([vp, dp, ctypes.POINTER(i), ctypes.POINTER(vp),
                                            ctypes.POINTER(vp), vp], i),
             "cfs_plan_set_option": ([vp, i, i], i),
+            "cfs_plan_autotune": ([vp, vp], i),
             "cfs_plan_get_option": ([vp, i, ctypes.POINTER(i)], i),
         }
         for name, (args, res) in sig.items():
@@ -216,6 +217,14 @@ class Plan:
     def set_option(self, option: int, value: int):
         """Choose a kernel shape (see cfs_plan_set_option)."""
         _check(lib().cfs_plan_set_option(self._h, int(option), int(value)), "cfs_plan_set_option")
+
+    def autotune(self, stream=None):
+        """Time the kernel-shape candidates on the GPU and keep the fastest
+        (cfs_plan_autotune); returns the options now in effect."""
+        _check(lib().cfs_plan_autotune(self._h, _stream_ptr(stream)), "cfs_plan_autotune")
+        return {name: self.get_option(opt) for name, opt in
+                (("x_lines", OPT_X_LINES), ("y_tile", OPT_Y_TILE),
+                 ("thomas_tile", OPT_THOMAS_TILE), ("pcr_parts", OPT_PCR_PARTS))}
 
     def get_option(self, option: int) -> int:
         """The kernel shape in effect, automatic choices resolved."""

@@ -94,6 +94,9 @@ struct cfs_plan {
   double* d_bwd;     // C_k/piv_k
   int thomas_tw;     // columns per shared-memory Thomas tile: 0 automatic,
                      // 8 or 16 forced, -1 the streaming kernel
+  int x_lines;       // x-lines per CTA of the x transforms (0: about 16 KB of data)
+  int tk_auto, tk32_auto;  // y tile widths chosen at creation
+  int pcr_parts;     // partitions of Helmholtz sets prepared without a count (0: auto)
   double* d_dzf;     // cell widths (weights of the Neumann mean)
   // Neumann (0,0) column: wn = w/sum(w), gn = g/sum(w) with g = T'^{-T} w,
   // hs = sc * T'^{-1} (0,1,..,1), T' the pinned operator; 3*nz doubles
@@ -140,6 +143,11 @@ cudaError_t launch_rfft_x32_to64(const cfs_plan* P, const float* in, double* out
                                  cudaStream_t st);
 cudaError_t launch_fft_y32(const cfs_plan* P, float* data, bool inverse, cudaStream_t st);
 cudaError_t launch_thomas32(const cfs_plan* P, float* data, cudaStream_t st);
+// x-lines per CTA of the x transforms of complex element size csize.
+int x_lines_per_cta(const cfs_plan* P, size_t csize);
+size_t x_smem_bytes(const cfs_plan* P, int lines, size_t csize);
+// Whether tk columns per y tile can run (alignment, shared memory).
+bool y_tile_ok(const cfs_plan* P, int tk, bool fp32);
 // Thomas tile width the plan's solves use (8, 16, or -1 for the streaming
 // kernel), for the FP64 or the FP32 spectrum; 0 if `tw` cannot run.
 int thomas_tile_width(const cfs_plan* P, bool fp32, int tw);
@@ -157,6 +165,9 @@ cudaError_t launch_pcr32(const cfs_plan* P, const HelmCoef& h, const float* rhs,
 // Algorithm 2, Step 1 for (c, loc) on the plan, from its cache or computed
 // and cached (plan.cu); nparts = 0 takes a cached set of any partition count.
 int plan_helm_prepare(cfs_plan* P, double c, int loc, int nparts, HelmCoef** out);
+void plan_helm_forget(cfs_plan* P, double c);
+// Allocates the plan's FP64 staging field if it has none yet.
+int plan_ensure_stage(cfs_plan* P);
 // Iterative refinement drivers (refine.cu): FP32 inner solves, FP64 residual
 // and accumulation.  They synchronise `st` once per iteration.
 int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st);

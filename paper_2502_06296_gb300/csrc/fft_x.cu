@@ -154,19 +154,24 @@ __global__ void __launch_bounds__(128) rfft_x_group_kernel(const XBox* boxes, Gr
                                 static_cast<const float2*>(x.post), x.lb, 1.0, 0, blk);
 }
 
-static int x_lines_per_cta(int M, size_t csize) {
+int x_lines_per_cta(const cfs_plan* P, size_t csize) {
+  if (P->x_lines > 0) return P->x_lines;
   // about 16 KB of complex data per buffer
   const int target = (int)(16384 / csize);
-  return M >= target ? 1 : target / M;
+  return P->M >= target ? 1 : target / P->M;
+}
+
+size_t x_smem_bytes(const cfs_plan* P, int lines, size_t csize) {
+  return csize * (size_t)(2 * lines * P->M + P->fx.ntw + P->M / 2 + 1);
 }
 
 template <class C, int OUT>
 static cudaError_t launch_x(const cfs_plan* P, const void* in, void* out, bool inverse,
                             double scale, const C* tw, const C* post, cudaStream_t st) {
   const long long nlines = (long long)P->ny * P->nz;
-  const int lb = x_lines_per_cta(P->M, sizeof(C));
+  const int lb = x_lines_per_cta(P, sizeof(C));
   const long long grid = (nlines + lb - 1) / lb;
-  const size_t smem = sizeof(C) * (size_t)(2 * lb * P->M + P->fx.ntw + P->M / 2 + 1);
+  const size_t smem = x_smem_bytes(P, lb, sizeof(C));
   const int scaled = (scale != 1.0);
   const C* cin = reinterpret_cast<const C*>(in);
   if (!inverse) {
@@ -198,7 +203,7 @@ cudaError_t launch_rfft_x32_to64(const cfs_plan* P, const float* in, double* out
 }
 
 size_t x_group_box(const cfs_plan* P, bool inverse, XBox* box, int* blocks) {
-  const int lb = x_lines_per_cta(P->M, sizeof(float2));
+  const int lb = x_lines_per_cta(P, sizeof(float2));
   box->d = P->fx;
   box->in = P->d_r32;
   box->out = inverse ? nullptr : P->d_r32;
@@ -207,7 +212,7 @@ size_t x_group_box(const cfs_plan* P, bool inverse, XBox* box, int* blocks) {
   box->nlines = (long long)P->ny * P->nz;
   box->lb = lb;
   *blocks = (int)((box->nlines + lb - 1) / lb);
-  return sizeof(float2) * (size_t)(2 * lb * P->M + P->fx.ntw + P->M / 2 + 1);
+  return x_smem_bytes(P, lb, sizeof(float2));
 }
 
 cudaError_t launch_rfft_x_group32(const XBox* boxes, GroupMap g, int total, size_t smem,

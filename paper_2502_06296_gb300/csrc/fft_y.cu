@@ -121,6 +121,13 @@ static cudaError_t launch_y(const cfs_plan* P, void* data, bool inverse, int tk,
   return cudaGetLastError();
 }
 
+bool y_tile_ok(const cfs_plan* P, int tk, bool fp32) {
+  const size_t csize = fp32 ? sizeof(float2) : sizeof(double2);
+  if (tk < 1 || tk > 32 || (fp32 && tk % 2)) return false;  // 16-byte TMA box rows
+  if (P->nbox > 1 && ((size_t)P->by * tk * csize) % 128 != 0) return false;
+  return 128 + csize * (size_t)(2 * tk * P->ny + P->fy.ntw) <= 227 * 1024;
+}
+
 cudaError_t launch_fft_y(const cfs_plan* P, double* data, bool inverse, cudaStream_t st) {
   return launch_y<double2>(P, data, inverse, P->tk, P->d_twy, st);
 }

@@ -240,6 +240,8 @@ extern "C" int cfs_plan_create(cfs_plan_t* out, int nx, int ny, int nz, double l
     plan_free(P);
     return CFS_EUNSUPPORTED;
   }
+  P->tk_auto = P->tk;
+  P->tk32_auto = P->tk32;
 
   std::vector<double2> twx, twy;
   if (!make_fft_desc(P->M, &P->fx, &twx) || !make_fft_desc(ny, &P->fy, &twy)) {
@@ -461,6 +463,20 @@ static int auto_parts(int n) {
   return p;
 }
 
+// Frees one cached set (the device must be idle on it).
+static void helm_release(cfs_plan* P, HelmCoef& h) {
+  const size_t n = (size_t)h.n, p = (size_t)h.nparts;
+  cudaFree(h.d_rows);
+  cudaFree(h.d_red);
+  P->device_bytes -= sizeof(double) * (5 * n + 6 * p);
+  if (h.d_rows32) {
+    cudaFree(h.d_rows32);
+    cudaFree(h.d_red32);
+    cudaFree(h.d_abc);
+    P->device_bytes -= sizeof(float) * (5 * n + 6 * p) + sizeof(double) * 3 * n;
+  }
+}
+
 static int helm_prepare(cfs_plan* P, double c, int loc, int nparts, HelmCoef** res) {
   if (!(c >= 0) || !isfinite(c)) return CFS_EINVAL;
   if (loc != CFS_LOC_CENTER && loc != CFS_LOC_FACE) return CFS_EINVAL;
@@ -478,7 +494,7 @@ static int helm_prepare(cfs_plan* P, double c, int loc, int nparts, HelmCoef** r
     C[i] = -c * C[i];
   }
   if (n < 3 || n > kPcrMaxUnknowns) return CFS_EUNSUPPORTED;
-  const int np = nparts ? nparts : auto_parts(n);
+  const int np = nparts ? nparts : (P->pcr_parts ? P->pcr_parts : auto_parts(n));
   if (pcr_smem_bytes(n, np) > 227 * 1024) return CFS_EUNSUPPORTED;
   HelmCoef h;
   memset(&h, 0, sizeof(h));
@@ -582,12 +598,7 @@ static int helm_prepare(cfs_plan* P, double c, int loc, int nparts, HelmCoef** r
     auto it = std::min_element(P->helm.begin(), P->helm.end(),
                                [](const HelmCoef& x, const HelmCoef& y) { return x.stamp < y.stamp; });
     cudaDeviceSynchronize();
-    cudaFree(it->d_rows);
-    cudaFree(it->d_red);
-    cudaFree(it->d_rows32);
-    cudaFree(it->d_red32);
-    cudaFree(it->d_abc);
-    P->device_bytes -= sizeof(double) * (5 * (size_t)it->n + 6 * (size_t)it->nparts);
+    helm_release(P, *it);
     P->helm.erase(it);
   }
   h.stamp = ++P->helm_clock;
@@ -597,7 +608,20 @@ static int helm_prepare(cfs_plan* P, double c, int loc, int nparts, HelmCoef** r
 }
 
 int chanfs::plan_helm_prepare(cfs_plan* P, double c, int loc, int nparts, HelmCoef** out) {
-  return helm_prepare(P, c, loc, nparts, out);
+  return helm_prepare(P, c, loc, nparts ? nparts : P->pcr_parts, out);
+}
+
+// Drops the cached Algorithm 2 sets of coefficient c (the tuner's probes).
+void chanfs::plan_helm_forget(cfs_plan* P, double c) {
+  cudaDeviceSynchronize();
+  for (size_t i = 0; i < P->helm.size();) {
+    if (P->helm[i].c == c) {
+      helm_release(P, P->helm[i]);
+      P->helm.erase(P->helm.begin() + i);
+    } else {
+      ++i;
+    }
+  }
 }
 
 extern "C" int cfs_helmholtz_prepare(cfs_plan_t P, double c, int loc, int nparts) {
@@ -610,7 +634,7 @@ extern "C" int cfs_helmholtz_solve(cfs_plan_t P, double c, int loc, const double
                                    void* stream) {
   if (!P || !rhs || !u || !aligned16(rhs) || !aligned16(u)) return CFS_EINVAL;
   HelmCoef* h = nullptr;
-  int rc = helm_prepare(P, c, loc, 0, &h);
+  int rc = helm_prepare(P, c, loc, P->pcr_parts, &h);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   if (P->dtype == CFS_F32_REFINED) {
@@ -646,6 +670,28 @@ extern "C" int cfs_plan_set_option(cfs_plan_t P, int option, int value) {
       P->thomas_tw = value;
       return CFS_OK;
     }
+    case CFS_OPT_X_LINES: {
+      if (value < 0 || value > 64) return CFS_EINVAL;
+      const size_t cs = (P->dtype == CFS_F32_REFINED) ? sizeof(float2) : sizeof(double2);
+      if (value > 0 && x_smem_bytes(P, value, cs) > 227 * 1024) return CFS_EUNSUPPORTED;
+      P->x_lines = value;
+      return CFS_OK;
+    }
+    case CFS_OPT_Y_TILE: {
+      const bool fp32 = (P->dtype == CFS_F32_REFINED);
+      if (value < 0 || value > 32) return CFS_EINVAL;
+      if (value > 0 && !y_tile_ok(P, value, fp32)) return CFS_EUNSUPPORTED;
+      if (fp32) P->tk32 = value ? value : P->tk32_auto;
+      else P->tk = value ? value : P->tk_auto;
+      return CFS_OK;
+    }
+    case CFS_OPT_PCR_PARTS: {
+      if (value < 0 || value > kPcrMaxParts) return CFS_EINVAL;
+      for (int n = P->nz - 1; value > 0 && n <= P->nz; ++n)  // face and centred fields
+        if (n / value < 3 || pcr_smem_bytes(n, value) > 227 * 1024) return CFS_EUNSUPPORTED;
+      P->pcr_parts = value;
+      return CFS_OK;
+    }
     default:
       return CFS_EINVAL;
   }
@@ -656,6 +702,15 @@ extern "C" int cfs_plan_get_option(cfs_plan_t P, int option, int* value) {
   switch (option) {
     case CFS_OPT_THOMAS_TILE:
       *value = thomas_tile_width(P, P->dtype == CFS_F32_REFINED, P->thomas_tw);
+      return CFS_OK;
+    case CFS_OPT_X_LINES:
+      *value = x_lines_per_cta(P, P->dtype == CFS_F32_REFINED ? sizeof(float2) : sizeof(double2));
+      return CFS_OK;
+    case CFS_OPT_Y_TILE:
+      *value = (P->dtype == CFS_F32_REFINED) ? P->tk32 : P->tk;
+      return CFS_OK;
+    case CFS_OPT_PCR_PARTS:
+      *value = P->pcr_parts ? P->pcr_parts : auto_parts(P->nz);
       return CFS_OK;
     default:
       return CFS_EINVAL;
@@ -672,6 +727,8 @@ extern "C" int cfs_last_info(cfs_plan_t P, int* iters, double* rel_residual) {
 // ----------------------------------------------------------------------------
 // Host-buffer variants
 // ----------------------------------------------------------------------------
+int chanfs::plan_ensure_stage(cfs_plan* P) { return ensure_stage(P); }
+
 static int ensure_stage(cfs_plan* P) {
   if (P->d_stage) return CFS_OK;
   const size_t bytes = sizeof(double) * (size_t)P->nx * P->ny * P->nz;

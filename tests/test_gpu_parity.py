@@ -337,3 +337,41 @@ def test_channel_workload_full_size(chanfs):
     for r, loc, u in zip(rhs, (0, 0, 1), us):
         uref = oracle.helmholtz_solve(r, dz, c, loc)
         assert rel(u, uref) < TOL
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_options_and_autotune_keep_results(chanfs, dtype):
+    """Every kernel shape the options allow computes the same solution."""
+    nx, ny, nz = 64, 48, 40
+    dz = make_dz(nz, 1.7)
+    f = synth.remove_weighted_mean(synth.normal(77, (nz, ny, nx)), dz)
+    rhs = synth.normal(78, (nz, ny, nx))
+    c = 2e-5
+    ref = oracle.poisson_solve(f, 2.0, 1.0, dz, 0)
+    href = oracle.helmholtz_solve(rhs, dz, c, 0)
+    tol = 1e-10 if dtype == 1 else TOL
+    with chanfs.Plan(nx, ny, nz, 2.0, 1.0, dz, 0, dtype) as plan:
+        for opt, vals in ((chanfs.OPT_X_LINES, (1, 4, 16)), (chanfs.OPT_Y_TILE, (2, 4, 16)),
+                          (chanfs.OPT_PCR_PARTS, (1, 3, 8))):
+            for v in vals:
+                plan.set_option(opt, v)
+                assert plan.get_option(opt) == v
+                p = host(plan.poisson_solve(dev(f)))
+                u = host(plan.helmholtz_solve(c, dev(rhs)))
+                assert rel(p, ref) < tol and rel(u, href) < tol, (opt, v)
+            plan.set_option(opt, 0)
+        for opt, bad in ((chanfs.OPT_X_LINES, 65), (chanfs.OPT_Y_TILE, 33), (chanfs.OPT_PCR_PARTS, 65)):
+            with pytest.raises(chanfs.ChanfsError):
+                plan.set_option(opt, bad)
+        with pytest.raises(chanfs.ChanfsError) as err:
+            plan.set_option(chanfs.OPT_PCR_PARTS, 20)  # 39 / 20 < 3 rows
+        assert err.value.status == chanfs.EUNSUPPORTED
+        chosen = plan.autotune()
+        assert chosen["x_lines"] >= 1 and chosen["y_tile"] >= 1 and chosen["pcr_parts"] >= 1
+        p = host(plan.poisson_solve(dev(f)))
+        u = host(plan.helmholtz_solve(c, dev(rhs)))
+        assert rel(p, ref) < tol and rel(u, href) < tol
+        assert plan.check() == 0
+    # a second plan of the same size takes the remembered choice
+    with chanfs.Plan(nx, ny, nz, 2.0, 1.0, dz, 0, dtype) as plan2:
+        assert plan2.autotune() == chosen
