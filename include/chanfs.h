@@ -245,6 +245,12 @@ int cfs_last_info(cfs_plan_t plan, int* iters, double* rel_residual);
  */
 typedef struct cfs_group* cfs_group_t;
 int cfs_group_create(cfs_group_t* group, int nplans, const cfs_plan_t* plans);
+/* cfs_group_reserve makes an empty group with room for `capacity` plans;
+ * cfs_group_rebind (re)binds it to nplans <= capacity plans without
+ * allocating, the tables copied on `stream` ahead of the next solves there
+ * (a serving loop keeps one group per stream and rebinds it per batch). */
+int cfs_group_reserve(cfs_group_t* group, int capacity);
+int cfs_group_rebind(cfs_group_t group, int nplans, const cfs_plan_t* plans, void* stream);
 int cfs_group_destroy(cfs_group_t group);
 int cfs_group_size(cfs_group_t group, int* nplans);
 int cfs_group_poisson_solve(cfs_group_t group, const double* const* f, double* const* p,
@@ -256,6 +262,52 @@ int cfs_group_poisson_solve(cfs_group_t group, const double* const* f, double* c
 int cfs_group_helmholtz_solve(cfs_group_t group, const double* c, const int* loc,
                               const double* const* rhs, double* const* u, void* stream);
 int cfs_group_last_info(cfs_group_t group, int* iters, double* rel_residual);
+
+/*
+ * Serving.  The paper has no counterpart.  A server takes Poisson and
+ * Helmholtz solve requests from many concurrently running simulations
+ * ("runs", one grid each) and answers them with FP32 + FP64-refined solves
+ * (tolerance 1e-10, at most 4 FP32 solves).  Each run's plan stays resident in
+ * device memory while the budget allows: it is created when a request first
+ * needs it (and tuned with cfs_plan_autotune if `autotune`), and the plans of
+ * idle runs are destroyed, least recently used first, when a new plan would
+ * exceed hbm_budget_bytes.  `workers` threads, each with its own CUDA stream,
+ * form batches continuously: a free worker takes the oldest request whose run
+ * is idle, adds every pending request of the same kind for other idle runs (up
+ * to max_batch), and solves them as one grouped solve; requests arriving
+ * meanwhile join the next batch, and batches of different workers overlap on
+ * the device.  A result is bit-identical to the refined solve of the run's
+ * plan alone.
+ *   cfs_server_add_run  a grid (as cfs_plan_create); nx % 4 == 0; returns the
+ *       run index.  CFS_EUNSUPPORTED if its plan alone exceeds the budget.
+ *   cfs_server_submit  kind CFS_REQ_POISSON (c, loc ignored) or
+ *       CFS_REQ_HELMHOLTZ (c >= 0, loc a cfs_loc); rhs and out: device fields
+ *       of the run's size, distinct, owned by the caller and left untouched
+ *       until the request completes.  Returns a ticket.
+ *   cfs_server_wait  waits up to timeout_s seconds (< 0: no limit) for the
+ *       ticket; CFS_ETIMEOUT if not done.  On success *status is the solve's
+ *       status and *latency_s the time from submission to completion, and the
+ *       ticket is retired.
+ *   cfs_server_destroy  finishes the pending requests, stops the workers and
+ *       destroys the plans.
+ */
+typedef struct cfs_server* cfs_server_t;
+enum { CFS_REQ_POISSON = 0, CFS_REQ_HELMHOLTZ = 1 };
+typedef struct {
+  unsigned long long submitted, completed, failed, batches;
+  int max_batch_seen, plans_created, plans_evicted, plans_resident;
+  size_t bytes_in_use;  /* plan bytes held (reserved estimates included) */
+} cfs_server_stats_t;
+int cfs_server_create(cfs_server_t* server, size_t hbm_budget_bytes, int workers, int max_batch,
+                      int autotune);
+int cfs_server_add_run(cfs_server_t server, int nx, int ny, int nz, double lx, double ly,
+                       const double* dz, int poisson_bc, int* run);
+int cfs_server_submit(cfs_server_t server, int run, int kind, double c, int loc, const double* rhs,
+                      double* out, unsigned long long* ticket);
+int cfs_server_wait(cfs_server_t server, unsigned long long ticket, double timeout_s, int* status,
+                    double* latency_s);
+int cfs_server_stats(cfs_server_t server, cfs_server_stats_t* stats);
+int cfs_server_destroy(cfs_server_t server);
 
 /*
  * Kernel-shape options of a plan.  The paper has no counterpart: an option

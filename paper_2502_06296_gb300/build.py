@@ -20,7 +20,8 @@ LIB = os.path.join(HERE, "libchanfs.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
          "-Xcompiler", "-Wall"]
-SOURCES = ["plan.cu", "fft_x.cu", "fft_y.cu", "thomas.cu", "pcr.cu", "refine.cu", "group.cu", "tune.cu", "noalloc.cu"]
+SOURCES = ["plan.cu", "fft_x.cu", "fft_y.cu", "thomas.cu", "pcr.cu", "refine.cu", "group.cu",
+           "tune.cu", "noalloc.cu", "server.cpp"]
 
 
 def _nvcc() -> str:
@@ -45,7 +46,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
         objs.append(o)
         if force or _stale(o, [s] + headers):
             jobs.append((s, o))
@@ -53,6 +54,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     def compile_one(job):
         s, o = job
         cmd = [nvcc, *ARCH, *FLAGS, "-c", s, "-o", o]
+        if s.endswith(".cpp"):  # host code: the worker threads need pthreads
+            cmd = [nvcc, *FLAGS, "-Xcompiler", "-pthread", "-c", s, "-o", o]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {s}:\n{r.stdout}\n{r.stderr}")
@@ -67,7 +70,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             fh.write("\n".join(logs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
+        cmd = [nvcc, *ARCH, "-shared", "-Xcompiler", "-pthread", "-o", tmp, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

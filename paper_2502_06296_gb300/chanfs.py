@@ -25,6 +25,16 @@ X_FORWARD, Y_FORWARD, Z_SOLVE, Y_INVERSE, X_INVERSE = 0, 1, 2, 3, 4
 
 OPT_THOMAS_TILE, OPT_X_LINES, OPT_Y_TILE, OPT_PCR_PARTS = 1, 2, 3, 4
 
+REQ_POISSON, REQ_HELMHOLTZ = 0, 1
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_ulonglong), ("completed", ctypes.c_ulonglong),
+                ("failed", ctypes.c_ulonglong), ("batches", ctypes.c_ulonglong),
+                ("max_batch_seen", ctypes.c_int), ("plans_created", ctypes.c_int),
+                ("plans_evicted", ctypes.c_int), ("plans_resident", ctypes.c_int),
+                ("bytes_in_use", ctypes.c_size_t)]
+
 OK, EINVAL, ENOMEM, EUNSUPPORTED, ECUDA, ETIMEOUT, ENOTCONVERGED = 0, -1, -2, -3, -4, -5, -6
 
 _lib = None
@@ -71,6 +81,14 @@ def lib():
             "cfs_group_helmholtz_solve": ([vp, dp, ctypes.POINTER(i), ctypes.POINTER(vp),
                                            ctypes.POINTER(vp), vp], i),
             "cfs_plan_set_option": ([vp, i, i], i),
+            "cfs_group_reserve": ([ctypes.POINTER(vp), i], i),
+            "cfs_group_rebind": ([vp, i, ctypes.POINTER(vp), vp], i),
+            "cfs_server_create": ([ctypes.POINTER(vp), ctypes.c_size_t, i, i, i], i),
+            "cfs_server_add_run": ([vp, i, i, i, d, d, dp, i, ctypes.POINTER(i)], i),
+            "cfs_server_submit": ([vp, i, i, d, i, vp, vp, ctypes.POINTER(ctypes.c_ulonglong)], i),
+            "cfs_server_wait": ([vp, ctypes.c_ulonglong, d, ctypes.POINTER(i), ctypes.POINTER(d)], i),
+            "cfs_server_stats": ([vp, ctypes.POINTER(ServerStats)], i),
+            "cfs_server_destroy": ([vp], i),
             "cfs_plan_autotune": ([vp, vp], i),
             "cfs_plan_get_option": ([vp, i, ctypes.POINTER(i)], i),
         }
@@ -331,6 +349,79 @@ class Group:
         rho = (ctypes.c_double * n)()
         _check(lib().cfs_group_last_info(self._h, it, rho), "cfs_group_last_info")
         return list(zip(list(it), list(rho)))
+
+
+class Server:
+    """Serving loop for solve requests of many runs (see cfs_server_create):
+    plans resident under an HBM budget, continuous batching by worker threads
+    with one CUDA stream each, FP32 + FP64-refined grouped solves."""
+
+    def __init__(self, budget_bytes: int, workers: int = 2, max_batch: int = 16,
+                 autotune: bool = True):
+        h = ctypes.c_void_p()
+        _check(lib().cfs_server_create(ctypes.byref(h), int(budget_bytes), int(workers),
+                                       int(max_batch), int(bool(autotune))), "cfs_server_create")
+        self._h = h
+        self._shapes = []
+        self._held = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cfs_server_destroy(self._h)
+            self._h = None
+            self._held.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def add_run(self, nx: int, ny: int, nz: int, lx: float, ly: float, dz, bc: int = NEUMANN) -> int:
+        dz = np.ascontiguousarray(dz, dtype=np.float64)
+        if dz.size != nz:
+            raise ValueError("dz must have nz entries")
+        run = ctypes.c_int(-1)
+        _check(lib().cfs_server_add_run(self._h, nx, ny, nz, float(lx), float(ly),
+                                        dz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), bc,
+                                        ctypes.byref(run)), "cfs_server_add_run")
+        self._shapes.append((nz, ny, nx))
+        return run.value
+
+    def submit(self, run: int, kind: int, rhs, out, c: float = 0.0, loc: int = CENTER) -> int:
+        """Queue a solve; rhs and out (float64 CUDA tensors of the run's shape)
+        are held until the ticket is waited for."""
+        import torch
+        shape = self._shapes[run] if 0 <= run < len(self._shapes) else None
+        for t, name in ((rhs, "rhs"), (out, "out")):
+            if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda \
+                    or not t.is_contiguous() or tuple(t.shape) != shape:
+                raise ValueError(f"{name} must be a contiguous float64 CUDA tensor of the run's shape")
+        ticket = ctypes.c_ulonglong(0)
+        _check(lib().cfs_server_submit(self._h, run, kind, float(c), loc, ctypes.c_void_p(rhs.data_ptr()),
+                                       ctypes.c_void_p(out.data_ptr()), ctypes.byref(ticket)),
+               "cfs_server_submit")
+        self._held[ticket.value] = (rhs, out)
+        return ticket.value
+
+    def wait(self, ticket: int, timeout: float = -1.0):
+        """(solve status, latency in seconds) of a ticket; raises on timeout."""
+        status, lat = ctypes.c_int(0), ctypes.c_double(0.0)
+        _check(lib().cfs_server_wait(self._h, ticket, float(timeout), ctypes.byref(status),
+                                     ctypes.byref(lat)), "cfs_server_wait")
+        self._held.pop(ticket, None)
+        return status.value, lat.value
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().cfs_server_stats(self._h, ctypes.byref(st)), "cfs_server_stats")
+        return {name: getattr(st, name) for name, _ in ServerStats._fields_}
 
 
 def _host_ptr(a, shape):

@@ -143,6 +143,7 @@ cudaError_t launch_group_update(const ResBox* boxes, int nbox, const float* fmax
                                 const double* tol, const int* maxit, int it, int* active,
                                 int* iters, double* rho, int* nactive, cudaStream_t st);
 cudaError_t launch_group_fmax(const ResBox* boxes, int nbox, float* fmax, cudaStream_t st);
+cudaError_t launch_group_zero_max(const ResBox* boxes, int nbox, cudaStream_t st);
 enum {
   GSTAGE_PLANE_SUM = 0,
   GSTAGE_MEAN_FINAL = 1,

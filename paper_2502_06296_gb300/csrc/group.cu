@@ -38,12 +38,43 @@ std::vector<int> offsets(const std::vector<int>& blocks, int* total) {
 
 }  // namespace
 
+// Descriptor tables of a bound group, at fixed offsets of one device buffer
+// (and of its pinned host staging copy) sized for the group's capacity.
+struct GroupTables {
+  size_t xf, xi, y, th, res, sx, sy, sth, sres, splane, sone, ssub, bytes;
+  explicit GroupTables(int cap) {
+    size_t o = 0;
+    auto take = [&](size_t n) {
+      const size_t at = o;
+      o += (n + 255) / 256 * 256;
+      return at;
+    };
+    xf = take(sizeof(XBox) * cap);
+    xi = take(sizeof(XBox) * cap);
+    y = take(sizeof(YBox) * cap);
+    th = take(sizeof(ThomasArgs) * cap);
+    res = take(sizeof(ResBox) * cap);
+    sx = take(sizeof(int) * (cap + 1));
+    sy = take(sizeof(int) * (cap + 1));
+    sth = take(sizeof(int) * (cap + 1));
+    sres = take(sizeof(int) * (cap + 1));
+    splane = take(sizeof(int) * (cap + 1));
+    sone = take(sizeof(int) * (cap + 1));
+    ssub = take(sizeof(int) * (cap + 1));
+    bytes = o;
+  }
+};
+
 struct cfs_group {
-  int nbox = 0;
+  int cap = 0;   // boxes the buffers hold
+  int nbox = 0;  // boxes bound
   int device = 0;
   std::vector<cfs_plan*> plans;
   std::vector<int> neumann;
-  // per-kernel descriptors and block offsets
+  GroupTables tab{1};
+  unsigned char* d_tab = nullptr;
+  unsigned char* h_tab = nullptr;  // pinned staging of the tables
+  // per-kernel descriptors and block offsets (inside d_tab)
   XBox* d_xf = nullptr;
   XBox* d_xi = nullptr;
   YBox* d_y = nullptr;
@@ -70,18 +101,18 @@ struct cfs_group {
   ResBox* d_hres = nullptr;
   ResBox* h_hres = nullptr;
   int* d_spcr = nullptr;
-  cudaEvent_t io_copied = nullptr;
-  std::vector<ResBox> res;  // host copy of d_res
+  cudaEvent_t io_copied = nullptr;  // staging buffers free again after this
+  std::vector<ResBox> res;          // host copy of the bound boxes' residual records
   std::vector<int> last_iters;
   std::vector<double> last_rho;
 };
 
 static void group_free(cfs_group* G) {
-  void* ptrs[] = {G->d_xf,  G->d_xi,   G->d_y,     G->d_th,   G->d_res,   G->d_sx,
-                  G->d_sy,  G->d_sth,  G->d_sres,  G->d_splane, G->d_sone, G->d_ssub,
-                  G->d_active, G->d_mean, G->d_fmax, G->d_tol, G->d_maxit, G->d_iters,
-                  G->d_rho, G->d_nactive, G->d_io, G->d_pcr, G->d_hres, G->d_spcr};
+  void* ptrs[] = {G->d_tab,   G->d_active, G->d_mean, G->d_fmax, G->d_tol,  G->d_maxit,
+                  G->d_iters, G->d_rho,    G->d_nactive, G->d_io, G->d_pcr, G->d_hres,
+                  G->d_spcr};
   for (void* p : ptrs) cudaFree(p);
+  if (G->h_tab) cudaFreeHost(G->h_tab);
   if (G->h_io) cudaFreeHost(G->h_io);
   if (G->h_pcr) cudaFreeHost(G->h_pcr);
   if (G->h_hres) cudaFreeHost(G->h_hres);
@@ -89,38 +120,78 @@ static void group_free(cfs_group* G) {
   delete G;
 }
 
-extern "C" int cfs_group_create(cfs_group_t* out, int nplans, const cfs_plan_t* plans) {
-  if (!out) return CFS_EINVAL;
-  *out = nullptr;
-  if (nplans < 1 || nplans > kMaxGroup || !plans) return CFS_EINVAL;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return CFS_ECUDA;
+static int group_alloc(cfs_group* G, int cap) {
+  G->cap = cap;
+  G->tab = GroupTables(cap);
+  cudaError_t e = cudaMalloc(&G->d_tab, G->tab.bytes);
+  if (e == cudaSuccess) e = cudaMallocHost(&G->h_tab, G->tab.bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_active, sizeof(int) * cap);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_mean, sizeof(int) * cap);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_fmax, sizeof(float) * cap);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_tol, sizeof(double) * cap);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_maxit, sizeof(int) * cap);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_iters, sizeof(int) * cap);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_rho, sizeof(double) * cap);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_nactive, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_io, sizeof(GroupIo) * cap);
+  if (e == cudaSuccess) e = cudaMallocHost(&G->h_io, sizeof(GroupIo) * cap);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_pcr, sizeof(PcrBox) * cap);
+  if (e == cudaSuccess) e = cudaMallocHost(&G->h_pcr, sizeof(PcrBox) * cap);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_hres, sizeof(ResBox) * cap);
+  if (e == cudaSuccess) e = cudaMallocHost(&G->h_hres, sizeof(ResBox) * cap);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_spcr, sizeof(int) * (cap + 1));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G->io_copied, cudaEventDisableTiming);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? CFS_ENOMEM : CFS_ECUDA;
+  const GroupTables& t = G->tab;
+  G->d_xf = reinterpret_cast<XBox*>(G->d_tab + t.xf);
+  G->d_xi = reinterpret_cast<XBox*>(G->d_tab + t.xi);
+  G->d_y = reinterpret_cast<YBox*>(G->d_tab + t.y);
+  G->d_th = reinterpret_cast<ThomasArgs*>(G->d_tab + t.th);
+  G->d_res = reinterpret_cast<ResBox*>(G->d_tab + t.res);
+  G->d_sx = reinterpret_cast<int*>(G->d_tab + t.sx);
+  G->d_sy = reinterpret_cast<int*>(G->d_tab + t.sy);
+  G->d_sth = reinterpret_cast<int*>(G->d_tab + t.sth);
+  G->d_sres = reinterpret_cast<int*>(G->d_tab + t.sres);
+  G->d_splane = reinterpret_cast<int*>(G->d_tab + t.splane);
+  G->d_sone = reinterpret_cast<int*>(G->d_tab + t.sone);
+  G->d_ssub = reinterpret_cast<int*>(G->d_tab + t.ssub);
+  return CFS_OK;
+}
+
+static int check_plans(int nplans, const cfs_plan_t* plans, int dev) {
   for (int b = 0; b < nplans; ++b) {
     if (!plans[b]) return CFS_EINVAL;
     if (plans[b]->dtype != CFS_F32_REFINED || plans[b]->device != dev) return CFS_EUNSUPPORTED;
     for (int c = 0; c < b; ++c)
       if (plans[c] == plans[b]) return CFS_EINVAL;  // boxes share the plan's work field
   }
-  cfs_group* G = new (std::nothrow) cfs_group();
-  if (!G) return CFS_ENOMEM;
-  G->nbox = nplans;
-  G->device = dev;
-  std::vector<XBox> xf(nplans), xi(nplans);
-  std::vector<YBox> y(nplans);
-  std::vector<ThomasArgs> th(nplans);
-  std::vector<ResBox> res(nplans);
+  return CFS_OK;
+}
+
+// Builds the descriptor tables of `plans` in the pinned staging buffer and
+// copies them to the device on `st` (ordered before the solves on st).
+static int group_bind(cfs_group* G, int nplans, const cfs_plan_t* plans, cudaStream_t st) {
+  if (cudaEventSynchronize(G->io_copied) != cudaSuccess) return CFS_ECUDA;  // staging free
+  const GroupTables& t = G->tab;
+  XBox* xf = reinterpret_cast<XBox*>(G->h_tab + t.xf);
+  XBox* xi = reinterpret_cast<XBox*>(G->h_tab + t.xi);
+  YBox* y = reinterpret_cast<YBox*>(G->h_tab + t.y);
+  ThomasArgs* th = reinterpret_cast<ThomasArgs*>(G->h_tab + t.th);
+  ResBox* res = reinterpret_cast<ResBox*>(G->h_tab + t.res);
   std::vector<int> bx(nplans), by(nplans), bth(nplans), bres(nplans), bplane(nplans),
-      bone(nplans, 1), bsub(nplans), maxit(nplans);
-  std::vector<double> tol(nplans);
-  int rc = CFS_OK;
-  for (int b = 0; b < nplans && !rc; ++b) {
+      bone(nplans, 1), bsub(nplans);
+  G->plans.clear();
+  G->neumann.clear();
+  G->res.assign(nplans, ResBox{});
+  G->smem_x = G->smem_y = 0;
+  for (int b = 0; b < nplans; ++b) {
     cfs_plan* P = plans[b];
     G->plans.push_back(P);
     G->neumann.push_back(P->bc == CFS_BC_NEUMANN);
     G->smem_x = std::max(G->smem_x, x_group_box(P, false, &xf[b], &bx[b]));
     x_group_box(P, true, &xi[b], &bx[b]);
     const size_t sy = y_group_box(P, &y[b], &by[b]);
-    if (!sy) rc = CFS_ECUDA;
+    if (!sy) return CFS_ECUDA;
     G->smem_y = std::max(G->smem_y, sy);
     thomas_group_box(P, &th[b], &bth[b]);
     const long long nxy = (long long)P->nx * P->ny;
@@ -140,53 +211,77 @@ extern "C" int cfs_group_create(cfs_group_t* out, int nplans, const cfs_plan_t* 
     r.idx2 = 1.0 / (dx * dx);
     r.idy2 = 1.0 / (dy * dy);
     r.neumann = (P->bc == CFS_BC_NEUMANN);
+    G->res[b] = r;
     bres[b] = (int)((nxy + 127) / 128);
     bplane[b] = P->nz;
     bsub[b] = (int)group_sub_blocks(nxy * P->nz);
-    tol[b] = P->tol;
-    maxit[b] = P->maxit;
   }
-  cudaError_t e = rc ? cudaErrorInvalidValue : cudaSuccess;
-  std::vector<int> sx = offsets(bx, &G->tx), sy = offsets(by, &G->ty), sth = offsets(bth, &G->tth),
-                   sres = offsets(bres, &G->tres), splane = offsets(bplane, &G->tplane),
-                   sone = offsets(bone, &G->tone), ssub = offsets(bsub, &G->tsub);
-  if (e == cudaSuccess) e = upload(&G->d_xf, xf);
-  if (e == cudaSuccess) e = upload(&G->d_xi, xi);
-  if (e == cudaSuccess) e = upload(&G->d_y, y);
-  if (e == cudaSuccess) e = upload(&G->d_th, th);
-  if (e == cudaSuccess) e = upload(&G->d_res, res);
-  if (e == cudaSuccess) e = upload(&G->d_sx, sx);
-  if (e == cudaSuccess) e = upload(&G->d_sy, sy);
-  if (e == cudaSuccess) e = upload(&G->d_sth, sth);
-  if (e == cudaSuccess) e = upload(&G->d_sres, sres);
-  if (e == cudaSuccess) e = upload(&G->d_splane, splane);
-  if (e == cudaSuccess) e = upload(&G->d_sone, sone);
-  if (e == cudaSuccess) e = upload(&G->d_ssub, ssub);
-  if (e == cudaSuccess) e = upload(&G->d_tol, tol);
-  if (e == cudaSuccess) e = upload(&G->d_maxit, maxit);
-  if (e == cudaSuccess) e = cudaMalloc(&G->d_active, sizeof(int) * nplans);
-  if (e == cudaSuccess) e = cudaMalloc(&G->d_mean, sizeof(int) * nplans);
-  if (e == cudaSuccess) e = cudaMalloc(&G->d_fmax, sizeof(float) * nplans);
-  if (e == cudaSuccess) e = cudaMalloc(&G->d_iters, sizeof(int) * nplans);
-  if (e == cudaSuccess) e = cudaMalloc(&G->d_rho, sizeof(double) * nplans);
-  if (e == cudaSuccess) e = cudaMalloc(&G->d_nactive, sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&G->d_io, sizeof(GroupIo) * nplans);
-  if (e == cudaSuccess) e = cudaMallocHost(&G->h_io, sizeof(GroupIo) * nplans);
-  if (e == cudaSuccess) e = cudaMalloc(&G->d_pcr, sizeof(PcrBox) * nplans);
-  if (e == cudaSuccess) e = cudaMallocHost(&G->h_pcr, sizeof(PcrBox) * nplans);
-  if (e == cudaSuccess) e = cudaMalloc(&G->d_hres, sizeof(ResBox) * nplans);
-  if (e == cudaSuccess) e = cudaMallocHost(&G->h_hres, sizeof(ResBox) * nplans);
-  if (e == cudaSuccess) e = cudaMalloc(&G->d_spcr, sizeof(int) * (nplans + 1));
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G->io_copied, cudaEventDisableTiming);
-  if (e != cudaSuccess) {
-    group_free(G);
-    return rc ? rc : (e == cudaErrorMemoryAllocation ? CFS_ENOMEM : CFS_ECUDA);
-  }
-  G->res = res;
+  auto put = [&](size_t at, const std::vector<int>& v) {
+    memcpy(G->h_tab + at, v.data(), sizeof(int) * v.size());
+  };
+  put(t.sx, offsets(bx, &G->tx));
+  put(t.sy, offsets(by, &G->ty));
+  put(t.sth, offsets(bth, &G->tth));
+  put(t.sres, offsets(bres, &G->tres));
+  put(t.splane, offsets(bplane, &G->tplane));
+  put(t.sone, offsets(bone, &G->tone));
+  put(t.ssub, offsets(bsub, &G->tsub));
+  cudaError_t e = cudaMemcpyAsync(G->d_tab, G->h_tab, t.bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaEventRecord(G->io_copied, st);
+  if (e != cudaSuccess) return CFS_ECUDA;
+  G->nbox = nplans;
   G->last_iters.assign(nplans, 0);
   G->last_rho.assign(nplans, 0.0);
+  return CFS_OK;
+}
+
+extern "C" int cfs_group_create(cfs_group_t* out, int nplans, const cfs_plan_t* plans) {
+  if (!out) return CFS_EINVAL;
+  *out = nullptr;
+  if (nplans < 1 || nplans > kMaxGroup || !plans) return CFS_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CFS_ECUDA;
+  int rc = check_plans(nplans, plans, dev);
+  if (rc) return rc;
+  cfs_group* G = new (std::nothrow) cfs_group();
+  if (!G) return CFS_ENOMEM;
+  G->device = dev;
+  rc = group_alloc(G, nplans);
+  if (!rc) rc = group_bind(G, nplans, plans, 0);
+  if (!rc && cudaStreamSynchronize(0) != cudaSuccess) rc = CFS_ECUDA;
+  if (rc) {
+    group_free(G);
+    return rc;
+  }
   *out = G;
   return CFS_OK;
+}
+
+extern "C" int cfs_group_reserve(cfs_group_t* out, int capacity) {
+  if (!out) return CFS_EINVAL;
+  *out = nullptr;
+  if (capacity < 1 || capacity > kMaxGroup) return CFS_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CFS_ECUDA;
+  cfs_group* G = new (std::nothrow) cfs_group();
+  if (!G) return CFS_ENOMEM;
+  G->device = dev;
+  const int rc = group_alloc(G, capacity);
+  if (rc) {
+    group_free(G);
+    return rc;
+  }
+  *out = G;
+  return CFS_OK;
+}
+
+extern "C" int cfs_group_rebind(cfs_group_t G, int nplans, const cfs_plan_t* plans,
+                                void* stream) {
+  if (!G || !plans || nplans < 1) return CFS_EINVAL;
+  if (nplans > G->cap) return CFS_EUNSUPPORTED;
+  int rc = check_plans(nplans, plans, G->device);
+  if (rc) return rc;
+  return group_bind(G, nplans, plans, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" int cfs_group_destroy(cfs_group_t G) {
@@ -200,7 +295,7 @@ static int rc_of(cudaError_t e) { return e == cudaSuccess ? CFS_OK : CFS_ECUDA; 
 
 extern "C" int cfs_group_poisson_solve(cfs_group_t G, const double* const* f, double* const* p,
                                        void* stream) {
-  if (!G || !f || !p) return CFS_EINVAL;
+  if (!G || !f || !p || G->nbox < 1) return CFS_EINVAL;
   const int nb = G->nbox;
   for (int b = 0; b < nb; ++b)
     if (!f[b] || !p[b] || static_cast<const void*>(f[b]) == static_cast<const void*>(p[b]))
@@ -242,6 +337,7 @@ extern "C" int cfs_group_poisson_solve(cfs_group_t G, const double* const* f, do
     e = launch_group_refine_stage(GSTAGE_MEAN_FINAL, G->d_res, g, G->tone, G->d_io, 0, st);
   }
   // r_0 = f - mean and its max-norm (the reference of each box)
+  if (e == cudaSuccess) e = launch_group_zero_max(G->d_res, nb, st);
   if (e == cudaSuccess) {
     g.start = G->d_sres;
     g.active = nullptr;
@@ -340,7 +436,7 @@ extern "C" int cfs_group_poisson_solve(cfs_group_t G, const double* const* f, do
 extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const int* loc,
                                          const double* const* rhs, double* const* u,
                                          void* stream) {
-  if (!G || !c || !loc || !rhs || !u) return CFS_EINVAL;
+  if (!G || !c || !loc || !rhs || !u || G->nbox < 1) return CFS_EINVAL;
   const int nb = G->nbox;
   for (int b = 0; b < nb; ++b)
     if (!rhs[b] || !u[b] || static_cast<const void*>(rhs[b]) == static_cast<const void*>(u[b]))
@@ -389,6 +485,7 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
     e = cudaMemcpyAsync(G->d_maxit, maxits.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st);
   // r_0 = rhs and its max-norm
   GroupMap g{G->d_sres, nullptr, nb};
+  if (e == cudaSuccess) e = launch_group_zero_max(G->d_hres, nb, st);
   if (e == cudaSuccess)
     e = launch_group_refine_stage(GSTAGE_HELM_RESIDUAL, G->d_hres, g, G->tres, G->d_io, 0, st);
   if (e == cudaSuccess) e = launch_group_fmax(G->d_hres, nb, G->d_fmax, st);

@@ -264,6 +264,13 @@ __global__ void group_update_kernel(const ResBox* boxes, int nbox, const float* 
   else atomicAdd(nactive, 1);
 }
 
+// Clears every box's max-norm word before the first residual (a plan's word
+// holds whatever its last solve, or its allocation, left there).
+__global__ void group_zero_max_kernel(const ResBox* boxes, int nbox) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < nbox) *boxes[b].rmax = 0u;
+}
+
 // The first residual's max |f - mean| of each box (the reference norm).
 __global__ void group_fmax_kernel(const ResBox* boxes, int nbox, float* fmax) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -301,6 +308,11 @@ cudaError_t launch_group_update(const ResBox* boxes, int nbox, const float* fmax
                                 int* iters, double* rho, int* nactive, cudaStream_t st) {
   group_update_kernel<<<(nbox + 127) / 128, 128, 0, st>>>(boxes, nbox, fmax, tol, maxit, it,
                                                           active, iters, rho, nactive);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group_zero_max(const ResBox* boxes, int nbox, cudaStream_t st) {
+  group_zero_max_kernel<<<(nbox + 127) / 128, 128, 0, st>>>(boxes, nbox);
   return cudaGetLastError();
 }
 

@@ -81,6 +81,7 @@ extern "C" int cfs_plan_autotune(cfs_plan_t P, void* stream) {
     }
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool had_stage = P->d_stage != nullptr;
   int rc = plan_ensure_stage(P);
   if (rc) return rc;
   const size_t npts = (size_t)P->nx * P->ny * P->nz;
@@ -175,6 +176,11 @@ extern "C" int cfs_plan_autotune(cfs_plan_t P, void* stream) {
     plan_helm_forget(P, kProbeC);
   }
   if (cudaStreamSynchronize(st) != cudaSuccess) return CFS_ECUDA;
+  if (!had_stage) {  // the scratch field was the tuner's own
+    cudaFree(P->d_stage);
+    P->d_stage = nullptr;
+    P->device_bytes -= sizeof(double) * npts;
+  }
   apply(P, best);
   std::lock_guard<std::mutex> lock(g_mu);
   g_cache[key] = best;

@@ -160,3 +160,22 @@ def test_group_helmholtz_matches_single_solves_and_oracle(chanfs):
         assert plan.check() == 0
     for p in plans:
         p.close()
+
+
+def test_group_ignores_stale_reduction_words(chanfs):
+    """A plan's max-norm word may hold anything when a grouped solve starts
+    (here: a huge value planted by a refined solve of a large right-hand
+    side that was then abandoned); the grouped solve must not read it."""
+    plan, f, dz = make_box(chanfs, 0, (32, 24, 16, 1.5, 0))
+    x = dev(f)
+    alone = host(plan.poisson_solve(x))
+    plan.set_refinement(1e-10, 1)
+    with pytest.raises(chanfs.ChanfsError):
+        plan.poisson_solve(dev(1e30 * f))  # leaves a huge residual norm in the word
+    plan.set_refinement(1e-10, 4)
+    with chanfs.Group([plan]) as g:
+        got = host(g.poisson_solve([x])[0])
+        gh = host(g.helmholtz_solve([1e-5], [x])[0])
+    assert np.array_equal(got, alone)
+    assert np.array_equal(gh, host(plan.helmholtz_solve(1e-5, x)))
+    plan.close()
