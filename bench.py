@@ -299,6 +299,200 @@ def run_mixed(chanfs, torch, device, reps: int = 5, warmup: int = 3):
 
 
 # ----------------------------------------------------------------------------
+# Batched ensemble: 48 boxes, grouped FP32 + FP64-refined solves vs per box
+# ----------------------------------------------------------------------------
+
+def run_ensemble(chanfs, torch, device, reps: int = 3):
+    """One ensemble step = per box a Poisson solve (Neumann) and three
+    Helmholtz solves (u, v centred, w face; the box's own alpha nu dt).
+    Grouped (one launch per stage for all boxes, autotuned shapes) against
+    the same work box by box in FP64 and box by box refined."""
+    cfg = synth.ENSEMBLE
+    boxes = synth.ensemble_boxes(cfg)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(cfg["seed"])
+    plans32, plans64, f, rhs = [], [], [], []
+    t0 = time.perf_counter()
+    for nx, ny, nz, beta, c in boxes:
+        dz = synth.tanh_dz(nz, beta)
+        p32 = chanfs.Plan(nx, ny, nz, cfg["lx"], cfg["ly"], dz, chanfs.NEUMANN, chanfs.F32_REFINED)
+        p32.autotune()
+        p64 = chanfs.Plan(nx, ny, nz, cfg["lx"], cfg["ly"], dz, chanfs.NEUMANN, chanfs.F64)
+        p64.autotune()
+        plans32.append(p32)
+        plans64.append(p64)
+        f.append(torch.randn(nz, ny, nx, dtype=torch.float64, device=device, generator=gen))
+        rhs.append([torch.randn(nz, ny, nx, dtype=torch.float64, device=device, generator=gen)
+                    for _ in range(3)])
+    setup_s = time.perf_counter() - t0
+    npts = sum(nx * ny * nz for nx, ny, nz, _, _ in boxes)
+    cs = [b[4] for b in boxes]
+    locs = (chanfs.CENTER, chanfs.CENTER, chanfs.FACE)
+    p = [torch.empty_like(x) for x in f]
+    u = [[torch.empty_like(x) for x in r] for r in rhs]
+    group = chanfs.Group(plans32)
+
+    def grouped():
+        group.poisson_solve(f, p)
+        for k in range(3):
+            group.helmholtz_solve(cs, [r[k] for r in rhs], [locs[k]] * len(boxes), [x[k] for x in u])
+
+    def per_box(plans):
+        def step():
+            for b, pl in enumerate(plans):
+                pl.poisson_solve(f[b], out=p[b])
+                for k in range(3):
+                    pl.helmholtz_solve(cs[b], rhs[b][k], locs[k], out=u[b][k])
+        return step
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    t_group = timed(grouped)
+    info = group.last_info()
+    t64 = timed(per_box(plans64))
+    t32 = timed(per_box(plans32))
+    group.close()
+    opts = {}
+    for (nx, ny, nz, _, _), pl in zip(boxes, plans32):
+        opts[f"{nx}x{ny}x{nz}"] = [pl.get_option(o) for o in (chanfs.OPT_X_LINES, chanfs.OPT_Y_TILE,
+                                                              chanfs.OPT_THOMAS_TILE, chanfs.OPT_PCR_PARTS)]
+    for pl in plans32 + plans64:
+        pl.close()
+    return {"workload": cfg["name"], "boxes": len(boxes), "points": npts,
+            "step": "per box: Poisson (Neumann) + 3 Helmholtz (u, v centred, w face)",
+            "grouped_refined_ms": round(t_group, 3), "per_box_f64_ms": round(t64, 3),
+            "per_box_refined_ms": round(t32, 3),
+            "grouped_ns_per_pt": t_group * 1e6 / npts, "per_box_f64_ns_per_pt": t64 * 1e6 / npts,
+            "speedup_vs_per_box_f64": t64 / t_group,
+            "max_fp32_solves_last_helmholtz": max(i for i, _ in info),
+            "max_rel_residual_last_helmholtz": max(r for _, r in info),
+            "autotuned": "x_lines, y_tile, thomas_tile, pcr_parts per refined box size",
+            "options": opts, "setup_s": round(setup_s, 1),
+            "timing": f"median of {reps} CUDA-event timings of whole steps; fields larger than "
+                      "L2 in total (no flush between steps)"}
+
+
+# ----------------------------------------------------------------------------
+# Serving stream: Poisson arrivals of Poisson/Helmholtz requests from 32 runs
+# ----------------------------------------------------------------------------
+
+def run_serving(chanfs, torch, device, nreq: int = 0, workers: int = 4, max_batch: int = 32):
+    cfg = dict(synth.SERVING)
+    if nreq:
+        cfg["nreq"] = nreq
+    runs, reqs = synth.serving_stream(cfg)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(cfg["seed"])
+    srv = chanfs.Server(int(cfg["budget_gb"] * 2**30), workers, max_batch, autotune=True)
+    fields = []
+    for nx, ny, nz, beta, _ in runs:
+        srv.add_run(nx, ny, nz, cfg["lx"], cfg["ly"], synth.tanh_dz(nz, beta), chanfs.NEUMANN)
+        x = torch.randn(nz, ny, nx, dtype=torch.float64, device=device, generator=gen)
+        fields.append((x, torch.empty_like(x)))
+    torch.cuda.synchronize()
+    # warm the plans (creation, tuning, the Helmholtz sets of each run)
+    t0 = time.perf_counter()
+    warm = []
+    for r, (nx, ny, nz, beta, cs) in enumerate(runs):
+        warm.append(srv.submit(r, chanfs.REQ_POISSON, fields[r][0], fields[r][1]))
+        for c in cs:
+            for loc in (chanfs.CENTER, chanfs.FACE):
+                warm.append(srv.submit(r, chanfs.REQ_HELMHOLTZ, fields[r][0], fields[r][1], c, loc))
+    for t in warm:
+        srv.wait(t)
+    warm_s = time.perf_counter() - t0
+    before = srv.stats()
+    tickets = []
+    start = time.perf_counter()
+    for arrival, r, kind, ci, loc in reqs:
+        while True:
+            lag = start + arrival - time.perf_counter()
+            if lag <= 0:
+                break
+            if lag > 2e-4:
+                time.sleep(lag - 1e-4)
+        tickets.append(srv.submit(r, kind, fields[r][0], fields[r][1], runs[r][4][ci], loc))
+    lat, failed, statuses = [], 0, {}
+    for t in tickets:
+        status, l = srv.wait(t)
+        lat.append(l)
+        failed += status != 0
+        if status:
+            statuses[chanfs.status_string(status)] = statuses.get(chanfs.status_string(status), 0) + 1
+    span = time.perf_counter() - start
+    after = srv.stats()
+    # capacity: the first `ncap` requests submitted at once (saturated server)
+    ncap = min(4000, len(reqs))
+    t0 = time.perf_counter()
+    cap_tickets = [srv.submit(r, kind, fields[r][0], fields[r][1], runs[r][4][ci], loc)
+                   for _, r, kind, ci, loc in reqs[:ncap]]
+    for t in cap_tickets:
+        srv.wait(t)
+    cap_s = time.perf_counter() - t0
+    srv.close()
+    # the same requests as plain per-request FP64 solves, one after another
+    plans64 = []
+    for nx, ny, nz, beta, _ in runs:
+        pl = chanfs.Plan(nx, ny, nz, cfg["lx"], cfg["ly"], synth.tanh_dz(nz, beta), chanfs.NEUMANN)
+        pl.autotune()
+        plans64.append(pl)
+
+    def fp64(sub):
+        for _, r, kind, ci, loc in sub:
+            if kind == 0:
+                plans64[r].poisson_solve(fields[r][0], out=fields[r][1])
+            else:
+                plans64[r].helmholtz_solve(runs[r][4][ci], fields[r][0], loc, out=fields[r][1])
+
+    fp64(reqs[:200])  # Helmholtz sets and warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fp64(reqs[:ncap])
+    torch.cuda.synchronize()
+    f64_s = time.perf_counter() - t0
+    for pl in plans64:
+        pl.close()
+    lat = np.array(lat)
+    pts = np.array([runs[r][0] * runs[r][1] * runs[r][2] for _, r, _, _, _ in reqs], dtype=np.float64)
+    nb = after["batches"] - before["batches"]
+    return {"workload": cfg["name"], "requests": len(reqs), "runs": len(runs),
+            "offered_rate_per_s": cfg["rate"], "arrival_span_s": reqs[-1][0],
+            "poisson_requests": sum(1 for q in reqs if q[2] == 0),
+            "solves_per_s": len(reqs) / span, "wall_s": span,
+            "p50_latency_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_latency_ms": float(np.percentile(lat, 99) * 1e3),
+            "mean_latency_ms": float(lat.mean() * 1e3), "failed": int(failed),
+            "failures": statuses,
+            "grid_points_per_s": float(pts.sum() / span),
+            "mean_batch": (after["completed"] - before["completed"]) / max(nb, 1),
+            "max_batch": after["max_batch_seen"], "plans_created": after["plans_created"],
+            "plans_evicted": after["plans_evicted"], "plan_bytes": after["bytes_in_use"],
+            "workers": workers, "budget_gb": cfg["budget_gb"], "warm_s": round(warm_s, 1),
+            "capacity_solves_per_s": ncap / cap_s,
+            "per_request_f64_solves_per_s": ncap / f64_s,
+            "capacity_vs_per_request_f64": f64_s / cap_s,
+            "capacity_sample": f"first {ncap} requests of the stream submitted at once, against the "
+                               "same requests solved one after another by FP64 plans",
+            "precision": "Poisson: FP32 solves + FP64 refinement to 1e-10 (at most 4 FP32 "
+                         "solves); Helmholtz: per size the faster of that and FP64 Algorithm 2 "
+                         "(autotuner), both within 1e-10",
+            "latency": "host clock from submission (at the scheduled arrival) to completion; "
+                       "plans warmed before the stream"}
+
+
+# ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
 
@@ -310,6 +504,22 @@ def run_mixed_only(args):
     from paper_2502_06296_gb300 import chanfs
     mixed = run_mixed(chanfs, torch, torch.device("cuda", 0), reps=args.steps, warmup=args.warmup)
     print(json.dumps({"mixed": mixed}), flush=True)
+    return 0
+
+
+def run_extras_only(args):
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2502_06296_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2502_06296_gb300 import chanfs
+    dev = torch.device("cuda", 0)
+    out = {}
+    if not args.no_ensemble:
+        out["ensemble"] = run_ensemble(chanfs, torch, dev)
+    if not args.no_serving:
+        out["serving"] = run_serving(chanfs, torch, dev, args.serve_requests)
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -468,6 +678,10 @@ def run_ours(args):
     del f, rhs, p, us, ref_bits
     if not args.no_mixed:
         line["mixed"] = run_mixed(chanfs, torch, device)
+    if not args.no_ensemble:
+        line["ensemble"] = run_ensemble(chanfs, torch, device)
+    if not args.no_serving:
+        line["serving"] = run_serving(chanfs, torch, device, args.serve_requests)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     else:
@@ -486,6 +700,12 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the FP32-refined vs FP64 solve of the 1024x768x512 workload")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the 48-box ensemble")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving stream")
+    ap.add_argument("--serve-requests", type=int, default=0,
+                    help="requests of the serving stream (0: the full 20,000)")
+    ap.add_argument("--extras-only", action="store_true",
+                    help="run only the ensemble and serving measurements")
     ap.add_argument("--mixed-only", action="store_true",
                     help="run only the FP32-refined vs FP64 comparison and print its object")
     ap.add_argument("--nz", type=int, default=0,
@@ -497,6 +717,8 @@ def main(argv=None):
         return run_reference(args)
     if args.mixed_only:
         return run_mixed_only(args)
+    if args.extras_only:
+        return run_extras_only(args)
     return run_ours(args)
 
 

@@ -324,13 +324,24 @@ int cfs_server_destroy(cfs_server_t server);
  *   CFS_OPT_PCR_PARTS  z-partitions of Algorithm 2 for Helmholtz sets that
  *       are prepared without an explicit count: 0 automatic (about 32 rows
  *       per partition) or 1..64, each partition at least 3 rows.
+ *   CFS_OPT_HELM_FP64  CFS_F32_REFINED plans: 1 solves Helmholtz by FP64
+ *       Algorithm 2 directly (no refinement; its error is that of the FP64
+ *       path, below the refinement target), 0 (default) refines FP32 solves.
+ *       On hardware where FP64 is scarce the refinement's FP64 residual costs
+ *       as much as the FP64 solve itself, so the tuner may pick 1.
  * cfs_plan_set_option returns CFS_EINVAL for an unknown option or value, and
  * CFS_EUNSUPPORTED if the value cannot run at this plan's size (a tile that
  * does not fit in shared memory).  cfs_plan_get_option reports the value in
  * effect, with automatic choices resolved (for CFS_F32_REFINED plans, the
  * choice of the FP32 inner solve).
  */
-enum { CFS_OPT_THOMAS_TILE = 1, CFS_OPT_X_LINES = 2, CFS_OPT_Y_TILE = 3, CFS_OPT_PCR_PARTS = 4 };
+enum {
+  CFS_OPT_THOMAS_TILE = 1,
+  CFS_OPT_X_LINES = 2,
+  CFS_OPT_Y_TILE = 3,
+  CFS_OPT_PCR_PARTS = 4,
+  CFS_OPT_HELM_FP64 = 5
+};
 int cfs_plan_set_option(cfs_plan_t plan, int option, int value);
 int cfs_plan_get_option(cfs_plan_t plan, int option, int* value);
 

@@ -95,13 +95,16 @@ struct PcrArgs {  // Algorithm 2 runtime (pcr.cu)
   const R* red;        // rl | rip | ripc             (3 * 2p)
 };
 
-struct PcrBox {  // one field of a grouped Algorithm 2 launch; maps 64-byte aligned
+template <class R>
+struct PcrBoxT {  // one field of a grouped Algorithm 2 launch; maps 64-byte aligned
   CUtensorMap in_map;
   CUtensorMap out_map;
-  PcrArgs<float> a;
+  PcrArgs<R> a;
   int* status;
   int blocks;  // blocks of this box (they stride over its tiles)
 };
+using PcrBox = PcrBoxT<float>;     // FP32 inner solves of refinement
+using PcrBox64 = PcrBoxT<double>;  // FP64 solves
 
 #ifdef __CUDACC__
 
@@ -135,6 +138,11 @@ cudaError_t launch_pcr_group32(const PcrBox* boxes, GroupMap g, int total, int t
                                size_t smem, cudaStream_t st);
 size_t pcr_group_box(const cfs_plan* P, const HelmCoef& h, PcrBox* box, int* blocks,
                      int* threads);
+// FP64 Algorithm 2 on the caller's fields (rhs -> u).
+cudaError_t launch_pcr_group64(const PcrBox64* boxes, GroupMap g, int total, int threads,
+                               size_t smem, cudaStream_t st);
+size_t pcr_group_box64(const cfs_plan* P, const HelmCoef& h, const double* rhs, double* u,
+                       PcrBox64* box, int* blocks, int* threads);
 
 // Grouped refinement kernels (refine.cu), launched by group.cu.
 cudaError_t launch_group_refine_stage(int stage, const ResBox* boxes, GroupMap g, int total,

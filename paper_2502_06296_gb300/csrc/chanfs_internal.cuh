@@ -97,6 +97,7 @@ struct cfs_plan {
   int x_lines;       // x-lines per CTA of the x transforms (0: about 16 KB of data)
   int tk_auto, tk32_auto;  // y tile widths chosen at creation
   int pcr_parts;     // partitions of Helmholtz sets prepared without a count (0: auto)
+  int helm_fp64;     // refined plans: Helmholtz by FP64 Algorithm 2 directly, no refinement
   double* d_dzf;     // cell widths (weights of the Neumann mean)
   // Neumann (0,0) column: wn = w/sum(w), gn = g/sum(w) with g = T'^{-T} w,
   // hs = sc * T'^{-1} (0,1,..,1), T' the pinned operator; 3*nz doubles
@@ -178,6 +179,15 @@ int refine_helmholtz(cfs_plan* P, const HelmCoef& h, const double* rhs, double* 
 // Device helpers (the FFT engine is in chanfs_fft.cuh)
 // ----------------------------------------------------------------------------
 #ifdef __CUDACC__
+
+// Lets `kernel` launch with up to the per-block maximum of dynamic shared
+// memory.  Always the same value: plans solved concurrently from several
+// host threads must not lower the limit under one another's launches.
+constexpr int kMaxDynSmem = 227 * 1024;
+template <class K>
+inline cudaError_t allow_max_smem(K kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));

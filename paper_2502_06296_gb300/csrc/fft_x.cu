@@ -176,11 +176,11 @@ static cudaError_t launch_x(const cfs_plan* P, const void* in, void* out, bool i
   const C* cin = reinterpret_cast<const C*>(in);
   if (!inverse) {
     auto k = rfft_x_kernel<false, C, OUT_SAME>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_smem(k);
     k<<<(unsigned)grid, 128, smem, st>>>(cin, out, nlines, P->fx, tw, post, lb, scale, scaled);
   } else {
     auto k = rfft_x_kernel<true, C, OUT>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_smem(k);
     k<<<(unsigned)grid, 128, smem, st>>>(cin, out, nlines, P->fx, tw, post, lb, scale, scaled);
   }
   return cudaGetLastError();
@@ -221,15 +221,15 @@ cudaError_t launch_rfft_x_group32(const XBox* boxes, GroupMap g, int total, size
   if (total <= 0) return cudaSuccess;
   if (!inverse) {
     auto k = rfft_x_group_kernel<false, OUT_SAME>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_smem(k);
     k<<<total, 128, smem, st>>>(boxes, g, io);
   } else if (out_mode == OUT_ADD) {
     auto k = rfft_x_group_kernel<true, OUT_ADD>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_smem(k);
     k<<<total, 128, smem, st>>>(boxes, g, io);
   } else {
     auto k = rfft_x_group_kernel<true, OUT_SET>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_smem(k);
     k<<<total, 128, smem, st>>>(boxes, g, io);
   }
   return cudaGetLastError();

@@ -111,11 +111,11 @@ static cudaError_t launch_y(const cfs_plan* P, void* data, bool inverse, int tk,
   dim3 grid((P->M + tk - 1) / tk, P->nz);
   if (!inverse) {
     auto k = fft_y_kernel<false, C>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_smem(k);
     k<<<grid, 128, smem, st>>>(map, P->fy, tw, tk, P->by, P->nbox, P->d_status);
   } else {
     auto k = fft_y_kernel<true, C>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_smem(k);
     k<<<grid, 128, smem, st>>>(map, P->fy, tw, tk, P->by, P->nbox, P->d_status);
   }
   return cudaGetLastError();
@@ -159,11 +159,11 @@ cudaError_t launch_fft_y_group32(const YBox* boxes, GroupMap g, int total, size_
   if (total <= 0) return cudaSuccess;
   if (!inverse) {
     auto k = fft_y_group_kernel<false>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_smem(k);
     k<<<total, 128, smem, st>>>(boxes, g);
   } else {
     auto k = fft_y_group_kernel<true>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_smem(k);
     k<<<total, 128, smem, st>>>(boxes, g);
   }
   return cudaGetLastError();

@@ -98,6 +98,9 @@ struct cfs_group {
   // Helmholtz: per-call Algorithm 2 and residual descriptors (c, loc vary)
   PcrBox* d_pcr = nullptr;
   PcrBox* h_pcr = nullptr;
+  PcrBox64* d_pcr64 = nullptr;  // boxes whose plans solve Helmholtz in FP64 directly
+  PcrBox64* h_pcr64 = nullptr;
+  int* d_spcr64 = nullptr;
   ResBox* d_hres = nullptr;
   ResBox* h_hres = nullptr;
   int* d_spcr = nullptr;
@@ -110,8 +113,9 @@ struct cfs_group {
 static void group_free(cfs_group* G) {
   void* ptrs[] = {G->d_tab,   G->d_active, G->d_mean, G->d_fmax, G->d_tol,  G->d_maxit,
                   G->d_iters, G->d_rho,    G->d_nactive, G->d_io, G->d_pcr, G->d_hres,
-                  G->d_spcr};
+                  G->d_spcr, G->d_pcr64, G->d_spcr64};
   for (void* p : ptrs) cudaFree(p);
+  if (G->h_pcr64) cudaFreeHost(G->h_pcr64);
   if (G->h_tab) cudaFreeHost(G->h_tab);
   if (G->h_io) cudaFreeHost(G->h_io);
   if (G->h_pcr) cudaFreeHost(G->h_pcr);
@@ -140,6 +144,9 @@ static int group_alloc(cfs_group* G, int cap) {
   if (e == cudaSuccess) e = cudaMalloc(&G->d_hres, sizeof(ResBox) * cap);
   if (e == cudaSuccess) e = cudaMallocHost(&G->h_hres, sizeof(ResBox) * cap);
   if (e == cudaSuccess) e = cudaMalloc(&G->d_spcr, sizeof(int) * (cap + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_pcr64, sizeof(PcrBox64) * cap);
+  if (e == cudaSuccess) e = cudaMallocHost(&G->h_pcr64, sizeof(PcrBox64) * cap);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_spcr64, sizeof(int) * (cap + 1));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G->io_copied, cudaEventDisableTiming);
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? CFS_ENOMEM : CFS_ECUDA;
   const GroupTables& t = G->tab;
@@ -446,21 +453,32 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
   if (e != cudaSuccess) return CFS_ECUDA;
   // Algorithm 2, Step 1 of every box (host, cached per plan), and the
   // per-call descriptors
-  std::vector<int> blocks(nb), on(nb);
+  // Boxes whose plans take FP64 Algorithm 2 directly (CFS_OPT_HELM_FP64) run
+  // in one FP64 launch; the others are refined together.
+  std::vector<int> blocks(nb, 0), blocks64(nb, 0), on(nb, 0), refined(nb, 0);
   std::vector<double> tol(nb);
   std::vector<int> maxits(nb);
-  int threads = 0;
-  size_t smem = 0;
+  int threads = 0, threads64 = 0, nref = 0;
+  size_t smem = 0, smem64 = 0;
   for (int b = 0; b < nb; ++b) {
     cfs_plan* P = G->plans[b];
     HelmCoef* h = nullptr;
     int rc = plan_helm_prepare(P, c[b], loc[b], 0, &h);
     if (rc) return rc;
     int th = 0;
-    const size_t sm = pcr_group_box(P, *h, &G->h_pcr[b], &blocks[b], &th);
-    if (!sm) return CFS_ECUDA;
-    threads = std::max(threads, th);
-    smem = std::max(smem, sm);
+    refined[b] = !P->helm_fp64;
+    nref += refined[b];
+    if (refined[b]) {
+      const size_t sm = pcr_group_box(P, *h, &G->h_pcr[b], &blocks[b], &th);
+      if (!sm) return CFS_ECUDA;
+      threads = std::max(threads, th);
+      smem = std::max(smem, sm);
+    } else {
+      const size_t sm = pcr_group_box64(P, *h, rhs[b], u[b], &G->h_pcr64[b], &blocks64[b], &th);
+      if (!sm) return CFS_ECUDA;
+      threads64 = std::max(threads64, th);
+      smem64 = std::max(smem64, sm);
+    }
     G->h_hres[b] = G->res[b];
     G->h_hres[b].abc = h->d_abc;
     G->h_hres[b].n = h->n;
@@ -468,11 +486,14 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
     tol[b] = P->tol;
     maxits[b] = P->maxit;
   }
-  int tpcr = 0;
-  std::vector<int> spcr = offsets(blocks, &tpcr);
+  int tpcr = 0, tpcr64 = 0;
+  std::vector<int> spcr = offsets(blocks, &tpcr), spcr64 = offsets(blocks64, &tpcr64);
   e = cudaMemcpyAsync(G->d_pcr, G->h_pcr, sizeof(PcrBox) * nb, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(G->d_hres, G->h_hres, sizeof(ResBox) * nb, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && tpcr64 > 0)
+    e = cudaMemcpyAsync(G->d_pcr64, G->h_pcr64, sizeof(PcrBox64) * nb, cudaMemcpyHostToDevice,
+                        st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(G->d_io, G->h_io, sizeof(GroupIo) * nb, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaEventRecord(G->io_copied, st);
@@ -480,11 +501,29 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
     e = cudaMemcpyAsync(G->d_spcr, spcr.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice,
                         st);
   if (e == cudaSuccess)
+    e = cudaMemcpyAsync(G->d_spcr64, spcr64.data(), sizeof(int) * (nb + 1),
+                        cudaMemcpyHostToDevice, st);
+  // the FP64 boxes: one launch, no refinement
+  if (e == cudaSuccess && tpcr64 > 0)
+    e = launch_pcr_group64(G->d_pcr64, GroupMap{G->d_spcr64, nullptr, nb}, tpcr64, threads64,
+                           smem64, st);
+  for (int b = 0; b < nb; ++b)
+    if (!refined[b]) {
+      G->last_iters[b] = 0;
+      G->last_rho[b] = 0.0;
+      G->plans[b]->last_iters = 0;
+      G->plans[b]->last_rho = 0.0;
+    }
+  if (nref == 0) return e == cudaSuccess ? CFS_OK : CFS_ECUDA;
+  if (e == cudaSuccess)
     e = cudaMemcpyAsync(G->d_tol, tol.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(G->d_maxit, maxits.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st);
-  // r_0 = rhs and its max-norm
-  GroupMap g{G->d_sres, nullptr, nb};
+  // r_0 = rhs and its max-norm (refined boxes)
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(G->d_active, refined.data(), sizeof(int) * nb, cudaMemcpyHostToDevice,
+                        st);
+  GroupMap g{G->d_sres, G->d_active, nb};
   if (e == cudaSuccess) e = launch_group_zero_max(G->d_hres, nb, st);
   if (e == cudaSuccess)
     e = launch_group_refine_stage(GSTAGE_HELM_RESIDUAL, G->d_hres, g, G->tres, G->d_io, 0, st);
@@ -496,6 +535,7 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
   if (e != cudaSuccess) return CFS_ECUDA;
   int nactive = 0, maxit = 0;
   for (int b = 0; b < nb; ++b) {
+    if (!refined[b]) continue;
     cfs_plan* P = G->plans[b];
     on[b] = fmax[b] != 0.0f;
     nactive += on[b];

@@ -149,11 +149,12 @@ __global__ void __launch_bounds__(1024) pcr_kernel(const __grid_constant__ CUten
 
 // One launch for several boxes (FP32 inner solves of grouped refinement): the
 // blocks of box b stride over its tiles.
-__global__ void __launch_bounds__(1024) pcr_group_kernel(const PcrBox* boxes, GroupMap g) {
+template <class R>
+__global__ void __launch_bounds__(1024) pcr_group_kernel(const PcrBoxT<R>* boxes, GroupMap g) {
   int b, blk;
   if (!group_block(g, &b, &blk)) return;
-  const PcrBox& x = boxes[b];
-  pcr_body<float>(&x.in_map, &x.out_map, x.a, x.status, blk, x.blocks);
+  const PcrBoxT<R>& x = boxes[b];
+  pcr_body<R>(&x.in_map, &x.out_map, x.a, x.status, blk, x.blocks);
 }
 
 // 2-D map over the first n rows of a field: ncols reals per row.
@@ -202,7 +203,7 @@ static cudaError_t launch_pcr_t(const cfs_plan* P, const HelmCoef& h, const R* r
   const size_t smem = pcr_smem_t<R>(h.n, h.nparts);
   const int threads = kPcrCols * h.nparts;
   auto kern = pcr_kernel<R>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  allow_max_smem(kern);
   int dev = 0, nsm = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -230,35 +231,59 @@ cudaError_t launch_pcr32(const cfs_plan* P, const HelmCoef& h, const float* rhs,
 // coefficients, few enough to spread a small box over many SMs.
 constexpr int kPcrGroupTiles = 8;
 
-size_t pcr_group_box(const cfs_plan* P, const HelmCoef& h, PcrBox* box, int* blocks,
-                     int* threads) {
-  PcrArgs<float>& a = box->a;
-  a.u = P->d_r32;
+template <class R>
+static size_t pcr_group_box_t(const cfs_plan* P, const HelmCoef& h, const R* rows, const R* red,
+                              const R* rhs, R* u, PcrBoxT<R>* box, int* blocks, int* threads) {
+  PcrArgs<R>& a = box->a;
+  a.u = u;
   a.ncols = (long long)P->nx * P->ny;
   a.n = h.n;
   a.nparts = h.nparts;
   a.face = (h.loc == CFS_LOC_FACE);
   a.nz = P->nz;
-  pcr_boxes(h.n, sizeof(float), &a.nbox, &a.by);
-  a.rows = h.d_rows32;
-  a.red = h.d_red32;
-  if (!pcr_map<float>(&box->in_map, P->d_r32, a.ncols, h.n, a.by) ||
-      !pcr_map<float>(&box->out_map, P->d_r32, a.ncols, h.n, a.by))
+  pcr_boxes(h.n, sizeof(R), &a.nbox, &a.by);
+  a.rows = rows;
+  a.red = red;
+  if (!pcr_map<R>(&box->in_map, rhs, a.ncols, h.n, a.by) ||
+      !pcr_map<R>(&box->out_map, u, a.ncols, h.n, a.by))
     return 0;
   const long long ntiles = (a.ncols + kPcrCols - 1) / kPcrCols;
   box->blocks = (int)((ntiles + kPcrGroupTiles - 1) / kPcrGroupTiles);
   box->status = P->d_status;
   *blocks = box->blocks;
   *threads = kPcrCols * h.nparts;
-  return pcr_smem_t<float>(h.n, h.nparts);
+  return pcr_smem_t<R>(h.n, h.nparts);
+}
+
+size_t pcr_group_box(const cfs_plan* P, const HelmCoef& h, PcrBox* box, int* blocks,
+                     int* threads) {
+  return pcr_group_box_t<float>(P, h, h.d_rows32, h.d_red32, P->d_r32, P->d_r32, box, blocks,
+                                threads);
+}
+
+size_t pcr_group_box64(const cfs_plan* P, const HelmCoef& h, const double* rhs, double* u,
+                       PcrBox64* box, int* blocks, int* threads) {
+  return pcr_group_box_t<double>(P, h, h.d_rows, h.d_red, rhs, u, box, blocks, threads);
+}
+
+template <class R>
+static cudaError_t launch_pcr_group_t(const PcrBoxT<R>* boxes, GroupMap g, int total,
+                                      int threads, size_t smem, cudaStream_t st) {
+  if (total <= 0) return cudaSuccess;
+  auto kern = pcr_group_kernel<R>;
+  allow_max_smem(kern);
+  kern<<<total, threads, smem, st>>>(boxes, g);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pcr_group32(const PcrBox* boxes, GroupMap g, int total, int threads,
                                size_t smem, cudaStream_t st) {
-  if (total <= 0) return cudaSuccess;
-  cudaFuncSetAttribute(pcr_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  pcr_group_kernel<<<total, threads, smem, st>>>(boxes, g);
-  return cudaGetLastError();
+  return launch_pcr_group_t<float>(boxes, g, total, threads, smem, st);
+}
+
+cudaError_t launch_pcr_group64(const PcrBox64* boxes, GroupMap g, int total, int threads,
+                               size_t smem, cudaStream_t st) {
+  return launch_pcr_group_t<double>(boxes, g, total, threads, smem, st);
 }
 
 }  // namespace chanfs
@@ -287,7 +312,7 @@ cudaError_t launch_pcr_raw(long long ncols, int nz, int n, int nparts, int loc, 
   const size_t smem = pcr_smem_t<double>(n, nparts);
   const int threads = kPcrCols * nparts;
   auto kern = pcr_kernel<double>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem(kern);
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 0, per_sm = 0;
   cudaGetDevice(&dev);

@@ -638,7 +638,7 @@ extern "C" int cfs_helmholtz_solve(cfs_plan_t P, double c, int loc, const double
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   if (P->dtype == CFS_F32_REFINED) {
-    if (rhs == u) {
+    if (rhs == u && !P->helm_fp64) {
       rc = ensure_stage(P);
       if (rc) return rc;
       if (cudaMemcpyAsync(P->d_stage, rhs, sizeof(double) * (size_t)P->nx * P->ny * P->nz,
@@ -646,7 +646,9 @@ extern "C" int cfs_helmholtz_solve(cfs_plan_t P, double c, int loc, const double
         return CFS_ECUDA;
       rhs = P->d_stage;
     }
-    return refine_helmholtz(P, *h, rhs, u, st);
+    if (!P->helm_fp64) return refine_helmholtz(P, *h, rhs, u, st);
+    P->last_iters = 0;
+    P->last_rho = 0.0;
   }
   return cuda_status(launch_pcr(P, *h, rhs, u, st));
 }
@@ -685,6 +687,10 @@ extern "C" int cfs_plan_set_option(cfs_plan_t P, int option, int value) {
       else P->tk = value ? value : P->tk_auto;
       return CFS_OK;
     }
+    case CFS_OPT_HELM_FP64:
+      if (value != 0 && value != 1) return CFS_EINVAL;
+      P->helm_fp64 = value;
+      return CFS_OK;
     case CFS_OPT_PCR_PARTS: {
       if (value < 0 || value > kPcrMaxParts) return CFS_EINVAL;
       for (int n = P->nz - 1; value > 0 && n <= P->nz; ++n)  // face and centred fields
@@ -711,6 +717,9 @@ extern "C" int cfs_plan_get_option(cfs_plan_t P, int option, int* value) {
       return CFS_OK;
     case CFS_OPT_PCR_PARTS:
       *value = P->pcr_parts ? P->pcr_parts : auto_parts(P->nz);
+      return CFS_OK;
+    case CFS_OPT_HELM_FP64:
+      *value = (P->dtype == CFS_F32_REFINED) ? P->helm_fp64 : 1;
       return CFS_OK;
     default:
       return CFS_EINVAL;

@@ -146,7 +146,15 @@ __device__ __forceinline__ void helm_residual_body(const double* __restrict__ rh
                                                    int nz, int mode, long long blk) {
   const long long col = blk * blockDim.x + threadIdx.x;
   float vmax = 0.0f;
-  if (col < ncols) {
+  if (col < ncols && mode == 0) {  // r = rhs: (I - c L_z) 0 vanishes exactly
+    for (int k = 0; k < n; ++k) {
+      const long long o = (long long)k * ncols + col;
+      const float rf = (float)rhs[o];
+      r32[o] = rf;
+      vmax = fmaxf(vmax, fabsf(rf));
+    }
+    if (n < nz) r32[(long long)(nz - 1) * ncols + col] = 0.0f;
+  } else if (col < ncols) {
     auto update = [&](int k) -> double {
       const long long o = (long long)k * ncols + col;
       if (mode == 0) return 0.0;

@@ -486,7 +486,7 @@ static int tile_occupancy(int nz) {
   const size_t smem = tile_smem<CS, TW, DG>(nz);
   if (smem > 227 * 1024) return 0;
   auto kern = thomas_tile_kernel<CS, TW, DG>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+  if (allow_max_smem(kern) !=
       cudaSuccess)
     return 0;
   int per_sm = 0;

@@ -21,7 +21,7 @@ using namespace chanfs;
 namespace {
 
 struct Choice {
-  int x_lines, y_tile, thomas, pcr_parts;
+  int x_lines, y_tile, thomas, pcr_parts, helm_fp64;
 };
 
 std::mutex g_mu;
@@ -66,6 +66,7 @@ static void apply(cfs_plan* P, const Choice& c) {
   else P->tk = c.y_tile;
   P->thomas_tw = c.thomas;
   P->pcr_parts = c.pcr_parts;
+  P->helm_fp64 = c.helm_fp64;
 }
 
 extern "C" int cfs_plan_autotune(cfs_plan_t P, void* stream) {
@@ -173,6 +174,26 @@ extern "C" int cfs_plan_autotune(cfs_plan_t P, void* stream) {
         best.pcr_parts = cand;
       }
     }
+    plan_helm_forget(P, kProbeC);
+  }
+  // Refined plans: refined Helmholtz against FP64 Algorithm 2 directly (both
+  // meet the refinement target), on a constant right-hand side
+  best.helm_fp64 = 0;
+  if (fp32 && P->nz <= kPcrMaxUnknowns) {
+    double* u = nullptr;
+    HelmCoef* h = nullptr;
+    if (cudaMalloc(&u, sizeof(double) * npts) == cudaSuccess &&
+        cudaMemsetAsync(s64, 0x3f, sizeof(double) * npts, st) == cudaSuccess &&
+        plan_helm_prepare(P, kProbeC, CFS_LOC_CENTER, best.pcr_parts, &h) == CFS_OK) {
+      const HelmCoef hc = *h;
+      const float t32 = best_ms(st, [&]() {
+        return refine_helmholtz(P, hc, s64, u, st) == CFS_OK ? cudaSuccess : cudaErrorUnknown;
+      });
+      const float t64 = best_ms(st, [&]() { return launch_pcr(P, hc, s64, u, st); });
+      best.helm_fp64 = t64 < t32;
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(u);
     plan_helm_forget(P, kProbeC);
   }
   if (cudaStreamSynchronize(st) != cudaSuccess) return CFS_ECUDA;

@@ -94,6 +94,58 @@ PRECISION = dict(name="poisson_uniform_1024x768x512", nx=1024, ny=768, nz=512, l
 CHANNEL_C = 0.5 * (1.0 / 5200.0) * 1e-4
 
 
+# Batched ensemble: 48 boxes drawn from a seed (sizes from the menus below,
+# tanh stretching in [1.2, 2.2], Helmholtz alpha nu dt log-uniform in [1e-6, 1e-4]).
+ENSEMBLE = dict(name="ensemble_48_boxes", nbox=48, nx=(128, 192, 256, 384), ny=(96, 128, 192),
+                nz=(64, 96, 128, 192), beta=(1.2, 2.2), c=(1e-6, 1e-4), seed=2502064,
+                lx=12.8, ly=6.4)
+# Serving stream: 20,000 requests, Poisson arrivals at 2,000 per second from 32
+# runs with sizes drawn per axis from the menu, 1:3 Poisson:Helmholtz.
+SERVING = dict(name="serving_20000_requests", nreq=20000, rate=2000.0, nruns=32,
+               sizes=(64, 96, 128, 192, 256, 384, 512), beta=(1.2, 2.2), c=(1e-6, 1e-4),
+               poisson_share=0.25, budget_gb=120, seed=2502065, lx=12.8, ly=6.4)
+
+
+def _draw(seed: int, n: int, offset: int) -> np.ndarray:
+    return uniform01(seed, n, offset)
+
+
+def ensemble_boxes(cfg=ENSEMBLE):
+    """[(nx, ny, nz, beta, c)] of the ensemble, from the counter stream."""
+    nb = cfg["nbox"]
+    u = _draw(cfg["seed"], 5 * nb, 0).reshape(nb, 5)
+    out = []
+    for b in range(nb):
+        pick = lambda menu, x: menu[min(int(x * len(menu)), len(menu) - 1)]
+        lo, hi = cfg["beta"]
+        clo, chi = cfg["c"]
+        out.append((pick(cfg["nx"], u[b, 0]), pick(cfg["ny"], u[b, 1]), pick(cfg["nz"], u[b, 2]),
+                    lo + (hi - lo) * u[b, 3], clo * (chi / clo) ** u[b, 4]))
+    return out
+
+
+def serving_stream(cfg=SERVING):
+    """Runs [(nx, ny, nz, beta, (c0, c1, c2))] and requests
+    [(arrival_s, run, kind 0 Poisson / 1 Helmholtz, which c, loc)]."""
+    nr, nq = cfg["nruns"], cfg["nreq"]
+    u = _draw(cfg["seed"], 7 * nr, 0).reshape(nr, 7)
+    menu = cfg["sizes"]
+    pick = lambda x: menu[min(int(x * len(menu)), len(menu) - 1)]
+    lo, hi = cfg["beta"]
+    clo, chi = cfg["c"]
+    runs = [(pick(u[r, 0]), pick(u[r, 1]), pick(u[r, 2]), lo + (hi - lo) * u[r, 3],
+             tuple(clo * (chi / clo) ** u[r, 4 + k] for k in range(3))) for r in range(nr)]
+    v = _draw(cfg["seed"], 5 * nq, 7 * nr).reshape(nq, 5)
+    gaps = -np.log1p(-v[:, 0]) / cfg["rate"]  # exponential inter-arrival times
+    t = np.cumsum(gaps)
+    reqs = []
+    for i in range(nq):
+        kind = 0 if v[i, 2] < cfg["poisson_share"] else 1
+        reqs.append((float(t[i]), min(int(v[i, 1] * nr), nr - 1), kind,
+                     min(int(v[i, 3] * 3), 2), 0 if v[i, 4] < 2.0 / 3.0 else 1))
+    return runs, reqs
+
+
 def grid_dz(cfg) -> np.ndarray:
     return uniform_dz(cfg["nz"]) if cfg["beta"] is None else tanh_dz(cfg["nz"], cfg["beta"])
 

@@ -179,3 +179,27 @@ def test_group_ignores_stale_reduction_words(chanfs):
     assert np.array_equal(got, alone)
     assert np.array_equal(gh, host(plan.helmholtz_solve(1e-5, x)))
     plan.close()
+
+
+def test_group_helmholtz_with_fp64_direct_boxes(chanfs):
+    """Boxes whose plans solve Helmholtz in FP64 directly (CFS_OPT_HELM_FP64)
+    run in their own launch of the same group call, bit-identical to their
+    single solves, and within 1e-12 of the oracle."""
+    boxes = [make_box(chanfs, i, s) for i, s in enumerate(BOXES[:4])]
+    plans = [b[0] for b in boxes]
+    for p in plans[::2]:
+        p.set_option(chanfs.OPT_HELM_FP64, 1)
+    cs = [1e-5, 2e-5, 3e-5, 4e-5]
+    locs = [chanfs.CENTER, chanfs.FACE, chanfs.FACE, chanfs.CENTER]
+    rhs = [synth.normal(800 + i, b[1].shape) for i, b in enumerate(boxes)]
+    rd = [dev(r) for r in rhs]
+    alone = [host(p.helmholtz_solve(c, r, loc)) for p, c, r, loc in zip(plans, cs, rd, locs)]
+    with chanfs.Group(plans) as g:
+        got = [host(o) for o in g.helmholtz_solve(cs, rd, locs)]
+        info = g.last_info()
+    for i, (plan, f, dz) in enumerate(boxes):
+        assert np.array_equal(got[i], alone[i]), i
+        ref = oracle.helmholtz_solve(rhs[i], dz, cs[i], locs[i])
+        assert rel(got[i], ref) < (1e-12 if i % 2 == 0 else TOL), (i, rel(got[i], ref))
+        assert (info[i][0] == 0) == (i % 2 == 0), info[i]
+        plan.close()
