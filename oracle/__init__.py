@@ -75,6 +75,8 @@ def _load():
             "or_apply_helmholtz": [i, i, i, dp, d, i, dp, dp],
             "or_poisson_solve": [i, i, i, d, d, dp, i, dp, dp],
             "or_helmholtz_solve": [i, i, i, dp, d, i, i, i, dp, dp],
+            "or_apply_helmholtz3d": [i, i, i, d, d, dp, d, i, dp, dp],
+            "or_helmholtz3d_solve": [i, i, i, d, d, dp, d, i, dp, dp],
             "or_spectral_forward": [i, i, i, dp, dp],
             "or_spectral_inverse": [i, i, i, dp, dp],
             "or_dense_solve": [i, dp, dp],
@@ -257,6 +259,26 @@ def helmholtz_solve(rhs, dzf, c: float, loc: int, method: int = THOMAS, nparts: 
     out = np.empty_like(rhs)
     _check(_load().or_helmholtz_solve(nx, ny, nz, _p(dzf), c, loc, method, nparts, _p(rhs), _p(out)),
            "helmholtz")
+    return out
+
+
+def apply_helmholtz3d(u, lx: float, ly: float, dzf, c: float, loc: int) -> np.ndarray:
+    """(I - c L) u, the full 3-D operator of Eq. 8 with Dirichlet z walls."""
+    u, dzf = _f64(u), _f64(dzf)
+    nx, ny, nz = _shape(u)
+    out = np.empty_like(u)
+    _check(_load().or_apply_helmholtz3d(nx, ny, nz, lx, ly, _p(dzf), c, loc, _p(u), _p(out)),
+           "apply_helmholtz3d")
+    return out
+
+
+def helmholtz3d_solve(rhs, lx: float, ly: float, dzf, c: float, loc: int) -> np.ndarray:
+    """u with (I - c L) u = rhs (Eq. 8) by eigenfunction expansion."""
+    rhs, dzf = _f64(rhs), _f64(dzf)
+    nx, ny, nz = _shape(rhs)
+    out = np.empty_like(rhs)
+    _check(_load().or_helmholtz3d_solve(nx, ny, nz, lx, ly, _p(dzf), c, loc, _p(rhs), _p(out)),
+           "helmholtz3d")
     return out
 
 

@@ -705,6 +705,96 @@ int or_helmholtz_solve(int nx, int ny, int nz, const double* dzf, double c,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Fully implicit 3-D Helmholtz (Eq. 8): (I - c L) u = rhs with L the full    */
+/* staggered Laplacian, periodic in x and y, homogeneous Dirichlet z walls   */
+/* (cell-centred u, v or face-located w as in the z-implicit solve).         */
+/* Apply: the stencil written out point by point (face fields: the wall slot */
+/* Nz-1 is passed through unchanged).                                        */
+/* ------------------------------------------------------------------------ */
+
+int or_apply_helmholtz3d(int nx, int ny, int nz, double lx, double ly,
+                         const double* dzf, double c, int loc, const double* u,
+                         double* out) {
+  if (nx < 1 || ny < 1 || nz < 3 || !(lx > 0) || !(ly > 0)) return -1;
+  if (loc != LOC_CENTER && loc != LOC_FACE) return -1;
+  double dx = lx / nx, dy = ly / ny;
+  double* dzc = (double*)malloc(sizeof(double) * (size_t)nz);
+  or_dzc(nz, dzf, dzc);
+  size_t sxy = (size_t)nx * ny;
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        size_t i = (size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z);
+        if (loc == LOC_FACE && z == nz - 1) {
+          out[i] = u[i];
+          continue;
+        }
+        int xp = (x + 1) % nx, xm = (x + nx - 1) % nx;
+        int yp = (y + 1) % ny, ym = (y + ny - 1) % ny;
+        size_t row = (size_t)nx * ((size_t)y + (size_t)ny * z);
+        size_t pl = (size_t)nx * ((size_t)ny * z);
+        double lxx = (u[row + xp] - 2.0 * u[i] + u[row + xm]) / (dx * dx);
+        double lyy = (u[pl + (size_t)nx * yp + x] - 2.0 * u[i] + u[pl + (size_t)nx * ym + x]) / (dy * dy);
+        const double* colp = u + (size_t)x + (size_t)nx * y;
+        double lzz = (loc == LOC_CENTER) ? lz_centre(nz, dzf, dzc, BC_DIRICHLET, colp, sxy, z)
+                                         : lz_face(nz, dzf, dzc, colp, sxy, z);
+        out[i] = u[i] - c * (lxx + lyy + lzz);
+      }
+  free(dzc);
+  return 0;
+}
+
+/* Solve by eigenfunction expansion, as the Poisson solve: DFT along x and y,  */
+/* per (kx,ky) the tridiagonal system with A' = -c A_k,                        */
+/* B' = 1 - c (B_k + lx[kx] + ly[ky]), C' = -c C_k (Dirichlet rows of the      */
+/* field's location; nonsingular for c >= 0), inverse DFTs with 1/(Nx Ny).     */
+int or_helmholtz3d_solve(int nx, int ny, int nz, double lx, double ly,
+                         const double* dzf, double c, int loc, const double* rhs,
+                         double* u) {
+  if (nx < 1 || ny < 1 || nz < 3 || !(lx > 0) || !(ly > 0) || !(c >= 0)) return -1;
+  if (loc != LOC_CENTER && loc != LOC_FACE) return -1;
+  size_t n3 = (size_t)nx * ny * nz, sxy = (size_t)nx * ny;
+  cplx* F = (cplx*)malloc(sizeof(cplx) * n3);
+  for (size_t i = 0; i < n3; ++i) F[i] = rhs[i];
+  int dims[3] = {nx, ny, nz};
+  fft_axis(F, dims, 0, -1);
+  fft_axis(F, dims, 1, -1);
+  double* lamx = (double*)malloc(sizeof(double) * (size_t)nx);
+  double* lamy = (double*)malloc(sizeof(double) * (size_t)ny);
+  or_eig_periodic(nx, lx / nx, lamx);
+  or_eig_periodic(ny, ly / ny, lamy);
+  double* A = (double*)malloc(sizeof(double) * (size_t)nz);
+  double* B = (double*)malloc(sizeof(double) * (size_t)nz);
+  double* C = (double*)malloc(sizeof(double) * (size_t)nz);
+  double* a = (double*)malloc(sizeof(double) * (size_t)nz);
+  double* b = (double*)malloc(sizeof(double) * (size_t)nz);
+  double* cc = (double*)malloc(sizeof(double) * (size_t)nz);
+  cplx* d = (cplx*)malloc(sizeof(cplx) * (size_t)nz);
+  cplx* x = (cplx*)malloc(sizeof(cplx) * (size_t)nz);
+  int n = or_lz_coefficients(nz, dzf, BC_DIRICHLET, loc, A, B, C);
+  for (int ky = 0; ky < ny; ++ky)
+    for (int kx = 0; kx < nx; ++kx) {
+      double lam = lamx[kx] + lamy[ky];
+      for (int k = 0; k < n; ++k) {
+        a[k] = -c * A[k];
+        b[k] = 1.0 - c * (B[k] + lam);
+        cc[k] = -c * C[k];
+        d[k] = F[(size_t)kx + (size_t)nx * ky + sxy * (size_t)k];
+      }
+      thomas_complex(n, a, b, cc, d, x);
+      for (int k = 0; k < n; ++k) F[(size_t)kx + (size_t)nx * ky + sxy * (size_t)k] = x[k];
+      for (int k = n; k < nz; ++k) F[(size_t)kx + (size_t)nx * ky + sxy * (size_t)k] = 0.0;
+    }
+  fft_axis(F, dims, 1, 1);
+  fft_axis(F, dims, 0, 1);
+  double scale = 1.0 / ((double)nx * (double)ny);
+  for (size_t i = 0; i < n3; ++i) u[i] = creal(F[i]) * scale;
+  free(x); free(d); free(cc); free(b); free(a); free(C); free(B); free(A);
+  free(lamy); free(lamx); free(F);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Spectral layout of the solver: App. A packing along x (even Nx: pair j of */
 /* a line is X_j for j >= 1 and X_0 + i X_{Nx/2} for j = 0), complex DFT     */
 /* along y of each pair, and for pair j = 0 the same packing idea once more  */

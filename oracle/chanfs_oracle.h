@@ -73,6 +73,13 @@ int or_poisson_solve(int nx, int ny, int nz, double lx, double ly,
 int or_helmholtz_solve(int nx, int ny, int nz, const double* dzf, double c,
                        int loc, int method, int nparts, const double* rhs,
                        double* u);
+/* Fully implicit 3-D Helmholtz (Eq. 8), Dirichlet z walls: apply and solve. */
+int or_apply_helmholtz3d(int nx, int ny, int nz, double lx, double ly,
+                         const double* dzf, double c, int loc, const double* u,
+                         double* out);
+int or_helmholtz3d_solve(int nx, int ny, int nz, double lx, double ly,
+                         const double* dzf, double c, int loc, const double* rhs,
+                         double* u);
 
 /* Spectral layout used by the solver: App. A packing along x, complex DFT
  * along y (pair j of a packed x-line read as one complex number), and pair 0
