@@ -299,6 +299,40 @@ def run_mixed(chanfs, torch, device, reps: int = 5, warmup: int = 3):
 
 
 # ----------------------------------------------------------------------------
+# Fully implicit 3-D Helmholtz (Eq. 8) on the channel workload
+# ----------------------------------------------------------------------------
+
+def run_helmholtz3d(chanfs, torch, device, plan, rhs, outs, reps: int = 5):
+    """u, v (centred) and w (face) fully implicit solves with the channel's
+    alpha nu dt, FP64, on the channel plan; median over reps of the three."""
+    c = synth.CHANNEL_C
+    locs = (chanfs.CENTER, chanfs.CENTER, chanfs.FACE)
+    for loc in (chanfs.CENTER, chanfs.FACE):
+        plan.helmholtz3d_prepare(c, loc)
+
+    def three():
+        for r, o, loc in zip(rhs, outs, locs):
+            plan.helmholtz3d_solve(c, r, loc, out=o)
+
+    three()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        three()
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    npts = rhs[0].numel()
+    t = statistics.median(ms)
+    return {"workload": CFG["name"], "solves": "u, v centred + w face, Dirichlet, c = alpha nu dt",
+            "ms_three_solves": round(t, 4), "ns_per_pt_per_solve": t * 1e6 / (3 * npts),
+            "launches_per_solve": 5, "precision": "f64"}
+
+
+# ----------------------------------------------------------------------------
 # Batched ensemble: 48 boxes, grouped FP32 + FP64-refined solves vs per box
 # ----------------------------------------------------------------------------
 
@@ -674,6 +708,7 @@ def run_ours(args):
         "clocks": clock,
         "device_status": status,
     }
+    line["helmholtz3d"] = run_helmholtz3d(chanfs, torch, device, plan, rhs, us)
     plan.close()
     del f, rhs, p, us, ref_bits
     if not args.no_mixed:

@@ -220,6 +220,22 @@ int cfs_plan_set_refinement(cfs_plan_t plan, double tol, int maxit);
 int cfs_last_info(cfs_plan_t plan, int* iters, double* rel_residual);
 
 /*
+ * cfs_helmholtz3d_solve -- the fully implicit Helmholtz solve of Eq. 8,
+ * (I - c L) u = rhs with L the whole staggered Laplacian (periodic x, y;
+ * homogeneous Dirichlet z walls, cell-centred or face-located field as in
+ * cfs_helmholtz_solve).  It runs on the Poisson machinery: packed x FFT, y
+ * FFT, one tridiagonal system per (kx, ky) with the diagonal
+ * 1 - c (B_k + lx + ly) and off-diagonals -c A_k, -c C_k, inverse transforms.
+ * The factors of every (kx, ky) system are computed on the GPU once per
+ * (c, loc) and cached (at most 4 sets, each as large as the Poisson factors);
+ * cfs_helmholtz3d_prepare computes a set ahead of time.  FP64 on every plan;
+ * c >= 0; rhs == u allowed; for a face field slot Nz-1 of u is written 0.
+ */
+int cfs_helmholtz3d_prepare(cfs_plan_t plan, double c, int loc);
+int cfs_helmholtz3d_solve(cfs_plan_t plan, double c, int loc, const double* rhs, double* u,
+                          void* stream);
+
+/*
  * Grouped solves.  The paper has no counterpart (it spreads one box over many
  * GPUs; a group puts many independent boxes on one).  A group is built from
  * up to 4096 CFS_F32_REFINED plans of the current device, of any sizes, z

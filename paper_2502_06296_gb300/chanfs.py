@@ -80,6 +80,8 @@ def lib():
             "cfs_group_last_info": ([vp, ctypes.POINTER(i), ctypes.POINTER(d)], i),
             "cfs_group_helmholtz_solve": ([vp, dp, ctypes.POINTER(i), ctypes.POINTER(vp),
                                            ctypes.POINTER(vp), vp], i),
+            "cfs_helmholtz3d_prepare": ([vp, d, i], i),
+            "cfs_helmholtz3d_solve": ([vp, d, i, vp, vp, vp], i),
             "cfs_plan_set_option": ([vp, i, i], i),
             "cfs_group_reserve": ([ctypes.POINTER(vp), i], i),
             "cfs_group_rebind": ([vp, i, ctypes.POINTER(vp), vp], i),
@@ -195,6 +197,17 @@ class Plan:
         _check(lib().cfs_helmholtz_solve(self._h, float(c), loc, self._field(rhs, "rhs"),
                                          self._field(out, "out"), _stream_ptr(stream)),
                "cfs_helmholtz_solve")
+        return out
+
+    def helmholtz3d_prepare(self, c: float, loc: int = CENTER):
+        _check(lib().cfs_helmholtz3d_prepare(self._h, float(c), loc), "cfs_helmholtz3d_prepare")
+
+    def helmholtz3d_solve(self, c: float, rhs, loc: int = CENTER, out=None, stream=None):
+        """(I - c L) u = rhs, the fully implicit Helmholtz solve (Eq. 8)."""
+        out = self._out(rhs, out)
+        _check(lib().cfs_helmholtz3d_solve(self._h, float(c), loc, self._field(rhs, "rhs"),
+                                           self._field(out, "out"), _stream_ptr(stream)),
+               "cfs_helmholtz3d_solve")
         return out
 
     def spectral_forward(self, f, out=None, stream=None):

@@ -69,6 +69,18 @@ struct HelmCoef {
   unsigned long long stamp;
 };
 
+// LU factors of the fully implicit Helmholtz systems of Eq. 8 for one
+// (c, loc): per (kx, ky pair, k) the same layout as the Poisson factors, over
+// the n = nz (centred) or nz - 1 (face) Dirichlet rows.
+struct Helm3Coef {
+  double c;
+  int loc;
+  int n;
+  double2* d_fwd;
+  double* d_bwd;
+  unsigned long long stamp;
+};
+
 }  // namespace chanfs
 
 // ----------------------------------------------------------------------------
@@ -121,6 +133,8 @@ struct cfs_plan {
   double last_rho;
   // Helmholtz cache
   std::vector<chanfs::HelmCoef> helm;
+  std::vector<chanfs::Helm3Coef> helm3;  // fully implicit 3-D sets (LRU, small)
+  std::vector<double> lamx_h, lamy_h;     // eigenvalues per kx in [0, M], ky pair
   unsigned long long helm_clock;
   // host-buffer staging
   double* d_stage;
@@ -152,6 +166,14 @@ bool y_tile_ok(const cfs_plan* P, int tk, bool fp32);
 // Thomas tile width the plan's solves use (8, 16, or -1 for the streaming
 // kernel), for the FP64 or the FP32 spectrum; 0 if `tw` cannot run.
 int thomas_tile_width(const cfs_plan* P, bool fp32, int tw);
+// Factors of n-row systems with diagonal B_k + lx[kx] + ly[kyp] (no pinned
+// column) into fwd/bwd; s = 2 / (Nx Ny) folded in as for the Poisson set.
+cudaError_t launch_thomas_factor_set(const cfs_plan* P, double2* fwd, double* bwd, int n,
+                                     const double* dA, const double* dB, const double* dC,
+                                     const double* dlx, const double* dly, cudaStream_t st);
+// The FP64 z sweeps with another factor set over n rows (no pinned column).
+cudaError_t launch_thomas_set(const cfs_plan* P, double* data, const double2* fwd,
+                              const double* bwd, int n, cudaStream_t st);
 cudaError_t launch_thomas_factor(cfs_plan* P, const double* dA, const double* dB,
                                  const double* dC, const double* dlamx, const double* dlamy,
                                  cudaStream_t st);

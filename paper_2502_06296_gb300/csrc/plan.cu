@@ -178,6 +178,10 @@ static void plan_free(cfs_plan* P) {
     cudaFree(h.d_red32);
     cudaFree(h.d_abc);
   }
+  for (auto& h : P->helm3) {
+    cudaFree(h.d_fwd);
+    cudaFree(h.d_bwd);
+  }
   delete P;
 }
 
@@ -259,6 +263,8 @@ extern "C" int cfs_plan_create(cfs_plan_t* out, int nx, int ny, int nz, double l
   std::vector<double> lamx(P->M + 1), lamy(P->nky);
   for (int k = 0; k <= P->M; ++k) lamx[k] = 2.0 * (cos(kTwoPi * k / nx) - 1.0) / (dx * dx);
   for (int k = 0; k < P->nky; ++k) lamy[k] = 2.0 * (cos(kTwoPi * k / ny) - 1.0) / (dy * dy);
+  P->lamx_h = lamx;
+  P->lamy_h = lamy;
   std::vector<double> A, B, C;
   z_stencil(P->dzf, poisson_bc, CFS_LOC_CENTER, A, B, C);
 
@@ -622,6 +628,100 @@ void chanfs::plan_helm_forget(cfs_plan* P, double c) {
       ++i;
     }
   }
+}
+
+// ----------------------------------------------------------------------------
+// Fully implicit 3-D Helmholtz (Eq. 8): (I - c L) u = rhs on the Poisson
+// machinery.  After the x and y transforms each (kx, ky) column solves
+//   -c A_k U_{k-1} + (1 - c (B_k + lx + ly)) U_k - c C_k U_{k+1} = F_k
+// on the Dirichlet rows of the field's location (n = nz centred, nz - 1
+// face); the factors of every column are computed once per (c, loc) on the
+// GPU and kept in a small LRU cache.
+// ----------------------------------------------------------------------------
+static int helm3_prepare(cfs_plan* P, double c, int loc, Helm3Coef** res) {
+  if (!(c >= 0) || !isfinite(c)) return CFS_EINVAL;
+  if (loc != CFS_LOC_CENTER && loc != CFS_LOC_FACE) return CFS_EINVAL;
+  for (auto& h : P->helm3)
+    if (h.c == c && h.loc == loc) {
+      h.stamp = ++P->helm_clock;
+      *res = &h;
+      return CFS_OK;
+    }
+  std::vector<double> A, B, C;
+  const int n = z_stencil(P->dzf, CFS_BC_DIRICHLET, loc, A, B, C);
+  for (int i = 0; i < n; ++i) {  // -c A, 1 - c B, -c C; the x-y shift enters as -c lambda
+    A[i] = -c * A[i];
+    B[i] = 1.0 - c * B[i];
+    C[i] = -c * C[i];
+  }
+  std::vector<double> lx(P->lamx_h), ly(P->lamy_h);
+  for (double& v : lx) v *= -c;
+  for (double& v : ly) v *= -c;
+  Helm3Coef h;
+  memset(&h, 0, sizeof(h));
+  h.c = c;
+  h.loc = loc;
+  h.n = n;
+  const size_t nfac = (size_t)(P->M + 1) * P->nky * n;
+  double *dA = nullptr, *dB = nullptr, *dC = nullptr, *dlx = nullptr, *dly = nullptr;
+  size_t scratch = 0;
+  int rc = dev_upload<double2>(&h.d_fwd, nullptr, nfac, &P->device_bytes);
+  if (!rc) rc = dev_upload<double>(&h.d_bwd, nullptr, nfac, &P->device_bytes);
+  if (!rc) rc = dev_upload(&dA, A.data(), (size_t)n, &scratch);
+  if (!rc) rc = dev_upload(&dB, B.data(), (size_t)n, &scratch);
+  if (!rc) rc = dev_upload(&dC, C.data(), (size_t)n, &scratch);
+  if (!rc) rc = dev_upload(&dlx, lx.data(), lx.size(), &scratch);
+  if (!rc) rc = dev_upload(&dly, ly.data(), ly.size(), &scratch);
+  if (!rc) rc = cuda_status(launch_thomas_factor_set(P, h.d_fwd, h.d_bwd, n, dA, dB, dC, dlx, dly, 0));
+  if (!rc) rc = cuda_status(cudaDeviceSynchronize());
+  cudaFree(dA);
+  cudaFree(dB);
+  cudaFree(dC);
+  cudaFree(dlx);
+  cudaFree(dly);
+  if (rc) {
+    cudaFree(h.d_fwd);
+    cudaFree(h.d_bwd);
+    return rc;
+  }
+  const size_t kMaxEntries = 4;  // each set is as large as the Poisson factors
+  if (P->helm3.size() >= kMaxEntries) {
+    auto it = std::min_element(P->helm3.begin(), P->helm3.end(),
+                               [](const Helm3Coef& x, const Helm3Coef& y) { return x.stamp < y.stamp; });
+    cudaDeviceSynchronize();
+    cudaFree(it->d_fwd);
+    cudaFree(it->d_bwd);
+    P->device_bytes -= (sizeof(double2) + sizeof(double)) * (size_t)(P->M + 1) * P->nky * it->n;
+    P->helm3.erase(it);
+  }
+  h.stamp = ++P->helm_clock;
+  P->helm3.push_back(h);
+  *res = &P->helm3.back();
+  return CFS_OK;
+}
+
+extern "C" int cfs_helmholtz3d_prepare(cfs_plan_t P, double c, int loc) {
+  if (!P) return CFS_EINVAL;
+  Helm3Coef* h = nullptr;
+  return helm3_prepare(P, c, loc, &h);
+}
+
+extern "C" int cfs_helmholtz3d_solve(cfs_plan_t P, double c, int loc, const double* rhs,
+                                     double* u, void* stream) {
+  if (!P || !rhs || !u || !aligned16(rhs) || !aligned16(u)) return CFS_EINVAL;
+  Helm3Coef* h = nullptr;
+  int rc = helm3_prepare(P, c, loc, &h);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = launch_rfft_x(P, rhs, u, false, 1.0, st);
+  if (e == cudaSuccess) e = launch_fft_y(P, u, false, st);
+  if (e == cudaSuccess) e = launch_thomas_set(P, u, h->d_fwd, h->d_bwd, h->n, st);
+  const size_t plane = (size_t)P->nx * P->ny;
+  if (e == cudaSuccess && h->n < P->nz)  // the wall slot of a face field
+    e = cudaMemsetAsync(u + plane * (P->nz - 1), 0, sizeof(double) * plane, st);
+  if (e == cudaSuccess) e = launch_fft_y(P, u, true, st);
+  if (e == cudaSuccess) e = launch_rfft_x(P, u, u, true, 1.0, st);
+  return cuda_status(e);
 }
 
 extern "C" int cfs_helmholtz_prepare(cfs_plan_t P, double c, int loc, int nparts) {

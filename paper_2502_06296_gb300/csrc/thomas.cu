@@ -600,6 +600,30 @@ __global__ void thomas_factor_kernel(double2* fwd, double* bwd, float2* fwd32, f
   }
 }
 
+cudaError_t launch_thomas_factor_set(const cfs_plan* P, double2* fwd, double* bwd, int n,
+                                     const double* dA, const double* dB, const double* dC,
+                                     const double* dlx, const double* dly, cudaStream_t st) {
+  const double s = 2.0 / ((double)P->nx * (double)P->ny);
+  dim3 grid((P->M + 1 + 127) / 128, P->nky);
+  thomas_factor_kernel<<<grid, 128, 0, st>>>(fwd, bwd, nullptr, nullptr, dA, dB, dC, dlx, dly,
+                                             P->M, P->nky, n, s, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_thomas_set(const cfs_plan* P, double* data, const double2* fwd,
+                              const double* bwd, int n, cudaStream_t st) {
+  ThomasArgs a = thomas_args(P, data);
+  a.fwd = fwd;
+  a.bwd = bwd;
+  a.fwd32 = nullptr;
+  a.bwd32 = nullptr;
+  a.nz = n;
+  a.neumann = 0;
+  a.kx64 = a.ky64 = 0;
+  thomas_kernel<double2><<<a.nblk_x * P->ny, kThomasBlock, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_thomas_factor(cfs_plan* P, const double* dA, const double* dB, const double* dC,
                                  const double* dlamx, const double* dlamy, cudaStream_t st) {
   const double s = 2.0 / ((double)P->nx * (double)P->ny);

@@ -375,3 +375,35 @@ def test_options_and_autotune_keep_results(chanfs, dtype):
     # a second plan of the same size takes the remembered choice
     with chanfs.Plan(nx, ny, nz, 2.0, 1.0, dz, 0, dtype) as plan2:
         assert plan2.autotune() == chosen
+
+
+# Fully implicit 3-D Helmholtz (Eq. 8) on the Poisson machinery
+HELM3_CASES = [
+    ((32, 24, 20), 1.8, 0, 1e-3), ((32, 24, 20), 1.8, 1, 1e-3), ((48, 36, 33), 2.0, 0, 0.5),
+    ((6, 9, 5), 1.2, 1, 1e-2), ((64, 288, 12), 1.5, 0, 1e-4), ((8, 1, 16), None, 1, 3.0),
+    ((16, 12, 10), 1.4, 0, 0.0),
+]
+
+
+@pytest.mark.parametrize("dims,beta,loc,c", HELM3_CASES)
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_helmholtz3d_matches_oracle(chanfs, dims, beta, loc, c, dtype):
+    nx, ny, nz = dims
+    if dtype == 1 and nx % 4:
+        pytest.skip("refined plans need nx % 4 == 0")
+    lx, ly = 2 * np.pi, np.pi
+    dz = make_dz(nz, beta)
+    f = synth.normal(13 * nx + ny + nz + loc, (nz, ny, nx))
+    ref = oracle.helmholtz3d_solve(f, lx, ly, dz, c, loc)
+    with chanfs.Plan(nx, ny, nz, lx, ly, dz, 0, dtype) as plan:
+        u = host(plan.helmholtz3d_solve(c, dev(f), loc))
+        assert rel(u, ref) < TOL, rel(u, ref)
+        if loc == 1:
+            assert np.all(u[-1] == 0.0)
+        t = dev(f)
+        plan.helmholtz3d_solve(c, t, loc, out=t)
+        assert np.array_equal(host(t), u)
+        # a second coefficient, then the first again (cached set)
+        plan.helmholtz3d_solve(2 * c + 1e-3, dev(f), loc)
+        assert np.array_equal(host(plan.helmholtz3d_solve(c, dev(f), loc)), u)
+        assert plan.check() == 0
