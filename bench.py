@@ -254,12 +254,14 @@ def run_reference(args):
 # FP32 solves + FP64 refinement against the FP64 solve (1024 x 768 x 512)
 # ----------------------------------------------------------------------------
 
-def run_mixed(chanfs, torch, device, reps: int = 5, warmup: int = 3):
+def run_mixed(chanfs, torch, device, reps: int = 5, warmup: int = 3, nz: int = 0):
     """Poisson solve of the 1024 x 768 x 512 uniform workload by an FP64 plan
     and by a CFS_F32_REFINED plan (tolerance 1e-10, at most 4 FP32 solves),
     each timed by CUDA events over `reps` solves after `warmup`; the refined
     result is compared with the FP64 one.  Fields are 3.2 GB (larger than L2)."""
-    cfg = synth.PRECISION
+    cfg = dict(synth.PRECISION)
+    if nz:  # reduced wall-normal size (profiling captures only)
+        cfg.update(nz=nz, name=f"poisson_uniform_{cfg['nx']}x{cfg['ny']}x{nz}")
     nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
     npts = nx * ny * nz
     dz = synth.grid_dz(cfg)
@@ -536,7 +538,8 @@ def run_mixed_only(args):
     from paper_2502_06296_gb300 import build as libbuild
     libbuild.build()
     from paper_2502_06296_gb300 import chanfs
-    mixed = run_mixed(chanfs, torch, torch.device("cuda", 0), reps=args.steps, warmup=args.warmup)
+    mixed = run_mixed(chanfs, torch, torch.device("cuda", 0), reps=args.steps, warmup=args.warmup,
+                      nz=args.mixed_nz)
     print(json.dumps({"mixed": mixed}), flush=True)
     return 0
 
@@ -580,6 +583,7 @@ def run_ours(args):
     c = synth.CHANNEL_C
     f_h, rhs_h = synth.channel_fields(cfg)
     plan = chanfs.Plan(nx, ny, nz, CFG["lx"], CFG["ly"], dz, chanfs.NEUMANN)
+    tuned = plan.autotune() if not args.nparts else None  # kernel shapes by measurement
     for loc in (chanfs.CENTER, chanfs.FACE):
         plan.helmholtz_prepare(c, loc, args.nparts)
     f = torch.from_numpy(f_h).to(device)
@@ -696,8 +700,10 @@ def run_ours(args):
         "config": {"workload": cfg["name"], "nx": nx, "ny": ny, "nz": nz, "lx": CFG["lx"],
                    "ly": CFG["ly"], "z_grid": "tanh(1.8) faces", "poisson_bc": "neumann",
                    "helmholtz_c": c, "helmholtz": "u,v centred + w face, Dirichlet, Algorithm 2",
-                   "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (604 MB fields)",
-                   "pcr_partitions": args.nparts or "auto"},
+                   "parallelism": f"replicas{world}",
+                   "l2": f"inputs larger than L2 ({npts * 8 / 1e6:.0f} MB fields, L2 129 MB)",
+                   "pcr_partitions": args.nparts or plan.get_option(chanfs.OPT_PCR_PARTS),
+                   "kernel_shapes": tuned or "fixed by --nparts"},
         "e2e": {"value": e2e["value"], "unit": UNIT, "h2d_bytes_per_step": 4 * field_bytes,
                 "d2h_bytes_per_step": 4 * field_bytes, "steps": e2e_steps,
                 "api": "cfs_poisson_solve_host + 3 x cfs_helmholtz_solve_host, pinned host buffers"},
@@ -741,6 +747,8 @@ def main(argv=None):
                     help="requests of the serving stream (0: the full 20,000)")
     ap.add_argument("--extras-only", action="store_true",
                     help="run only the ensemble and serving measurements")
+    ap.add_argument("--mixed-nz", type=int, default=0,
+                    help="wall-normal size of the mixed comparison (profiling captures only)")
     ap.add_argument("--mixed-only", action="store_true",
                     help="run only the FP32-refined vs FP64 comparison and print its object")
     ap.add_argument("--nz", type=int, default=0,
