@@ -76,6 +76,13 @@ def _load():
             "or_poisson_solve": [i, i, i, d, d, dp, i, dp, dp],
             "or_helmholtz_solve": [i, i, i, dp, d, i, i, i, dp, dp],
             "or_apply_helmholtz3d": [i, i, i, d, d, dp, d, i, dp, dp],
+            "or_dct2": [i, dp, dp],
+            "or_idct2": [i, dp, dp],
+            "or_dst2": [i, dp, dp],
+            "or_idst2": [i, dp, dp],
+            "or_eig_wall": [i, d, i, dp],
+            "or_apply_poisson_walls": [i, i, i, d, d, dp, i, i, dp, dp],
+            "or_poisson_solve_walls": [i, i, i, d, d, dp, i, i, dp, dp],
             "or_helmholtz3d_solve": [i, i, i, d, d, dp, d, i, dp, dp],
             "or_spectral_forward": [i, i, i, dp, dp],
             "or_spectral_inverse": [i, i, i, dp, dp],
@@ -259,6 +266,58 @@ def helmholtz_solve(rhs, dzf, c: float, loc: int, method: int = THOMAS, nparts: 
     out = np.empty_like(rhs)
     _check(_load().or_helmholtz_solve(nx, ny, nz, _p(dzf), c, loc, method, nparts, _p(rhs), _p(out)),
            "helmholtz")
+    return out
+
+
+Y_PERIODIC, Y_NEUMANN, Y_DIRICHLET = 0, 1, 2
+
+
+def _r2r(name, x):
+    x = _f64(x)
+    out = np.empty_like(x)
+    _check(getattr(_load(), name)(x.size, _p(x), _p(out)), name)
+    return out
+
+
+def dct2(x):
+    """DCT-II by its definition: X_k = sum_j x_j cos(pi k (j + 1/2) / n)."""
+    return _r2r("or_dct2", x)
+
+
+def idct2(X):
+    return _r2r("or_idct2", X)
+
+
+def dst2(x):
+    """DST-II by its definition: X_k = sum_j x_j sin(pi (k + 1)(j + 1/2) / n)."""
+    return _r2r("or_dst2", x)
+
+
+def idst2(X):
+    return _r2r("or_idst2", X)
+
+
+def eig_wall(n: int, h: float, ybc: int) -> np.ndarray:
+    out = np.empty(n)
+    _check(_load().or_eig_wall(n, h, ybc, _p(out)), "eig_wall")
+    return out
+
+
+def apply_poisson_walls(p, lx: float, ly: float, dzf, bc: int, ybc: int) -> np.ndarray:
+    p, dzf = _f64(p), _f64(dzf)
+    nx, ny, nz = _shape(p)
+    out = np.empty_like(p)
+    _check(_load().or_apply_poisson_walls(nx, ny, nz, lx, ly, _p(dzf), bc, ybc, _p(p), _p(out)),
+           "apply_poisson_walls")
+    return out
+
+
+def poisson_solve_walls(f, lx: float, ly: float, dzf, bc: int, ybc: int) -> np.ndarray:
+    f, dzf = _f64(f), _f64(dzf)
+    nx, ny, nz = _shape(f)
+    out = np.empty_like(f)
+    _check(_load().or_poisson_solve_walls(nx, ny, nz, lx, ly, _p(dzf), bc, ybc, _p(f), _p(out)),
+           "poisson_solve_walls")
     return out
 
 

@@ -795,6 +795,207 @@ int or_helmholtz3d_solve(int nx, int ny, int nz, double lx, double ly,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Walls in y (Sec. 2.2.1 names DCT/DST for non-periodic directions).        */
+/* Cell-centred unknowns, ghost p_{-1} = +-p_0 and p_{Ny} = +-p_{Ny-1}:      */
+/*   Neumann   (+): eigenvectors cos(pi k (j+1/2)/N), k = 0..N-1 (DCT-II);   */
+/*   Dirichlet (-): eigenvectors sin(pi (k+1)(j+1/2)/N), k = 0..N-1 (DST-II); */
+/* eigenvalues 2(cos(pi k/N) - 1)/h^2 and 2(cos(pi (k+1)/N) - 1)/h^2.        */
+/* The transforms below are their definitions, summed directly.             */
+/* ybc: 0 periodic, 1 Neumann walls, 2 Dirichlet walls.                      */
+/* ------------------------------------------------------------------------ */
+enum { Y_PERIODIC = 0, Y_NEUMANN = 1, Y_DIRICHLET = 2 };
+static const double PI_HALF_TURN = 3.141592653589793238462643383279502884;
+
+int or_dct2(int n, const double* x, double* X) {
+  if (n < 1) return -1;
+  for (int k = 0; k < n; ++k) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) s += x[j] * cos(PI_HALF_TURN * k * (j + 0.5) / n);
+    X[k] = s;
+  }
+  return 0;
+}
+
+int or_idct2(int n, const double* X, double* x) {
+  if (n < 1) return -1;
+  for (int j = 0; j < n; ++j) {
+    double s = X[0];
+    for (int k = 1; k < n; ++k) s += 2.0 * X[k] * cos(PI_HALF_TURN * k * (j + 0.5) / n);
+    x[j] = s / n;
+  }
+  return 0;
+}
+
+int or_dst2(int n, const double* x, double* X) {
+  if (n < 1) return -1;
+  for (int k = 0; k < n; ++k) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) s += x[j] * sin(PI_HALF_TURN * (k + 1) * (j + 0.5) / n);
+    X[k] = s;
+  }
+  return 0;
+}
+
+int or_idst2(int n, const double* X, double* x) {
+  if (n < 1) return -1;
+  for (int j = 0; j < n; ++j) {
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) {
+      const double w = (k == n - 1) ? 1.0 : 2.0;
+      s += w * X[k] * sin(PI_HALF_TURN * (k + 1) * (j + 0.5) / n);
+    }
+    x[j] = s / n;
+  }
+  return 0;
+}
+
+int or_eig_wall(int n, double h, int ybc, double* lam) {
+  if (n < 1 || !(h > 0) || (ybc != Y_NEUMANN && ybc != Y_DIRICHLET)) return -1;
+  for (int k = 0; k < n; ++k) {
+    const int m = (ybc == Y_NEUMANN) ? k : k + 1;
+    lam[k] = 2.0 * (cos(PI_HALF_TURN * m / n) - 1.0) / (h * h);
+  }
+  return 0;
+}
+
+/* L p with walls in y: the 7-point stencil written out point by point. */
+int or_apply_poisson_walls(int nx, int ny, int nz, double lx, double ly, const double* dzf,
+                           int bc, int ybc, const double* p, double* out) {
+  if (nx < 1 || ny < 1 || nz < 3 || !(lx > 0) || !(ly > 0)) return -1;
+  if (bc != BC_NEUMANN && bc != BC_DIRICHLET) return -1;
+  if (ybc != Y_PERIODIC && ybc != Y_NEUMANN && ybc != Y_DIRICHLET) return -1;
+  double dx = lx / nx, dy = ly / ny;
+  double* dzc = (double*)malloc(sizeof(double) * (size_t)nz);
+  or_dzc(nz, dzf, dzc);
+  size_t sxy = (size_t)nx * ny;
+  const double g = (ybc == Y_NEUMANN) ? 1.0 : -1.0;  /* ghost = g * boundary value */
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        size_t pl = sxy * (size_t)z;
+        size_t i = pl + (size_t)nx * y + x;
+        int xp = (x + 1) % nx, xm = (x + nx - 1) % nx;
+        double lxx = (p[pl + (size_t)nx * y + xp] - 2.0 * p[i] + p[pl + (size_t)nx * y + xm]) / (dx * dx);
+        double up, dn;
+        if (ybc == Y_PERIODIC) {
+          up = p[pl + (size_t)nx * ((y + 1) % ny) + x];
+          dn = p[pl + (size_t)nx * ((y + ny - 1) % ny) + x];
+        } else {
+          up = (y + 1 < ny) ? p[pl + (size_t)nx * (y + 1) + x] : g * p[i];
+          dn = (y > 0) ? p[pl + (size_t)nx * (y - 1) + x] : g * p[i];
+        }
+        double lyy = (up - 2.0 * p[i] + dn) / (dy * dy);
+        double lzz = lz_centre(nz, dzf, dzc, bc, p + (size_t)x + (size_t)nx * y, sxy, z);
+        out[i] = lxx + lyy + lzz;
+      }
+  free(dzc);
+  return 0;
+}
+
+/* Transform along y of every (x, z) line of a complex field: DFT, or the
+ * DCT-II / DST-II of real and imaginary parts (inverse: the inverse sums). */
+static void y_walls_axis(cplx* F, int nx, int ny, int nz, int ybc, int inverse) {
+  double* re = (double*)malloc(sizeof(double) * (size_t)ny);
+  double* im = (double*)malloc(sizeof(double) * (size_t)ny);
+  double* ro = (double*)malloc(sizeof(double) * (size_t)ny);
+  double* io = (double*)malloc(sizeof(double) * (size_t)ny);
+  for (int z = 0; z < nz; ++z)
+    for (int x = 0; x < nx; ++x) {
+      cplx* base = F + (size_t)x + (size_t)nx * (size_t)ny * z;
+      for (int y = 0; y < ny; ++y) {
+        re[y] = creal(base[(size_t)nx * y]);
+        im[y] = cimag(base[(size_t)nx * y]);
+      }
+      if (ybc == Y_NEUMANN) {
+        if (inverse) { or_idct2(ny, re, ro); or_idct2(ny, im, io); }
+        else { or_dct2(ny, re, ro); or_dct2(ny, im, io); }
+      } else {
+        if (inverse) { or_idst2(ny, re, ro); or_idst2(ny, im, io); }
+        else { or_dst2(ny, re, ro); or_dst2(ny, im, io); }
+      }
+      for (int y = 0; y < ny; ++y) base[(size_t)nx * y] = ro[y] + I * io[y];
+    }
+  free(io); free(ro); free(im); free(re);
+}
+
+/* Poisson solve with walls in y: DFT along x, DCT-II / DST-II (or DFT)
+ * along y, one tridiagonal system per (kx, ky) with lx[kx] + ly[ky], inverse
+ * transforms.  The (0,0) system is singular when both y and z walls are
+ * Neumann (or y periodic and z Neumann): pinned, then the dz-weighted mean
+ * removed, as in or_poisson_solve; the rhs is projected first. */
+int or_poisson_solve_walls(int nx, int ny, int nz, double lx, double ly, const double* dzf,
+                           int bc, int ybc, const double* f, double* p) {
+  if (nx < 1 || ny < 1 || nz < 3 || !(lx > 0) || !(ly > 0)) return -1;
+  if (bc != BC_NEUMANN && bc != BC_DIRICHLET) return -1;
+  if (ybc != Y_PERIODIC && ybc != Y_NEUMANN && ybc != Y_DIRICHLET) return -1;
+  if (ybc == Y_PERIODIC) return or_poisson_solve(nx, ny, nz, lx, ly, dzf, bc, f, p);
+  const int has_null = (bc == BC_NEUMANN && ybc == Y_NEUMANN);
+  size_t n = (size_t)nx * ny * nz, sxy = (size_t)nx * ny;
+  cplx* F = (cplx*)malloc(sizeof(cplx) * n);
+  double wmean = 0.0;
+  if (has_null) {
+    double sw = 0.0, swf = 0.0;
+    for (int z = 0; z < nz; ++z)
+      for (size_t c = 0; c < sxy; ++c) {
+        swf += dzf[z] * f[c + sxy * (size_t)z];
+        sw += dzf[z];
+      }
+    wmean = swf / sw;
+  }
+  for (size_t i = 0; i < n; ++i) F[i] = f[i] - wmean;
+  int dims[3] = {nx, ny, nz};
+  fft_axis(F, dims, 0, -1);
+  y_walls_axis(F, nx, ny, nz, ybc, 0);
+  double* lamx = (double*)malloc(sizeof(double) * (size_t)nx);
+  double* lamy = (double*)malloc(sizeof(double) * (size_t)ny);
+  or_eig_periodic(nx, lx / nx, lamx);
+  or_eig_wall(ny, ly / ny, ybc, lamy);
+  double* A = (double*)malloc(sizeof(double) * (size_t)nz);
+  double* B = (double*)malloc(sizeof(double) * (size_t)nz);
+  double* C = (double*)malloc(sizeof(double) * (size_t)nz);
+  double* a = (double*)malloc(sizeof(double) * (size_t)nz);
+  double* b = (double*)malloc(sizeof(double) * (size_t)nz);
+  double* c = (double*)malloc(sizeof(double) * (size_t)nz);
+  cplx* d = (cplx*)malloc(sizeof(cplx) * (size_t)nz);
+  cplx* x = (cplx*)malloc(sizeof(cplx) * (size_t)nz);
+  or_lz_coefficients(nz, dzf, bc, LOC_CENTER, A, B, C);
+  for (int ky = 0; ky < ny; ++ky)
+    for (int kx = 0; kx < nx; ++kx) {
+      double lam = lamx[kx] + lamy[ky];
+      for (int k = 0; k < nz; ++k) {
+        a[k] = A[k];
+        b[k] = B[k] + lam;
+        c[k] = C[k];
+        d[k] = F[(size_t)kx + (size_t)nx * ky + sxy * (size_t)k];
+      }
+      int singular = (has_null && kx == 0 && ky == 0);
+      if (singular) {
+        b[0] = 1.0;
+        c[0] = 0.0;
+        d[0] = 0.0;
+      }
+      thomas_complex(nz, a, b, c, d, x);
+      if (singular) {
+        cplx sw = 0.0, swx = 0.0;
+        for (int k = 0; k < nz; ++k) {
+          swx += dzf[k] * x[k];
+          sw += dzf[k];
+        }
+        cplx mean = swx / sw;
+        for (int k = 0; k < nz; ++k) x[k] -= mean;
+      }
+      for (int k = 0; k < nz; ++k) F[(size_t)kx + (size_t)nx * ky + sxy * (size_t)k] = x[k];
+    }
+  y_walls_axis(F, nx, ny, nz, ybc, 1);
+  fft_axis(F, dims, 0, 1);
+  double scale = 1.0 / (double)nx;
+  for (size_t i = 0; i < n; ++i) p[i] = creal(F[i]) * scale;
+  free(x); free(d); free(c); free(b); free(a); free(C); free(B); free(A);
+  free(lamy); free(lamx); free(F);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Spectral layout of the solver: App. A packing along x (even Nx: pair j of */
 /* a line is X_j for j >= 1 and X_0 + i X_{Nx/2} for j = 0), complex DFT     */
 /* along y of each pair, and for pair j = 0 the same packing idea once more  */

@@ -73,6 +73,19 @@ int or_poisson_solve(int nx, int ny, int nz, double lx, double ly,
 int or_helmholtz_solve(int nx, int ny, int nz, const double* dzf, double c,
                        int loc, int method, int nparts, const double* rhs,
                        double* u);
+/* Walls in y (ybc 0 periodic, 1 Neumann, 2 Dirichlet; cell-centred): the
+ * DCT-II / DST-II and inverses by their definitions, the wall eigenvalues,
+ * the operator and the Poisson solve. */
+int or_dct2(int n, const double* x, double* X);
+int or_idct2(int n, const double* X, double* x);
+int or_dst2(int n, const double* x, double* X);
+int or_idst2(int n, const double* X, double* x);
+int or_eig_wall(int n, double h, int ybc, double* lam);
+int or_apply_poisson_walls(int nx, int ny, int nz, double lx, double ly, const double* dzf,
+                           int bc, int ybc, const double* p, double* out);
+int or_poisson_solve_walls(int nx, int ny, int nz, double lx, double ly, const double* dzf,
+                           int bc, int ybc, const double* f, double* p);
+
 /* Fully implicit 3-D Helmholtz (Eq. 8), Dirichlet z walls: apply and solve. */
 int or_apply_helmholtz3d(int nx, int ny, int nz, double lx, double ly,
                          const double* dzf, double c, int loc, const double* u,

@@ -564,3 +564,81 @@ def test_helmholtz3d_reduces_to_z_implicit_and_identity(loc):
     if loc == 1:
         g[-1] = 0.0
     assert _rel(oracle.helmholtz3d_solve(g, 1.0, 1.0, dzf, 0.0, loc), g) < 1e-15
+
+
+# ----------------------------------------------------------------------------
+# Walls in y: DCT-II / DST-II (Sec. 2.2.1) and the Poisson solve with them
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 3, 8, 12, 27])
+def test_dct_dst_match_scipy_and_invert(n):
+    scipy_fft = pytest.importorskip("scipy.fft")
+    x = synth.normal(n, (n,))
+    # scipy's unnormalised type-2 transforms are twice the plain sums
+    assert np.max(np.abs(oracle.dct2(x) - scipy_fft.dct(x, type=2) / 2)) < 1e-13 * n
+    assert np.max(np.abs(oracle.dst2(x) - scipy_fft.dst(x, type=2) / 2)) < 1e-13 * n
+    assert np.max(np.abs(oracle.idct2(oracle.dct2(x)) - x)) < 1e-13 * n
+    assert np.max(np.abs(oracle.idst2(oracle.dst2(x)) - x)) < 1e-13 * n
+
+
+@pytest.mark.parametrize("ybc", [1, 2])
+def test_wall_eigenpairs_of_the_y_stencil(ybc):
+    """cos / sin modes of the cell-centred wall stencil have the tabulated
+    eigenvalues (the operator is applied point by point)."""
+    ny, nz, ly = 12, 4, 3.0
+    dy = ly / ny
+    lam = oracle.eig_wall(ny, dy, ybc)
+    j = np.arange(ny) + 0.5
+    for k in range(ny):
+        mode = np.cos(np.pi * k * j / ny) if ybc == 1 else np.sin(np.pi * (k + 1) * j / ny)
+        p = np.broadcast_to(mode[None, :, None], (nz, ny, 3)).copy()
+        # Neumann z walls: a z-constant field has no z contribution
+        lp = oracle.apply_poisson_walls(p, 1.0, ly, synth.uniform_dz(nz), 0, ybc)
+        assert np.max(np.abs(lp - lam[k] * p)) < 1e-10 * max(1.0, abs(lam[k]))
+
+
+@pytest.mark.parametrize("dims,beta,bc,ybc", [((4, 4, 4), 1.5, 0, 1), ((4, 5, 4), 1.5, 1, 1),
+                                              ((3, 4, 5), None, 0, 2), ((4, 3, 5), 1.8, 1, 2),
+                                              ((2, 6, 4), 1.2, 0, 1), ((6, 4, 6), 1.6, 0, 2)])
+def test_poisson_walls_match_dense_bruteforce(dims, beta, bc, ybc):
+    nx, ny, nz = dims
+    lx, ly = 2.0, 1.5
+    dzf = synth.uniform_dz(nz) if beta is None else synth.tanh_dz(nz, beta)
+    f = synth.normal(41 + nx + ny + nz + bc + ybc, (nz, ny, nx))
+    n = nx * ny * nz
+    L = np.zeros((n, n))
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1.0
+        L[:, i] = oracle.apply_poisson_walls(e.reshape(nz, ny, nx), lx, ly, dzf, bc, ybc).ravel()
+    p = oracle.poisson_solve_walls(f, lx, ly, dzf, bc, ybc)
+    w = np.repeat(dzf, nx * ny)
+    if bc == 0 and ybc == 1:  # null space: the constants (bordered system)
+        K = np.zeros((n + 1, n + 1))
+        K[:n, :n] = L
+        K[:n, n] = 1.0
+        K[n, :n] = w
+        ref = np.linalg.solve(K, np.concatenate([f.ravel(), [0.0]]))[:n]
+        assert abs(w @ p.ravel()) < 1e-12 * np.sum(w) * np.max(np.abs(p))
+    else:
+        ref = np.linalg.solve(L, f.ravel())
+    assert _rel(p.ravel(), ref) < 1e-11
+
+
+@pytest.mark.parametrize("bc,ybc", [(0, 1), (1, 1), (0, 2), (1, 2)])
+def test_poisson_walls_single_mode_closed_form(bc, ybc):
+    nx, ny, nz = 8, 12, 10
+    lx, ly = 2 * np.pi, 3.0
+    dx, dy, dz = lx / nx, ly / ny, 2.0 / nz
+    x = np.arange(nx) * dx
+    jj = np.arange(ny) + 0.5
+    zc = (np.arange(nz) + 0.5) * dz
+    for m, k, l in [(1, 2, 1), (3, 0, 2), (0, 5, 3), (2, 11, 4)]:
+        gy = np.cos(np.pi * k * jj / ny) if ybc == 1 else np.sin(np.pi * (k + 1) * jj / ny)
+        gz = np.cos(np.pi * l * zc / 2.0) if bc == 0 else np.sin(np.pi * l * zc / 2.0)
+        f = gz[:, None, None] * gy[None, :, None] * np.cos(2 * np.pi * m * x / lx)[None, None, :]
+        kk = k if ybc == 1 else k + 1
+        lam = 2 * (np.cos(2 * np.pi * m / nx) - 1) / dx**2 + 2 * (np.cos(np.pi * kk / ny) - 1) / dy**2 \
+            + 2 * (np.cos(np.pi * l / nz) - 1) / dz**2
+        p = oracle.poisson_solve_walls(f, lx, ly, synth.uniform_dz(nz), bc, ybc)
+        assert _rel(p, f / lam) < 1e-12
