@@ -335,6 +335,37 @@ def run_helmholtz3d(chanfs, torch, device, plan, rhs, outs, reps: int = 5):
 
 
 # ----------------------------------------------------------------------------
+# Walls in y (DCT-II / DST-II) on the channel workload
+# ----------------------------------------------------------------------------
+
+def run_ywalls(chanfs, torch, device, f, reps: int = 5):
+    """The channel's Poisson solve with Neumann or Dirichlet walls in y
+    instead of periodicity, FP64, median of reps solves each."""
+    nz, ny, nx = f.shape
+    dz = synth.grid_dz(CFG)
+    out = {"workload": CFG["name"], "precision": "f64"}
+    p = torch.empty_like(f)
+    for name, ybc in (("neumann", chanfs.Y_NEUMANN), ("dirichlet", chanfs.Y_DIRICHLET)):
+        with chanfs.Plan(nx, ny, nz, CFG["lx"], CFG["ly"], dz, chanfs.NEUMANN, chanfs.F64,
+                         ybc) as plan:
+            plan.poisson_solve(f, out=p)
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(reps):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                plan.poisson_solve(f, out=p)
+                b.record()
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            t = statistics.median(ms)
+            out[name] = {"ms": round(t, 4), "ns_per_pt": t * 1e6 / f.numel(),
+                         "device_status": plan.check()}
+    return out
+
+
+# ----------------------------------------------------------------------------
 # Batched ensemble: 48 boxes, grouped FP32 + FP64-refined solves vs per box
 # ----------------------------------------------------------------------------
 
@@ -715,6 +746,7 @@ def run_ours(args):
         "device_status": status,
     }
     line["helmholtz3d"] = run_helmholtz3d(chanfs, torch, device, plan, rhs, us)
+    line["ywalls"] = run_ywalls(chanfs, torch, device, f)
     plan.close()
     del f, rhs, p, us, ref_bits
     if not args.no_mixed:

@@ -86,6 +86,24 @@ const char* cfs_status_string(int status);
 int cfs_plan_create(cfs_plan_t* plan, int nx, int ny, int nz, double lx,
                     double ly, const double* dz, int poisson_bc, int dtype);
 
+/*
+ * cfs_plan_create_walls -- as cfs_plan_create, with walls in y as well
+ * (Sec. 2.2.1 names cosine/sine transforms for non-periodic directions).
+ *   ybc  CFS_Y_PERIODIC (what cfs_plan_create makes), CFS_Y_NEUMANN or
+ *        CFS_Y_DIRICHLET: homogeneous walls at y = 0 and y = ly, cell-centred
+ *        unknowns, mirror ghosts p_{-1} = +-p_0 and p_{Ny} = +-p_{Ny-1}.
+ * With walls the y transform is DCT-II (Neumann) or DST-II (Dirichlet), each
+ * computed by one complex FFT of length Ny; the eigenvalues are
+ * 2(cos(pi k/Ny) - 1)/dy^2 and 2(cos(pi (k+1)/Ny) - 1)/dy^2, k < Ny.  The
+ * solution's null space (constants) exists only with Neumann walls in both
+ * y and z; the Neumann conventions above apply to it.  The Poisson,
+ * z-implicit Helmholtz, refined and grouped solves support y walls;
+ * cfs_helmholtz3d_* returns CFS_EUNSUPPORTED on such plans.
+ */
+enum { CFS_Y_PERIODIC = 0, CFS_Y_NEUMANN = 1, CFS_Y_DIRICHLET = 2 };
+int cfs_plan_create_walls(cfs_plan_t* plan, int nx, int ny, int nz, double lx, double ly,
+                          const double* dz, int poisson_bc, int ybc, int dtype);
+
 /* Release the plan and everything it owns.  Waits for the device. */
 int cfs_plan_destroy(cfs_plan_t plan);
 

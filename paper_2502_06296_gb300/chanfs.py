@@ -27,6 +27,8 @@ OPT_THOMAS_TILE, OPT_X_LINES, OPT_Y_TILE, OPT_PCR_PARTS, OPT_HELM_FP64 = 1, 2, 3
 
 REQ_POISSON, REQ_HELMHOLTZ = 0, 1
 
+Y_PERIODIC, Y_NEUMANN, Y_DIRICHLET = 0, 1, 2
+
 
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_ulonglong), ("completed", ctypes.c_ulonglong),
@@ -59,6 +61,7 @@ def lib():
             "cfs_version": ([], i),
             "cfs_status_string": ([i], ctypes.c_char_p),
             "cfs_plan_create": ([ctypes.POINTER(vp), i, i, i, d, d, dp, i, i], i),
+            "cfs_plan_create_walls": ([ctypes.POINTER(vp), i, i, i, d, d, dp, i, i, i], i),
             "cfs_plan_destroy": ([vp], i),
             "cfs_plan_device_bytes": ([vp, ctypes.POINTER(ctypes.c_size_t)], i),
             "cfs_poisson_solve": ([vp, vp, vp, vp], i),
@@ -128,21 +131,24 @@ def _stream_ptr(stream):
 
 
 class Plan:
-    """One grid: Nx x Ny x Nz cells, periodic x/y of lengths lx, ly, and the
-    z cell widths dz (host array).  See cfs_plan_create."""
+    """One grid: Nx x Ny x Nz cells, periodic x of length lx, y of length ly
+    (periodic, or walls: ybc), and the z cell widths dz (host array).  See
+    cfs_plan_create / cfs_plan_create_walls."""
 
     def __init__(self, nx: int, ny: int, nz: int, lx: float, ly: float, dz, bc: int = NEUMANN,
-                 dtype: int = F64):
+                 dtype: int = F64, ybc: int = Y_PERIODIC):
         self.dtype = dtype
         dz = np.ascontiguousarray(dz, dtype=np.float64)
         if dz.size != nz:
             raise ValueError("dz must have nz entries")
         self.nx, self.ny, self.nz, self.lx, self.ly, self.bc = nx, ny, nz, lx, ly, bc
+        self.ybc = ybc
         self.dz = dz.copy()
         h = ctypes.c_void_p()
-        rc = lib().cfs_plan_create(ctypes.byref(h), nx, ny, nz, lx, ly,
-                                   dz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), bc, dtype)
-        _check(rc, "cfs_plan_create")
+        rc = lib().cfs_plan_create_walls(ctypes.byref(h), nx, ny, nz, lx, ly,
+                                         dz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), bc,
+                                         ybc, dtype)
+        _check(rc, "cfs_plan_create_walls")
         self._h = h
 
     @property

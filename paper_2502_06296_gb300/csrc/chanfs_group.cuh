@@ -44,7 +44,9 @@ struct YBox {  // FFT along y on TMA tiles (fft_y.cu); the map is 64-byte aligne
   CUtensorMap map;
   FftDesc d;
   const void* tw;
+  const void* wy;  // wall-transform factors (y walls)
   int tk, by, nbox, ntx;
+  int ytype;       // 0 periodic y (FFT), 1 DCT-II, 2 DST-II
   int* status;
 };
 
@@ -61,6 +63,7 @@ struct ThomasArgs {  // z sweeps of Eq. 12 (thomas.cu)
   int nblk_x;            // blocks along kx per ky
   int neumann;
   int kx64, ky64;        // FP32 spectra: columns kx < kx64, |ky| < ky64 in FP64
+  int ywall;             // y walls: every slot ky is its own column (no +-ky pairs)
 };
 
 struct ResBox {  // refinement residual and norms (refine.cu)
@@ -73,7 +76,8 @@ struct ResBox {  // refinement residual and norms (refine.cu)
   unsigned int* rmax;  // max |r| (float bits)
   int nx, ny, nz, n;   // n = Helmholtz unknowns per column
   double idx2, idy2;
-  int neumann;
+  int neumann;         // the operator has the constants as null space (mean removal)
+  int ybc;             // 0 periodic y, 1 Neumann walls, 2 Dirichlet walls
 };
 
 // Blocks of the grouped mean subtraction for a field of n points.

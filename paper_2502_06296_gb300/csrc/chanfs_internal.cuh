@@ -89,9 +89,13 @@ struct Helm3Coef {
 struct cfs_plan {
   int device;
   int nx, ny, nz, M;  // M = nx/2 complex points per packed x-line
-  int nky;            // ky pairs handled by the Thomas kernel: ny/2 + 1
+  int nky;            // ky rows of the factor tables: ny/2 + 1 pairs (periodic y), else ny
   double lx, ly;
   int bc;
+  int ybc;            // y: CFS_Y_PERIODIC, CFS_Y_NEUMANN or CFS_Y_DIRICHLET
+  int has_null;       // Neumann z walls with Neumann or periodic y: constants are the null space
+  double2* d_wy;      // y walls: exp(-i pi k / 2 Ny), k < Ny (FP32 copy d_wy32)
+  float2* d_wy32;
   std::vector<double> dzf;  // host copy of the cell widths
   // FFT plans and tables
   chanfs::FftDesc fx, fy;

@@ -15,17 +15,117 @@
 
 namespace chanfs {
 
-// Tile bx (columns [bx * tk, bx * tk + tk)) of z plane z.
+// Walls in y (Sec. 2.2.1 names cosine / sine transforms for non-periodic
+// directions).  A column of N values is transformed by DCT-II (Neumann walls)
+// or DST-II (Dirichlet walls) through one complex FFT of length N:
+//   v_n = x_{2n}, v_{N-1-n} = x_{2n+1}   (even samples up, odd samples down)
+//   V = FFT(v),  X_k = (w_k V_k + conj(w_k) V_{N-k}) / 2,  w_k = exp(-i pi k / 2N)
+// which holds for complex columns because the transform is real-linear.  The
+// inverse recovers V_k = conj(w_k) (X_k - i X_{N-k}) (V_0 = X_0), transforms
+// back and undoes the reordering; like the FFT it returns N times the column.
+// DST-II is DCT-II of (-1)^j x_j with the output order reversed.
+enum { Y_FFT = 0, Y_DCT = 1, Y_DST = 2 };
+
+// Elements of one y-tile buffer: tk x n values rounded up to 128 bytes.
+__host__ __device__ inline int y_buf_elems(int tk, int n, int csize) {
+  const int bytes = (tk * n * csize + 127) / 128 * 128;
+  return bytes / csize;
+}
+
+inline size_t y_smem_bytes(int tk, int n, int ntw, size_t csize) {
+  return 128 + csize * (2 * (size_t)y_buf_elems(tk, n, (int)csize) + (size_t)ntw);
+}
+
+template <class C>
+__device__ __forceinline__ C cmul_conj_a(C a, C b) {  // conj(a) * b
+  return mkc<C>(fma(a.x, b.x, a.y * b.y), fma(a.x, b.y, -a.y * b.x));
+}
+
+// The wall transform of a loaded tile (buf0), stored back by TMA.
+template <bool INV, class C>
+__device__ __forceinline__ void y_wall_transform(C* buf0, C* buf1, const FftDesc& d, int tk,
+                                                 const C* tw, int ytype,
+                                                 const C* __restrict__ wy, const CUtensorMap* map,
+                                                 int by, int nbox, int x0, int z) {
+  using T = typename cscal<C>::T;
+  const int N = d.n;
+  const bool dst = (ytype == Y_DST);
+  const T h = T(0.5);
+  C* res;
+  if (!INV) {
+    for (int e = threadIdx.x; e < N * tk; e += blockDim.x) {  // reorder (and signs)
+      const int j = e / tk, c = e - j * tk;
+      const int t = (j & 1) ? N - 1 - (j >> 1) : (j >> 1);
+      C v = buf0[e];
+      if (dst && (j & 1)) v = mkc<C>(-v.x, -v.y);
+      buf1[t * tk + c] = v;
+    }
+    __syncthreads();
+    res = stockham_smem<false, true>(buf1, buf0, d, tk, tk, 1, tw);
+    C* out = (res == buf0) ? buf1 : buf0;
+    for (int e = threadIdx.x; e < (N / 2 + 1) * tk; e += blockDim.x) {
+      const int k = e / tk, c = e - k * tk;
+      const int kn = (k == 0) ? 0 : N - k;
+      const C vk = res[k * tk + c], vn = res[kn * tk + c];
+      const C wk = wy[k], wn = wy[kn];
+      const C a = cmul(wk, vk), b = cmul_conj_a(wk, vn);  // X_k
+      out[(dst ? N - 1 - k : k) * tk + c] = mkc<C>(h * (a.x + b.x), h * (a.y + b.y));
+      if (kn != k) {
+        const C a2 = cmul(wn, vn), b2 = cmul_conj_a(wn, vk);  // X_{N-k}
+        out[(dst ? N - 1 - kn : kn) * tk + c] = mkc<C>(h * (a2.x + b2.x), h * (a2.y + b2.y));
+      }
+    }
+    res = out;
+  } else {
+    for (int e = threadIdx.x; e < (N / 2 + 1) * tk; e += blockDim.x) {
+      const int k = e / tk, c = e - k * tk;
+      const int kn = (k == 0) ? 0 : N - k;
+      const C xk = buf0[(dst ? N - 1 - k : k) * tk + c];
+      if (k == 0) {
+        buf1[c] = xk;
+        continue;
+      }
+      const C xn = buf0[(dst ? N - 1 - kn : kn) * tk + c];
+      // V_k = conj(w_k) (X_k - i X_{N-k})
+      buf1[k * tk + c] = cmul_conj_a(wy[k], mkc<C>(xk.x + xn.y, xk.y - xn.x));
+      if (kn != k) buf1[kn * tk + c] = cmul_conj_a(wy[kn], mkc<C>(xn.x + xk.y, xn.y - xk.x));
+    }
+    __syncthreads();
+    res = stockham_smem<true, true>(buf1, buf0, d, tk, tk, 1, tw);
+    C* out = (res == buf0) ? buf1 : buf0;
+    for (int e = threadIdx.x; e < N * tk; e += blockDim.x) {  // undo the reordering
+      const int j = e / tk, c = e - j * tk;
+      const int t = (j & 1) ? N - 1 - (j >> 1) : (j >> 1);
+      C v = res[t * tk + c];
+      if (dst && (j & 1)) v = mkc<C>(-v.x, -v.y);
+      out[e] = v;
+    }
+    res = out;
+  }
+  fence_proxy_async();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < nbox; ++b) tma_store_3d(map, res + b * by * tk, x0, b * by, z);
+    tma_store_commit_and_wait_read();
+  }
+}
+
+// Tile bx (columns [bx * tk, bx * tk + tk)) of z plane z; ytype is Y_FFT for
+// periodic y, else the wall transform, with wy[k] = exp(-i pi k / 2N).
 template <bool INV, class C>
 __device__ __forceinline__ void fft_y_body(const CUtensorMap* map, const FftDesc& d,
                                            const C* __restrict__ twg, int tk, int by, int nbox,
-                                           int* status, int bx, int z) {
+                                           int* status, int bx, int z, int ytype,
+                                           const C* __restrict__ wy) {
   using T = typename cscal<C>::T;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
   C* buf0 = reinterpret_cast<C*>(smem_raw + 128);
-  C* buf1 = buf0 + tk * d.n;
-  C* tw = buf1 + tk * d.n;
+  // both ping-pong buffers start on 128-byte boundaries: either may be the
+  // source of the TMA store
+  const int bstride = y_buf_elems(tk, d.n, (int)sizeof(C));
+  C* buf1 = buf0 + bstride;
+  C* tw = buf1 + bstride;
   const int x0 = 2 * tk * bx;  // in reals: a 16-byte aligned coordinate
 
   if (threadIdx.x == 0) {
@@ -51,6 +151,10 @@ __device__ __forceinline__ void fft_y_body(const CUtensorMap* map, const FftDesc
   // once more along y: slot ky (0 < 2ky < Ny) holds F(0,ky), slot Ny-ky holds
   // F(Nx/2,ky), and the self-conjugate slots (ky = 0, Ny/2) keep the real pair
   // F(0,ky) + i F(Nx/2,ky).  Every slot is then one column of Eq. 12.
+  if (ytype != Y_FFT) {  // walls: cosine or sine transform of every column
+    y_wall_transform<INV>(buf0, buf1, d, tk, tw, ytype, wy, map, by, nbox, x0, z);
+    return;
+  }
   if (INV && bx == 0) {  // re-tangle before the inverse transform
     for (int ky = 1 + threadIdx.x; 2 * ky < ny; ky += blockDim.x) {
       const C f0 = buf0[ky * tk], fm = buf0[(ny - ky) * tk];
@@ -82,8 +186,9 @@ __device__ __forceinline__ void fft_y_body(const CUtensorMap* map, const FftDesc
 template <bool INV, class C>
 __global__ void __launch_bounds__(128) fft_y_kernel(const __grid_constant__ CUtensorMap map,
                                                     FftDesc d, const C* __restrict__ twg,
-                                                    int tk, int by, int nbox, int* status) {
-  fft_y_body<INV, C>(&map, d, twg, tk, by, nbox, status, blockIdx.x, blockIdx.y);
+                                                    int tk, int by, int nbox, int* status,
+                                                    int ytype, const C* __restrict__ wy) {
+  fft_y_body<INV, C>(&map, d, twg, tk, by, nbox, status, blockIdx.x, blockIdx.y, ytype, wy);
 }
 
 // One launch for several boxes (FP32 inner solves of grouped refinement).
@@ -93,12 +198,13 @@ __global__ void __launch_bounds__(128) fft_y_group_kernel(const YBox* boxes, Gro
   if (!group_block(g, &b, &blk)) return;
   const YBox& y = boxes[b];
   fft_y_body<INV, float2>(&y.map, y.d, static_cast<const float2*>(y.tw), y.tk, y.by, y.nbox,
-                          y.status, blk % y.ntx, blk / y.ntx);
+                          y.status, blk % y.ntx, blk / y.ntx, y.ytype,
+                          static_cast<const float2*>(y.wy));
 }
 
 template <class C>
 static cudaError_t launch_y(const cfs_plan* P, void* data, bool inverse, int tk, const C* tw,
-                            cudaStream_t st) {
+                            const C* wy, cudaStream_t st) {
   if (P->ny == 1) return cudaSuccess;  // length-1 transform is the identity
   using T = typename cscal<C>::T;
   CUtensorMap map;
@@ -107,16 +213,16 @@ static cudaError_t launch_y(const cfs_plan* P, void* data, bool inverse, int tk,
                                  (cuuint64_t)(2 * P->M) * P->ny * sizeof(T)};
   const cuuint32_t box[3] = {(cuuint32_t)(2 * tk), (cuuint32_t)P->by, 1};
   if (!encode_map(&map, sizeof(T), 3, data, gdim, gstride, box)) return cudaErrorInvalidValue;
-  const size_t smem = 128 + sizeof(C) * (size_t)(2 * tk * P->ny + P->fy.ntw);
+  const size_t smem = y_smem_bytes(tk, P->ny, P->fy.ntw, sizeof(C));
   dim3 grid((P->M + tk - 1) / tk, P->nz);
   if (!inverse) {
     auto k = fft_y_kernel<false, C>;
     allow_max_smem(k);
-    k<<<grid, 128, smem, st>>>(map, P->fy, tw, tk, P->by, P->nbox, P->d_status);
+    k<<<grid, 128, smem, st>>>(map, P->fy, tw, tk, P->by, P->nbox, P->d_status, P->ybc, wy);
   } else {
     auto k = fft_y_kernel<true, C>;
     allow_max_smem(k);
-    k<<<grid, 128, smem, st>>>(map, P->fy, tw, tk, P->by, P->nbox, P->d_status);
+    k<<<grid, 128, smem, st>>>(map, P->fy, tw, tk, P->by, P->nbox, P->d_status, P->ybc, wy);
   }
   return cudaGetLastError();
 }
@@ -125,15 +231,15 @@ bool y_tile_ok(const cfs_plan* P, int tk, bool fp32) {
   const size_t csize = fp32 ? sizeof(float2) : sizeof(double2);
   if (tk < 1 || tk > 32 || (fp32 && tk % 2)) return false;  // 16-byte TMA box rows
   if (P->nbox > 1 && ((size_t)P->by * tk * csize) % 128 != 0) return false;
-  return 128 + csize * (size_t)(2 * tk * P->ny + P->fy.ntw) <= 227 * 1024;
+  return y_smem_bytes(tk, P->ny, P->fy.ntw, csize) <= 227 * 1024;
 }
 
 cudaError_t launch_fft_y(const cfs_plan* P, double* data, bool inverse, cudaStream_t st) {
-  return launch_y<double2>(P, data, inverse, P->tk, P->d_twy, st);
+  return launch_y<double2>(P, data, inverse, P->tk, P->d_twy, P->d_wy, st);
 }
 
 cudaError_t launch_fft_y32(const cfs_plan* P, float* data, bool inverse, cudaStream_t st) {
-  return launch_y<float2>(P, data, inverse, P->tk32, P->d_twy32, st);
+  return launch_y<float2>(P, data, inverse, P->tk32, P->d_twy32, P->d_wy32, st);
 }
 
 size_t y_group_box(const cfs_plan* P, YBox* box, int* blocks) {
@@ -150,8 +256,10 @@ size_t y_group_box(const cfs_plan* P, YBox* box, int* blocks) {
   box->nbox = P->nbox;
   box->ntx = (P->M + tk - 1) / tk;
   box->status = P->d_status;
+  box->ytype = P->ybc;
+  box->wy = P->d_wy32;
   *blocks = (P->ny == 1) ? 0 : box->ntx * P->nz;  // a length-1 transform is the identity
-  return 128 + sizeof(float2) * (size_t)(2 * tk * P->ny + P->fy.ntw);
+  return y_smem_bytes(tk, P->ny, P->fy.ntw, sizeof(float2));
 }
 
 cudaError_t launch_fft_y_group32(const YBox* boxes, GroupMap g, int total, size_t smem,

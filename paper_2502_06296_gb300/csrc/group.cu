@@ -194,7 +194,7 @@ static int group_bind(cfs_group* G, int nplans, const cfs_plan_t* plans, cudaStr
   for (int b = 0; b < nplans; ++b) {
     cfs_plan* P = plans[b];
     G->plans.push_back(P);
-    G->neumann.push_back(P->bc == CFS_BC_NEUMANN);
+    G->neumann.push_back(P->has_null);
     G->smem_x = std::max(G->smem_x, x_group_box(P, false, &xf[b], &bx[b]));
     x_group_box(P, true, &xi[b], &bx[b]);
     const size_t sy = y_group_box(P, &y[b], &by[b]);
@@ -217,7 +217,8 @@ static int group_bind(cfs_group* G, int nplans, const cfs_plan_t* plans, cudaStr
     const double dx = P->lx / P->nx, dy = P->ly / P->ny;
     r.idx2 = 1.0 / (dx * dx);
     r.idy2 = 1.0 / (dy * dy);
-    r.neumann = (P->bc == CFS_BC_NEUMANN);
+    r.neumann = P->has_null;
+    r.ybc = P->ybc;
     G->res[b] = r;
     bres[b] = (int)((nxy + 127) / 128);
     bplane[b] = P->nz;

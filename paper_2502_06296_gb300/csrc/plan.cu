@@ -170,6 +170,8 @@ static void plan_free(cfs_plan* P) {
   cudaFree(P->d_r32);
   cudaFree(P->d_red);
   cudaFree(P->d_zop);
+  cudaFree(P->d_wy);
+  cudaFree(P->d_wy32);
 
   for (auto& h : P->helm) {
     cudaFree(h.d_rows);
@@ -187,10 +189,17 @@ static void plan_free(cfs_plan* P) {
 
 extern "C" int cfs_plan_create(cfs_plan_t* out, int nx, int ny, int nz, double lx, double ly,
                                const double* dz, int poisson_bc, int dtype) {
+  return cfs_plan_create_walls(out, nx, ny, nz, lx, ly, dz, poisson_bc, CFS_Y_PERIODIC, dtype);
+}
+
+extern "C" int cfs_plan_create_walls(cfs_plan_t* out, int nx, int ny, int nz, double lx,
+                                     double ly, const double* dz, int poisson_bc, int ybc,
+                                     int dtype) {
   if (!out) return CFS_EINVAL;
   *out = nullptr;
   if (!dz || !(lx > 0) || !(ly > 0) || !isfinite(lx) || !isfinite(ly)) return CFS_EINVAL;
   if (poisson_bc != CFS_BC_NEUMANN && poisson_bc != CFS_BC_DIRICHLET) return CFS_EINVAL;
+  if (ybc != CFS_Y_PERIODIC && ybc != CFS_Y_NEUMANN && ybc != CFS_Y_DIRICHLET) return CFS_EINVAL;
   if (dtype != CFS_F64 && dtype != CFS_F32_REFINED) return CFS_EUNSUPPORTED;
   // FP32 rows must be whole 16-byte units for the TMA copies
   if (dtype == CFS_F32_REFINED && nx % 4 != 0) return CFS_EUNSUPPORTED;
@@ -207,10 +216,12 @@ extern "C" int cfs_plan_create(cfs_plan_t* out, int nx, int ny, int nz, double l
   P->ny = ny;
   P->nz = nz;
   P->M = nx / 2;
-  P->nky = ny / 2 + 1;
+  P->nky = (ybc == CFS_Y_PERIODIC) ? ny / 2 + 1 : ny;
   P->lx = lx;
   P->ly = ly;
   P->bc = poisson_bc;
+  P->ybc = ybc;
+  P->has_null = (poisson_bc == CFS_BC_NEUMANN && ybc != CFS_Y_DIRICHLET);
   P->dzf.assign(dz, dz + nz);
   P->helm_clock = 0;
   P->device_bytes = 0;
@@ -262,7 +273,18 @@ extern "C" int cfs_plan_create(cfs_plan_t* out, int nx, int ny, int nz, double l
   const double dx = lx / nx, dy = ly / ny;
   std::vector<double> lamx(P->M + 1), lamy(P->nky);
   for (int k = 0; k <= P->M; ++k) lamx[k] = 2.0 * (cos(kTwoPi * k / nx) - 1.0) / (dx * dx);
-  for (int k = 0; k < P->nky; ++k) lamy[k] = 2.0 * (cos(kTwoPi * k / ny) - 1.0) / (dy * dy);
+  for (int k = 0; k < P->nky; ++k) {
+    // periodic: pairs +-ky; walls: cos(pi k (j+1/2)/Ny) (Neumann) or
+    // sin(pi (k+1)(j+1/2)/Ny) (Dirichlet) eigenvectors of the mirrored stencil
+    const double angle = (ybc == CFS_Y_PERIODIC) ? kTwoPi * k / ny
+                         : (ybc == CFS_Y_NEUMANN) ? 0.5 * kTwoPi * k / ny
+                                                  : 0.5 * kTwoPi * (k + 1) / ny;
+    lamy[k] = 2.0 * (cos(angle) - 1.0) / (dy * dy);
+  }
+  // wall transforms: w_k = exp(-i pi k / 2Ny)
+  std::vector<double2> wy;
+  if (ybc != CFS_Y_PERIODIC)
+    for (int k = 0; k < ny; ++k) wy.push_back(chanfs::root(k, 4 * ny));
   P->lamx_h = lamx;
   P->lamy_h = lamy;
   std::vector<double> A, B, C;
@@ -273,7 +295,7 @@ extern "C" int cfs_plan_create(cfs_plan_t* out, int nx, int ny, int nz, double l
   std::vector<double> sing(3 * (size_t)nz, 0.0);
   P->sing_sc = 2.0 / ((double)nx * (double)ny);  // the factor scale s
   P->sing_cg = 0.0;
-  if (poisson_bc == CFS_BC_NEUMANN) {
+  if (P->has_null) {
     std::vector<double> a(A), b(B), c(C), rhs(nz, 1.0), h(nz), g(nz);
     b[0] = 1.0;
     c[0] = 0.0;
@@ -325,6 +347,7 @@ extern "C" int cfs_plan_create(cfs_plan_t* out, int nx, int ny, int nz, double l
   if (!rc) rc = dev_upload(&P->d_post, post.data(), post.size(), &P->device_bytes);
   if (!rc) rc = dev_upload(&P->d_dzf, P->dzf.data(), (size_t)nz, &P->device_bytes);
   if (!rc) rc = dev_upload(&P->d_sing, sing.data(), sing.size(), &P->device_bytes);
+  if (!rc && !wy.empty()) rc = dev_upload(&P->d_wy, wy.data(), wy.size(), &P->device_bytes);
   if (!rc) rc = dev_upload<double2>(&P->d_fwd, nullptr, nfac, &P->device_bytes);
   if (!rc) rc = dev_upload<double>(&P->d_bwd, nullptr, nfac, &P->device_bytes);
   if (!rc) rc = dev_upload<int>(&P->d_status, nullptr, 1, &P->device_bytes);
@@ -339,6 +362,10 @@ extern "C" int cfs_plan_create(cfs_plan_t* out, int nx, int ny, int nz, double l
     rc = dev_upload(&P->d_twx32, twx32.data(), twx32.size(), &P->device_bytes);
     if (!rc) rc = dev_upload(&P->d_twy32, twy32.data(), twy32.size(), &P->device_bytes);
     if (!rc) rc = dev_upload(&P->d_post32, post32.data(), post32.size(), &P->device_bytes);
+    if (!rc && !wy.empty()) {
+      const std::vector<float2> wy32 = f32(wy);
+      rc = dev_upload(&P->d_wy32, wy32.data(), wy32.size(), &P->device_bytes);
+    }
     if (!rc) rc = dev_upload<float2>(&P->d_fwd32, nullptr, nfac, &P->device_bytes);
     if (!rc) rc = dev_upload<float>(&P->d_bwd32, nullptr, nfac, &P->device_bytes);
     if (!rc) rc = dev_upload<float>(&P->d_r32, nullptr, (size_t)nx * ny * nz, &P->device_bytes);
@@ -702,6 +729,7 @@ static int helm3_prepare(cfs_plan* P, double c, int loc, Helm3Coef** res) {
 
 extern "C" int cfs_helmholtz3d_prepare(cfs_plan_t P, double c, int loc) {
   if (!P) return CFS_EINVAL;
+  if (P->ybc != CFS_Y_PERIODIC) return CFS_EUNSUPPORTED;
   Helm3Coef* h = nullptr;
   return helm3_prepare(P, c, loc, &h);
 }
@@ -709,6 +737,7 @@ extern "C" int cfs_helmholtz3d_prepare(cfs_plan_t P, double c, int loc) {
 extern "C" int cfs_helmholtz3d_solve(cfs_plan_t P, double c, int loc, const double* rhs,
                                      double* u, void* stream) {
   if (!P || !rhs || !u || !aligned16(rhs) || !aligned16(u)) return CFS_EINVAL;
+  if (P->ybc != CFS_Y_PERIODIC) return CFS_EUNSUPPORTED;
   Helm3Coef* h = nullptr;
   int rc = helm3_prepare(P, c, loc, &h);
   if (rc) return rc;

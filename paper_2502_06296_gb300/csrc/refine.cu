@@ -90,7 +90,7 @@ __global__ void mean_final_kernel(const double* partial, int nz, const double* d
 __device__ __forceinline__ void poisson_residual_body(
     const double* __restrict__ f, const double* __restrict__ p, const double* __restrict__ zop,
     const double* __restrict__ mean, float* __restrict__ r32, unsigned int* rmax, int nx, int ny,
-    int nz, double idx2, double idy2, long long blk) {
+    int nz, double idx2, double idy2, int ybc, long long blk) {
   const long long nxy = (long long)nx * ny;
   const long long col = blk * blockDim.x + threadIdx.x;
   float vmax = 0.0f;
@@ -99,8 +99,18 @@ __device__ __forceinline__ void poisson_residual_body(
     const int i = (int)(col % nx), j = (int)(col / nx);
     const long long ip = (i + 1 == nx) ? col - i : col + 1;
     const long long im = (i == 0) ? col + nx - 1 : col - 1;
-    const long long jp = (j + 1 == ny) ? col - (long long)j * nx : col + nx;
-    const long long jm = (j == 0) ? col + (long long)(ny - 1) * nx : col - nx;
+    // y neighbours: periodic, or the mirror ghost of a wall (+p Neumann, -p Dirichlet)
+    long long jp, jm;
+    bool np_ = false, nm_ = false;  // negate the ghost
+    if (ybc == CFS_Y_PERIODIC) {
+      jp = (j + 1 == ny) ? col - (long long)j * nx : col + nx;
+      jm = (j == 0) ? col + (long long)(ny - 1) * nx : col - nx;
+    } else {
+      jp = (j + 1 == ny) ? col : col + nx;
+      jm = (j == 0) ? col : col - nx;
+      np_ = (ybc == CFS_Y_DIRICHLET) && (j + 1 == ny);
+      nm_ = (ybc == CFS_Y_DIRICHLET) && (j == 0);
+    }
     double pkm = 0.0, pk = p ? p[col] : 0.0;
     for (int k = 0; k < nz; ++k) {
       const long long o = (long long)k * nxy;
@@ -108,7 +118,8 @@ __device__ __forceinline__ void poisson_residual_body(
       double r = f[o + col] - mu;
       if (p) {
         const double sx = p[o + ip] + p[o + im];
-        const double sy = p[o + jp] + p[o + jm];
+        const double yp = p[o + jp], ym = p[o + jm];
+        const double sy = (np_ ? -yp : yp) + (nm_ ? -ym : ym);
         double t = zop[nz + k] * pk;
         t = fma(idx2, sx, t);
         t = fma(idy2, sy, t);
@@ -129,8 +140,8 @@ __device__ __forceinline__ void poisson_residual_body(
 __global__ void __launch_bounds__(kResBlock) poisson_residual_kernel(
     const double* __restrict__ f, const double* __restrict__ p, const double* __restrict__ zop,
     const double* __restrict__ mean, float* __restrict__ r32, unsigned int* rmax, int nx, int ny,
-    int nz, double idx2, double idy2) {
-  poisson_residual_body(f, p, zop, mean, r32, rmax, nx, ny, nz, idx2, idy2, blockIdx.x);
+    int nz, double idx2, double idy2, int ybc) {
+  poisson_residual_body(f, p, zop, mean, r32, rmax, nx, ny, nz, idx2, idy2, ybc, blockIdx.x);
 }
 
 // Helmholtz: u (+)= delta, then r = rhs - (I - c L_z) u, as FP32, and max |r|.
@@ -233,7 +244,7 @@ __global__ void __launch_bounds__(kResBlock) poisson_residual_group_kernel(const
   if (!group_block(g, &b, &blk)) return;
   const ResBox& r = boxes[b];
   poisson_residual_body(io[b].f, with_p ? io[b].p : nullptr, r.zop, r.neumann ? r.mean : nullptr,
-                        r.r32, r.rmax, r.nx, r.ny, r.nz, r.idx2, r.idy2, blk);
+                        r.r32, r.rmax, r.nx, r.ny, r.nz, r.idx2, r.idy2, r.ybc, blk);
 }
 
 __global__ void __launch_bounds__(kResBlock) helm_residual_group_kernel(const ResBox* boxes,
@@ -350,7 +361,7 @@ int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st) {
   const unsigned grid = (unsigned)((nxy + kResBlock - 1) / kResBlock);
   double* mean = nullptr;
   cudaError_t e = cudaSuccess;
-  if (P->bc == CFS_BC_NEUMANN) {  // remove the dz-weighted mean of f (compatibility)
+  if (P->has_null) {  // remove the dz-weighted mean of f (compatibility)
     mean = P->d_red + 1;
     plane_sum_kernel<<<P->nz, 256, 0, st>>>(f, nxy, P->d_dzf, P->d_red + 2);
     mean_final_kernel<<<1, 256, 0, st>>>(P->d_red + 2, P->nz, P->d_dzf, nxy, mean);
@@ -360,7 +371,8 @@ int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaMemsetAsync(P->d_red, 0, sizeof(unsigned int), st);
   if (e == cudaSuccess) {
     poisson_residual_kernel<<<grid, kResBlock, 0, st>>>(f, nullptr, P->d_zop, mean, P->d_r32,
-                                                        max_word(P), P->nx, P->ny, P->nz, idx2, idy2);
+                                                        max_word(P), P->nx, P->ny, P->nz, idx2,
+                                                        idy2, P->ybc);
     e = cudaGetLastError();
   }
   float fmax = 0.0f;
@@ -384,7 +396,7 @@ int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st) {
     if (e == cudaSuccess) {
       poisson_residual_kernel<<<grid, kResBlock, 0, st>>>(f, p, P->d_zop, mean, P->d_r32,
                                                           max_word(P), P->nx, P->ny, P->nz, idx2,
-                                                          idy2);
+                                                          idy2, P->ybc);
       e = cudaGetLastError();
     }
     float rmax = 0.0f;
@@ -395,7 +407,7 @@ int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st) {
     P->last_rho = (double)rmax / (double)fmax;
     if (P->last_rho <= P->tol) break;
   }
-  if (P->bc == CFS_BC_NEUMANN) {
+  if (P->has_null) {
     // The residual cannot see a constant, so the FP32 rounding of each
     // correction's mean accumulates unchecked; restore the zero dz-weighted
     // mean of p in FP64.

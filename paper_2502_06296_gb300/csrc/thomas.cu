@@ -163,7 +163,10 @@ __device__ __forceinline__ void thomas_body(const ThomasArgs& a, int blk) {
   if (j >= a.M) return;
   // factor sets of the real (x) and imaginary (y) parts
   int kx_x = j, kx_y = j, kp_x, kp_y;
-  if (j > 0) {
+  if (a.ywall) {  // every slot its own column; column 0 holds the real pair F(0) + i F(M)
+    kp_x = kp_y = ky;
+    if (j == 0) kx_y = a.M;
+  } else if (j > 0) {
     kp_x = kp_y = min(ky, a.ny - ky);
   } else if (2 * ky == 0 || 2 * ky == a.ny) {  // real pair F(0,ky) + i F(M,ky)
     kp_x = kp_y = ky;
@@ -407,7 +410,10 @@ __global__ void __launch_bounds__(2 * TW) thomas_tile_kernel(const __grid_consta
     const int j = j0 + c;
     if (j < a.M) {
       int kx = j, kp;
-      if (j > 0) {
+      if (a.ywall) {
+        kp = ky;
+        if (j == 0 && comp) kx = a.M;
+      } else if (j > 0) {
         kp = min(ky, a.ny - ky);
       } else if (2 * ky == 0 || 2 * ky == a.ny) {  // real pair F(0,ky) + i F(M,ky)
         kp = ky;
@@ -458,9 +464,10 @@ static ThomasArgs thomas_args(const cfs_plan* P, void* data) {
   a.nz = P->nz;
   a.nky = P->nky;
   a.nblk_x = (P->M + kThomasBlock - 1) / kThomasBlock;
-  a.neumann = (P->bc == CFS_BC_NEUMANN);
+  a.neumann = P->has_null;
   a.kx64 = P->kx64;
   a.ky64 = P->ky64;
+  a.ywall = (P->ybc != CFS_Y_PERIODIC);
   return a;
 }
 
@@ -619,7 +626,7 @@ cudaError_t launch_thomas_set(const cfs_plan* P, double* data, const double2* fw
   a.bwd32 = nullptr;
   a.nz = n;
   a.neumann = 0;
-  a.kx64 = a.ky64 = 0;
+  a.kx64 = a.ky64 = 0;  // (ywall as for the plan)
   thomas_kernel<double2><<<a.nblk_x * P->ny, kThomasBlock, 0, st>>>(a);
   return cudaGetLastError();
 }
@@ -630,7 +637,7 @@ cudaError_t launch_thomas_factor(cfs_plan* P, const double* dA, const double* dB
   dim3 grid((P->M + 1 + 127) / 128, P->nky);
   thomas_factor_kernel<<<grid, 128, 0, st>>>(P->d_fwd, P->d_bwd, P->d_fwd32, P->d_bwd32, dA, dB,
                                              dC, dlamx, dlamy, P->M, P->nky, P->nz, s,
-                                             P->bc == CFS_BC_NEUMANN);
+                                             P->has_null);
   return cudaGetLastError();
 }
 

@@ -124,6 +124,7 @@ POISSON_CASES = [
     ((48, 36, 20), 1.8, 0),       # stretched, ragged y tiles
     ((48, 36, 20), 1.8, 1),
     ((6, 9, 5), 1.2, 0),          # odd complex lengths
+    ((6, 27, 5), 1.2, 1),         # odd y pass count: the result tile in the second buffer
     ((2, 1, 3), None, 0),         # degenerate: one x pair, ny = 1, nz = 3
     ((8, 1, 16), 1.5, 1),
     ((64, 384, 12), 1.8, 0),      # two TMA boxes along y
