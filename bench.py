@@ -270,6 +270,7 @@ def run_mixed(chanfs, torch, device, reps: int = 5, warmup: int = 3, nz: int = 0
     out, res = {}, {}
     for name, dtype in (("f64", chanfs.F64), ("f32_refined", chanfs.F32_REFINED)):
         with chanfs.Plan(nx, ny, nz, cfg["lx"], cfg["ly"], dz, chanfs.NEUMANN, dtype) as plan:
+            tuned = plan.autotune()  # kernel shapes by measurement, for both plans
             p = torch.empty_like(f)
             for _ in range(warmup):
                 plan.poisson_solve(f, out=p)
@@ -286,7 +287,7 @@ def run_mixed(chanfs, torch, device, reps: int = 5, warmup: int = 3, nz: int = 0
             ms = [ev[r].elapsed_time(ev[r + 1]) for r in range(reps)]
             entry = {"ms": round(statistics.median(ms), 4),
                      "ns_per_pt": statistics.median(ms) * 1e6 / npts,
-                     "device_status": plan.check()}
+                     "device_status": plan.check(), "kernel_shapes": tuned}
             if iters:
                 entry["fp32_solves"] = max(i for i, _ in iters)
                 entry["rel_residual"] = max(r for _, r in iters)

@@ -390,6 +390,15 @@ int cfs_plan_get_option(cfs_plan_t plan, int option, int* value);
 int cfs_plan_autotune(cfs_plan_t plan, void* stream);
 
 /*
+ * cfs_selfcheck_conversions -- a diagnostic with no counterpart in the paper.
+ * The refinement kernels convert between FP32 and FP64 on the integer units
+ * (the hardware conversions share the scarce FP64 pipe); this runs `samples`
+ * hashed operands (any double, exact rounding ties, any float) through both
+ * and reports in *mismatches how many results differ in any bit (0 expected).
+ */
+int cfs_selfcheck_conversions(unsigned long long samples, unsigned long long* mismatches);
+
+/*
  * cfs_plan_check -- wait for the device and report device-side failures
  * recorded since the last check (then clear them).  *device_error (may be
  * NULL) receives the raw failure bits.  Returns CFS_ETIMEOUT if a bounded

@@ -86,6 +86,7 @@ def lib():
             "cfs_helmholtz3d_prepare": ([vp, d, i], i),
             "cfs_helmholtz3d_solve": ([vp, d, i, vp, vp, vp], i),
             "cfs_plan_set_option": ([vp, i, i], i),
+            "cfs_selfcheck_conversions": ([ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_ulonglong)], i),
             "cfs_group_reserve": ([ctypes.POINTER(vp), i], i),
             "cfs_group_rebind": ([vp, i, ctypes.POINTER(vp), vp], i),
             "cfs_server_create": ([ctypes.POINTER(vp), ctypes.c_size_t, i, i, i], i),
@@ -442,6 +443,15 @@ class Server:
         st = ServerStats()
         _check(lib().cfs_server_stats(self._h, ctypes.byref(st)), "cfs_server_stats")
         return {name: getattr(st, name) for name, _ in ServerStats._fields_}
+
+
+def selfcheck_conversions(samples: int = 1 << 22) -> int:
+    """Bit mismatches of the library's FP32 <-> FP64 conversions against the
+    hardware's over `samples` hashed operands (cfs_selfcheck_conversions)."""
+    bad = ctypes.c_ulonglong(0)
+    _check(lib().cfs_selfcheck_conversions(int(samples), ctypes.byref(bad)),
+           "cfs_selfcheck_conversions")
+    return bad.value
 
 
 def _host_ptr(a, shape):

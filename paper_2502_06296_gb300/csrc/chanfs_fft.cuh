@@ -224,14 +224,20 @@ __device__ C* stockham_smem(C* a, C* b, const FftDesc& d, int nb, int es, int bs
     const C* twp = tw + d.twoff[p];
     const int nbf = n / R;
     const int total = nbf * nb;
+    // (fast, slow) index of work item t, stepped by blockDim.x without a
+    // division per item: the fast index runs over batches (BATCH_FAST) or
+    // butterflies
+    const int nfast = BATCH_FAST ? nb : nbf;
+    const int sfast = blockDim.x % nfast, sslow = blockDim.x / nfast;
+    int fi = threadIdx.x % nfast, si = threadIdx.x / nfast;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      int bat, j;
-      if (BATCH_FAST) {
-        bat = t % nb;
-        j = t / nb;
-      } else {
-        j = t % nbf;
-        bat = t / nbf;
+      const int bat = BATCH_FAST ? fi : si;
+      const int j = BATCH_FAST ? si : fi;
+      fi += sfast;
+      si += sslow;
+      if (fi >= nfast) {
+        fi -= nfast;
+        ++si;
       }
       const C* in = a + bat * bs;
       C* out = b + bat * bs;

@@ -38,6 +38,7 @@ struct XBox {  // packed real FFT along x (fft_x.cu)
   const void* post;
   long long nlines;
   int lb;
+  int* status;
 };
 
 struct YBox {  // FFT along y on TMA tiles (fft_y.cu); the map is 64-byte aligned

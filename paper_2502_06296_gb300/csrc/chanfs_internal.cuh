@@ -215,6 +215,35 @@ inline cudaError_t allow_max_smem(K kernel) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
 }
 
+// Conversions between FP32 and FP64 on the integer units.  On GB300 the
+// hardware conversion instructions share the FP64 pipe (2 lanes per SM per
+// clock), which the refinement kernels already saturate; these produce the
+// same bits (IEEE 754 binary32 <-> binary64, round to nearest even) from the
+// fields of the encodings, and hand the rare operands (zero, subnormal,
+// infinite, NaN, out of range) to the hardware conversion.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if ((u & 0x7fffffffu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+  if (e == 0u || e == 0xffu) return (double)f;
+  // exponent bias 127 -> 1023; 23 mantissa bits -> the top of 52
+  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xfffffu);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  if (e < 897u || e > 1150u) return __double2float_rn(x);  // not a normal binary32
+  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);  // the top 23 mantissa bits
+  const unsigned rest = lo & 0x1fffffffu;                  // the 29 dropped bits
+  unsigned bits = (hi & 0x80000000u) | ((e - 896u) << 23) | m;
+  // round to nearest, ties to even; a carry out of the mantissa raises the
+  // exponent (and reaches infinity past the largest binary32)
+  bits += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  return __uint_as_float(bits);
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }

@@ -16,116 +16,146 @@
 // it to an FP64 field (OUT_ADD), the correction step p += delta.
 #include "chanfs_fft.cuh"
 #include "chanfs_group.cuh"
+#include "chanfs_tma.cuh"
 
 namespace chanfs {
 
-// Block `blk` of the transform: lines [blk * lb, blk * lb + lb).
+// Block `blk` of the transform: lines [blk * lb, blk * lb + lb).  The lines
+// of a block are one contiguous span: a bulk copy brings it into shared
+// memory and another writes the result back, so the global traffic is two
+// large asynchronous transfers per block and no thread computes an address
+// per element.
 template <bool INV, class C, int OUT>
 __device__ __forceinline__ void rfft_x_body(const C* in, void* outv, long long nlines,
                                             const FftDesc& d, const C* __restrict__ twg,
                                             const C* __restrict__ postg, int lb, double scale,
-                                            int scaled, long long blk) {
+                                            int scaled, int* status, long long blk) {
   using T = typename cscal<C>::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int M = d.n;
   const int bs = M;  // batch stride (complex)
-  C* buf0 = reinterpret_cast<C*>(smem_raw);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  C* buf0 = reinterpret_cast<C*>(smem_raw + 128);
   C* buf1 = buf0 + lb * bs;
   C* tw = buf1 + lb * bs;
   C* post = tw + d.ntw;
   const int npost = M / 2 + 1;
-
-  for (int e = threadIdx.x; e < d.ntw; e += blockDim.x) tw[e] = twg[e];
-  for (int e = threadIdx.x; e < npost; e += blockDim.x) post[e] = postg[e];
-
   const long long line0 = blk * lb;
+  const int valid = (int)min((long long)lb, nlines - line0);  // lines of this block
+  const uint32_t span = (uint32_t)((size_t)valid * M * sizeof(C));
   const C zero = mkc<C>(T(0), T(0));
   const T h = T(0.5);
 
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(bar, span);
+    bulk_load(INV ? buf1 : buf0, in + line0 * M, span, bar);
+  }
+  for (int e = threadIdx.x; e < d.ntw; e += blockDim.x) tw[e] = twg[e];
+  for (int e = threadIdx.x; e < npost; e += blockDim.x) post[e] = postg[e];
+  if (!INV)  // the lines past the end of the field transform zeros
+    for (int e = valid * M + threadIdx.x; e < lb * M; e += blockDim.x) buf0[e] = zero;
+  const int ok = __syncthreads_and(mbar_wait(bar, 0) ? 1 : 0);
+  if (!ok) {
+    if (threadIdx.x == 0) atomicOr(status, kErrTmaTimeout);
+    return;  // nothing is stored
+  }
+  // work item e of a line-major loop over (line l, index k < npost), stepped
+  // by blockDim.x without a division per item
+  const int sk = blockDim.x % npost, sl = blockDim.x / npost;
+
   if (!INV) {
-    C* out = reinterpret_cast<C*>(outv);
-    // contiguous span of lb*M complex values
-    const C* src = in + line0 * M;
-    for (int e = threadIdx.x; e < lb * M; e += blockDim.x) {
-      int l = e / M;
-      buf0[e] = (line0 + l < nlines) ? src[e] : zero;
-    }
-    __syncthreads();
     C* Z = stockham_smem<false, false>(buf0, buf1, d, lb, 1, bs, tw);
+    C* ob = (Z == buf0) ? buf1 : buf0;
     // untangle the half-length spectrum into the packed real spectrum
-    for (int e = threadIdx.x; e < lb * npost; e += blockDim.x) {
-      int l = e / npost, k = e % npost;
-      long long line = line0 + l;
-      if (line >= nlines) continue;
+    int l = threadIdx.x / npost, k = threadIdx.x % npost;
+    for (int e = threadIdx.x; e < valid * npost; e += blockDim.x) {
       const C* z = Z + l * bs;
-      C* o = out + line * M;
+      C* o = ob + l * bs;
       if (k == 0) {
-        C z0 = z[0];
+        const C z0 = z[0];
         o[0] = mkc<C>(z0.x + z0.y, z0.x - z0.y);  // (X_0, X_M)
-        continue;
+      } else {
+        const C zk = z[k], zm = z[M - k];
+        const C E = mkc<C>(zk.x + zm.x, zk.y - zm.y);
+        const C O = mkc<C>(zk.x - zm.x, zk.y + zm.y);
+        const C u = cmul(O, post[k]);  // (W^k/2) O
+        const C t = mkc<C>(u.y, -u.x);  // -i (W^k/2) O
+        o[k] = mkc<C>(fma(h, E.x, t.x), fma(h, E.y, t.y));
+        if (M - k != k) o[M - k] = mkc<C>(fma(h, E.x, -t.x), fma(-h, E.y, t.y));
       }
-      C zk = z[k], zm = z[M - k];
-      C E = mkc<C>(zk.x + zm.x, zk.y - zm.y);
-      C O = mkc<C>(zk.x - zm.x, zk.y + zm.y);
-      C u = cmul(O, post[k]);          // (W^k/2) O
-      C t = mkc<C>(u.y, -u.x);         // -i (W^k/2) O
-      o[k] = mkc<C>(fma(h, E.x, t.x), fma(h, E.y, t.y));
-      if (M - k != k) o[M - k] = mkc<C>(fma(h, E.x, -t.x), fma(-h, E.y, t.y));
+      k += sk;
+      l += sl;
+      if (k >= npost) {
+        k -= npost;
+        ++l;
+      }
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      bulk_store(reinterpret_cast<C*>(outv) + line0 * M, ob, span);
+      tma_store_commit_and_wait_read();
     }
   } else {
-    __syncthreads();  // the untangling factors are read right away
     // re-tangle: Z_k = E/2 + i conj(W^k/2) T,  T = X_k - conj X_{M-k}
+    int l = threadIdx.x / npost, k = threadIdx.x % npost;
     for (int e = threadIdx.x; e < lb * npost; e += blockDim.x) {
-      int l = e / npost, k = e % npost;
-      long long line = line0 + l;
       C* z = buf0 + l * bs;
-      if (line >= nlines) {
-        z[k] = zero;
-        if (k > 0) z[M - k] = zero;
-        continue;
-      }
-      const C* x = in + line * M;
       C zk, zm;
-      if (k == 0) {
-        C x0 = x[0];  // (X_0, X_M)
+      if (l >= valid) {
+        zk = zm = zero;
+      } else if (k == 0) {
+        const C x0 = buf1[l * bs];  // (X_0, X_M)
         zk = mkc<C>(h * (x0.x + x0.y), h * (x0.x - x0.y));
         zm = zk;
       } else {
-        C xk = x[k], xm = x[M - k];
-        C E = mkc<C>(xk.x + xm.x, xk.y - xm.y);
-        C Tt = mkc<C>(xk.x - xm.x, xk.y + xm.y);
-        C u = cmulc(Tt, post[k]);  // conj(W^k/2) T
+        const C* x = buf1 + l * bs;
+        const C xk = x[k], xm = x[M - k];
+        const C E = mkc<C>(xk.x + xm.x, xk.y - xm.y);
+        const C Tt = mkc<C>(xk.x - xm.x, xk.y + xm.y);
+        const C u = cmulc(Tt, post[k]);  // conj(W^k/2) T
         zk = mkc<C>(fma(h, E.x, -u.y), fma(h, E.y, u.x));
         zm = mkc<C>(fma(h, E.x, u.y), fma(-h, E.y, u.x));
       }
       if (scaled) {
         const T sc = T(scale);
-        zk.x *= sc; zk.y *= sc;
-        zm.x *= sc; zm.y *= sc;
+        zk.x *= sc;
+        zk.y *= sc;
+        zm.x *= sc;
+        zm.y *= sc;
       }
       z[k] = zk;
       if (k > 0 && M - k != k) z[M - k] = zm;
+      k += sk;
+      l += sl;
+      if (k >= npost) {
+        k -= npost;
+        ++l;
+      }
     }
     __syncthreads();
     C* res = stockham_smem<true, false>(buf0, buf1, d, lb, 1, bs, tw);
     if (OUT == OUT_SAME) {
-      C* dst = reinterpret_cast<C*>(outv) + line0 * M;
-      for (int e = threadIdx.x; e < lb * M; e += blockDim.x) {
-        int l = e / M;
-        if (line0 + l < nlines) dst[e] = res[e];
+      fence_proxy_async();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        bulk_store(reinterpret_cast<C*>(outv) + line0 * M, res, span);
+        tma_store_commit_and_wait_read();
       }
     } else {
       double2* dst = reinterpret_cast<double2*>(outv) + line0 * M;
-      for (int e = threadIdx.x; e < lb * M; e += blockDim.x) {
-        int l = e / M;
-        if (line0 + l < nlines) {
-          const C r = res[e];
-          if (OUT == OUT_SET) {
-            dst[e] = make_double2((double)r.x, (double)r.y);
-          } else {
-            double2 p = dst[e];
-            dst[e] = make_double2(p.x + (double)r.x, p.y + (double)r.y);
-          }
+      for (int e = threadIdx.x; e < valid * M; e += blockDim.x) {
+        const C r = res[e];
+        if (OUT == OUT_SET) {
+          dst[e] = make_double2(f32_to_f64(r.x), f32_to_f64(r.y));
+        } else {
+          const double2 p = dst[e];
+          dst[e] = make_double2(p.x + f32_to_f64(r.x), p.y + f32_to_f64(r.y));
         }
       }
     }
@@ -136,8 +166,9 @@ template <bool INV, class C, int OUT>
 __global__ void __launch_bounds__(128) rfft_x_kernel(const C* in, void* outv, long long nlines,
                                                      FftDesc d, const C* __restrict__ twg,
                                                      const C* __restrict__ postg, int lb,
-                                                     double scale, int scaled) {
-  rfft_x_body<INV, C, OUT>(in, outv, nlines, d, twg, postg, lb, scale, scaled, blockIdx.x);
+                                                     double scale, int scaled, int* status) {
+  rfft_x_body<INV, C, OUT>(in, outv, nlines, d, twg, postg, lb, scale, scaled, status,
+                           blockIdx.x);
 }
 
 // One launch for several boxes (FP32 inner solves of grouped refinement):
@@ -151,7 +182,7 @@ __global__ void __launch_bounds__(128) rfft_x_group_kernel(const XBox* boxes, Gr
   void* out = (OUT == OUT_SAME) ? x.out : static_cast<void*>(io[b].p);
   rfft_x_body<INV, float2, OUT>(static_cast<const float2*>(x.in), out, x.nlines, x.d,
                                 static_cast<const float2*>(x.tw),
-                                static_cast<const float2*>(x.post), x.lb, 1.0, 0, blk);
+                                static_cast<const float2*>(x.post), x.lb, 1.0, 0, x.status, blk);
 }
 
 int x_lines_per_cta(const cfs_plan* P, size_t csize) {
@@ -162,7 +193,7 @@ int x_lines_per_cta(const cfs_plan* P, size_t csize) {
 }
 
 size_t x_smem_bytes(const cfs_plan* P, int lines, size_t csize) {
-  return csize * (size_t)(2 * lines * P->M + P->fx.ntw + P->M / 2 + 1);
+  return 128 + csize * (size_t)(2 * lines * P->M + P->fx.ntw + P->M / 2 + 1);
 }
 
 template <class C, int OUT>
@@ -177,11 +208,13 @@ static cudaError_t launch_x(const cfs_plan* P, const void* in, void* out, bool i
   if (!inverse) {
     auto k = rfft_x_kernel<false, C, OUT_SAME>;
     allow_max_smem(k);
-    k<<<(unsigned)grid, 128, smem, st>>>(cin, out, nlines, P->fx, tw, post, lb, scale, scaled);
+    k<<<(unsigned)grid, 128, smem, st>>>(cin, out, nlines, P->fx, tw, post, lb, scale, scaled,
+                                         P->d_status);
   } else {
     auto k = rfft_x_kernel<true, C, OUT>;
     allow_max_smem(k);
-    k<<<(unsigned)grid, 128, smem, st>>>(cin, out, nlines, P->fx, tw, post, lb, scale, scaled);
+    k<<<(unsigned)grid, 128, smem, st>>>(cin, out, nlines, P->fx, tw, post, lb, scale, scaled,
+                                         P->d_status);
   }
   return cudaGetLastError();
 }
@@ -211,6 +244,7 @@ size_t x_group_box(const cfs_plan* P, bool inverse, XBox* box, int* blocks) {
   box->post = P->d_post32;
   box->nlines = (long long)P->ny * P->nz;
   box->lb = lb;
+  box->status = P->d_status;
   *blocks = (int)((box->nlines + lb - 1) / lb);
   return x_smem_bytes(P, lb, sizeof(float2));
 }

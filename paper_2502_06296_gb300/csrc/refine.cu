@@ -86,7 +86,8 @@ __global__ void mean_final_kernel(const double* partial, int nz, const double* d
 // r = (f - mean) - L p, written as FP32, and max |r|.  One thread per (x, y)
 // column marching up in z with p_{k-1}, p_k, p_{k+1} in registers; the x and
 // y neighbours of a plane are shared through L1.  p == nullptr: r = f - mean.
-// zop = [A_k | B_k - 2/dx^2 - 2/dy^2 | C_k]; FP64: 9 instructions per point.
+// zop = [A_k | B_k - 2/dx^2 - 2/dy^2 | C_k]; FP64: 8 instructions per point
+// (the FP32 rounding of r runs on the integer units).
 __device__ __forceinline__ void poisson_residual_body(
     const double* __restrict__ f, const double* __restrict__ p, const double* __restrict__ zop,
     const double* __restrict__ mean, float* __restrict__ r32, unsigned int* rmax, int nx, int ny,
@@ -115,19 +116,21 @@ __device__ __forceinline__ void poisson_residual_body(
     for (int k = 0; k < nz; ++k) {
       const long long o = (long long)k * nxy;
       const double pkp = (p && k + 1 < nz) ? p[o + nxy + col] : 0.0;
-      double r = f[o + col] - mu;
-      if (p) {
+      double r;
+      if (p) {  // r = f - (mean + L p); the mean rides in the first FMA
         const double sx = p[o + ip] + p[o + im];
         const double yp = p[o + jp], ym = p[o + jm];
         const double sy = (np_ ? -yp : yp) + (nm_ ? -ym : ym);
-        double t = zop[nz + k] * pk;
+        double t = fma(zop[nz + k], pk, mu);
         t = fma(idx2, sx, t);
         t = fma(idy2, sy, t);
         t = fma(zop[k], pkm, t);
         t = fma(zop[2 * nz + k], pkp, t);
-        r -= t;
+        r = f[o + col] - t;
+      } else {
+        r = f[o + col] - mu;
       }
-      const float rf = (float)r;
+      const float rf = f64_to_f32(r);
       r32[o + col] = rf;
       vmax = fmaxf(vmax, fabsf(rf));
       pkm = pk;
@@ -160,7 +163,7 @@ __device__ __forceinline__ void helm_residual_body(const double* __restrict__ rh
   if (col < ncols && mode == 0) {  // r = rhs: (I - c L_z) 0 vanishes exactly
     for (int k = 0; k < n; ++k) {
       const long long o = (long long)k * ncols + col;
-      const float rf = (float)rhs[o];
+      const float rf = f64_to_f32(rhs[o]);
       r32[o] = rf;
       vmax = fmaxf(vmax, fabsf(rf));
     }
@@ -169,7 +172,7 @@ __device__ __forceinline__ void helm_residual_body(const double* __restrict__ rh
     auto update = [&](int k) -> double {
       const long long o = (long long)k * ncols + col;
       if (mode == 0) return 0.0;
-      const double d = (double)r32[o];
+      const double d = f32_to_f64(r32[o]);
       const double v = (mode == 1) ? d : u[o] + d;
       u[o] = v;
       return v;
@@ -181,7 +184,7 @@ __device__ __forceinline__ void helm_residual_body(const double* __restrict__ rh
       double t = abc[n + k] * uk;
       t = fma(abc[k], um, t);
       t = fma(abc[2 * n + k], up, t);
-      const float rf = (float)(rhs[o] - t);
+      const float rf = f64_to_f32(rhs[o] - t);
       r32[o] = rf;
       vmax = fmaxf(vmax, fabsf(rf));
       um = uk;
@@ -340,6 +343,33 @@ cudaError_t launch_group_fmax(const ResBox* boxes, int nbox, float* fmax, cudaSt
   return cudaGetLastError();
 }
 
+// ----------------------------------------------------------------------------
+// Self-check of the integer-unit conversions against the hardware's: sample
+// i is a hashed 64-bit pattern (any double: every exponent, the special
+// values), the same with its 29 dropped mantissa bits set to an exact tie
+// inside the binary32 range, and its low 32 bits as a float.
+// ----------------------------------------------------------------------------
+__global__ void conversion_check_kernel(unsigned long long n, unsigned long long* bad) {
+  unsigned long long local = 0;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    unsigned long long z = (i + 1) * 0x9E3779B97F4A7C15ull;  // splitmix64 of the counter
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const double x = __longlong_as_double((long long)z);
+    local += __float_as_uint(f64_to_f32(x)) != __float_as_uint(__double2float_rn(x));
+    const unsigned long long e = 897ull + ((z >> 52) % 254ull);  // a binary32 exponent
+    const unsigned long long t =
+        (z & 0x800FFFFFE0000000ull) | (e << 52) | 0x10000000ull;  // exact tie
+    const double xt = __longlong_as_double((long long)t);
+    local += __float_as_uint(f64_to_f32(xt)) != __float_as_uint(__double2float_rn(xt));
+    const float f = __uint_as_float((unsigned)z);
+    local += __double_as_longlong(f32_to_f64(f)) != __double_as_longlong((double)f);
+  }
+  if (local) atomicAdd(bad, local);
+}
+
 static int cuda_rc(cudaError_t e) { return e == cudaSuccess ? CFS_OK : CFS_ECUDA; }
 
 // Reads back the max-norm word (one synchronisation of st).
@@ -454,3 +484,19 @@ int refine_helmholtz(cfs_plan* P, const HelmCoef& h, const double* rhs, double* 
 }
 
 }  // namespace chanfs
+
+extern "C" int cfs_selfcheck_conversions(unsigned long long samples,
+                                         unsigned long long* mismatches) {
+  if (!mismatches || samples == 0) return CFS_EINVAL;
+  unsigned long long* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(d, 0, sizeof(unsigned long long));
+  if (e == cudaSuccess) {
+    chanfs::conversion_check_kernel<<<1216, 256>>>(samples, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpy(mismatches, d, sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return e == cudaSuccess ? CFS_OK : CFS_ECUDA;
+}

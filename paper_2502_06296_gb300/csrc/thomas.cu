@@ -25,7 +25,11 @@ namespace chanfs {
 
 
 constexpr int kThomasBlock = 64;
-constexpr int kPrefetch = 3;
+// Rows each thread keeps in flight ahead of its sweep (by arithmetic type): an
+// FP64 sweep is bound by the FP64 pipe and needs few; an FP32 sweep is bound
+// by memory latency.
+template <class CA> struct prefetch_rows { static constexpr int value = 3; };
+template <> struct prefetch_rows<float2> { static constexpr int value = 6; };
 
 template <class C> struct cplx_traits;
 template <> struct cplx_traits<double2> {
@@ -42,7 +46,7 @@ template <class CA, class CS> __device__ __forceinline__ CA cvt(CS v) {
 
 // One column sweep: storage type CS (the spectrum), arithmetic type CA with
 // its factor tables F (pairs) and B (scalars).  Pointers step by a row stride
-// and each thread keeps the next kPrefetch rows in flight while the recurrence
+// and each thread keeps the next prefetch_rows<CA> rows in flight while the recurrence
 // consumes the current one (the sweep is sequential in k, and there are only
 // a few warps per SM, so this in-thread prefetch is what hides the memory
 // latency).  Real and imaginary parts use factor sets x and y, which differ
@@ -61,34 +65,35 @@ __device__ __forceinline__ void sweep_column(const ThomasArgs& a, CS* const s0, 
                                              const F2* const fy0, const F1* const bx0,
                                              const F1* const by0, const bool sing) {
   using T = typename cplx_traits<CA>::T;
+  constexpr int PF = prefetch_rows<CA>::value;
   const int nz = a.nz;
   const long long rs = (long long)a.ny * a.M;         // spectrum row stride
   const long long rt = (long long)a.nky * (a.M + 1);  // factor row stride
 
   // forward: g_k = (s/piv_k) f_k - (A_k/piv_k) g_{k-1}, in place
-  CS qu[kPrefetch];
-  F2 qx[kPrefetch], qy[kPrefetch];
+  CS qu[PF];
+  F2 qx[PF], qy[PF];
 #pragma unroll
-  for (int i = 0; i < kPrefetch; ++i) {
+  for (int i = 0; i < PF; ++i) {
     if (i < nz) {
       qu[i] = s0[i * rs];
       qx[i] = fx0[i * rt];
       qy[i] = fy0[i * rt];
     }
   }
-  const CS* pu = s0 + kPrefetch * rs;  // next rows to prefetch
-  const F2* px = fx0 + kPrefetch * rt;
-  const F2* py = fy0 + kPrefetch * rt;
+  const CS* pu = s0 + PF * rs;  // next rows to prefetch
+  const F2* px = fx0 + PF * rt;
+  const F2* py = fy0 + PF * rt;
   CS* ps = s0;                         // row being written
   CA g = cplx_traits<CA>::mk(T(0), T(0));
   double mu = 0.0, gam = 0.0;
-  for (int k = 0; k < nz; k += kPrefetch) {
+  for (int k = 0; k < nz; k += PF) {
 #pragma unroll
-    for (int i = 0; i < kPrefetch; ++i) {
+    for (int i = 0; i < PF; ++i) {
       if (k + i >= nz) break;
       CA u = cvt<CA>(qu[i]);
       const F2 fx = qx[i], fy = qy[i];
-      if (k + i + kPrefetch < nz) {
+      if (k + i + PF < nz) {
         qu[i] = *pu;
         qx[i] = *px;
         qy[i] = *py;
@@ -109,31 +114,31 @@ __device__ __forceinline__ void sweep_column(const ThomasArgs& a, CS* const s0, 
   const double nu = sing ? a.sing_sc * (gam - mu * a.sing_cg) : 0.0;
 
   // backward: x_k = g_k - (C_k/piv_k) x_{k+1}, from the top wall down
-  CS qg[kPrefetch];
-  F1 qbx[kPrefetch], qby[kPrefetch];
+  CS qg[PF];
+  F1 qbx[PF], qby[PF];
   CS* const s1 = s0 + (long long)(nz - 1) * rs;
   const F1* const bx1 = bx0 + (long long)(nz - 1) * rt;
   const F1* const by1 = by0 + (long long)(nz - 1) * rt;
 #pragma unroll
-  for (int i = 0; i < kPrefetch; ++i) {
+  for (int i = 0; i < PF; ++i) {
     if (i < nz) {
       qg[i] = s1[-i * rs];
       qbx[i] = bx1[-i * rt];
       qby[i] = by1[-i * rt];
     }
   }
-  const CS* pg = s1 - kPrefetch * rs;
-  const F1* pbx = bx1 - kPrefetch * rt;
-  const F1* pby = by1 - kPrefetch * rt;
+  const CS* pg = s1 - PF * rs;
+  const F1* pbx = bx1 - PF * rt;
+  const F1* pby = by1 - PF * rt;
   ps = s1;
   CA x = cplx_traits<CA>::mk(T(0), T(0));
-  for (int r = 0; r < nz; r += kPrefetch) {
+  for (int r = 0; r < nz; r += PF) {
 #pragma unroll
-    for (int i = 0; i < kPrefetch; ++i) {
+    for (int i = 0; i < PF; ++i) {
       if (r + i >= nz) break;
       const CA gg = cvt<CA>(qg[i]);
       const F1 bx = qbx[i], by = qby[i];
-      if (r + i + kPrefetch < nz) {
+      if (r + i + PF < nz) {
         qg[i] = *pg;
         qbx[i] = *pbx;
         qby[i] = *pby;

@@ -171,3 +171,9 @@ def test_refined_precision_workload_full_size(chanfs):
     ph = host(p)
     r = f - oracle.apply_poisson(ph, cfg["lx"], cfg["ly"], dz, 0)
     assert np.max(np.abs(r)) / np.max(np.abs(f)) < 2 * TOL
+
+
+def test_integer_unit_conversions_match_the_hardware(chanfs):
+    """The refinement's FP32 <-> FP64 conversions, done on the integer units,
+    give the hardware conversion's bits for every sampled operand."""
+    assert chanfs.selfcheck_conversions(1 << 24) == 0
