@@ -33,6 +33,7 @@ struct GroupIo {
 struct XBox {  // packed real FFT along x (fft_x.cu)
   FftDesc d;
   const void* in;
+  const void* in2;  // forward transforms of later refinement iterations read this
   void* out;
   const void* tw;
   const void* post;
@@ -74,6 +75,9 @@ struct ResBox {  // refinement residual and norms (refine.cu)
   double* partial;     // nz plane sums
   double* mean;        // dz-weighted mean
   float* r32;          // FP32 residual / correction
+  float* r32b;         // FP32 residual of the later iterations
+  double* r64;         // FP64 residual kept between iterations
+  const float* zop2;   // double-float split of zop, 1/dx^2, 1/dy^2
   unsigned int* rmax;  // max |r| (float bits)
   int nx, ny, nz, n;   // n = Helmholtz unknowns per column
   double idx2, idy2;
@@ -133,7 +137,7 @@ __device__ __forceinline__ bool group_block(const GroupMap& g, int* box, int* bl
 // Grouped launchers (one per translation unit).  `total` = start[nbox];
 // `smem` = the largest dynamic shared memory any box needs.
 cudaError_t launch_rfft_x_group32(const XBox* boxes, GroupMap g, int total, size_t smem,
-                                  bool inverse, int out_mode, const GroupIo* io,
+                                  bool inverse, int out_mode, const GroupIo* io, int alt_in,
                                   cudaStream_t st);
 cudaError_t launch_fft_y_group32(const YBox* boxes, GroupMap g, int total, size_t smem,
                                  bool inverse, cudaStream_t st);
@@ -162,7 +166,8 @@ enum {
   GSTAGE_MEAN_FINAL = 1,
   GSTAGE_RESIDUAL = 2,
   GSTAGE_SUBTRACT = 3,
-  GSTAGE_HELM_RESIDUAL = 4  // flag = mode of helm_residual_kernel
+  GSTAGE_HELM_RESIDUAL = 4,  // flag = mode of helm_residual_kernel
+  GSTAGE_UPDATE = 5          // r64 -= L delta (double-float), r32b and max
 };
 
 // Host-side descriptions of one plan's box for the grouped kernels.

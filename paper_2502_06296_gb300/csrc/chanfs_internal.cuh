@@ -129,6 +129,9 @@ struct cfs_plan {
   float* d_bwd32;
   int kx64, ky64;    // columns kx < kx64, min(ky, Ny-ky) < ky64 stay FP64
   float* d_r32;      // FP32 residual / correction field (in-place inner solve)
+  float* d_r32b;     // the FP32 residual of the later iterations (input of their solves)
+  double* d_r64;     // the FP64 residual kept between iterations
+  float* d_zop2;     // double-float split of zop and of 1/dx^2, 1/dy^2: hi[3nz+2] | lo[3nz+2]
   double* d_red;     // reduction scratch: [0] max |r| (float bits), [1] mean, [2..] partials
   double* d_zop;     // 3*nz doubles: A_k | B_k - 2/dx^2 - 2/dy^2 | C_k of the Poisson operator
   double tol;        // relative residual target

@@ -148,6 +148,14 @@ __device__ __forceinline__ void rfft_x_body(const C* in, void* outv, long long n
         tma_store_commit_and_wait_read();
       }
     } else {
+      if (OUT == OUT_ADD) {  // the correction stays behind for the residual update
+        fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          bulk_store(const_cast<C*>(in) + line0 * M, res, span);
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        }
+      }
       double2* dst = reinterpret_cast<double2*>(outv) + line0 * M;
       for (int e = threadIdx.x; e < valid * M; e += blockDim.x) {
         const C r = res[e];
@@ -158,6 +166,8 @@ __device__ __forceinline__ void rfft_x_body(const C* in, void* outv, long long n
           dst[e] = make_double2(p.x + f32_to_f64(r.x), p.y + f32_to_f64(r.y));
         }
       }
+      if (OUT == OUT_ADD && threadIdx.x == 0)
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     }
   }
 }
@@ -175,12 +185,13 @@ __global__ void __launch_bounds__(128) rfft_x_kernel(const C* in, void* outv, lo
 // the inverse's FP64 output goes to each box's solution in `io`.
 template <bool INV, int OUT>
 __global__ void __launch_bounds__(128) rfft_x_group_kernel(const XBox* boxes, GroupMap g,
-                                                           const GroupIo* io) {
+                                                           const GroupIo* io, int alt_in) {
   int b, blk;
   if (!group_block(g, &b, &blk)) return;
   const XBox& x = boxes[b];
   void* out = (OUT == OUT_SAME) ? x.out : static_cast<void*>(io[b].p);
-  rfft_x_body<INV, float2, OUT>(static_cast<const float2*>(x.in), out, x.nlines, x.d,
+  const float2* in = static_cast<const float2*>(alt_in ? x.in2 : x.in);
+  rfft_x_body<INV, float2, OUT>(in, out, x.nlines, x.d,
                                 static_cast<const float2*>(x.tw),
                                 static_cast<const float2*>(x.post), x.lb, 1.0, 0, x.status, blk);
 }
@@ -239,6 +250,7 @@ size_t x_group_box(const cfs_plan* P, bool inverse, XBox* box, int* blocks) {
   const int lb = x_lines_per_cta(P, sizeof(float2));
   box->d = P->fx;
   box->in = P->d_r32;
+  box->in2 = P->d_r32b;
   box->out = inverse ? nullptr : P->d_r32;
   box->tw = P->d_twx32;
   box->post = P->d_post32;
@@ -250,21 +262,21 @@ size_t x_group_box(const cfs_plan* P, bool inverse, XBox* box, int* blocks) {
 }
 
 cudaError_t launch_rfft_x_group32(const XBox* boxes, GroupMap g, int total, size_t smem,
-                                  bool inverse, int out_mode, const GroupIo* io,
+                                  bool inverse, int out_mode, const GroupIo* io, int alt_in,
                                   cudaStream_t st) {
   if (total <= 0) return cudaSuccess;
   if (!inverse) {
     auto k = rfft_x_group_kernel<false, OUT_SAME>;
     allow_max_smem(k);
-    k<<<total, 128, smem, st>>>(boxes, g, io);
+    k<<<total, 128, smem, st>>>(boxes, g, io, alt_in);
   } else if (out_mode == OUT_ADD) {
     auto k = rfft_x_group_kernel<true, OUT_ADD>;
     allow_max_smem(k);
-    k<<<total, 128, smem, st>>>(boxes, g, io);
+    k<<<total, 128, smem, st>>>(boxes, g, io, alt_in);
   } else {
     auto k = rfft_x_group_kernel<true, OUT_SET>;
     allow_max_smem(k);
-    k<<<total, 128, smem, st>>>(boxes, g, io);
+    k<<<total, 128, smem, st>>>(boxes, g, io, alt_in);
   }
   return cudaGetLastError();
 }

@@ -209,6 +209,9 @@ static int group_bind(cfs_group* G, int nplans, const cfs_plan_t* plans, cudaStr
     r.partial = P->d_red + 2;
     r.mean = P->d_red + 1;
     r.r32 = P->d_r32;
+    r.r32b = P->d_r32b;
+    r.r64 = P->d_r64;
+    r.zop2 = P->d_zop2;
     r.rmax = reinterpret_cast<unsigned int*>(P->d_red);
     r.nx = P->nx;
     r.ny = P->ny;
@@ -377,7 +380,8 @@ extern "C" int cfs_group_poisson_solve(cfs_group_t G, const double* const* f, do
   g.active = G->d_active;
   for (int it = 0; it < maxit && nactive > 0 && e == cudaSuccess; ++it) {
     g.start = G->d_sx;
-    e = launch_rfft_x_group32(G->d_xf, g, G->tx, G->smem_x, false, OUT_SAME, G->d_io, st);
+    e = launch_rfft_x_group32(G->d_xf, g, G->tx, G->smem_x, false, OUT_SAME, G->d_io, it >= 2,
+                              st);
     if (e == cudaSuccess) {
       g.start = G->d_sy;
       e = launch_fft_y_group32(G->d_y, g, G->ty, G->smem_y, false, st);
@@ -393,11 +397,12 @@ extern "C" int cfs_group_poisson_solve(cfs_group_t G, const double* const* f, do
     if (e == cudaSuccess) {
       g.start = G->d_sx;
       e = launch_rfft_x_group32(G->d_xi, g, G->tx, G->smem_x, true, it > 0 ? OUT_ADD : OUT_SET,
-                                G->d_io, st);
+                                G->d_io, 0, st);
     }
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess) {  // the first residual directly in FP64, then updates
       g.start = G->d_sres;
-      e = launch_group_refine_stage(GSTAGE_RESIDUAL, G->d_res, g, G->tres, G->d_io, 1, st);
+      e = launch_group_refine_stage(it == 0 ? GSTAGE_RESIDUAL : GSTAGE_UPDATE, G->d_res, g,
+                                    G->tres, G->d_io, 1, st);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(G->d_nactive, 0, sizeof(int), st);
     if (e == cudaSuccess)

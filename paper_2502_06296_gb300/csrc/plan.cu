@@ -168,6 +168,9 @@ static void plan_free(cfs_plan* P) {
   cudaFree(P->d_fwd32);
   cudaFree(P->d_bwd32);
   cudaFree(P->d_r32);
+  cudaFree(P->d_r32b);
+  cudaFree(P->d_r64);
+  cudaFree(P->d_zop2);
   cudaFree(P->d_red);
   cudaFree(P->d_zop);
   cudaFree(P->d_wy);
@@ -371,6 +374,20 @@ extern "C" int cfs_plan_create_walls(cfs_plan_t* out, int nx, int ny, int nz, do
     if (!rc) rc = dev_upload<float>(&P->d_r32, nullptr, (size_t)nx * ny * nz, &P->device_bytes);
     if (!rc) rc = dev_upload<double>(&P->d_red, nullptr, (size_t)nz + 8, &P->device_bytes);
     if (!rc) rc = dev_upload(&P->d_zop, zop.data(), zop.size(), &P->device_bytes);
+    // double-float split (hi = fl32(v), lo = fl32(v - hi)) of the operator's
+    // coefficients for the residual update r - L delta of later iterations
+    std::vector<double> coef(zop);
+    coef.push_back(1.0 / (dx * dx));
+    coef.push_back(1.0 / (dy * dy));
+    std::vector<float> z2(2 * coef.size());
+    for (size_t i = 0; i < coef.size(); ++i) {
+      const float hi = (float)coef[i];
+      z2[i] = hi;
+      z2[coef.size() + i] = (float)(coef[i] - (double)hi);
+    }
+    if (!rc) rc = dev_upload(&P->d_zop2, z2.data(), z2.size(), &P->device_bytes);
+    if (!rc) rc = dev_upload<float>(&P->d_r32b, nullptr, (size_t)nx * ny * nz, &P->device_bytes);
+    if (!rc) rc = dev_upload<double>(&P->d_r64, nullptr, (size_t)nx * ny * nz, &P->device_bytes);
   }
 
   if (!rc) rc = dev_upload(&dA, A.data(), A.size(), &scratch);

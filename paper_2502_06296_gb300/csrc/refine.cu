@@ -86,12 +86,14 @@ __global__ void mean_final_kernel(const double* partial, int nz, const double* d
 // r = (f - mean) - L p, written as FP32, and max |r|.  One thread per (x, y)
 // column marching up in z with p_{k-1}, p_k, p_{k+1} in registers; the x and
 // y neighbours of a plane are shared through L1.  p == nullptr: r = f - mean.
+// r64 (may be null) receives r in FP64 for the residual updates that follow.
 // zop = [A_k | B_k - 2/dx^2 - 2/dy^2 | C_k]; FP64: 8 instructions per point
 // (the FP32 rounding of r runs on the integer units).
 __device__ __forceinline__ void poisson_residual_body(
     const double* __restrict__ f, const double* __restrict__ p, const double* __restrict__ zop,
-    const double* __restrict__ mean, float* __restrict__ r32, unsigned int* rmax, int nx, int ny,
-    int nz, double idx2, double idy2, int ybc, long long blk) {
+    const double* __restrict__ mean, float* __restrict__ r32, double* __restrict__ r64,
+    unsigned int* rmax, int nx, int ny, int nz, double idx2, double idy2, int ybc,
+    long long blk) {
   const long long nxy = (long long)nx * ny;
   const long long col = blk * blockDim.x + threadIdx.x;
   float vmax = 0.0f;
@@ -132,6 +134,7 @@ __device__ __forceinline__ void poisson_residual_body(
       }
       const float rf = f64_to_f32(r);
       r32[o + col] = rf;
+      if (r64) r64[o + col] = r;
       vmax = fmaxf(vmax, fabsf(rf));
       pkm = pk;
       pk = pkp;
@@ -140,11 +143,105 @@ __device__ __forceinline__ void poisson_residual_body(
   block_max_to(vmax, rmax);
 }
 
+// ----------------------------------------------------------------------------
+// Residual update of the later iterations: r_new = r_old - L delta for the FP32
+// correction delta (exact FP32 values) just added to p.  L delta is formed in
+// double-float arithmetic on the FP32 units: each coefficient c is split as
+// hi + lo (hi = fl32(c), lo = fl32(c - hi)); hi * d is taken exactly as
+// p + e by TwoProd (an FMA gives e), lo * d is added to e, the p parts are
+// summed exactly by TwoSum and the small parts plainly.  The result holds
+// L delta to about 2^-48 of sum |c d|, and after the first correction
+// |delta| is small, so r_new is as accurate as a direct FP64 evaluation
+// (whose error is about 2^-53 ||L|| |p|).  FP64: 2 instructions per point.
+// The first residual of a solve (|delta| ~ |p|) stays the direct FP64 one.
+// ----------------------------------------------------------------------------
+struct DoubleFloat {
+  float s, e;
+};
+
+// s + t = a + b exactly (Knuth's TwoSum); the _rn intrinsics keep the
+// compiler from contracting or reassociating the steps.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void df_acc(DoubleFloat& acc, float chi, float clo, float d) {
+  const float p = __fmul_rn(chi, d);
+  float e = __fmaf_rn(chi, d, -p);  // chi * d - p, exact
+  e = __fmaf_rn(clo, d, e);
+  float s, t;
+  two_sum(acc.s, p, s, t);
+  acc.s = s;
+  acc.e = __fadd_rn(acc.e, __fadd_rn(t, e));
+}
+
+// z2 = hi[3nz + 2] | lo[3nz + 2]: the split zop rows, then 1/dx^2, 1/dy^2.
+__device__ __forceinline__ void poisson_update_body(const float* __restrict__ dlt,
+                                                    double* __restrict__ r64,
+                                                    float* __restrict__ r32,
+                                                    const float* __restrict__ z2,
+                                                    unsigned int* rmax, int nx, int ny, int nz,
+                                                    int ybc, long long blk) {
+  const long long nxy = (long long)nx * ny;
+  const long long col = blk * blockDim.x + threadIdx.x;
+  float vmax = 0.0f;
+  if (col < nxy) {
+    const int i = (int)(col % nx), j = (int)(col / nx);
+    const long long ip = (i + 1 == nx) ? col - i : col + 1;
+    const long long im = (i == 0) ? col + nx - 1 : col - 1;
+    long long jp, jm;
+    bool np_ = false, nm_ = false;
+    if (ybc == CFS_Y_PERIODIC) {
+      jp = (j + 1 == ny) ? col - (long long)j * nx : col + nx;
+      jm = (j == 0) ? col + (long long)(ny - 1) * nx : col - nx;
+    } else {
+      jp = (j + 1 == ny) ? col : col + nx;
+      jm = (j == 0) ? col : col - nx;
+      np_ = (ybc == CFS_Y_DIRICHLET) && (j + 1 == ny);
+      nm_ = (ybc == CFS_Y_DIRICHLET) && (j == 0);
+    }
+    const int nc = 3 * nz + 2;
+    const float axh = z2[3 * nz], axl = z2[nc + 3 * nz];
+    const float ayh = z2[3 * nz + 1], ayl = z2[nc + 3 * nz + 1];
+    float dkm = 0.0f, dk = dlt[col];
+    for (int k = 0; k < nz; ++k) {
+      const long long o = (long long)k * nxy;
+      const float dkp = (k + 1 < nz) ? dlt[o + nxy + col] : 0.0f;
+      const float yp = dlt[o + jp], ym = dlt[o + jm];
+      DoubleFloat acc{0.0f, 0.0f};
+      df_acc(acc, z2[nz + k], z2[nc + nz + k], dk);
+      df_acc(acc, axh, axl, dlt[o + ip]);
+      df_acc(acc, axh, axl, dlt[o + im]);
+      df_acc(acc, ayh, ayl, np_ ? -yp : yp);
+      df_acc(acc, ayh, ayl, nm_ ? -ym : ym);
+      df_acc(acc, z2[k], z2[nc + k], dkm);
+      df_acc(acc, z2[2 * nz + k], z2[nc + 2 * nz + k], dkp);
+      const double r = r64[o + col] - (f32_to_f64(acc.s) + f32_to_f64(acc.e));
+      r64[o + col] = r;
+      const float rf = f64_to_f32(r);
+      r32[o + col] = rf;
+      vmax = fmaxf(vmax, fabsf(rf));
+      dkm = dk;
+      dk = dkp;
+    }
+  }
+  block_max_to(vmax, rmax);
+}
+
+__global__ void __launch_bounds__(kResBlock) poisson_update_kernel(
+    const float* __restrict__ dlt, double* __restrict__ r64, float* __restrict__ r32,
+    const float* __restrict__ z2, unsigned int* rmax, int nx, int ny, int nz, int ybc) {
+  poisson_update_body(dlt, r64, r32, z2, rmax, nx, ny, nz, ybc, blockIdx.x);
+}
+
 __global__ void __launch_bounds__(kResBlock) poisson_residual_kernel(
     const double* __restrict__ f, const double* __restrict__ p, const double* __restrict__ zop,
-    const double* __restrict__ mean, float* __restrict__ r32, unsigned int* rmax, int nx, int ny,
-    int nz, double idx2, double idy2, int ybc) {
-  poisson_residual_body(f, p, zop, mean, r32, rmax, nx, ny, nz, idx2, idy2, ybc, blockIdx.x);
+    const double* __restrict__ mean, float* __restrict__ r32, double* __restrict__ r64,
+    unsigned int* rmax, int nx, int ny, int nz, double idx2, double idy2, int ybc) {
+  poisson_residual_body(f, p, zop, mean, r32, r64, rmax, nx, ny, nz, idx2, idy2, ybc,
+                        blockIdx.x);
 }
 
 // Helmholtz: u (+)= delta, then r = rhs - (I - c L_z) u, as FP32, and max |r|.
@@ -247,7 +344,8 @@ __global__ void __launch_bounds__(kResBlock) poisson_residual_group_kernel(const
   if (!group_block(g, &b, &blk)) return;
   const ResBox& r = boxes[b];
   poisson_residual_body(io[b].f, with_p ? io[b].p : nullptr, r.zop, r.neumann ? r.mean : nullptr,
-                        r.r32, r.rmax, r.nx, r.ny, r.nz, r.idx2, r.idy2, r.ybc, blk);
+                        r.r32, with_p ? r.r64 : nullptr, r.rmax, r.nx, r.ny, r.nz, r.idx2,
+                        r.idy2, r.ybc, blk);
 }
 
 __global__ void __launch_bounds__(kResBlock) helm_residual_group_kernel(const ResBox* boxes,
@@ -259,6 +357,14 @@ __global__ void __launch_bounds__(kResBlock) helm_residual_group_kernel(const Re
   const ResBox& r = boxes[b];
   helm_residual_body(io[b].f, io[b].p, r.r32, r.abc, r.rmax, (long long)r.nx * r.ny, r.n, r.nz,
                      mode, blk);
+}
+
+__global__ void __launch_bounds__(kResBlock) poisson_update_group_kernel(const ResBox* boxes,
+                                                                         GroupMap g) {
+  int b, blk;
+  if (!group_block(g, &b, &blk)) return;
+  const ResBox& r = boxes[b];
+  poisson_update_body(r.r32, r.r64, r.r32b, r.zop2, r.rmax, r.nx, r.ny, r.nz, r.ybc, blk);
 }
 
 __global__ void subtract_mean_group_kernel(const ResBox* boxes, GroupMap g, const GroupIo* io) {
@@ -314,6 +420,9 @@ cudaError_t launch_group_refine_stage(int stage, const ResBox* boxes, GroupMap g
       break;
     case GSTAGE_RESIDUAL:
       poisson_residual_group_kernel<<<total, kResBlock, 0, st>>>(boxes, g, io, flag);
+      break;
+    case GSTAGE_UPDATE:
+      poisson_update_group_kernel<<<total, kResBlock, 0, st>>>(boxes, g);
       break;
     case GSTAGE_HELM_RESIDUAL:
       helm_residual_group_kernel<<<total, kResBlock, 0, st>>>(boxes, g, io, flag);
@@ -401,8 +510,8 @@ int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaMemsetAsync(P->d_red, 0, sizeof(unsigned int), st);
   if (e == cudaSuccess) {
     poisson_residual_kernel<<<grid, kResBlock, 0, st>>>(f, nullptr, P->d_zop, mean, P->d_r32,
-                                                        max_word(P), P->nx, P->ny, P->nz, idx2,
-                                                        idy2, P->ybc);
+                                                        nullptr, max_word(P), P->nx, P->ny, P->nz,
+                                                        idx2, idy2, P->ybc);
     e = cudaGetLastError();
   }
   float fmax = 0.0f;
@@ -415,18 +524,24 @@ int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st) {
     return cuda_rc(cudaMemsetAsync(p, 0, sizeof(double) * (size_t)nxy * P->nz, st));
   }
   for (int it = 0; it < P->maxit; ++it) {
-    // delta = solve32(r), in place in r32; p (+)= delta fused into the last pass
-    e = launch_rfft_x32(P, P->d_r32, P->d_r32, false, st);
+    // delta = solve32(r) in r32 (the right-hand side of the later iterations
+    // comes from r32b); p (+)= delta fused into the last pass, which also
+    // leaves delta in r32 for the residual update
+    e = launch_rfft_x32(P, it >= 2 ? P->d_r32b : P->d_r32, P->d_r32, false, st);
     if (e == cudaSuccess) e = launch_fft_y32(P, P->d_r32, false, st);
     if (e == cudaSuccess) e = launch_thomas32(P, P->d_r32, st);
     if (e == cudaSuccess) e = launch_fft_y32(P, P->d_r32, true, st);
     if (e == cudaSuccess) e = launch_rfft_x32_to64(P, P->d_r32, p, it > 0, st);
-    // r = f - mean - L p
     if (e == cudaSuccess) e = cudaMemsetAsync(P->d_red, 0, sizeof(unsigned int), st);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && it == 0) {  // r = f - mean - L p, directly in FP64
       poisson_residual_kernel<<<grid, kResBlock, 0, st>>>(f, p, P->d_zop, mean, P->d_r32,
-                                                          max_word(P), P->nx, P->ny, P->nz, idx2,
-                                                          idy2, P->ybc);
+                                                          P->d_r64, max_word(P), P->nx, P->ny,
+                                                          P->nz, idx2, idy2, P->ybc);
+      e = cudaGetLastError();
+    } else if (e == cudaSuccess) {  // r -= L delta
+      poisson_update_kernel<<<grid, kResBlock, 0, st>>>(P->d_r32, P->d_r64, P->d_r32b, P->d_zop2,
+                                                        max_word(P), P->nx, P->ny, P->nz,
+                                                        P->ybc);
       e = cudaGetLastError();
     }
     float rmax = 0.0f;

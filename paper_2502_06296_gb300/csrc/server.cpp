@@ -54,10 +54,11 @@ struct Run {
 };
 
 // Device bytes of a refined plan of this size: FP64 and FP32 factors of
-// every (kx, ky) system, the FP32 work field, and a margin for the tables.
+// every (kx, ky) system, the two FP32 and the FP64 work fields, and a margin
+// for the tables.
 size_t plan_estimate(int nx, int ny, int nz) {
   const size_t cols = (size_t)(nx / 2 + 1) * (ny / 2 + 1);
-  return cols * nz * (24 + 12) + (size_t)nx * ny * nz * 4 + (size_t)(1u << 20);
+  return cols * nz * (24 + 12) + (size_t)nx * ny * nz * (4 + 4 + 8) + (size_t)(1u << 20);
 }
 
 }  // namespace
