@@ -339,11 +339,10 @@ def run_helmholtz3d(chanfs, torch, device, plan, rhs, outs, reps: int = 5):
 # Walls in y (DCT-II / DST-II) on the channel workload
 # ----------------------------------------------------------------------------
 
-def run_ywalls(chanfs, torch, device, f, reps: int = 5):
+def run_ywalls(chanfs, torch, device, f, dz, reps: int = 5):
     """The channel's Poisson solve with Neumann or Dirichlet walls in y
     instead of periodicity, FP64, median of reps solves each."""
     nz, ny, nx = f.shape
-    dz = synth.grid_dz(CFG)
     out = {"workload": CFG["name"], "precision": "f64"}
     p = torch.empty_like(f)
     for name, ybc in (("neumann", chanfs.Y_NEUMANN), ("dirichlet", chanfs.Y_DIRICHLET)):
@@ -747,7 +746,7 @@ def run_ours(args):
         "device_status": status,
     }
     line["helmholtz3d"] = run_helmholtz3d(chanfs, torch, device, plan, rhs, us)
-    line["ywalls"] = run_ywalls(chanfs, torch, device, f)
+    line["ywalls"] = run_ywalls(chanfs, torch, device, f, dz)
     plan.close()
     del f, rhs, p, us, ref_bits
     if not args.no_mixed:
