@@ -84,6 +84,8 @@ def _load():
             "or_apply_poisson_walls": [i, i, i, d, d, dp, i, i, dp, dp],
             "or_poisson_solve_walls": [i, i, i, d, d, dp, i, i, dp, dp],
             "or_helmholtz3d_solve": [i, i, i, d, d, dp, d, i, dp, dp],
+            "or_apply_helmholtz3d_walls": [i, i, i, d, d, dp, d, i, i, dp, dp],
+            "or_helmholtz3d_solve_walls": [i, i, i, d, d, dp, d, i, i, dp, dp],
             "or_spectral_forward": [i, i, i, dp, dp],
             "or_spectral_inverse": [i, i, i, dp, dp],
             "or_dense_solve": [i, dp, dp],
@@ -321,23 +323,23 @@ def poisson_solve_walls(f, lx: float, ly: float, dzf, bc: int, ybc: int) -> np.n
     return out
 
 
-def apply_helmholtz3d(u, lx: float, ly: float, dzf, c: float, loc: int) -> np.ndarray:
+def apply_helmholtz3d(u, lx: float, ly: float, dzf, c: float, loc: int, ybc: int = 0) -> np.ndarray:
     """(I - c L) u, the full 3-D operator of Eq. 8 with Dirichlet z walls."""
     u, dzf = _f64(u), _f64(dzf)
     nx, ny, nz = _shape(u)
     out = np.empty_like(u)
-    _check(_load().or_apply_helmholtz3d(nx, ny, nz, lx, ly, _p(dzf), c, loc, _p(u), _p(out)),
-           "apply_helmholtz3d")
+    _check(_load().or_apply_helmholtz3d_walls(nx, ny, nz, lx, ly, _p(dzf), c, loc, ybc, _p(u),
+                                              _p(out)), "apply_helmholtz3d")
     return out
 
 
-def helmholtz3d_solve(rhs, lx: float, ly: float, dzf, c: float, loc: int) -> np.ndarray:
+def helmholtz3d_solve(rhs, lx: float, ly: float, dzf, c: float, loc: int, ybc: int = 0) -> np.ndarray:
     """u with (I - c L) u = rhs (Eq. 8) by eigenfunction expansion."""
     rhs, dzf = _f64(rhs), _f64(dzf)
     nx, ny, nz = _shape(rhs)
     out = np.empty_like(rhs)
-    _check(_load().or_helmholtz3d_solve(nx, ny, nz, lx, ly, _p(dzf), c, loc, _p(rhs), _p(out)),
-           "helmholtz3d")
+    _check(_load().or_helmholtz3d_solve_walls(nx, ny, nz, lx, ly, _p(dzf), c, loc, ybc, _p(rhs),
+                                              _p(out)), "helmholtz3d")
     return out
 
 

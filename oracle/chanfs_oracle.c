@@ -712,11 +712,23 @@ int or_helmholtz_solve(int nx, int ny, int nz, const double* dzf, double c,
 /* Nz-1 is passed through unchanged).                                        */
 /* ------------------------------------------------------------------------ */
 
+int or_apply_helmholtz3d_walls(int nx, int ny, int nz, double lx, double ly,
+                               const double* dzf, double c, int loc, int ybc, const double* u,
+                               double* out);
+
 int or_apply_helmholtz3d(int nx, int ny, int nz, double lx, double ly,
                          const double* dzf, double c, int loc, const double* u,
                          double* out) {
+  return or_apply_helmholtz3d_walls(nx, ny, nz, lx, ly, dzf, c, loc, 0, u, out);
+}
+
+int or_apply_helmholtz3d_walls(int nx, int ny, int nz, double lx, double ly,
+                               const double* dzf, double c, int loc, int ybc, const double* u,
+                               double* out) {
   if (nx < 1 || ny < 1 || nz < 3 || !(lx > 0) || !(ly > 0)) return -1;
   if (loc != LOC_CENTER && loc != LOC_FACE) return -1;
+  if (ybc < 0 || ybc > 2) return -1;
+  const double g = (ybc == 1) ? 1.0 : -1.0;  /* wall ghost = g * boundary value */
   double dx = lx / nx, dy = ly / ny;
   double* dzc = (double*)malloc(sizeof(double) * (size_t)nz);
   or_dzc(nz, dzf, dzc);
@@ -734,7 +746,12 @@ int or_apply_helmholtz3d(int nx, int ny, int nz, double lx, double ly,
         size_t row = (size_t)nx * ((size_t)y + (size_t)ny * z);
         size_t pl = (size_t)nx * ((size_t)ny * z);
         double lxx = (u[row + xp] - 2.0 * u[i] + u[row + xm]) / (dx * dx);
-        double lyy = (u[pl + (size_t)nx * yp + x] - 2.0 * u[i] + u[pl + (size_t)nx * ym + x]) / (dy * dy);
+        double up = u[pl + (size_t)nx * yp + x], dn = u[pl + (size_t)nx * ym + x];
+        if (ybc != 0) {
+          up = (y + 1 < ny) ? u[pl + (size_t)nx * (y + 1) + x] : g * u[i];
+          dn = (y > 0) ? u[pl + (size_t)nx * (y - 1) + x] : g * u[i];
+        }
+        double lyy = (up - 2.0 * u[i] + dn) / (dy * dy);
         const double* colp = u + (size_t)x + (size_t)nx * y;
         double lzz = (loc == LOC_CENTER) ? lz_centre(nz, dzf, dzc, BC_DIRICHLET, colp, sxy, z)
                                          : lz_face(nz, dzf, dzc, colp, sxy, z);
@@ -748,21 +765,36 @@ int or_apply_helmholtz3d(int nx, int ny, int nz, double lx, double ly,
 /* per (kx,ky) the tridiagonal system with A' = -c A_k,                        */
 /* B' = 1 - c (B_k + lx[kx] + ly[ky]), C' = -c C_k (Dirichlet rows of the      */
 /* field's location; nonsingular for c >= 0), inverse DFTs with 1/(Nx Ny).     */
+int or_helmholtz3d_solve_walls(int nx, int ny, int nz, double lx, double ly,
+                               const double* dzf, double c, int loc, int ybc,
+                               const double* rhs, double* u);
+static void y_walls_axis(cplx* F, int nx, int ny, int nz, int ybc, int inverse);
+
 int or_helmholtz3d_solve(int nx, int ny, int nz, double lx, double ly,
                          const double* dzf, double c, int loc, const double* rhs,
                          double* u) {
+  return or_helmholtz3d_solve_walls(nx, ny, nz, lx, ly, dzf, c, loc, 0, rhs, u);
+}
+
+/* ybc as for the Poisson solve with walls: DFT, DCT-II or DST-II along y. */
+int or_helmholtz3d_solve_walls(int nx, int ny, int nz, double lx, double ly,
+                               const double* dzf, double c, int loc, int ybc,
+                               const double* rhs, double* u) {
   if (nx < 1 || ny < 1 || nz < 3 || !(lx > 0) || !(ly > 0) || !(c >= 0)) return -1;
   if (loc != LOC_CENTER && loc != LOC_FACE) return -1;
+  if (ybc < 0 || ybc > 2) return -1;
   size_t n3 = (size_t)nx * ny * nz, sxy = (size_t)nx * ny;
   cplx* F = (cplx*)malloc(sizeof(cplx) * n3);
   for (size_t i = 0; i < n3; ++i) F[i] = rhs[i];
   int dims[3] = {nx, ny, nz};
   fft_axis(F, dims, 0, -1);
-  fft_axis(F, dims, 1, -1);
+  if (ybc == 0) fft_axis(F, dims, 1, -1);
+  else y_walls_axis(F, nx, ny, nz, ybc, 0);
   double* lamx = (double*)malloc(sizeof(double) * (size_t)nx);
   double* lamy = (double*)malloc(sizeof(double) * (size_t)ny);
   or_eig_periodic(nx, lx / nx, lamx);
-  or_eig_periodic(ny, ly / ny, lamy);
+  if (ybc == 0) or_eig_periodic(ny, ly / ny, lamy);
+  else or_eig_wall(ny, ly / ny, ybc, lamy);
   double* A = (double*)malloc(sizeof(double) * (size_t)nz);
   double* B = (double*)malloc(sizeof(double) * (size_t)nz);
   double* C = (double*)malloc(sizeof(double) * (size_t)nz);
@@ -785,9 +817,11 @@ int or_helmholtz3d_solve(int nx, int ny, int nz, double lx, double ly,
       for (int k = 0; k < n; ++k) F[(size_t)kx + (size_t)nx * ky + sxy * (size_t)k] = x[k];
       for (int k = n; k < nz; ++k) F[(size_t)kx + (size_t)nx * ky + sxy * (size_t)k] = 0.0;
     }
-  fft_axis(F, dims, 1, 1);
+  if (ybc == 0) fft_axis(F, dims, 1, 1);
+  else y_walls_axis(F, nx, ny, nz, ybc, 1);
   fft_axis(F, dims, 0, 1);
-  double scale = 1.0 / ((double)nx * (double)ny);
+  /* the inverse wall transforms include their 1/Ny */
+  double scale = 1.0 / ((double)nx * (ybc == 0 ? (double)ny : 1.0));
   for (size_t i = 0; i < n3; ++i) u[i] = creal(F[i]) * scale;
   free(x); free(d); free(cc); free(b); free(a); free(C); free(B); free(A);
   free(lamy); free(lamx); free(F);

@@ -93,6 +93,13 @@ int or_apply_helmholtz3d(int nx, int ny, int nz, double lx, double ly,
 int or_helmholtz3d_solve(int nx, int ny, int nz, double lx, double ly,
                          const double* dzf, double c, int loc, const double* rhs,
                          double* u);
+/* The same with walls in y (ybc 0 periodic, 1 Neumann, 2 Dirichlet). */
+int or_apply_helmholtz3d_walls(int nx, int ny, int nz, double lx, double ly,
+                               const double* dzf, double c, int loc, int ybc, const double* u,
+                               double* out);
+int or_helmholtz3d_solve_walls(int nx, int ny, int nz, double lx, double ly,
+                               const double* dzf, double c, int loc, int ybc,
+                               const double* rhs, double* u);
 
 /* Spectral layout used by the solver: App. A packing along x, complex DFT
  * along y (pair j of a packed x-line read as one complex number), and pair 0

@@ -500,12 +500,14 @@ def test_oracle_reproduces_its_stored_fixture():
 # Fully implicit 3-D Helmholtz (Eq. 8): (I - c L) u = rhs, Dirichlet z walls
 # ----------------------------------------------------------------------------
 
-@pytest.mark.parametrize("dims,beta,loc,c", [((4, 3, 5), 1.5, 0, 0.05), ((4, 3, 5), 1.5, 1, 0.05),
-                                             ((6, 4, 6), None, 0, 1.0), ((5, 6, 4), 1.8, 1, 3e-3),
-                                             ((2, 1, 7), 1.2, 0, 0.2)])
-def test_helmholtz3d_matches_dense_bruteforce(dims, beta, loc, c):
+@pytest.mark.parametrize("dims,beta,loc,c,ybc", [((4, 3, 5), 1.5, 0, 0.05, 0), ((4, 3, 5), 1.5, 1, 0.05, 0),
+                                                 ((6, 4, 6), None, 0, 1.0, 0), ((5, 6, 4), 1.8, 1, 3e-3, 0),
+                                                 ((2, 1, 7), 1.2, 0, 0.2, 0), ((4, 5, 4), 1.5, 0, 0.1, 1),
+                                                 ((4, 3, 5), 1.4, 1, 0.3, 2), ((3, 6, 4), None, 1, 2.0, 1)])
+def test_helmholtz3d_matches_dense_bruteforce(dims, beta, loc, c, ybc):
     """The eigenfunction-expansion solve against the assembled 3-D operator
-    (a separate, point-by-point stencil apply) solved densely."""
+    (a separate, point-by-point stencil apply) solved densely; y periodic or
+    with Neumann / Dirichlet walls."""
     nx, ny, nz = dims
     lx, ly = 2.0, 1.5
     dzf = synth.uniform_dz(nz) if beta is None else synth.tanh_dz(nz, beta)
@@ -517,9 +519,9 @@ def test_helmholtz3d_matches_dense_bruteforce(dims, beta, loc, c):
     for i in range(n):
         e = np.zeros(n)
         e[i] = 1.0
-        K[:, i] = oracle.apply_helmholtz3d(e.reshape(nz, ny, nx), lx, ly, dzf, c, loc).ravel()
+        K[:, i] = oracle.apply_helmholtz3d(e.reshape(nz, ny, nx), lx, ly, dzf, c, loc, ybc).ravel()
     ref = np.linalg.solve(K, f.ravel()).reshape(nz, ny, nx)
-    u = oracle.helmholtz3d_solve(f, lx, ly, dzf, c, loc)
+    u = oracle.helmholtz3d_solve(f, lx, ly, dzf, c, loc, ybc)
     assert _rel(u, ref) < 1e-12
     if loc == 1:
         assert np.all(u[-1] == 0.0)
