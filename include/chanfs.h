@@ -96,9 +96,8 @@ int cfs_plan_create(cfs_plan_t* plan, int nx, int ny, int nz, double lx,
  * computed by one complex FFT of length Ny; the eigenvalues are
  * 2(cos(pi k/Ny) - 1)/dy^2 and 2(cos(pi (k+1)/Ny) - 1)/dy^2, k < Ny.  The
  * solution's null space (constants) exists only with Neumann walls in both
- * y and z; the Neumann conventions above apply to it.  The Poisson,
- * z-implicit Helmholtz, refined and grouped solves support y walls;
- * cfs_helmholtz3d_* returns CFS_EUNSUPPORTED on such plans.
+ * y and z; the Neumann conventions above apply to it.  Every solve supports
+ * y walls (the fully implicit Helmholtz uses the same y transforms).
  */
 enum { CFS_Y_PERIODIC = 0, CFS_Y_NEUMANN = 1, CFS_Y_DIRICHLET = 2 };
 int cfs_plan_create_walls(cfs_plan_t* plan, int nx, int ny, int nz, double lx, double ly,
@@ -239,9 +238,9 @@ int cfs_last_info(cfs_plan_t plan, int* iters, double* rel_residual);
 
 /*
  * cfs_helmholtz3d_solve -- the fully implicit Helmholtz solve of Eq. 8,
- * (I - c L) u = rhs with L the whole staggered Laplacian (periodic x, y;
- * homogeneous Dirichlet z walls, cell-centred or face-located field as in
- * cfs_helmholtz_solve).  It runs on the Poisson machinery: packed x FFT, y
+ * (I - c L) u = rhs with L the whole staggered Laplacian (periodic x; y as
+ * the plan's, periodic or walls; homogeneous Dirichlet z walls, cell-centred
+ * or face-located field as in cfs_helmholtz_solve).  It runs on the Poisson machinery: packed x FFT, y
  * FFT, one tridiagonal system per (kx, ky) with the diagonal
  * 1 - c (B_k + lx + ly) and off-diagonals -c A_k, -c C_k, inverse transforms.
  * The factors of every (kx, ky) system are computed on the GPU once per

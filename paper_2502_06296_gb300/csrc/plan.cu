@@ -746,7 +746,6 @@ static int helm3_prepare(cfs_plan* P, double c, int loc, Helm3Coef** res) {
 
 extern "C" int cfs_helmholtz3d_prepare(cfs_plan_t P, double c, int loc) {
   if (!P) return CFS_EINVAL;
-  if (P->ybc != CFS_Y_PERIODIC) return CFS_EUNSUPPORTED;
   Helm3Coef* h = nullptr;
   return helm3_prepare(P, c, loc, &h);
 }
@@ -754,7 +753,6 @@ extern "C" int cfs_helmholtz3d_prepare(cfs_plan_t P, double c, int loc) {
 extern "C" int cfs_helmholtz3d_solve(cfs_plan_t P, double c, int loc, const double* rhs,
                                      double* u, void* stream) {
   if (!P || !rhs || !u || !aligned16(rhs) || !aligned16(u)) return CFS_EINVAL;
-  if (P->ybc != CFS_Y_PERIODIC) return CFS_EUNSUPPORTED;
   Helm3Coef* h = nullptr;
   int rc = helm3_prepare(P, c, loc, &h);
   if (rc) return rc;

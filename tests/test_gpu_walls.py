@@ -71,9 +71,11 @@ def test_poisson_with_y_walls_matches_oracle(chanfs, dims, beta, bc, ybc):
         # the z-implicit Helmholtz does not see y
         u = host(plan.helmholtz_solve(1e-4, dev(f), chanfs.FACE))
         assert rel(u, oracle.helmholtz_solve(f, dz, 1e-4, 1)) < 1e-12
-        with pytest.raises(chanfs.ChanfsError) as err:
-            plan.helmholtz3d_solve(1e-3, dev(f))
-        assert err.value.status == chanfs.EUNSUPPORTED
+        # the fully implicit Helmholtz (Eq. 8) with the same y transforms
+        for loc, c in ((chanfs.CENTER, 1e-3), (chanfs.FACE, 0.2)):
+            u3 = host(plan.helmholtz3d_solve(c, dev(f), loc))
+            ref3 = oracle.helmholtz3d_solve(f, lx, ly, dz, c, loc, ybc)
+            assert rel(u3, ref3) < 1e-12, (loc, rel(u3, ref3))
         assert plan.check() == 0
 
 
