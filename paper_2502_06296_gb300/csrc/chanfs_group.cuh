@@ -76,7 +76,7 @@ struct ResBox {  // refinement residual and norms (refine.cu)
   double* mean;        // dz-weighted mean
   float* r32;          // FP32 residual / correction
   float* r32b;         // FP32 residual of the later iterations
-  double* r64;         // FP64 residual kept between iterations
+  float2* rdf;         // residual kept between iterations, double-float (hi, lo)
   const float* zop2;   // double-float split of zop, 1/dx^2, 1/dy^2
   unsigned int* rmax;  // max |r| (float bits)
   int nx, ny, nz, n;   // n = Helmholtz unknowns per column
@@ -167,7 +167,7 @@ enum {
   GSTAGE_RESIDUAL = 2,
   GSTAGE_SUBTRACT = 3,
   GSTAGE_HELM_RESIDUAL = 4,  // flag = mode of helm_residual_kernel
-  GSTAGE_UPDATE = 5          // r64 -= L delta (double-float), r32b and max
+  GSTAGE_UPDATE = 5          // r -= L delta (double-float), r32b and max
 };
 
 // Host-side descriptions of one plan's box for the grouped kernels.

@@ -130,7 +130,7 @@ struct cfs_plan {
   int kx64, ky64;    // columns kx < kx64, min(ky, Ny-ky) < ky64 stay FP64
   float* d_r32;      // FP32 residual / correction field (in-place inner solve)
   float* d_r32b;     // the FP32 residual of the later iterations (input of their solves)
-  double* d_r64;     // the FP64 residual kept between iterations
+  float2* d_rdf;     // the residual kept between iterations, double-float (hi, lo)
   float* d_zop2;     // double-float split of zop and of 1/dx^2, 1/dy^2: hi[3nz+2] | lo[3nz+2]
   double* d_red;     // reduction scratch: [0] max |r| (float bits), [1] mean, [2..] partials
   double* d_zop;     // 3*nz doubles: A_k | B_k - 2/dx^2 - 2/dy^2 | C_k of the Poisson operator
@@ -221,30 +221,57 @@ inline cudaError_t allow_max_smem(K kernel) {
 // Conversions between FP32 and FP64 on the integer units.  On GB300 the
 // hardware conversion instructions share the FP64 pipe (2 lanes per SM per
 // clock), which the refinement kernels already saturate; these produce the
-// same bits (IEEE 754 binary32 <-> binary64, round to nearest even) from the
-// fields of the encodings, and hand the rare operands (zero, subnormal,
-// infinite, NaN, out of range) to the hardware conversion.
+// values of IEEE 754 binary32 <-> binary64 conversion (round to nearest,
+// ties to even) from the fields of the encodings alone, subnormals, infinities
+// and out-of-range values included, so that no operand falls back to the
+// hardware instruction (a fallback branch the compiler may turn into a select
+// that runs the hardware conversion on every operand).  NaN maps to a quiet
+// NaN of the same sign.
 __device__ __forceinline__ double f32_to_f64(float f) {
   const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xffu;
-  if ((u & 0x7fffffffu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
-  if (e == 0u || e == 0xffu) return (double)f;
-  // exponent bias 127 -> 1023; 23 mantissa bits -> the top of 52
-  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xfffffu);
-  return __hiloint2double((int)hi, (int)(u << 29));
+  const unsigned a = u & 0x7fffffffu;
+  unsigned hi = 0u, lo = 0u;
+  if (a >= 0x00800000u) {  // normal, infinity or NaN: bias 127 -> 1023
+    const unsigned e = a >> 23;
+    hi = (e == 0xffu ? 0x7ff00000u : (e + 896u) << 20) | ((a >> 3) & 0xfffffu);
+    lo = a << 29;
+  } else if (a != 0u) {  // subnormal a * 2^-149: the leading bit moves to bit 23
+    const unsigned sh = (unsigned)__clz((int)a) - 8u;
+    const unsigned m = a << sh;
+    hi = ((897u - sh) << 20) | ((m >> 3) & 0xfffffu);
+    lo = m << 29;
+  }
+  return __hiloint2double((int)((u & 0x80000000u) | hi), (int)lo);
 }
 
 __device__ __forceinline__ float f64_to_f32(double x) {
   const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
   const unsigned e = (hi >> 20) & 0x7ffu;
-  if (e < 897u || e > 1150u) return __double2float_rn(x);  // not a normal binary32
-  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);  // the top 23 mantissa bits
-  const unsigned rest = lo & 0x1fffffffu;                  // the 29 dropped bits
-  unsigned bits = (hi & 0x80000000u) | ((e - 896u) << 23) | m;
-  // round to nearest, ties to even; a carry out of the mantissa raises the
-  // exponent (and reaches infinity past the largest binary32)
-  bits += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
-  return __uint_as_float(bits);
+  unsigned bits;
+  if (e >= 897u && e <= 1150u) {  // a normal binary32 (or its rounding overflows)
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);  // the top 23 mantissa bits
+    const unsigned rest = lo & 0x1fffffffu;                  // the 29 dropped bits
+    bits = ((e - 896u) << 23) | m;
+    // a carry out of the mantissa raises the exponent (to infinity past the
+    // largest binary32)
+    bits += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  } else if (e > 1150u) {  // too large, infinity or NaN
+    bits = (e == 0x7ffu && ((hi & 0xfffffu) | lo)) ? 0x7fc00000u : 0x7f800000u;
+  } else if (e == 0u) {  // binary64 zero or subnormal: rounds to zero
+    bits = 0u;
+  } else {  // a binary32 subnormal: significand * 2^(e - 1075) in units of 2^-149
+    const unsigned sh = 926u - e;  // >= 30
+    if (sh > 63u) {
+      bits = 0u;  // below half the smallest subnormal
+    } else {
+      const unsigned long long M =
+          (1ull << 52) | ((unsigned long long)(hi & 0xfffffu) << 32) | lo;
+      const unsigned long long q = M >> sh, r = M & ((1ull << sh) - 1ull);
+      const unsigned long long half = 1ull << (sh - 1u);
+      bits = (unsigned)(q + ((r > half || (r == half && (q & 1ull))) ? 1ull : 0ull));
+    }
+  }
+  return __uint_as_float((hi & 0x80000000u) | bits);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {

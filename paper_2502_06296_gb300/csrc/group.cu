@@ -210,7 +210,7 @@ static int group_bind(cfs_group* G, int nplans, const cfs_plan_t* plans, cudaStr
     r.mean = P->d_red + 1;
     r.r32 = P->d_r32;
     r.r32b = P->d_r32b;
-    r.r64 = P->d_r64;
+    r.rdf = P->d_rdf;
     r.zop2 = P->d_zop2;
     r.rmax = reinterpret_cast<unsigned int*>(P->d_red);
     r.nx = P->nx;

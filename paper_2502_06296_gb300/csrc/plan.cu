@@ -169,7 +169,7 @@ static void plan_free(cfs_plan* P) {
   cudaFree(P->d_bwd32);
   cudaFree(P->d_r32);
   cudaFree(P->d_r32b);
-  cudaFree(P->d_r64);
+  cudaFree(P->d_rdf);
   cudaFree(P->d_zop2);
   cudaFree(P->d_red);
   cudaFree(P->d_zop);
@@ -387,7 +387,7 @@ extern "C" int cfs_plan_create_walls(cfs_plan_t* out, int nx, int ny, int nz, do
     }
     if (!rc) rc = dev_upload(&P->d_zop2, z2.data(), z2.size(), &P->device_bytes);
     if (!rc) rc = dev_upload<float>(&P->d_r32b, nullptr, (size_t)nx * ny * nz, &P->device_bytes);
-    if (!rc) rc = dev_upload<double>(&P->d_r64, nullptr, (size_t)nx * ny * nz, &P->device_bytes);
+    if (!rc) rc = dev_upload<float2>(&P->d_rdf, nullptr, (size_t)nx * ny * nz, &P->device_bytes);
   }
 
   if (!rc) rc = dev_upload(&dA, A.data(), A.size(), &scratch);

@@ -86,12 +86,13 @@ __global__ void mean_final_kernel(const double* partial, int nz, const double* d
 // r = (f - mean) - L p, written as FP32, and max |r|.  One thread per (x, y)
 // column marching up in z with p_{k-1}, p_k, p_{k+1} in registers; the x and
 // y neighbours of a plane are shared through L1.  p == nullptr: r = f - mean.
-// r64 (may be null) receives r in FP64 for the residual updates that follow.
+// rdf (may be null) receives r as a double-float pair hi + lo (hi = fl32(r),
+// lo = fl32(r - hi); one more FP64 instruction) for the updates that follow.
 // zop = [A_k | B_k - 2/dx^2 - 2/dy^2 | C_k]; FP64: 8 instructions per point
 // (the FP32 rounding of r runs on the integer units).
 __device__ __forceinline__ void poisson_residual_body(
     const double* __restrict__ f, const double* __restrict__ p, const double* __restrict__ zop,
-    const double* __restrict__ mean, float* __restrict__ r32, double* __restrict__ r64,
+    const double* __restrict__ mean, float* __restrict__ r32, float2* __restrict__ rdf,
     unsigned int* rmax, int nx, int ny, int nz, double idx2, double idy2, int ybc,
     long long blk) {
   const long long nxy = (long long)nx * ny;
@@ -134,7 +135,7 @@ __device__ __forceinline__ void poisson_residual_body(
       }
       const float rf = f64_to_f32(r);
       r32[o + col] = rf;
-      if (r64) r64[o + col] = r;
+      if (rdf) rdf[o + col] = make_float2(rf, f64_to_f32(r - f32_to_f64(rf)));
       vmax = fmaxf(vmax, fabsf(rf));
       pkm = pk;
       pk = pkp;
@@ -152,7 +153,8 @@ __device__ __forceinline__ void poisson_residual_body(
 // summed exactly by TwoSum and the small parts plainly.  The result holds
 // L delta to about 2^-48 of sum |c d|, and after the first correction
 // |delta| is small, so r_new is as accurate as a direct FP64 evaluation
-// (whose error is about 2^-53 ||L|| |p|).  FP64: 2 instructions per point.
+// (whose error is about 2^-53 ||L|| |p|).  The residual itself is kept as a
+// double-float pair too, so the update runs without FP64 instructions.
 // The first residual of a solve (|delta| ~ |p|) stays the direct FP64 one.
 // ----------------------------------------------------------------------------
 struct DoubleFloat {
@@ -179,7 +181,7 @@ __device__ __forceinline__ void df_acc(DoubleFloat& acc, float chi, float clo, f
 
 // z2 = hi[3nz + 2] | lo[3nz + 2]: the split zop rows, then 1/dx^2, 1/dy^2.
 __device__ __forceinline__ void poisson_update_body(const float* __restrict__ dlt,
-                                                    double* __restrict__ r64,
+                                                    float2* __restrict__ rdf,
                                                     float* __restrict__ r32,
                                                     const float* __restrict__ z2,
                                                     unsigned int* rmax, int nx, int ny, int nz,
@@ -218,9 +220,15 @@ __device__ __forceinline__ void poisson_update_body(const float* __restrict__ dl
       df_acc(acc, ayh, ayl, nm_ ? -ym : ym);
       df_acc(acc, z2[k], z2[nc + k], dkm);
       df_acc(acc, z2[2 * nz + k], z2[nc + 2 * nz + k], dkp);
-      const double r = r64[o + col] - (f32_to_f64(acc.s) + f32_to_f64(acc.e));
-      r64[o + col] = r;
-      const float rf = f64_to_f32(r);
+      // (hi, lo) - (s + e) in double-float: TwoSum of the leading parts, the
+      // rest added to the error term, renormalised by a second TwoSum
+      const float2 rp = rdf[o + col];
+      float sh, se, hi, lo;
+      two_sum(rp.x, -acc.s, sh, se);
+      se = __fadd_rn(se, __fsub_rn(rp.y, acc.e));
+      two_sum(sh, se, hi, lo);
+      rdf[o + col] = make_float2(hi, lo);
+      const float rf = hi;
       r32[o + col] = rf;
       vmax = fmaxf(vmax, fabsf(rf));
       dkm = dk;
@@ -231,16 +239,16 @@ __device__ __forceinline__ void poisson_update_body(const float* __restrict__ dl
 }
 
 __global__ void __launch_bounds__(kResBlock) poisson_update_kernel(
-    const float* __restrict__ dlt, double* __restrict__ r64, float* __restrict__ r32,
+    const float* __restrict__ dlt, float2* __restrict__ rdf, float* __restrict__ r32,
     const float* __restrict__ z2, unsigned int* rmax, int nx, int ny, int nz, int ybc) {
-  poisson_update_body(dlt, r64, r32, z2, rmax, nx, ny, nz, ybc, blockIdx.x);
+  poisson_update_body(dlt, rdf, r32, z2, rmax, nx, ny, nz, ybc, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(kResBlock) poisson_residual_kernel(
     const double* __restrict__ f, const double* __restrict__ p, const double* __restrict__ zop,
-    const double* __restrict__ mean, float* __restrict__ r32, double* __restrict__ r64,
+    const double* __restrict__ mean, float* __restrict__ r32, float2* __restrict__ rdf,
     unsigned int* rmax, int nx, int ny, int nz, double idx2, double idy2, int ybc) {
-  poisson_residual_body(f, p, zop, mean, r32, r64, rmax, nx, ny, nz, idx2, idy2, ybc,
+  poisson_residual_body(f, p, zop, mean, r32, rdf, rmax, nx, ny, nz, idx2, idy2, ybc,
                         blockIdx.x);
 }
 
@@ -344,7 +352,7 @@ __global__ void __launch_bounds__(kResBlock) poisson_residual_group_kernel(const
   if (!group_block(g, &b, &blk)) return;
   const ResBox& r = boxes[b];
   poisson_residual_body(io[b].f, with_p ? io[b].p : nullptr, r.zop, r.neumann ? r.mean : nullptr,
-                        r.r32, with_p ? r.r64 : nullptr, r.rmax, r.nx, r.ny, r.nz, r.idx2,
+                        r.r32, with_p ? r.rdf : nullptr, r.rmax, r.nx, r.ny, r.nz, r.idx2,
                         r.idy2, r.ybc, blk);
 }
 
@@ -364,7 +372,7 @@ __global__ void __launch_bounds__(kResBlock) poisson_update_group_kernel(const R
   int b, blk;
   if (!group_block(g, &b, &blk)) return;
   const ResBox& r = boxes[b];
-  poisson_update_body(r.r32, r.r64, r.r32b, r.zop2, r.rmax, r.nx, r.ny, r.nz, r.ybc, blk);
+  poisson_update_body(r.r32, r.rdf, r.r32b, r.zop2, r.rmax, r.nx, r.ny, r.nz, r.ybc, blk);
 }
 
 __global__ void subtract_mean_group_kernel(const ResBox* boxes, GroupMap g, const GroupIo* io) {
@@ -458,6 +466,14 @@ cudaError_t launch_group_fmax(const ResBox* boxes, int nbox, float* fmax, cudaSt
 // values), the same with its 29 dropped mantissa bits set to an exact tie
 // inside the binary32 range, and its low 32 bits as a float.
 // ----------------------------------------------------------------------------
+// Equal encodings, or both NaN (the NaN payload is not specified).
+__device__ __forceinline__ bool same_f32(float a, float b) {
+  return __float_as_uint(a) == __float_as_uint(b) || (a != a && b != b);
+}
+__device__ __forceinline__ bool same_f64(double a, double b) {
+  return __double_as_longlong(a) == __double_as_longlong(b) || (a != a && b != b);
+}
+
 __global__ void conversion_check_kernel(unsigned long long n, unsigned long long* bad) {
   unsigned long long local = 0;
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
@@ -467,14 +483,29 @@ __global__ void conversion_check_kernel(unsigned long long n, unsigned long long
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     z ^= z >> 31;
     const double x = __longlong_as_double((long long)z);
-    local += __float_as_uint(f64_to_f32(x)) != __float_as_uint(__double2float_rn(x));
+    local += !same_f32(f64_to_f32(x), __double2float_rn(x));
     const unsigned long long e = 897ull + ((z >> 52) % 254ull);  // a binary32 exponent
     const unsigned long long t =
         (z & 0x800FFFFFE0000000ull) | (e << 52) | 0x10000000ull;  // exact tie
     const double xt = __longlong_as_double((long long)t);
-    local += __float_as_uint(f64_to_f32(xt)) != __float_as_uint(__double2float_rn(xt));
+    local += !same_f32(f64_to_f32(xt), __double2float_rn(xt));
+    // binary32 subnormal results and their ties: exponents 870..896
+    const unsigned long long es = 870ull + ((z >> 40) % 27ull);
+    const double xs = __longlong_as_double((long long)((z & 0x800FFFFFFFFFFFFFull) | (es << 52)));
+    local += !same_f32(f64_to_f32(xs), __double2float_rn(xs));
+    // a tie at the rounding position (exponents 874..896: the tie bit is in
+    // the stored mantissa)
+    const unsigned long long et = 874ull + ((z >> 40) % 23ull);
+    const unsigned long long sh = 926ull - et;  // 30..52
+    const unsigned long long mt =
+        ((z & 0x000FFFFFFFFFFFFFull) & ~((1ull << sh) - 1ull)) | (1ull << (sh - 1));
+    const double xst =
+        __longlong_as_double((long long)((z & 0x8000000000000000ull) | (et << 52) | mt));
+    local += !same_f32(f64_to_f32(xst), __double2float_rn(xst));
     const float f = __uint_as_float((unsigned)z);
-    local += __double_as_longlong(f32_to_f64(f)) != __double_as_longlong((double)f);
+    local += !same_f64(f32_to_f64(f), (double)f);
+    const float fs = __uint_as_float((unsigned)(z >> 32) & 0x807FFFFFu);  // subnormal or zero
+    local += !same_f64(f32_to_f64(fs), (double)fs);
   }
   if (local) atomicAdd(bad, local);
 }
@@ -535,11 +566,11 @@ int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st) {
     if (e == cudaSuccess) e = cudaMemsetAsync(P->d_red, 0, sizeof(unsigned int), st);
     if (e == cudaSuccess && it == 0) {  // r = f - mean - L p, directly in FP64
       poisson_residual_kernel<<<grid, kResBlock, 0, st>>>(f, p, P->d_zop, mean, P->d_r32,
-                                                          P->d_r64, max_word(P), P->nx, P->ny,
+                                                          P->d_rdf, max_word(P), P->nx, P->ny,
                                                           P->nz, idx2, idy2, P->ybc);
       e = cudaGetLastError();
     } else if (e == cudaSuccess) {  // r -= L delta
-      poisson_update_kernel<<<grid, kResBlock, 0, st>>>(P->d_r32, P->d_r64, P->d_r32b, P->d_zop2,
+      poisson_update_kernel<<<grid, kResBlock, 0, st>>>(P->d_r32, P->d_rdf, P->d_r32b, P->d_zop2,
                                                         max_word(P), P->nx, P->ny, P->nz,
                                                         P->ybc);
       e = cudaGetLastError();
