@@ -258,10 +258,17 @@ int cfs_helmholtz3d_solve(cfs_plan_t plan, double c, int loc, const double* rhs,
  * up to 4096 CFS_F32_REFINED plans of the current device, of any sizes, z
  * grids, walls and refinement settings.  Every stage of the refined Poisson
  * solve (FP32 transforms and z sweeps, FP64 residual, means and correction) is
- * then one kernel launch for all boxes, and the host waits once per
- * refinement iteration for the whole group instead of once per box.  Each box
- * follows its own refined solve exactly, stopping test included, so its
- * result is bit-identical to cfs_poisson_solve on its plan.
+ * then one kernel launch for all boxes, and the refinement loop runs on the
+ * device: a solve is one CUDA graph whose loop is a conditional WHILE node,
+ * the kernel that ends an iteration setting its condition; the host waits
+ * once, at the end.  The graph reads every per-box record from the group's
+ * tables, so it depends only on the launch shape (number of boxes, blocks and
+ * shared memory of each stage) and is reused across rebindings.  A shape is
+ * captured at its second solve (its first runs as direct launches with the
+ * loop on the host, so one-off shapes pay no capture); 128 graphs are kept
+ * per group.  Each box follows its own refined solve
+ * exactly, stopping test included, so its result is bit-identical to
+ * cfs_poisson_solve on its plan.
  *   cfs_group_create   plans: nplans distinct plan handles (not owned: keep
  *                      them alive while the group exists).  CFS_EUNSUPPORTED
  *                      if a plan is not CFS_F32_REFINED or lives on another
@@ -295,6 +302,10 @@ int cfs_group_poisson_solve(cfs_group_t group, const double* const* f, double* c
 int cfs_group_helmholtz_solve(cfs_group_t group, const double* c, const int* loc,
                               const double* const* rhs, double* const* u, void* stream);
 int cfs_group_last_info(cfs_group_t group, int* iters, double* rel_residual);
+/* on = 0: later solves of the group launch their stages directly and run the
+ * refinement loop on the host (one wait per iteration); on != 0 (the
+ * default): graphs as above.  Both give bit-identical results. */
+int cfs_group_set_graphs(cfs_group_t group, int on);
 
 /*
  * Serving.  The paper has no counterpart.  A server takes Poisson and

@@ -81,6 +81,7 @@ def lib():
             "cfs_group_size": ([vp, ctypes.POINTER(i)], i),
             "cfs_group_poisson_solve": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp], i),
             "cfs_group_last_info": ([vp, ctypes.POINTER(i), ctypes.POINTER(d)], i),
+            "cfs_group_set_graphs": ([vp, i], i),
             "cfs_group_helmholtz_solve": ([vp, dp, ctypes.POINTER(i), ctypes.POINTER(vp),
                                            ctypes.POINTER(vp), vp], i),
             "cfs_helmholtz3d_prepare": ([vp, d, i], i),
@@ -309,13 +310,28 @@ class Group:
     """Several CFS_F32_REFINED plans solved together, one launch per stage for
     all boxes (see cfs_group_create).  The plans must outlive the group."""
 
-    def __init__(self, plans):
+    def __init__(self, plans, capacity=None):
+        """capacity (default: len(plans)): the most plans a later rebind()
+        may take."""
         self.plans = list(plans)
         n = len(self.plans)
-        arr = (ctypes.c_void_p * n)(*[p._h for p in self.plans])
         h = ctypes.c_void_p()
-        _check(lib().cfs_group_create(ctypes.byref(h), n, arr), "cfs_group_create")
-        self._h = h
+        if capacity is None:
+            arr = (ctypes.c_void_p * n)(*[p._h for p in self.plans])
+            _check(lib().cfs_group_create(ctypes.byref(h), n, arr), "cfs_group_create")
+            self._h = h
+        else:
+            _check(lib().cfs_group_reserve(ctypes.byref(h), int(capacity)), "cfs_group_reserve")
+            self._h = h
+            self.rebind(self.plans)
+
+    def rebind(self, plans, stream=None):
+        """Binds the group to other plans (at most its capacity)."""
+        plans = list(plans)
+        n = len(plans)
+        arr = (ctypes.c_void_p * n)(*[p._h for p in plans])
+        _check(lib().cfs_group_rebind(self._h, n, arr, _stream_ptr(stream)), "cfs_group_rebind")
+        self.plans = plans
 
     def close(self):
         if getattr(self, "_h", None):
@@ -362,6 +378,11 @@ class Group:
         _check(lib().cfs_group_helmholtz_solve(self._h, ca, la, fp, pp, _stream_ptr(stream)),
                "cfs_group_helmholtz_solve")
         return outs
+
+    def set_graphs(self, on):
+        """Graph-launched solves with the refinement loop on the device (the
+        default), or direct launches with the loop on the host (on=False)."""
+        _check(lib().cfs_group_set_graphs(self._h, int(bool(on))), "cfs_group_set_graphs")
 
     def last_info(self):
         """Per plan: (FP32 solves, final relative residual) of the last solve."""

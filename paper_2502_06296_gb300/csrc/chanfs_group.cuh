@@ -156,10 +156,17 @@ size_t pcr_group_box64(const cfs_plan* P, const HelmCoef& h, const double* rhs, 
 // Grouped refinement kernels (refine.cu), launched by group.cu.
 cudaError_t launch_group_refine_stage(int stage, const ResBox* boxes, GroupMap g, int total,
                                       const GroupIo* io, int flag, cudaStream_t st);
-cudaError_t launch_group_update(const ResBox* boxes, int nbox, const float* fmax,
-                                const double* tol, const int* maxit, int it, int* active,
-                                int* iters, double* rho, int* nactive, cudaStream_t st);
-cudaError_t launch_group_fmax(const ResBox* boxes, int nbox, float* fmax, cudaStream_t st);
+struct GroupCtl {  // device-side iteration state of a grouped refined solve
+  int it;          // iterations done
+  int nactive;     // boxes still iterating after the last one
+};
+cudaError_t launch_group_start(const ResBox* boxes, int nbox, float* fmax, const int* eligible,
+                               int* active, int* mean_on, int* zero, int* iters, double* rho,
+                               GroupCtl* ctl, cudaStream_t st);
+cudaError_t launch_group_iter_end(const ResBox* boxes, int nbox, const float* fmax,
+                                  const double* tol, const int* maxit, int* active, int* iters,
+                                  double* rho, GroupCtl* ctl, cudaGraphConditionalHandle cond,
+                                  int set_cond, cudaStream_t st);
 cudaError_t launch_group_zero_max(const ResBox* boxes, int nbox, cudaStream_t st);
 enum {
   GSTAGE_PLANE_SUM = 0,
@@ -167,7 +174,8 @@ enum {
   GSTAGE_RESIDUAL = 2,
   GSTAGE_SUBTRACT = 3,
   GSTAGE_HELM_RESIDUAL = 4,  // flag = mode of helm_residual_kernel
-  GSTAGE_UPDATE = 5          // r -= L delta (double-float), r32b and max
+  GSTAGE_UPDATE = 5,         // r -= L delta (double-float), r32b and max
+  GSTAGE_ZERO = 6            // zero solution (boxes with a zero right-hand side)
 };
 
 // Host-side descriptions of one plan's box for the grouped kernels.

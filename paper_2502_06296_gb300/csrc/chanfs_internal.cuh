@@ -2,6 +2,8 @@
 // translation units of libchanfs (not part of the public ABI).
 #pragma once
 
+#include <mutex>
+
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -11,6 +13,14 @@
 #include "../../include/chanfs.h"
 
 namespace chanfs {
+
+// Serialises CUDA graph captures with the library calls that synchronise the
+// whole device or allocate and free device memory (plan creation and
+// destruction, coefficient caches, tuning, group set-up): such a call from
+// one thread while another thread captures a graph would invalidate the
+// capture.  Recursive: those calls nest.
+std::recursive_mutex& capture_mutex();
+using CaptureLock = std::lock_guard<std::recursive_mutex>;
 
 // ----------------------------------------------------------------------------
 // Limits

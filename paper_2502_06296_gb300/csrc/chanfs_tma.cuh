@@ -99,6 +99,15 @@ __device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t 
                : "memory");
 }
 
+// A tensor map read from global memory whose bytes may have been rewritten
+// since an earlier launch read it (grouped solves re-upload their descriptor
+// tables between calls; graph replays reuse the same addresses): the
+// acquire makes the thread's later TMA operations fetch the current
+// descriptor instead of a copy the tensormap proxy may still hold.
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+}
+
 // Generic-proxy writes to shared memory become visible to later TMA stores.
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

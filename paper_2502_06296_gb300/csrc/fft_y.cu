@@ -197,6 +197,7 @@ __global__ void __launch_bounds__(128) fft_y_group_kernel(const YBox* boxes, Gro
   int b, blk;
   if (!group_block(g, &b, &blk)) return;
   const YBox& y = boxes[b];
+  if (threadIdx.x == 0) tensormap_acquire(&y.map);  // thread 0 issues the TMA copies
   fft_y_body<INV, float2>(&y.map, y.d, static_cast<const float2*>(y.tw), y.tk, y.by, y.nbox,
                           y.status, blk % y.ntx, blk / y.ntx, y.ytype,
                           static_cast<const float2*>(y.wy));

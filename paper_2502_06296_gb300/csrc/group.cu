@@ -6,8 +6,13 @@
 // kernels' arithmetic and block partition, the same stopping rule on its own
 // tolerance and FP32-solve budget), so a box's result does not depend on the
 // group it is solved in.  Boxes that converge drop out of the later stages
-// through a device-side mask; the host reads one word per iteration (are any
-// boxes still iterating?) instead of one per box.
+// through a device-side mask, and the iteration itself is driven from the
+// device: a solve is one CUDA graph whose refinement loop is a conditional
+// WHILE node; the kernel that closes an iteration sets the loop condition
+// (any box still iterating?).  The host takes part only at the end, to read
+// the iteration counts.  Graphs are keyed by launch shape and captured at a
+// shape's second solve; other solves run the same launches directly with the
+// loop on the host.
 #include <string.h>
 
 #include <algorithm>
@@ -41,7 +46,7 @@ std::vector<int> offsets(const std::vector<int>& blocks, int* total) {
 // Descriptor tables of a bound group, at fixed offsets of one device buffer
 // (and of its pinned host staging copy) sized for the group's capacity.
 struct GroupTables {
-  size_t xf, xi, y, th, res, sx, sy, sth, sres, splane, sone, ssub, bytes;
+  size_t xf, xi, y, th, res, sx, sy, sth, sres, splane, sone, ssub, neu, bytes;
   explicit GroupTables(int cap) {
     size_t o = 0;
     auto take = [&](size_t n) {
@@ -61,6 +66,7 @@ struct GroupTables {
     splane = take(sizeof(int) * (cap + 1));
     sone = take(sizeof(int) * (cap + 1));
     ssub = take(sizeof(int) * (cap + 1));
+    neu = take(sizeof(int) * cap);
     bytes = o;
   }
 };
@@ -82,11 +88,15 @@ struct cfs_group {
   ResBox* d_res = nullptr;
   int *d_sx = nullptr, *d_sy = nullptr, *d_sth = nullptr, *d_sres = nullptr;
   int *d_splane = nullptr, *d_sone = nullptr, *d_ssub = nullptr;
+  int* d_neumann = nullptr;  // boxes whose operator has the constants as null space
   int tx = 0, ty = 0, tth = 0, tres = 0, tplane = 0, tone = 0, tsub = 0;
   size_t smem_x = 0, smem_y = 0;
   // refinement state
   int* d_active = nullptr;  // boxes still iterating
   int* d_mean = nullptr;    // boxes whose mean is removed (Neumann, nonzero rhs)
+  int* d_zero = nullptr;    // boxes with a zero right-hand side (zero solution)
+  int* d_elig = nullptr;    // Helmholtz: boxes that are refined (the others solve in FP64)
+  GroupCtl* d_ctl = nullptr;
   float* d_fmax = nullptr;
   double* d_tol = nullptr;
   int* d_maxit = nullptr;
@@ -104,17 +114,92 @@ struct cfs_group {
   ResBox* d_hres = nullptr;
   ResBox* h_hres = nullptr;
   int* d_spcr = nullptr;
+  // pinned per-call staging: the copies of a solve (graph nodes included)
+  // read these when they run
+  double* h_tol = nullptr;
+  int* h_maxit = nullptr;
+  int* h_elig = nullptr;
+  int* h_spcr = nullptr;
+  int* h_spcr64 = nullptr;
+  int* h_iters = nullptr;  // results, written by the solve's last copies
+  double* h_rho = nullptr;
+  GroupCtl* h_ctl = nullptr;
+  // Graphs of solves, keyed by launch shape.  A graph's kernels read every
+  // per-box record from the group's device tables, so a graph captured for
+  // one binding serves any later binding with the same launch shape (number
+  // of boxes, total blocks and shared memory of each stage).
+  bool graphs = true;
+  cudaStream_t cap_main = nullptr, cap_body = nullptr;
+  struct Graph {
+    std::vector<long long> sig;
+    cudaGraphExec_t exec = nullptr;
+  };
+  std::vector<Graph> cache;  // least recently used first
+  // launch shapes seen but not yet captured: a shape is captured at its
+  // second solve, so that one-off shapes (a serving loop's varied batches)
+  // run as direct launches and do not pay for a capture
+  std::vector<std::vector<long long>> seen;
   cudaEvent_t io_copied = nullptr;  // staging buffers free again after this
   std::vector<ResBox> res;          // host copy of the bound boxes' residual records
   std::vector<int> last_iters;
   std::vector<double> last_rho;
 };
 
+constexpr size_t kGraphCache = 128;  // graphs kept per group
+constexpr size_t kSeenShapes = 512;  // uncaptured shapes remembered per group
+
+static void drop_graphs(cfs_group* G) {
+  for (auto& g : G->cache)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  G->cache.clear();
+  G->seen.clear();
+}
+
+// The cached graph of launch shape `sig` (moved to the back), or null.
+static cudaGraphExec_t find_graph(cfs_group* G, const std::vector<long long>& sig) {
+  for (size_t i = 0; i < G->cache.size(); ++i)
+    if (G->cache[i].sig == sig) {
+      cfs_group::Graph g = G->cache[i];
+      G->cache.erase(G->cache.begin() + (long)i);
+      G->cache.push_back(g);
+      return g.exec;
+    }
+  return nullptr;
+}
+
+// Whether a solve of launch shape `sig` should capture a graph: on the
+// shape's second solve (the first runs as direct launches).
+static bool capture_now(cfs_group* G, const std::vector<long long>& sig) {
+  for (size_t i = 0; i < G->seen.size(); ++i)
+    if (G->seen[i] == sig) {
+      G->seen.erase(G->seen.begin() + (long)i);
+      return true;
+    }
+  if (G->seen.size() >= kSeenShapes) G->seen.erase(G->seen.begin());
+  G->seen.push_back(sig);
+  return false;
+}
+
+static void keep_graph(cfs_group* G, const std::vector<long long>& sig, cudaGraphExec_t exec) {
+  if (G->cache.size() >= kGraphCache) {
+    cudaGraphExecDestroy(G->cache.front().exec);
+    G->cache.erase(G->cache.begin());
+  }
+  G->cache.push_back({sig, exec});
+}
+
 static void group_free(cfs_group* G) {
+  drop_graphs(G);
   void* ptrs[] = {G->d_tab,   G->d_active, G->d_mean, G->d_fmax, G->d_tol,  G->d_maxit,
                   G->d_iters, G->d_rho,    G->d_nactive, G->d_io, G->d_pcr, G->d_hres,
-                  G->d_spcr, G->d_pcr64, G->d_spcr64};
+                  G->d_spcr, G->d_pcr64, G->d_spcr64, G->d_zero, G->d_elig, G->d_ctl};
   for (void* p : ptrs) cudaFree(p);
+  void* hptrs[] = {G->h_tol, G->h_maxit, G->h_elig, G->h_spcr, G->h_spcr64,
+                   G->h_iters, G->h_rho, G->h_ctl};
+  for (void* p : hptrs)
+    if (p) cudaFreeHost(p);
+  if (G->cap_main) cudaStreamDestroy(G->cap_main);
+  if (G->cap_body) cudaStreamDestroy(G->cap_body);
   if (G->h_pcr64) cudaFreeHost(G->h_pcr64);
   if (G->h_tab) cudaFreeHost(G->h_tab);
   if (G->h_io) cudaFreeHost(G->h_io);
@@ -147,6 +232,19 @@ static int group_alloc(cfs_group* G, int cap) {
   if (e == cudaSuccess) e = cudaMalloc(&G->d_pcr64, sizeof(PcrBox64) * cap);
   if (e == cudaSuccess) e = cudaMallocHost(&G->h_pcr64, sizeof(PcrBox64) * cap);
   if (e == cudaSuccess) e = cudaMalloc(&G->d_spcr64, sizeof(int) * (cap + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_zero, sizeof(int) * cap);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_elig, sizeof(int) * cap);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_ctl, sizeof(GroupCtl));
+  if (e == cudaSuccess) e = cudaMallocHost(&G->h_tol, sizeof(double) * cap);
+  if (e == cudaSuccess) e = cudaMallocHost(&G->h_maxit, sizeof(int) * cap);
+  if (e == cudaSuccess) e = cudaMallocHost(&G->h_elig, sizeof(int) * cap);
+  if (e == cudaSuccess) e = cudaMallocHost(&G->h_spcr, sizeof(int) * (cap + 1));
+  if (e == cudaSuccess) e = cudaMallocHost(&G->h_spcr64, sizeof(int) * (cap + 1));
+  if (e == cudaSuccess) e = cudaMallocHost(&G->h_iters, sizeof(int) * cap);
+  if (e == cudaSuccess) e = cudaMallocHost(&G->h_rho, sizeof(double) * cap);
+  if (e == cudaSuccess) e = cudaMallocHost(&G->h_ctl, sizeof(GroupCtl));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&G->cap_main, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&G->cap_body, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G->io_copied, cudaEventDisableTiming);
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? CFS_ENOMEM : CFS_ECUDA;
   const GroupTables& t = G->tab;
@@ -162,6 +260,7 @@ static int group_alloc(cfs_group* G, int cap) {
   G->d_splane = reinterpret_cast<int*>(G->d_tab + t.splane);
   G->d_sone = reinterpret_cast<int*>(G->d_tab + t.sone);
   G->d_ssub = reinterpret_cast<int*>(G->d_tab + t.ssub);
+  G->d_neumann = reinterpret_cast<int*>(G->d_tab + t.neu);
   return CFS_OK;
 }
 
@@ -237,6 +336,7 @@ static int group_bind(cfs_group* G, int nplans, const cfs_plan_t* plans, cudaStr
   put(t.splane, offsets(bplane, &G->tplane));
   put(t.sone, offsets(bone, &G->tone));
   put(t.ssub, offsets(bsub, &G->tsub));
+  put(t.neu, G->neumann);
   cudaError_t e = cudaMemcpyAsync(G->d_tab, G->h_tab, t.bytes, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaEventRecord(G->io_copied, st);
   if (e != cudaSuccess) return CFS_ECUDA;
@@ -247,6 +347,7 @@ static int group_bind(cfs_group* G, int nplans, const cfs_plan_t* plans, cudaStr
 }
 
 extern "C" int cfs_group_create(cfs_group_t* out, int nplans, const cfs_plan_t* plans) {
+  CaptureLock lock(capture_mutex());
   if (!out) return CFS_EINVAL;
   *out = nullptr;
   if (nplans < 1 || nplans > kMaxGroup || !plans) return CFS_EINVAL;
@@ -269,6 +370,7 @@ extern "C" int cfs_group_create(cfs_group_t* out, int nplans, const cfs_plan_t* 
 }
 
 extern "C" int cfs_group_reserve(cfs_group_t* out, int capacity) {
+  CaptureLock lock(capture_mutex());
   if (!out) return CFS_EINVAL;
   *out = nullptr;
   if (capacity < 1 || capacity > kMaxGroup) return CFS_EINVAL;
@@ -296,6 +398,7 @@ extern "C" int cfs_group_rebind(cfs_group_t G, int nplans, const cfs_plan_t* pla
 }
 
 extern "C" int cfs_group_destroy(cfs_group_t G) {
+  CaptureLock lock(capture_mutex());
   if (!G) return CFS_EINVAL;
   cudaDeviceSynchronize();
   group_free(G);
@@ -303,6 +406,186 @@ extern "C" int cfs_group_destroy(cfs_group_t G) {
 }
 
 static int rc_of(cudaError_t e) { return e == cudaSuccess ? CFS_OK : CFS_ECUDA; }
+
+namespace {
+
+constexpr cudaMemcpyKind kH2D = cudaMemcpyHostToDevice;
+constexpr cudaMemcpyKind kD2H = cudaMemcpyDeviceToHost;
+
+// Builds and instantiates the graph of one solve: head() (the stages up to
+// the loop), a WHILE node whose body is one loop iteration, then tail().
+// The kernels that close an iteration set the node's condition through
+// `cond`; it is 0 at each launch until the head sets it.
+template <class Head, class Body, class Tail>
+cudaError_t build_graph(cfs_group* G, Head head, Body body, Tail tail, cudaGraphExec_t* out) {
+  CaptureLock lock(capture_mutex());
+  *out = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaGraphCreate(&graph, 0);
+  if (e != cudaSuccess) return e;
+  cudaGraphConditionalHandle cond = 0;
+  e = cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault);
+  bool capturing = false;
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(G->cap_main, graph, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed);
+  capturing = e == cudaSuccess;
+  if (e == cudaSuccess) e = head(G->cap_main, cond);
+  // the loop node after everything captured so far
+  cudaGraphNode_t loop = nullptr;
+  cudaGraph_t loop_body = nullptr;
+  if (e == cudaSuccess) {
+    cudaStreamCaptureStatus status;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    e = cudaStreamGetCaptureInfo(G->cap_main, &status, nullptr, &cg, &deps, nullptr, &ndeps);
+    if (e == cudaSuccess && status != cudaStreamCaptureStatusActive) e = cudaErrorStreamCaptureInvalidated;
+    if (e == cudaSuccess) {
+      cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+      np.conditional.handle = cond;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      e = cudaGraphAddNode(&loop, cg, deps, nullptr, ndeps, &np);
+      if (e == cudaSuccess) loop_body = np.conditional.phGraph_out[0];
+    }
+    if (e == cudaSuccess)
+      e = cudaStreamUpdateCaptureDependencies(G->cap_main, &loop, nullptr, 1,
+                                              cudaStreamSetCaptureDependencies);
+  }
+  if (e == cudaSuccess) {
+    e = cudaStreamBeginCaptureToGraph(G->cap_body, loop_body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      const cudaError_t eb = body(G->cap_body, cond);
+      cudaGraph_t ended = nullptr;
+      e = cudaStreamEndCapture(G->cap_body, &ended);
+      if (eb != cudaSuccess) e = eb;
+    }
+  }
+  if (e == cudaSuccess) e = tail(G->cap_main);
+  if (capturing) {
+    cudaGraph_t ended = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(G->cap_main, &ended);
+    if (e == cudaSuccess) e = ee;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    *out = nullptr;
+    cudaGetLastError();
+  }
+  return e;
+}
+
+// ---- Poisson: stages of one grouped solve --------------------------------
+
+// Copies of the call's pointers and settings, the dz-weighted mean of f
+// (Neumann boxes), r_0 = f - mean with its norm, the start state, and the
+// zero solution of boxes whose right-hand side is zero.
+cudaError_t poisson_head(cfs_group* G, cudaStream_t st) {
+  const int nb = G->nbox;
+  cudaError_t e = cudaMemcpyAsync(G->d_io, G->h_io, sizeof(GroupIo) * nb, kH2D, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(G->d_tol, G->h_tol, sizeof(double) * nb, kH2D, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(G->d_maxit, G->h_maxit, sizeof(int) * nb, kH2D, st);
+  GroupMap g{G->d_splane, G->d_neumann, nb};
+  if (e == cudaSuccess)
+    e = launch_group_refine_stage(GSTAGE_PLANE_SUM, G->d_res, g, G->tplane, G->d_io, 0, st);
+  g.start = G->d_sone;
+  if (e == cudaSuccess)
+    e = launch_group_refine_stage(GSTAGE_MEAN_FINAL, G->d_res, g, G->tone, G->d_io, 0, st);
+  if (e == cudaSuccess) e = launch_group_zero_max(G->d_res, nb, st);
+  g = GroupMap{G->d_sres, nullptr, nb};
+  if (e == cudaSuccess)
+    e = launch_group_refine_stage(GSTAGE_RESIDUAL, G->d_res, g, G->tres, G->d_io, 0, st);
+  if (e == cudaSuccess)
+    e = launch_group_start(G->d_res, nb, G->d_fmax, nullptr, G->d_active, G->d_mean, G->d_zero,
+                           G->d_iters, G->d_rho, G->d_ctl, st);
+  g = GroupMap{G->d_ssub, G->d_zero, nb};
+  if (e == cudaSuccess)
+    e = launch_group_refine_stage(GSTAGE_ZERO, G->d_res, g, G->tsub, G->d_io, 0, st);
+  return e;
+}
+
+// One iteration: FP32 solve of the current residual, correction of p, new
+// residual, stopping test.  kind 0: the first (p = delta, residual directly
+// in FP64); kind 1: the second (p += delta, double-float residual update);
+// kind 2: the later ones (as 1, the FP32 right-hand side read from r32b).
+cudaError_t poisson_iteration(cfs_group* G, int kind, cudaGraphConditionalHandle cond,
+                              int set_cond, cudaStream_t st) {
+  const int nb = G->nbox;
+  GroupMap g{G->d_sx, G->d_active, nb};
+  cudaError_t e = launch_rfft_x_group32(G->d_xf, g, G->tx, G->smem_x, false, OUT_SAME, G->d_io,
+                                        kind == 2, st);
+  if (e == cudaSuccess) {
+    g.start = G->d_sy;
+    e = launch_fft_y_group32(G->d_y, g, G->ty, G->smem_y, false, st);
+  }
+  if (e == cudaSuccess) {
+    g.start = G->d_sth;
+    e = launch_thomas_group32(G->d_th, g, G->tth, st);
+  }
+  if (e == cudaSuccess) {
+    g.start = G->d_sy;
+    e = launch_fft_y_group32(G->d_y, g, G->ty, G->smem_y, true, st);
+  }
+  if (e == cudaSuccess) {
+    g.start = G->d_sx;
+    e = launch_rfft_x_group32(G->d_xi, g, G->tx, G->smem_x, true, kind == 0 ? OUT_SET : OUT_ADD,
+                              G->d_io, 0, st);
+  }
+  if (e == cudaSuccess) {
+    g.start = G->d_sres;
+    e = launch_group_refine_stage(kind == 0 ? GSTAGE_RESIDUAL : GSTAGE_UPDATE, G->d_res, g,
+                                  G->tres, G->d_io, 1, st);
+  }
+  if (e == cudaSuccess)
+    e = launch_group_iter_end(G->d_res, nb, G->d_fmax, G->d_tol, G->d_maxit, G->d_active,
+                              G->d_iters, G->d_rho, G->d_ctl, cond, set_cond, st);
+  return e;
+}
+
+// The zero dz-weighted mean of p restored (Neumann boxes, as the single
+// solve does), and the iteration counts and residuals copied out.
+cudaError_t poisson_tail(cfs_group* G, cudaStream_t st) {
+  const int nb = G->nbox;
+  GroupMap g{G->d_splane, G->d_mean, nb};
+  cudaError_t e =
+      launch_group_refine_stage(GSTAGE_PLANE_SUM, G->d_res, g, G->tplane, G->d_io, 1, st);
+  g.start = G->d_sone;
+  if (e == cudaSuccess)
+    e = launch_group_refine_stage(GSTAGE_MEAN_FINAL, G->d_res, g, G->tone, G->d_io, 0, st);
+  g.start = G->d_ssub;
+  if (e == cudaSuccess)
+    e = launch_group_refine_stage(GSTAGE_SUBTRACT, G->d_res, g, G->tsub, G->d_io, 0, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(G->h_iters, G->d_iters, sizeof(int) * nb, kD2H, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(G->h_rho, G->d_rho, sizeof(double) * nb, kD2H, st);
+  return e;
+}
+
+// Host-side loop: reads the count of boxes still iterating after each one.
+cudaError_t read_nactive(cfs_group* G, cudaStream_t st, int* nactive) {
+  cudaError_t e = cudaMemcpyAsync(G->h_ctl, G->d_ctl, sizeof(GroupCtl), kD2H, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  *nactive = e == cudaSuccess ? G->h_ctl->nactive : 0;
+  return e;
+}
+
+// Results of a finished solve (h_iters, h_rho) into the group and plans.
+int finish(cfs_group* G, const int* skip) {
+  int rc = CFS_OK;
+  for (int b = 0; b < G->nbox; ++b) {
+    G->last_iters[b] = G->h_iters[b];
+    G->last_rho[b] = G->h_rho[b];
+    G->plans[b]->last_iters = G->h_iters[b];
+    G->plans[b]->last_rho = G->h_rho[b];
+    if (skip && skip[b]) continue;
+    if (!(G->h_rho[b] <= G->plans[b]->tol)) rc = CFS_ENOTCONVERGED;
+  }
+  return rc;
+}
+
+}  // namespace
 
 extern "C" int cfs_group_poisson_solve(cfs_group_t G, const double* const* f, double* const* p,
                                        void* stream) {
@@ -312,138 +595,60 @@ extern "C" int cfs_group_poisson_solve(cfs_group_t G, const double* const* f, do
     if (!f[b] || !p[b] || static_cast<const void*>(f[b]) == static_cast<const void*>(p[b]))
       return CFS_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // the staging buffer of the previous call must have been copied
+  // the staging buffers of the previous call must have been read
   cudaError_t e = cudaEventSynchronize(G->io_copied);
-  for (int b = 0; b < nb && e == cudaSuccess; ++b) G->h_io[b] = GroupIo{f[b], p[b]};
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(G->d_io, G->h_io, sizeof(GroupIo) * nb, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return CFS_ECUDA;
+  for (int b = 0; b < nb; ++b) {
+    G->h_io[b] = GroupIo{f[b], p[b]};
+    G->h_tol[b] = G->plans[b]->tol;
+    G->h_maxit[b] = G->plans[b]->maxit;
+  }
+  const std::vector<long long> sig = {0, nb, G->tx, G->ty, G->tth, G->tres, G->tplane, G->tone,
+                                      G->tsub, (long long)G->smem_x, (long long)G->smem_y};
+  cudaGraphExec_t exec = G->graphs ? find_graph(G, sig) : nullptr;
+  if (exec || (G->graphs && capture_now(G, sig))) {
+    if (!exec) {
+      e = build_graph(
+          G,
+          [&](cudaStream_t s, cudaGraphConditionalHandle c) {
+            cudaError_t r = poisson_head(G, s);
+            if (r == cudaSuccess) r = poisson_iteration(G, 0, c, 1, s);
+            if (r == cudaSuccess) r = poisson_iteration(G, 1, c, 1, s);
+            return r;
+          },
+          [&](cudaStream_t s, cudaGraphConditionalHandle c) {
+            return poisson_iteration(G, 2, c, 1, s);
+          },
+          [&](cudaStream_t s) { return poisson_tail(G, s); }, &exec);
+      if (e != cudaSuccess) return CFS_ECUDA;
+      keep_graph(G, sig, exec);
+    }
+    e = cudaGraphLaunch(exec, st);
+  } else {
+    e = poisson_head(G, st);
+    int nactive = 0;
+    if (e == cudaSuccess) e = poisson_iteration(G, 0, 0, 0, st);
+    if (e == cudaSuccess) e = read_nactive(G, st, &nactive);
+    for (int kind = 1; nactive > 0 && e == cudaSuccess; kind = 2) {
+      e = poisson_iteration(G, kind, 0, 0, st);
+      if (e == cudaSuccess) e = read_nactive(G, st, &nactive);
+    }
+    if (e == cudaSuccess) e = poisson_tail(G, st);
+  }
   if (e == cudaSuccess) e = cudaEventRecord(G->io_copied, st);
-  if (e != cudaSuccess) return CFS_ECUDA;
-
-  // the plans' current refinement settings
-  std::vector<double> tol(nb);
-  std::vector<int> maxits(nb);
-  for (int b = 0; b < nb; ++b) {
-    tol[b] = G->plans[b]->tol;
-    maxits[b] = G->plans[b]->maxit;
-  }
-  e = cudaMemcpyAsync(G->d_tol, tol.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(G->d_maxit, maxits.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return CFS_ECUDA;
-
-  std::vector<int> on(nb), mean_on(nb);
-  for (int b = 0; b < nb; ++b) mean_on[b] = G->neumann[b];
-  const GroupMap all{nullptr, nullptr, nb};
-  GroupMap g = all;
-  // remove the dz-weighted mean of f (Neumann boxes)
-  e = cudaMemcpyAsync(G->d_mean, mean_on.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) {
-    g.start = G->d_splane;
-    g.active = G->d_mean;
-    e = launch_group_refine_stage(GSTAGE_PLANE_SUM, G->d_res, g, G->tplane, G->d_io, 0, st);
-  }
-  if (e == cudaSuccess) {
-    g.start = G->d_sone;
-    e = launch_group_refine_stage(GSTAGE_MEAN_FINAL, G->d_res, g, G->tone, G->d_io, 0, st);
-  }
-  // r_0 = f - mean and its max-norm (the reference of each box)
-  if (e == cudaSuccess) e = launch_group_zero_max(G->d_res, nb, st);
-  if (e == cudaSuccess) {
-    g.start = G->d_sres;
-    g.active = nullptr;
-    e = launch_group_refine_stage(GSTAGE_RESIDUAL, G->d_res, g, G->tres, G->d_io, 0, st);
-  }
-  if (e == cudaSuccess) e = launch_group_fmax(G->d_res, nb, G->d_fmax, st);
-  std::vector<float> fmax(nb);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(fmax.data(), G->d_fmax, sizeof(float) * nb, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return CFS_ECUDA;
-  int nactive = 0;
-  for (int b = 0; b < nb; ++b) {
-    cfs_plan* P = G->plans[b];
-    on[b] = fmax[b] != 0.0f;
-    mean_on[b] = on[b] && G->neumann[b];
-    nactive += on[b];
-    G->last_iters[b] = 0;
-    G->last_rho[b] = 0.0;
-    if (!on[b])  // zero right-hand side: zero solution
-      e = cudaMemsetAsync(p[b], 0, sizeof(double) * (size_t)P->nx * P->ny * P->nz, st);
-  }
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(G->d_active, on.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(G->d_mean, mean_on.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st);
-  int maxit = 0;
-  for (int b = 0; b < nb; ++b) maxit = std::max(maxit, G->plans[b]->maxit);
-  g.active = G->d_active;
-  for (int it = 0; it < maxit && nactive > 0 && e == cudaSuccess; ++it) {
-    g.start = G->d_sx;
-    e = launch_rfft_x_group32(G->d_xf, g, G->tx, G->smem_x, false, OUT_SAME, G->d_io, it >= 2,
-                              st);
-    if (e == cudaSuccess) {
-      g.start = G->d_sy;
-      e = launch_fft_y_group32(G->d_y, g, G->ty, G->smem_y, false, st);
-    }
-    if (e == cudaSuccess) {
-      g.start = G->d_sth;
-      e = launch_thomas_group32(G->d_th, g, G->tth, st);
-    }
-    if (e == cudaSuccess) {
-      g.start = G->d_sy;
-      e = launch_fft_y_group32(G->d_y, g, G->ty, G->smem_y, true, st);
-    }
-    if (e == cudaSuccess) {
-      g.start = G->d_sx;
-      e = launch_rfft_x_group32(G->d_xi, g, G->tx, G->smem_x, true, it > 0 ? OUT_ADD : OUT_SET,
-                                G->d_io, 0, st);
-    }
-    if (e == cudaSuccess) {  // the first residual directly in FP64, then updates
-      g.start = G->d_sres;
-      e = launch_group_refine_stage(it == 0 ? GSTAGE_RESIDUAL : GSTAGE_UPDATE, G->d_res, g,
-                                    G->tres, G->d_io, 1, st);
-    }
-    if (e == cudaSuccess) e = cudaMemsetAsync(G->d_nactive, 0, sizeof(int), st);
-    if (e == cudaSuccess)
-      e = launch_group_update(G->d_res, nb, G->d_fmax, G->d_tol, G->d_maxit, it, G->d_active,
-                              G->d_iters, G->d_rho, G->d_nactive, st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(&nactive, G->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  }
-  // restore the zero dz-weighted mean of p (Neumann boxes), as the single solve does
-  g.active = G->d_mean;
-  if (e == cudaSuccess) {
-    g.start = G->d_splane;
-    e = launch_group_refine_stage(GSTAGE_PLANE_SUM, G->d_res, g, G->tplane, G->d_io, 1, st);
-  }
-  if (e == cudaSuccess) {
-    g.start = G->d_sone;
-    e = launch_group_refine_stage(GSTAGE_MEAN_FINAL, G->d_res, g, G->tone, G->d_io, 0, st);
-  }
-  if (e == cudaSuccess) {
-    g.start = G->d_ssub;
-    e = launch_group_refine_stage(GSTAGE_SUBTRACT, G->d_res, g, G->tsub, G->d_io, 0, st);
-  }
-  std::vector<int> iters(nb);
-  std::vector<double> rho(nb);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(iters.data(), G->d_iters, sizeof(int) * nb, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(rho.data(), G->d_rho, sizeof(double) * nb, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return rc_of(e);
-  int rc = CFS_OK;
-  for (int b = 0; b < nb; ++b) {
-    if (!on[b]) continue;
-    G->last_iters[b] = iters[b];
-    G->last_rho[b] = rho[b];
-    G->plans[b]->last_iters = iters[b];
-    G->plans[b]->last_rho = rho[b];
-    if (!(rho[b] <= G->plans[b]->tol)) rc = CFS_ENOTCONVERGED;
-  }
-  return rc;
+  return finish(G, nullptr);
+}
+
+// End of a grouped Helmholtz call whose work was issued on st with status e.
+static int finish_helm(cfs_group* G, cudaError_t e, cudaStream_t st) {
+  if (e == cudaSuccess) e = cudaEventRecord(G->io_copied, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return rc_of(e);
+  std::vector<int> fp64(G->nbox);
+  for (int b = 0; b < G->nbox; ++b) fp64[b] = !G->h_elig[b];
+  return finish(G, fp64.data());
 }
 
 extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const int* loc,
@@ -458,12 +663,10 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
   cudaError_t e = cudaEventSynchronize(G->io_copied);  // staging of the previous call is free
   if (e != cudaSuccess) return CFS_ECUDA;
   // Algorithm 2, Step 1 of every box (host, cached per plan), and the
-  // per-call descriptors
-  // Boxes whose plans take FP64 Algorithm 2 directly (CFS_OPT_HELM_FP64) run
-  // in one FP64 launch; the others are refined together.
-  std::vector<int> blocks(nb, 0), blocks64(nb, 0), on(nb, 0), refined(nb, 0);
-  std::vector<double> tol(nb);
-  std::vector<int> maxits(nb);
+  // per-call descriptors.  Boxes whose plans take FP64 Algorithm 2 directly
+  // (CFS_OPT_HELM_FP64) run in one FP64 launch; the others are refined
+  // together.
+  std::vector<int> blocks(nb, 0), blocks64(nb, 0);
   int threads = 0, threads64 = 0, nref = 0;
   size_t smem = 0, smem64 = 0;
   for (int b = 0; b < nb; ++b) {
@@ -472,9 +675,9 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
     int rc = plan_helm_prepare(P, c[b], loc[b], 0, &h);
     if (rc) return rc;
     int th = 0;
-    refined[b] = !P->helm_fp64;
-    nref += refined[b];
-    if (refined[b]) {
+    G->h_elig[b] = !P->helm_fp64;
+    nref += G->h_elig[b];
+    if (G->h_elig[b]) {
       const size_t sm = pcr_group_box(P, *h, &G->h_pcr[b], &blocks[b], &th);
       if (!sm) return CFS_ECUDA;
       threads = std::max(threads, th);
@@ -489,105 +692,108 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
     G->h_hres[b].abc = h->d_abc;
     G->h_hres[b].n = h->n;
     G->h_io[b] = GroupIo{rhs[b], u[b]};
-    tol[b] = P->tol;
-    maxits[b] = P->maxit;
+    G->h_tol[b] = P->tol;
+    G->h_maxit[b] = P->maxit;
   }
   int tpcr = 0, tpcr64 = 0;
-  std::vector<int> spcr = offsets(blocks, &tpcr), spcr64 = offsets(blocks64, &tpcr64);
-  e = cudaMemcpyAsync(G->d_pcr, G->h_pcr, sizeof(PcrBox) * nb, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(G->d_hres, G->h_hres, sizeof(ResBox) * nb, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && tpcr64 > 0)
-    e = cudaMemcpyAsync(G->d_pcr64, G->h_pcr64, sizeof(PcrBox64) * nb, cudaMemcpyHostToDevice,
-                        st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(G->d_io, G->h_io, sizeof(GroupIo) * nb, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaEventRecord(G->io_copied, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(G->d_spcr, spcr.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice,
-                        st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(G->d_spcr64, spcr64.data(), sizeof(int) * (nb + 1),
-                        cudaMemcpyHostToDevice, st);
-  // the FP64 boxes: one launch, no refinement
-  if (e == cudaSuccess && tpcr64 > 0)
-    e = launch_pcr_group64(G->d_pcr64, GroupMap{G->d_spcr64, nullptr, nb}, tpcr64, threads64,
-                           smem64, st);
-  for (int b = 0; b < nb; ++b)
-    if (!refined[b]) {
-      G->last_iters[b] = 0;
-      G->last_rho[b] = 0.0;
-      G->plans[b]->last_iters = 0;
-      G->plans[b]->last_rho = 0.0;
+  const std::vector<int> spcr = offsets(blocks, &tpcr), spcr64 = offsets(blocks64, &tpcr64);
+  memcpy(G->h_spcr, spcr.data(), sizeof(int) * (nb + 1));
+  memcpy(G->h_spcr64, spcr64.data(), sizeof(int) * (nb + 1));
+
+  auto head = [&](cudaStream_t s) {
+    cudaError_t r = cudaMemcpyAsync(G->d_pcr, G->h_pcr, sizeof(PcrBox) * nb, kH2D, s);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(G->d_hres, G->h_hres, sizeof(ResBox) * nb, kH2D, s);
+    if (r == cudaSuccess && tpcr64 > 0)
+      r = cudaMemcpyAsync(G->d_pcr64, G->h_pcr64, sizeof(PcrBox64) * nb, kH2D, s);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(G->d_io, G->h_io, sizeof(GroupIo) * nb, kH2D, s);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(G->d_spcr, G->h_spcr, sizeof(int) * (nb + 1), kH2D, s);
+    if (r == cudaSuccess)
+      r = cudaMemcpyAsync(G->d_spcr64, G->h_spcr64, sizeof(int) * (nb + 1), kH2D, s);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(G->d_tol, G->h_tol, sizeof(double) * nb, kH2D, s);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(G->d_maxit, G->h_maxit, sizeof(int) * nb, kH2D, s);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(G->d_elig, G->h_elig, sizeof(int) * nb, kH2D, s);
+    // the FP64 boxes: one launch, no refinement
+    if (r == cudaSuccess && tpcr64 > 0)
+      r = launch_pcr_group64(G->d_pcr64, GroupMap{G->d_spcr64, nullptr, nb}, tpcr64, threads64,
+                             smem64, s);
+    if (nref == 0) return r;
+    // r_0 = rhs and its max-norm (refined boxes), the start state, zero
+    // solutions of zero right-hand sides
+    GroupMap g{G->d_sres, G->d_elig, nb};
+    if (r == cudaSuccess) r = launch_group_zero_max(G->d_hres, nb, s);
+    if (r == cudaSuccess)
+      r = launch_group_refine_stage(GSTAGE_HELM_RESIDUAL, G->d_hres, g, G->tres, G->d_io, 0, s);
+    if (r == cudaSuccess)
+      r = launch_group_start(G->d_hres, nb, G->d_fmax, G->d_elig, G->d_active, nullptr,
+                             G->d_zero, G->d_iters, G->d_rho, G->d_ctl, s);
+    g = GroupMap{G->d_ssub, G->d_zero, nb};
+    if (r == cudaSuccess)
+      r = launch_group_refine_stage(GSTAGE_ZERO, G->d_hres, g, G->tsub, G->d_io, 0, s);
+    return r;
+  };
+  // one iteration: FP32 Algorithm 2 on the residual, u updated, new residual
+  // (mode 1: u = delta, 2: u += delta), stopping test
+  auto iteration = [&](int mode, cudaGraphConditionalHandle cond, int set_cond, cudaStream_t s) {
+    GroupMap g{G->d_spcr, G->d_active, nb};
+    cudaError_t r = launch_pcr_group32(G->d_pcr, g, tpcr, threads, smem, s);
+    g.start = G->d_sres;
+    if (r == cudaSuccess)
+      r = launch_group_refine_stage(GSTAGE_HELM_RESIDUAL, G->d_hres, g, G->tres, G->d_io, mode, s);
+    if (r == cudaSuccess)
+      r = launch_group_iter_end(G->d_hres, nb, G->d_fmax, G->d_tol, G->d_maxit, G->d_active,
+                                G->d_iters, G->d_rho, G->d_ctl, cond, set_cond, s);
+    return r;
+  };
+  auto tail = [&](cudaStream_t s) {
+    cudaError_t r = cudaMemcpyAsync(G->h_iters, G->d_iters, sizeof(int) * nb, kD2H, s);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(G->h_rho, G->d_rho, sizeof(double) * nb, kD2H, s);
+    return r;
+  };
+
+  if (nref == 0) {  // FP64 boxes only: no refinement loop
+    e = head(st);
+    for (int b = 0; b < nb; ++b) {
+      G->h_iters[b] = 0;
+      G->h_rho[b] = 0.0;
     }
-  if (nref == 0) return e == cudaSuccess ? CFS_OK : CFS_ECUDA;
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(G->d_tol, tol.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(G->d_maxit, maxits.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st);
-  // r_0 = rhs and its max-norm (refined boxes)
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(G->d_active, refined.data(), sizeof(int) * nb, cudaMemcpyHostToDevice,
-                        st);
-  GroupMap g{G->d_sres, G->d_active, nb};
-  if (e == cudaSuccess) e = launch_group_zero_max(G->d_hres, nb, st);
-  if (e == cudaSuccess)
-    e = launch_group_refine_stage(GSTAGE_HELM_RESIDUAL, G->d_hres, g, G->tres, G->d_io, 0, st);
-  if (e == cudaSuccess) e = launch_group_fmax(G->d_hres, nb, G->d_fmax, st);
-  std::vector<float> fmax(nb);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(fmax.data(), G->d_fmax, sizeof(float) * nb, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return CFS_ECUDA;
-  int nactive = 0, maxit = 0;
-  for (int b = 0; b < nb; ++b) {
-    if (!refined[b]) continue;
-    cfs_plan* P = G->plans[b];
-    on[b] = fmax[b] != 0.0f;
-    nactive += on[b];
-    maxit = std::max(maxit, P->maxit);
-    G->last_iters[b] = 0;
-    G->last_rho[b] = 0.0;
-    if (!on[b])  // zero right-hand side: zero solution
-      e = cudaMemsetAsync(u[b], 0, sizeof(double) * (size_t)P->nx * P->ny * P->nz, st);
+    return finish_helm(G, e, st);
   }
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(G->d_active, on.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st);
-  g.active = G->d_active;
-  for (int it = 0; it < maxit && nactive > 0 && e == cudaSuccess; ++it) {
-    g.start = G->d_spcr;
-    e = launch_pcr_group32(G->d_pcr, g, tpcr, threads, smem, st);
-    if (e == cudaSuccess) {
-      g.start = G->d_sres;
-      e = launch_group_refine_stage(GSTAGE_HELM_RESIDUAL, G->d_hres, g, G->tres, G->d_io,
-                                    it == 0 ? 1 : 2, st);
+  const std::vector<long long> sig = {1, nb, tpcr, tpcr64, threads, threads64,
+                                      (long long)smem, (long long)smem64, G->tres, G->tsub};
+  cudaGraphExec_t exec = G->graphs ? find_graph(G, sig) : nullptr;
+  if (exec || (G->graphs && capture_now(G, sig))) {
+    if (!exec) {
+      e = build_graph(
+          G,
+          [&](cudaStream_t s, cudaGraphConditionalHandle cnd) {
+            cudaError_t r = head(s);
+            if (r == cudaSuccess) r = iteration(1, cnd, 1, s);
+            return r;
+          },
+          [&](cudaStream_t s, cudaGraphConditionalHandle cnd) { return iteration(2, cnd, 1, s); },
+          tail, &exec);
+      if (e != cudaSuccess) return CFS_ECUDA;
+      keep_graph(G, sig, exec);
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(G->d_nactive, 0, sizeof(int), st);
-    if (e == cudaSuccess)
-      e = launch_group_update(G->d_hres, nb, G->d_fmax, G->d_tol, G->d_maxit, it, G->d_active,
-                              G->d_iters, G->d_rho, G->d_nactive, st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(&nactive, G->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    e = cudaGraphLaunch(exec, st);
+  } else {
+    e = head(st);
+    int nactive = 0;
+    if (e == cudaSuccess) e = iteration(1, 0, 0, st);
+    if (e == cudaSuccess) e = read_nactive(G, st, &nactive);
+    while (nactive > 0 && e == cudaSuccess) {
+      e = iteration(2, 0, 0, st);
+      if (e == cudaSuccess) e = read_nactive(G, st, &nactive);
+    }
+    if (e == cudaSuccess) e = tail(st);
   }
-  std::vector<int> iters(nb);
-  std::vector<double> rho(nb);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(iters.data(), G->d_iters, sizeof(int) * nb, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(rho.data(), G->d_rho, sizeof(double) * nb, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return rc_of(e);
-  int rc = CFS_OK;
-  for (int b = 0; b < nb; ++b) {
-    if (!on[b]) continue;
-    G->last_iters[b] = iters[b];
-    G->last_rho[b] = rho[b];
-    G->plans[b]->last_iters = iters[b];
-    G->plans[b]->last_rho = rho[b];
-    if (!(rho[b] <= G->plans[b]->tol)) rc = CFS_ENOTCONVERGED;
-  }
-  return rc;
+  return finish_helm(G, e, st);
+}
+
+extern "C" int cfs_group_set_graphs(cfs_group_t G, int on) {
+  if (!G) return CFS_EINVAL;
+  G->graphs = on != 0;
+  return CFS_OK;
 }
 
 extern "C" int cfs_group_last_info(cfs_group_t G, int* iters, double* rel_residual) {

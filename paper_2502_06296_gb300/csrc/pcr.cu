@@ -154,6 +154,10 @@ __global__ void __launch_bounds__(1024) pcr_group_kernel(const PcrBoxT<R>* boxes
   int b, blk;
   if (!group_block(g, &b, &blk)) return;
   const PcrBoxT<R>& x = boxes[b];
+  if (threadIdx.x == 0) {  // thread 0 issues the TMA copies
+    tensormap_acquire(&x.in_map);
+    tensormap_acquire(&x.out_map);
+  }
   pcr_body<R>(&x.in_map, &x.out_map, x.a, x.status, blk, x.blocks);
 }
 

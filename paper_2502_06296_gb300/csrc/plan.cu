@@ -136,6 +136,11 @@ static void thomas_host(const std::vector<double>& a, const std::vector<double>&
 // ----------------------------------------------------------------------------
 // Public ABI
 // ----------------------------------------------------------------------------
+std::recursive_mutex& chanfs::capture_mutex() {
+  static std::recursive_mutex mu;
+  return mu;
+}
+
 extern "C" int cfs_version(void) { return CHANFS_VERSION; }
 
 extern "C" const char* cfs_status_string(int s) {
@@ -198,6 +203,7 @@ extern "C" int cfs_plan_create(cfs_plan_t* out, int nx, int ny, int nz, double l
 extern "C" int cfs_plan_create_walls(cfs_plan_t* out, int nx, int ny, int nz, double lx,
                                      double ly, const double* dz, int poisson_bc, int ybc,
                                      int dtype) {
+  CaptureLock lock(capture_mutex());
   if (!out) return CFS_EINVAL;
   *out = nullptr;
   if (!dz || !(lx > 0) || !(ly > 0) || !isfinite(lx) || !isfinite(ly)) return CFS_EINVAL;
@@ -412,6 +418,7 @@ extern "C" int cfs_plan_create_walls(cfs_plan_t* out, int nx, int ny, int nz, do
 
 extern "C" int cfs_plan_destroy(cfs_plan_t P) {
   if (!P) return CFS_EINVAL;
+  CaptureLock lock(capture_mutex());
   cudaDeviceSynchronize();
   plan_free(P);
   return CFS_OK;
@@ -528,6 +535,7 @@ static void helm_release(cfs_plan* P, HelmCoef& h) {
 }
 
 static int helm_prepare(cfs_plan* P, double c, int loc, int nparts, HelmCoef** res) {
+  CaptureLock lock(capture_mutex());
   if (!(c >= 0) || !isfinite(c)) return CFS_EINVAL;
   if (loc != CFS_LOC_CENTER && loc != CFS_LOC_FACE) return CFS_EINVAL;
   if (nparts < 0 || nparts > kPcrMaxParts) return CFS_EUNSUPPORTED;
@@ -663,6 +671,7 @@ int chanfs::plan_helm_prepare(cfs_plan* P, double c, int loc, int nparts, HelmCo
 
 // Drops the cached Algorithm 2 sets of coefficient c (the tuner's probes).
 void chanfs::plan_helm_forget(cfs_plan* P, double c) {
+  CaptureLock lock(capture_mutex());
   cudaDeviceSynchronize();
   for (size_t i = 0; i < P->helm.size();) {
     if (P->helm[i].c == c) {
@@ -683,6 +692,7 @@ void chanfs::plan_helm_forget(cfs_plan* P, double c) {
 // GPU and kept in a small LRU cache.
 // ----------------------------------------------------------------------------
 static int helm3_prepare(cfs_plan* P, double c, int loc, Helm3Coef** res) {
+  CaptureLock lock(capture_mutex());
   if (!(c >= 0) || !isfinite(c)) return CFS_EINVAL;
   if (loc != CFS_LOC_CENTER && loc != CFS_LOC_FACE) return CFS_EINVAL;
   for (auto& h : P->helm3)
@@ -884,6 +894,7 @@ int chanfs::plan_ensure_stage(cfs_plan* P) { return ensure_stage(P); }
 
 static int ensure_stage(cfs_plan* P) {
   if (P->d_stage) return CFS_OK;
+  CaptureLock lock(capture_mutex());
   const size_t bytes = sizeof(double) * (size_t)P->nx * P->ny * P->nz;
   if (cudaMalloc(&P->d_stage, bytes) != cudaSuccess) return CFS_ENOMEM;
   P->device_bytes += bytes;
@@ -923,6 +934,7 @@ extern "C" int cfs_helmholtz_solve_host(cfs_plan_t P, double c, int loc, const d
 
 extern "C" int cfs_plan_check(cfs_plan_t P, int* device_error) {
   if (!P) return CFS_EINVAL;
+  CaptureLock lock(capture_mutex());
   cudaError_t e = cudaDeviceSynchronize();
   int bits = 0;
   if (e == cudaSuccess) e = cudaMemcpy(&bits, P->d_status, sizeof(int), cudaMemcpyDeviceToHost);

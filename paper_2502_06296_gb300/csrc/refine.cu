@@ -383,21 +383,77 @@ __global__ void subtract_mean_group_kernel(const ResBox* boxes, GroupMap g, cons
   subtract_mean_body(io[b].p, n, r.mean, blk, group_sub_blocks(n));
 }
 
-// After a residual: each active box takes its relative residual and leaves
-// the iteration once it meets its tolerance or has used its FP32 solves.
-// One thread per box; `nactive` counts the boxes still iterating.
-__global__ void group_update_kernel(const ResBox* boxes, int nbox, const float* fmax,
-                                    const double* tol, const int* maxit, int it, int* active,
-                                    int* iters, double* rho, int* nactive) {
+// Zero solution of the boxes whose right-hand side is zero.
+__global__ void zero_fill_group_kernel(const ResBox* boxes, GroupMap g, const GroupIo* io) {
+  int b, blk;
+  if (!group_block(g, &b, &blk)) return;
+  const ResBox& r = boxes[b];
+  const long long n = (long long)r.nx * r.ny * r.nz;
+  const long long nblk = group_sub_blocks(n);
+  double* p = io[b].p;
+  for (long long i = blk * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) p[i] = 0.0;
+}
+
+// After the first residual r_0 = f (- mean): each box's reference norm
+// max|r_0| and its starting state.  A box iterates if it is eligible (null:
+// every box) and r_0 is not zero; an eligible box with r_0 = 0 has the zero
+// solution (zero[b]).  mean_on (may be null) marks the iterating boxes whose
+// solution mean is removed at the end.  Every box starts at 0 iterations.
+__global__ void group_start_kernel(const ResBox* boxes, int nbox, float* fmax,
+                                   const int* eligible, int* active, int* mean_on, int* zero,
+                                   int* iters, double* rho, GroupCtl* ctl) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nbox || !active[b]) return;
+  if (b == 0) {
+    ctl->it = 0;
+    ctl->nactive = 0;
+  }
+  if (b >= nbox) return;
   unsigned int* w = boxes[b].rmax;
-  const float rmax = __uint_as_float(*w);
+  const float f = __uint_as_float(*w);
   *w = 0u;
-  rho[b] = (double)rmax / (double)fmax[b];
-  iters[b] = it + 1;
-  if (rho[b] <= tol[b] || it + 1 >= maxit[b]) active[b] = 0;
-  else atomicAdd(nactive, 1);
+  fmax[b] = f;
+  const int elig = eligible ? eligible[b] : 1;
+  const int on = elig && f != 0.0f;
+  active[b] = on;
+  if (mean_on) mean_on[b] = on && boxes[b].neumann;
+  zero[b] = elig && !on;
+  iters[b] = 0;
+  rho[b] = 0.0;
+}
+
+// After a residual of iteration ctl->it: each active box takes its relative
+// residual and leaves the iteration once it meets its tolerance or has used
+// its FP32 solves.  One block; ctl->nactive counts the boxes still
+// iterating, ctl->it advances, and inside a graph the loop's condition is
+// set to (nactive > 0).
+__global__ void __launch_bounds__(1024) group_iter_end_kernel(
+    const ResBox* boxes, int nbox, const float* fmax, const double* tol, const int* maxit,
+    int* active, int* iters, double* rho, GroupCtl* ctl, cudaGraphConditionalHandle cond,
+    int set_cond) {
+  __shared__ int count;
+  if (threadIdx.x == 0) count = 0;
+  __syncthreads();
+  const int it = ctl->it;
+  int mine = 0;
+  for (int b = threadIdx.x; b < nbox; b += blockDim.x) {
+    if (!active[b]) continue;
+    unsigned int* w = boxes[b].rmax;
+    const float rmax = __uint_as_float(*w);
+    *w = 0u;
+    const double r = (double)rmax / (double)fmax[b];
+    rho[b] = r;
+    iters[b] = it + 1;
+    if (r <= tol[b] || it + 1 >= maxit[b]) active[b] = 0;
+    else ++mine;
+  }
+  if (mine) atomicAdd(&count, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ctl->it = it + 1;
+    ctl->nactive = count;
+    // (a refined solve takes at most 64 FP32 solves: a second bound on the loop)
+    if (set_cond) cudaGraphSetConditional(cond, (count > 0 && it + 1 < 64) ? 1u : 0u);
+  }
 }
 
 // Clears every box's max-norm word before the first residual (a plan's word
@@ -405,15 +461,6 @@ __global__ void group_update_kernel(const ResBox* boxes, int nbox, const float* 
 __global__ void group_zero_max_kernel(const ResBox* boxes, int nbox) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b < nbox) *boxes[b].rmax = 0u;
-}
-
-// The first residual's max |f - mean| of each box (the reference norm).
-__global__ void group_fmax_kernel(const ResBox* boxes, int nbox, float* fmax) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nbox) return;
-  unsigned int* w = boxes[b].rmax;
-  fmax[b] = __uint_as_float(*w);
-  *w = 0u;
 }
 
 cudaError_t launch_group_refine_stage(int stage, const ResBox* boxes, GroupMap g, int total,
@@ -435,6 +482,9 @@ cudaError_t launch_group_refine_stage(int stage, const ResBox* boxes, GroupMap g
     case GSTAGE_HELM_RESIDUAL:
       helm_residual_group_kernel<<<total, kResBlock, 0, st>>>(boxes, g, io, flag);
       break;
+    case GSTAGE_ZERO:
+      zero_fill_group_kernel<<<total, 256, 0, st>>>(boxes, g, io);
+      break;
     default:
       subtract_mean_group_kernel<<<total, 256, 0, st>>>(boxes, g, io);
       break;
@@ -442,11 +492,20 @@ cudaError_t launch_group_refine_stage(int stage, const ResBox* boxes, GroupMap g
   return cudaGetLastError();
 }
 
-cudaError_t launch_group_update(const ResBox* boxes, int nbox, const float* fmax,
-                                const double* tol, const int* maxit, int it, int* active,
-                                int* iters, double* rho, int* nactive, cudaStream_t st) {
-  group_update_kernel<<<(nbox + 127) / 128, 128, 0, st>>>(boxes, nbox, fmax, tol, maxit, it,
-                                                          active, iters, rho, nactive);
+cudaError_t launch_group_start(const ResBox* boxes, int nbox, float* fmax, const int* eligible,
+                               int* active, int* mean_on, int* zero, int* iters, double* rho,
+                               GroupCtl* ctl, cudaStream_t st) {
+  group_start_kernel<<<(nbox + 127) / 128, 128, 0, st>>>(boxes, nbox, fmax, eligible, active,
+                                                         mean_on, zero, iters, rho, ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group_iter_end(const ResBox* boxes, int nbox, const float* fmax,
+                                  const double* tol, const int* maxit, int* active, int* iters,
+                                  double* rho, GroupCtl* ctl, cudaGraphConditionalHandle cond,
+                                  int set_cond, cudaStream_t st) {
+  group_iter_end_kernel<<<1, 1024, 0, st>>>(boxes, nbox, fmax, tol, maxit, active, iters, rho,
+                                            ctl, cond, set_cond);
   return cudaGetLastError();
 }
 
@@ -455,10 +514,6 @@ cudaError_t launch_group_zero_max(const ResBox* boxes, int nbox, cudaStream_t st
   return cudaGetLastError();
 }
 
-cudaError_t launch_group_fmax(const ResBox* boxes, int nbox, float* fmax, cudaStream_t st) {
-  group_fmax_kernel<<<(nbox + 127) / 128, 128, 0, st>>>(boxes, nbox, fmax);
-  return cudaGetLastError();
-}
 
 // ----------------------------------------------------------------------------
 // Self-check of the integer-unit conversions against the hardware's: sample
@@ -633,6 +688,7 @@ int refine_helmholtz(cfs_plan* P, const HelmCoef& h, const double* rhs, double* 
 
 extern "C" int cfs_selfcheck_conversions(unsigned long long samples,
                                          unsigned long long* mismatches) {
+  chanfs::CaptureLock lock(chanfs::capture_mutex());
   if (!mismatches || samples == 0) return CFS_EINVAL;
   unsigned long long* d = nullptr;
   cudaError_t e = cudaMalloc(&d, sizeof(unsigned long long));

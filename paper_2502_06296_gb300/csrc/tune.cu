@@ -71,6 +71,7 @@ static void apply(cfs_plan* P, const Choice& c) {
 
 extern "C" int cfs_plan_autotune(cfs_plan_t P, void* stream) {
   if (!P) return CFS_EINVAL;
+  CaptureLock capture_lock(capture_mutex());
   const bool fp32 = (P->dtype == CFS_F32_REFINED);
   const auto key = std::make_tuple(P->nx, P->ny, P->nz, P->dtype);
   {

@@ -203,3 +203,62 @@ def test_group_helmholtz_with_fp64_direct_boxes(chanfs):
         assert rel(got[i], ref) < (1e-12 if i % 2 == 0 else TOL), (i, rel(got[i], ref))
         assert (info[i][0] == 0) == (i % 2 == 0), info[i]
         plan.close()
+
+
+def test_graph_and_host_loop_give_the_same_bits(chanfs):
+    """A grouped solve launched as one CUDA graph (refinement loop in a
+    conditional node; captured at a launch shape's second solve) and the same
+    solve with the loop on the host give identical fields and iteration
+    records, for Poisson and for Helmholtz calls of several shapes."""
+    boxes = [make_box(chanfs, i, s) for i, s in enumerate(BOXES[:3])]
+    plans = [b[0] for b in boxes]
+    fs = [dev(b[1]) for b in boxes]
+    rhs = [dev(synth.normal(900 + i, b[1].shape)) for i, b in enumerate(boxes)]
+    C, F = chanfs.CENTER, chanfs.FACE
+    patterns = [[C, C, C], [F, F, F], [C, F, C], [F, C, F], [C, C, F], [F, F, C], [C, C, C]]
+    cs = [1e-5, 4e-5, 1e-4]
+    with chanfs.Group(plans) as g:
+        graph_p = [[host(o) for o in g.poisson_solve(fs)] for _ in range(3)]
+        graph_pi = g.last_info()
+        graph_h = []
+        for locs in patterns:
+            for _ in range(2):  # direct launches or a capture, then a graph replay
+                graph_h.append(([host(o) for o in g.helmholtz_solve(cs, rhs, locs)],
+                                g.last_info()))
+        g.set_graphs(False)
+        host_p = [host(o) for o in g.poisson_solve(fs)]
+        host_pi = g.last_info()
+        host_h = []
+        for locs in patterns:
+            host_h.append(([host(o) for o in g.helmholtz_solve(cs, rhs, locs)], g.last_info()))
+    assert graph_pi == host_pi
+    for rep in graph_p:
+        for a, b in zip(rep, host_p):
+            assert np.array_equal(a, b)
+    for k, (ga, gi) in enumerate(graph_h):
+        ha, hi = host_h[k // 2]
+        assert gi == hi
+        for a, b in zip(ga, ha):
+            assert np.array_equal(a, b)
+    for p in plans:
+        p.close()
+
+
+def test_rebinding_reuses_or_captures_graphs(chanfs):
+    """Rebinding to other boxes (a new launch shape) and back (a cached
+    graph, now reading the re-uploaded tables) gives each box its own bits."""
+    boxes = [make_box(chanfs, i, s) for i, s in enumerate(BOXES[:4])]
+    plans = [b[0] for b in boxes]
+    fs = [dev(b[1]) for b in boxes]
+    alone = [host(p.poisson_solve(f)) for p, f in zip(plans, fs)]
+    with chanfs.Group(plans[:2], capacity=4) as g:
+        first = [host(o) for o in g.poisson_solve(fs[:2])]
+        g.rebind(plans[1:4])
+        second = [host(o) for o in g.poisson_solve(fs[1:4])]
+        g.rebind(plans[:2])
+        third = [host(o) for o in g.poisson_solve(fs[:2])]
+    assert all(np.array_equal(a, b) for a, b in zip(first, alone[:2]))
+    assert all(np.array_equal(a, b) for a, b in zip(third, alone[:2]))
+    assert all(np.array_equal(a, b) for a, b in zip(second, alone[1:4]))
+    for p in plans:
+        p.close()
