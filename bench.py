@@ -44,14 +44,24 @@ from paper_2502_06296_gb300 import synth  # noqa: E402
 METRIC = "Poisson+Helmholtz ns/grid-pt, % HBM peak; mixed vs FP64 at 1e-10; p99 latency"
 UNIT = "ns/grid-pt"
 CFG = synth.CHANNEL
-STAGES = ["x_forward", "y_forward", "z_thomas", "y_inverse", "x_inverse", "pcr_u", "pcr_v", "pcr_w"]
+STAGES = ["x_forward", "y_forward", "z_thomas", "y_inverse", "x_inverse", "helm_u", "helm_v",
+          "helm_w"]
+HELM_STAGES = ("helm_u", "helm_v", "helm_w")
 KERNEL_OF_STAGE = {"x_forward": "rfft_x_kernel<false>", "y_forward": "fft_y_kernel<false>",
                    "z_thomas": "thomas_kernel", "y_inverse": "fft_y_kernel<true>",
-                   "x_inverse": "rfft_x_kernel<true>", "pcr_u": "pcr_kernel",
-                   "pcr_v": "pcr_kernel", "pcr_w": "pcr_kernel"}
+                   "x_inverse": "rfft_x_kernel<true>", "helm_u": "pcr_kernel",
+                   "helm_v": "pcr_kernel", "helm_w": "pcr_kernel"}
 SOURCE_OF_STAGE = {"x_forward": "fft_x.cu", "x_inverse": "fft_x.cu", "y_forward": "fft_y.cu",
-                   "y_inverse": "fft_y.cu", "z_thomas": "thomas.cu", "pcr_u": "pcr.cu",
-                   "pcr_v": "pcr.cu", "pcr_w": "pcr.cu"}
+                   "y_inverse": "fft_y.cu", "z_thomas": "thomas.cu", "helm_u": "pcr.cu",
+                   "helm_v": "pcr.cu", "helm_w": "pcr.cu"}
+
+
+def set_helm_method(thomas: bool):
+    """The Helmholtz stages run Algorithm 2 (pcr_kernel) or Thomas sweeps
+    (helm_thomas_kernel), as the plan's option says."""
+    for s in HELM_STAGES:
+        KERNEL_OF_STAGE[s] = "helm_thomas_kernel" if thomas else "pcr_kernel"
+        SOURCE_OF_STAGE[s] = "helm_thomas.cu" if thomas else "pcr.cu"
 
 
 # ----------------------------------------------------------------------------
@@ -67,6 +77,8 @@ def stage_work(stage: str, nx: int, ny: int, nz: int):
         flops = (nx // 2) * nz * 5.0 * ny * np.log2(ny)
     elif stage == "z_thomas":
         flops = 5.0 * npts  # forward: 2 mul + 1 add, backward: 1 mul + 1 add
+    elif KERNEL_OF_STAGE[stage] == "helm_thomas_kernel":
+        flops = 5.0 * npts  # forward: 1 mul + 1 FMA, backward: 1 FMA
     else:
         flops = 9.0 * npts  # Algorithm 2: 2 + 2 (Step 2) + 5 (Step 4)
     return float(flops), 16.0 * npts
@@ -437,8 +449,9 @@ def run_ensemble(chanfs, torch, device, reps: int = 3):
     group.close()
     opts = {}
     for (nx, ny, nz, _, _), pl in zip(boxes, plans32):
-        opts[f"{nx}x{ny}x{nz}"] = [pl.get_option(o) for o in (chanfs.OPT_X_LINES, chanfs.OPT_Y_TILE,
-                                                              chanfs.OPT_THOMAS_TILE, chanfs.OPT_PCR_PARTS)]
+        opts[f"{nx}x{ny}x{nz}"] = [pl.get_option(o) for o in (
+            chanfs.OPT_X_LINES, chanfs.OPT_Y_TILE, chanfs.OPT_THOMAS_TILE, chanfs.OPT_PCR_PARTS,
+            chanfs.OPT_HELM_FP64, chanfs.OPT_HELM_THOMAS, chanfs.OPT_HELM_THOMAS32)]
     for pl in plans32 + plans64:
         pl.close()
     return {"workload": cfg["name"], "boxes": len(boxes), "points": npts,
@@ -453,10 +466,98 @@ def run_ensemble(chanfs, torch, device, reps: int = 3):
             "speedup_vs_per_box_f64": t64 / t_group,
             "max_fp32_solves_last_helmholtz": max(i for i, _ in info),
             "max_rel_residual_last_helmholtz": max(r for _, r in info),
-            "autotuned": "x_lines, y_tile, thomas_tile, pcr_parts per refined box size",
+            "autotuned": "per refined box size: x_lines, y_tile, thomas_tile, pcr_parts, "
+                         "helm_fp64, helm_thomas, helm_thomas32 (Thomas sweeps vs Algorithm 2)",
             "options": opts, "setup_s": round(setup_s, 1),
             "timing": f"median of {reps} CUDA-event timings of whole steps; fields larger than "
                       "L2 in total (no flush between steps)"}
+
+
+def run_cufft_comparison(torch, f, stage_ms, reps: int = 5):
+    """cuFFT (through torch.fft) D2Z / Z2D over (y, x) of the FP64 channel
+    field, timed for comparison only (the library does not use it), beside
+    the x + y stages of the solve (packed real FFT along x, complex FFT along
+    y of the half spectrum)."""
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+    nz, ny, nx = f.shape
+    spec = torch.fft.rfft2(f)
+    t_fwd = timed(lambda: torch.fft.rfft2(f))
+    t_inv = timed(lambda: torch.fft.irfft2(spec, s=(ny, nx)))
+    del spec
+    ours_fwd = stage_ms["x_forward"] + stage_ms["y_forward"]
+    ours_inv = stage_ms["y_inverse"] + stage_ms["x_inverse"]
+    return {"what": "torch.fft.rfft2 / irfft2 (cuFFT D2Z / Z2D) over (y, x) of the FP64 "
+                    f"{nx}x{ny}x{nz} field, comparison only",
+            "cufft_forward_ms": round(t_fwd, 4), "cufft_inverse_ms": round(t_inv, 4),
+            "ours_forward_ms": round(ours_fwd, 4), "ours_inverse_ms": round(ours_inv, 4),
+            "ours_vs_cufft": round((t_fwd + t_inv) / (ours_fwd + ours_inv), 3)}
+
+
+def run_stress(chanfs, torch, device, reps: int = 3):
+    """The paper's per-GPU weak-scaling box shape, 3456 x 3072 x 30 (318.5 M
+    points, a thin wall-normal direction), on one GPU: FP64 Poisson solve and
+    the three Helmholtz solves of the channel step (tanh 1.8 grid, the
+    channel's alpha nu dt), shapes from the tuner; Helmholtz by Algorithm 2
+    and by the tuner's choice."""
+    cfg = dict(synth.STRESS)
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    npts = nx * ny * nz
+    dz = synth.grid_dz(cfg)
+    c = synth.CHANNEL_C
+    gen = torch.Generator(device=device)
+    gen.manual_seed(cfg["seed"])
+    f = torch.randn(nz, ny, nx, dtype=torch.float64, device=device, generator=gen)
+    w = torch.from_numpy(dz).to(device)
+    f -= (f.sum(dim=(1, 2)) * w).sum() / (w.sum() * nx * ny)  # zero dz-weighted mean
+    r = torch.randn(nz, ny, nx, dtype=torch.float64, device=device, generator=gen)
+    out = torch.empty_like(f)
+    locs = (chanfs.CENTER, chanfs.CENTER, chanfs.FACE)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    with chanfs.Plan(nx, ny, nz, cfg["lx"], cfg["ly"], dz, chanfs.NEUMANN) as plan:
+        tuned = plan.autotune()
+        thomas = plan.get_option(chanfs.OPT_HELM_THOMAS)
+        t_p = timed(lambda: plan.poisson_solve(f, out=out))
+        plan.set_option(chanfs.OPT_HELM_THOMAS, 0)
+        t_pcr = timed(lambda: [plan.helmholtz_solve(c, r, loc, out=out) for loc in locs])
+        plan.set_option(chanfs.OPT_HELM_THOMAS, 1)
+        t_th = timed(lambda: [plan.helmholtz_solve(c, r, loc, out=out) for loc in locs])
+        status = plan.check()
+    del f, r, out
+    return {"workload": cfg["name"], "points": npts, "precision": "f64",
+            "poisson_ms": round(t_p, 4), "poisson_ns_per_pt": t_p * 1e6 / npts,
+            "helmholtz3_algorithm2_ms": round(t_pcr, 4),
+            "helmholtz3_thomas_ms": round(t_th, 4),
+            "step_ms_algorithm2": round(t_p + t_pcr, 4),
+            "step_ns_per_pt_algorithm2": (t_p + t_pcr) * 1e6 / npts,
+            "tuner_helmholtz": "thomas" if thomas else "algorithm2",
+            "kernel_shapes": tuned, "device_status": status,
+            "timing": f"median of {reps} CUDA-event timings; fields 2.5 GB (larger than L2)"}
 
 
 # ----------------------------------------------------------------------------
@@ -591,6 +692,8 @@ def run_extras_only(args):
     from paper_2502_06296_gb300 import chanfs
     dev = torch.device("cuda", 0)
     out = {}
+    if not args.no_stress:
+        out["stress"] = run_stress(chanfs, torch, dev)
     if not args.no_ensemble:
         out["ensemble"] = run_ensemble(chanfs, torch, dev)
     if not args.no_serving:
@@ -623,6 +726,11 @@ def run_ours(args):
     f_h, rhs_h = synth.channel_fields(cfg)
     plan = chanfs.Plan(nx, ny, nz, CFG["lx"], CFG["ly"], dz, chanfs.NEUMANN)
     tuned = plan.autotune() if not args.nparts else None  # kernel shapes by measurement
+    # the workload's Helmholtz solves are Algorithm 2 (pre-processed PCR),
+    # whatever the tuner found for the Thomas alternative
+    helm_thomas_tuned = plan.get_option(chanfs.OPT_HELM_THOMAS)
+    plan.set_option(chanfs.OPT_HELM_THOMAS, 0)
+    set_helm_method(False)
     for loc in (chanfs.CENTER, chanfs.FACE):
         plan.helmholtz_prepare(c, loc, args.nparts)
     f = torch.from_numpy(f_h).to(device)
@@ -742,7 +850,8 @@ def run_ours(args):
                    "parallelism": f"replicas{world}",
                    "l2": f"inputs larger than L2 ({npts * 8 / 1e6:.0f} MB fields, L2 129 MB)",
                    "pcr_partitions": args.nparts or plan.get_option(chanfs.OPT_PCR_PARTS),
-                   "kernel_shapes": tuned or "fixed by --nparts"},
+                   "kernel_shapes": tuned or "fixed by --nparts",
+                   "helmholtz_tuner_choice": "thomas" if helm_thomas_tuned else "algorithm2"},
         "e2e": {"value": e2e["value"], "unit": UNIT, "h2d_bytes_per_step": 4 * field_bytes,
                 "d2h_bytes_per_step": 4 * field_bytes, "steps": e2e_steps,
                 "api": "cfs_poisson_solve_host + 3 x cfs_helmholtz_solve_host, pinned host buffers"},
@@ -755,8 +864,11 @@ def run_ours(args):
     }
     line["helmholtz3d"] = run_helmholtz3d(chanfs, torch, device, plan, rhs, us)
     line["ywalls"] = run_ywalls(chanfs, torch, device, f, dz)
+    line["cufft_comparison"] = run_cufft_comparison(torch, f, mean_ms)
     plan.close()
     del f, rhs, p, us, ref_bits
+    if not args.no_stress:
+        line["stress"] = run_stress(chanfs, torch, device)
     if not args.no_mixed:
         line["mixed"] = run_mixed(chanfs, torch, device)
     if not args.no_ensemble:
@@ -782,11 +894,13 @@ def main(argv=None):
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the FP32-refined vs FP64 solve of the 1024x768x512 workload")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 48-box ensemble")
+    ap.add_argument("--no-stress", action="store_true",
+                    help="skip the 3456x3072x30 single-GPU box")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving stream")
     ap.add_argument("--serve-requests", type=int, default=0,
                     help="requests of the serving stream (0: the full 20,000)")
     ap.add_argument("--extras-only", action="store_true",
-                    help="run only the ensemble and serving measurements")
+                    help="run only the stress box, ensemble and serving measurements")
     ap.add_argument("--mixed-nz", type=int, default=0,
                     help="wall-normal size of the mixed comparison (profiling captures only)")
     ap.add_argument("--mixed-only", action="store_true",

@@ -67,7 +67,7 @@ const char* cfs_status_string(int status);
  * cfs_plan_create -- set up a solver for one grid on the current CUDA device
  * (Sec. 2.2.1 "Fourier-based synthesis", Eq. 12; App. A for the layout).
  *   nx     cells along x; even, nx/2 = 2^a 3^b, 2 <= nx <= 4096.
- *   ny     cells along y; 2^a 3^b, 1 <= ny <= 1024.
+ *   ny     cells along y; 2^a 3^b, 1 <= ny <= 4096.
  *   nz     cells along z; 3 <= nz <= 16384.
  *   lx,ly  domain lengths (> 0); dx = lx/nx, dy = ly/ny.
  *   dz     nz HOST doubles, the cell widths along z (all > 0); copied.
@@ -373,6 +373,12 @@ int cfs_server_destroy(cfs_server_t server);
  *       path, below the refinement target), 0 (default) refines FP32 solves.
  *       On hardware where FP64 is scarce the refinement's FP64 residual costs
  *       as much as the FP64 solve itself, so the tuner may pick 1.
+ *   CFS_OPT_HELM_THOMAS  1: the FP64 Helmholtz solves of Eq. 11 run as one
+ *       Thomas sweep per (x, y) column (factors of I - c L_z computed once per
+ *       (c, loc), 3 FP64 instructions per unknown, the intermediate through
+ *       memory); 0 (default): Algorithm 2.  Both are exact direct methods.
+ *   CFS_OPT_HELM_THOMAS32  the same choice for the FP32 inner Helmholtz solves
+ *       of CFS_F32_REFINED plans.
  * cfs_plan_set_option returns CFS_EINVAL for an unknown option or value, and
  * CFS_EUNSUPPORTED if the value cannot run at this plan's size (a tile that
  * does not fit in shared memory).  cfs_plan_get_option reports the value in
@@ -384,7 +390,9 @@ enum {
   CFS_OPT_X_LINES = 2,
   CFS_OPT_Y_TILE = 3,
   CFS_OPT_PCR_PARTS = 4,
-  CFS_OPT_HELM_FP64 = 5
+  CFS_OPT_HELM_FP64 = 5,
+  CFS_OPT_HELM_THOMAS = 6,
+  CFS_OPT_HELM_THOMAS32 = 7
 };
 int cfs_plan_set_option(cfs_plan_t plan, int option, int value);
 int cfs_plan_get_option(cfs_plan_t plan, int option, int* value);

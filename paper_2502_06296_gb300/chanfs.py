@@ -24,6 +24,7 @@ F64, F32_REFINED = 0, 1
 X_FORWARD, Y_FORWARD, Z_SOLVE, Y_INVERSE, X_INVERSE = 0, 1, 2, 3, 4
 
 OPT_THOMAS_TILE, OPT_X_LINES, OPT_Y_TILE, OPT_PCR_PARTS, OPT_HELM_FP64 = 1, 2, 3, 4, 5
+OPT_HELM_THOMAS, OPT_HELM_THOMAS32 = 6, 7
 
 REQ_POISSON, REQ_HELMHOLTZ = 0, 1
 
@@ -264,7 +265,8 @@ class Plan:
         return {name: self.get_option(opt) for name, opt in
                 (("x_lines", OPT_X_LINES), ("y_tile", OPT_Y_TILE),
                  ("thomas_tile", OPT_THOMAS_TILE), ("pcr_parts", OPT_PCR_PARTS),
-                 ("helm_fp64", OPT_HELM_FP64))}
+                 ("helm_fp64", OPT_HELM_FP64), ("helm_thomas", OPT_HELM_THOMAS),
+                 ("helm_thomas32", OPT_HELM_THOMAS32))}
 
     def get_option(self, option: int) -> int:
         """The kernel shape in effect, automatic choices resolved."""

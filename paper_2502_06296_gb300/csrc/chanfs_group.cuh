@@ -91,6 +91,15 @@ inline __host__ __device__ long long group_sub_blocks(long long n) {
   return b < 1216 ? b : 1216;
 }
 
+struct HThomasBox {  // Helmholtz Thomas sweep of one box (helm_thomas.cu)
+  const void* rhs;     // FP32 inner solves: the plan's residual field (in place)
+  void* u;
+  const void* fac;     // fs | fa | fc, 3n
+  long long ncols;     // Nx * Ny
+  int n, nz, face;
+  int per_call;        // FP64 boxes: rhs and u from the call's GroupIo table
+};
+
 template <class R>
 struct PcrArgs {  // Algorithm 2 runtime (pcr.cu)
   R* u;                // output field (for the face wall row)
@@ -152,6 +161,14 @@ cudaError_t launch_pcr_group64(const PcrBox64* boxes, GroupMap g, int total, int
                                size_t smem, cudaStream_t st);
 size_t pcr_group_box64(const cfs_plan* P, const HelmCoef& h, const double* rhs, double* u,
                        PcrBox64* box, int* blocks, int* threads);
+
+// Thomas sweeps of the Helmholtz systems (helm_thomas.cu): `fp32` boxes are
+// the FP32 inner solves of refinement, the others FP64 solves on the call's
+// fields.  Returns the box's shared memory; *blocks its block count.
+size_t helm_thomas_group_box(const cfs_plan* P, const HelmCoef& h, bool fp32, HThomasBox* box,
+                             int* blocks);
+cudaError_t launch_helm_thomas_group(const HThomasBox* boxes, GroupMap g, int total, size_t smem,
+                                     bool fp32, const GroupIo* io, cudaStream_t st);
 
 // Grouped refinement kernels (refine.cu), launched by group.cu.
 cudaError_t launch_group_refine_stage(int stage, const ResBox* boxes, GroupMap g, int total,

@@ -27,7 +27,7 @@ using CaptureLock = std::lock_guard<std::recursive_mutex>;
 // ----------------------------------------------------------------------------
 constexpr int kMaxPasses = 16;     // radix passes of one FFT
 constexpr int kMaxNx = 4096;       // x cells (complex length nx/2 <= 2048)
-constexpr int kMaxNy = 1024;       // y cells
+constexpr int kMaxNy = 4096;       // y cells (a y tile of one FP64 column fits in shared memory)
 constexpr int kMaxNz = 16384;      // z cells
 constexpr int kPcrMaxParts = 64;   // z-partitions (half-warps) of the PCR kernel
 constexpr int kPcrMaxUnknowns = 1024;  // rows of a PCR tile in shared memory
@@ -76,6 +76,8 @@ struct HelmCoef {
   float* d_rows32; // FP32 copies (refined plans)
   float* d_red32;
   double* d_abc;   // 3*n doubles: A' | B' | C' of I - c L_z (refinement residual)
+  double* d_th;    // 3*n doubles: Thomas factors fs | fa | fc of I - c L_z
+  float* d_th32;   // FP32 copies (refined plans)
   unsigned long long stamp;
 };
 
@@ -124,6 +126,8 @@ struct cfs_plan {
   int tk_auto, tk32_auto;  // y tile widths chosen at creation
   int pcr_parts;     // partitions of Helmholtz sets prepared without a count (0: auto)
   int helm_fp64;     // refined plans: Helmholtz by FP64 Algorithm 2 directly, no refinement
+  int helm_thomas;   // FP64 Helmholtz solves by Thomas sweeps instead of Algorithm 2
+  int helm_thomas32; // FP32 inner Helmholtz solves of refinement by Thomas sweeps
   double* d_dzf;     // cell widths (weights of the Neumann mean)
   // Neumann (0,0) column: wn = w/sum(w), gn = g/sum(w) with g = T'^{-T} w,
   // hs = sc * T'^{-1} (0,1,..,1), T' the pinned operator; 3*nz doubles
@@ -200,6 +204,17 @@ size_t pcr_smem_bytes(int n, int nparts);
 cudaError_t launch_pcr_raw(long long ncols, int nz, int n, int nparts, int loc, const double* rows,
                            const double* red, const double* rhs, double* u, int* status,
                            cudaStream_t st);
+// The Helmholtz systems by a Thomas sweep per column (helm_thomas.cu).
+cudaError_t launch_helm_thomas(const cfs_plan* P, const HelmCoef& h, const double* rhs,
+                               double* u, cudaStream_t st);
+cudaError_t launch_helm_thomas32(const cfs_plan* P, const HelmCoef& h, const float* rhs,
+                                 float* u, cudaStream_t st);
+// The plan's choice between them and Algorithm 2 (CFS_OPT_HELM_THOMAS for FP64
+// solves, CFS_OPT_HELM_THOMAS32 for the FP32 inner solves of refinement).
+cudaError_t launch_helm64(const cfs_plan* P, const HelmCoef& h, const double* rhs, double* u,
+                          cudaStream_t st);
+cudaError_t launch_helm32(const cfs_plan* P, const HelmCoef& h, const float* rhs, float* u,
+                          cudaStream_t st);
 cudaError_t launch_pcr32(const cfs_plan* P, const HelmCoef& h, const float* rhs, float* u,
                          cudaStream_t st);
 // Algorithm 2, Step 1 for (c, loc) on the plan, from its cache or computed

@@ -114,6 +114,12 @@ struct cfs_group {
   ResBox* d_hres = nullptr;
   ResBox* h_hres = nullptr;
   int* d_spcr = nullptr;
+  HThomasBox* d_hth = nullptr;  // boxes whose Helmholtz systems take Thomas sweeps
+  HThomasBox* h_hth = nullptr;
+  int* d_sth32 = nullptr;  // block offsets: FP32 inner Thomas sweeps
+  int* d_sth64 = nullptr;  // FP64 direct Thomas sweeps
+  int* h_sth32 = nullptr;
+  int* h_sth64 = nullptr;
   // pinned per-call staging: the copies of a solve (graph nodes included)
   // read these when they run
   double* h_tol = nullptr;
@@ -192,10 +198,11 @@ static void group_free(cfs_group* G) {
   drop_graphs(G);
   void* ptrs[] = {G->d_tab,   G->d_active, G->d_mean, G->d_fmax, G->d_tol,  G->d_maxit,
                   G->d_iters, G->d_rho,    G->d_nactive, G->d_io, G->d_pcr, G->d_hres,
-                  G->d_spcr, G->d_pcr64, G->d_spcr64, G->d_zero, G->d_elig, G->d_ctl};
+                  G->d_spcr, G->d_pcr64, G->d_spcr64, G->d_zero, G->d_elig, G->d_ctl,
+                  G->d_hth, G->d_sth32, G->d_sth64};
   for (void* p : ptrs) cudaFree(p);
   void* hptrs[] = {G->h_tol, G->h_maxit, G->h_elig, G->h_spcr, G->h_spcr64,
-                   G->h_iters, G->h_rho, G->h_ctl};
+                   G->h_iters, G->h_rho, G->h_ctl, G->h_hth, G->h_sth32, G->h_sth64};
   for (void* p : hptrs)
     if (p) cudaFreeHost(p);
   if (G->cap_main) cudaStreamDestroy(G->cap_main);
@@ -243,6 +250,12 @@ static int group_alloc(cfs_group* G, int cap) {
   if (e == cudaSuccess) e = cudaMallocHost(&G->h_iters, sizeof(int) * cap);
   if (e == cudaSuccess) e = cudaMallocHost(&G->h_rho, sizeof(double) * cap);
   if (e == cudaSuccess) e = cudaMallocHost(&G->h_ctl, sizeof(GroupCtl));
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_hth, sizeof(HThomasBox) * cap);
+  if (e == cudaSuccess) e = cudaMallocHost(&G->h_hth, sizeof(HThomasBox) * cap);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_sth32, sizeof(int) * (cap + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_sth64, sizeof(int) * (cap + 1));
+  if (e == cudaSuccess) e = cudaMallocHost(&G->h_sth32, sizeof(int) * (cap + 1));
+  if (e == cudaSuccess) e = cudaMallocHost(&G->h_sth64, sizeof(int) * (cap + 1));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&G->cap_main, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&G->cap_body, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G->io_copied, cudaEventDisableTiming);
@@ -666,9 +679,9 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
   // per-call descriptors.  Boxes whose plans take FP64 Algorithm 2 directly
   // (CFS_OPT_HELM_FP64) run in one FP64 launch; the others are refined
   // together.
-  std::vector<int> blocks(nb, 0), blocks64(nb, 0);
+  std::vector<int> blocks(nb, 0), blocks64(nb, 0), bt32(nb, 0), bt64(nb, 0);
   int threads = 0, threads64 = 0, nref = 0;
-  size_t smem = 0, smem64 = 0;
+  size_t smem = 0, smem64 = 0, smem_t32 = 0, smem_t64 = 0;
   for (int b = 0; b < nb; ++b) {
     cfs_plan* P = G->plans[b];
     HelmCoef* h = nullptr;
@@ -677,11 +690,16 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
     int th = 0;
     G->h_elig[b] = !P->helm_fp64;
     nref += G->h_elig[b];
-    if (G->h_elig[b]) {
+    memset(&G->h_hth[b], 0, sizeof(HThomasBox));
+    if (G->h_elig[b] && P->helm_thomas32) {
+      smem_t32 = std::max(smem_t32, helm_thomas_group_box(P, *h, true, &G->h_hth[b], &bt32[b]));
+    } else if (G->h_elig[b]) {
       const size_t sm = pcr_group_box(P, *h, &G->h_pcr[b], &blocks[b], &th);
       if (!sm) return CFS_ECUDA;
       threads = std::max(threads, th);
       smem = std::max(smem, sm);
+    } else if (P->helm_thomas) {
+      smem_t64 = std::max(smem_t64, helm_thomas_group_box(P, *h, false, &G->h_hth[b], &bt64[b]));
     } else {
       const size_t sm = pcr_group_box64(P, *h, rhs[b], u[b], &G->h_pcr64[b], &blocks64[b], &th);
       if (!sm) return CFS_ECUDA;
@@ -695,10 +713,13 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
     G->h_tol[b] = P->tol;
     G->h_maxit[b] = P->maxit;
   }
-  int tpcr = 0, tpcr64 = 0;
+  int tpcr = 0, tpcr64 = 0, tt32 = 0, tt64 = 0;
   const std::vector<int> spcr = offsets(blocks, &tpcr), spcr64 = offsets(blocks64, &tpcr64);
+  const std::vector<int> st32 = offsets(bt32, &tt32), st64 = offsets(bt64, &tt64);
   memcpy(G->h_spcr, spcr.data(), sizeof(int) * (nb + 1));
   memcpy(G->h_spcr64, spcr64.data(), sizeof(int) * (nb + 1));
+  memcpy(G->h_sth32, st32.data(), sizeof(int) * (nb + 1));
+  memcpy(G->h_sth64, st64.data(), sizeof(int) * (nb + 1));
 
   auto head = [&](cudaStream_t s) {
     cudaError_t r = cudaMemcpyAsync(G->d_pcr, G->h_pcr, sizeof(PcrBox) * nb, kH2D, s);
@@ -712,10 +733,20 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
     if (r == cudaSuccess) r = cudaMemcpyAsync(G->d_tol, G->h_tol, sizeof(double) * nb, kH2D, s);
     if (r == cudaSuccess) r = cudaMemcpyAsync(G->d_maxit, G->h_maxit, sizeof(int) * nb, kH2D, s);
     if (r == cudaSuccess) r = cudaMemcpyAsync(G->d_elig, G->h_elig, sizeof(int) * nb, kH2D, s);
-    // the FP64 boxes: one launch, no refinement
+    if (r == cudaSuccess && tt32 + tt64 > 0) {
+      r = cudaMemcpyAsync(G->d_hth, G->h_hth, sizeof(HThomasBox) * nb, kH2D, s);
+      if (r == cudaSuccess)
+        r = cudaMemcpyAsync(G->d_sth32, G->h_sth32, sizeof(int) * (nb + 1), kH2D, s);
+      if (r == cudaSuccess)
+        r = cudaMemcpyAsync(G->d_sth64, G->h_sth64, sizeof(int) * (nb + 1), kH2D, s);
+    }
+    // the FP64 boxes: one launch per method, no refinement
     if (r == cudaSuccess && tpcr64 > 0)
       r = launch_pcr_group64(G->d_pcr64, GroupMap{G->d_spcr64, nullptr, nb}, tpcr64, threads64,
                              smem64, s);
+    if (r == cudaSuccess && tt64 > 0)
+      r = launch_helm_thomas_group(G->d_hth, GroupMap{G->d_sth64, nullptr, nb}, tt64, smem_t64,
+                                   false, G->d_io, s);
     if (nref == 0) return r;
     // r_0 = rhs and its max-norm (refined boxes), the start state, zero
     // solutions of zero right-hand sides
@@ -736,6 +767,9 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
   auto iteration = [&](int mode, cudaGraphConditionalHandle cond, int set_cond, cudaStream_t s) {
     GroupMap g{G->d_spcr, G->d_active, nb};
     cudaError_t r = launch_pcr_group32(G->d_pcr, g, tpcr, threads, smem, s);
+    g.start = G->d_sth32;
+    if (r == cudaSuccess)
+      r = launch_helm_thomas_group(G->d_hth, g, tt32, smem_t32, true, G->d_io, s);
     g.start = G->d_sres;
     if (r == cudaSuccess)
       r = launch_group_refine_stage(GSTAGE_HELM_RESIDUAL, G->d_hres, g, G->tres, G->d_io, mode, s);
@@ -758,8 +792,11 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
     }
     return finish_helm(G, e, st);
   }
-  const std::vector<long long> sig = {1, nb, tpcr, tpcr64, threads, threads64,
-                                      (long long)smem, (long long)smem64, G->tres, G->tsub};
+  const std::vector<long long> sig = {1,        nb,       tpcr,
+                                      tpcr64,   threads,  threads64,
+                                      (long long)smem,    (long long)smem64,
+                                      tt32,     tt64,     (long long)smem_t32,
+                                      (long long)smem_t64, G->tres, G->tsub};
   cudaGraphExec_t exec = G->graphs ? find_graph(G, sig) : nullptr;
   if (exec || (G->graphs && capture_now(G, sig))) {
     if (!exec) {

@@ -525,12 +525,14 @@ static void helm_release(cfs_plan* P, HelmCoef& h) {
   const size_t n = (size_t)h.n, p = (size_t)h.nparts;
   cudaFree(h.d_rows);
   cudaFree(h.d_red);
-  P->device_bytes -= sizeof(double) * (5 * n + 6 * p);
+  cudaFree(h.d_th);
+  P->device_bytes -= sizeof(double) * (5 * n + 6 * p + 3 * n);
   if (h.d_rows32) {
     cudaFree(h.d_rows32);
     cudaFree(h.d_red32);
     cudaFree(h.d_abc);
-    P->device_bytes -= sizeof(float) * (5 * n + 6 * p) + sizeof(double) * 3 * n;
+    cudaFree(h.d_th32);
+    P->device_bytes -= sizeof(float) * (5 * n + 6 * p + 3 * n) + sizeof(double) * 3 * n;
   }
 }
 
@@ -627,8 +629,20 @@ static int helm_prepare(cfs_plan* P, double c, int loc, int nparts, HelmCoef** r
     rip[j] = 1.0 / piv;
     ripc[j] = rc[j] / piv;
   }
+  // Thomas factors of the same system: fs = 1/piv, fa = A'/piv, fc = C'/piv
+  std::vector<double> th(3 * (size_t)n);
+  {
+    double pv = B[0];
+    for (int i = 0; i < n; ++i) {
+      if (i > 0) pv = B[i] - A[i] * th[2 * (size_t)n + i - 1];
+      th[i] = 1.0 / pv;
+      th[(size_t)n + i] = (i > 0) ? A[i] / pv : 0.0;
+      th[2 * (size_t)n + i] = (i < n - 1) ? C[i] / pv : 0.0;
+    }
+  }
   int rcode = dev_upload(&h.d_rows, rows.data(), rows.size(), &P->device_bytes);
   if (!rcode) rcode = dev_upload(&h.d_red, red.data(), red.size(), &P->device_bytes);
+  if (!rcode) rcode = dev_upload(&h.d_th, th.data(), th.size(), &P->device_bytes);
   if (!rcode && P->dtype == CFS_F32_REFINED) {
     // FP32 copies for the inner solves; the FP64 rows of I - c L_z for the residual
     std::vector<float> rows32(rows.begin(), rows.end()), red32(red.begin(), red.end());
@@ -641,13 +655,17 @@ static int helm_prepare(cfs_plan* P, double c, int loc, int nparts, HelmCoef** r
     rcode = dev_upload(&h.d_rows32, rows32.data(), rows32.size(), &P->device_bytes);
     if (!rcode) rcode = dev_upload(&h.d_red32, red32.data(), red32.size(), &P->device_bytes);
     if (!rcode) rcode = dev_upload(&h.d_abc, abc.data(), abc.size(), &P->device_bytes);
+    std::vector<float> th32(th.begin(), th.end());
+    if (!rcode) rcode = dev_upload(&h.d_th32, th32.data(), th32.size(), &P->device_bytes);
   }
   if (rcode) {
     cudaFree(h.d_rows);
     cudaFree(h.d_red);
+    cudaFree(h.d_th);
     cudaFree(h.d_rows32);
     cudaFree(h.d_red32);
     cudaFree(h.d_abc);
+    cudaFree(h.d_th32);
     return rcode;
   }
   // bounded cache: evict the least recently used entry
@@ -804,7 +822,18 @@ extern "C" int cfs_helmholtz_solve(cfs_plan_t P, double c, int loc, const double
     P->last_iters = 0;
     P->last_rho = 0.0;
   }
-  return cuda_status(launch_pcr(P, *h, rhs, u, st));
+  return cuda_status(launch_helm64(P, *h, rhs, u, st));
+}
+
+cudaError_t chanfs::launch_helm64(const cfs_plan* P, const HelmCoef& h, const double* rhs,
+                                  double* u, cudaStream_t st) {
+  return P->helm_thomas ? launch_helm_thomas(P, h, rhs, u, st) : launch_pcr(P, h, rhs, u, st);
+}
+
+cudaError_t chanfs::launch_helm32(const cfs_plan* P, const HelmCoef& h, const float* rhs,
+                                  float* u, cudaStream_t st) {
+  return P->helm_thomas32 ? launch_helm_thomas32(P, h, rhs, u, st)
+                          : launch_pcr32(P, h, rhs, u, st);
 }
 
 extern "C" int cfs_plan_set_refinement(cfs_plan_t P, double tol, int maxit) {
@@ -845,6 +874,15 @@ extern "C" int cfs_plan_set_option(cfs_plan_t P, int option, int value) {
       if (value != 0 && value != 1) return CFS_EINVAL;
       P->helm_fp64 = value;
       return CFS_OK;
+    case CFS_OPT_HELM_THOMAS:
+      if (value != 0 && value != 1) return CFS_EINVAL;
+      P->helm_thomas = value;
+      return CFS_OK;
+    case CFS_OPT_HELM_THOMAS32:
+      if (value != 0 && value != 1) return CFS_EINVAL;
+      if (value && P->dtype != CFS_F32_REFINED) return CFS_EUNSUPPORTED;
+      P->helm_thomas32 = value;
+      return CFS_OK;
     case CFS_OPT_PCR_PARTS: {
       if (value < 0 || value > kPcrMaxParts) return CFS_EINVAL;
       for (int n = P->nz - 1; value > 0 && n <= P->nz; ++n)  // face and centred fields
@@ -874,6 +912,12 @@ extern "C" int cfs_plan_get_option(cfs_plan_t P, int option, int* value) {
       return CFS_OK;
     case CFS_OPT_HELM_FP64:
       *value = (P->dtype == CFS_F32_REFINED) ? P->helm_fp64 : 1;
+      return CFS_OK;
+    case CFS_OPT_HELM_THOMAS:
+      *value = P->helm_thomas;
+      return CFS_OK;
+    case CFS_OPT_HELM_THOMAS32:
+      *value = P->helm_thomas32;
       return CFS_OK;
     default:
       return CFS_EINVAL;

@@ -671,7 +671,7 @@ int refine_helmholtz(cfs_plan* P, const HelmCoef& h, const double* rhs, double* 
   if (fmax == 0.0f)
     return cuda_rc(cudaMemsetAsync(u, 0, sizeof(double) * (size_t)ncols * P->nz, st));
   for (int it = 0; it < P->maxit; ++it) {
-    cudaError_t e = launch_pcr32(P, h, P->d_r32, P->d_r32, st);
+    cudaError_t e = launch_helm32(P, h, P->d_r32, P->d_r32, st);
     if (e == cudaSuccess) e = residual(it == 0 ? 1 : 2);
     float rmax = 0.0f;
     rc = cuda_rc(e);

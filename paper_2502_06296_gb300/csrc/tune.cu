@@ -2,13 +2,15 @@
 //
 // For one plan the tuner times, with CUDA events on the caller's stream, the
 // candidates of each kernel-shape option (x-lines per CTA, y-tile width,
-// Thomas sweep shape, Algorithm 2 partition count) on the plan's own work
-// fields, and keeps the fastest of each.  The options do not interact through
+// Thomas sweep shape, Algorithm 2 partition count, Algorithm 2 or Thomas
+// sweeps for the Helmholtz systems, refined or FP64 Helmholtz) on the plan's
+// own work fields, and keeps the fastest of each.  The options do not interact through
 // the arithmetic (each only reshapes one kernel's launch), so they are tuned
 // one after the other.  Choices are remembered per process for the plan's
 // (nx, ny, nz, dtype).
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -21,7 +23,7 @@ using namespace chanfs;
 namespace {
 
 struct Choice {
-  int x_lines, y_tile, thomas, pcr_parts, helm_fp64;
+  int x_lines, y_tile, thomas, pcr_parts, helm_fp64, helm_thomas, helm_thomas32;
 };
 
 std::mutex g_mu;
@@ -67,6 +69,8 @@ static void apply(cfs_plan* P, const Choice& c) {
   P->thomas_tw = c.thomas;
   P->pcr_parts = c.pcr_parts;
   P->helm_fp64 = c.helm_fp64;
+  P->helm_thomas = c.helm_thomas;
+  P->helm_thomas32 = c.helm_thomas32;
 }
 
 extern "C" int cfs_plan_autotune(cfs_plan_t P, void* stream) {
@@ -177,12 +181,35 @@ extern "C" int cfs_plan_autotune(cfs_plan_t P, void* stream) {
     }
     plan_helm_forget(P, kProbeC);
   }
-  // Refined plans: refined Helmholtz against FP64 Algorithm 2 directly (both
-  // meet the refinement target), on a constant right-hand side
+  // Helmholtz by Algorithm 2 (best partition count) or by Thomas sweeps: in
+  // the plan's own arithmetic, and for refined plans also in FP64 (the FP64
+  // direct solve of CFS_OPT_HELM_FP64)
+  best.helm_thomas = best.helm_thomas32 = 0;
+  float t_direct64 = 1e30f;
+  {
+    HelmCoef* h = nullptr;
+    if (plan_helm_prepare(P, kProbeC, CFS_LOC_CENTER, best.pcr_parts, &h) == CFS_OK) {
+      const HelmCoef hc = *h;
+      const float tp64 = best_ms(st, [&]() { return launch_pcr(P, hc, s64, s64, st); });
+      const float tt64 = best_ms(st, [&]() { return launch_helm_thomas(P, hc, s64, s64, st); });
+      best.helm_thomas = tt64 < tp64;
+      t_direct64 = std::min(tp64, tt64);
+      if (fp32) {
+        const float tp32 = best_ms(st, [&]() { return launch_pcr32(P, hc, s32, s32, st); });
+        const float tt32 =
+            best_ms(st, [&]() { return launch_helm_thomas32(P, hc, s32, s32, st); });
+        best.helm_thomas32 = tt32 < tp32;
+      }
+    }
+    plan_helm_forget(P, kProbeC);
+  }
+  // Refined plans: refined Helmholtz against the FP64 direct solve (both meet
+  // the refinement target), on a constant right-hand side
   best.helm_fp64 = 0;
   if (fp32 && P->nz <= kPcrMaxUnknowns) {
     double* u = nullptr;
     HelmCoef* h = nullptr;
+    P->helm_thomas32 = best.helm_thomas32;
     if (cudaMalloc(&u, sizeof(double) * npts) == cudaSuccess &&
         cudaMemsetAsync(s64, 0x3f, sizeof(double) * npts, st) == cudaSuccess &&
         plan_helm_prepare(P, kProbeC, CFS_LOC_CENTER, best.pcr_parts, &h) == CFS_OK) {
@@ -190,8 +217,7 @@ extern "C" int cfs_plan_autotune(cfs_plan_t P, void* stream) {
       const float t32 = best_ms(st, [&]() {
         return refine_helmholtz(P, hc, s64, u, st) == CFS_OK ? cudaSuccess : cudaErrorUnknown;
       });
-      const float t64 = best_ms(st, [&]() { return launch_pcr(P, hc, s64, u, st); });
-      best.helm_fp64 = t64 < t32;
+      best.helm_fp64 = t_direct64 < t32;
     }
     cudaStreamSynchronize(st);
     cudaFree(u);

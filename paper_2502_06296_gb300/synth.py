@@ -90,6 +90,10 @@ CHANNEL = dict(name="channel_512x384x384_tanh1.8", nx=512, ny=384, nz=384, lx=12
 # Neumann walls, uniform[-1, 1] right-hand side minus its mean) at 1024 x 768 x 512.
 PRECISION = dict(name="poisson_uniform_1024x768x512", nx=1024, ny=768, nz=512, lx=2 * np.pi,
                  ly=np.pi, beta=None, seed=20250207)
+# The paper's per-GPU machine of its weak-scaling runs (3456 x 3072 x 30), on one
+# GPU: a thin wall-normal direction (tanh 1.8 grid), the channel's box lengths.
+STRESS = dict(name="stress_3456x3072x30_tanh1.8", nx=3456, ny=3072, nz=30, lx=12.8, ly=6.4,
+              beta=1.8, seed=2502066)
 # Helmholtz coefficient of Eq. (11): alpha * nu * dt with alpha = 0.5, nu = 1/5200, dt = 1e-4.
 CHANNEL_C = 0.5 * (1.0 / 5200.0) * 1e-4
 

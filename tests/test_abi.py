@@ -50,7 +50,7 @@ def _create(lib, nx, ny, nz, lx=1.0, ly=1.0, dz=None, bc=0, dtype=0):
     (dict(nx=7, ny=8, nz=8), chanfs.EUNSUPPORTED),      # odd nx
     (dict(nx=10, ny=8, nz=8), chanfs.EUNSUPPORTED),     # nx/2 = 5 not 2^a 3^b
     (dict(nx=8, ny=5, nz=8), chanfs.EUNSUPPORTED),      # ny = 5
-    (dict(nx=8, ny=2048, nz=8), chanfs.EUNSUPPORTED),   # ny too large
+    (dict(nx=8, ny=8192, nz=8), chanfs.EUNSUPPORTED),   # ny too large
     (dict(nx=8192, ny=8, nz=8), chanfs.EUNSUPPORTED),   # nx too large
     (dict(nx=8, ny=8, nz=2), chanfs.EINVAL),            # nz < 3
     (dict(nx=0, ny=8, nz=8), chanfs.EINVAL),

@@ -262,3 +262,29 @@ def test_rebinding_reuses_or_captures_graphs(chanfs):
     assert all(np.array_equal(a, b) for a, b in zip(second, alone[1:4]))
     for p in plans:
         p.close()
+
+
+def test_group_helmholtz_with_thomas_boxes(chanfs):
+    """Boxes whose Helmholtz systems take Thomas sweeps (FP32 inner solves,
+    or FP64 direct) run in their own launches of the same group call,
+    bit-identical to their single solves."""
+    boxes = [make_box(chanfs, i, s) for i, s in enumerate(BOXES[:4])]
+    plans = [b[0] for b in boxes]
+    plans[0].set_option(chanfs.OPT_HELM_THOMAS32, 1)
+    plans[1].set_option(chanfs.OPT_HELM_FP64, 1)
+    plans[1].set_option(chanfs.OPT_HELM_THOMAS, 1)
+    plans[2].set_option(chanfs.OPT_HELM_FP64, 1)
+    cs = [1e-5, 2e-5, 3e-5, 4e-5]
+    locs = [chanfs.FACE, chanfs.CENTER, chanfs.FACE, chanfs.CENTER]
+    rhs = [synth.normal(850 + i, b[1].shape) for i, b in enumerate(boxes)]
+    rd = [dev(r) for r in rhs]
+    alone = [host(p.helmholtz_solve(c, r, loc)) for p, c, r, loc in zip(plans, cs, rd, locs)]
+    with chanfs.Group(plans) as g:
+        for _ in range(2):  # direct launches, then a captured graph
+            got = [host(o) for o in g.helmholtz_solve(cs, rd, locs)]
+            for i in range(4):
+                assert np.array_equal(got[i], alone[i]), i
+    for i, (plan, f, dz) in enumerate(boxes):
+        ref = oracle.helmholtz_solve(rhs[i], dz, cs[i], locs[i])
+        assert rel(got[i], ref) < (1e-12 if i in (1, 2) else TOL), (i, rel(got[i], ref))
+        plan.close()

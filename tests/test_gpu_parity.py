@@ -361,7 +361,18 @@ def test_options_and_autotune_keep_results(chanfs, dtype):
                 u = host(plan.helmholtz_solve(c, dev(rhs)))
                 assert rel(p, ref) < tol and rel(u, href) < tol, (opt, v)
             plan.set_option(opt, 0)
-        for opt, bad in ((chanfs.OPT_X_LINES, 65), (chanfs.OPT_Y_TILE, 33), (chanfs.OPT_PCR_PARTS, 65)):
+        thomas_opt = chanfs.OPT_HELM_THOMAS32 if dtype == 1 else chanfs.OPT_HELM_THOMAS
+        for v in (1, 0):  # Thomas sweeps or Algorithm 2 for the Helmholtz systems
+            plan.set_option(thomas_opt, v)
+            assert plan.get_option(thomas_opt) == v
+            u = host(plan.helmholtz_solve(c, dev(rhs)))
+            assert rel(u, href) < tol, (thomas_opt, v)
+        if dtype == 0:
+            with pytest.raises(chanfs.ChanfsError) as err:
+                plan.set_option(chanfs.OPT_HELM_THOMAS32, 1)  # FP64 plans have no FP32 solves
+            assert err.value.status == chanfs.EUNSUPPORTED
+        for opt, bad in ((chanfs.OPT_X_LINES, 65), (chanfs.OPT_Y_TILE, 33), (chanfs.OPT_PCR_PARTS, 65),
+                         (chanfs.OPT_HELM_THOMAS, 2), (chanfs.OPT_HELM_THOMAS32, -1)):
             with pytest.raises(chanfs.ChanfsError):
                 plan.set_option(opt, bad)
         with pytest.raises(chanfs.ChanfsError) as err:
@@ -376,6 +387,42 @@ def test_options_and_autotune_keep_results(chanfs, dtype):
     # a second plan of the same size takes the remembered choice
     with chanfs.Plan(nx, ny, nz, 2.0, 1.0, dz, 0, dtype) as plan2:
         assert plan2.autotune() == chosen
+
+
+# The z-implicit Helmholtz systems by Thomas sweeps (the tuner's alternative
+# to Algorithm 2): column counts that leave a partial block, columns shorter
+# than the in-thread prefetch, centred and face fields
+HTH_CASES = [
+    ((64, 48, 40), 1.7, 0, 2e-5), ((64, 48, 40), 1.7, 1, 2e-5), ((24, 9, 5), 1.3, 0, 1e-2),
+    ((24, 9, 4), 1.3, 1, 1e-2), ((12, 6, 33), None, 1, 0.3), ((36, 27, 19), 2.2, 0, 0.0),
+]
+
+
+@pytest.mark.parametrize("dims,beta,loc,c", HTH_CASES)
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_helmholtz_thomas_matches_oracle(chanfs, dims, beta, loc, c, dtype):
+    nx, ny, nz = dims
+    if dtype == 1 and nx % 4:
+        pytest.skip("refined plans need nx % 4 == 0")
+    dz = make_dz(nz, beta)
+    rhs = synth.normal(31 * nx + nz + loc, (nz, ny, nx))
+    ref = oracle.helmholtz_solve(rhs, dz, c, loc)
+    tol = 1e-10 if dtype == 1 else TOL
+    with chanfs.Plan(nx, ny, nz, 1.0, 1.0, dz, 0, dtype) as plan:
+        plan.set_option(chanfs.OPT_HELM_THOMAS32 if dtype == 1 else chanfs.OPT_HELM_THOMAS, 1)
+        u = host(plan.helmholtz_solve(c, dev(rhs), loc))
+        assert rel(u, ref) < tol, rel(u, ref)
+        if loc == 1:
+            assert np.all(u[-1] == 0.0)
+        t = dev(rhs)  # in place
+        plan.helmholtz_solve(c, t, loc, out=t)
+        assert np.array_equal(host(t), u)
+        if dtype == 1:  # FP64 direct solve by Thomas sweeps
+            plan.set_option(chanfs.OPT_HELM_FP64, 1)
+            plan.set_option(chanfs.OPT_HELM_THOMAS, 1)
+            u64 = host(plan.helmholtz_solve(c, dev(rhs), loc))
+            assert rel(u64, ref) < TOL, rel(u64, ref)
+        assert plan.check() == 0
 
 
 # Fully implicit 3-D Helmholtz (Eq. 8) on the Poisson machinery
@@ -407,4 +454,77 @@ def test_helmholtz3d_matches_oracle(chanfs, dims, beta, loc, c, dtype):
         # a second coefficient, then the first again (cached set)
         plan.helmholtz3d_solve(2 * c + 1e-3, dev(f), loc)
         assert np.array_equal(host(plan.helmholtz3d_solve(c, dev(f), loc)), u)
+        assert plan.check() == 0
+
+
+def sampled_residual(f, p, lx, ly, dz, bc, c=None, loc=0, samples=20000, seed=5):
+    """max |f - L p| (Poisson) or |f - (p - c L_z p)| (Helmholtz, c given) at
+    seeded sample points, with the oracle's z stencil, relative to max |f|."""
+    nz, ny, nx = f.shape
+    A, B, C = oracle.lz_coefficients(dz, bc, loc)
+    n = len(A)
+    rng = np.random.default_rng(seed)
+    k = rng.integers(0, n, samples)
+    j = rng.integers(0, ny, samples)
+    i = rng.integers(0, nx, samples)
+    P = p[k, j, i]
+    Lz = B[k] * P
+    Lz += np.where(k > 0, A[k] * p[np.maximum(k - 1, 0), j, i], 0.0)
+    Lz += np.where(k < n - 1, C[k] * p[np.minimum(k + 1, n - 1), j, i], 0.0)
+    if c is None:
+        dx2, dy2 = (lx / nx) ** 2, (ly / ny) ** 2
+        L = (p[k, j, (i + 1) % nx] - 2 * P + p[k, j, (i - 1) % nx]) / dx2
+        L += (p[k, (j + 1) % ny, i] - 2 * P + p[k, (j - 1) % ny, i]) / dy2
+        r = f[k, j, i] - (L + Lz)
+    else:
+        r = f[k, j, i] - (P - c * Lz)
+    return float(np.max(np.abs(r)) / np.max(np.abs(f)))
+
+
+@pytest.mark.slow
+def test_stress_box_full_size(chanfs):
+    """The 3456 x 3072 x 30 box of the benchmark (tuned shapes, both
+    Helmholtz methods): the residual of the Eq. 12 / Eq. 11 operators at
+    sampled points, and the zero weighted mean of the Poisson solution."""
+    cfg = synth.STRESS
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    dz = synth.grid_dz(cfg)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(cfg["seed"])
+    f = torch.randn(nz, ny, nx, dtype=torch.float64, device="cuda", generator=gen)
+    w = torch.from_numpy(dz).cuda()
+    f -= (f.sum(dim=(1, 2)) * w).sum() / (w.sum() * nx * ny)
+    fh = host(f)
+    with chanfs.Plan(nx, ny, nz, cfg["lx"], cfg["ly"], dz, chanfs.NEUMANN) as plan:
+        plan.autotune()
+        p = host(plan.poisson_solve(f))
+        assert sampled_residual(fh, p, cfg["lx"], cfg["ly"], dz, 0) < 1e-12
+        mean = float(np.tensordot(p.sum(axis=(1, 2)), dz, 1) / (dz.sum() * nx * ny))
+        assert abs(mean) < 1e-12 * np.max(np.abs(p))
+        del p
+        for thomas in (0, 1):
+            plan.set_option(chanfs.OPT_HELM_THOMAS, thomas)
+            for loc in (chanfs.CENTER, chanfs.FACE):
+                u = host(plan.helmholtz_solve(synth.CHANNEL_C, f, loc))
+                assert sampled_residual(fh, u, 0, 0, dz, 1, synth.CHANNEL_C, loc) < 1e-12
+        assert plan.check() == 0
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_thin_box_matches_oracle(chanfs, dtype):
+    """A reduced box of the stress shape (x and y lengths with factors of 3,
+    a thin z) against the oracle, Helmholtz by both methods."""
+    nx, ny, nz = 432, 384, 30
+    dz = make_dz(nz, 1.8)
+    f = synth.remove_weighted_mean(synth.normal(91, (nz, ny, nx)), dz)
+    tol = 1e-10 if dtype == 1 else TOL
+    ref = oracle.poisson_solve(f, 12.8, 6.4, dz, 0)
+    href = oracle.helmholtz_solve(f, dz, 1e-4, 1)
+    with chanfs.Plan(nx, ny, nz, 12.8, 6.4, dz, 0, dtype) as plan:
+        plan.autotune()
+        assert rel(host(plan.poisson_solve(dev(f))), ref) < tol
+        opt = chanfs.OPT_HELM_THOMAS32 if dtype == 1 else chanfs.OPT_HELM_THOMAS
+        for v in (0, 1):
+            plan.set_option(opt, v)
+            assert rel(host(plan.helmholtz_solve(1e-4, dev(f), 1)), href) < tol
         assert plan.check() == 0
