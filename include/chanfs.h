@@ -379,6 +379,11 @@ int cfs_server_destroy(cfs_server_t server);
  *       memory); 0 (default): Algorithm 2.  Both are exact direct methods.
  *   CFS_OPT_HELM_THOMAS32  the same choice for the FP32 inner Helmholtz solves
  *       of CFS_F32_REFINED plans.
+ *   CFS_OPT_FFT_RADIX  largest radix of the Stockham passes of the x and y
+ *       transforms: 8 (0 or 8, the default: radix-8 passes, then 4, 2, 3s) or
+ *       4 (radix-4 passes, then 2, 3s).  Setting it rebuilds the twiddle
+ *       tables (it waits for the device); groups bound to the plan must be
+ *       rebound.
  * cfs_plan_set_option returns CFS_EINVAL for an unknown option or value, and
  * CFS_EUNSUPPORTED if the value cannot run at this plan's size (a tile that
  * does not fit in shared memory).  cfs_plan_get_option reports the value in
@@ -392,7 +397,8 @@ enum {
   CFS_OPT_PCR_PARTS = 4,
   CFS_OPT_HELM_FP64 = 5,
   CFS_OPT_HELM_THOMAS = 6,
-  CFS_OPT_HELM_THOMAS32 = 7
+  CFS_OPT_HELM_THOMAS32 = 7,
+  CFS_OPT_FFT_RADIX = 8
 };
 int cfs_plan_set_option(cfs_plan_t plan, int option, int value);
 int cfs_plan_get_option(cfs_plan_t plan, int option, int* value);

@@ -24,7 +24,7 @@ F64, F32_REFINED = 0, 1
 X_FORWARD, Y_FORWARD, Z_SOLVE, Y_INVERSE, X_INVERSE = 0, 1, 2, 3, 4
 
 OPT_THOMAS_TILE, OPT_X_LINES, OPT_Y_TILE, OPT_PCR_PARTS, OPT_HELM_FP64 = 1, 2, 3, 4, 5
-OPT_HELM_THOMAS, OPT_HELM_THOMAS32 = 6, 7
+OPT_HELM_THOMAS, OPT_HELM_THOMAS32, OPT_FFT_RADIX = 6, 7, 8
 
 REQ_POISSON, REQ_HELMHOLTZ = 0, 1
 
@@ -266,7 +266,7 @@ class Plan:
                 (("x_lines", OPT_X_LINES), ("y_tile", OPT_Y_TILE),
                  ("thomas_tile", OPT_THOMAS_TILE), ("pcr_parts", OPT_PCR_PARTS),
                  ("helm_fp64", OPT_HELM_FP64), ("helm_thomas", OPT_HELM_THOMAS),
-                 ("helm_thomas32", OPT_HELM_THOMAS32))}
+                 ("helm_thomas32", OPT_HELM_THOMAS32), ("fft_radix", OPT_FFT_RADIX))}
 
     def get_option(self, option: int) -> int:
         """The kernel shape in effect, automatic choices resolved."""

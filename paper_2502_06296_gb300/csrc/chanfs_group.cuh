@@ -192,7 +192,8 @@ enum {
   GSTAGE_SUBTRACT = 3,
   GSTAGE_HELM_RESIDUAL = 4,  // flag = mode of helm_residual_kernel
   GSTAGE_UPDATE = 5,         // r -= L delta (double-float), r32b and max
-  GSTAGE_ZERO = 6            // zero solution (boxes with a zero right-hand side)
+  GSTAGE_ZERO = 6,           // zero solution (boxes with a zero right-hand side)
+  GSTAGE_START = 7           // r_0 = f - mean as FP32 and its norm (sub-block partition)
 };
 
 // Host-side descriptions of one plan's box for the grouped kernels.

@@ -54,7 +54,8 @@ struct FftDesc {
 };
 
 // Builds the radix plan and its FP64 twiddle table on the host.
-bool make_fft_desc(int n, FftDesc* d, std::vector<double2>* tw);
+// Passes of radix 8 (max_radix 8) or 4 first, then at most one 2, then 3s.
+bool make_fft_desc(int n, FftDesc* d, std::vector<double2>* tw, int max_radix);
 
 // ----------------------------------------------------------------------------
 // Helmholtz coefficient set for Algorithm 2 (one (c, loc, nparts) entry).
@@ -128,6 +129,7 @@ struct cfs_plan {
   int helm_fp64;     // refined plans: Helmholtz by FP64 Algorithm 2 directly, no refinement
   int helm_thomas;   // FP64 Helmholtz solves by Thomas sweeps instead of Algorithm 2
   int helm_thomas32; // FP32 inner Helmholtz solves of refinement by Thomas sweeps
+  int fft_radix;     // largest radix of the x and y FFT passes (8 or 4)
   double* d_dzf;     // cell widths (weights of the Neumann mean)
   // Neumann (0,0) column: wn = w/sum(w), gn = g/sum(w) with g = T'^{-T} w,
   // hs = sc * T'^{-1} (0,1,..,1), T' the pinned operator; 3*nz doubles
@@ -205,6 +207,7 @@ cudaError_t launch_pcr_raw(long long ncols, int nz, int n, int nparts, int loc, 
                            const double* red, const double* rhs, double* u, int* status,
                            cudaStream_t st);
 // The Helmholtz systems by a Thomas sweep per column (helm_thomas.cu).
+int plan_set_radix(cfs_plan* P, int max_radix);
 cudaError_t launch_helm_thomas(const cfs_plan* P, const HelmCoef& h, const double* rhs,
                                double* u, cudaStream_t st);
 cudaError_t launch_helm_thomas32(const cfs_plan* P, const HelmCoef& h, const float* rhs,

@@ -13,6 +13,7 @@
 // the iteration counts.  Graphs are keyed by launch shape and captured at a
 // shape's second solve; other solves run the same launches directly with the
 // loop on the host.
+#include <stdint.h>
 #include <string.h>
 
 #include <algorithm>
@@ -420,6 +421,9 @@ extern "C" int cfs_group_destroy(cfs_group_t G) {
 
 static int rc_of(cudaError_t e) { return e == cudaSuccess ? CFS_OK : CFS_ECUDA; }
 
+// Fields are read and written by 16-byte bulk copies and vector loads.
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
 namespace {
 
 constexpr cudaMemcpyKind kH2D = cudaMemcpyHostToDevice;
@@ -508,9 +512,9 @@ cudaError_t poisson_head(cfs_group* G, cudaStream_t st) {
   if (e == cudaSuccess)
     e = launch_group_refine_stage(GSTAGE_MEAN_FINAL, G->d_res, g, G->tone, G->d_io, 0, st);
   if (e == cudaSuccess) e = launch_group_zero_max(G->d_res, nb, st);
-  g = GroupMap{G->d_sres, nullptr, nb};
+  g = GroupMap{G->d_ssub, nullptr, nb};
   if (e == cudaSuccess)
-    e = launch_group_refine_stage(GSTAGE_RESIDUAL, G->d_res, g, G->tres, G->d_io, 0, st);
+    e = launch_group_refine_stage(GSTAGE_START, G->d_res, g, G->tsub, G->d_io, 0, st);
   if (e == cudaSuccess)
     e = launch_group_start(G->d_res, nb, G->d_fmax, nullptr, G->d_active, G->d_mean, G->d_zero,
                            G->d_iters, G->d_rho, G->d_ctl, st);
@@ -605,7 +609,8 @@ extern "C" int cfs_group_poisson_solve(cfs_group_t G, const double* const* f, do
   if (!G || !f || !p || G->nbox < 1) return CFS_EINVAL;
   const int nb = G->nbox;
   for (int b = 0; b < nb; ++b)
-    if (!f[b] || !p[b] || static_cast<const void*>(f[b]) == static_cast<const void*>(p[b]))
+    if (!f[b] || !p[b] || static_cast<const void*>(f[b]) == static_cast<const void*>(p[b]) ||
+        !aligned16(f[b]) || !aligned16(p[b]))
       return CFS_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // the staging buffers of the previous call must have been read
@@ -616,7 +621,8 @@ extern "C" int cfs_group_poisson_solve(cfs_group_t G, const double* const* f, do
     G->h_tol[b] = G->plans[b]->tol;
     G->h_maxit[b] = G->plans[b]->maxit;
   }
-  const std::vector<long long> sig = {0, nb, G->tx, G->ty, G->tth, G->tres, G->tplane, G->tone,
+  const std::vector<long long> sig = {0,       nb,      G->tx,     G->ty,
+                                      G->tth,  G->tres, G->tplane, G->tone,
                                       G->tsub, (long long)G->smem_x, (long long)G->smem_y};
   cudaGraphExec_t exec = G->graphs ? find_graph(G, sig) : nullptr;
   if (exec || (G->graphs && capture_now(G, sig))) {
@@ -670,7 +676,8 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
   if (!G || !c || !loc || !rhs || !u || G->nbox < 1) return CFS_EINVAL;
   const int nb = G->nbox;
   for (int b = 0; b < nb; ++b)
-    if (!rhs[b] || !u[b] || static_cast<const void*>(rhs[b]) == static_cast<const void*>(u[b]))
+    if (!rhs[b] || !u[b] || static_cast<const void*>(rhs[b]) == static_cast<const void*>(u[b]) ||
+        !aligned16(rhs[b]) || !aligned16(u[b]))
       return CFS_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaEventSynchronize(G->io_copied);  // staging of the previous call is free

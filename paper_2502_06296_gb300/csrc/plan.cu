@@ -26,13 +26,14 @@ static double2 root(long long e, long long n) {
   return make_double2(cos(a), -sin(a));
 }
 
-bool make_fft_desc(int n, FftDesc* d, std::vector<double2>* tw) {
+bool make_fft_desc(int n, FftDesc* d, std::vector<double2>* tw, int max_radix) {
   memset(d, 0, sizeof(*d));
   d->n = n;
   int rest = n;
   std::vector<int> rad;
-  while (rest % 8 == 0) { rad.push_back(8); rest /= 8; }
-  if (rest % 4 == 0) { rad.push_back(4); rest /= 4; }
+  if (max_radix >= 8)
+    while (rest % 8 == 0) { rad.push_back(8); rest /= 8; }
+  while (rest % 4 == 0) { rad.push_back(4); rest /= 4; }
   if (rest % 2 == 0) { rad.push_back(2); rest /= 2; }
   while (rest % 3 == 0) { rad.push_back(3); rest /= 3; }
   if (rest != 1 || (int)rad.size() > kMaxPasses) return false;
@@ -268,7 +269,8 @@ extern "C" int cfs_plan_create_walls(cfs_plan_t* out, int nx, int ny, int nz, do
   P->tk32_auto = P->tk32;
 
   std::vector<double2> twx, twy;
-  if (!make_fft_desc(P->M, &P->fx, &twx) || !make_fft_desc(ny, &P->fy, &twy)) {
+  P->fft_radix = 8;
+  if (!make_fft_desc(P->M, &P->fx, &twx, 8) || !make_fft_desc(ny, &P->fy, &twy, 8)) {
     plan_free(P);
     return CFS_EUNSUPPORTED;
   }
@@ -843,6 +845,36 @@ extern "C" int cfs_plan_set_refinement(cfs_plan_t P, double tol, int maxit) {
   return CFS_OK;
 }
 
+// Rebuilds the x and y radix plans with passes of at most max_radix (8 or 4)
+// and replaces their twiddle tables (FP64, and FP32 for refined plans).  The
+// table sizes do not change (n - 1 entries), so neither do the tiles.
+int chanfs::plan_set_radix(cfs_plan* P, int max_radix) {
+  if (P->fft_radix == max_radix) return CFS_OK;
+  CaptureLock lock(capture_mutex());
+  FftDesc fx, fy;
+  std::vector<double2> twx, twy;
+  if (!make_fft_desc(P->M, &fx, &twx, max_radix) || !make_fft_desc(P->ny, &fy, &twy, max_radix))
+    return CFS_EUNSUPPORTED;
+  cudaDeviceSynchronize();  // no solve may be reading the old tables
+  auto put64 = [&](double2* dst, const std::vector<double2>& v) {
+    return cudaMemcpy(dst, v.data(), sizeof(double2) * v.size(), cudaMemcpyHostToDevice);
+  };
+  auto put32 = [&](float2* dst, const std::vector<double2>& v) {
+    std::vector<float2> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = make_float2((float)v[i].x, (float)v[i].y);
+    return cudaMemcpy(dst, o.data(), sizeof(float2) * o.size(), cudaMemcpyHostToDevice);
+  };
+  cudaError_t e = put64(P->d_twx, twx);
+  if (e == cudaSuccess) e = put64(P->d_twy, twy);
+  if (e == cudaSuccess && P->d_twx32) e = put32(P->d_twx32, twx);
+  if (e == cudaSuccess && P->d_twy32) e = put32(P->d_twy32, twy);
+  if (e != cudaSuccess) return CFS_ECUDA;
+  P->fx = fx;
+  P->fy = fy;
+  P->fft_radix = max_radix;
+  return CFS_OK;
+}
+
 extern "C" int cfs_plan_set_option(cfs_plan_t P, int option, int value) {
   if (!P) return CFS_EINVAL;
   switch (option) {
@@ -878,6 +910,9 @@ extern "C" int cfs_plan_set_option(cfs_plan_t P, int option, int value) {
       if (value != 0 && value != 1) return CFS_EINVAL;
       P->helm_thomas = value;
       return CFS_OK;
+    case CFS_OPT_FFT_RADIX:
+      if (value != 0 && value != 4 && value != 8) return CFS_EINVAL;
+      return plan_set_radix(P, value ? value : 8);
     case CFS_OPT_HELM_THOMAS32:
       if (value != 0 && value != 1) return CFS_EINVAL;
       if (value && P->dtype != CFS_F32_REFINED) return CFS_EUNSUPPORTED;
@@ -915,6 +950,9 @@ extern "C" int cfs_plan_get_option(cfs_plan_t P, int option, int* value) {
       return CFS_OK;
     case CFS_OPT_HELM_THOMAS:
       *value = P->helm_thomas;
+      return CFS_OK;
+    case CFS_OPT_FFT_RADIX:
+      *value = P->fft_radix;
       return CFS_OK;
     case CFS_OPT_HELM_THOMAS32:
       *value = P->helm_thomas32;

@@ -37,12 +37,30 @@ __device__ __forceinline__ void block_max_to(float v, unsigned int* out) {
 // Neumann compatibility: the dz-weighted mean of f, reduced in a fixed order
 // (one block per z plane, then one block over the planes) so that results
 // are bit-reproducible.
+// Each thread sums a strided part of the plane with 16-byte loads, eight
+// values in flight and four accumulators (a plane is an even number of
+// values: nx is even), then the block reduces in a fixed tree.
 __device__ __forceinline__ void plane_sum_body(const double* __restrict__ f, long long nxy,
                                                const double* dzf, double* partial, int k) {
   __shared__ double sh[256];
-  const double* plane = f + (long long)k * nxy;
-  double s = 0.0;
-  for (long long i = threadIdx.x; i < nxy; i += blockDim.x) s += plane[i];
+  const double2* plane = reinterpret_cast<const double2*>(f + (long long)k * nxy);
+  const long long n2 = nxy >> 1;
+  const long long B = blockDim.x;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  long long i = threadIdx.x;
+  for (; i + 3 * B < n2; i += 4 * B) {
+    const double2 a = plane[i], b = plane[i + B], c = plane[i + 2 * B], d = plane[i + 3 * B];
+    s0 += a.x + c.x;
+    s1 += a.y + c.y;
+    s2 += b.x + d.x;
+    s3 += b.y + d.y;
+  }
+  for (; i < n2; i += B) {
+    const double2 a = plane[i];
+    s0 += a.x;
+    s1 += a.y;
+  }
+  const double s = (s0 + s1) + (s2 + s3);
   sh[threadIdx.x] = s;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
@@ -244,6 +262,33 @@ __global__ void __launch_bounds__(kResBlock) poisson_update_kernel(
   poisson_update_body(dlt, rdf, r32, z2, rmax, nx, ny, nz, ybc, blockIdx.x);
 }
 
+// r_0 = f - mean (mean may be null: r_0 = f) as FP32, and max |r_0|: a flat
+// pass over the n points (n even) with 16-byte loads, blocks striding by
+// nblk (the same partition in the single and the grouped launch).
+__device__ __forceinline__ void rhs_start_body(const double* __restrict__ f,
+                                               const double* __restrict__ mean,
+                                               float* __restrict__ r32, unsigned int* rmax,
+                                               long long n, long long blk, long long nblk) {
+  const double mu = mean ? *mean : 0.0;
+  const double2* f2 = reinterpret_cast<const double2*>(f);
+  float2* r2 = reinterpret_cast<float2*>(r32);
+  float vmax = 0.0f;
+  for (long long i = blk * blockDim.x + threadIdx.x; i < (n >> 1); i += nblk * blockDim.x) {
+    const double2 v = f2[i];
+    const float2 r = make_float2(f64_to_f32(v.x - mu), f64_to_f32(v.y - mu));
+    r2[i] = r;
+    vmax = fmaxf(vmax, fmaxf(fabsf(r.x), fabsf(r.y)));
+  }
+  block_max_to(vmax, rmax);
+}
+
+__global__ void __launch_bounds__(256) rhs_start_kernel(const double* __restrict__ f,
+                                                        const double* __restrict__ mean,
+                                                        float* __restrict__ r32,
+                                                        unsigned int* rmax, long long n) {
+  rhs_start_body(f, mean, r32, rmax, n, blockIdx.x, gridDim.x);
+}
+
 __global__ void __launch_bounds__(kResBlock) poisson_residual_kernel(
     const double* __restrict__ f, const double* __restrict__ p, const double* __restrict__ zop,
     const double* __restrict__ mean, float* __restrict__ r32, float2* __restrict__ rdf,
@@ -354,6 +399,16 @@ __global__ void __launch_bounds__(kResBlock) poisson_residual_group_kernel(const
   poisson_residual_body(io[b].f, with_p ? io[b].p : nullptr, r.zop, r.neumann ? r.mean : nullptr,
                         r.r32, with_p ? r.rdf : nullptr, r.rmax, r.nx, r.ny, r.nz, r.idx2,
                         r.idy2, r.ybc, blk);
+}
+
+__global__ void __launch_bounds__(256) rhs_start_group_kernel(const ResBox* boxes, GroupMap g,
+                                                              const GroupIo* io) {
+  int b, blk;
+  if (!group_block(g, &b, &blk)) return;
+  const ResBox& r = boxes[b];
+  const long long n = (long long)r.nx * r.ny * r.nz;
+  rhs_start_body(io[b].f, r.neumann ? r.mean : nullptr, r.r32, r.rmax, n, blk,
+                 group_sub_blocks(n));
 }
 
 __global__ void __launch_bounds__(kResBlock) helm_residual_group_kernel(const ResBox* boxes,
@@ -485,6 +540,9 @@ cudaError_t launch_group_refine_stage(int stage, const ResBox* boxes, GroupMap g
     case GSTAGE_ZERO:
       zero_fill_group_kernel<<<total, 256, 0, st>>>(boxes, g, io);
       break;
+    case GSTAGE_START:
+      rhs_start_group_kernel<<<total, 256, 0, st>>>(boxes, g, io);
+      break;
     default:
       subtract_mean_group_kernel<<<total, 256, 0, st>>>(boxes, g, io);
       break;
@@ -595,9 +653,9 @@ int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st) {
   // r_0 = f - mean and the reference norm ||f - mean||_inf
   if (e == cudaSuccess) e = cudaMemsetAsync(P->d_red, 0, sizeof(unsigned int), st);
   if (e == cudaSuccess) {
-    poisson_residual_kernel<<<grid, kResBlock, 0, st>>>(f, nullptr, P->d_zop, mean, P->d_r32,
-                                                        nullptr, max_word(P), P->nx, P->ny, P->nz,
-                                                        idx2, idy2, P->ybc);
+    const long long n = nxy * P->nz;
+    rhs_start_kernel<<<(unsigned)group_sub_blocks(n), 256, 0, st>>>(f, mean, P->d_r32,
+                                                                   max_word(P), n);
     e = cudaGetLastError();
   }
   float fmax = 0.0f;

@@ -25,9 +25,10 @@ namespace chanfs {
 
 
 constexpr int kThomasBlock = 64;
-// Rows each thread keeps in flight ahead of its sweep (by arithmetic type): an
-// FP64 sweep is bound by the FP64 pipe and needs few; an FP32 sweep is bound
-// by memory latency.
+// Rows each thread keeps in flight ahead of its sweep (by arithmetic type):
+// an FP64 sweep is bound by the FP64 pipe and needs few; an FP32 sweep is
+// bound by memory latency.  (Deeper prefetch spills at the register budget
+// of 14 blocks of 64 threads per SM.)
 template <class CA> struct prefetch_rows { static constexpr int value = 3; };
 template <> struct prefetch_rows<float2> { static constexpr int value = 6; };
 
@@ -60,30 +61,32 @@ template <class CA, class CS> __device__ __forceinline__ CA cvt(CS v) {
 //   x  = T'^{-1} E' - mu h - nu,  E' = (0, E_1, ..)
 //   nu = (g^T E' - mu g^T 1') / sum w     (dz-weighted mean of the solution)
 // with h = T'^{-1} (0, 1, .., 1) and g = T'^{-T} w precomputed by the plan.
-template <class CS, class CA, class F2, class F1>
+//
+// ONE: the real and imaginary parts share factor set x (every column but
+// kx = 0); fy0 and by0 are then not read.
+template <class CS, class CA, bool ONE, int PF, class F2, class F1>
 __device__ __forceinline__ void sweep_column(const ThomasArgs& a, CS* const s0, const F2* const fx0,
                                              const F2* const fy0, const F1* const bx0,
                                              const F1* const by0, const bool sing) {
   using T = typename cplx_traits<CA>::T;
-  constexpr int PF = prefetch_rows<CA>::value;
   const int nz = a.nz;
   const long long rs = (long long)a.ny * a.M;         // spectrum row stride
   const long long rt = (long long)a.nky * (a.M + 1);  // factor row stride
 
   // forward: g_k = (s/piv_k) f_k - (A_k/piv_k) g_{k-1}, in place
   CS qu[PF];
-  F2 qx[PF], qy[PF];
+  F2 qx[PF], qy[ONE ? 1 : PF];
 #pragma unroll
   for (int i = 0; i < PF; ++i) {
     if (i < nz) {
       qu[i] = s0[i * rs];
       qx[i] = fx0[i * rt];
-      qy[i] = fy0[i * rt];
+      if (!ONE) qy[i] = fy0[i * rt];
     }
   }
   const CS* pu = s0 + PF * rs;  // next rows to prefetch
   const F2* px = fx0 + PF * rt;
-  const F2* py = fy0 + PF * rt;
+  const F2* py = ONE ? px : fy0 + PF * rt;
   CS* ps = s0;                         // row being written
   CA g = cplx_traits<CA>::mk(T(0), T(0));
   double mu = 0.0, gam = 0.0;
@@ -92,15 +95,15 @@ __device__ __forceinline__ void sweep_column(const ThomasArgs& a, CS* const s0, 
     for (int i = 0; i < PF; ++i) {
       if (k + i >= nz) break;
       CA u = cvt<CA>(qu[i]);
-      const F2 fx = qx[i], fy = qy[i];
+      const F2 fx = qx[i], fy = ONE ? fx : qy[i];
       if (k + i + PF < nz) {
         qu[i] = *pu;
         qx[i] = *px;
-        qy[i] = *py;
+        if (!ONE) qy[i] = *py;
       }
       pu += rs;
       px += rt;
-      py += rt;
+      if (!ONE) py += rt;
       if (sing) {
         mu = fma(a.sing[k + i], (double)u.x, mu);
         if (k + i > 0) gam = fma(a.sing[nz + k + i], (double)u.x, gam);
@@ -115,16 +118,16 @@ __device__ __forceinline__ void sweep_column(const ThomasArgs& a, CS* const s0, 
 
   // backward: x_k = g_k - (C_k/piv_k) x_{k+1}, from the top wall down
   CS qg[PF];
-  F1 qbx[PF], qby[PF];
+  F1 qbx[PF], qby[ONE ? 1 : PF];
   CS* const s1 = s0 + (long long)(nz - 1) * rs;
   const F1* const bx1 = bx0 + (long long)(nz - 1) * rt;
-  const F1* const by1 = by0 + (long long)(nz - 1) * rt;
+  const F1* const by1 = ONE ? bx1 : by0 + (long long)(nz - 1) * rt;
 #pragma unroll
   for (int i = 0; i < PF; ++i) {
     if (i < nz) {
       qg[i] = s1[-i * rs];
       qbx[i] = bx1[-i * rt];
-      qby[i] = by1[-i * rt];
+      if (!ONE) qby[i] = by1[-i * rt];
     }
   }
   const CS* pg = s1 - PF * rs;
@@ -137,15 +140,15 @@ __device__ __forceinline__ void sweep_column(const ThomasArgs& a, CS* const s0, 
     for (int i = 0; i < PF; ++i) {
       if (r + i >= nz) break;
       const CA gg = cvt<CA>(qg[i]);
-      const F1 bx = qbx[i], by = qby[i];
+      const F1 bx = qbx[i], by = ONE ? bx : qby[i];
       if (r + i + PF < nz) {
         qg[i] = *pg;
         qbx[i] = *pbx;
-        qby[i] = *pby;
+        if (!ONE) qby[i] = *pby;
       }
       pg -= rs;
       pbx -= rt;
-      pby -= rt;
+      if (!ONE) pby -= rt;
       x = cplx_traits<CA>::mk(fma(-bx, x.x, gg.x), fma(-by, x.y, gg.y));
       CA out = x;
       if (sing) out.x = (T)(fma(-mu, a.sing[2 * nz + (nz - 1 - r - i)], (double)out.x) - nu);
@@ -161,11 +164,16 @@ __device__ __forceinline__ void sweep_column(const ThomasArgs& a, CS* const s0, 
 // refinement) the near-singular columns of small |kx|, |ky| -- the singular
 // Neumann (0,0) one included -- are still solved in FP64 arithmetic with the
 // FP64 factors, the rest in FP32.
+//
+// The columns split into two launches: the main kernel takes every column
+// with kx >= 1 in the spectrum's own precision, whose real and imaginary
+// parts share one factor set (fewer loads and registers, deeper prefetch);
+// the special kernel takes column kx = 0 of every slot (two real columns, or
+// the singular one) and, for FP32 spectra, the FP64 columns.
+
+// Column (ky, j) in full generality.
 template <class CS>
-__device__ __forceinline__ void thomas_body(const ThomasArgs& a, int blk) {
-  const int ky = blk / a.nblk_x;
-  const int j = (blk % a.nblk_x) * kThomasBlock + threadIdx.x;
-  if (j >= a.M) return;
+__device__ __forceinline__ void thomas_column(const ThomasArgs& a, int ky, int j) {
   // factor sets of the real (x) and imaginary (y) parts
   int kx_x = j, kx_y = j, kp_x, kp_y;
   if (a.ywall) {  // every slot its own column; column 0 holds the real pair F(0) + i F(M)
@@ -188,23 +196,89 @@ __device__ __forceinline__ void thomas_body(const ThomasArgs& a, int blk) {
   const long long oy = (long long)kp_y * (a.M + 1) + kx_y;
   const bool fp64 = sizeof(CS) == sizeof(double2) || sing ||
                     (kx_x < a.kx64 && kp_x < a.ky64 && kx_y < a.kx64 && kp_y < a.ky64);
+  // (one row of prefetch: these few columns run beside the main ones, whose
+  // register budget the kernel keeps)
   if (fp64)
-    sweep_column<CS, double2>(a, s0, a.fwd + ox, a.fwd + oy, a.bwd + ox, a.bwd + oy, sing);
+    sweep_column<CS, double2, false, 1>(a, s0, a.fwd + ox, a.fwd + oy, a.bwd + ox, a.bwd + oy,
+                                        sing);
   else
-    sweep_column<CS, float2>(a, s0, a.fwd32 + ox, a.fwd32 + oy, a.bwd32 + ox, a.bwd32 + oy, false);
+    sweep_column<CS, float2, false, 1>(a, s0, a.fwd32 + ox, a.fwd32 + oy, a.bwd32 + ox,
+                                       a.bwd32 + oy, false);
+}
+
+// Whether column (ky, j >= 1) of an FP32 spectrum is solved in FP64.
+__device__ __forceinline__ bool fp64_column(const ThomasArgs& a, int ky, int j) {
+  const int kp = a.ywall ? ky : min(ky, a.ny - ky);
+  return j < a.kx64 && kp < a.ky64;
 }
 
 template <class CS>
-__global__ void __launch_bounds__(kThomasBlock, 11) thomas_kernel(ThomasArgs a) {
-  thomas_body<CS>(a, blockIdx.x);
+__device__ __forceinline__ void thomas_body(const ThomasArgs& a, int blk) {
+  const int ky = blk / a.nblk_x;
+  const int j = (blk % a.nblk_x) * kThomasBlock + threadIdx.x;
+  if (j == 0 || j >= a.M) return;
+  if (sizeof(CS) == sizeof(float2) && fp64_column(a, ky, j)) return;
+  const int kp = a.ywall ? ky : min(ky, a.ny - ky);
+  CS* const s0 = reinterpret_cast<CS*>(a.S) + (long long)ky * a.M + j;
+  const long long o = (long long)kp * (a.M + 1) + j;
+  if constexpr (sizeof(CS) == sizeof(double2))
+    sweep_column<CS, double2, true, prefetch_rows<double2>::value>(a, s0, a.fwd + o, a.fwd + o,
+                                                                   a.bwd + o, a.bwd + o, false);
+  else
+    sweep_column<CS, float2, true, prefetch_rows<float2>::value>(
+        a, s0, a.fwd32 + o, a.fwd32 + o, a.bwd32 + o, a.bwd32 + o, false);
+}
+
+// Columns per slot of the special kernel: kx = 0, and for FP32 spectra the
+// FP64 columns kx < kx64.
+template <class CS>
+__host__ __device__ inline int special_width(const ThomasArgs& a) {
+  if (sizeof(CS) == sizeof(double2)) return 1;
+  const int w = a.kx64 > 1 ? a.kx64 : 1;
+  return w < a.M ? w : a.M;
+}
+
+template <class CS>
+__device__ __forceinline__ void thomas_special_body(const ThomasArgs& a, int blk) {
+  const int kxs = special_width<CS>(a);
+  const int t = blk * kThomasBlock + threadIdx.x;
+  const int j = t % kxs, ky = t / kxs;
+  if (ky >= a.ny) return;
+  if (j > 0 && !fp64_column(a, ky, j)) return;  // the main kernel's column
+  thomas_column<CS>(a, ky, j);
+}
+
+template <class CS>
+__host__ __device__ inline int special_blocks(const ThomasArgs& a) {
+  return (a.ny * special_width<CS>(a) + kThomasBlock - 1) / kThomasBlock;
+}
+
+// One launch: the special columns' blocks first (their sweeps are the
+// longest-latency ones and overlap the main columns), then the main blocks.
+template <class CS>
+__device__ __forceinline__ void thomas_launch_body(const ThomasArgs& a, int blk) {
+  const int nsp = special_blocks<CS>(a);
+  if (blk < nsp) thomas_special_body<CS>(a, blk);
+  else thomas_body<CS>(a, blk - nsp);
+}
+
+template <class CS>
+__global__ void __launch_bounds__(kThomasBlock, 14) thomas_kernel(ThomasArgs a) {
+  thomas_launch_body<CS>(a, blockIdx.x);
 }
 
 // One launch for several boxes (FP32 inner solves of grouped refinement).
-__global__ void __launch_bounds__(kThomasBlock, 11) thomas_group_kernel(const ThomasArgs* boxes,
+__global__ void __launch_bounds__(kThomasBlock, 14) thomas_group_kernel(const ThomasArgs* boxes,
                                                                         GroupMap g) {
   int b, blk;
   if (!group_block(g, &b, &blk)) return;
-  thomas_body<float2>(boxes[b], blk);
+  thomas_launch_body<float2>(boxes[b], blk);
+}
+
+template <class CS>
+static cudaError_t launch_streaming(const ThomasArgs& a, int ny, cudaStream_t st) {
+  thomas_kernel<CS><<<special_blocks<CS>(a) + a.nblk_x * ny, kThomasBlock, 0, st>>>(a);
+  return cudaGetLastError();
 }
 
 // ----------------------------------------------------------------------------
@@ -558,9 +632,7 @@ static cudaError_t launch_thomas_t(const cfs_plan* P, void* data, cudaStream_t s
   const int tw = pick_tile_width<CS>(P, P->thomas_tw);
   if (tw == 16) return launch_tile<CS, 16, tile_depth<CS, 16>::DG>(P, data, st);
   if (tw == 8) return launch_tile<CS, 8, tile_depth<CS, 8>::DG>(P, data, st);
-  ThomasArgs a = thomas_args(P, data);
-  thomas_kernel<CS><<<a.nblk_x * P->ny, kThomasBlock, 0, st>>>(a);
-  return cudaGetLastError();
+  return launch_streaming<CS>(thomas_args(P, data), P->ny, st);
 }
 
 cudaError_t launch_thomas(const cfs_plan* P, double* data, cudaStream_t st) {
@@ -632,8 +704,7 @@ cudaError_t launch_thomas_set(const cfs_plan* P, double* data, const double2* fw
   a.nz = n;
   a.neumann = 0;
   a.kx64 = a.ky64 = 0;  // (ywall as for the plan)
-  thomas_kernel<double2><<<a.nblk_x * P->ny, kThomasBlock, 0, st>>>(a);
-  return cudaGetLastError();
+  return launch_streaming<double2>(a, P->ny, st);
 }
 
 cudaError_t launch_thomas_factor(cfs_plan* P, const double* dA, const double* dB, const double* dC,
@@ -648,7 +719,7 @@ cudaError_t launch_thomas_factor(cfs_plan* P, const double* dA, const double* dB
 
 size_t thomas_group_box(const cfs_plan* P, ThomasArgs* box, int* blocks) {
   *box = thomas_args(P, P->d_r32);
-  *blocks = box->nblk_x * P->ny;
+  *blocks = special_blocks<float2>(*box) + box->nblk_x * P->ny;
   return 0;
 }
 

@@ -1,7 +1,7 @@
 // tune.cu -- per-size choice of kernel shapes by measurement.
 //
 // For one plan the tuner times, with CUDA events on the caller's stream, the
-// candidates of each kernel-shape option (x-lines per CTA, y-tile width,
+// candidates of each kernel-shape option (FFT radix plan, x-lines per CTA, y-tile width,
 // Thomas sweep shape, Algorithm 2 partition count, Algorithm 2 or Thomas
 // sweeps for the Helmholtz systems, refined or FP64 Helmholtz) on the plan's
 // own work fields, and keeps the fastest of each.  The options do not interact through
@@ -23,7 +23,7 @@ using namespace chanfs;
 namespace {
 
 struct Choice {
-  int x_lines, y_tile, thomas, pcr_parts, helm_fp64, helm_thomas, helm_thomas32;
+  int x_lines, y_tile, thomas, pcr_parts, helm_fp64, helm_thomas, helm_thomas32, radix;
 };
 
 std::mutex g_mu;
@@ -63,6 +63,7 @@ constexpr double kProbeC = 3.0517578125e-5;  // Helmholtz coefficient of the pro
 }  // namespace
 
 static void apply(cfs_plan* P, const Choice& c) {
+  plan_set_radix(P, c.radix);
   P->x_lines = c.x_lines;
   if (P->dtype == CFS_F32_REFINED) P->tk32 = c.y_tile;
   else P->tk = c.y_tile;
@@ -99,6 +100,31 @@ extern "C" int cfs_plan_autotune(cfs_plan_t P, void* stream) {
   const size_t cs = fp32 ? sizeof(float2) : sizeof(double2);
   Choice best{};
 
+  // radix plan of the x and y transforms (default tiles), all four passes
+  {
+    float tbest = 1e30f;
+    best.radix = 8;
+    for (int r : {8, 4}) {
+      if (plan_set_radix(P, r) != CFS_OK) continue;
+      const float t = best_ms(st, [&]() {
+        cudaError_t e = fp32 ? launch_rfft_x32(P, s32, s32, false, st)
+                             : launch_rfft_x(P, s64, s64, false, 1.0, st);
+        if (e == cudaSuccess)
+          e = fp32 ? launch_fft_y32(P, s32, false, st) : launch_fft_y(P, s64, false, st);
+        if (e == cudaSuccess)
+          e = fp32 ? launch_fft_y32(P, s32, true, st) : launch_fft_y(P, s64, true, st);
+        if (e == cudaSuccess)
+          e = fp32 ? launch_rfft_x32_to64(P, s32, s64, false, st)
+                   : launch_rfft_x(P, s64, s64, true, 1.0, st);
+        return e;
+      });
+      if (t < tbest) {
+        tbest = t;
+        best.radix = r;
+      }
+    }
+    if (plan_set_radix(P, best.radix) != CFS_OK) return CFS_ECUDA;
+  }
   // x-lines per CTA: forward and inverse x transform
   {
     float tbest = 1e30f;

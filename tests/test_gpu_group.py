@@ -132,6 +132,16 @@ def test_group_rejects_bad_arguments(chanfs):
         with pytest.raises(chanfs.ChanfsError) as err:
             g.poisson_solve([t], [t])
         assert err.value.status == chanfs.EINVAL
+        # fields must start on 16-byte boundaries (rejected before any launch)
+        flat = torch.zeros(10 * 12 * 16 + 1, dtype=torch.float64, device="cuda")
+        odd = flat[1:].view(10, 12, 16)
+        for args in (([odd], [t]), ([t], [odd])):
+            with pytest.raises(chanfs.ChanfsError) as err:
+                g.poisson_solve(*args)
+            assert err.value.status == chanfs.EINVAL
+        with pytest.raises(chanfs.ChanfsError) as err:
+            g.helmholtz_solve([1e-3], [odd], [0], [t])
+        assert err.value.status == chanfs.EINVAL
     p64.close()
     p32.close()
 

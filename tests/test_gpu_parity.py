@@ -353,7 +353,7 @@ def test_options_and_autotune_keep_results(chanfs, dtype):
     tol = 1e-10 if dtype == 1 else TOL
     with chanfs.Plan(nx, ny, nz, 2.0, 1.0, dz, 0, dtype) as plan:
         for opt, vals in ((chanfs.OPT_X_LINES, (1, 4, 16)), (chanfs.OPT_Y_TILE, (2, 4, 16)),
-                          (chanfs.OPT_PCR_PARTS, (1, 3, 8))):
+                          (chanfs.OPT_PCR_PARTS, (1, 3, 8)), (chanfs.OPT_FFT_RADIX, (4, 8))):
             for v in vals:
                 plan.set_option(opt, v)
                 assert plan.get_option(opt) == v
@@ -372,7 +372,8 @@ def test_options_and_autotune_keep_results(chanfs, dtype):
                 plan.set_option(chanfs.OPT_HELM_THOMAS32, 1)  # FP64 plans have no FP32 solves
             assert err.value.status == chanfs.EUNSUPPORTED
         for opt, bad in ((chanfs.OPT_X_LINES, 65), (chanfs.OPT_Y_TILE, 33), (chanfs.OPT_PCR_PARTS, 65),
-                         (chanfs.OPT_HELM_THOMAS, 2), (chanfs.OPT_HELM_THOMAS32, -1)):
+                         (chanfs.OPT_HELM_THOMAS, 2), (chanfs.OPT_HELM_THOMAS32, -1),
+                         (chanfs.OPT_FFT_RADIX, 2)):
             with pytest.raises(chanfs.ChanfsError):
                 plan.set_option(opt, bad)
         with pytest.raises(chanfs.ChanfsError) as err:
