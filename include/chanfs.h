@@ -417,8 +417,12 @@ int cfs_plan_autotune(cfs_plan_t plan, void* stream);
  * cfs_selfcheck_conversions -- a diagnostic with no counterpart in the paper.
  * The refinement kernels convert between FP32 and FP64 on the integer units
  * (the hardware conversions share the scarce FP64 pipe); this runs `samples`
- * hashed operands (any double, exact rounding ties, any float) through both
- * and reports in *mismatches how many results differ in any bit (0 expected).
+ * hashed operands (any double, exact rounding ties, binary32 subnormal
+ * results and their ties, any float, float subnormals, and the double-float
+ * split hi = fl32(x), lo = fl32(x - hi) of doubles in the binary32 range)
+ * through both and reports in *mismatches how many results differ in any
+ * bit (0 expected; NaN results compare equal whatever their payload, and a
+ * lo below the normal binary32 range is not compared: the split returns 0).
  */
 int cfs_selfcheck_conversions(unsigned long long samples, unsigned long long* mismatches);
 

@@ -302,6 +302,47 @@ __device__ __forceinline__ float f64_to_f32(double x) {
   return __uint_as_float((hi & 0x80000000u) | bits);
 }
 
+// x as a double-float pair: hi = fl32(x) and lo = fl32(x - hi) (x - hi is
+// exact in binary64), from the fields of x alone.  For x inside the normal
+// binary32 range, x - hi is the 29 bits dropped by the rounding of hi, less
+// 2^29 units if hi rounded up, so lo is that signed integer d times
+// 2^(e - 1075), rounded to nearest even.  Outside that range lo is +0 (hi
+// then carries x to binary32 precision, or x is below it); a lo below the
+// normal binary32 range is a zero of its sign.
+__device__ __forceinline__ void f64_split(double x, float* hi, float* lo) {
+  const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
+  const unsigned e = (hw >> 20) & 0x7ffu;
+  *hi = f64_to_f32(x);
+  unsigned lbits = 0u;
+  if (e >= 897u && e <= 1150u) {
+    const unsigned m = ((hw & 0xfffffu) << 3) | (lw >> 29);
+    const unsigned rest = lw & 0x1fffffffu;
+    const bool up = rest > 0x10000000u || (rest == 0x10000000u && (m & 1u));
+    const int d = up ? (int)rest - 0x20000000 : (int)rest;  // |d| <= 2^28
+    if (d != 0) {
+      const unsigned a = d < 0 ? (unsigned)(-d) : (unsigned)d;
+      const int lz = __clz((int)a);          // leading bit at 31 - lz
+      const int ef = (int)e - 917 - lz;      // binary32 exponent field of a * 2^(e-1075)
+      const unsigned neg = ((hw >> 31) ^ (d < 0 ? 1u : 0u)) & 1u;
+      lbits = neg << 31;
+      if (ef >= 1) {
+        unsigned frac;
+        if (lz >= 8) {  // at most 24 significant bits: exact
+          frac = a << (lz - 8);
+        } else {        // round the low 8 - lz bits away, ties to even
+          const int sh = 8 - lz;
+          const unsigned q = a >> sh, r = a & ((1u << sh) - 1u), half = 1u << (sh - 1);
+          frac = q + ((r > half || (r == half && (q & 1u))) ? 1u : 0u);
+        }
+        // frac holds the significand with its leading bit at 23 (or 24
+        // after a carry, which the exponent field below absorbs)
+        lbits |= ((unsigned)ef << 23) + (frac - 0x800000u);
+      }
+    }
+  }
+  *lo = __uint_as_float(lbits);
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }

@@ -105,9 +105,9 @@ __global__ void mean_final_kernel(const double* partial, int nz, const double* d
 // column marching up in z with p_{k-1}, p_k, p_{k+1} in registers; the x and
 // y neighbours of a plane are shared through L1.  p == nullptr: r = f - mean.
 // rdf (may be null) receives r as a double-float pair hi + lo (hi = fl32(r),
-// lo = fl32(r - hi); one more FP64 instruction) for the updates that follow.
+// lo = fl32(r - hi), both from the fields of r) for the updates that follow.
 // zop = [A_k | B_k - 2/dx^2 - 2/dy^2 | C_k]; FP64: 8 instructions per point
-// (the FP32 rounding of r runs on the integer units).
+// (the FP32 roundings of r run on the integer units).
 __device__ __forceinline__ void poisson_residual_body(
     const double* __restrict__ f, const double* __restrict__ p, const double* __restrict__ zop,
     const double* __restrict__ mean, float* __restrict__ r32, float2* __restrict__ rdf,
@@ -151,9 +151,10 @@ __device__ __forceinline__ void poisson_residual_body(
       } else {
         r = f[o + col] - mu;
       }
-      const float rf = f64_to_f32(r);
+      float rf, rlo;
+      f64_split(r, &rf, &rlo);  // on the integer units
       r32[o + col] = rf;
-      if (rdf) rdf[o + col] = make_float2(rf, f64_to_f32(r - f32_to_f64(rf)));
+      if (rdf) rdf[o + col] = make_float2(rf, rlo);
       vmax = fmaxf(vmax, fabsf(rf));
       pkm = pk;
       pk = pkp;
@@ -617,6 +618,16 @@ __global__ void conversion_check_kernel(unsigned long long n, unsigned long long
     local += !same_f32(f64_to_f32(xst), __double2float_rn(xst));
     const float f = __uint_as_float((unsigned)z);
     local += !same_f64(f32_to_f64(f), (double)f);
+    // the double-float split, for values in the normal binary32 range (and
+    // lo counted only where the hardware's lo is normal or zero)
+    const unsigned long long en = 897ull + ((z >> 45) % 254ull);
+    const double xn = __longlong_as_double((long long)((z & 0x800FFFFFFFFFFFFFull) | (en << 52)));
+    float split_hi, split_lo;
+    f64_split(xn, &split_hi, &split_lo);
+    const float hh = __double2float_rn(xn);
+    const float hl = __double2float_rn(xn - (double)hh);
+    const bool tiny = hl != 0.0f && fabsf(hl) < 1.17549435e-38f;
+    local += !same_f32(split_hi, hh) || (!tiny && !same_f32(split_lo, hl));
     const float fs = __uint_as_float((unsigned)(z >> 32) & 0x807FFFFFu);  // subnormal or zero
     local += !same_f64(f32_to_f64(fs), (double)fs);
   }
