@@ -226,22 +226,29 @@ __device__ __forceinline__ void poisson_update_body(const float* __restrict__ dl
     const int nc = 3 * nz + 2;
     const float axh = z2[3 * nz], axl = z2[nc + 3 * nz];
     const float ayh = z2[3 * nz + 1], ayl = z2[nc + 3 * nz + 1];
+    // the loads of plane k + 1 are issued one iteration ahead, so that they
+    // are in flight while plane k is combined
     float dkm = 0.0f, dk = dlt[col];
+    float dkp = (nz > 1) ? dlt[nxy + col] : 0.0f;
+    float xp = dlt[ip], xm = dlt[im], yp = dlt[jp], ym = dlt[jm];
+    float2 rp = rdf[col];
     for (int k = 0; k < nz; ++k) {
       const long long o = (long long)k * nxy;
-      const float dkp = (k + 1 < nz) ? dlt[o + nxy + col] : 0.0f;
-      const float yp = dlt[o + jp], ym = dlt[o + jm];
+      const bool more = k + 1 < nz;
+      const long long on = more ? o + nxy : o;  // plane k + 1 (clamped)
+      const float dkp2 = (k + 2 < nz) ? dlt[on + nxy + col] : 0.0f;
+      const float xpn = dlt[on + ip], xmn = dlt[on + im], ypn = dlt[on + jp], ymn = dlt[on + jm];
+      const float2 rpn = rdf[on + col];
       DoubleFloat acc{0.0f, 0.0f};
       df_acc(acc, z2[nz + k], z2[nc + nz + k], dk);
-      df_acc(acc, axh, axl, dlt[o + ip]);
-      df_acc(acc, axh, axl, dlt[o + im]);
+      df_acc(acc, axh, axl, xp);
+      df_acc(acc, axh, axl, xm);
       df_acc(acc, ayh, ayl, np_ ? -yp : yp);
       df_acc(acc, ayh, ayl, nm_ ? -ym : ym);
       df_acc(acc, z2[k], z2[nc + k], dkm);
       df_acc(acc, z2[2 * nz + k], z2[nc + 2 * nz + k], dkp);
       // (hi, lo) - (s + e) in double-float: TwoSum of the leading parts, the
       // rest added to the error term, renormalised by a second TwoSum
-      const float2 rp = rdf[o + col];
       float sh, se, hi, lo;
       two_sum(rp.x, -acc.s, sh, se);
       se = __fadd_rn(se, __fsub_rn(rp.y, acc.e));
@@ -252,6 +259,12 @@ __device__ __forceinline__ void poisson_update_body(const float* __restrict__ dl
       vmax = fmaxf(vmax, fabsf(rf));
       dkm = dk;
       dk = dkp;
+      dkp = dkp2;
+      xp = xpn;
+      xm = xmn;
+      yp = ypn;
+      ym = ymn;
+      rp = rpn;
     }
   }
   block_max_to(vmax, rmax);

@@ -132,12 +132,16 @@ extern "C" int cfs_plan_autotune(cfs_plan_t P, void* stream) {
     for (int lines : {1, 2, 4, 8, 16, 32, 64}) {
       if (lines > nlines || x_smem_bytes(P, lines, cs) > 227 * 1024) continue;
       P->x_lines = lines;
+      // the transforms of one refined solve (two forward, the inverse that
+      // sets p and the one that adds to it), or of one FP64 solve
       const float t = best_ms(st, [&]() {
         cudaError_t e = fp32 ? launch_rfft_x32(P, s32, s32, false, st)
                              : launch_rfft_x(P, s64, s64, false, 1.0, st);
         if (e == cudaSuccess)
           e = fp32 ? launch_rfft_x32_to64(P, s32, s64, false, st)
                    : launch_rfft_x(P, s64, s64, true, 1.0, st);
+        if (fp32 && e == cudaSuccess) e = launch_rfft_x32(P, s32, s32, false, st);
+        if (fp32 && e == cudaSuccess) e = launch_rfft_x32_to64(P, s32, s64, true, st);
         return e;
       });
       if (t < tbest) {
