@@ -103,7 +103,7 @@ __global__ void mean_final_kernel(const double* partial, int nz, const double* d
 
 // r = (f - mean) - L p, written as FP32, and max |r|.  One thread per (x, y)
 // column marching up in z with p_{k-1}, p_k, p_{k+1} in registers; the x and
-// y neighbours of a plane are shared through L1.  p == nullptr: r = f - mean.
+// y neighbours of a plane are shared through L1.
 // rdf (may be null) receives r as a double-float pair hi + lo (hi = fl32(r),
 // lo = fl32(r - hi), both from the fields of r) for the updates that follow.
 // zop = [A_k | B_k - 2/dx^2 - 2/dy^2 | C_k]; FP64: 8 instructions per point
@@ -133,24 +133,25 @@ __device__ __forceinline__ void poisson_residual_body(
       np_ = (ybc == CFS_Y_DIRICHLET) && (j + 1 == ny);
       nm_ = (ybc == CFS_Y_DIRICHLET) && (j == 0);
     }
-    double pkm = 0.0, pk = p ? p[col] : 0.0;
+    // the loads of plane k + 1 are issued one iteration ahead
+    double pkm = 0.0, pk = p[col];
+    double pkp = (nz > 1) ? p[nxy + col] : 0.0;
+    double xp = p[ip], xm = p[im], yp = p[jp], ym = p[jm], fk = f[col];
     for (int k = 0; k < nz; ++k) {
       const long long o = (long long)k * nxy;
-      const double pkp = (p && k + 1 < nz) ? p[o + nxy + col] : 0.0;
-      double r;
-      if (p) {  // r = f - (mean + L p); the mean rides in the first FMA
-        const double sx = p[o + ip] + p[o + im];
-        const double yp = p[o + jp], ym = p[o + jm];
-        const double sy = (np_ ? -yp : yp) + (nm_ ? -ym : ym);
-        double t = fma(zop[nz + k], pk, mu);
-        t = fma(idx2, sx, t);
-        t = fma(idy2, sy, t);
-        t = fma(zop[k], pkm, t);
-        t = fma(zop[2 * nz + k], pkp, t);
-        r = f[o + col] - t;
-      } else {
-        r = f[o + col] - mu;
-      }
+      const long long on = (k + 1 < nz) ? o + nxy : o;  // plane k + 1 (clamped)
+      const double pkp2 = (k + 2 < nz) ? p[on + nxy + col] : 0.0;
+      const double xpn = p[on + ip], xmn = p[on + im], ypn = p[on + jp], ymn = p[on + jm];
+      const double fkn = f[on + col];
+      // r = f - (mean + L p); the mean rides in the first FMA
+      const double sx = xp + xm;
+      const double sy = (np_ ? -yp : yp) + (nm_ ? -ym : ym);
+      double t = fma(zop[nz + k], pk, mu);
+      t = fma(idx2, sx, t);
+      t = fma(idy2, sy, t);
+      t = fma(zop[k], pkm, t);
+      t = fma(zop[2 * nz + k], pkp, t);
+      const double r = fk - t;
       float rf, rlo;
       f64_split(r, &rf, &rlo);  // on the integer units
       r32[o + col] = rf;
@@ -158,6 +159,12 @@ __device__ __forceinline__ void poisson_residual_body(
       vmax = fmaxf(vmax, fabsf(rf));
       pkm = pk;
       pk = pkp;
+      pkp = pkp2;
+      xp = xpn;
+      xm = xmn;
+      yp = ypn;
+      ym = ymn;
+      fk = fkn;
     }
   }
   block_max_to(vmax, rmax);
@@ -405,14 +412,12 @@ __global__ void mean_final_group_kernel(const ResBox* boxes, GroupMap g) {
 
 __global__ void __launch_bounds__(kResBlock) poisson_residual_group_kernel(const ResBox* boxes,
                                                                            GroupMap g,
-                                                                           const GroupIo* io,
-                                                                           int with_p) {
+                                                                           const GroupIo* io) {
   int b, blk;
   if (!group_block(g, &b, &blk)) return;
   const ResBox& r = boxes[b];
-  poisson_residual_body(io[b].f, with_p ? io[b].p : nullptr, r.zop, r.neumann ? r.mean : nullptr,
-                        r.r32, with_p ? r.rdf : nullptr, r.rmax, r.nx, r.ny, r.nz, r.idx2,
-                        r.idy2, r.ybc, blk);
+  poisson_residual_body(io[b].f, io[b].p, r.zop, r.neumann ? r.mean : nullptr, r.r32, r.rdf,
+                        r.rmax, r.nx, r.ny, r.nz, r.idx2, r.idy2, r.ybc, blk);
 }
 
 __global__ void __launch_bounds__(256) rhs_start_group_kernel(const ResBox* boxes, GroupMap g,
@@ -543,7 +548,7 @@ cudaError_t launch_group_refine_stage(int stage, const ResBox* boxes, GroupMap g
       mean_final_group_kernel<<<total, 256, 0, st>>>(boxes, g);
       break;
     case GSTAGE_RESIDUAL:
-      poisson_residual_group_kernel<<<total, kResBlock, 0, st>>>(boxes, g, io, flag);
+      poisson_residual_group_kernel<<<total, kResBlock, 0, st>>>(boxes, g, io);
       break;
     case GSTAGE_UPDATE:
       poisson_update_group_kernel<<<total, kResBlock, 0, st>>>(boxes, g);
