@@ -189,15 +189,17 @@ template <int R, bool INV, class C> __device__ __forceinline__ void dft_tw(C* v,
 
 // One Stockham radix-R butterfly: reads R points j + r*n/R of one batch from
 // `in`, applies the twiddles of pass (L, R), transforms, and writes them to
-// positions (j - k)*R + k + r*L of `out` (k = j mod L).  es = element stride.
+// positions (j - k)*R + k + r*L of `out` (k = j mod L, by a mask when L is a
+// power of two: lmask = L - 1, else -1).  es = element stride.
 template <int R, bool INV, class C>
 __device__ __forceinline__ void stockham_bfly(const C* __restrict__ in, C* __restrict__ out, int j,
-                                              int L, int n, int es, const C* __restrict__ tw) {
+                                              int L, int lmask, int n, int es,
+                                              const C* __restrict__ tw) {
   C v[R];
   const int q = n / R;
 #pragma unroll
   for (int r = 0; r < R; ++r) v[r] = in[(j + r * q) * es];
-  const int k = j % L;
+  const int k = lmask >= 0 ? (j & lmask) : j % L;
   if (L > 1) {
     C w[R - 1];
 #pragma unroll
@@ -221,6 +223,7 @@ __device__ C* stockham_smem(C* a, C* b, const FftDesc& d, int nb, int es, int bs
   const int n = d.n;
   for (int p = 0; p < d.npass; ++p) {
     const int R = d.radix[p], L = d.span[p];
+    const int lmask = (L & (L - 1)) == 0 ? L - 1 : -1;
     const C* twp = tw + d.twoff[p];
     const int nbf = n / R;
     const int total = nbf * nb;
@@ -242,10 +245,10 @@ __device__ C* stockham_smem(C* a, C* b, const FftDesc& d, int nb, int es, int bs
       const C* in = a + bat * bs;
       C* out = b + bat * bs;
       switch (R) {
-        case 8: stockham_bfly<8, INV>(in, out, j, L, n, es, twp); break;
-        case 4: stockham_bfly<4, INV>(in, out, j, L, n, es, twp); break;
-        case 3: stockham_bfly<3, INV>(in, out, j, L, n, es, twp); break;
-        default: stockham_bfly<2, INV>(in, out, j, L, n, es, twp); break;
+        case 8: stockham_bfly<8, INV>(in, out, j, L, lmask, n, es, twp); break;
+        case 4: stockham_bfly<4, INV>(in, out, j, L, lmask, n, es, twp); break;
+        case 3: stockham_bfly<3, INV>(in, out, j, L, lmask, n, es, twp); break;
+        default: stockham_bfly<2, INV>(in, out, j, L, lmask, n, es, twp); break;
       }
     }
     __syncthreads();
