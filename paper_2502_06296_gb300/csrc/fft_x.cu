@@ -69,7 +69,7 @@ __device__ __forceinline__ void rfft_x_body(const C* in, void* outv, long long n
   const int sk = blockDim.x % npost, sl = blockDim.x / npost;
 
   if (!INV) {
-    C* Z = stockham_smem<false, false>(buf0, buf1, d, lb, 1, bs, tw);
+    C* Z = stockham_lines<false>(buf0, buf1, d, lb, tw);
     C* ob = (Z == buf0) ? buf1 : buf0;
     // untangle the half-length spectrum into the packed real spectrum
     int l = threadIdx.x / npost, k = threadIdx.x % npost;
@@ -139,7 +139,7 @@ __device__ __forceinline__ void rfft_x_body(const C* in, void* outv, long long n
       }
     }
     __syncthreads();
-    C* res = stockham_smem<true, false>(buf0, buf1, d, lb, 1, bs, tw);
+    C* res = stockham_lines<true>(buf0, buf1, d, lb, tw);
     if (OUT == OUT_SAME) {
       fence_proxy_async();
       __syncthreads();

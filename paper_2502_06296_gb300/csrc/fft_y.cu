@@ -164,7 +164,7 @@ __device__ __forceinline__ void fft_y_body(const CUtensorMap* map, const FftDesc
     __syncthreads();
   }
   // element (y, c) of the tile sits at y*tk + c: element stride tk, batch stride 1
-  C* res = stockham_smem<INV, true>(buf0, buf1, d, tk, tk, 1, tw);
+  C* res = stockham_tile<INV>(buf0, buf1, d, tk, tw);
   if (!INV && bx == 0) {  // untangle after the forward transform
     for (int ky = 1 + threadIdx.x; 2 * ky < ny; ky += blockDim.x) {
       const C zz = res[ky * tk], zm = res[(ny - ky) * tk];
