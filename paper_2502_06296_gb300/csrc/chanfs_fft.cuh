@@ -407,8 +407,14 @@ __device__ __forceinline__ C* stockham_tile(C* a, C* b, const FftDesc& d, int tk
       case 192:
         if (is_fixed_plan<192>(d)) return stockham_fixed_cols<INV, 192, 0>(a, b, tk, tw);
         break;
+      case 256:
+        if (is_fixed_plan<256>(d)) return stockham_fixed_cols<INV, 256, 0>(a, b, tk, tw);
+        break;
       case 384:
         if (is_fixed_plan<384>(d)) return stockham_fixed_cols<INV, 384, 0>(a, b, tk, tw);
+        break;
+      case 512:
+        if (is_fixed_plan<512>(d)) return stockham_fixed_cols<INV, 512, 0>(a, b, tk, tw);
         break;
       case 768:
         if (is_fixed_plan<768>(d)) return stockham_fixed_cols<INV, 768, 0>(a, b, tk, tw);
@@ -430,6 +436,12 @@ __device__ __forceinline__ C* stockham_lines(C* a, C* b, const FftDesc& d, int n
                                              const C* __restrict__ tw) {
   if constexpr (sizeof(C) == sizeof(float2)) {
     switch (d.n) {
+      case 32:
+        if (is_fixed_plan<32>(d)) return stockham_fixed<INV, 32, 0>(a, b, nb, tw);
+        break;
+      case 48:
+        if (is_fixed_plan<48>(d)) return stockham_fixed<INV, 48, 0>(a, b, nb, tw);
+        break;
       case 64:
         if (is_fixed_plan<64>(d)) return stockham_fixed<INV, 64, 0>(a, b, nb, tw);
         break;
@@ -444,6 +456,9 @@ __device__ __forceinline__ C* stockham_lines(C* a, C* b, const FftDesc& d, int n
         break;
       case 256:
         if (is_fixed_plan<256>(d)) return stockham_fixed<INV, 256, 0>(a, b, nb, tw);
+        break;
+      case 384:
+        if (is_fixed_plan<384>(d)) return stockham_fixed<INV, 384, 0>(a, b, nb, tw);
         break;
       case 512:
         if (is_fixed_plan<512>(d)) return stockham_fixed<INV, 512, 0>(a, b, nb, tw);
