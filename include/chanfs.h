@@ -414,6 +414,22 @@ int cfs_plan_get_option(cfs_plan_t plan, int option, int* value);
 int cfs_plan_autotune(cfs_plan_t plan, void* stream);
 
 /*
+ * The tuner's remembered choices across processes (no counterpart in the
+ * paper).  cfs_autotune_save writes every choice of this process to a text
+ * file at `path`, one line per (nx, ny, nz, dtype) with the name of the GPU
+ * it was measured on.  cfs_autotune_load reads such a file and takes the
+ * lines measured on a GPU of the current device's name (choices this
+ * process already holds are kept); *loaded (may be null) receives the number
+ * taken.  A taken choice is checked against the plan it is applied to (tile
+ * sizes, shared memory) and timed afresh if it does not fit.  Both return
+ * CFS_EINVAL if the file cannot be opened or a line is malformed (lines
+ * before it are taken).  cfs_autotune_clear forgets every choice.
+ */
+int cfs_autotune_save(const char* path);
+int cfs_autotune_load(const char* path, int* loaded);
+int cfs_autotune_clear(void);
+
+/*
  * cfs_selfcheck_conversions -- a diagnostic with no counterpart in the paper.
  * The refinement kernels convert between FP32 and FP64 on the integer units
  * (the hardware conversions share the scarce FP64 pipe); this runs `samples`

@@ -83,6 +83,9 @@ def lib():
             "cfs_group_poisson_solve": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp], i),
             "cfs_group_last_info": ([vp, ctypes.POINTER(i), ctypes.POINTER(d)], i),
             "cfs_group_set_graphs": ([vp, i], i),
+            "cfs_autotune_save": ([ctypes.c_char_p], i),
+            "cfs_autotune_load": ([ctypes.c_char_p, ctypes.POINTER(i)], i),
+            "cfs_autotune_clear": ([], i),
             "cfs_group_helmholtz_solve": ([vp, dp, ctypes.POINTER(i), ctypes.POINTER(vp),
                                            ctypes.POINTER(vp), vp], i),
             "cfs_helmholtz3d_prepare": ([vp, d, i], i),
@@ -466,6 +469,24 @@ class Server:
         st = ServerStats()
         _check(lib().cfs_server_stats(self._h, ctypes.byref(st)), "cfs_server_stats")
         return {name: getattr(st, name) for name, _ in ServerStats._fields_}
+
+
+def autotune_save(path) -> None:
+    """Write the tuner's choices of this process to a text file."""
+    _check(lib().cfs_autotune_save(str(path).encode()), "cfs_autotune_save")
+
+
+def autotune_load(path) -> int:
+    """Take the choices of a file written by autotune_save on this kind of
+    GPU; returns how many were taken."""
+    n = ctypes.c_int(0)
+    _check(lib().cfs_autotune_load(str(path).encode(), ctypes.byref(n)), "cfs_autotune_load")
+    return n.value
+
+
+def autotune_clear() -> None:
+    """Forget every tuning choice of this process."""
+    _check(lib().cfs_autotune_clear(), "cfs_autotune_clear")
 
 
 def selfcheck_conversions(samples: int = 1 << 22) -> int:

@@ -8,10 +8,12 @@
 // the arithmetic (each only reshapes one kernel's launch), so they are tuned
 // one after the other.  Choices are remembered per process for the plan's
 // (nx, ny, nz, dtype).
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
 #include <map>
+#include <string>
 #include <mutex>
 #include <tuple>
 #include <vector>
@@ -62,6 +64,21 @@ constexpr double kProbeC = 3.0517578125e-5;  // Helmholtz coefficient of the pro
 
 }  // namespace
 
+// Whether choice c can run on plan P (a choice read from a file may not).
+static bool fits(const cfs_plan* P, const Choice& c) {
+  const bool fp32 = (P->dtype == CFS_F32_REFINED);
+  const size_t cs = fp32 ? sizeof(float2) : sizeof(double2);
+  if (c.x_lines < 1 || c.x_lines > 64 || x_smem_bytes(P, c.x_lines, cs) > 227 * 1024) return false;
+  if (!y_tile_ok(P, c.y_tile, fp32)) return false;
+  if (c.thomas != -1 && thomas_tile_width(P, fp32, c.thomas) != c.thomas) return false;
+  if (c.pcr_parts < 0 || c.pcr_parts > kPcrMaxParts) return false;
+  for (int n = P->nz - 1; c.pcr_parts > 0 && n <= P->nz; ++n)
+    if (n / c.pcr_parts < 3 || pcr_smem_bytes(n, c.pcr_parts) > 227 * 1024) return false;
+  if ((c.helm_fp64 | c.helm_thomas | c.helm_thomas32) & ~1) return false;
+  if (c.helm_thomas32 && !fp32) return false;
+  return c.radix == 4 || c.radix == 8;
+}
+
 static void apply(cfs_plan* P, const Choice& c) {
   plan_set_radix(P, c.radix);
   P->x_lines = c.x_lines;
@@ -83,8 +100,11 @@ extern "C" int cfs_plan_autotune(cfs_plan_t P, void* stream) {
     std::lock_guard<std::mutex> lock(g_mu);
     auto it = g_cache.find(key);
     if (it != g_cache.end()) {
-      apply(P, it->second);
-      return CFS_OK;
+      if (fits(P, it->second)) {
+        apply(P, it->second);
+        return CFS_OK;
+      }
+      g_cache.erase(it);  // a loaded choice that does not fit this plan: time afresh
     }
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -262,5 +282,80 @@ extern "C" int cfs_plan_autotune(cfs_plan_t P, void* stream) {
   apply(P, best);
   std::lock_guard<std::mutex> lock(g_mu);
   g_cache[key] = best;
+  return CFS_OK;
+}
+
+// ---- remembered choices across processes ---------------------------------
+
+// The current device's name with blanks replaced (one token of a line).
+static bool device_name(std::string* out) {
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+    return false;
+  std::string n(prop.name);
+  for (char& ch : n)
+    if (ch == ' ' || ch == '\t') ch = '_';
+  *out = n.empty() ? std::string("unknown") : n;
+  return true;
+}
+
+static const char kTuneTag[] = "chanfs-tune-1";
+
+extern "C" int cfs_autotune_save(const char* path) {
+  if (!path) return CFS_EINVAL;
+  std::string name;
+  if (!device_name(&name)) return CFS_ECUDA;
+  FILE* fp = fopen(path, "w");
+  if (!fp) return CFS_EINVAL;
+  std::lock_guard<std::mutex> lock(g_mu);
+  bool ok = true;
+  for (const auto& kv : g_cache) {
+    const Choice& c = kv.second;
+    ok = ok && fprintf(fp, "%s %s %d %d %d %d %d %d %d %d %d %d %d %d\n", kTuneTag, name.c_str(),
+                       std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
+                       std::get<3>(kv.first), c.x_lines, c.y_tile, c.thomas, c.pcr_parts,
+                       c.helm_fp64, c.helm_thomas, c.helm_thomas32, c.radix) > 0;
+  }
+  ok = (fclose(fp) == 0) && ok;
+  return ok ? CFS_OK : CFS_EINVAL;
+}
+
+extern "C" int cfs_autotune_load(const char* path, int* loaded) {
+  if (loaded) *loaded = 0;
+  if (!path) return CFS_EINVAL;
+  FILE* fp = fopen(path, "r");
+  if (!fp) return CFS_EINVAL;
+  std::string name;
+  if (!device_name(&name)) {
+    fclose(fp);
+    return CFS_ECUDA;
+  }
+  int rc = CFS_OK, taken = 0;
+  char line[512];
+  while (fgets(line, sizeof(line), fp)) {
+    char tag[32], gpu[256];
+    int nx, ny, nz, dtype;
+    Choice c{};
+    if (line[0] == '\n' || line[0] == '#') continue;
+    if (sscanf(line, "%31s %255s %d %d %d %d %d %d %d %d %d %d %d %d", tag, gpu, &nx, &ny, &nz,
+               &dtype, &c.x_lines, &c.y_tile, &c.thomas, &c.pcr_parts, &c.helm_fp64,
+               &c.helm_thomas, &c.helm_thomas32, &c.radix) != 14 ||
+        strcmp(tag, kTuneTag) != 0) {
+      rc = CFS_EINVAL;
+      break;
+    }
+    if (name != gpu) continue;  // measured on another kind of GPU
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (g_cache.emplace(std::make_tuple(nx, ny, nz, dtype), c).second) ++taken;
+  }
+  fclose(fp);
+  if (loaded) *loaded = taken;
+  return rc;
+}
+
+extern "C" int cfs_autotune_clear(void) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_cache.clear();
   return CFS_OK;
 }

@@ -87,3 +87,13 @@ def test_product_package_does_not_import_the_oracle():
                 src = open(os.path.join(root, fn)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", src, re.M), fn
                 assert "chanfs_oracle" not in src, fn
+
+
+def test_tuning_file_entry_points_check_their_arguments(lib, tmp_path):
+    assert lib.cfs_autotune_save(None) == chanfs.EINVAL
+    assert lib.cfs_autotune_load(None, None) == chanfs.EINVAL
+    missing = str(tmp_path / "no_such_file").encode()
+    n = ctypes.c_int(7)
+    assert lib.cfs_autotune_load(missing, ctypes.byref(n)) == chanfs.EINVAL
+    assert n.value == 0
+    assert lib.cfs_autotune_clear() == chanfs.OK

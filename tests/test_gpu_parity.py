@@ -529,3 +529,29 @@ def test_thin_box_matches_oracle(chanfs, dtype):
             plan.set_option(opt, v)
             assert rel(host(plan.helmholtz_solve(1e-4, dev(f), 1)), href) < tol
         assert plan.check() == 0
+
+
+def test_tuning_choices_survive_a_file_round_trip(chanfs, tmp_path):
+    """Choices saved to a file and loaded in a clean tuner are applied to new
+    plans of the same size without timing; lines of another GPU are skipped
+    and a malformed line is rejected."""
+    nx, ny, nz = 64, 48, 40
+    dz = make_dz(nz, 1.5)
+    with chanfs.Plan(nx, ny, nz, 2.0, 1.0, dz, 0, chanfs.F32_REFINED) as plan:
+        chosen = plan.autotune()
+    path = tmp_path / "tune.txt"
+    chanfs.autotune_save(path)
+    text = path.read_text().splitlines()
+    assert any(f" {nx} {ny} {nz} 1 " in line for line in text)
+    chanfs.autotune_clear()
+    other = tmp_path / "other.txt"
+    other.write_text("chanfs-tune-1 Some_Other_GPU 8 8 8 0 1 1 -1 0 0 0 0 8\n"
+                     + path.read_text())
+    assert chanfs.autotune_load(other) >= 1
+    with chanfs.Plan(nx, ny, nz, 2.0, 1.0, dz, 0, chanfs.F32_REFINED) as plan2:
+        assert plan2.autotune() == chosen
+    bad = tmp_path / "bad.txt"
+    bad.write_text("not a tuning line\n")
+    with pytest.raises(chanfs.ChanfsError) as err:
+        chanfs.autotune_load(bad)
+    assert err.value.status == chanfs.EINVAL
