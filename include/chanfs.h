@@ -194,6 +194,24 @@ int cfs_helmholtz_solve_host(cfs_plan_t plan, double c, int loc,
                              const double* rhs, double* u, void* stream);
 
 /*
+ * cfs_solve_batch_host -- n solves on one plan through host buffers (no
+ * counterpart in the paper): kind[i] CFS_REQ_POISSON (in[i] = f, out[i] = p)
+ * or CFS_REQ_HELMHOLTZ (in[i] = rhs, out[i] = u, coefficient c[i], location
+ * loc[i]; c and loc may be null if no solve is a Helmholtz one).  The copy of
+ * each field to the device and of each result back overlap the solves of
+ * the others: two device slots of (input, output) fields, allocated at the
+ * first call and kept with the plan (4 fields), and two copy streams; the
+ * solves run on `stream`, after the work already there.  Host buffers should
+ * be pinned for the copies to overlap.  Returns when every result has
+ * arrived: CFS_OK, the first error, or CFS_ENOTCONVERGED if a refined solve
+ * missed its tolerance (every output is still written).  A step of the
+ * channel workload is one call: the Poisson solve and the three Helmholtz
+ * solves of u, v and w.
+ */
+int cfs_solve_batch_host(cfs_plan_t plan, int n, const int* kind, const double* c, const int* loc,
+                         const double* const* in, double* const* out, void* stream);
+
+/*
  * cfs_helmholtz_solve_noalloc -- the solve of cfs_helmholtz_solve without a
  * plan and without allocating any memory.  The paper has no counterpart; it
  * exists for callers that cannot allocate device memory where they solve:

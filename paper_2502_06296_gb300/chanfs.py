@@ -83,6 +83,9 @@ def lib():
             "cfs_group_poisson_solve": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp], i),
             "cfs_group_last_info": ([vp, ctypes.POINTER(i), ctypes.POINTER(d)], i),
             "cfs_group_set_graphs": ([vp, i], i),
+            "cfs_solve_batch_host": ([vp, i, ctypes.POINTER(i), ctypes.POINTER(d),
+                                      ctypes.POINTER(i), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                      vp], i),
             "cfs_autotune_save": ([ctypes.c_char_p], i),
             "cfs_autotune_load": ([ctypes.c_char_p, ctypes.POINTER(i)], i),
             "cfs_autotune_clear": ([], i),
@@ -252,6 +255,19 @@ class Plan:
                                               _host_ptr(out, self.shape), _stream_ptr(stream)),
                "cfs_helmholtz_solve_host")
         return out
+
+    def solve_batch_host(self, jobs, stream=None):
+        """jobs: a list of (kind, c, loc, input, output) with pinned (or any)
+        host arrays / CPU tensors of the plan's shape; solved in order with
+        the copies overlapped (cfs_solve_batch_host)."""
+        n = len(jobs)
+        kinds = (ctypes.c_int * n)(*[int(j[0]) for j in jobs])
+        cs = (ctypes.c_double * n)(*[float(j[1]) for j in jobs])
+        locs = (ctypes.c_int * n)(*[int(j[2]) for j in jobs])
+        ins = (ctypes.c_void_p * n)(*[_host_ptr(j[3], self.shape).value for j in jobs])
+        outs = (ctypes.c_void_p * n)(*[_host_ptr(j[4], self.shape).value for j in jobs])
+        _check(lib().cfs_solve_batch_host(self._h, n, kinds, cs, locs, ins, outs,
+                                          _stream_ptr(stream)), "cfs_solve_batch_host")
 
     def set_refinement(self, tol: float = 1e-10, maxit: int = 4):
         """Refined plans: stop at ||r||_inf <= tol ||b||_inf or after maxit FP32 solves."""

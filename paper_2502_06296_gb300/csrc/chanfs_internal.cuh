@@ -161,6 +161,11 @@ struct cfs_plan {
   unsigned long long helm_clock;
   // host-buffer staging
   double* d_stage;
+  // batched host-buffer solves: two slots of (input, output) device fields,
+  // two copy streams and their events (created at the first batch)
+  double* d_batch;
+  cudaStream_t copy_in, copy_out;
+  cudaEvent_t ev_entry, ev_in[2], ev_done[2], ev_free[2];
   // device status word
   int* d_status;
   size_t device_bytes;

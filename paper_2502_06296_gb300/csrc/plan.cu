@@ -167,6 +167,14 @@ static void plan_free(cfs_plan* P) {
   cudaFree(P->d_dzf);
   cudaFree(P->d_sing);
   cudaFree(P->d_stage);
+  cudaFree(P->d_batch);
+  cudaStream_t sts[] = {P->copy_in, P->copy_out};
+  for (cudaStream_t q : sts)
+    if (q) cudaStreamDestroy(q);
+  cudaEvent_t evs[] = {P->ev_entry, P->ev_in[0],   P->ev_in[1],   P->ev_done[0],
+                       P->ev_done[1], P->ev_free[0], P->ev_free[1]};
+  for (cudaEvent_t e : evs)
+    if (e) cudaEventDestroy(e);
   cudaFree(P->d_status);
   cudaFree(P->d_twx32);
   cudaFree(P->d_twy32);
@@ -1012,6 +1020,99 @@ extern "C" int cfs_helmholtz_solve_host(cfs_plan_t P, double c, int loc, const d
   if (cudaMemcpyAsync(u, P->d_stage, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return CFS_ECUDA;
   return cuda_status(cudaStreamSynchronize(st));
+}
+
+// Staging and copy streams of batched host-buffer solves, made once.
+static int ensure_batch(cfs_plan* P) {
+  if (P->d_batch) return CFS_OK;
+  CaptureLock lock(capture_mutex());
+  const size_t bytes = 4 * sizeof(double) * (size_t)P->nx * P->ny * P->nz;
+  if (cudaMalloc(&P->d_batch, bytes) != cudaSuccess) {
+    P->d_batch = nullptr;
+    return CFS_ENOMEM;
+  }
+  P->device_bytes += bytes;
+  cudaError_t e = cudaSuccess;
+  for (cudaStream_t* q : {&P->copy_in, &P->copy_out})
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(q, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev_entry, cudaEventDisableTiming);
+  for (int s = 0; s < 2 && e == cudaSuccess; ++s)
+    for (cudaEvent_t* v : {&P->ev_in[s], &P->ev_done[s], &P->ev_free[s]})
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(v, cudaEventDisableTiming);
+  return e == cudaSuccess ? CFS_OK : CFS_ECUDA;
+}
+
+// n solves through host buffers, pipelined over two device slots: while
+// solve i runs on `stream`, the input of solve i + 1 is copied in on one
+// copy stream and the output of solve i - 1 copied out on the other (both
+// directions at once).  An input slot is free once the solve that read it
+// is done, an output slot once its copy out is done.  The copy of the next
+// input is enqueued before solve i starts, so that it proceeds even while a
+// refined solve waits on the host.
+extern "C" int cfs_solve_batch_host(cfs_plan_t P, int n, const int* kind, const double* c,
+                                    const int* loc, const double* const* in, double* const* out,
+                                    void* stream) {
+  if (!P || n < 0 || (n > 0 && (!kind || !in || !out))) return CFS_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    if (!in[i] || !out[i]) return CFS_EINVAL;
+    if (kind[i] == CFS_REQ_HELMHOLTZ) {
+      if (!c || !loc || !(c[i] >= 0) || !isfinite(c[i])) return CFS_EINVAL;
+      if (loc[i] != CFS_LOC_CENTER && loc[i] != CFS_LOC_FACE) return CFS_EINVAL;
+    } else if (kind[i] != CFS_REQ_POISSON) {
+      return CFS_EINVAL;
+    }
+  }
+  if (n == 0) return CFS_OK;
+  int rc = ensure_batch(P);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nf = (size_t)P->nx * P->ny * P->nz;
+  const size_t bytes = sizeof(double) * nf;
+  double* din[2] = {P->d_batch, P->d_batch + nf};
+  double* dout[2] = {P->d_batch + 2 * nf, P->d_batch + 3 * nf};
+  // the copies start after the work already on the caller's stream
+  cudaError_t e = cudaEventRecord(P->ev_entry, st);
+  for (cudaStream_t q : {P->copy_in, P->copy_out})
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(q, P->ev_entry, 0);
+  auto copy_in = [&](int i) {
+    const int s = i & 1;
+    cudaError_t r = cudaSuccess;
+    if (i >= 2) r = cudaStreamWaitEvent(P->copy_in, P->ev_done[s], 0);  // solve i-2 read it
+    if (r == cudaSuccess)
+      r = cudaMemcpyAsync(din[s], in[i], bytes, cudaMemcpyHostToDevice, P->copy_in);
+    if (r == cudaSuccess) r = cudaEventRecord(P->ev_in[s], P->copy_in);
+    return r;
+  };
+  if (e == cudaSuccess) e = copy_in(0);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    const int s = i & 1;
+    if (i + 1 < n) e = copy_in(i + 1);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, P->ev_in[s], 0);
+    if (e == cudaSuccess && i >= 2)  // the output of solve i-2 has been copied out
+      e = cudaStreamWaitEvent(st, P->ev_free[s], 0);
+    if (e != cudaSuccess) break;
+    const int r = (kind[i] == CFS_REQ_POISSON)
+                      ? cfs_poisson_solve(P, din[s], dout[s], stream)
+                      : cfs_helmholtz_solve(P, c[i], loc[i], din[s], dout[s], stream);
+    if (r != CFS_OK && r != CFS_ENOTCONVERGED) {
+      rc = r;
+      break;
+    }
+    if (r == CFS_ENOTCONVERGED && rc == CFS_OK) rc = r;
+    e = cudaEventRecord(P->ev_done[s], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P->copy_out, P->ev_done[s], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out[i], dout[s], bytes, cudaMemcpyDeviceToHost, P->copy_out);
+    if (e == cudaSuccess) e = cudaEventRecord(P->ev_free[s], P->copy_out);
+  }
+  // every copy has landed (or the work stops here) before returning
+  const cudaError_t e1 = cudaStreamSynchronize(P->copy_in);
+  const cudaError_t e2 = cudaStreamSynchronize(P->copy_out);
+  const cudaError_t e3 = cudaStreamSynchronize(st);
+  if (rc != CFS_OK && rc != CFS_ENOTCONVERGED) return rc;
+  if (e != cudaSuccess || e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
+    return CFS_ECUDA;
+  return rc;
 }
 
 extern "C" int cfs_plan_check(cfs_plan_t P, int* device_error) {

@@ -97,3 +97,10 @@ def test_tuning_file_entry_points_check_their_arguments(lib, tmp_path):
     assert lib.cfs_autotune_load(missing, ctypes.byref(n)) == chanfs.EINVAL
     assert n.value == 0
     assert lib.cfs_autotune_clear() == chanfs.OK
+
+
+def test_batch_host_entry_point_checks_its_arguments(lib):
+    i3 = (ctypes.c_int * 1)(5)  # not a request kind
+    p = (ctypes.c_void_p * 1)(None)
+    assert lib.cfs_solve_batch_host(None, 1, i3, None, None, p, p, None) == chanfs.EINVAL
+    assert lib.cfs_solve_batch_host(None, -1, None, None, None, None, None, None) == chanfs.EINVAL

@@ -555,3 +555,29 @@ def test_tuning_choices_survive_a_file_round_trip(chanfs, tmp_path):
     with pytest.raises(chanfs.ChanfsError) as err:
         chanfs.autotune_load(bad)
     assert err.value.status == chanfs.EINVAL
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_batch_of_host_solves_matches_single_solves(chanfs, dtype):
+    """A channel-like step through cfs_solve_batch_host (Poisson + three
+    Helmholtz, copies overlapped with the solves) gives the bits of the
+    device solves one by one; a second batch reuses the plan's slots."""
+    nx, ny, nz = 64, 48, 40
+    dz = make_dz(nz, 1.8)
+    f = synth.remove_weighted_mean(synth.normal(61, (nz, ny, nx)), dz)
+    rhs = [synth.normal(62 + i, (nz, ny, nx)) for i in range(3)]
+    c = 2e-5
+    locs = (chanfs.CENTER, chanfs.CENTER, chanfs.FACE)
+    with chanfs.Plan(nx, ny, nz, 2.0, 1.0, dz, 0, dtype) as plan:
+        want = [host(plan.poisson_solve(dev(f)))]
+        want += [host(plan.helmholtz_solve(c, dev(r), loc)) for r, loc in zip(rhs, locs)]
+        ins = [torch.from_numpy(x).pin_memory() for x in [f] + rhs]
+        for _ in range(2):
+            outs = [torch.full_like(x, float("nan")).pin_memory() for x in ins]
+            jobs = [(chanfs.REQ_POISSON, 0.0, 0, ins[0], outs[0])]
+            jobs += [(chanfs.REQ_HELMHOLTZ, c, loc, ins[1 + i], outs[1 + i])
+                     for i, loc in enumerate(locs)]
+            plan.solve_batch_host(jobs)
+            for got, w in zip(outs, want):
+                assert np.array_equal(got.numpy(), w)
+        assert plan.check() == 0
