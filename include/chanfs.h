@@ -199,10 +199,13 @@ int cfs_helmholtz_solve_host(cfs_plan_t plan, double c, int loc,
  * or CFS_REQ_HELMHOLTZ (in[i] = rhs, out[i] = u, coefficient c[i], location
  * loc[i]; c and loc may be null if no solve is a Helmholtz one).  The copy of
  * each field to the device and of each result back overlap the solves of
- * the others: two device slots of (input, output) fields, allocated at the
- * first call and kept with the plan (4 fields), and two copy streams; the
- * solves run on `stream`, after the work already there.  Host buffers should
- * be pinned for the copies to overlap.  Returns when every result has
+ * the others: up to 4 device slots of (input, output) fields (as many as the
+ * batch has solves, kept with the plan at the largest size used), one
+ * copy-in stream and a copy-out stream per compute stream.  The solves run
+ * after the work already on `stream`: Poisson solves on `stream`, and on
+ * CFS_F64 plans the Helmholtz solves on a second stream beside them (they
+ * share no plan scratch; refined solves all run on `stream`).  Host buffers
+ * should be pinned for the copies to overlap.  Returns when every result has
  * arrived: CFS_OK, the first error, or CFS_ENOTCONVERGED if a refined solve
  * missed its tolerance (every output is still written).  A step of the
  * channel workload is one call: the Poisson solve and the three Helmholtz

@@ -33,6 +33,7 @@ constexpr int kPcrMaxParts = 64;   // z-partitions (half-warps) of the PCR kerne
 constexpr int kPcrMaxUnknowns = 1024;  // rows of a PCR tile in shared memory
 
 constexpr int kMaxGroup = 4096;     // plans of one grouped solve
+constexpr int kBatchSlots = 4;      // device slots of a batch of host-buffer solves
 
 // Device status bits (plan->d_status)
 constexpr int kErrTmaTimeout = 1;
@@ -161,11 +162,14 @@ struct cfs_plan {
   unsigned long long helm_clock;
   // host-buffer staging
   double* d_stage;
-  // batched host-buffer solves: two slots of (input, output) device fields,
-  // two copy streams and their events (created at the first batch)
+  // batched host-buffer solves: up to kBatchSlots slots of (input, output)
+  // device fields (as many as the largest batch so far), a copy-in stream,
+  // a second compute stream and a copy-out stream per compute stream, and
+  // their events (created at the first batch)
   double* d_batch;
-  cudaStream_t copy_in, copy_out;
-  cudaEvent_t ev_entry, ev_in[2], ev_done[2], ev_free[2];
+  int batch_slots;
+  cudaStream_t copy_in, copy_out, copy_out2, compute2;
+  cudaEvent_t ev_entry, ev_in[4], ev_done[4], ev_free[4];
   // device status word
   int* d_status;
   size_t device_bytes;

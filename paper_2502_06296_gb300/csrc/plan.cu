@@ -168,13 +168,12 @@ static void plan_free(cfs_plan* P) {
   cudaFree(P->d_sing);
   cudaFree(P->d_stage);
   cudaFree(P->d_batch);
-  cudaStream_t sts[] = {P->copy_in, P->copy_out};
-  for (cudaStream_t q : sts)
+  for (cudaStream_t q : {P->copy_in, P->copy_out, P->copy_out2, P->compute2})
     if (q) cudaStreamDestroy(q);
-  cudaEvent_t evs[] = {P->ev_entry, P->ev_in[0],   P->ev_in[1],   P->ev_done[0],
-                       P->ev_done[1], P->ev_free[0], P->ev_free[1]};
-  for (cudaEvent_t e : evs)
-    if (e) cudaEventDestroy(e);
+  if (P->ev_entry) cudaEventDestroy(P->ev_entry);
+  for (int k = 0; k < kBatchSlots; ++k)
+    for (cudaEvent_t e : {P->ev_in[k], P->ev_done[k], P->ev_free[k]})
+      if (e) cudaEventDestroy(e);
   cudaFree(P->d_status);
   cudaFree(P->d_twx32);
   cudaFree(P->d_twy32);
@@ -1022,33 +1021,47 @@ extern "C" int cfs_helmholtz_solve_host(cfs_plan_t P, double c, int loc, const d
   return cuda_status(cudaStreamSynchronize(st));
 }
 
-// Staging and copy streams of batched host-buffer solves, made once.
-static int ensure_batch(cfs_plan* P) {
-  if (P->d_batch) return CFS_OK;
+// Staging of batched host-buffer solves (grown to `slots` slots), its
+// streams and events (made once).
+static int ensure_batch(cfs_plan* P, int slots) {
   CaptureLock lock(capture_mutex());
-  const size_t bytes = 4 * sizeof(double) * (size_t)P->nx * P->ny * P->nz;
-  if (cudaMalloc(&P->d_batch, bytes) != cudaSuccess) {
-    P->d_batch = nullptr;
-    return CFS_ENOMEM;
+  const size_t field = sizeof(double) * (size_t)P->nx * P->ny * P->nz;
+  if (slots > P->batch_slots) {
+    if (P->d_batch) {
+      cudaDeviceSynchronize();  // no earlier batch may still use the old slots
+      cudaFree(P->d_batch);
+      P->device_bytes -= 2 * field * (size_t)P->batch_slots;
+      P->d_batch = nullptr;
+      P->batch_slots = 0;
+    }
+    if (cudaMalloc(&P->d_batch, 2 * field * (size_t)slots) != cudaSuccess) {
+      P->d_batch = nullptr;
+      return CFS_ENOMEM;
+    }
+    P->batch_slots = slots;
+    P->device_bytes += 2 * field * (size_t)slots;
   }
-  P->device_bytes += bytes;
+  if (P->copy_in) return CFS_OK;
   cudaError_t e = cudaSuccess;
-  for (cudaStream_t* q : {&P->copy_in, &P->copy_out})
+  for (cudaStream_t* q : {&P->copy_in, &P->copy_out, &P->copy_out2, &P->compute2})
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(q, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev_entry, cudaEventDisableTiming);
-  for (int s = 0; s < 2 && e == cudaSuccess; ++s)
-    for (cudaEvent_t* v : {&P->ev_in[s], &P->ev_done[s], &P->ev_free[s]})
+  for (int k = 0; k < kBatchSlots && e == cudaSuccess; ++k)
+    for (cudaEvent_t* v : {&P->ev_in[k], &P->ev_done[k], &P->ev_free[k]})
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(v, cudaEventDisableTiming);
   return e == cudaSuccess ? CFS_OK : CFS_ECUDA;
 }
 
-// n solves through host buffers, pipelined over two device slots: while
-// solve i runs on `stream`, the input of solve i + 1 is copied in on one
-// copy stream and the output of solve i - 1 copied out on the other (both
-// directions at once).  An input slot is free once the solve that read it
-// is done, an output slot once its copy out is done.  The copy of the next
-// input is enqueued before solve i starts, so that it proceeds even while a
-// refined solve waits on the host.
+// n solves through host buffers, pipelined over up to kBatchSlots device
+// slots (job i in slot i mod K): the inputs are copied in back to back on one
+// copy stream as their slots free up; each solve starts when its input has
+// arrived and its slot's previous output has been copied out; each result is
+// copied out as soon as its solve ends.  On FP64 plans the Helmholtz solves
+// run on a second compute stream, beside the Poisson solves (the two kinds
+// share no plan scratch; refined solves share the FP32 work fields and stay
+// on the caller's stream), each compute stream with its own copy-out stream.
+// The copy of the next input is enqueued before solve i starts, so that it
+// proceeds even while a refined solve waits on the host.
 extern "C" int cfs_solve_batch_host(cfs_plan_t P, int n, const int* kind, const double* c,
                                     const int* loc, const double* const* in, double* const* out,
                                     void* stream) {
@@ -1063,55 +1076,64 @@ extern "C" int cfs_solve_batch_host(cfs_plan_t P, int n, const int* kind, const 
     }
   }
   if (n == 0) return CFS_OK;
-  int rc = ensure_batch(P);
+  const int K = std::min(n, kBatchSlots);
+  int rc = ensure_batch(P, K);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
+  const bool two = (P->dtype == CFS_F64);  // Helmholtz beside Poisson
   const size_t nf = (size_t)P->nx * P->ny * P->nz;
   const size_t bytes = sizeof(double) * nf;
-  double* din[2] = {P->d_batch, P->d_batch + nf};
-  double* dout[2] = {P->d_batch + 2 * nf, P->d_batch + 3 * nf};
-  // the copies start after the work already on the caller's stream
+  auto din = [&](int s) { return P->d_batch + (size_t)(2 * s) * nf; };
+  auto dout = [&](int s) { return P->d_batch + (size_t)(2 * s + 1) * nf; };
+  auto cstream = [&](int i) {
+    return (two && kind[i] == CFS_REQ_HELMHOLTZ) ? P->compute2 : st;
+  };
+  auto ostream = [&](int i) {
+    return (two && kind[i] == CFS_REQ_HELMHOLTZ) ? P->copy_out2 : P->copy_out;
+  };
+  // everything starts after the work already on the caller's stream
   cudaError_t e = cudaEventRecord(P->ev_entry, st);
-  for (cudaStream_t q : {P->copy_in, P->copy_out})
+  for (cudaStream_t q : {P->copy_in, P->copy_out, P->copy_out2, P->compute2})
     if (e == cudaSuccess) e = cudaStreamWaitEvent(q, P->ev_entry, 0);
   auto copy_in = [&](int i) {
-    const int s = i & 1;
+    const int s = i % K;
     cudaError_t r = cudaSuccess;
-    if (i >= 2) r = cudaStreamWaitEvent(P->copy_in, P->ev_done[s], 0);  // solve i-2 read it
+    if (i >= K) r = cudaStreamWaitEvent(P->copy_in, P->ev_done[s], 0);  // solve i-K read it
     if (r == cudaSuccess)
-      r = cudaMemcpyAsync(din[s], in[i], bytes, cudaMemcpyHostToDevice, P->copy_in);
+      r = cudaMemcpyAsync(din(s), in[i], bytes, cudaMemcpyHostToDevice, P->copy_in);
     if (r == cudaSuccess) r = cudaEventRecord(P->ev_in[s], P->copy_in);
     return r;
   };
   if (e == cudaSuccess) e = copy_in(0);
   for (int i = 0; i < n && e == cudaSuccess; ++i) {
-    const int s = i & 1;
+    const int s = i % K;
+    cudaStream_t cs = cstream(i);
     if (i + 1 < n) e = copy_in(i + 1);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, P->ev_in[s], 0);
-    if (e == cudaSuccess && i >= 2)  // the output of solve i-2 has been copied out
-      e = cudaStreamWaitEvent(st, P->ev_free[s], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, P->ev_in[s], 0);
+    if (e == cudaSuccess && i >= K)  // the output of solve i-K has been copied out
+      e = cudaStreamWaitEvent(cs, P->ev_free[s], 0);
     if (e != cudaSuccess) break;
     const int r = (kind[i] == CFS_REQ_POISSON)
-                      ? cfs_poisson_solve(P, din[s], dout[s], stream)
-                      : cfs_helmholtz_solve(P, c[i], loc[i], din[s], dout[s], stream);
+                      ? cfs_poisson_solve(P, din(s), dout(s), cs)
+                      : cfs_helmholtz_solve(P, c[i], loc[i], din(s), dout(s), cs);
     if (r != CFS_OK && r != CFS_ENOTCONVERGED) {
       rc = r;
       break;
     }
     if (r == CFS_ENOTCONVERGED && rc == CFS_OK) rc = r;
-    e = cudaEventRecord(P->ev_done[s], st);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(P->copy_out, P->ev_done[s], 0);
+    cudaStream_t os = ostream(i);
+    e = cudaEventRecord(P->ev_done[s], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(os, P->ev_done[s], 0);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(out[i], dout[s], bytes, cudaMemcpyDeviceToHost, P->copy_out);
-    if (e == cudaSuccess) e = cudaEventRecord(P->ev_free[s], P->copy_out);
+      e = cudaMemcpyAsync(out[i], dout(s), bytes, cudaMemcpyDeviceToHost, os);
+    if (e == cudaSuccess) e = cudaEventRecord(P->ev_free[s], os);
   }
   // every copy has landed (or the work stops here) before returning
-  const cudaError_t e1 = cudaStreamSynchronize(P->copy_in);
-  const cudaError_t e2 = cudaStreamSynchronize(P->copy_out);
-  const cudaError_t e3 = cudaStreamSynchronize(st);
+  cudaError_t ef = cudaSuccess;
+  for (cudaStream_t q : {P->copy_in, P->compute2, P->copy_out, P->copy_out2, st})
+    if (cudaStreamSynchronize(q) != cudaSuccess) ef = cudaErrorUnknown;
   if (rc != CFS_OK && rc != CFS_ENOTCONVERGED) return rc;
-  if (e != cudaSuccess || e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
-    return CFS_ECUDA;
+  if (e != cudaSuccess || ef != cudaSuccess) return CFS_ECUDA;
   return rc;
 }
 
