@@ -83,6 +83,10 @@ struct ResBox {  // refinement residual and norms (refine.cu)
   double idx2, idy2;
   int neumann;         // the operator has the constants as null space (mean removal)
   int ybc;             // 0 periodic y, 1 Neumann walls, 2 Dirichlet walls
+  const float* dz2;    // double-float split of the cell widths
+  double* mpart;       // per-block weighted sums of a correction
+  double* mnum;        // running weighted sum of the solution
+  double inv_wn;       // 1 / (sum of the cell widths * Nx * Ny)
 };
 
 // Blocks of the grouped mean subtraction for a field of n points.
@@ -193,7 +197,9 @@ enum {
   GSTAGE_HELM_RESIDUAL = 4,  // flag = mode of helm_residual_kernel
   GSTAGE_UPDATE = 5,         // r -= L delta (double-float), r32b and max
   GSTAGE_ZERO = 6,           // zero solution (boxes with a zero right-hand side)
-  GSTAGE_START = 7           // r_0 = f - mean as FP32 and its norm (sub-block partition)
+  GSTAGE_START = 7,          // r_0 = f - mean as FP32 and its norm (sub-block partition)
+  GSTAGE_MEAN_ACC = 8,       // running weighted sum of the solution += the correction's
+  GSTAGE_MEAN_FROM_NUM = 9   // the solution's weighted mean from the running sum
 };
 
 // Host-side descriptions of one plan's box for the grouped kernels.

@@ -149,6 +149,9 @@ struct cfs_plan {
   float* d_r32b;     // the FP32 residual of the later iterations (input of their solves)
   float2* d_rdf;     // the residual kept between iterations, double-float (hi, lo)
   float* d_zop2;     // double-float split of zop and of 1/dx^2, 1/dy^2: hi[3nz+2] | lo[3nz+2]
+  float* d_dz2;      // double-float split of the cell widths: hi[nz] | lo[nz]
+  double* d_mpart;   // per-block dz-weighted sums of a correction (residual grid blocks)
+  double inv_wn;     // 1 / (sum of the cell widths * Nx * Ny)
   double* d_red;     // reduction scratch: [0] max |r| (float bits), [1] mean, [2..] partials
   double* d_zop;     // 3*nz doubles: A_k | B_k - 2/dx^2 - 2/dy^2 | C_k of the Poisson operator
   double tol;        // relative residual target

@@ -335,6 +335,10 @@ static int group_bind(cfs_group* G, int nplans, const cfs_plan_t* plans, cudaStr
     r.idy2 = 1.0 / (dy * dy);
     r.neumann = P->has_null;
     r.ybc = P->ybc;
+    r.dz2 = P->d_dz2;
+    r.mpart = P->d_mpart;
+    r.mnum = P->d_red + 2 + P->nz;  // after the plane partials
+    r.inv_wn = P->inv_wn;
     G->res[b] = r;
     bres[b] = (int)((nxy + 127) / 128);
     bplane[b] = P->nz;
@@ -556,6 +560,10 @@ cudaError_t poisson_iteration(cfs_group* G, int kind, cudaGraphConditionalHandle
     e = launch_group_refine_stage(kind == 0 ? GSTAGE_RESIDUAL : GSTAGE_UPDATE, G->d_res, g,
                                   G->tres, G->d_io, 1, st);
   }
+  if (e == cudaSuccess) {  // the weighted sum of p, correction by correction (Neumann boxes)
+    g.start = G->d_sone;
+    e = launch_group_refine_stage(GSTAGE_MEAN_ACC, G->d_res, g, G->tone, G->d_io, 0, st);
+  }
   if (e == cudaSuccess)
     e = launch_group_iter_end(G->d_res, nb, G->d_fmax, G->d_tol, G->d_maxit, G->d_active,
                               G->d_iters, G->d_rho, G->d_ctl, cond, set_cond, st);
@@ -563,15 +571,13 @@ cudaError_t poisson_iteration(cfs_group* G, int kind, cudaGraphConditionalHandle
 }
 
 // The zero dz-weighted mean of p restored (Neumann boxes, as the single
-// solve does), and the iteration counts and residuals copied out.
+// solve does: the mean from the running weighted sum of the corrections),
+// and the iteration counts and residuals copied out.
 cudaError_t poisson_tail(cfs_group* G, cudaStream_t st) {
   const int nb = G->nbox;
-  GroupMap g{G->d_splane, G->d_mean, nb};
+  GroupMap g{G->d_sone, G->d_mean, nb};
   cudaError_t e =
-      launch_group_refine_stage(GSTAGE_PLANE_SUM, G->d_res, g, G->tplane, G->d_io, 1, st);
-  g.start = G->d_sone;
-  if (e == cudaSuccess)
-    e = launch_group_refine_stage(GSTAGE_MEAN_FINAL, G->d_res, g, G->tone, G->d_io, 0, st);
+      launch_group_refine_stage(GSTAGE_MEAN_FROM_NUM, G->d_res, g, G->tone, G->d_io, 0, st);
   g.start = G->d_ssub;
   if (e == cudaSuccess)
     e = launch_group_refine_stage(GSTAGE_SUBTRACT, G->d_res, g, G->tsub, G->d_io, 0, st);

@@ -184,6 +184,8 @@ static void plan_free(cfs_plan* P) {
   cudaFree(P->d_r32b);
   cudaFree(P->d_rdf);
   cudaFree(P->d_zop2);
+  cudaFree(P->d_dz2);
+  cudaFree(P->d_mpart);
   cudaFree(P->d_red);
   cudaFree(P->d_zop);
   cudaFree(P->d_wy);
@@ -401,6 +403,20 @@ extern "C" int cfs_plan_create_walls(cfs_plan_t* out, int nx, int ny, int nz, do
       z2[coef.size() + i] = (float)(coef[i] - (double)hi);
     }
     if (!rc) rc = dev_upload(&P->d_zop2, z2.data(), z2.size(), &P->device_bytes);
+    // the weighted mean of the solution is accumulated from the corrections
+    std::vector<float> dz2(2 * (size_t)nz);
+    double wsum = 0.0;
+    for (int k = 0; k < nz; ++k) {
+      const float hi = (float)P->dzf[k];
+      dz2[k] = hi;
+      dz2[nz + k] = (float)(P->dzf[k] - (double)hi);
+      wsum += P->dzf[k];
+    }
+    P->inv_wn = 1.0 / (wsum * (double)nx * (double)ny);
+    if (!rc) rc = dev_upload(&P->d_dz2, dz2.data(), dz2.size(), &P->device_bytes);
+    if (!rc)
+      rc = dev_upload<double>(&P->d_mpart, nullptr, ((size_t)nx * ny + 127) / 128,
+                              &P->device_bytes);
     if (!rc) rc = dev_upload<float>(&P->d_r32b, nullptr, (size_t)nx * ny * nz, &P->device_bytes);
     if (!rc) rc = dev_upload<float2>(&P->d_rdf, nullptr, (size_t)nx * ny * nz, &P->device_bytes);
   }

@@ -34,6 +34,44 @@ __device__ __forceinline__ void block_max_to(float v, unsigned int* out) {
   }
 }
 
+// The block's sum of v in a fixed order (shuffle tree per warp, then the
+// warps in order), written to *slot by thread 0.  Every thread calls it.
+__device__ __forceinline__ void block_sum_to(double v, double* slot) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __shared__ double wsum[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) wsum[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += wsum[i];
+    *slot = t;
+  }
+}
+
+// Double-float accumulation on the FP32 units (see the residual update below).
+struct DoubleFloat {
+  float s, e;
+};
+
+// s + t = a + b exactly (Knuth's TwoSum); the _rn intrinsics keep the
+// compiler from contracting or reassociating the steps.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void df_acc(DoubleFloat& acc, float chi, float clo, float d) {
+  const float p = __fmul_rn(chi, d);
+  float e = __fmaf_rn(chi, d, -p);  // chi * d - p, exact
+  e = __fmaf_rn(clo, d, e);
+  float s, t;
+  two_sum(acc.s, p, s, t);
+  acc.s = s;
+  acc.e = __fadd_rn(acc.e, __fadd_rn(t, e));
+}
+
 // Neumann compatibility: the dz-weighted mean of f, reduced in a fixed order
 // (one block per z plane, then one block over the planes) so that results
 // are bit-reproducible.
@@ -112,10 +150,11 @@ __device__ __forceinline__ void poisson_residual_body(
     const double* __restrict__ f, const double* __restrict__ p, const double* __restrict__ zop,
     const double* __restrict__ mean, float* __restrict__ r32, float2* __restrict__ rdf,
     unsigned int* rmax, int nx, int ny, int nz, double idx2, double idy2, int ybc,
-    long long blk) {
+    const float* __restrict__ dz2, double* mpart, long long blk) {
   const long long nxy = (long long)nx * ny;
   const long long col = blk * blockDim.x + threadIdx.x;
   float vmax = 0.0f;
+  DoubleFloat macc{0.0f, 0.0f};  // sum_k dz_k p_k of the column (p is a first correction)
   if (col < nxy) {
     const double mu = mean ? *mean : 0.0;
     const int i = (int)(col % nx), j = (int)(col / nx);
@@ -157,6 +196,7 @@ __device__ __forceinline__ void poisson_residual_body(
       r32[o + col] = rf;
       if (rdf) rdf[o + col] = make_float2(rf, rlo);
       vmax = fmaxf(vmax, fabsf(rf));
+      if (mpart) df_acc(macc, dz2[k], dz2[nz + k], f64_to_f32(pk));  // p holds FP32 values
       pkm = pk;
       pk = pkp;
       pkp = pkp2;
@@ -167,6 +207,7 @@ __device__ __forceinline__ void poisson_residual_body(
       fk = fkn;
     }
   }
+  if (mpart) block_sum_to(f32_to_f64(macc.s) + f32_to_f64(macc.e), mpart + blk);
   block_max_to(vmax, rmax);
 }
 
@@ -183,38 +224,18 @@ __device__ __forceinline__ void poisson_residual_body(
 // double-float pair too, so the update runs without FP64 instructions.
 // The first residual of a solve (|delta| ~ |p|) stays the direct FP64 one.
 // ----------------------------------------------------------------------------
-struct DoubleFloat {
-  float s, e;
-};
-
-// s + t = a + b exactly (Knuth's TwoSum); the _rn intrinsics keep the
-// compiler from contracting or reassociating the steps.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-__device__ __forceinline__ void df_acc(DoubleFloat& acc, float chi, float clo, float d) {
-  const float p = __fmul_rn(chi, d);
-  float e = __fmaf_rn(chi, d, -p);  // chi * d - p, exact
-  e = __fmaf_rn(clo, d, e);
-  float s, t;
-  two_sum(acc.s, p, s, t);
-  acc.s = s;
-  acc.e = __fadd_rn(acc.e, __fadd_rn(t, e));
-}
-
 // z2 = hi[3nz + 2] | lo[3nz + 2]: the split zop rows, then 1/dx^2, 1/dy^2.
 __device__ __forceinline__ void poisson_update_body(const float* __restrict__ dlt,
                                                     float2* __restrict__ rdf,
                                                     float* __restrict__ r32,
                                                     const float* __restrict__ z2,
                                                     unsigned int* rmax, int nx, int ny, int nz,
-                                                    int ybc, long long blk) {
+                                                    int ybc, const float* __restrict__ dz2,
+                                                    double* mpart, long long blk) {
   const long long nxy = (long long)nx * ny;
   const long long col = blk * blockDim.x + threadIdx.x;
   float vmax = 0.0f;
+  DoubleFloat macc{0.0f, 0.0f};  // sum_k dz_k delta_k of the column
   if (col < nxy) {
     const int i = (int)(col % nx), j = (int)(col / nx);
     const long long ip = (i + 1 == nx) ? col - i : col + 1;
@@ -264,6 +285,7 @@ __device__ __forceinline__ void poisson_update_body(const float* __restrict__ dl
       const float rf = hi;
       r32[o + col] = rf;
       vmax = fmaxf(vmax, fabsf(rf));
+      if (mpart) df_acc(macc, dz2[k], dz2[nz + k], dk);
       dkm = dk;
       dk = dkp;
       dkp = dkp2;
@@ -274,13 +296,37 @@ __device__ __forceinline__ void poisson_update_body(const float* __restrict__ dl
       rp = rpn;
     }
   }
+  if (mpart) block_sum_to(f32_to_f64(macc.s) + f32_to_f64(macc.e), mpart + blk);
   block_max_to(vmax, rmax);
 }
 
 __global__ void __launch_bounds__(kResBlock) poisson_update_kernel(
     const float* __restrict__ dlt, float2* __restrict__ rdf, float* __restrict__ r32,
-    const float* __restrict__ z2, unsigned int* rmax, int nx, int ny, int nz, int ybc) {
-  poisson_update_body(dlt, rdf, r32, z2, rmax, nx, ny, nz, ybc, blockIdx.x);
+    const float* __restrict__ z2, unsigned int* rmax, int nx, int ny, int nz, int ybc,
+    const float* __restrict__ dz2, double* mpart) {
+  poisson_update_body(dlt, rdf, r32, z2, rmax, nx, ny, nz, ybc, dz2, mpart, blockIdx.x);
+}
+
+// The dz-weighted sum of a correction, from the per-block sums of the
+// residual kernels, added in a fixed order to the running sum *num (the
+// numerator of the weighted mean of the solution).
+__device__ __forceinline__ void mean_acc_body(const double* __restrict__ mpart, int nparts,
+                                              double* num) {
+  double t = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) t += mpart[i];
+  __shared__ double tot;
+  block_sum_to(t, &tot);
+  __syncthreads();
+  if (threadIdx.x == 0) *num += tot;
+}
+
+__global__ void mean_acc_kernel(const double* __restrict__ mpart, int nparts, double* num) {
+  mean_acc_body(mpart, nparts, num);
+}
+
+// mean = num * inv (inv = 1 / (sum of the cell widths * Nx * Ny)).
+__global__ void mean_from_num_kernel(const double* num, double inv, double* mean) {
+  if (threadIdx.x == 0) *mean = *num * inv;
 }
 
 // r_0 = f - mean (mean may be null: r_0 = f) as FP32, and max |r_0|: a flat
@@ -313,9 +359,10 @@ __global__ void __launch_bounds__(256) rhs_start_kernel(const double* __restrict
 __global__ void __launch_bounds__(kResBlock) poisson_residual_kernel(
     const double* __restrict__ f, const double* __restrict__ p, const double* __restrict__ zop,
     const double* __restrict__ mean, float* __restrict__ r32, float2* __restrict__ rdf,
-    unsigned int* rmax, int nx, int ny, int nz, double idx2, double idy2, int ybc) {
-  poisson_residual_body(f, p, zop, mean, r32, rdf, rmax, nx, ny, nz, idx2, idy2, ybc,
-                        blockIdx.x);
+    unsigned int* rmax, int nx, int ny, int nz, double idx2, double idy2, int ybc,
+    const float* __restrict__ dz2, double* mpart) {
+  poisson_residual_body(f, p, zop, mean, r32, rdf, rmax, nx, ny, nz, idx2, idy2, ybc, dz2,
+                        mpart, blockIdx.x);
 }
 
 // Helmholtz: u (+)= delta, then r = rhs - (I - c L_z) u, as FP32, and max |r|.
@@ -417,7 +464,25 @@ __global__ void __launch_bounds__(kResBlock) poisson_residual_group_kernel(const
   if (!group_block(g, &b, &blk)) return;
   const ResBox& r = boxes[b];
   poisson_residual_body(io[b].f, io[b].p, r.zop, r.neumann ? r.mean : nullptr, r.r32, r.rdf,
-                        r.rmax, r.nx, r.ny, r.nz, r.idx2, r.idy2, r.ybc, blk);
+                        r.rmax, r.nx, r.ny, r.nz, r.idx2, r.idy2, r.ybc, r.dz2,
+                        r.neumann ? r.mpart : nullptr, blk);
+}
+
+// One block per box (Neumann boxes; the others have nothing to sum).
+__global__ void mean_acc_group_kernel(const ResBox* boxes, GroupMap g) {
+  int b, blk;
+  if (!group_block(g, &b, &blk)) return;
+  const ResBox& r = boxes[b];
+  if (!r.neumann) return;
+  const long long nxy = (long long)r.nx * r.ny;
+  mean_acc_body(r.mpart, (int)((nxy + kResBlock - 1) / kResBlock), r.mnum);
+}
+
+__global__ void mean_from_num_group_kernel(const ResBox* boxes, GroupMap g) {
+  int b, blk;
+  if (!group_block(g, &b, &blk)) return;
+  const ResBox& r = boxes[b];
+  if (threadIdx.x == 0) *r.mean = *r.mnum * r.inv_wn;
 }
 
 __global__ void __launch_bounds__(256) rhs_start_group_kernel(const ResBox* boxes, GroupMap g,
@@ -446,7 +511,8 @@ __global__ void __launch_bounds__(kResBlock) poisson_update_group_kernel(const R
   int b, blk;
   if (!group_block(g, &b, &blk)) return;
   const ResBox& r = boxes[b];
-  poisson_update_body(r.r32, r.rdf, r.r32b, r.zop2, r.rmax, r.nx, r.ny, r.nz, r.ybc, blk);
+  poisson_update_body(r.r32, r.rdf, r.r32b, r.zop2, r.rmax, r.nx, r.ny, r.nz, r.ybc, r.dz2,
+                      r.neumann ? r.mpart : nullptr, blk);
 }
 
 __global__ void subtract_mean_group_kernel(const ResBox* boxes, GroupMap g, const GroupIo* io) {
@@ -490,6 +556,7 @@ __global__ void group_start_kernel(const ResBox* boxes, int nbox, float* fmax,
   const int on = elig && f != 0.0f;
   active[b] = on;
   if (mean_on) mean_on[b] = on && boxes[b].neumann;
+  if (boxes[b].mnum) *boxes[b].mnum = 0.0;
   zero[b] = elig && !on;
   iters[b] = 0;
   rho[b] = 0.0;
@@ -561,6 +628,12 @@ cudaError_t launch_group_refine_stage(int stage, const ResBox* boxes, GroupMap g
       break;
     case GSTAGE_START:
       rhs_start_group_kernel<<<total, 256, 0, st>>>(boxes, g, io);
+      break;
+    case GSTAGE_MEAN_ACC:
+      mean_acc_group_kernel<<<total, 256, 0, st>>>(boxes, g);
+      break;
+    case GSTAGE_MEAN_FROM_NUM:
+      mean_from_num_group_kernel<<<total, 32, 0, st>>>(boxes, g);
       break;
     default:
       subtract_mean_group_kernel<<<total, 256, 0, st>>>(boxes, g, io);
@@ -666,6 +739,9 @@ static int read_max(cfs_plan* P, cudaStream_t st, float* out) {
 
 static unsigned int* max_word(cfs_plan* P) { return reinterpret_cast<unsigned int*>(P->d_red); }
 
+// The running dz-weighted sum of the solution (after the plane partials).
+static double* mean_num(cfs_plan* P) { return P->d_red + 2 + P->nz; }
+
 int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st) {
   const long long nxy = (long long)P->nx * P->ny;
   const double dx = P->lx / P->nx, dy = P->ly / P->ny;
@@ -678,6 +754,7 @@ int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st) {
     plane_sum_kernel<<<P->nz, 256, 0, st>>>(f, nxy, P->d_dzf, P->d_red + 2);
     mean_final_kernel<<<1, 256, 0, st>>>(P->d_red + 2, P->nz, P->d_dzf, nxy, mean);
     e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemsetAsync(mean_num(P), 0, sizeof(double), st);
   }
   // r_0 = f - mean and the reference norm ||f - mean||_inf
   if (e == cudaSuccess) e = cudaMemsetAsync(P->d_red, 0, sizeof(unsigned int), st);
@@ -706,15 +783,22 @@ int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st) {
     if (e == cudaSuccess) e = launch_fft_y32(P, P->d_r32, true, st);
     if (e == cudaSuccess) e = launch_rfft_x32_to64(P, P->d_r32, p, it > 0, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->d_red, 0, sizeof(unsigned int), st);
+    // (Neumann: each kernel also sums its correction, dz-weighted, per block)
+    double* mpart = P->has_null ? P->d_mpart : nullptr;
     if (e == cudaSuccess && it == 0) {  // r = f - mean - L p, directly in FP64
       poisson_residual_kernel<<<grid, kResBlock, 0, st>>>(f, p, P->d_zop, mean, P->d_r32,
                                                           P->d_rdf, max_word(P), P->nx, P->ny,
-                                                          P->nz, idx2, idy2, P->ybc);
+                                                          P->nz, idx2, idy2, P->ybc, P->d_dz2,
+                                                          mpart);
       e = cudaGetLastError();
     } else if (e == cudaSuccess) {  // r -= L delta
       poisson_update_kernel<<<grid, kResBlock, 0, st>>>(P->d_r32, P->d_rdf, P->d_r32b, P->d_zop2,
                                                         max_word(P), P->nx, P->ny, P->nz,
-                                                        P->ybc);
+                                                        P->ybc, P->d_dz2, mpart);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && mpart) {  // the weighted sum of p, correction by correction
+      mean_acc_kernel<<<1, 256, 0, st>>>(mpart, (int)grid, mean_num(P));
       e = cudaGetLastError();
     }
     float rmax = 0.0f;
@@ -728,9 +812,11 @@ int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st) {
   if (P->has_null) {
     // The residual cannot see a constant, so the FP32 rounding of each
     // correction's mean accumulates unchecked; restore the zero dz-weighted
-    // mean of p in FP64.
-    plane_sum_kernel<<<P->nz, 256, 0, st>>>(p, nxy, P->d_dzf, P->d_red + 2);
-    mean_final_kernel<<<1, 256, 0, st>>>(P->d_red + 2, P->nz, P->d_dzf, nxy, P->d_red + 1);
+    // mean of p.  p is the sum of the corrections (each added in FP64), so
+    // its weighted sum is the sum of theirs, accumulated by the residual
+    // kernels that read every correction (double-float per column, FP64
+    // across columns, in a fixed order).
+    mean_from_num_kernel<<<1, 32, 0, st>>>(mean_num(P), P->inv_wn, P->d_red + 1);
     subtract_mean_kernel<<<1216, 256, 0, st>>>(p, nxy * P->nz, P->d_red + 1);
     rc = cuda_rc(cudaGetLastError());
     if (rc) return rc;
