@@ -69,7 +69,7 @@ struct ThomasArgs {  // z sweeps of Eq. 12 (thomas.cu)
 };
 
 struct ResBox {  // refinement residual and norms (refine.cu)
-  const double* zop;   // Poisson: A_k | B_k - 2/dx^2 - 2/dy^2 | C_k
+  const float* zd2;    // Poisson: double-float split of D_k (first residual, refine.cu)
   const double* abc;   // Helmholtz: A' | B' | C'
   const double* dzf;   // cell widths
   double* partial;     // nz plane sums
@@ -80,7 +80,6 @@ struct ResBox {  // refinement residual and norms (refine.cu)
   const float* zop2;   // double-float split of zop, 1/dx^2, 1/dy^2
   unsigned int* rmax;  // max |r| (float bits)
   int nx, ny, nz, n;   // n = Helmholtz unknowns per column
-  double idx2, idy2;
   int neumann;         // the operator has the constants as null space (mean removal)
   int ybc;             // 0 periodic y, 1 Neumann walls, 2 Dirichlet walls
   const float* dz2;    // double-float split of the cell widths

@@ -153,7 +153,7 @@ struct cfs_plan {
   double* d_mpart;   // per-block dz-weighted sums of a correction (residual grid blocks)
   double inv_wn;     // 1 / (sum of the cell widths * Nx * Ny)
   double* d_red;     // reduction scratch: [0] max |r| (float bits), [1] mean, [2..] partials
-  double* d_zop;     // 3*nz doubles: A_k | B_k - 2/dx^2 - 2/dy^2 | C_k of the Poisson operator
+  float* d_zd2;      // D_k = A_k + B'_k + C_k + 2/dx^2 + 2/dy^2 (exact sum), split: hi[nz] | lo[nz]
   double tol;        // relative residual target
   int maxit;         // at most this many corrections
   int last_iters;

@@ -13,7 +13,8 @@
 //
 // C = double2 is the FP64 solve.  C = float2 is the inner solve of iterative
 // refinement; its inverse can write the FP64 result directly (OUT_SET) or add
-// it to an FP64 field (OUT_ADD), the correction step p += delta.
+// it to an FP64 field (OUT_ADD), the correction step p += delta; both leave
+// the FP32 correction in place too, for the residual kernels.
 #include "chanfs_fft.cuh"
 #include "chanfs_group.cuh"
 #include "chanfs_tma.cuh"
@@ -148,7 +149,7 @@ __device__ __forceinline__ void rfft_x_body(const C* in, void* outv, long long n
         tma_store_commit_and_wait_read();
       }
     } else {
-      if (OUT == OUT_ADD) {  // the correction stays behind for the residual update
+      {  // the correction also stays behind (FP32, in place) for the residual kernels
         fence_proxy_async();
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -166,8 +167,7 @@ __device__ __forceinline__ void rfft_x_body(const C* in, void* outv, long long n
           dst[e] = make_double2(p.x + f32_to_f64(r.x), p.y + f32_to_f64(r.y));
         }
       }
-      if (OUT == OUT_ADD && threadIdx.x == 0)
-        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     }
   }
 }

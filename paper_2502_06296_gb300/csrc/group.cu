@@ -317,7 +317,7 @@ static int group_bind(cfs_group* G, int nplans, const cfs_plan_t* plans, cudaStr
     const long long nxy = (long long)P->nx * P->ny;
     ResBox& r = res[b];
     memset(&r, 0, sizeof(r));
-    r.zop = P->d_zop;
+    r.zd2 = P->d_zd2;
     r.dzf = P->d_dzf;
     r.partial = P->d_red + 2;
     r.mean = P->d_red + 1;
@@ -331,8 +331,6 @@ static int group_bind(cfs_group* G, int nplans, const cfs_plan_t* plans, cudaStr
     r.nz = P->nz;
     r.n = P->nz;
     const double dx = P->lx / P->nx, dy = P->ly / P->ny;
-    r.idx2 = 1.0 / (dx * dx);
-    r.idy2 = 1.0 / (dy * dy);
     r.neumann = P->has_null;
     r.ybc = P->ybc;
     r.dz2 = P->d_dz2;
@@ -537,7 +535,7 @@ cudaError_t poisson_iteration(cfs_group* G, int kind, cudaGraphConditionalHandle
   const int nb = G->nbox;
   GroupMap g{G->d_sx, G->d_active, nb};
   cudaError_t e = launch_rfft_x_group32(G->d_xf, g, G->tx, G->smem_x, false, OUT_SAME, G->d_io,
-                                        kind == 2, st);
+                                        kind >= 1, st);
   if (e == cudaSuccess) {
     g.start = G->d_sy;
     e = launch_fft_y_group32(G->d_y, g, G->ty, G->smem_y, false, st);

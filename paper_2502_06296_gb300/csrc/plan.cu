@@ -187,7 +187,7 @@ static void plan_free(cfs_plan* P) {
   cudaFree(P->d_dz2);
   cudaFree(P->d_mpart);
   cudaFree(P->d_red);
-  cudaFree(P->d_zop);
+  cudaFree(P->d_zd2);
   cudaFree(P->d_wy);
   cudaFree(P->d_wy32);
 
@@ -390,7 +390,6 @@ extern "C" int cfs_plan_create_walls(cfs_plan_t* out, int nx, int ny, int nz, do
     if (!rc) rc = dev_upload<float>(&P->d_bwd32, nullptr, nfac, &P->device_bytes);
     if (!rc) rc = dev_upload<float>(&P->d_r32, nullptr, (size_t)nx * ny * nz, &P->device_bytes);
     if (!rc) rc = dev_upload<double>(&P->d_red, nullptr, (size_t)nz + 8, &P->device_bytes);
-    if (!rc) rc = dev_upload(&P->d_zop, zop.data(), zop.size(), &P->device_bytes);
     // double-float split (hi = fl32(v), lo = fl32(v - hi)) of the operator's
     // coefficients for the residual update r - L delta of later iterations
     std::vector<double> coef(zop);
@@ -403,6 +402,25 @@ extern "C" int cfs_plan_create_walls(cfs_plan_t* out, int nx, int ny, int nz, do
       z2[coef.size() + i] = (float)(coef[i] - (double)hi);
     }
     if (!rc) rc = dev_upload(&P->d_zop2, z2.data(), z2.size(), &P->device_bytes);
+    // D_k = A_k + B'_k + C_k + 2/dx^2 + 2/dy^2, the centre weight left when the
+    // stencil is written in differences (first residual), summed exactly (a
+    // TwoSum cascade; the FP64 rounding residue of zero in the interior)
+    std::vector<float> zd2(2 * (size_t)nz);
+    for (int k = 0; k < nz; ++k) {
+      const double terms[5] = {zop[k], zop[nz + k], zop[2 * nz + k], 2.0 / (dx * dx),
+                               2.0 / (dy * dy)};
+      double s = 0.0, err = 0.0;
+      for (double v : terms) {
+        const double t = s + v, bb = t - s;
+        err += (s - (t - bb)) + (v - bb);
+        s = t;
+      }
+      const double d = s + err;
+      const float hi = (float)d;
+      zd2[k] = hi;
+      zd2[nz + k] = (float)(d - (double)hi);
+    }
+    if (!rc) rc = dev_upload(&P->d_zd2, zd2.data(), zd2.size(), &P->device_bytes);
     // the weighted mean of the solution is accumulated from the corrections
     std::vector<float> dz2(2 * (size_t)nz);
     double wsum = 0.0;

@@ -139,78 +139,6 @@ __global__ void mean_final_kernel(const double* partial, int nz, const double* d
   mean_final_body(partial, nz, dzf, nxy, mean);
 }
 
-// r = (f - mean) - L p, written as FP32, and max |r|.  One thread per (x, y)
-// column marching up in z with p_{k-1}, p_k, p_{k+1} in registers; the x and
-// y neighbours of a plane are shared through L1.
-// rdf (may be null) receives r as a double-float pair hi + lo (hi = fl32(r),
-// lo = fl32(r - hi), both from the fields of r) for the updates that follow.
-// zop = [A_k | B_k - 2/dx^2 - 2/dy^2 | C_k]; FP64: 8 instructions per point
-// (the FP32 roundings of r run on the integer units).
-__device__ __forceinline__ void poisson_residual_body(
-    const double* __restrict__ f, const double* __restrict__ p, const double* __restrict__ zop,
-    const double* __restrict__ mean, float* __restrict__ r32, float2* __restrict__ rdf,
-    unsigned int* rmax, int nx, int ny, int nz, double idx2, double idy2, int ybc,
-    const float* __restrict__ dz2, double* mpart, long long blk) {
-  const long long nxy = (long long)nx * ny;
-  const long long col = blk * blockDim.x + threadIdx.x;
-  float vmax = 0.0f;
-  DoubleFloat macc{0.0f, 0.0f};  // sum_k dz_k p_k of the column (p is a first correction)
-  if (col < nxy) {
-    const double mu = mean ? *mean : 0.0;
-    const int i = (int)(col % nx), j = (int)(col / nx);
-    const long long ip = (i + 1 == nx) ? col - i : col + 1;
-    const long long im = (i == 0) ? col + nx - 1 : col - 1;
-    // y neighbours: periodic, or the mirror ghost of a wall (+p Neumann, -p Dirichlet)
-    long long jp, jm;
-    bool np_ = false, nm_ = false;  // negate the ghost
-    if (ybc == CFS_Y_PERIODIC) {
-      jp = (j + 1 == ny) ? col - (long long)j * nx : col + nx;
-      jm = (j == 0) ? col + (long long)(ny - 1) * nx : col - nx;
-    } else {
-      jp = (j + 1 == ny) ? col : col + nx;
-      jm = (j == 0) ? col : col - nx;
-      np_ = (ybc == CFS_Y_DIRICHLET) && (j + 1 == ny);
-      nm_ = (ybc == CFS_Y_DIRICHLET) && (j == 0);
-    }
-    // the loads of plane k + 1 are issued one iteration ahead
-    double pkm = 0.0, pk = p[col];
-    double pkp = (nz > 1) ? p[nxy + col] : 0.0;
-    double xp = p[ip], xm = p[im], yp = p[jp], ym = p[jm], fk = f[col];
-    for (int k = 0; k < nz; ++k) {
-      const long long o = (long long)k * nxy;
-      const long long on = (k + 1 < nz) ? o + nxy : o;  // plane k + 1 (clamped)
-      const double pkp2 = (k + 2 < nz) ? p[on + nxy + col] : 0.0;
-      const double xpn = p[on + ip], xmn = p[on + im], ypn = p[on + jp], ymn = p[on + jm];
-      const double fkn = f[on + col];
-      // r = f - (mean + L p); the mean rides in the first FMA
-      const double sx = xp + xm;
-      const double sy = (np_ ? -yp : yp) + (nm_ ? -ym : ym);
-      double t = fma(zop[nz + k], pk, mu);
-      t = fma(idx2, sx, t);
-      t = fma(idy2, sy, t);
-      t = fma(zop[k], pkm, t);
-      t = fma(zop[2 * nz + k], pkp, t);
-      const double r = fk - t;
-      float rf, rlo;
-      f64_split(r, &rf, &rlo);  // on the integer units
-      r32[o + col] = rf;
-      if (rdf) rdf[o + col] = make_float2(rf, rlo);
-      vmax = fmaxf(vmax, fabsf(rf));
-      if (mpart) df_acc(macc, dz2[k], dz2[nz + k], f64_to_f32(pk));  // p holds FP32 values
-      pkm = pk;
-      pk = pkp;
-      pkp = pkp2;
-      xp = xpn;
-      xm = xmn;
-      yp = ypn;
-      ym = ymn;
-      fk = fkn;
-    }
-  }
-  if (mpart) block_sum_to(f32_to_f64(macc.s) + f32_to_f64(macc.e), mpart + blk);
-  block_max_to(vmax, rmax);
-}
-
 // ----------------------------------------------------------------------------
 // Residual update of the later iterations: r_new = r_old - L delta for the FP32
 // correction delta (exact FP32 values) just added to p.  L delta is formed in
@@ -222,7 +150,8 @@ __device__ __forceinline__ void poisson_residual_body(
 // |delta| is small, so r_new is as accurate as a direct FP64 evaluation
 // (whose error is about 2^-53 ||L|| |p|).  The residual itself is kept as a
 // double-float pair too, so the update runs without FP64 instructions.
-// The first residual of a solve (|delta| ~ |p|) stays the direct FP64 one.
+// The first residual of a solve (|delta| ~ |p|) takes the stencil in
+// differences (below).
 // ----------------------------------------------------------------------------
 // z2 = hi[3nz + 2] | lo[3nz + 2]: the split zop rows, then 1/dx^2, 1/dy^2.
 __device__ __forceinline__ void poisson_update_body(const float* __restrict__ dlt,
@@ -307,6 +236,131 @@ __global__ void __launch_bounds__(kResBlock) poisson_update_kernel(
   poisson_update_body(dlt, rdf, r32, z2, rmax, nx, ny, nz, ybc, dz2, mpart, blockIdx.x);
 }
 
+// ----------------------------------------------------------------------------
+// First residual of a solve: r_1 = (f - mean) - L delta for the first FP32
+// correction delta (= p).  Here |delta| ~ |p|, and the stencil's terms, of
+// size |p|/h^2, cancel down to the size of f: the update's double-float
+// error, 2^-48 of sum |c d|, would then exceed a direct FP64 evaluation's
+// 2^-53 of the same sum by 2^5.  So L is taken in differences,
+//   L d = A_k (d_{k-1} - d_k) + C_k (d_{k+1} - d_k)
+//       + (1/dx^2) [(d_{i+1} - d) + (d_{i-1} - d)]
+//       + (1/dy^2) [(d_{j+1} - d) + (d_{j-1} - d)] + D_k d,
+//   D_k = A_k + B'_k + C_k + 2/dx^2 + 2/dy^2   (B'_k the zop centre row),
+// the same sum regrouped (the ghost values of the walls enter as they do in
+// the direct form).  D_k is summed exactly on the host; it is the rounding
+// residue of zero in the interior and carries the wall terms of Dirichlet
+// walls.  The difference of two FP32 values is exact as a TwoSum pair, so
+// each term has the size of c |d_n - d|, and the error is 2^-48 of sum
+// c |d_n - d| ~ 6 * 2^-48 |grad p| / h, against the direct FP64 evaluation's
+// 12 * 2^-53 |p| / h^2: 16 h |grad p| / |p| times that, below it where the
+// field is resolved by more than about 100 points per wavelength and never
+// above it by more than 2^5.  The solution of the Poisson equation (Eq. 4) is
+// smooth (its grid-scale part is O(h^2 |f|)).  f - mean is one FP64
+// subtraction; its split into hi + lo runs on the integer units.
+// ----------------------------------------------------------------------------
+// acc (+)= c * (a - b), the difference exact (TwoSum), c = ch + cl.
+template <bool INIT>
+__device__ __forceinline__ void diff_acc(DoubleFloat& acc, float ch, float cl, float a, float b) {
+  float dh, dl;
+  two_sum(a, -b, dh, dl);
+  const float q = __fmul_rn(ch, dh);
+  float e = __fmaf_rn(ch, dh, -q);  // ch * dh - q, exact
+  e = __fmaf_rn(ch, dl, e);
+  e = __fmaf_rn(cl, dh, e);
+  if (INIT) {
+    acc.s = q;
+    acc.e = e;
+  } else {
+    float s, t;
+    two_sum(acc.s, q, s, t);
+    acc.s = s;
+    acc.e = __fadd_rn(acc.e, __fadd_rn(t, e));
+  }
+}
+
+// z2 as for the update; zd2 = hi[nz] | lo[nz] of D_k.  r32 must not alias
+// dlt (the neighbours of a column are read from dlt).
+__device__ __forceinline__ void poisson_first_body(
+    const double* __restrict__ f, const double* __restrict__ mean, const float* __restrict__ dlt,
+    float2* __restrict__ rdf, float* __restrict__ r32, const float* __restrict__ z2,
+    const float* __restrict__ zd2, unsigned int* rmax, int nx, int ny, int nz, int ybc,
+    const float* __restrict__ dz2, double* mpart, long long blk) {
+  const long long nxy = (long long)nx * ny;
+  const long long col = blk * blockDim.x + threadIdx.x;
+  float vmax = 0.0f;
+  DoubleFloat macc{0.0f, 0.0f};  // sum_k dz_k delta_k of the column
+  if (col < nxy) {
+    const double mu = mean ? *mean : 0.0;
+    const int i = (int)(col % nx), j = (int)(col / nx);
+    const long long ip = (i + 1 == nx) ? col - i : col + 1;
+    const long long im = (i == 0) ? col + nx - 1 : col - 1;
+    // y neighbours: periodic, or the mirror ghost of a wall (+d Neumann, -d Dirichlet)
+    long long jp, jm;
+    bool np_ = false, nm_ = false;  // negate the ghost
+    if (ybc == CFS_Y_PERIODIC) {
+      jp = (j + 1 == ny) ? col - (long long)j * nx : col + nx;
+      jm = (j == 0) ? col + (long long)(ny - 1) * nx : col - nx;
+    } else {
+      jp = (j + 1 == ny) ? col : col + nx;
+      jm = (j == 0) ? col : col - nx;
+      np_ = (ybc == CFS_Y_DIRICHLET) && (j + 1 == ny);
+      nm_ = (ybc == CFS_Y_DIRICHLET) && (j == 0);
+    }
+    const int nc = 3 * nz + 2;
+    const float axh = z2[3 * nz], axl = z2[nc + 3 * nz];
+    const float ayh = z2[3 * nz + 1], ayl = z2[nc + 3 * nz + 1];
+    // the loads of plane k + 1 are issued one iteration ahead
+    float dkm = 0.0f, dk = dlt[col];
+    float dkp = (nz > 1) ? dlt[nxy + col] : 0.0f;
+    float xp = dlt[ip], xm = dlt[im], yp = dlt[jp], ym = dlt[jm];
+    double fk = f[col];
+    for (int k = 0; k < nz; ++k) {
+      const long long o = (long long)k * nxy;
+      const long long on = (k + 1 < nz) ? o + nxy : o;  // plane k + 1 (clamped)
+      const float dkp2 = (k + 2 < nz) ? dlt[on + nxy + col] : 0.0f;
+      const float xpn = dlt[on + ip], xmn = dlt[on + im], ypn = dlt[on + jp], ymn = dlt[on + jm];
+      const double fkn = f[on + col];
+      DoubleFloat acc;
+      diff_acc<true>(acc, z2[k], z2[nc + k], dkm, dk);  // dkm = 0 below the first row
+      diff_acc<false>(acc, z2[2 * nz + k], z2[nc + 2 * nz + k], dkp, dk);
+      diff_acc<false>(acc, axh, axl, xp, dk);
+      diff_acc<false>(acc, axh, axl, xm, dk);
+      diff_acc<false>(acc, ayh, ayl, np_ ? -yp : yp, dk);
+      diff_acc<false>(acc, ayh, ayl, nm_ ? -ym : ym, dk);
+      df_acc(acc, zd2[k], zd2[nz + k], dk);
+      // ((f - mean) split) - (s + e), renormalised as in the update
+      float fh, fl, sh, se, hi, lo;
+      f64_split(fk - mu, &fh, &fl);
+      two_sum(fh, -acc.s, sh, se);
+      se = __fadd_rn(se, __fsub_rn(fl, acc.e));
+      two_sum(sh, se, hi, lo);
+      rdf[o + col] = make_float2(hi, lo);
+      r32[o + col] = hi;
+      vmax = fmaxf(vmax, fabsf(hi));
+      if (mpart) df_acc(macc, dz2[k], dz2[nz + k], dk);
+      dkm = dk;
+      dk = dkp;
+      dkp = dkp2;
+      xp = xpn;
+      xm = xmn;
+      yp = ypn;
+      ym = ymn;
+      fk = fkn;
+    }
+  }
+  if (mpart) block_sum_to(f32_to_f64(macc.s) + f32_to_f64(macc.e), mpart + blk);
+  block_max_to(vmax, rmax);
+}
+
+__global__ void __launch_bounds__(kResBlock) poisson_first_kernel(
+    const double* __restrict__ f, const double* __restrict__ mean, const float* __restrict__ dlt,
+    float2* __restrict__ rdf, float* __restrict__ r32, const float* __restrict__ z2,
+    const float* __restrict__ zd2, unsigned int* rmax, int nx, int ny, int nz, int ybc,
+    const float* __restrict__ dz2, double* mpart) {
+  poisson_first_body(f, mean, dlt, rdf, r32, z2, zd2, rmax, nx, ny, nz, ybc, dz2, mpart,
+                     blockIdx.x);
+}
+
 // The dz-weighted sum of a correction, from the per-block sums of the
 // residual kernels, added in a fixed order to the running sum *num (the
 // numerator of the weighted mean of the solution).
@@ -354,15 +408,6 @@ __global__ void __launch_bounds__(256) rhs_start_kernel(const double* __restrict
                                                         float* __restrict__ r32,
                                                         unsigned int* rmax, long long n) {
   rhs_start_body(f, mean, r32, rmax, n, blockIdx.x, gridDim.x);
-}
-
-__global__ void __launch_bounds__(kResBlock) poisson_residual_kernel(
-    const double* __restrict__ f, const double* __restrict__ p, const double* __restrict__ zop,
-    const double* __restrict__ mean, float* __restrict__ r32, float2* __restrict__ rdf,
-    unsigned int* rmax, int nx, int ny, int nz, double idx2, double idy2, int ybc,
-    const float* __restrict__ dz2, double* mpart) {
-  poisson_residual_body(f, p, zop, mean, r32, rdf, rmax, nx, ny, nz, idx2, idy2, ybc, dz2,
-                        mpart, blockIdx.x);
 }
 
 // Helmholtz: u (+)= delta, then r = rhs - (I - c L_z) u, as FP32, and max |r|.
@@ -457,15 +502,14 @@ __global__ void mean_final_group_kernel(const ResBox* boxes, GroupMap g) {
   mean_final_body(r.partial, r.nz, r.dzf, (long long)r.nx * r.ny, r.mean);
 }
 
-__global__ void __launch_bounds__(kResBlock) poisson_residual_group_kernel(const ResBox* boxes,
-                                                                           GroupMap g,
-                                                                           const GroupIo* io) {
+__global__ void __launch_bounds__(kResBlock) poisson_first_group_kernel(const ResBox* boxes,
+                                                                        GroupMap g,
+                                                                        const GroupIo* io) {
   int b, blk;
   if (!group_block(g, &b, &blk)) return;
   const ResBox& r = boxes[b];
-  poisson_residual_body(io[b].f, io[b].p, r.zop, r.neumann ? r.mean : nullptr, r.r32, r.rdf,
-                        r.rmax, r.nx, r.ny, r.nz, r.idx2, r.idy2, r.ybc, r.dz2,
-                        r.neumann ? r.mpart : nullptr, blk);
+  poisson_first_body(io[b].f, r.neumann ? r.mean : nullptr, r.r32, r.rdf, r.r32b, r.zop2, r.zd2,
+                     r.rmax, r.nx, r.ny, r.nz, r.ybc, r.dz2, r.neumann ? r.mpart : nullptr, blk);
 }
 
 // One block per box (Neumann boxes; the others have nothing to sum).
@@ -615,7 +659,7 @@ cudaError_t launch_group_refine_stage(int stage, const ResBox* boxes, GroupMap g
       mean_final_group_kernel<<<total, 256, 0, st>>>(boxes, g);
       break;
     case GSTAGE_RESIDUAL:
-      poisson_residual_group_kernel<<<total, kResBlock, 0, st>>>(boxes, g, io);
+      poisson_first_group_kernel<<<total, kResBlock, 0, st>>>(boxes, g, io);
       break;
     case GSTAGE_UPDATE:
       poisson_update_group_kernel<<<total, kResBlock, 0, st>>>(boxes, g);
@@ -744,8 +788,6 @@ static double* mean_num(cfs_plan* P) { return P->d_red + 2 + P->nz; }
 
 int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st) {
   const long long nxy = (long long)P->nx * P->ny;
-  const double dx = P->lx / P->nx, dy = P->ly / P->ny;
-  const double idx2 = 1.0 / (dx * dx), idy2 = 1.0 / (dy * dy);
   const unsigned grid = (unsigned)((nxy + kResBlock - 1) / kResBlock);
   double* mean = nullptr;
   cudaError_t e = cudaSuccess;
@@ -777,7 +819,7 @@ int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st) {
     // delta = solve32(r) in r32 (the right-hand side of the later iterations
     // comes from r32b); p (+)= delta fused into the last pass, which also
     // leaves delta in r32 for the residual update
-    e = launch_rfft_x32(P, it >= 2 ? P->d_r32b : P->d_r32, P->d_r32, false, st);
+    e = launch_rfft_x32(P, it >= 1 ? P->d_r32b : P->d_r32, P->d_r32, false, st);
     if (e == cudaSuccess) e = launch_fft_y32(P, P->d_r32, false, st);
     if (e == cudaSuccess) e = launch_thomas32(P, P->d_r32, st);
     if (e == cudaSuccess) e = launch_fft_y32(P, P->d_r32, true, st);
@@ -785,11 +827,10 @@ int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st) {
     if (e == cudaSuccess) e = cudaMemsetAsync(P->d_red, 0, sizeof(unsigned int), st);
     // (Neumann: each kernel also sums its correction, dz-weighted, per block)
     double* mpart = P->has_null ? P->d_mpart : nullptr;
-    if (e == cudaSuccess && it == 0) {  // r = f - mean - L p, directly in FP64
-      poisson_residual_kernel<<<grid, kResBlock, 0, st>>>(f, p, P->d_zop, mean, P->d_r32,
-                                                          P->d_rdf, max_word(P), P->nx, P->ny,
-                                                          P->nz, idx2, idy2, P->ybc, P->d_dz2,
-                                                          mpart);
+    if (e == cudaSuccess && it == 0) {  // r = (f - mean) - L delta, by differences
+      poisson_first_kernel<<<grid, kResBlock, 0, st>>>(f, mean, P->d_r32, P->d_rdf, P->d_r32b,
+                                                       P->d_zop2, P->d_zd2, max_word(P), P->nx,
+                                                       P->ny, P->nz, P->ybc, P->d_dz2, mpart);
       e = cudaGetLastError();
     } else if (e == cudaSuccess) {  // r -= L delta
       poisson_update_kernel<<<grid, kResBlock, 0, st>>>(P->d_r32, P->d_rdf, P->d_r32b, P->d_zop2,
