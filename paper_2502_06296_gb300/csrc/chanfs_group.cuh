@@ -69,7 +69,6 @@ struct ThomasArgs {  // z sweeps of Eq. 12 (thomas.cu)
 };
 
 struct ResBox {  // refinement residual and norms (refine.cu)
-  const float* zd2;    // Poisson: double-float split of D_k (first residual, refine.cu)
   const double* abc;   // Helmholtz: A' | B' | C'
   const double* dzf;   // cell widths
   double* partial;     // nz plane sums
@@ -77,12 +76,11 @@ struct ResBox {  // refinement residual and norms (refine.cu)
   float* r32;          // FP32 residual / correction
   float* r32b;         // FP32 residual of the later iterations
   float2* rdf;         // residual kept between iterations, double-float (hi, lo)
-  const float* zop2;   // double-float split of zop, 1/dx^2, 1/dy^2
+  const float4* zk;    // Poisson: packed double-float coefficients per plane (refine.cu)
   unsigned int* rmax;  // max |r| (float bits)
   int nx, ny, nz, n;   // n = Helmholtz unknowns per column
   int neumann;         // the operator has the constants as null space (mean removal)
   int ybc;             // 0 periodic y, 1 Neumann walls, 2 Dirichlet walls
-  const float* dz2;    // double-float split of the cell widths
   double* mpart;       // per-block weighted sums of a correction
   double* mnum;        // running weighted sum of the solution
   double inv_wn;       // 1 / (sum of the cell widths * Nx * Ny)

@@ -148,12 +148,11 @@ struct cfs_plan {
   float* d_r32;      // FP32 residual / correction field (in-place inner solve)
   float* d_r32b;     // the FP32 residual of the later iterations (input of their solves)
   float2* d_rdf;     // the residual kept between iterations, double-float (hi, lo)
-  float* d_zop2;     // double-float split of zop and of 1/dx^2, 1/dy^2: hi[3nz+2] | lo[3nz+2]
-  float* d_dz2;      // double-float split of the cell widths: hi[nz] | lo[nz]
+  float4* d_zk;      // per plane k, split hi + lo: (A_k, C_k), (B'_k, dz_k), (D_k, dz_k); then
+                     // (1/dx^2, 1/dy^2).  D_k = A_k + B'_k + C_k + 2/dx^2 + 2/dy^2 (exact sum)
   double* d_mpart;   // per-block dz-weighted sums of a correction (residual grid blocks)
   double inv_wn;     // 1 / (sum of the cell widths * Nx * Ny)
   double* d_red;     // reduction scratch: [0] max |r| (float bits), [1] mean, [2..] partials
-  float* d_zd2;      // D_k = A_k + B'_k + C_k + 2/dx^2 + 2/dy^2 (exact sum), split: hi[nz] | lo[nz]
   double tol;        // relative residual target
   int maxit;         // at most this many corrections
   int last_iters;

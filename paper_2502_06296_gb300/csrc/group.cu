@@ -317,14 +317,13 @@ static int group_bind(cfs_group* G, int nplans, const cfs_plan_t* plans, cudaStr
     const long long nxy = (long long)P->nx * P->ny;
     ResBox& r = res[b];
     memset(&r, 0, sizeof(r));
-    r.zd2 = P->d_zd2;
     r.dzf = P->d_dzf;
     r.partial = P->d_red + 2;
     r.mean = P->d_red + 1;
     r.r32 = P->d_r32;
     r.r32b = P->d_r32b;
     r.rdf = P->d_rdf;
-    r.zop2 = P->d_zop2;
+    r.zk = P->d_zk;
     r.rmax = reinterpret_cast<unsigned int*>(P->d_red);
     r.nx = P->nx;
     r.ny = P->ny;
@@ -333,7 +332,6 @@ static int group_bind(cfs_group* G, int nplans, const cfs_plan_t* plans, cudaStr
     const double dx = P->lx / P->nx, dy = P->ly / P->ny;
     r.neumann = P->has_null;
     r.ybc = P->ybc;
-    r.dz2 = P->d_dz2;
     r.mpart = P->d_mpart;
     r.mnum = P->d_red + 2 + P->nz;  // after the plane partials
     r.inv_wn = P->inv_wn;

@@ -183,11 +183,9 @@ static void plan_free(cfs_plan* P) {
   cudaFree(P->d_r32);
   cudaFree(P->d_r32b);
   cudaFree(P->d_rdf);
-  cudaFree(P->d_zop2);
-  cudaFree(P->d_dz2);
+  cudaFree(P->d_zk);
   cudaFree(P->d_mpart);
   cudaFree(P->d_red);
-  cudaFree(P->d_zd2);
   cudaFree(P->d_wy);
   cudaFree(P->d_wy32);
 
@@ -390,48 +388,44 @@ extern "C" int cfs_plan_create_walls(cfs_plan_t* out, int nx, int ny, int nz, do
     if (!rc) rc = dev_upload<float>(&P->d_bwd32, nullptr, nfac, &P->device_bytes);
     if (!rc) rc = dev_upload<float>(&P->d_r32, nullptr, (size_t)nx * ny * nz, &P->device_bytes);
     if (!rc) rc = dev_upload<double>(&P->d_red, nullptr, (size_t)nz + 8, &P->device_bytes);
-    // double-float split (hi = fl32(v), lo = fl32(v - hi)) of the operator's
-    // coefficients for the residual update r - L delta of later iterations
-    std::vector<double> coef(zop);
-    coef.push_back(1.0 / (dx * dx));
-    coef.push_back(1.0 / (dy * dy));
-    std::vector<float> z2(2 * coef.size());
-    for (size_t i = 0; i < coef.size(); ++i) {
-      const float hi = (float)coef[i];
-      z2[i] = hi;
-      z2[coef.size() + i] = (float)(coef[i] - (double)hi);
-    }
-    if (!rc) rc = dev_upload(&P->d_zop2, z2.data(), z2.size(), &P->device_bytes);
-    // D_k = A_k + B'_k + C_k + 2/dx^2 + 2/dy^2, the centre weight left when the
-    // stencil is written in differences (first residual), summed exactly (a
-    // TwoSum cascade; the FP64 rounding residue of zero in the interior)
-    std::vector<float> zd2(2 * (size_t)nz);
+    // The residual kernels' coefficients, each split as hi = fl32(v),
+    // lo = fl32(v - hi), packed per plane (three float4: (A, C), (B', dz),
+    // (D, dz)) and then (1/dx^2, 1/dy^2).  D_k = A_k + B'_k + C_k + 2/dx^2 +
+    // 2/dy^2 is the centre weight left when the stencil is written in
+    // differences (first residual); it is summed exactly (a TwoSum cascade:
+    // in the interior it is the FP64 rounding residue of zero).
+    auto split = [](double v, float* h, float* l) {
+      *h = (float)v;
+      *l = (float)(v - (double)*h);
+    };
+    std::vector<float4> zk(3 * (size_t)nz + 1);
+    double wsum = 0.0;
     for (int k = 0; k < nz; ++k) {
       const double terms[5] = {zop[k], zop[nz + k], zop[2 * nz + k], 2.0 / (dx * dx),
                                2.0 / (dy * dy)};
-      double s = 0.0, err = 0.0;
+      double sum = 0.0, err = 0.0;
       for (double v : terms) {
-        const double t = s + v, bb = t - s;
-        err += (s - (t - bb)) + (v - bb);
-        s = t;
+        const double t = sum + v, bb = t - sum;
+        err += (sum - (t - bb)) + (v - bb);
+        sum = t;
       }
-      const double d = s + err;
-      const float hi = (float)d;
-      zd2[k] = hi;
-      zd2[nz + k] = (float)(d - (double)hi);
-    }
-    if (!rc) rc = dev_upload(&P->d_zd2, zd2.data(), zd2.size(), &P->device_bytes);
-    // the weighted mean of the solution is accumulated from the corrections
-    std::vector<float> dz2(2 * (size_t)nz);
-    double wsum = 0.0;
-    for (int k = 0; k < nz; ++k) {
-      const float hi = (float)P->dzf[k];
-      dz2[k] = hi;
-      dz2[nz + k] = (float)(P->dzf[k] - (double)hi);
+      float4& ac = zk[3 * (size_t)k];
+      float4& bw = zk[3 * (size_t)k + 1];
+      float4& dw = zk[3 * (size_t)k + 2];
+      split(zop[k], &ac.x, &ac.y);
+      split(zop[2 * nz + k], &ac.z, &ac.w);
+      split(zop[nz + k], &bw.x, &bw.y);
+      split(P->dzf[k], &bw.z, &bw.w);
+      split(sum + err, &dw.x, &dw.y);
+      dw.z = bw.z;
+      dw.w = bw.w;
       wsum += P->dzf[k];
     }
+    float4& axy = zk[3 * (size_t)nz];
+    split(1.0 / (dx * dx), &axy.x, &axy.y);
+    split(1.0 / (dy * dy), &axy.z, &axy.w);
+    if (!rc) rc = dev_upload(&P->d_zk, zk.data(), zk.size(), &P->device_bytes);
     P->inv_wn = 1.0 / (wsum * (double)nx * (double)ny);
-    if (!rc) rc = dev_upload(&P->d_dz2, dz2.data(), dz2.size(), &P->device_bytes);
     if (!rc)
       rc = dev_upload<double>(&P->d_mpart, nullptr, ((size_t)nx * ny + 127) / 128,
                               &P->device_bytes);

@@ -62,14 +62,21 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
   t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// acc (+)= (chi + clo) * d; INIT: acc = the product.
+template <bool INIT = false>
 __device__ __forceinline__ void df_acc(DoubleFloat& acc, float chi, float clo, float d) {
   const float p = __fmul_rn(chi, d);
   float e = __fmaf_rn(chi, d, -p);  // chi * d - p, exact
   e = __fmaf_rn(clo, d, e);
-  float s, t;
-  two_sum(acc.s, p, s, t);
-  acc.s = s;
-  acc.e = __fadd_rn(acc.e, __fadd_rn(t, e));
+  if (INIT) {
+    acc.s = p;
+    acc.e = e;
+  } else {
+    float s, t;
+    two_sum(acc.s, p, s, t);
+    acc.s = s;
+    acc.e = __fadd_rn(acc.e, __fadd_rn(t, e));
+  }
 }
 
 // Neumann compatibility: the dz-weighted mean of f, reduced in a fixed order
@@ -153,36 +160,37 @@ __global__ void mean_final_kernel(const double* partial, int nz, const double* d
 // The first residual of a solve (|delta| ~ |p|) takes the stencil in
 // differences (below).
 // ----------------------------------------------------------------------------
-// z2 = hi[3nz + 2] | lo[3nz + 2]: the split zop rows, then 1/dx^2, 1/dy^2.
+// zk: the per-plane coefficients split hi + lo, packed so that a plane's are
+// two 16-byte loads: zk[3k] = (A_k, C_k), zk[3k+1] = (B'_k, dz_k),
+// zk[3k+2] = (D_k, dz_k) (first residual, below), zk[3nz] = (1/dx^2, 1/dy^2),
+// each pair as (hi, lo).
+template <class I>
 __device__ __forceinline__ void poisson_update_body(const float* __restrict__ dlt,
                                                     float2* __restrict__ rdf,
                                                     float* __restrict__ r32,
-                                                    const float* __restrict__ z2,
+                                                    const float4* __restrict__ zk,
                                                     unsigned int* rmax, int nx, int ny, int nz,
-                                                    int ybc, const float* __restrict__ dz2,
-                                                    double* mpart, long long blk) {
-  const long long nxy = (long long)nx * ny;
-  const long long col = blk * blockDim.x + threadIdx.x;
+                                                    int ybc, double* mpart, long long blk) {
+  const I nxy = (I)nx * ny;
+  const I col = (I)(blk * blockDim.x + threadIdx.x);
   float vmax = 0.0f;
   DoubleFloat macc{0.0f, 0.0f};  // sum_k dz_k delta_k of the column
   if (col < nxy) {
     const int i = (int)(col % nx), j = (int)(col / nx);
-    const long long ip = (i + 1 == nx) ? col - i : col + 1;
-    const long long im = (i == 0) ? col + nx - 1 : col - 1;
-    long long jp, jm;
+    const I ip = (i + 1 == nx) ? col - i : col + 1;
+    const I im = (i == 0) ? col + nx - 1 : col - 1;
+    I jp, jm;
     bool np_ = false, nm_ = false;
     if (ybc == CFS_Y_PERIODIC) {
-      jp = (j + 1 == ny) ? col - (long long)j * nx : col + nx;
-      jm = (j == 0) ? col + (long long)(ny - 1) * nx : col - nx;
+      jp = (j + 1 == ny) ? col - (I)j * nx : col + nx;
+      jm = (j == 0) ? col + (I)(ny - 1) * nx : col - nx;
     } else {
       jp = (j + 1 == ny) ? col : col + nx;
       jm = (j == 0) ? col : col - nx;
       np_ = (ybc == CFS_Y_DIRICHLET) && (j + 1 == ny);
       nm_ = (ybc == CFS_Y_DIRICHLET) && (j == 0);
     }
-    const int nc = 3 * nz + 2;
-    const float axh = z2[3 * nz], axl = z2[nc + 3 * nz];
-    const float ayh = z2[3 * nz + 1], ayl = z2[nc + 3 * nz + 1];
+    const float4 axy = zk[3 * nz];
     // the loads of plane k + 1 are issued one iteration ahead, so that they
     // are in flight while plane k is combined
     float dkm = 0.0f, dk = dlt[col];
@@ -190,20 +198,21 @@ __device__ __forceinline__ void poisson_update_body(const float* __restrict__ dl
     float xp = dlt[ip], xm = dlt[im], yp = dlt[jp], ym = dlt[jm];
     float2 rp = rdf[col];
     for (int k = 0; k < nz; ++k) {
-      const long long o = (long long)k * nxy;
+      const I o = (I)k * nxy;
       const bool more = k + 1 < nz;
-      const long long on = more ? o + nxy : o;  // plane k + 1 (clamped)
+      const I on = more ? o + nxy : o;  // plane k + 1 (clamped)
       const float dkp2 = (k + 2 < nz) ? dlt[on + nxy + col] : 0.0f;
       const float xpn = dlt[on + ip], xmn = dlt[on + im], ypn = dlt[on + jp], ymn = dlt[on + jm];
       const float2 rpn = rdf[on + col];
-      DoubleFloat acc{0.0f, 0.0f};
-      df_acc(acc, z2[nz + k], z2[nc + nz + k], dk);
-      df_acc(acc, axh, axl, xp);
-      df_acc(acc, axh, axl, xm);
-      df_acc(acc, ayh, ayl, np_ ? -yp : yp);
-      df_acc(acc, ayh, ayl, nm_ ? -ym : ym);
-      df_acc(acc, z2[k], z2[nc + k], dkm);
-      df_acc(acc, z2[2 * nz + k], z2[nc + 2 * nz + k], dkp);
+      const float4 ac = zk[3 * k], bw = zk[3 * k + 1];
+      DoubleFloat acc;
+      df_acc<true>(acc, bw.x, bw.y, dk);
+      df_acc<false>(acc, axy.x, axy.y, xp);
+      df_acc<false>(acc, axy.x, axy.y, xm);
+      df_acc<false>(acc, axy.z, axy.w, np_ ? -yp : yp);
+      df_acc<false>(acc, axy.z, axy.w, nm_ ? -ym : ym);
+      df_acc<false>(acc, ac.x, ac.y, dkm);
+      df_acc<false>(acc, ac.z, ac.w, dkp);
       // (hi, lo) - (s + e) in double-float: TwoSum of the leading parts, the
       // rest added to the error term, renormalised by a second TwoSum
       float sh, se, hi, lo;
@@ -214,7 +223,7 @@ __device__ __forceinline__ void poisson_update_body(const float* __restrict__ dl
       const float rf = hi;
       r32[o + col] = rf;
       vmax = fmaxf(vmax, fabsf(rf));
-      if (mpart) df_acc(macc, dz2[k], dz2[nz + k], dk);
+      if (mpart) df_acc<false>(macc, bw.z, bw.w, dk);
       dkm = dk;
       dk = dkp;
       dkp = dkp2;
@@ -229,11 +238,19 @@ __device__ __forceinline__ void poisson_update_body(const float* __restrict__ dl
   block_max_to(vmax, rmax);
 }
 
+// Index type of a residual kernel: 32-bit offsets where every index of the
+// field (and the look-ahead two planes on) fits, which saves the 64-bit
+// address arithmetic of the six loads and three stores per point.
+inline __host__ __device__ bool res_idx32(int nx, int ny, int nz) {
+  return (long long)nx * ny * (nz + 2) + kResBlock < (1LL << 31);
+}
+
+template <class I>
 __global__ void __launch_bounds__(kResBlock) poisson_update_kernel(
     const float* __restrict__ dlt, float2* __restrict__ rdf, float* __restrict__ r32,
-    const float* __restrict__ z2, unsigned int* rmax, int nx, int ny, int nz, int ybc,
-    const float* __restrict__ dz2, double* mpart) {
-  poisson_update_body(dlt, rdf, r32, z2, rmax, nx, ny, nz, ybc, dz2, mpart, blockIdx.x);
+    const float4* __restrict__ zk, unsigned int* rmax, int nx, int ny, int nz, int ybc,
+    double* mpart) {
+  poisson_update_body<I>(dlt, rdf, r32, zk, rmax, nx, ny, nz, ybc, mpart, blockIdx.x);
 }
 
 // ----------------------------------------------------------------------------
@@ -278,56 +295,55 @@ __device__ __forceinline__ void diff_acc(DoubleFloat& acc, float ch, float cl, f
   }
 }
 
-// z2 as for the update; zd2 = hi[nz] | lo[nz] of D_k.  r32 must not alias
-// dlt (the neighbours of a column are read from dlt).
+// zk as for the update.  r32 must not alias dlt (the neighbours of a column
+// are read from dlt).
+template <class I>
 __device__ __forceinline__ void poisson_first_body(
     const double* __restrict__ f, const double* __restrict__ mean, const float* __restrict__ dlt,
-    float2* __restrict__ rdf, float* __restrict__ r32, const float* __restrict__ z2,
-    const float* __restrict__ zd2, unsigned int* rmax, int nx, int ny, int nz, int ybc,
-    const float* __restrict__ dz2, double* mpart, long long blk) {
-  const long long nxy = (long long)nx * ny;
-  const long long col = blk * blockDim.x + threadIdx.x;
+    float2* __restrict__ rdf, float* __restrict__ r32, const float4* __restrict__ zk,
+    unsigned int* rmax, int nx, int ny, int nz, int ybc, double* mpart, long long blk) {
+  const I nxy = (I)nx * ny;
+  const I col = (I)(blk * blockDim.x + threadIdx.x);
   float vmax = 0.0f;
   DoubleFloat macc{0.0f, 0.0f};  // sum_k dz_k delta_k of the column
   if (col < nxy) {
     const double mu = mean ? *mean : 0.0;
     const int i = (int)(col % nx), j = (int)(col / nx);
-    const long long ip = (i + 1 == nx) ? col - i : col + 1;
-    const long long im = (i == 0) ? col + nx - 1 : col - 1;
+    const I ip = (i + 1 == nx) ? col - i : col + 1;
+    const I im = (i == 0) ? col + nx - 1 : col - 1;
     // y neighbours: periodic, or the mirror ghost of a wall (+d Neumann, -d Dirichlet)
-    long long jp, jm;
+    I jp, jm;
     bool np_ = false, nm_ = false;  // negate the ghost
     if (ybc == CFS_Y_PERIODIC) {
-      jp = (j + 1 == ny) ? col - (long long)j * nx : col + nx;
-      jm = (j == 0) ? col + (long long)(ny - 1) * nx : col - nx;
+      jp = (j + 1 == ny) ? col - (I)j * nx : col + nx;
+      jm = (j == 0) ? col + (I)(ny - 1) * nx : col - nx;
     } else {
       jp = (j + 1 == ny) ? col : col + nx;
       jm = (j == 0) ? col : col - nx;
       np_ = (ybc == CFS_Y_DIRICHLET) && (j + 1 == ny);
       nm_ = (ybc == CFS_Y_DIRICHLET) && (j == 0);
     }
-    const int nc = 3 * nz + 2;
-    const float axh = z2[3 * nz], axl = z2[nc + 3 * nz];
-    const float ayh = z2[3 * nz + 1], ayl = z2[nc + 3 * nz + 1];
+    const float4 axy = zk[3 * nz];
     // the loads of plane k + 1 are issued one iteration ahead
     float dkm = 0.0f, dk = dlt[col];
     float dkp = (nz > 1) ? dlt[nxy + col] : 0.0f;
     float xp = dlt[ip], xm = dlt[im], yp = dlt[jp], ym = dlt[jm];
     double fk = f[col];
     for (int k = 0; k < nz; ++k) {
-      const long long o = (long long)k * nxy;
-      const long long on = (k + 1 < nz) ? o + nxy : o;  // plane k + 1 (clamped)
+      const I o = (I)k * nxy;
+      const I on = (k + 1 < nz) ? o + nxy : o;  // plane k + 1 (clamped)
       const float dkp2 = (k + 2 < nz) ? dlt[on + nxy + col] : 0.0f;
       const float xpn = dlt[on + ip], xmn = dlt[on + im], ypn = dlt[on + jp], ymn = dlt[on + jm];
       const double fkn = f[on + col];
+      const float4 ac = zk[3 * k], dw = zk[3 * k + 2];
       DoubleFloat acc;
-      diff_acc<true>(acc, z2[k], z2[nc + k], dkm, dk);  // dkm = 0 below the first row
-      diff_acc<false>(acc, z2[2 * nz + k], z2[nc + 2 * nz + k], dkp, dk);
-      diff_acc<false>(acc, axh, axl, xp, dk);
-      diff_acc<false>(acc, axh, axl, xm, dk);
-      diff_acc<false>(acc, ayh, ayl, np_ ? -yp : yp, dk);
-      diff_acc<false>(acc, ayh, ayl, nm_ ? -ym : ym, dk);
-      df_acc(acc, zd2[k], zd2[nz + k], dk);
+      diff_acc<true>(acc, ac.x, ac.y, dkm, dk);  // dkm = 0 below the first row
+      diff_acc<false>(acc, ac.z, ac.w, dkp, dk);
+      diff_acc<false>(acc, axy.x, axy.y, xp, dk);
+      diff_acc<false>(acc, axy.x, axy.y, xm, dk);
+      diff_acc<false>(acc, axy.z, axy.w, np_ ? -yp : yp, dk);
+      diff_acc<false>(acc, axy.z, axy.w, nm_ ? -ym : ym, dk);
+      df_acc<false>(acc, dw.x, dw.y, dk);
       // ((f - mean) split) - (s + e), renormalised as in the update
       float fh, fl, sh, se, hi, lo;
       f64_split(fk - mu, &fh, &fl);
@@ -337,7 +353,7 @@ __device__ __forceinline__ void poisson_first_body(
       rdf[o + col] = make_float2(hi, lo);
       r32[o + col] = hi;
       vmax = fmaxf(vmax, fabsf(hi));
-      if (mpart) df_acc(macc, dz2[k], dz2[nz + k], dk);
+      if (mpart) df_acc<false>(macc, dw.z, dw.w, dk);
       dkm = dk;
       dk = dkp;
       dkp = dkp2;
@@ -352,13 +368,12 @@ __device__ __forceinline__ void poisson_first_body(
   block_max_to(vmax, rmax);
 }
 
+template <class I>
 __global__ void __launch_bounds__(kResBlock) poisson_first_kernel(
     const double* __restrict__ f, const double* __restrict__ mean, const float* __restrict__ dlt,
-    float2* __restrict__ rdf, float* __restrict__ r32, const float* __restrict__ z2,
-    const float* __restrict__ zd2, unsigned int* rmax, int nx, int ny, int nz, int ybc,
-    const float* __restrict__ dz2, double* mpart) {
-  poisson_first_body(f, mean, dlt, rdf, r32, z2, zd2, rmax, nx, ny, nz, ybc, dz2, mpart,
-                     blockIdx.x);
+    float2* __restrict__ rdf, float* __restrict__ r32, const float4* __restrict__ zk,
+    unsigned int* rmax, int nx, int ny, int nz, int ybc, double* mpart) {
+  poisson_first_body<I>(f, mean, dlt, rdf, r32, zk, rmax, nx, ny, nz, ybc, mpart, blockIdx.x);
 }
 
 // The dz-weighted sum of a correction, from the per-block sums of the
@@ -508,8 +523,14 @@ __global__ void __launch_bounds__(kResBlock) poisson_first_group_kernel(const Re
   int b, blk;
   if (!group_block(g, &b, &blk)) return;
   const ResBox& r = boxes[b];
-  poisson_first_body(io[b].f, r.neumann ? r.mean : nullptr, r.r32, r.rdf, r.r32b, r.zop2, r.zd2,
-                     r.rmax, r.nx, r.ny, r.nz, r.ybc, r.dz2, r.neumann ? r.mpart : nullptr, blk);
+  const double* mean = r.neumann ? r.mean : nullptr;
+  double* mpart = r.neumann ? r.mpart : nullptr;
+  if (res_idx32(r.nx, r.ny, r.nz))
+    poisson_first_body<int>(io[b].f, mean, r.r32, r.rdf, r.r32b, r.zk, r.rmax, r.nx, r.ny, r.nz,
+                            r.ybc, mpart, blk);
+  else
+    poisson_first_body<long long>(io[b].f, mean, r.r32, r.rdf, r.r32b, r.zk, r.rmax, r.nx, r.ny,
+                                  r.nz, r.ybc, mpart, blk);
 }
 
 // One block per box (Neumann boxes; the others have nothing to sum).
@@ -555,8 +576,13 @@ __global__ void __launch_bounds__(kResBlock) poisson_update_group_kernel(const R
   int b, blk;
   if (!group_block(g, &b, &blk)) return;
   const ResBox& r = boxes[b];
-  poisson_update_body(r.r32, r.rdf, r.r32b, r.zop2, r.rmax, r.nx, r.ny, r.nz, r.ybc, r.dz2,
-                      r.neumann ? r.mpart : nullptr, blk);
+  double* mpart = r.neumann ? r.mpart : nullptr;
+  if (res_idx32(r.nx, r.ny, r.nz))
+    poisson_update_body<int>(r.r32, r.rdf, r.r32b, r.zk, r.rmax, r.nx, r.ny, r.nz, r.ybc, mpart,
+                             blk);
+  else
+    poisson_update_body<long long>(r.r32, r.rdf, r.r32b, r.zk, r.rmax, r.nx, r.ny, r.nz, r.ybc,
+                                   mpart, blk);
 }
 
 __global__ void subtract_mean_group_kernel(const ResBox* boxes, GroupMap g, const GroupIo* io) {
@@ -789,6 +815,7 @@ static double* mean_num(cfs_plan* P) { return P->d_red + 2 + P->nz; }
 int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st) {
   const long long nxy = (long long)P->nx * P->ny;
   const unsigned grid = (unsigned)((nxy + kResBlock - 1) / kResBlock);
+  const bool idx32 = res_idx32(P->nx, P->ny, P->nz);
   double* mean = nullptr;
   cudaError_t e = cudaSuccess;
   if (P->has_null) {  // remove the dz-weighted mean of f (compatibility)
@@ -828,14 +855,14 @@ int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st) {
     // (Neumann: each kernel also sums its correction, dz-weighted, per block)
     double* mpart = P->has_null ? P->d_mpart : nullptr;
     if (e == cudaSuccess && it == 0) {  // r = (f - mean) - L delta, by differences
-      poisson_first_kernel<<<grid, kResBlock, 0, st>>>(f, mean, P->d_r32, P->d_rdf, P->d_r32b,
-                                                       P->d_zop2, P->d_zd2, max_word(P), P->nx,
-                                                       P->ny, P->nz, P->ybc, P->d_dz2, mpart);
+      auto k = idx32 ? poisson_first_kernel<int> : poisson_first_kernel<long long>;
+      k<<<grid, kResBlock, 0, st>>>(f, mean, P->d_r32, P->d_rdf, P->d_r32b, P->d_zk, max_word(P),
+                                    P->nx, P->ny, P->nz, P->ybc, mpart);
       e = cudaGetLastError();
     } else if (e == cudaSuccess) {  // r -= L delta
-      poisson_update_kernel<<<grid, kResBlock, 0, st>>>(P->d_r32, P->d_rdf, P->d_r32b, P->d_zop2,
-                                                        max_word(P), P->nx, P->ny, P->nz,
-                                                        P->ybc, P->d_dz2, mpart);
+      auto k = idx32 ? poisson_update_kernel<int> : poisson_update_kernel<long long>;
+      k<<<grid, kResBlock, 0, st>>>(P->d_r32, P->d_rdf, P->d_r32b, P->d_zk, max_word(P), P->nx,
+                                    P->ny, P->nz, P->ybc, mpart);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess && mpart) {  // the weighted sum of p, correction by correction
