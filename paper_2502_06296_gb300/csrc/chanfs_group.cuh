@@ -178,23 +178,22 @@ struct GroupCtl {  // device-side iteration state of a grouped refined solve
   int it;          // iterations done
   int nactive;     // boxes still iterating after the last one
 };
-cudaError_t launch_group_start(const ResBox* boxes, int nbox, float* fmax, const int* eligible,
-                               int* active, int* mean_on, int* zero, int* iters, double* rho,
-                               GroupCtl* ctl, cudaStream_t st);
-cudaError_t launch_group_iter_end(const ResBox* boxes, int nbox, const float* fmax,
+cudaError_t launch_group_start(const ResBox* boxes, int nbox, int keys, double* fmax,
+                               const int* eligible, int* active, int* mean_on, int* zero,
+                               int* iters, double* rho, GroupCtl* ctl, cudaStream_t st);
+cudaError_t launch_group_iter_end(const ResBox* boxes, int nbox, const double* fmax,
                                   const double* tol, const int* maxit, int* active, int* iters,
                                   double* rho, GroupCtl* ctl, cudaGraphConditionalHandle cond,
                                   int set_cond, cudaStream_t st);
 cudaError_t launch_group_zero_max(const ResBox* boxes, int nbox, cudaStream_t st);
 enum {
-  GSTAGE_PLANE_SUM = 0,
   GSTAGE_MEAN_FINAL = 1,
   GSTAGE_RESIDUAL = 2,
   GSTAGE_SUBTRACT = 3,
   GSTAGE_HELM_RESIDUAL = 4,  // flag = mode of helm_residual_kernel
   GSTAGE_UPDATE = 5,         // r -= L delta (double-float), r32b and max
   GSTAGE_ZERO = 6,           // zero solution (boxes with a zero right-hand side)
-  GSTAGE_START = 7,          // r_0 = f - mean as FP32 and its norm (sub-block partition)
+  GSTAGE_START = 7,          // r_0 = f as FP32, its extremes, plane sums (plane x chunk blocks)
   GSTAGE_MEAN_ACC = 8,       // running weighted sum of the solution += the correction's
   GSTAGE_MEAN_FROM_NUM = 9   // the solution's weighted mean from the running sum
 };

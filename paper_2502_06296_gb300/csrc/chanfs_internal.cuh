@@ -95,6 +95,14 @@ struct Helm3Coef {
   unsigned long long stamp;
 };
 
+// Chunks per z plane of the refined Poisson start pass (refine.cu): about
+// 2432 blocks (16 per SM) over the nz planes, at most kMaxStartChunks.
+constexpr int kMaxStartChunks = 16;
+inline __host__ __device__ int start_chunks(int nz) {
+  const int c = (2432 + nz - 1) / nz;
+  return c < 1 ? 1 : (c > kMaxStartChunks ? kMaxStartChunks : c);
+}
+
 }  // namespace chanfs
 
 // ----------------------------------------------------------------------------
@@ -152,7 +160,9 @@ struct cfs_plan {
                      // (1/dx^2, 1/dy^2).  D_k = A_k + B'_k + C_k + 2/dx^2 + 2/dy^2 (exact sum)
   double* d_mpart;   // per-block dz-weighted sums of a correction (residual grid blocks)
   double inv_wn;     // 1 / (sum of the cell widths * Nx * Ny)
-  double* d_red;     // reduction scratch: [0] max |r| (float bits), [1] mean, [2..] partials
+  double* d_red;     // reduction scratch: [0] two 32-bit words (max |r| as float bits; the
+                     // start pass's extreme keys), [1] mean, [2] running weighted sum of
+                     // the solution, [3..) nz * start_chunks(nz) plane partials
   double tol;        // relative residual target
   int maxit;         // at most this many corrections
   int last_iters;

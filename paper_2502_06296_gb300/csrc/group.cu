@@ -98,7 +98,7 @@ struct cfs_group {
   int* d_zero = nullptr;    // boxes with a zero right-hand side (zero solution)
   int* d_elig = nullptr;    // Helmholtz: boxes that are refined (the others solve in FP64)
   GroupCtl* d_ctl = nullptr;
-  float* d_fmax = nullptr;
+  double* d_fmax = nullptr;
   double* d_tol = nullptr;
   int* d_maxit = nullptr;
   int* d_iters = nullptr;
@@ -224,7 +224,7 @@ static int group_alloc(cfs_group* G, int cap) {
   if (e == cudaSuccess) e = cudaMallocHost(&G->h_tab, G->tab.bytes);
   if (e == cudaSuccess) e = cudaMalloc(&G->d_active, sizeof(int) * cap);
   if (e == cudaSuccess) e = cudaMalloc(&G->d_mean, sizeof(int) * cap);
-  if (e == cudaSuccess) e = cudaMalloc(&G->d_fmax, sizeof(float) * cap);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_fmax, sizeof(double) * cap);
   if (e == cudaSuccess) e = cudaMalloc(&G->d_tol, sizeof(double) * cap);
   if (e == cudaSuccess) e = cudaMalloc(&G->d_maxit, sizeof(int) * cap);
   if (e == cudaSuccess) e = cudaMalloc(&G->d_iters, sizeof(int) * cap);
@@ -318,7 +318,7 @@ static int group_bind(cfs_group* G, int nplans, const cfs_plan_t* plans, cudaStr
     ResBox& r = res[b];
     memset(&r, 0, sizeof(r));
     r.dzf = P->d_dzf;
-    r.partial = P->d_red + 2;
+    r.partial = P->d_red + 3;
     r.mean = P->d_red + 1;
     r.r32 = P->d_r32;
     r.r32b = P->d_r32b;
@@ -333,11 +333,11 @@ static int group_bind(cfs_group* G, int nplans, const cfs_plan_t* plans, cudaStr
     r.neumann = P->has_null;
     r.ybc = P->ybc;
     r.mpart = P->d_mpart;
-    r.mnum = P->d_red + 2 + P->nz;  // after the plane partials
+    r.mnum = P->d_red + 2;
     r.inv_wn = P->inv_wn;
     G->res[b] = r;
     bres[b] = (int)((nxy + 127) / 128);
-    bplane[b] = P->nz;
+    bplane[b] = P->nz * start_chunks(P->nz);
     bsub[b] = (int)group_sub_blocks(nxy * P->nz);
   }
   auto put = [&](size_t at, const std::vector<int>& v) {
@@ -497,27 +497,25 @@ cudaError_t build_graph(cfs_group* G, Head head, Body body, Tail tail, cudaGraph
 
 // ---- Poisson: stages of one grouped solve --------------------------------
 
-// Copies of the call's pointers and settings, the dz-weighted mean of f
-// (Neumann boxes), r_0 = f - mean with its norm, the start state, and the
+// Copies of the call's pointers and settings, the start pass (r_0 = f as
+// FP32, its extremes, the plane sums of Neumann boxes), the dz-weighted mean
+// of f (Neumann boxes), the reference norms and the start state, and the
 // zero solution of boxes whose right-hand side is zero.
 cudaError_t poisson_head(cfs_group* G, cudaStream_t st) {
   const int nb = G->nbox;
   cudaError_t e = cudaMemcpyAsync(G->d_io, G->h_io, sizeof(GroupIo) * nb, kH2D, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(G->d_tol, G->h_tol, sizeof(double) * nb, kH2D, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(G->d_maxit, G->h_maxit, sizeof(int) * nb, kH2D, st);
-  GroupMap g{G->d_splane, G->d_neumann, nb};
+  if (e == cudaSuccess) e = launch_group_zero_max(G->d_res, nb, st);
+  GroupMap g{G->d_splane, nullptr, nb};
   if (e == cudaSuccess)
-    e = launch_group_refine_stage(GSTAGE_PLANE_SUM, G->d_res, g, G->tplane, G->d_io, 0, st);
-  g.start = G->d_sone;
+    e = launch_group_refine_stage(GSTAGE_START, G->d_res, g, G->tplane, G->d_io, 0, st);
+  g = GroupMap{G->d_sone, G->d_neumann, nb};
   if (e == cudaSuccess)
     e = launch_group_refine_stage(GSTAGE_MEAN_FINAL, G->d_res, g, G->tone, G->d_io, 0, st);
-  if (e == cudaSuccess) e = launch_group_zero_max(G->d_res, nb, st);
-  g = GroupMap{G->d_ssub, nullptr, nb};
   if (e == cudaSuccess)
-    e = launch_group_refine_stage(GSTAGE_START, G->d_res, g, G->tsub, G->d_io, 0, st);
-  if (e == cudaSuccess)
-    e = launch_group_start(G->d_res, nb, G->d_fmax, nullptr, G->d_active, G->d_mean, G->d_zero,
-                           G->d_iters, G->d_rho, G->d_ctl, st);
+    e = launch_group_start(G->d_res, nb, 1, G->d_fmax, nullptr, G->d_active, G->d_mean,
+                           G->d_zero, G->d_iters, G->d_rho, G->d_ctl, st);
   g = GroupMap{G->d_ssub, G->d_zero, nb};
   if (e == cudaSuccess)
     e = launch_group_refine_stage(GSTAGE_ZERO, G->d_res, g, G->tsub, G->d_io, 0, st);
@@ -764,7 +762,7 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
     if (r == cudaSuccess)
       r = launch_group_refine_stage(GSTAGE_HELM_RESIDUAL, G->d_hres, g, G->tres, G->d_io, 0, s);
     if (r == cudaSuccess)
-      r = launch_group_start(G->d_hres, nb, G->d_fmax, G->d_elig, G->d_active, nullptr,
+      r = launch_group_start(G->d_hres, nb, 0, G->d_fmax, G->d_elig, G->d_active, nullptr,
                              G->d_zero, G->d_iters, G->d_rho, G->d_ctl, s);
     g = GroupMap{G->d_ssub, G->d_zero, nb};
     if (r == cudaSuccess)

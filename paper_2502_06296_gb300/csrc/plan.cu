@@ -387,7 +387,9 @@ extern "C" int cfs_plan_create_walls(cfs_plan_t* out, int nx, int ny, int nz, do
     if (!rc) rc = dev_upload<float2>(&P->d_fwd32, nullptr, nfac, &P->device_bytes);
     if (!rc) rc = dev_upload<float>(&P->d_bwd32, nullptr, nfac, &P->device_bytes);
     if (!rc) rc = dev_upload<float>(&P->d_r32, nullptr, (size_t)nx * ny * nz, &P->device_bytes);
-    if (!rc) rc = dev_upload<double>(&P->d_red, nullptr, (size_t)nz + 8, &P->device_bytes);
+    if (!rc)
+      rc = dev_upload<double>(&P->d_red, nullptr, (size_t)nz * start_chunks(nz) + 8,
+                              &P->device_bytes);
     // The residual kernels' coefficients, each split as hi = fl32(v),
     // lo = fl32(v - hi), packed per plane (three float4: (A, C), (B', dz),
     // (D, dz)) and then (1/dx^2, 1/dy^2).  D_k = A_k + B'_k + C_k + 2/dx^2 +

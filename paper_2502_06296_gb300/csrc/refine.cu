@@ -79,55 +79,114 @@ __device__ __forceinline__ void df_acc(DoubleFloat& acc, float chi, float clo, f
   }
 }
 
-// Neumann compatibility: the dz-weighted mean of f, reduced in a fixed order
-// (one block per z plane, then one block over the planes) so that results
-// are bit-reproducible.
-// Each thread sums a strided part of the plane with 16-byte loads, eight
-// values in flight and four accumulators (a plane is an even number of
-// values: nx is even), then the block reduces in a fixed tree.
-__device__ __forceinline__ void plane_sum_body(const double* __restrict__ f, long long nxy,
-                                               const double* dzf, double* partial, int k) {
+// ----------------------------------------------------------------------------
+// Start of a refined Poisson solve, one pass over f: r_0 = f as FP32 (the
+// right-hand side of the first FP32 solve), the dz-weighted plane sums of f
+// for the Neumann compatibility mean (partial may be null), and the largest
+// and smallest r_0 (the reference norm max |f - mean| follows from them and
+// the mean).  The first solve does not need f - mean: its (0, 0) column
+// removes the mean of its right-hand side, as the FP64 solve's does.
+// Block b takes chunk b % nch of plane b / nch (16-byte loads, four
+// accumulators), and the sums are reduced in a fixed order (per block, then
+// per plane, then over the planes), so results are bit-reproducible.
+// ----------------------------------------------------------------------------
+// Order-preserving key of a float (larger float, larger key; 0 below all).
+__device__ __forceinline__ unsigned int float_key(float v) {
+  const unsigned int u = __float_as_uint(v);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__host__ __device__ inline float key_float(unsigned int k) {
+  const unsigned int u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+  float v;
+  memcpy(&v, &u, sizeof(v));
+  return v;
+}
+
+// words[0] = max key(r), words[1] = max key(-r) over the block (atomics).
+__device__ __forceinline__ void block_extremes_to(float hi, float lo, unsigned int* words) {
+  unsigned int a = float_key(hi), b = float_key(-lo);
+  for (int o = 16; o > 0; o >>= 1) {
+    a = max(a, __shfl_down_sync(0xffffffffu, a, o));
+    b = max(b, __shfl_down_sync(0xffffffffu, b, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(words, a);
+    atomicMax(words + 1, b);
+  }
+}
+
+__device__ __forceinline__ void start_body(const double* __restrict__ f, long long nxy,
+                                           const double* __restrict__ dzf, double* partial,
+                                           float* __restrict__ r32, unsigned int* words,
+                                           long long blk, int nch) {
   __shared__ double sh[256];
-  const double2* plane = reinterpret_cast<const double2*>(f + (long long)k * nxy);
-  const long long n2 = nxy >> 1;
+  const int k = (int)(blk / nch), c = (int)(blk % nch);
+  const long long n2 = nxy >> 1;  // nx is even
+  const long long lo = n2 * c / nch, hi = n2 * (c + 1) / nch;
+  const double2* f2 = reinterpret_cast<const double2*>(f + (long long)k * nxy);
+  float2* r2 = reinterpret_cast<float2*>(r32 + (long long)k * nxy);
   const long long B = blockDim.x;
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  long long i = threadIdx.x;
-  for (; i + 3 * B < n2; i += 4 * B) {
-    const double2 a = plane[i], b = plane[i + B], c = plane[i + 2 * B], d = plane[i + 3 * B];
-    s0 += a.x + c.x;
-    s1 += a.y + c.y;
-    s2 += b.x + d.x;
-    s3 += b.y + d.y;
+  float vmax = -INFINITY, vmin = INFINITY;
+  long long i = lo + threadIdx.x;
+  for (; i + 3 * B < hi; i += 4 * B) {
+    const double2 v0 = f2[i], v1 = f2[i + B], v2 = f2[i + 2 * B], v3 = f2[i + 3 * B];
+    const float2 a = make_float2(f64_to_f32(v0.x), f64_to_f32(v0.y));
+    const float2 b = make_float2(f64_to_f32(v1.x), f64_to_f32(v1.y));
+    const float2 cc = make_float2(f64_to_f32(v2.x), f64_to_f32(v2.y));
+    const float2 d = make_float2(f64_to_f32(v3.x), f64_to_f32(v3.y));
+    r2[i] = a;
+    r2[i + B] = b;
+    r2[i + 2 * B] = cc;
+    r2[i + 3 * B] = d;
+    vmax = fmaxf(fmaxf(fmaxf(vmax, fmaxf(a.x, a.y)), fmaxf(b.x, b.y)),
+                 fmaxf(fmaxf(cc.x, cc.y), fmaxf(d.x, d.y)));
+    vmin = fminf(fminf(fminf(vmin, fminf(a.x, a.y)), fminf(b.x, b.y)),
+                 fminf(fminf(cc.x, cc.y), fminf(d.x, d.y)));
+    if (partial) {
+      s0 += v0.x + v2.x;
+      s1 += v0.y + v2.y;
+      s2 += v1.x + v3.x;
+      s3 += v1.y + v3.y;
+    }
   }
-  for (; i < n2; i += B) {
-    const double2 a = plane[i];
-    s0 += a.x;
-    s1 += a.y;
+  for (; i < hi; i += B) {
+    const double2 v = f2[i];
+    const float2 a = make_float2(f64_to_f32(v.x), f64_to_f32(v.y));
+    r2[i] = a;
+    vmax = fmaxf(vmax, fmaxf(a.x, a.y));
+    vmin = fminf(vmin, fminf(a.x, a.y));
+    if (partial) {
+      s0 += v.x;
+      s1 += v.y;
+    }
   }
-  const double s = (s0 + s1) + (s2 + s3);
-  sh[threadIdx.x] = s;
+  block_extremes_to(vmax, vmin, words);
+  if (!partial) return;
+  sh[threadIdx.x] = (s0 + s1) + (s2 + s3);
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
     if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) partial[k] = dzf[k] * sh[0];
+  if (threadIdx.x == 0) partial[blk] = dzf[k] * sh[0];
 }
 
-__global__ void plane_sum_kernel(const double* __restrict__ f, long long nxy, const double* dzf,
-                                 double* partial) {
-  plane_sum_body(f, nxy, dzf, partial, blockIdx.x);
+__global__ void __launch_bounds__(256) start_kernel(const double* __restrict__ f, long long nxy,
+                                                    const double* __restrict__ dzf,
+                                                    double* partial, float* __restrict__ r32,
+                                                    unsigned int* words, int nch) {
+  start_body(f, nxy, dzf, partial, r32, words, blockIdx.x, nch);
 }
 
-__device__ __forceinline__ void mean_final_body(const double* partial, int nz, const double* dzf,
-                                                long long nxy, double* mean) {
+// mean = (sum of the nz * nch partials) / (sum_k dz_k * Nx * Ny), fixed order.
+__device__ __forceinline__ void mean_final_body(const double* partial, int nz, int nch,
+                                                const double* dzf, long long nxy, double* mean) {
   __shared__ double sh[256], shw[256];
   double s = 0.0, w = 0.0;
-  for (int k = threadIdx.x; k < nz; k += blockDim.x) {
-    s += partial[k];
-    w += dzf[k];
-  }
+  for (int i = threadIdx.x; i < nz * nch; i += blockDim.x) s += partial[i];
+  for (int k = threadIdx.x; k < nz; k += blockDim.x) w += dzf[k];
   sh[threadIdx.x] = s;
   shw[threadIdx.x] = w;
   __syncthreads();
@@ -141,9 +200,17 @@ __device__ __forceinline__ void mean_final_body(const double* partial, int nz, c
   if (threadIdx.x == 0) *mean = sh[0] / (shw[0] * (double)nxy);
 }
 
-__global__ void mean_final_kernel(const double* partial, int nz, const double* dzf, long long nxy,
-                                  double* mean) {
-  mean_final_body(partial, nz, dzf, nxy, mean);
+__global__ void mean_final_kernel(const double* partial, int nz, int nch, const double* dzf,
+                                  long long nxy, double* mean) {
+  mean_final_body(partial, nz, nch, dzf, nxy, mean);
+}
+
+// The reference norm max |r_0 - mean| from the extremes of r_0 (mean 0
+// without a null space).
+__host__ __device__ inline double start_norm(const unsigned int* words, double mean) {
+  const double hi = (double)key_float(words[0]), lo = -(double)key_float(words[1]);
+  const double a = hi - mean, b = mean - lo;
+  return a > b ? a : b;
 }
 
 // ----------------------------------------------------------------------------
@@ -398,33 +465,6 @@ __global__ void mean_from_num_kernel(const double* num, double inv, double* mean
   if (threadIdx.x == 0) *mean = *num * inv;
 }
 
-// r_0 = f - mean (mean may be null: r_0 = f) as FP32, and max |r_0|: a flat
-// pass over the n points (n even) with 16-byte loads, blocks striding by
-// nblk (the same partition in the single and the grouped launch).
-__device__ __forceinline__ void rhs_start_body(const double* __restrict__ f,
-                                               const double* __restrict__ mean,
-                                               float* __restrict__ r32, unsigned int* rmax,
-                                               long long n, long long blk, long long nblk) {
-  const double mu = mean ? *mean : 0.0;
-  const double2* f2 = reinterpret_cast<const double2*>(f);
-  float2* r2 = reinterpret_cast<float2*>(r32);
-  float vmax = 0.0f;
-  for (long long i = blk * blockDim.x + threadIdx.x; i < (n >> 1); i += nblk * blockDim.x) {
-    const double2 v = f2[i];
-    const float2 r = make_float2(f64_to_f32(v.x - mu), f64_to_f32(v.y - mu));
-    r2[i] = r;
-    vmax = fmaxf(vmax, fmaxf(fabsf(r.x), fabsf(r.y)));
-  }
-  block_max_to(vmax, rmax);
-}
-
-__global__ void __launch_bounds__(256) rhs_start_kernel(const double* __restrict__ f,
-                                                        const double* __restrict__ mean,
-                                                        float* __restrict__ r32,
-                                                        unsigned int* rmax, long long n) {
-  rhs_start_body(f, mean, r32, rmax, n, blockIdx.x, gridDim.x);
-}
-
 // Helmholtz: u (+)= delta, then r = rhs - (I - c L_z) u, as FP32, and max |r|.
 // mode 0: u is not read (r = rhs); 1: u = delta; 2: u += delta.  delta is read
 // from r32 and overwritten by the new residual.  One thread per column,
@@ -501,20 +541,21 @@ __global__ void subtract_mean_kernel(double* __restrict__ p, long long n,
 // per-box arithmetic and block partition as the single-plan kernels).
 // ----------------------------------------------------------------------------
 
-__global__ void plane_sum_group_kernel(const ResBox* boxes, GroupMap g, const GroupIo* io,
-                                       int of_solution) {
+// Start pass: nz * start_chunks(nz) blocks per box.
+__global__ void __launch_bounds__(256) start_group_kernel(const ResBox* boxes, GroupMap g,
+                                                          const GroupIo* io) {
   int b, blk;
   if (!group_block(g, &b, &blk)) return;
   const ResBox& r = boxes[b];
-  const double* src = of_solution ? io[b].p : io[b].f;
-  plane_sum_body(src, (long long)r.nx * r.ny, r.dzf, r.partial, blk);
+  start_body(io[b].f, (long long)r.nx * r.ny, r.dzf, r.neumann ? r.partial : nullptr, r.r32,
+             r.rmax, blk, start_chunks(r.nz));
 }
 
 __global__ void mean_final_group_kernel(const ResBox* boxes, GroupMap g) {
   int b, blk;
   if (!group_block(g, &b, &blk)) return;
   const ResBox& r = boxes[b];
-  mean_final_body(r.partial, r.nz, r.dzf, (long long)r.nx * r.ny, r.mean);
+  mean_final_body(r.partial, r.nz, start_chunks(r.nz), r.dzf, (long long)r.nx * r.ny, r.mean);
 }
 
 __global__ void __launch_bounds__(kResBlock) poisson_first_group_kernel(const ResBox* boxes,
@@ -548,16 +589,6 @@ __global__ void mean_from_num_group_kernel(const ResBox* boxes, GroupMap g) {
   if (!group_block(g, &b, &blk)) return;
   const ResBox& r = boxes[b];
   if (threadIdx.x == 0) *r.mean = *r.mnum * r.inv_wn;
-}
-
-__global__ void __launch_bounds__(256) rhs_start_group_kernel(const ResBox* boxes, GroupMap g,
-                                                              const GroupIo* io) {
-  int b, blk;
-  if (!group_block(g, &b, &blk)) return;
-  const ResBox& r = boxes[b];
-  const long long n = (long long)r.nx * r.ny * r.nz;
-  rhs_start_body(io[b].f, r.neumann ? r.mean : nullptr, r.r32, r.rmax, n, blk,
-                 group_sub_blocks(n));
 }
 
 __global__ void __launch_bounds__(kResBlock) helm_residual_group_kernel(const ResBox* boxes,
@@ -604,12 +635,14 @@ __global__ void zero_fill_group_kernel(const ResBox* boxes, GroupMap g, const Gr
   for (long long i = blk * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) p[i] = 0.0;
 }
 
-// After the first residual r_0 = f (- mean): each box's reference norm
-// max|r_0| and its starting state.  A box iterates if it is eligible (null:
-// every box) and r_0 is not zero; an eligible box with r_0 = 0 has the zero
+// After the start: each box's reference norm and its starting state.  keys:
+// the Poisson start pass left the extreme keys of r_0 = f (the norm is
+// max |f - mean|, the mean of Neumann boxes); otherwise the norm word holds
+// max |r_0| (Helmholtz).  A box iterates if it is eligible (null: every box)
+// and the norm is not zero; an eligible box with a zero norm has the zero
 // solution (zero[b]).  mean_on (may be null) marks the iterating boxes whose
 // solution mean is removed at the end.  Every box starts at 0 iterations.
-__global__ void group_start_kernel(const ResBox* boxes, int nbox, float* fmax,
+__global__ void group_start_kernel(const ResBox* boxes, int nbox, int keys, double* fmax,
                                    const int* eligible, int* active, int* mean_on, int* zero,
                                    int* iters, double* rho, GroupCtl* ctl) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -619,11 +652,12 @@ __global__ void group_start_kernel(const ResBox* boxes, int nbox, float* fmax,
   }
   if (b >= nbox) return;
   unsigned int* w = boxes[b].rmax;
-  const float f = __uint_as_float(*w);
-  *w = 0u;
+  const double f = keys ? start_norm(w, boxes[b].neumann ? *boxes[b].mean : 0.0)
+                        : (double)__uint_as_float(w[0]);
+  w[0] = 0u;
   fmax[b] = f;
   const int elig = eligible ? eligible[b] : 1;
-  const int on = elig && f != 0.0f;
+  const int on = elig && f != 0.0;
   active[b] = on;
   if (mean_on) mean_on[b] = on && boxes[b].neumann;
   if (boxes[b].mnum) *boxes[b].mnum = 0.0;
@@ -638,7 +672,7 @@ __global__ void group_start_kernel(const ResBox* boxes, int nbox, float* fmax,
 // iterating, ctl->it advances, and inside a graph the loop's condition is
 // set to (nactive > 0).
 __global__ void __launch_bounds__(1024) group_iter_end_kernel(
-    const ResBox* boxes, int nbox, const float* fmax, const double* tol, const int* maxit,
+    const ResBox* boxes, int nbox, const double* fmax, const double* tol, const int* maxit,
     int* active, int* iters, double* rho, GroupCtl* ctl, cudaGraphConditionalHandle cond,
     int set_cond) {
   __shared__ int count;
@@ -651,7 +685,7 @@ __global__ void __launch_bounds__(1024) group_iter_end_kernel(
     unsigned int* w = boxes[b].rmax;
     const float rmax = __uint_as_float(*w);
     *w = 0u;
-    const double r = (double)rmax / (double)fmax[b];
+    const double r = (double)rmax / fmax[b];
     rho[b] = r;
     iters[b] = it + 1;
     if (r <= tol[b] || it + 1 >= maxit[b]) active[b] = 0;
@@ -671,16 +705,16 @@ __global__ void __launch_bounds__(1024) group_iter_end_kernel(
 // holds whatever its last solve, or its allocation, left there).
 __global__ void group_zero_max_kernel(const ResBox* boxes, int nbox) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b < nbox) *boxes[b].rmax = 0u;
+  if (b < nbox) {  // the norm word and the start pass's second key
+    boxes[b].rmax[0] = 0u;
+    boxes[b].rmax[1] = 0u;
+  }
 }
 
 cudaError_t launch_group_refine_stage(int stage, const ResBox* boxes, GroupMap g, int total,
                                       const GroupIo* io, int flag, cudaStream_t st) {
   if (total <= 0) return cudaSuccess;
   switch (stage) {
-    case GSTAGE_PLANE_SUM:
-      plane_sum_group_kernel<<<total, 256, 0, st>>>(boxes, g, io, flag);
-      break;
     case GSTAGE_MEAN_FINAL:
       mean_final_group_kernel<<<total, 256, 0, st>>>(boxes, g);
       break;
@@ -697,7 +731,7 @@ cudaError_t launch_group_refine_stage(int stage, const ResBox* boxes, GroupMap g
       zero_fill_group_kernel<<<total, 256, 0, st>>>(boxes, g, io);
       break;
     case GSTAGE_START:
-      rhs_start_group_kernel<<<total, 256, 0, st>>>(boxes, g, io);
+      start_group_kernel<<<total, 256, 0, st>>>(boxes, g, io);
       break;
     case GSTAGE_MEAN_ACC:
       mean_acc_group_kernel<<<total, 256, 0, st>>>(boxes, g);
@@ -712,15 +746,15 @@ cudaError_t launch_group_refine_stage(int stage, const ResBox* boxes, GroupMap g
   return cudaGetLastError();
 }
 
-cudaError_t launch_group_start(const ResBox* boxes, int nbox, float* fmax, const int* eligible,
-                               int* active, int* mean_on, int* zero, int* iters, double* rho,
-                               GroupCtl* ctl, cudaStream_t st) {
-  group_start_kernel<<<(nbox + 127) / 128, 128, 0, st>>>(boxes, nbox, fmax, eligible, active,
-                                                         mean_on, zero, iters, rho, ctl);
+cudaError_t launch_group_start(const ResBox* boxes, int nbox, int keys, double* fmax,
+                               const int* eligible, int* active, int* mean_on, int* zero,
+                               int* iters, double* rho, GroupCtl* ctl, cudaStream_t st) {
+  group_start_kernel<<<(nbox + 127) / 128, 128, 0, st>>>(boxes, nbox, keys, fmax, eligible,
+                                                         active, mean_on, zero, iters, rho, ctl);
   return cudaGetLastError();
 }
 
-cudaError_t launch_group_iter_end(const ResBox* boxes, int nbox, const float* fmax,
+cudaError_t launch_group_iter_end(const ResBox* boxes, int nbox, const double* fmax,
                                   const double* tol, const int* maxit, int* active, int* iters,
                                   double* rho, GroupCtl* ctl, cudaGraphConditionalHandle cond,
                                   int set_cond, cudaStream_t st) {
@@ -810,36 +844,41 @@ static int read_max(cfs_plan* P, cudaStream_t st, float* out) {
 static unsigned int* max_word(cfs_plan* P) { return reinterpret_cast<unsigned int*>(P->d_red); }
 
 // The running dz-weighted sum of the solution (after the plane partials).
-static double* mean_num(cfs_plan* P) { return P->d_red + 2 + P->nz; }
+static double* mean_num(cfs_plan* P) { return P->d_red + 2; }
 
 int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st) {
   const long long nxy = (long long)P->nx * P->ny;
   const unsigned grid = (unsigned)((nxy + kResBlock - 1) / kResBlock);
   const bool idx32 = res_idx32(P->nx, P->ny, P->nz);
   double* mean = nullptr;
-  cudaError_t e = cudaSuccess;
-  if (P->has_null) {  // remove the dz-weighted mean of f (compatibility)
+  // one pass over f: r_0 = f as FP32, the extremes of r_0 and (Neumann) the
+  // plane sums of the compatibility mean; then the reference norm
+  // ||f - mean||_inf from the extremes and the mean
+  const int nch = start_chunks(P->nz);
+  cudaError_t e = cudaMemsetAsync(P->d_red, 0, 2 * sizeof(unsigned int), st);
+  if (e == cudaSuccess) {
+    start_kernel<<<(unsigned)(P->nz * nch), 256, 0, st>>>(
+        f, nxy, P->d_dzf, P->has_null ? P->d_red + 3 : nullptr, P->d_r32, max_word(P), nch);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && P->has_null) {  // the dz-weighted mean of f (compatibility)
     mean = P->d_red + 1;
-    plane_sum_kernel<<<P->nz, 256, 0, st>>>(f, nxy, P->d_dzf, P->d_red + 2);
-    mean_final_kernel<<<1, 256, 0, st>>>(P->d_red + 2, P->nz, P->d_dzf, nxy, mean);
+    mean_final_kernel<<<1, 256, 0, st>>>(P->d_red + 3, P->nz, nch, P->d_dzf, nxy, mean);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemsetAsync(mean_num(P), 0, sizeof(double), st);
   }
-  // r_0 = f - mean and the reference norm ||f - mean||_inf
-  if (e == cudaSuccess) e = cudaMemsetAsync(P->d_red, 0, sizeof(unsigned int), st);
-  if (e == cudaSuccess) {
-    const long long n = nxy * P->nz;
-    rhs_start_kernel<<<(unsigned)group_sub_blocks(n), 256, 0, st>>>(f, mean, P->d_r32,
-                                                                   max_word(P), n);
-    e = cudaGetLastError();
-  }
-  float fmax = 0.0f;
+  double head[2] = {0.0, 0.0};  // the key words, the mean
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(head, P->d_red, sizeof(head), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   int rc = cuda_rc(e);
-  if (!rc) rc = read_max(P, st, &fmax);
   if (rc) return rc;
+  unsigned int keys[2];
+  memcpy(keys, &head[0], sizeof(keys));
+  const double fmax = start_norm(keys, P->has_null ? head[1] : 0.0);
   P->last_iters = 0;
   P->last_rho = 0.0;
-  if (fmax == 0.0f) {  // zero right-hand side: zero solution
+  if (fmax == 0.0) {  // zero right-hand side: zero solution
     return cuda_rc(cudaMemsetAsync(p, 0, sizeof(double) * (size_t)nxy * P->nz, st));
   }
   for (int it = 0; it < P->maxit; ++it) {
