@@ -40,6 +40,8 @@ struct XBox {  // packed real FFT along x (fft_x.cu)
   long long nlines;
   int lb;
   int* status;
+  const double* msum;  // inverse, correction pass: the solution's weighted sum (may be null)
+  double minv;         // 1 / (sum of the cell widths * Nx * Ny)
 };
 
 struct YBox {  // FFT along y on TMA tiles (fft_y.cu); the map is 64-byte aligned
@@ -182,9 +184,9 @@ cudaError_t launch_group_start(const ResBox* boxes, int nbox, int keys, double* 
                                const int* eligible, int* active, int* mean_on, int* zero,
                                int* iters, double* rho, GroupCtl* ctl, cudaStream_t st);
 cudaError_t launch_group_iter_end(const ResBox* boxes, int nbox, const double* fmax,
-                                  const double* tol, const int* maxit, int* active, int* iters,
-                                  double* rho, GroupCtl* ctl, cudaGraphConditionalHandle cond,
-                                  int set_cond, cudaStream_t st);
+                                  const double* tol, const int* maxit, int* active,
+                                  int* mean_on, int* iters, double* rho, GroupCtl* ctl,
+                                  cudaGraphConditionalHandle cond, int set_cond, cudaStream_t st);
 cudaError_t launch_group_zero_max(const ResBox* boxes, int nbox, cudaStream_t st);
 enum {
   GSTAGE_MEAN_FINAL = 1,

@@ -198,8 +198,9 @@ cudaError_t launch_fft_y(const cfs_plan* P, double* data, bool inverse, cudaStre
 cudaError_t launch_thomas(const cfs_plan* P, double* data, cudaStream_t st);
 cudaError_t launch_rfft_x32(const cfs_plan* P, const float* in, float* out, bool inverse,
                             cudaStream_t st);
+// add: p += delta (less msum * inv_wn when msum is not null), else p = delta
 cudaError_t launch_rfft_x32_to64(const cfs_plan* P, const float* in, double* out, bool add,
-                                 cudaStream_t st);
+                                 cudaStream_t st, const double* msum = nullptr);
 cudaError_t launch_fft_y32(const cfs_plan* P, float* data, bool inverse, cudaStream_t st);
 cudaError_t launch_thomas32(const cfs_plan* P, float* data, cudaStream_t st);
 // x-lines per CTA of the x transforms of complex element size csize.

@@ -30,7 +30,8 @@ template <bool INV, class C, int OUT>
 __device__ __forceinline__ void rfft_x_body(const C* in, void* outv, long long nlines,
                                             const FftDesc& d, const C* __restrict__ twg,
                                             const C* __restrict__ postg, int lb, double scale,
-                                            int scaled, int* status, long long blk) {
+                                            int scaled, int* status, long long blk,
+                                            const double* msum = nullptr, double minv = 0.0) {
   using T = typename cscal<C>::T;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int M = d.n;
@@ -149,6 +150,17 @@ __device__ __forceinline__ void rfft_x_body(const C* in, void* outv, long long n
         tma_store_commit_and_wait_read();
       }
     } else {
+      if (OUT == OUT_ADD && msum) {
+        // the correction less the solution's current weighted mean (msum *
+        // minv), so that p keeps a zero mean without a pass of its own; the
+        // correction stored for the residual update is this one
+        const T m = T(*msum * minv);
+        for (int e = threadIdx.x; e < valid * M; e += blockDim.x) {
+          res[e].x -= m;
+          res[e].y -= m;
+        }
+        __syncthreads();
+      }
       {  // the correction also stays behind (FP32, in place) for the residual kernels
         fence_proxy_async();
         __syncthreads();
@@ -176,9 +188,10 @@ template <bool INV, class C, int OUT>
 __global__ void __launch_bounds__(128) rfft_x_kernel(const C* in, void* outv, long long nlines,
                                                      FftDesc d, const C* __restrict__ twg,
                                                      const C* __restrict__ postg, int lb,
-                                                     double scale, int scaled, int* status) {
+                                                     double scale, int scaled, int* status,
+                                                     const double* msum, double minv) {
   rfft_x_body<INV, C, OUT>(in, outv, nlines, d, twg, postg, lb, scale, scaled, status,
-                           blockIdx.x);
+                           blockIdx.x, msum, minv);
 }
 
 // One launch for several boxes (FP32 inner solves of grouped refinement):
@@ -193,7 +206,8 @@ __global__ void __launch_bounds__(128) rfft_x_group_kernel(const XBox* boxes, Gr
   const float2* in = static_cast<const float2*>(alt_in ? x.in2 : x.in);
   rfft_x_body<INV, float2, OUT>(in, out, x.nlines, x.d,
                                 static_cast<const float2*>(x.tw),
-                                static_cast<const float2*>(x.post), x.lb, 1.0, 0, x.status, blk);
+                                static_cast<const float2*>(x.post), x.lb, 1.0, 0, x.status, blk,
+                                x.msum, x.minv);
 }
 
 int x_lines_per_cta(const cfs_plan* P, size_t csize) {
@@ -209,7 +223,8 @@ size_t x_smem_bytes(const cfs_plan* P, int lines, size_t csize) {
 
 template <class C, int OUT>
 static cudaError_t launch_x(const cfs_plan* P, const void* in, void* out, bool inverse,
-                            double scale, const C* tw, const C* post, cudaStream_t st) {
+                            double scale, const C* tw, const C* post, cudaStream_t st,
+                            const double* msum = nullptr) {
   const long long nlines = (long long)P->ny * P->nz;
   const int lb = x_lines_per_cta(P, sizeof(C));
   const long long grid = (nlines + lb - 1) / lb;
@@ -220,12 +235,12 @@ static cudaError_t launch_x(const cfs_plan* P, const void* in, void* out, bool i
     auto k = rfft_x_kernel<false, C, OUT_SAME>;
     allow_max_smem(k);
     k<<<(unsigned)grid, 128, smem, st>>>(cin, out, nlines, P->fx, tw, post, lb, scale, scaled,
-                                         P->d_status);
+                                         P->d_status, nullptr, 0.0);
   } else {
     auto k = rfft_x_kernel<true, C, OUT>;
     allow_max_smem(k);
     k<<<(unsigned)grid, 128, smem, st>>>(cin, out, nlines, P->fx, tw, post, lb, scale, scaled,
-                                         P->d_status);
+                                         P->d_status, msum, P->inv_wn);
   }
   return cudaGetLastError();
 }
@@ -241,8 +256,9 @@ cudaError_t launch_rfft_x32(const cfs_plan* P, const float* in, float* out, bool
 }
 
 cudaError_t launch_rfft_x32_to64(const cfs_plan* P, const float* in, double* out, bool add,
-                                 cudaStream_t st) {
-  if (add) return launch_x<float2, OUT_ADD>(P, in, out, true, 1.0, P->d_twx32, P->d_post32, st);
+                                 cudaStream_t st, const double* msum) {
+  if (add)
+    return launch_x<float2, OUT_ADD>(P, in, out, true, 1.0, P->d_twx32, P->d_post32, st, msum);
   return launch_x<float2, OUT_SET>(P, in, out, true, 1.0, P->d_twx32, P->d_post32, st);
 }
 
@@ -257,6 +273,10 @@ size_t x_group_box(const cfs_plan* P, bool inverse, XBox* box, int* blocks) {
   box->nlines = (long long)P->ny * P->nz;
   box->lb = lb;
   box->status = P->d_status;
+  // the correction pass of refinement keeps the solution's mean at zero
+  // (Neumann plans: the running weighted sum of p, see refine.cu)
+  box->msum = (inverse && P->has_null) ? P->d_red + 2 : nullptr;
+  box->minv = P->inv_wn;
   *blocks = (int)((box->nlines + lb - 1) / lb);
   return x_smem_bytes(P, lb, sizeof(float2));
 }

@@ -560,13 +560,14 @@ cudaError_t poisson_iteration(cfs_group* G, int kind, cudaGraphConditionalHandle
   }
   if (e == cudaSuccess)
     e = launch_group_iter_end(G->d_res, nb, G->d_fmax, G->d_tol, G->d_maxit, G->d_active,
-                              G->d_iters, G->d_rho, G->d_ctl, cond, set_cond, st);
+                              G->d_mean, G->d_iters, G->d_rho, G->d_ctl, cond, set_cond, st);
   return e;
 }
 
-// The zero dz-weighted mean of p restored (Neumann boxes, as the single
-// solve does: the mean from the running weighted sum of the corrections),
-// and the iteration counts and residuals copied out.
+// The zero dz-weighted mean of p restored (Neumann boxes that stopped after
+// one FP32 solve, as the single solve does: the mean from the running
+// weighted sum of the corrections), and the iteration counts and residuals
+// copied out.
 cudaError_t poisson_tail(cfs_group* G, cudaStream_t st) {
   const int nb = G->nbox;
   GroupMap g{G->d_sone, G->d_mean, nb};
@@ -782,7 +783,7 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
       r = launch_group_refine_stage(GSTAGE_HELM_RESIDUAL, G->d_hres, g, G->tres, G->d_io, mode, s);
     if (r == cudaSuccess)
       r = launch_group_iter_end(G->d_hres, nb, G->d_fmax, G->d_tol, G->d_maxit, G->d_active,
-                                G->d_iters, G->d_rho, G->d_ctl, cond, set_cond, s);
+                                nullptr, G->d_iters, G->d_rho, G->d_ctl, cond, set_cond, s);
     return r;
   };
   auto tail = [&](cudaStream_t s) {

@@ -670,11 +670,13 @@ __global__ void group_start_kernel(const ResBox* boxes, int nbox, int keys, doub
 // residual and leaves the iteration once it meets its tolerance or has used
 // its FP32 solves.  One block; ctl->nactive counts the boxes still
 // iterating, ctl->it advances, and inside a graph the loop's condition is
-// set to (nactive > 0).
+// set to (nactive > 0).  mean_on (may be null): a box that leaves after
+// more than one FP32 solve needs no final mean removal (its correction
+// passes kept the mean at zero; see refine_poisson).
 __global__ void __launch_bounds__(1024) group_iter_end_kernel(
     const ResBox* boxes, int nbox, const double* fmax, const double* tol, const int* maxit,
-    int* active, int* iters, double* rho, GroupCtl* ctl, cudaGraphConditionalHandle cond,
-    int set_cond) {
+    int* active, int* mean_on, int* iters, double* rho, GroupCtl* ctl,
+    cudaGraphConditionalHandle cond, int set_cond) {
   __shared__ int count;
   if (threadIdx.x == 0) count = 0;
   __syncthreads();
@@ -688,8 +690,12 @@ __global__ void __launch_bounds__(1024) group_iter_end_kernel(
     const double r = (double)rmax / fmax[b];
     rho[b] = r;
     iters[b] = it + 1;
-    if (r <= tol[b] || it + 1 >= maxit[b]) active[b] = 0;
-    else ++mine;
+    if (r <= tol[b] || it + 1 >= maxit[b]) {
+      active[b] = 0;
+      if (mean_on && it >= 1) mean_on[b] = 0;
+    } else {
+      ++mine;
+    }
   }
   if (mine) atomicAdd(&count, mine);
   __syncthreads();
@@ -755,11 +761,11 @@ cudaError_t launch_group_start(const ResBox* boxes, int nbox, int keys, double* 
 }
 
 cudaError_t launch_group_iter_end(const ResBox* boxes, int nbox, const double* fmax,
-                                  const double* tol, const int* maxit, int* active, int* iters,
-                                  double* rho, GroupCtl* ctl, cudaGraphConditionalHandle cond,
-                                  int set_cond, cudaStream_t st) {
-  group_iter_end_kernel<<<1, 1024, 0, st>>>(boxes, nbox, fmax, tol, maxit, active, iters, rho,
-                                            ctl, cond, set_cond);
+                                  const double* tol, const int* maxit, int* active,
+                                  int* mean_on, int* iters, double* rho, GroupCtl* ctl,
+                                  cudaGraphConditionalHandle cond, int set_cond, cudaStream_t st) {
+  group_iter_end_kernel<<<1, 1024, 0, st>>>(boxes, nbox, fmax, tol, maxit, active, mean_on,
+                                            iters, rho, ctl, cond, set_cond);
   return cudaGetLastError();
 }
 
@@ -889,7 +895,8 @@ int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st) {
     if (e == cudaSuccess) e = launch_fft_y32(P, P->d_r32, false, st);
     if (e == cudaSuccess) e = launch_thomas32(P, P->d_r32, st);
     if (e == cudaSuccess) e = launch_fft_y32(P, P->d_r32, true, st);
-    if (e == cudaSuccess) e = launch_rfft_x32_to64(P, P->d_r32, p, it > 0, st);
+    if (e == cudaSuccess)
+      e = launch_rfft_x32_to64(P, P->d_r32, p, it > 0, st, P->has_null ? mean_num(P) : nullptr);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->d_red, 0, sizeof(unsigned int), st);
     // (Neumann: each kernel also sums its correction, dz-weighted, per block)
     double* mpart = P->has_null ? P->d_mpart : nullptr;
@@ -916,13 +923,17 @@ int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st) {
     P->last_rho = (double)rmax / (double)fmax;
     if (P->last_rho <= P->tol) break;
   }
-  if (P->has_null) {
+  if (P->has_null && P->last_iters == 1) {
     // The residual cannot see a constant, so the FP32 rounding of each
-    // correction's mean accumulates unchecked; restore the zero dz-weighted
-    // mean of p.  p is the sum of the corrections (each added in FP64), so
-    // its weighted sum is the sum of theirs, accumulated by the residual
-    // kernels that read every correction (double-float per column, FP64
-    // across columns, in a fixed order).
+    // correction's mean would accumulate unchecked.  p is the sum of the
+    // corrections (each added in FP64), so its dz-weighted sum is the sum of
+    // theirs, accumulated by the residual kernels that read every correction
+    // (double-float per column, FP64 across columns, in a fixed order).  Each
+    // correction pass after the first subtracts the mean so far from its
+    // correction; what is left is the mean of the last correction, at the
+    // FP32 rounding of a correction that is itself small.  A solve that
+    // stopped after its first FP32 solve has the mean of that solve left:
+    // it is removed here.
     mean_from_num_kernel<<<1, 32, 0, st>>>(mean_num(P), P->inv_wn, P->d_red + 1);
     subtract_mean_kernel<<<1216, 256, 0, st>>>(p, nxy * P->nz, P->d_red + 1);
     rc = cuda_rc(cudaGetLastError());

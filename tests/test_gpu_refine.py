@@ -68,6 +68,9 @@ def test_refined_poisson_matches_fp64_oracle(chanfs, dims, beta, bc, dist):
         iters, rho = plan.last_info()
         assert rho <= TOL and 1 <= iters <= 4, (iters, rho)
         assert rel(p, ref) < TOL, rel(p, ref)
+        if bc == 0:  # the solution's zero dz-weighted mean (kept by the correction passes)
+            m = (np.repeat(dz, nx * ny) @ p.ravel()) / (dz.sum() * nx * ny)
+            assert abs(m) <= 1e-13 * np.max(np.abs(p)), m
         # the residual as the oracle computes it
         r = f - oracle.apply_poisson(p, lx, ly, dz, bc)
         if bc == 0:
@@ -78,6 +81,46 @@ def test_refined_poisson_matches_fp64_oracle(chanfs, dims, beta, bc, dist):
         plan.poisson_solve(t, out=t)
         assert np.array_equal(host(t), p)
         assert plan.check() == 0
+
+
+# Right-hand sides that make the first residual's cancellation hard: a field
+# with most of its energy at mid wavenumbers (p is then far from smooth on
+# the grid), on a strongly stretched grid, with both wall conditions.
+HARD = [
+    (0, 2.6, "mid"), (1, 2.6, "mid"), (0, 2.6, "noise"), (1, 0.0, "mid"),
+]
+
+
+@pytest.mark.parametrize("bc,beta,kind", HARD)
+def test_refined_residual_is_evaluated_to_fp64_accuracy(chanfs, bc, beta, kind):
+    """The library's residual norm against the oracle's FP64 residual of the
+    returned solution, at a tolerance ten times below the default."""
+    nx, ny, nz = 64, 48, 96
+    lx, ly = 6.4, 3.2
+    dz = synth.uniform_dz(nz) if beta == 0.0 else synth.tanh_dz(nz, beta)
+    f = synth.normal(77 + bc, (nz, ny, nx))
+    if kind == "mid":  # modes kx = nx/4, ky = ny/4 and a z wave of 12 cells
+        x = np.arange(nx) / nx
+        y = np.arange(ny) / ny
+        zc = np.cumsum(dz) - 0.5 * dz
+        f = f * 1e-3 + (np.sin(2 * np.pi * 16 * x)[None, None, :]
+                        * np.cos(2 * np.pi * 12 * y)[None, :, None]
+                        * np.cos(np.pi * 8 * zc)[:, None, None])
+    if bc == 0:
+        f = synth.remove_weighted_mean(f, dz)
+    tol = 1e-11
+    with chanfs.Plan(nx, ny, nz, lx, ly, dz, bc, chanfs.F32_REFINED) as plan:
+        plan.set_refinement(tol, 8)
+        p = host(plan.poisson_solve(dev(f)))
+        iters, rho = plan.last_info()
+        assert rho <= tol, (iters, rho)
+        r = f - oracle.apply_poisson(p, lx, ly, dz, bc)
+        if bc == 0:
+            r -= (np.repeat(dz, nx * ny) @ r.ravel()) / (dz.sum() * nx * ny)
+        true_rho = np.max(np.abs(r)) / np.max(np.abs(f))
+        assert true_rho < 2 * tol, (true_rho, rho)
+        ref = oracle.poisson_solve(f, lx, ly, dz, bc)
+        assert rel(p, ref) < 10 * tol, rel(p, ref)
 
 
 @pytest.mark.parametrize("tw", [-1, 8, 16])
