@@ -309,10 +309,31 @@ __device__ __forceinline__ bool is_fixed_plan(const FftDesc& d) {
   return d.n == N && d.npass == np && d.radix[0] == r0;
 }
 
-// The Stockham passes of a compile-time length N over `nb` contiguous
-// batches (element stride 1, batch stride N): the same butterflies and
-// twiddles as stockham_smem with every radix, span, stride and offset a
-// constant.  Returns the buffer holding the result.
+// Shared-memory layout of the intermediate passes of stockham_fixed:
+// element e of a batch at e + e/16 (batch stride N + N/16).  In the
+// unpadded layout the writes of the passes with span L < 16 (and the reads
+// that follow) put a warp's 8-byte accesses on a few banks -- 16-way for the
+// first pass's stride-R writes; with one pad element per 16 every such
+// warp access takes the minimum two wavefronts.  The input of the first pass
+// and the output of the last keep the contiguous layout that the bulk copies
+// load and store.
+__host__ __device__ constexpr int fixed_padded(int n) { return n + n / 16; }
+__device__ __forceinline__ int pad16(int e) { return e + (e >> 4); }
+
+// Elements of one x-transform buffer of `lines` lines of m complex points:
+// FP32 buffers have room for the padded layout, rounded to an even count
+// (the next buffer starts on a 16-byte boundary).
+__host__ __device__ inline int xbuf_elems(int lines, int m, bool fp32) {
+  if (!fp32) return lines * m;
+  const int e = lines * fixed_padded(m);
+  return (e + 1) & ~1;
+}
+
+// The Stockham passes of a compile-time length N over `nb` batches (element
+// stride 1; batch stride N in the first pass's input and the last pass's
+// output, fixed_padded(N) between passes): the same butterflies and twiddles
+// as stockham_smem with every radix, span, stride and offset a constant.
+// Returns the buffer holding the result.
 template <bool INV, int N, int P, class C>
 __device__ __forceinline__ C* stockham_fixed(C* a, C* b, int nb, const C* __restrict__ tw) {
   if constexpr (fixed_radix(N, P) == 0) {
@@ -320,15 +341,17 @@ __device__ __forceinline__ C* stockham_fixed(C* a, C* b, int nb, const C* __rest
   } else {
     constexpr int R = fixed_radix(N, P), L = fixed_span(N, P), TO = fixed_twoff(N, P);
     constexpr int Q = N / R;  // butterflies per batch, and the input stride
+    constexpr bool PIN = P > 0, POUT = P + 1 < fixed_npass(N);
+    constexpr int SIN = PIN ? fixed_padded(N) : N, SOUT = POUT ? fixed_padded(N) : N;
     const int total = Q * nb;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
       const int bat = t / Q;
       const int j = t - bat * Q;
-      const C* in = a + bat * N;
-      C* out = b + bat * N;
+      const C* in = a + bat * SIN;
+      C* out = b + bat * SOUT;
       C v[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[r] = in[j + r * Q];
+      for (int r = 0; r < R; ++r) v[r] = in[PIN ? pad16(j + r * Q) : j + r * Q];
       const int k = j % L;
       if constexpr (L > 1) {
         C w[R - 1];
@@ -340,7 +363,7 @@ __device__ __forceinline__ C* stockham_fixed(C* a, C* b, int nb, const C* __rest
       }
       const int o = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) out[o + r * L] = v[r];
+      for (int r = 0; r < R; ++r) out[POUT ? pad16(o + r * L) : o + r * L] = v[r];
     }
     __syncthreads();
     return stockham_fixed<INV, N, P + 1>(b, a, nb, tw);

@@ -38,8 +38,9 @@ __device__ __forceinline__ void rfft_x_body(const C* in, void* outv, long long n
   const int bs = M;  // batch stride (complex)
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
   C* buf0 = reinterpret_cast<C*>(smem_raw + 128);
-  C* buf1 = buf0 + lb * bs;
-  C* tw = buf1 + lb * bs;
+  const int cap = xbuf_elems(lb, M, sizeof(C) == sizeof(float2));  // elements per buffer
+  C* buf1 = buf0 + cap;
+  C* tw = buf1 + cap;
   C* post = tw + d.ntw;
   const int npost = M / 2 + 1;
   const long long line0 = blk * lb;
@@ -218,7 +219,8 @@ int x_lines_per_cta(const cfs_plan* P, size_t csize) {
 }
 
 size_t x_smem_bytes(const cfs_plan* P, int lines, size_t csize) {
-  return 128 + csize * (size_t)(2 * lines * P->M + P->fx.ntw + P->M / 2 + 1);
+  const size_t cap = (size_t)xbuf_elems(lines, P->M, csize == sizeof(float2));
+  return 128 + csize * (2 * cap + (size_t)P->fx.ntw + P->M / 2 + 1);
 }
 
 template <class C, int OUT>
