@@ -371,7 +371,10 @@ __device__ __forceinline__ C* stockham_fixed(C* a, C* b, int nb, const C* __rest
 }
 
 // The same for the y transform's tile: `tk` interleaved columns (element e
-// of column c at e*tk + c), consecutive threads on consecutive columns.
+// of column c at e*tk + c), consecutive threads on consecutive columns.  The
+// intermediate passes use the padded layout (flat index i at i + i/16; see
+// stockham_fixed): for narrow tiles (tk < 16) the first pass's writes were
+// bank conflicts of up to 8 ways.
 template <bool INV, int N, int P, class C>
 __device__ __forceinline__ C* stockham_fixed_cols(C* a, C* b, int tk, const C* __restrict__ tw) {
   if constexpr (fixed_radix(N, P) == 0) {
@@ -379,15 +382,16 @@ __device__ __forceinline__ C* stockham_fixed_cols(C* a, C* b, int tk, const C* _
   } else {
     constexpr int R = fixed_radix(N, P), L = fixed_span(N, P), TO = fixed_twoff(N, P);
     constexpr int Q = N / R;
+    constexpr bool PIN = P > 0, POUT = P + 1 < fixed_npass(N);
     const int total = Q * tk;
     const int sfast = blockDim.x % tk, sslow = blockDim.x / tk;
     int c = threadIdx.x % tk, j = threadIdx.x / tk;  // column (fast), butterfly (slow)
     const int qs = Q * tk, ls = L * tk;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      const C* in = a + j * tk + c;
+      const int i0 = j * tk + c;
       C v[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[r] = in[r * qs];
+      for (int r = 0; r < R; ++r) v[r] = a[PIN ? pad16(i0 + r * qs) : i0 + r * qs];
       const int k = j % L;
       if constexpr (L > 1) {
         C w[R - 1];
@@ -397,9 +401,9 @@ __device__ __forceinline__ C* stockham_fixed_cols(C* a, C* b, int tk, const C* _
       } else {
         dft<R, INV>(v);
       }
-      C* out = b + ((j - k) * R + k) * tk + c;
+      const int o0 = ((j - k) * R + k) * tk + c;
 #pragma unroll
-      for (int r = 0; r < R; ++r) out[r * ls] = v[r];
+      for (int r = 0; r < R; ++r) b[POUT ? pad16(o0 + r * ls) : o0 + r * ls] = v[r];
       c += sfast;
       j += sslow;
       if (c >= tk) {

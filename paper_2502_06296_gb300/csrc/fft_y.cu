@@ -26,9 +26,11 @@ namespace chanfs {
 // DST-II is DCT-II of (-1)^j x_j with the output order reversed.
 enum { Y_FFT = 0, Y_DCT = 1, Y_DST = 2 };
 
-// Elements of one y-tile buffer: tk x n values rounded up to 128 bytes.
+// Elements of one y-tile buffer: tk x n values (FP32 tiles: with room for
+// the padded layout of stockham_fixed_cols) rounded up to 128 bytes.
 __host__ __device__ inline int y_buf_elems(int tk, int n, int csize) {
-  const int bytes = (tk * n * csize + 127) / 128 * 128;
+  const int e = tk * n + (csize == (int)sizeof(float2) ? tk * n / 16 : 0);
+  const int bytes = (e * csize + 127) / 128 * 128;
   return bytes / csize;
 }
 
