@@ -416,6 +416,16 @@ __device__ __forceinline__ C* stockham_fixed_cols(C* a, C* b, int tk, const C* _
   }
 }
 
+// Whether an FP32 y tile of length d.n takes the compile-time path below.
+__host__ __device__ inline bool tile_fixed_len(const FftDesc& d) {
+  switch (d.n) {
+    case 64: case 96: case 128: case 192: case 256: case 384: case 512: case 768:
+      return d.npass == fixed_npass(d.n) && d.radix[0] == fixed_radix(d.n, 0);
+    default:
+      return false;
+  }
+}
+
 // All passes of a y tile (FP32: the compile-time path for common lengths).
 template <bool INV, class C>
 __device__ __forceinline__ C* stockham_tile(C* a, C* b, const FftDesc& d, int tk,

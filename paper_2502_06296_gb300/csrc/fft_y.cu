@@ -38,6 +38,19 @@ inline size_t y_smem_bytes(int tk, int n, int ntw, size_t csize) {
   return 128 + csize * (2 * (size_t)y_buf_elems(tk, n, (int)csize) + (size_t)ntw);
 }
 
+// Whether a tile reads its twiddles from the global table (L1-cached) rather
+// than a shared-memory copy: FP32 FFT tiles of the compile-time lengths.  A
+// tile is small (a few KB per column pair), so the per-CTA copy of the table
+// was as much traffic as the tile and its shared memory cost occupancy.
+__host__ __device__ inline bool y_global_tw(const FftDesc& d, int ytype, bool fp32) {
+  return fp32 && ytype == Y_FFT && tile_fixed_len(d);
+}
+
+inline size_t y_smem_of(const cfs_plan* P, int tk, bool fp32) {
+  const int ntw = y_global_tw(P->fy, P->ybc, fp32) ? 0 : P->fy.ntw;
+  return y_smem_bytes(tk, P->ny, ntw, fp32 ? sizeof(float2) : sizeof(double2));
+}
+
 template <class C>
 __device__ __forceinline__ C cmul_conj_a(C a, C b) {  // conj(a) * b
   return mkc<C>(fma(a.x, b.x, a.y * b.y), fma(a.x, b.y, -a.y * b.x));
@@ -139,7 +152,9 @@ __device__ __forceinline__ void fft_y_body(const CUtensorMap* map, const FftDesc
     mbar_expect_tx(bar, (uint32_t)(nbox * by * tk * sizeof(C)));
     for (int b = 0; b < nbox; ++b) tma_load_3d(buf0 + b * by * tk, map, bar, x0, b * by, z);
   }
-  for (int e = threadIdx.x; e < d.ntw; e += blockDim.x) tw[e] = twg[e];
+  const bool gtw = y_global_tw(d, ytype, sizeof(C) == sizeof(float2));
+  if (!gtw)
+    for (int e = threadIdx.x; e < d.ntw; e += blockDim.x) tw[e] = twg[e];
   // every thread waits (bounded); the CTA then agrees on one outcome, which
   // also publishes the twiddles
   const int ok = __syncthreads_and(mbar_wait(bar, 0) ? 1 : 0);
@@ -166,7 +181,7 @@ __device__ __forceinline__ void fft_y_body(const CUtensorMap* map, const FftDesc
     __syncthreads();
   }
   // element (y, c) of the tile sits at y*tk + c: element stride tk, batch stride 1
-  C* res = stockham_tile<INV>(buf0, buf1, d, tk, tw);
+  C* res = stockham_tile<INV>(buf0, buf1, d, tk, gtw ? twg : tw);
   if (!INV && bx == 0) {  // untangle after the forward transform
     for (int ky = 1 + threadIdx.x; 2 * ky < ny; ky += blockDim.x) {
       const C zz = res[ky * tk], zm = res[(ny - ky) * tk];
@@ -216,7 +231,7 @@ static cudaError_t launch_y(const cfs_plan* P, void* data, bool inverse, int tk,
                                  (cuuint64_t)(2 * P->M) * P->ny * sizeof(T)};
   const cuuint32_t box[3] = {(cuuint32_t)(2 * tk), (cuuint32_t)P->by, 1};
   if (!encode_map(&map, sizeof(T), 3, data, gdim, gstride, box)) return cudaErrorInvalidValue;
-  const size_t smem = y_smem_bytes(tk, P->ny, P->fy.ntw, sizeof(C));
+  const size_t smem = y_smem_of(P, tk, sizeof(C) == sizeof(float2));
   dim3 grid((P->M + tk - 1) / tk, P->nz);
   if (!inverse) {
     auto k = fft_y_kernel<false, C>;
@@ -234,7 +249,7 @@ bool y_tile_ok(const cfs_plan* P, int tk, bool fp32) {
   const size_t csize = fp32 ? sizeof(float2) : sizeof(double2);
   if (tk < 1 || tk > 32 || (fp32 && tk % 2)) return false;  // 16-byte TMA box rows
   if (P->nbox > 1 && ((size_t)P->by * tk * csize) % 128 != 0) return false;
-  return y_smem_bytes(tk, P->ny, P->fy.ntw, csize) <= 227 * 1024;
+  return y_smem_of(P, tk, fp32) <= 227 * 1024;
 }
 
 cudaError_t launch_fft_y(const cfs_plan* P, double* data, bool inverse, cudaStream_t st) {
@@ -262,7 +277,7 @@ size_t y_group_box(const cfs_plan* P, YBox* box, int* blocks) {
   box->ytype = P->ybc;
   box->wy = P->d_wy32;
   *blocks = (P->ny == 1) ? 0 : box->ntx * P->nz;  // a length-1 transform is the identity
-  return y_smem_bytes(tk, P->ny, P->fy.ntw, sizeof(float2));
+  return y_smem_of(P, tk, true);
 }
 
 cudaError_t launch_fft_y_group32(const YBox* boxes, GroupMap g, int total, size_t smem,
