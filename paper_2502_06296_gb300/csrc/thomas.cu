@@ -31,6 +31,9 @@ constexpr int kThomasBlock = 64;
 // of 14 blocks of 64 threads per SM.)
 template <class CA> struct prefetch_rows { static constexpr int value = 3; };
 template <> struct prefetch_rows<float2> { static constexpr int value = 6; };
+// The same for a thread that sweeps two columns (sweep_pair): two rows per step.
+template <class CA> struct pair_prefetch_rows { static constexpr int value = 2; };
+template <> struct pair_prefetch_rows<float2> { static constexpr int value = 3; };
 
 template <class C> struct cplx_traits;
 template <> struct cplx_traits<double2> {
@@ -206,6 +209,100 @@ __device__ __forceinline__ void thomas_column(const ThomasArgs& a, int ky, int j
                                        a.bwd32 + oy, false);
 }
 
+// Columns (ky, j) and (Ny - ky, j) of a periodic-y spectrum share one factor
+// set (the eigenvalue depends on |ky|): one thread sweeps both, so that the
+// factors are read once for two columns and the two recurrences are
+// independent work for the same thread (the sweeps are bound by memory
+// latency).  ONE factor set (kx >= 1); both columns advance row by row.
+template <class CS, class CA, int PF, class F2, class F1>
+__device__ __forceinline__ void sweep_pair(const ThomasArgs& a, CS* const s0, CS* const t0,
+                                           const F2* const fx0, const F1* const bx0) {
+  using T = typename cplx_traits<CA>::T;
+  const int nz = a.nz;
+  const long long rs = (long long)a.ny * a.M;         // spectrum row stride
+  const long long rt = (long long)a.nky * (a.M + 1);  // factor row stride
+
+  // forward: g_k = (s/piv_k) f_k - (A_k/piv_k) g_{k-1}, in place, both columns
+  CS qu[PF], qv[PF];
+  F2 qx[PF];
+#pragma unroll
+  for (int i = 0; i < PF; ++i) {
+    if (i < nz) {
+      qu[i] = s0[i * rs];
+      qv[i] = t0[i * rs];
+      qx[i] = fx0[i * rt];
+    }
+  }
+  long long off = PF * rs;  // next row to prefetch (spectrum)
+  const F2* px = fx0 + PF * rt;
+  long long w = 0;          // row being written
+  CA g = cplx_traits<CA>::mk(T(0), T(0)), h = g;
+  for (int k = 0; k < nz; k += PF) {
+#pragma unroll
+    for (int i = 0; i < PF; ++i) {
+      if (k + i >= nz) break;
+      const CA u = cvt<CA>(qu[i]), v = cvt<CA>(qv[i]);
+      const F2 fx = qx[i];
+      if (k + i + PF < nz) {
+        qu[i] = s0[off];
+        qv[i] = t0[off];
+        qx[i] = *px;
+      }
+      off += rs;
+      px += rt;
+      g = cplx_traits<CA>::mk(fma(-fx.y, g.x, fx.x * u.x), fma(-fx.y, g.y, fx.x * u.y));
+      h = cplx_traits<CA>::mk(fma(-fx.y, h.x, fx.x * v.x), fma(-fx.y, h.y, fx.x * v.y));
+      s0[w] = cvt<CS>(g);
+      t0[w] = cvt<CS>(h);
+      w += rs;
+    }
+  }
+
+  // backward: x_k = g_k - (C_k/piv_k) x_{k+1}, from the top wall down
+  CS qg[PF], qh[PF];
+  F1 qb[PF];
+  const long long top = (long long)(nz - 1) * rs;
+  const F1* const bx1 = bx0 + (long long)(nz - 1) * rt;
+#pragma unroll
+  for (int i = 0; i < PF; ++i) {
+    if (i < nz) {
+      qg[i] = s0[top - i * rs];
+      qh[i] = t0[top - i * rs];
+      qb[i] = bx1[-i * rt];
+    }
+  }
+  off = top - PF * rs;
+  const F1* pb = bx1 - PF * rt;
+  w = top;
+  CA x = cplx_traits<CA>::mk(T(0), T(0)), y = x;
+  for (int r = 0; r < nz; r += PF) {
+#pragma unroll
+    for (int i = 0; i < PF; ++i) {
+      if (r + i >= nz) break;
+      const CA gg = cvt<CA>(qg[i]), hh = cvt<CA>(qh[i]);
+      const F1 b = qb[i];
+      if (r + i + PF < nz) {
+        qg[i] = s0[off];
+        qh[i] = t0[off];
+        qb[i] = *pb;
+      }
+      off -= rs;
+      pb -= rt;
+      x = cplx_traits<CA>::mk(fma(-b, x.x, gg.x), fma(-b, x.y, gg.y));
+      y = cplx_traits<CA>::mk(fma(-b, y.x, hh.x), fma(-b, y.y, hh.y));
+      s0[w] = cvt<CS>(x);
+      t0[w] = cvt<CS>(y);
+      w -= rs;
+    }
+  }
+}
+
+// Rows of main blocks: periodic y pairs the slots ky and Ny - ky (kp = 0 ..
+// Ny/2); y walls have every slot its own column.
+__host__ __device__ inline int main_rows(const ThomasArgs& a) {
+  return a.ywall ? a.ny : a.ny / 2 + 1;
+}
+
 // Whether column (ky, j >= 1) of an FP32 spectrum is solved in FP64.
 __device__ __forceinline__ bool fp64_column(const ThomasArgs& a, int ky, int j) {
   const int kp = a.ywall ? ky : min(ky, a.ny - ky);
@@ -214,10 +311,22 @@ __device__ __forceinline__ bool fp64_column(const ThomasArgs& a, int ky, int j) 
 
 template <class CS>
 __device__ __forceinline__ void thomas_body(const ThomasArgs& a, int blk) {
-  const int ky = blk / a.nblk_x;
+  const int ky = blk / a.nblk_x;  // (the pair index kp for periodic y)
   const int j = (blk % a.nblk_x) * kThomasBlock + threadIdx.x;
   if (j == 0 || j >= a.M) return;
   if (sizeof(CS) == sizeof(float2) && fp64_column(a, ky, j)) return;
+  if (!a.ywall && ky > 0 && 2 * ky != a.ny) {  // slots ky and Ny - ky together
+    CS* const s0 = reinterpret_cast<CS*>(a.S) + (long long)ky * a.M + j;
+    CS* const t0 = reinterpret_cast<CS*>(a.S) + (long long)(a.ny - ky) * a.M + j;
+    const long long o = (long long)ky * (a.M + 1) + j;
+    if constexpr (sizeof(CS) == sizeof(double2))
+      sweep_pair<CS, double2, pair_prefetch_rows<double2>::value>(a, s0, t0, a.fwd + o,
+                                                                  a.bwd + o);
+    else
+      sweep_pair<CS, float2, pair_prefetch_rows<float2>::value>(a, s0, t0, a.fwd32 + o,
+                                                                a.bwd32 + o);
+    return;
+  }
   const int kp = a.ywall ? ky : min(ky, a.ny - ky);
   CS* const s0 = reinterpret_cast<CS*>(a.S) + (long long)ky * a.M + j;
   const long long o = (long long)kp * (a.M + 1) + j;
@@ -276,8 +385,8 @@ __global__ void __launch_bounds__(kThomasBlock, 14) thomas_group_kernel(const Th
 }
 
 template <class CS>
-static cudaError_t launch_streaming(const ThomasArgs& a, int ny, cudaStream_t st) {
-  thomas_kernel<CS><<<special_blocks<CS>(a) + a.nblk_x * ny, kThomasBlock, 0, st>>>(a);
+static cudaError_t launch_streaming(const ThomasArgs& a, cudaStream_t st) {
+  thomas_kernel<CS><<<special_blocks<CS>(a) + a.nblk_x * main_rows(a), kThomasBlock, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -632,7 +741,7 @@ static cudaError_t launch_thomas_t(const cfs_plan* P, void* data, cudaStream_t s
   const int tw = pick_tile_width<CS>(P, P->thomas_tw);
   if (tw == 16) return launch_tile<CS, 16, tile_depth<CS, 16>::DG>(P, data, st);
   if (tw == 8) return launch_tile<CS, 8, tile_depth<CS, 8>::DG>(P, data, st);
-  return launch_streaming<CS>(thomas_args(P, data), P->ny, st);
+  return launch_streaming<CS>(thomas_args(P, data), st);
 }
 
 cudaError_t launch_thomas(const cfs_plan* P, double* data, cudaStream_t st) {
@@ -704,7 +813,7 @@ cudaError_t launch_thomas_set(const cfs_plan* P, double* data, const double2* fw
   a.nz = n;
   a.neumann = 0;
   a.kx64 = a.ky64 = 0;  // (ywall as for the plan)
-  return launch_streaming<double2>(a, P->ny, st);
+  return launch_streaming<double2>(a, st);
 }
 
 cudaError_t launch_thomas_factor(cfs_plan* P, const double* dA, const double* dB, const double* dC,
@@ -719,7 +828,7 @@ cudaError_t launch_thomas_factor(cfs_plan* P, const double* dA, const double* dB
 
 size_t thomas_group_box(const cfs_plan* P, ThomasArgs* box, int* blocks) {
   *box = thomas_args(P, P->d_r32);
-  *blocks = special_blocks<float2>(*box) + box->nblk_x * P->ny;
+  *blocks = special_blocks<float2>(*box) + box->nblk_x * main_rows(*box);
   return 0;
 }
 
