@@ -51,6 +51,11 @@ inline size_t y_smem_of(const cfs_plan* P, int tk, bool fp32) {
   return y_smem_bytes(tk, P->ny, ntw, fp32 ? sizeof(float2) : sizeof(double2));
 }
 
+// Threads per tile: FP32 tiles are bound by latency (a tile's passes are
+// short against its copies), so they take more warps per tile; FP64 tiles
+// are bound by the FP64 pipe.
+template <class C> constexpr int y_threads() { return sizeof(C) == sizeof(float2) ? 256 : 128; }
+
 template <class C>
 __device__ __forceinline__ C cmul_conj_a(C a, C b) {  // conj(a) * b
   return mkc<C>(fma(a.x, b.x, a.y * b.y), fma(a.x, b.y, -a.y * b.x));
@@ -201,7 +206,7 @@ __device__ __forceinline__ void fft_y_body(const CUtensorMap* map, const FftDesc
 }
 
 template <bool INV, class C>
-__global__ void __launch_bounds__(128) fft_y_kernel(const __grid_constant__ CUtensorMap map,
+__global__ void __launch_bounds__(256) fft_y_kernel(const __grid_constant__ CUtensorMap map,
                                                     FftDesc d, const C* __restrict__ twg,
                                                     int tk, int by, int nbox, int* status,
                                                     int ytype, const C* __restrict__ wy) {
@@ -210,7 +215,7 @@ __global__ void __launch_bounds__(128) fft_y_kernel(const __grid_constant__ CUte
 
 // One launch for several boxes (FP32 inner solves of grouped refinement).
 template <bool INV>
-__global__ void __launch_bounds__(128) fft_y_group_kernel(const YBox* boxes, GroupMap g) {
+__global__ void __launch_bounds__(256, 1) fft_y_group_kernel(const YBox* boxes, GroupMap g) {
   int b, blk;
   if (!group_block(g, &b, &blk)) return;
   const YBox& y = boxes[b];
@@ -236,11 +241,13 @@ static cudaError_t launch_y(const cfs_plan* P, void* data, bool inverse, int tk,
   if (!inverse) {
     auto k = fft_y_kernel<false, C>;
     allow_max_smem(k);
-    k<<<grid, 128, smem, st>>>(map, P->fy, tw, tk, P->by, P->nbox, P->d_status, P->ybc, wy);
+    k<<<grid, y_threads<C>(), smem, st>>>(map, P->fy, tw, tk, P->by, P->nbox, P->d_status,
+                                          P->ybc, wy);
   } else {
     auto k = fft_y_kernel<true, C>;
     allow_max_smem(k);
-    k<<<grid, 128, smem, st>>>(map, P->fy, tw, tk, P->by, P->nbox, P->d_status, P->ybc, wy);
+    k<<<grid, y_threads<C>(), smem, st>>>(map, P->fy, tw, tk, P->by, P->nbox, P->d_status,
+                                          P->ybc, wy);
   }
   return cudaGetLastError();
 }
@@ -286,11 +293,11 @@ cudaError_t launch_fft_y_group32(const YBox* boxes, GroupMap g, int total, size_
   if (!inverse) {
     auto k = fft_y_group_kernel<false>;
     allow_max_smem(k);
-    k<<<total, 128, smem, st>>>(boxes, g);
+    k<<<total, y_threads<float2>(), smem, st>>>(boxes, g);
   } else {
     auto k = fft_y_group_kernel<true>;
     allow_max_smem(k);
-    k<<<total, 128, smem, st>>>(boxes, g);
+    k<<<total, y_threads<float2>(), smem, st>>>(boxes, g);
   }
   return cudaGetLastError();
 }
