@@ -18,6 +18,8 @@
 // The singular Neumann column (0, 0) is pinned (row 0 -> F_0 = 0); the
 // removal of the dz-weighted mean of its right-hand side and of its solution
 // is folded into the same two sweeps by linearity.
+#include <atomic>
+
 #include "chanfs_tma.cuh"
 #include "chanfs_group.cuh"
 
@@ -31,9 +33,12 @@ constexpr int kThomasBlock = 64;
 // of 14 blocks of 64 threads per SM.)
 template <class CA> struct prefetch_rows { static constexpr int value = 3; };
 template <> struct prefetch_rows<float2> { static constexpr int value = 6; };
-// The same for a thread that sweeps two columns (sweep_pair): two rows per step.
-template <class CA> struct pair_prefetch_rows { static constexpr int value = 2; };
-template <> struct pair_prefetch_rows<float2> { static constexpr int value = 3; };
+// The same for a thread that sweeps two columns (sweep_pair): two rows per
+// step.  DEEP: the launch fits in one wave at 8 blocks per SM (FP64 plans of
+// moderate size), so each thread may keep a deeper queue.
+template <class CA, bool DEEP> struct pair_prefetch_rows { static constexpr int value = 2; };
+template <> struct pair_prefetch_rows<double2, true> { static constexpr int value = 4; };
+template <bool DEEP> struct pair_prefetch_rows<float2, DEEP> { static constexpr int value = 3; };
 
 template <class C> struct cplx_traits;
 template <> struct cplx_traits<double2> {
@@ -309,7 +314,7 @@ __device__ __forceinline__ bool fp64_column(const ThomasArgs& a, int ky, int j) 
   return j < a.kx64 && kp < a.ky64;
 }
 
-template <class CS>
+template <class CS, bool DEEP>
 __device__ __forceinline__ void thomas_body(const ThomasArgs& a, int blk) {
   const int ky = blk / a.nblk_x;  // (the pair index kp for periodic y)
   const int j = (blk % a.nblk_x) * kThomasBlock + threadIdx.x;
@@ -320,10 +325,10 @@ __device__ __forceinline__ void thomas_body(const ThomasArgs& a, int blk) {
     CS* const t0 = reinterpret_cast<CS*>(a.S) + (long long)(a.ny - ky) * a.M + j;
     const long long o = (long long)ky * (a.M + 1) + j;
     if constexpr (sizeof(CS) == sizeof(double2))
-      sweep_pair<CS, double2, pair_prefetch_rows<double2>::value>(a, s0, t0, a.fwd + o,
+      sweep_pair<CS, double2, pair_prefetch_rows<double2, DEEP>::value>(a, s0, t0, a.fwd + o,
                                                                   a.bwd + o);
     else
-      sweep_pair<CS, float2, pair_prefetch_rows<float2>::value>(a, s0, t0, a.fwd32 + o,
+      sweep_pair<CS, float2, pair_prefetch_rows<float2, DEEP>::value>(a, s0, t0, a.fwd32 + o,
                                                                 a.bwd32 + o);
     return;
   }
@@ -364,16 +369,18 @@ __host__ __device__ inline int special_blocks(const ThomasArgs& a) {
 
 // One launch: the special columns' blocks first (their sweeps are the
 // longest-latency ones and overlap the main columns), then the main blocks.
-template <class CS>
+template <class CS, bool DEEP>
 __device__ __forceinline__ void thomas_launch_body(const ThomasArgs& a, int blk) {
   const int nsp = special_blocks<CS>(a);
   if (blk < nsp) thomas_special_body<CS>(a, blk);
-  else thomas_body<CS>(a, blk - nsp);
+  else thomas_body<CS, DEEP>(a, blk - nsp);
 }
 
-template <class CS>
-__global__ void __launch_bounds__(kThomasBlock, 14) thomas_kernel(ThomasArgs a) {
-  thomas_launch_body<CS>(a, blockIdx.x);
+// Resident blocks the register budget is sized for: 14 per SM, or 8 with
+// deeper prefetch queues (DEEP) for launches that fit in one wave of those.
+template <class CS, bool DEEP>
+__global__ void __launch_bounds__(kThomasBlock, DEEP ? 8 : 14) thomas_kernel(ThomasArgs a) {
+  thomas_launch_body<CS, DEEP>(a, blockIdx.x);
 }
 
 // One launch for several boxes (FP32 inner solves of grouped refinement).
@@ -381,12 +388,27 @@ __global__ void __launch_bounds__(kThomasBlock, 14) thomas_group_kernel(const Th
                                                                         GroupMap g) {
   int b, blk;
   if (!group_block(g, &b, &blk)) return;
-  thomas_launch_body<float2>(boxes[b], blk);
+  thomas_launch_body<float2, false>(boxes[b], blk);
 }
 
 template <class CS>
 static cudaError_t launch_streaming(const ThomasArgs& a, cudaStream_t st) {
-  thomas_kernel<CS><<<special_blocks<CS>(a) + a.nblk_x * main_rows(a), kThomasBlock, 0, st>>>(a);
+  const long long blocks = special_blocks<CS>(a) + (long long)a.nblk_x * main_rows(a);
+  static std::atomic<int> sms{0};  // SMs of the device (the same on every GB300 of a process)
+  int nsm = sms.load(std::memory_order_relaxed);
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    sms.store(nsm, std::memory_order_relaxed);
+  }
+  if constexpr (sizeof(CS) == sizeof(double2)) {
+    if (blocks <= 8LL * nsm) {
+      thomas_kernel<CS, true><<<(unsigned)blocks, kThomasBlock, 0, st>>>(a);
+      return cudaGetLastError();
+    }
+  }
+  thomas_kernel<CS, false><<<(unsigned)blocks, kThomasBlock, 0, st>>>(a);
   return cudaGetLastError();
 }
 
