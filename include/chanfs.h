@@ -243,13 +243,21 @@ int cfs_helmholtz_solve_noalloc(int nx, int ny, int nz, const double* dz,
 /*
  * Iterative refinement (plans created with CFS_F32_REFINED).  A solve starts
  * from x = 0 and repeats { delta = FP32 solve of r; x += delta in FP64;
- * r = b - A x in FP64 } until ||r||_inf <= tol ||b||_inf or `maxit` FP32
- * solves were done (defaults: tol = 1e-10, maxit = 4).  A is the staggered
- * 7-point Laplacian (Poisson; b is the right-hand side minus its dz-weighted
- * mean for Neumann walls) or I - c L_z (Helmholtz).  FP64 is used for the
- * residual, the accumulation, the coefficient pre-processing and the z sweep
- * of the near-singular low-wavenumber columns.  Each iteration reads the
- * residual norm back, so refined solves synchronise `stream`; when the
+ * r = b - A x } until ||r||_inf <= tol ||b||_inf or `maxit` FP32 solves were
+ * done (defaults: tol = 1e-10, maxit = 4).  A is the staggered 7-point
+ * Laplacian (Poisson; b is the right-hand side minus its dz-weighted mean for
+ * Neumann walls) or I - c L_z (Helmholtz).  Helmholtz residuals are formed in
+ * FP64.  Poisson residuals are formed in double-float arithmetic (the
+ * coefficients split hi + lo, the residual kept as an FP32 pair): the first
+ * with the stencil written in differences of the correction (exact in FP32),
+ * as accurate as an FP64 evaluation for a solution resolved by the grid, the
+ * later ones as r -= A delta.  With Neumann walls the running dz-weighted
+ * mean of x is subtracted from each correction after the first, so x keeps
+ * a zero mean up to the FP32 rounding of its last correction (a solve that
+ * stops after one FP32 solve has its mean removed in FP64 at the end).  FP64
+ * is also used for the accumulation, the coefficient pre-processing and the
+ * z sweep of the near-singular low-wavenumber columns.  Each iteration reads
+ * the residual norm back, so refined solves synchronise `stream`; when the
  * target is missed the solve returns CFS_ENOTCONVERGED with its best x.
  * cfs_last_info reports the FP32 solves done and the final relative residual
  * of the last refined solve.
@@ -278,7 +286,7 @@ int cfs_helmholtz3d_solve(cfs_plan_t plan, double c, int loc, const double* rhs,
  * GPUs; a group puts many independent boxes on one).  A group is built from
  * up to 4096 CFS_F32_REFINED plans of the current device, of any sizes, z
  * grids, walls and refinement settings.  Every stage of the refined Poisson
- * solve (FP32 transforms and z sweeps, FP64 residual, means and correction) is
+ * solve (start pass, FP32 transforms and z sweeps, residuals, means) is
  * then one kernel launch for all boxes, and the refinement loop runs on the
  * device: a solve is one CUDA graph whose loop is a conditional WHILE node,
  * the kernel that ends an iteration setting its condition; the host waits
@@ -392,8 +400,9 @@ int cfs_server_destroy(cfs_server_t server);
  *   CFS_OPT_HELM_FP64  CFS_F32_REFINED plans: 1 solves Helmholtz by FP64
  *       Algorithm 2 directly (no refinement; its error is that of the FP64
  *       path, below the refinement target), 0 (default) refines FP32 solves.
- *       On hardware where FP64 is scarce the refinement's FP64 residual costs
- *       as much as the FP64 solve itself, so the tuner may pick 1.
+ *       On hardware where FP64 is scarce the refinement's FP64 Helmholtz
+ *       residual costs as much as the FP64 solve itself, so the tuner may
+ *       pick 1.
  *   CFS_OPT_HELM_THOMAS  1: the FP64 Helmholtz solves of Eq. 11 run as one
  *       Thomas sweep per (x, y) column (factors of I - c L_z computed once per
  *       (c, loc), 3 FP64 instructions per unknown, the intermediate through

@@ -73,7 +73,7 @@ struct ThomasArgs {  // z sweeps of Eq. 12 (thomas.cu)
 struct ResBox {  // refinement residual and norms (refine.cu)
   const double* abc;   // Helmholtz: A' | B' | C'
   const double* dzf;   // cell widths
-  double* partial;     // nz plane sums
+  double* partial;     // nz * start_chunks(nz) plane-chunk sums of the start pass
   double* mean;        // dz-weighted mean
   float* r32;          // FP32 residual / correction
   float* r32b;         // FP32 residual of the later iterations

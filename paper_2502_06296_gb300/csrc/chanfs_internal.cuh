@@ -248,8 +248,9 @@ int plan_helm_prepare(cfs_plan* P, double c, int loc, int nparts, HelmCoef** out
 void plan_helm_forget(cfs_plan* P, double c);
 // Allocates the plan's FP64 staging field if it has none yet.
 int plan_ensure_stage(cfs_plan* P);
-// Iterative refinement drivers (refine.cu): FP32 inner solves, FP64 residual
-// and accumulation.  They synchronise `st` once per iteration.
+// Iterative refinement drivers (refine.cu): FP32 inner solves, residuals in
+// double-float (Poisson) or FP64 (Helmholtz), FP64 accumulation.  They
+// synchronise `st` once per iteration.
 int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st);
 int refine_helmholtz(cfs_plan* P, const HelmCoef& h, const double* rhs, double* u,
                      cudaStream_t st);

@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(kResBlock) helm_residual_kernel(
   helm_residual_body(rhs, u, r32, abc, rmax, ncols, n, nz, mode, blockIdx.x);
 }
 
-// p -= mean (the dz-weighted mean computed by the two kernels above).
+// p -= mean (the dz-weighted mean of p, from its running weighted sum).
 __device__ __forceinline__ void subtract_mean_body(double* __restrict__ p, long long n,
                                                    const double* __restrict__ mean, long long blk,
                                                    long long nblk) {
