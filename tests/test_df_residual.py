@@ -191,3 +191,24 @@ def test_difference_form_first_residual(kind):
     if kind == "smooth":
         assert np.max(err_df) * 4 < np.max(err_plain)
         assert np.max(err_df) < 1e-11 * np.max(np.abs(f))  # vs the 1e-10 target
+
+
+def test_residual_update_for_a_small_correction():
+    """r_new = r_old - L delta in the direct double-float form (the later
+    iterations): for a correction of 1e-6 of the solution's size its error,
+    2^-44 of sum |c delta| at most, is far below the FP64 rounding of the
+    first residual's terms."""
+    nx, ny, nz, lx, ly = 8, 6, 64, 1.0, 0.75
+    dz = synth.tanh_dz(nz, 2.4)
+    A, Bp, C, idx2, idy2 = operator(nz, dz, nx, ny, lx, ly)
+    rng = np.random.default_rng(11)
+    delta = (1e-6 * rng.standard_normal((nz, ny, nx))).astype(np.float32)
+    r_old = 1e-6 * rng.standard_normal((nz, ny, nx))  # a residual after one FP32 solve
+    # r_old carried as the pair (hi, lo); the update subtracts L delta from it
+    exact, _, _ = residuals(r_old, delta, A, Bp, C, idx2, idy2)
+    upd = direct_double_float(r_old, delta, A, Bp, C, idx2, idy2)
+    direct, _ = scale_terms(delta, A, Bp, C, idx2, idy2)
+    err = np.abs(upd - exact)
+    assert np.all(err <= 2.0 ** -44 * direct + 2.0 ** -46 * np.abs(r_old))
+    # against the scale of the solution (|p| ~ 1, |f| ~ 1 here): far below 1e-10
+    assert np.max(err) < 1e-14
