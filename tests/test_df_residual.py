@@ -212,3 +212,30 @@ def test_residual_update_for_a_small_correction():
     assert np.all(err <= 2.0 ** -44 * direct + 2.0 ** -46 * np.abs(r_old))
     # against the scale of the solution (|p| ~ 1, |f| ~ 1 here): far below 1e-10
     assert np.max(err) < 1e-14
+
+
+def test_running_mean_removal_leaves_the_last_corrections_rounding():
+    """Each correction pass after the first subtracts the running dz-weighted
+    mean of p (rounded to FP32) from its FP32 correction before adding it in
+    FP64: the mean left in p is the mean of the last correction plus roundings,
+    far below its size.  Emulated with corrections whose own means are those
+    an FP32 solve leaves (2^-24 of their size)."""
+    rng = np.random.default_rng(3)
+    nz, nxy = 48, 512
+    dz = synth.tanh_dz(nz, 1.8)
+    w = np.repeat(dz, nxy) / (dz.sum() * nxy)  # weights of the dz-weighted mean
+    p = np.zeros(nz * nxy)
+    sizes = [1.0, 1e-6, 1e-12]
+    for it, size in enumerate(sizes):
+        delta = size * rng.standard_normal(nz * nxy)
+        delta -= w @ delta                      # the solve's own mean removal ...
+        delta += size * 2.0 ** -24 * rng.standard_normal()  # ... up to FP32 rounding
+        delta = delta.astype(np.float32)
+        if it > 0:
+            m = np.float32(w @ p)               # running mean, rounded to FP32
+            delta = (delta - m).astype(np.float32)
+        p = p + delta.astype(np.float64)
+        if it == 0:
+            first_mean = abs(w @ p)
+    assert first_mean > 1e-9                    # the first solve's mean is visible ...
+    assert abs(w @ p) < 1e-15 * np.max(np.abs(p))  # ... and gone after the next passes
