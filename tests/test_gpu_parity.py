@@ -318,26 +318,103 @@ def test_host_buffer_entry_points_match_device_path(chanfs):
         assert np.array_equal(out, u_dev)
 
 
-@pytest.mark.slow
-def test_channel_workload_full_size(chanfs):
-    """The benchmark's 512 x 384 x 384 channel step, in the launch
-    configuration the benchmark times: every element against the oracle."""
+@pytest.fixture(scope="module")
+def channel_reference():
+    """The 512 x 384 x 384 channel workload's inputs and the oracle's FP64
+    solutions (Poisson, and Helmholtz for u, v centred and w face)."""
     cfg = synth.CHANNEL
-    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
     dz = synth.grid_dz(cfg)
     f, rhs = synth.channel_fields(cfg)
     c = synth.CHANNEL_C
+    p = oracle.poisson_solve(f, cfg["lx"], cfg["ly"], dz, 0)
+    us = [oracle.helmholtz_solve(r, dz, c, loc) for r, loc in zip(rhs, CHANNEL_LOCS)]
+    return cfg, dz, f, rhs, p, us
+
+
+CHANNEL_LOCS = (0, 0, 1)  # u, v cell-centred; w face-located
+
+
+def _channel_solve_and_check(plan, f_d, rhs_d, p_ref, u_refs, what, poisson=True,
+                             helmholtz=True):
+    p = None
+    if poisson:
+        p = host(plan.poisson_solve(f_d))
+        assert rel(p, p_ref) < TOL, (what, rel(p, p_ref))
+    if helmholtz:
+        for r, loc, uref in zip(rhs_d, CHANNEL_LOCS, u_refs):
+            u = host(plan.helmholtz_solve(synth.CHANNEL_C, r, loc))
+            assert rel(u, uref) < TOL, (what, loc, rel(u, uref))
+    assert plan.check() == 0
+    return p
+
+
+@pytest.mark.slow
+def test_channel_workload_full_size(chanfs, channel_reference):
+    """The benchmark's 512 x 384 x 384 channel step in the launch
+    configuration the benchmark times: shapes chosen by the autotuner, the
+    Helmholtz solves by Algorithm 2 with the tuned partition count, the
+    Poisson solve both whole and stage by stage; every element against the
+    oracle."""
+    cfg, dz, f, rhs, p_ref, u_refs = channel_reference
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    c = synth.CHANNEL_C
+    f_d = dev(f)
+    rhs_d = [dev(r) for r in rhs]
     with chanfs.Plan(nx, ny, nz, cfg["lx"], cfg["ly"], dz, chanfs.NEUMANN) as plan:
-        p = host(plan.poisson_solve(dev(f)))
-        us = [host(plan.helmholtz_solve(c, dev(r), loc)) for r, loc in zip(rhs, (0, 0, 1))]
+        shapes = plan.autotune()
+        plan.set_option(chanfs.OPT_HELM_THOMAS, 0)
+        for loc in (chanfs.CENTER, chanfs.FACE):
+            plan.helmholtz_prepare(c, loc, 0)
+        p = _channel_solve_and_check(plan, f_d, rhs_d, p_ref, u_refs, shapes)
+        # the benchmark launches the five Poisson kernels one by one
+        s = torch.empty_like(f_d)
+        plan.poisson_stage(chanfs.X_FORWARD, f_d, out=s)
+        for stage in (chanfs.Y_FORWARD, chanfs.Z_SOLVE, chanfs.Y_INVERSE, chanfs.X_INVERSE):
+            plan.poisson_stage(stage, s, out=s)
+        assert np.array_equal(host(s), p)
         assert plan.check() == 0
-    ref = oracle.poisson_solve(f, cfg["lx"], cfg["ly"], dz, 0)
-    assert rel(p, ref) < TOL, rel(p, ref)
     res = f - oracle.apply_poisson(p, cfg["lx"], cfg["ly"], dz, 0)
     assert np.max(np.abs(res)) / np.max(np.abs(f)) < 1e-12
-    for r, loc, u in zip(rhs, (0, 0, 1), us):
-        uref = oracle.helmholtz_solve(r, dz, c, loc)
-        assert rel(u, uref) < TOL
+
+
+# The candidates the autotuner times for each option (csrc/tune.cu), and
+# whether the option shapes the Poisson or the Helmholtz kernels; a candidate
+# that cannot run at this size is rejected by set_option.
+TUNER_CANDIDATES = [
+    ("OPT_FFT_RADIX", (8, 4), "poisson"),
+    ("OPT_X_LINES", (1, 2, 4, 8, 16, 32, 64), "poisson"),
+    ("OPT_Y_TILE", (1, 2, 4, 8, 16, 32), "poisson"),
+    ("OPT_THOMAS_TILE", (-1, 8, 16), "poisson"),
+    ("OPT_PCR_PARTS", (1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64), "helmholtz"),
+    ("OPT_HELM_THOMAS", (0, 1), "helmholtz"),
+]
+
+
+@pytest.mark.slow
+def test_channel_workload_every_tuner_candidate(chanfs, channel_reference):
+    """Whatever shape the autotuner picks for the benchmark's channel step,
+    the result meets the oracle: every candidate of every option, one option
+    at a time from the defaults, every element at full size."""
+    cfg, dz, f, rhs, p_ref, u_refs = channel_reference
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    f_d = dev(f)
+    rhs_d = [dev(r) for r in rhs]
+    ran = 0
+    with chanfs.Plan(nx, ny, nz, cfg["lx"], cfg["ly"], dz, chanfs.NEUMANN) as plan:
+        for name, values, kind in TUNER_CANDIDATES:
+            opt = getattr(chanfs, name)
+            for v in values:
+                try:
+                    plan.set_option(opt, v)
+                except chanfs.ChanfsError as err:
+                    assert err.status == chanfs.EUNSUPPORTED, (name, v)
+                    continue
+                _channel_solve_and_check(plan, f_d, rhs_d, p_ref, u_refs, (name, v),
+                                         poisson=kind == "poisson",
+                                         helmholtz=kind == "helmholtz")
+                ran += 1
+            plan.set_option(opt, 0)  # back to the automatic choice
+    assert ran >= 20
 
 
 @pytest.mark.parametrize("dtype", [0, 1])

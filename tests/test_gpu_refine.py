@@ -194,25 +194,24 @@ def test_refined_helmholtz_matches_fp64_oracle(chanfs, nx, ny, nz, beta, loc, c)
 
 @pytest.mark.slow
 def test_refined_precision_workload_full_size(chanfs):
-    """The 1024 x 768 x 512 uniform precision workload: the refined solve
-    meets the residual target (checked with the oracle's operator) and agrees
-    with the FP64 GPU solve of the same right-hand side."""
+    """The 1024 x 768 x 512 uniform precision workload in the launch
+    configuration the benchmark times (shapes from the autotuner): the
+    refined solve meets the residual target and matches the oracle's FP64
+    solution element by element."""
     cfg = synth.PRECISION
     nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
     dz = synth.grid_dz(cfg)
     f = synth.precision_rhs(cfg)
-    fd = dev(f)
     with chanfs.Plan(nx, ny, nz, cfg["lx"], cfg["ly"], dz, 0, chanfs.F32_REFINED) as plan:
-        p = plan.poisson_solve(fd)
+        plan.autotune()
+        p = host(plan.poisson_solve(dev(f)))
         iters, rho = plan.last_info()
         assert rho <= TOL and iters <= 4, (iters, rho)
-    with chanfs.Plan(nx, ny, nz, cfg["lx"], cfg["ly"], dz, 0, chanfs.F64) as plan:
-        p64 = plan.poisson_solve(fd)
-    torch.cuda.synchronize()
-    err = float((p - p64).abs().max() / p64.abs().max())
-    assert err < TOL, err
-    ph = host(p)
-    r = f - oracle.apply_poisson(ph, cfg["lx"], cfg["ly"], dz, 0)
+        assert plan.check() == 0
+    ref = oracle.poisson_solve(f, cfg["lx"], cfg["ly"], dz, 0)
+    assert rel(p, ref) < TOL, rel(p, ref)
+    del ref
+    r = f - oracle.apply_poisson(p, cfg["lx"], cfg["ly"], dz, 0)
     assert np.max(np.abs(r)) / np.max(np.abs(f)) < 2 * TOL
 
 
