@@ -141,8 +141,9 @@ int cfs_helmholtz_prepare(cfs_plan_t plan, double c, int loc, int nparts);
  * (Eq. 11) by Steps 2-4 of Algorithm 2: runtime forward/backward reduction of
  * the right-hand side only, the reduced boundary system, and reconstruction.
  *   rhs  device field (read), u  device field (written); rhs == u allowed.
- * Uses the coefficients cached by cfs_helmholtz_prepare (any nparts) or
- * prepares with nparts = 0 on a miss.
+ * Uses the set cached by cfs_helmholtz_prepare with the plan's
+ * CFS_OPT_PCR_PARTS count (when that option is 0: any cached set of (c, loc),
+ * else one prepared with nparts = 0 on a miss).
  */
 int cfs_helmholtz_solve(cfs_plan_t plan, double c, int loc, const double* rhs,
                         double* u, void* stream);
@@ -221,24 +222,33 @@ int cfs_solve_batch_host(cfs_plan_t plan, int n, const int* kind, const double* 
  * cudaMalloc and cudaFree synchronise the whole device, stalling every other
  * stream in flight, and applications that reserve the device memory up front
  * for their own pool have none left to give.
- *   nx, ny, nz, dz  grid as for cfs_plan_create (dz on the HOST); nx*ny even.
+ *   nx, ny, nz, dz  grid as for cfs_plan_create (dz: nz HOST doubles, read
+ *                   before the call returns); nx*ny even.
  *   c, loc          as for cfs_helmholtz_solve; nparts as for
- *                   cfs_helmholtz_prepare (0 = same choice as the plan).
+ *                   cfs_helmholtz_prepare (0 = about 32 rows per partition).
  *   rhs, u          device fields as for cfs_helmholtz_solve (rhs == u allowed).
- * The Algorithm 2 coefficients are computed on the host and copied into a
- * fixed device array inside the library, sized for at most 1024 unknowns
- * per column and 64 partitions (about 44 KB, held by every GPU that loads
- * the library until the process exits); larger sizes return
- * CFS_EUNSUPPORTED.  The first call on a device looks up that array's
- * address (cudaGetSymbolAddress), so make it before any stream capture.
- * Every call overwrites the whole coefficient set and clears the array's
- * status word; there is one array per device, so calls whose work overlaps
- * on the GPU (other streams, other host threads) race.  The call waits for
- * its small coefficient copy, then queues the solve on `stream` and returns.
+ *   device_status   DEVICE pointer to one int owned by the caller (4-byte
+ *                   aligned): the call sets it to 0 on `stream`, and the
+ *                   solve ORs failure bits into it (nonzero: a bounded wait
+ *                   inside the kernel ran out and u is not valid).  Read it
+ *                   once the work on `stream` has finished.
+ * The Algorithm 2 coefficients are computed by a small kernel on `stream`,
+ * in FP64 from the cell widths (passed as kernel parameters), into a fixed
+ * device array inside the library, sized for at most 1024 unknowns per
+ * column and 64 partitions (about 44 KB, held by every GPU that loads the
+ * library until the process exits); larger sizes return CFS_EUNSUPPORTED
+ * before anything is queued.  The call queues that kernel and the solve and
+ * returns without waiting for the device.  The first call on a device looks
+ * up the array's address there (cudaGetSymbolAddress), so make it before any
+ * stream capture.  Every call overwrites the whole coefficient set; there is
+ * one array per device, so calls whose work overlaps on one GPU (other
+ * streams, other host threads) race and may read each other's coefficients.
+ * Calls on different devices do not share anything.
  */
 int cfs_helmholtz_solve_noalloc(int nx, int ny, int nz, const double* dz,
                                 double c, int loc, int nparts,
-                                const double* rhs, double* u, void* stream);
+                                const double* rhs, double* u,
+                                int* device_status, void* stream);
 
 /*
  * Iterative refinement (plans created with CFS_F32_REFINED).  A solve starts
@@ -471,6 +481,19 @@ int cfs_autotune_clear(void);
  * lo below the normal binary32 range is not compared: the split returns 0).
  */
 int cfs_selfcheck_conversions(unsigned long long samples, unsigned long long* mismatches);
+
+/*
+ * cfs_probe_fma -- a measurement with no counterpart in the paper: the FMA
+ * rate of the current GPU in FP64 (bits = 64) or FP32 (bits = 32), the
+ * roofline peak of kernels bound by those instructions.  Every thread of one
+ * full wave of 256-thread blocks (as many per SM as fit, at most 8) runs 16
+ * independent FMA chains for `iters` steps (1 <= iters <= 2^40); after one
+ * shorter warm-up launch the timed launch is measured with CUDA events on
+ * the legacy default stream.
+ * *fma_per_s receives FMAs per second, *ms (may be NULL) the launch time.
+ * Waits for the device.
+ */
+int cfs_probe_fma(int bits, long long iters, double* fma_per_s, double* ms);
 
 /*
  * cfs_plan_check -- wait for the device and report device-side failures

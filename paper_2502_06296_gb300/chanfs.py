@@ -75,8 +75,9 @@ def lib():
             "cfs_plan_check": ([vp, ctypes.POINTER(i)], i),
             "cfs_poisson_stage": ([vp, i, vp, vp, vp], i),
             "cfs_plan_set_refinement": ([vp, d, i], i),
-            "cfs_helmholtz_solve_noalloc": ([i, i, i, dp, d, i, i, vp, vp, vp], i),
+            "cfs_helmholtz_solve_noalloc": ([i, i, i, dp, d, i, i, vp, vp, vp, vp], i),
             "cfs_last_info": ([vp, ctypes.POINTER(i), ctypes.POINTER(d)], i),
+            "cfs_probe_fma": ([i, ctypes.c_longlong, dp, dp], i),
             "cfs_group_create": ([ctypes.POINTER(vp), i, ctypes.POINTER(vp)], i),
             "cfs_group_destroy": ([vp], i),
             "cfs_group_size": ([vp, ctypes.POINTER(i)], i),
@@ -308,9 +309,12 @@ class Plan:
 
 
 def helmholtz_solve_noalloc(dz, c: float, rhs, loc: int = CENTER, nparts: int = 0, out=None,
-                            stream=None):
+                            status=None, stream=None):
     """cfs_helmholtz_solve_noalloc: the Helmholtz solve without a plan and
-    without device allocation by the library (see include/chanfs.h)."""
+    without device allocation by the library (see include/chanfs.h).
+    `status` is a CUDA int32 tensor of at least one element that receives the
+    solve's failure bits (allocated here if not given); returns (u, status).
+    Read status after the stream has finished: nonzero means u is invalid."""
     import torch
     dz = np.ascontiguousarray(dz, dtype=np.float64)
     nz, ny, nx = rhs.shape
@@ -320,11 +324,16 @@ def helmholtz_solve_noalloc(dz, c: float, rhs, loc: int = CENTER, nparts: int = 
     for t, name in ((rhs, "rhs"), (out, "out")):
         if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous() or t.shape != rhs.shape:
             raise TypeError(f"{name} must be a contiguous float64 CUDA tensor of the rhs shape")
+    if status is None:
+        status = torch.zeros(1, dtype=torch.int32, device=rhs.device)
+    if status.dtype != torch.int32 or not status.is_cuda or status.numel() < 1:
+        raise TypeError("status must be a CUDA int32 tensor")
     _check(lib().cfs_helmholtz_solve_noalloc(nx, ny, nz, dz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                              float(c), loc, nparts, ctypes.c_void_p(rhs.data_ptr()),
-                                             ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+                                             ctypes.c_void_p(out.data_ptr()),
+                                             ctypes.c_void_p(status.data_ptr()), _stream_ptr(stream)),
            "cfs_helmholtz_solve_noalloc")
-    return out
+    return out, status
 
 
 class Group:
@@ -503,6 +512,15 @@ def autotune_load(path) -> int:
 def autotune_clear() -> None:
     """Forget every tuning choice of this process."""
     _check(lib().cfs_autotune_clear(), "cfs_autotune_clear")
+
+
+def probe_fma(bits: int = 64, iters: int = 1 << 15):
+    """(FMAs per second, launch ms) of the current GPU in FP64 or FP32
+    (cfs_probe_fma)."""
+    rate, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib().cfs_probe_fma(int(bits), int(iters), ctypes.byref(rate), ctypes.byref(ms)),
+           "cfs_probe_fma")
+    return rate.value, ms.value
 
 
 def selfcheck_conversions(samples: int = 1 << 22) -> int:

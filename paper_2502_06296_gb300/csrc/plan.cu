@@ -7,6 +7,7 @@
 #include <new>
 #include <vector>
 
+#include "chanfs_alg2.cuh"
 #include "chanfs_internal.cuh"
 
 using namespace chanfs;
@@ -83,35 +84,11 @@ static int dev_upload(T** dst, const T* src, size_t count, size_t* acc) {
 static int z_stencil(const std::vector<double>& dzf, int bc, int loc, std::vector<double>& A,
                      std::vector<double>& B, std::vector<double>& C) {
   const int nz = (int)dzf.size();
-  std::vector<double> dzc(nz > 1 ? nz - 1 : 1);
-  for (int k = 0; k + 1 < nz; ++k) dzc[k] = 0.5 * (dzf[k] + dzf[k + 1]);
-  if (loc == CFS_LOC_CENTER) {
-    A.assign(nz, 0.0);
-    B.assign(nz, 0.0);
-    C.assign(nz, 0.0);
-    for (int k = 0; k < nz; ++k) {
-      const double lo = (k > 0) ? 1.0 / (dzf[k] * dzc[k - 1]) : 1.0 / (dzf[0] * dzf[0]);
-      const double hi = (k < nz - 1) ? 1.0 / (dzf[k] * dzc[k]) : 1.0 / (dzf[k] * dzf[k]);
-      double diag = -(lo + hi);
-      if (k == 0) diag += (bc == CFS_BC_NEUMANN) ? lo : -lo;
-      if (k == nz - 1) diag += (bc == CFS_BC_NEUMANN) ? hi : -hi;
-      A[k] = (k > 0) ? lo : 0.0;
-      C[k] = (k < nz - 1) ? hi : 0.0;
-      B[k] = diag;
-    }
-    return nz;
-  }
-  const int n = nz - 1;
+  const int n = (loc == CFS_LOC_CENTER) ? nz : nz - 1;
   A.assign(n, 0.0);
   B.assign(n, 0.0);
   C.assign(n, 0.0);
-  for (int j = 0; j < n; ++j) {
-    const double lo = 1.0 / (dzc[j] * dzf[j]);
-    const double hi = 1.0 / (dzc[j] * dzf[j + 1]);
-    A[j] = (j > 0) ? lo : 0.0;
-    C[j] = (j < n - 1) ? hi : 0.0;
-    B[j] = -(lo + hi);
-  }
+  for (int k = 0; k < n; ++k) z_operator_row(k, nz, dzf.data(), bc, loc, &A[k], &B[k], &C[k]);
   return n;
 }
 
@@ -550,14 +527,7 @@ static HelmCoef* helm_find(cfs_plan* P, double c, int loc, int nparts) {
   return nullptr;
 }
 
-static int auto_parts(int n) {
-  // about 32 rows per partition, at least 3
-  int p = (n + 31) / 32;
-  if (p > kPcrMaxParts) p = kPcrMaxParts;
-  if (p < 1) p = 1;
-  while (p > 1 && n / p < 3) --p;
-  return p;
-}
+static int auto_parts(int n) { return alg2_auto_parts(n, kPcrMaxParts); }
 
 // Frees one cached set (the device must be idle on it).
 static void helm_release(cfs_plan* P, HelmCoef& h) {
@@ -602,7 +572,7 @@ static int helm_prepare(cfs_plan* P, double c, int loc, int nparts, HelmCoef** r
   h.nparts = np;
   h.n = n;
   h.mmax = 0;
-  for (int q = 0; q <= np; ++q) h.start[q] = (int)(((long long)q * n) / np);
+  for (int q = 0; q <= np; ++q) h.start[q] = alg2_part_start(q, n, np);
   for (int q = 0; q < np; ++q) {
     const int m = h.start[q + 1] - h.start[q];
     if (m < 3) return CFS_EUNSUPPORTED;
@@ -616,58 +586,27 @@ static int helm_prepare(cfs_plan* P, double c, int loc, int nparts, HelmCoef** r
   double* cpv = ap + n;
   const int J = 2 * np;
   std::vector<double> ra(J), rb(J), rc(J);
-  std::vector<double> a(n), b(n), cc(n);
   for (int q = 0; q < np; ++q) {
     const int o = h.start[q], m = h.start[q + 1] - o;
-    const double *Aq = &A[o], *Bq = &B[o], *Cq = &C[o];
-    double *aq = &a[o], *bq = &b[o], *cq = &cc[o];
-    // Step 1 of Algorithm 2
-    aq[1] = Aq[1];
-    bq[1] = Bq[1];
-    for (int i = 2; i <= m - 1; ++i) {
-      bq[i] = Bq[i] - Aq[i] * Cq[i - 1] / bq[i - 1];
-      aq[i] = -Aq[i] * aq[i - 1] / bq[i - 1];
-    }
-    cq[m - 1] = Cq[m - 1];
-    cq[m - 2] = Cq[m - 2];
-    for (int i = m - 3; i >= 1; --i) {
-      aq[i] = aq[i] - Cq[i] * aq[i + 1] / bq[i + 1];
-      cq[i] = -Cq[i] * cq[i + 1] / bq[i + 1];
-    }
-    aq[0] = Aq[0];
-    bq[0] = Bq[0] - Cq[0] * aq[1] / Bq[1];
-    cq[0] = -Cq[0] * cq[1] / Bq[1];
-    // run-time factors of Steps 2 and 4 (divisions done here, once)
-    for (int i = 0; i < m; ++i) {
-      alpha[o + i] = (i >= 2) ? Aq[i] / bq[i - 1] : 0.0;
-      beta[o + i] = (i <= m - 3) ? Cq[i] / bq[i + 1] : 0.0;
-      ib[o + i] = 1.0 / bq[i];
-      ap[o + i] = aq[i] / bq[i];
-      cpv[o + i] = cq[i] / bq[i];
-    }
-    // Step 3: the partition's two rows of the reduced boundary system
-    ra[2 * q] = aq[0];
-    rb[2 * q] = bq[0];
-    rc[2 * q] = cq[0];
-    ra[2 * q + 1] = aq[m - 1];
-    rb[2 * q + 1] = bq[m - 1];
-    rc[2 * q + 1] = cq[m - 1];
+    // Step 1 of Algorithm 2, and the partition's two rows of the reduced system
+    auto row = [&](int i, double* lo, double* diag, double* hi) {
+      *lo = A[o + i];
+      *diag = B[o + i];
+      *hi = C[o + i];
+    };
+    double first[3], last[3];
+    alg2_factor_partition(m, row, alpha + o, beta + o, ib + o, ap + o, cpv + o, first, last);
+    ra[2 * q] = first[0];
+    rb[2 * q] = first[1];
+    rc[2 * q] = first[2];
+    ra[2 * q + 1] = last[0];
+    rb[2 * q + 1] = last[1];
+    rc[2 * q + 1] = last[2];
   }
-  // LU of the reduced system (no pivoting: diagonally dominant)
+  // LU of the reduced system (Step 3; no pivoting: diagonally dominant)
   std::vector<double> red(3 * (size_t)J);
-  double* rl = red.data();
-  double* rip = rl + J;
-  double* ripc = rip + J;
-  double piv = rb[0];
-  rl[0] = 0.0;
-  rip[0] = 1.0 / piv;
-  ripc[0] = rc[0] / piv;
-  for (int j = 1; j < J; ++j) {
-    rl[j] = ra[j] / piv;
-    piv = rb[j] - rl[j] * rc[j - 1];
-    rip[j] = 1.0 / piv;
-    ripc[j] = rc[j] / piv;
-  }
+  alg2_reduced_factor(J, ra.data(), rb.data(), rc.data(), red.data(), red.data() + J,
+                      red.data() + 2 * J);
   // Thomas factors of the same system: fs = 1/piv, fa = A'/piv, fc = C'/piv
   std::vector<double> th(3 * (size_t)n);
   {
