@@ -90,6 +90,31 @@ def fp64_peak_tflops(sm_count: int = 152, clock_mhz: float = 2070.0) -> float:
     return sm_count * 2 * 2 * clock_mhz * 1e6 / 1e12
 
 
+def run_fma_probe(chanfs, device_index: int, reps: int = 5) -> dict:
+    """FP64 and FP32 FMA rates of this GPU (cfs_probe_fma), with the SM clock
+    sampled meanwhile: the evidence for the FP64 unit count in the peak."""
+    with ClockSampler(device_index) as clk:
+        r64 = [chanfs.probe_fma(64, 1 << 14) for _ in range(reps)]
+        r32 = [chanfs.probe_fma(32, 1 << 20) for _ in range(reps)]
+    clock = clk.summary() or {}
+    import torch
+    nsm = torch.cuda.get_device_properties(device_index).multi_processor_count
+    mhz = clock.get("sm_mhz") or 0.0
+    f64 = statistics.median(r for r, _ in r64)
+    f32 = statistics.median(r for r, _ in r32)
+    out = {"fp64_fma_per_s": f64, "fp32_fma_per_s": f32, "sms": nsm,
+           "launch_ms_fp64": round(statistics.median(m for _, m in r64), 3),
+           "launch_ms_fp32": round(statistics.median(m for _, m in r32), 3),
+           "sm_mhz_median": mhz, "clock_samples": clock.get("samples"),
+           "reasons": clock.get("reasons"), "reps": reps,
+           "how": "cfs_probe_fma: one full wave of 256-thread blocks, 16 independent FMA chains per "
+                  "thread, CUDA events; median of reps"}
+    if mhz:
+        out["fp64_fma_per_sm_per_clk"] = f64 / (nsm * mhz * 1e6)
+        out["fp32_fma_per_sm_per_clk"] = f32 / (nsm * mhz * 1e6)
+    return out
+
+
 def read_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -564,59 +589,92 @@ def run_stress(chanfs, torch, device, reps: int = 3):
 # Serving stream: Poisson arrivals of Poisson/Helmholtz requests from 32 runs
 # ----------------------------------------------------------------------------
 
-def run_serving(chanfs, torch, device, nreq: int = 0, workers: int = 4, max_batch: int = 32):
+def run_serving(chanfs, torch, device, nreq: int = 0, workers: int = 4, max_batch: int = 32,
+                slots: int = 2, rates=(2000.0, 3500.0)):
+    """The serving stream through cfs_server_*: the seeded arrivals at each
+    offered rate in `rates` (the stream's own 2000/s, then its arrival times
+    scaled to a rate near capacity), p50/p99 latency, solves/s and batching;
+    then capacity (requests submitted at once) against per-request FP64."""
     cfg = dict(synth.SERVING)
     if nreq:
         cfg["nreq"] = nreq
     runs, reqs = synth.serving_stream(cfg)
     gen = torch.Generator(device=device)
     gen.manual_seed(cfg["seed"])
-    srv = chanfs.Server(int(cfg["budget_gb"] * 2**30), workers, max_batch, autotune=True)
+    srv = chanfs.Server(int(cfg["budget_gb"] * 2**30), workers, max_batch, autotune=True,
+                        slots_per_run=slots)
+    # per run: one right-hand side and `slots` outputs (requests of one run
+    # in flight at the same time write different outputs)
     fields = []
     for nx, ny, nz, beta, _ in runs:
         srv.add_run(nx, ny, nz, cfg["lx"], cfg["ly"], synth.tanh_dz(nz, beta), chanfs.NEUMANN)
         x = torch.randn(nz, ny, nx, dtype=torch.float64, device=device, generator=gen)
-        fields.append((x, torch.empty_like(x)))
+        fields.append((x, [torch.empty_like(x) for _ in range(slots)]))
     torch.cuda.synchronize()
-    # warm the plans (creation, tuning, the Helmholtz sets of each run)
+    nth = [0] * len(runs)
+
+    def submit(r, kind, ci, loc):
+        out = fields[r][1][nth[r] % slots]
+        nth[r] += 1
+        return srv.submit(r, kind, fields[r][0], out, runs[r][4][ci], loc)
+
+    # warm the plans (creation, tuning, the Helmholtz sets of each run), every slot
     t0 = time.perf_counter()
-    warm = []
-    for r, (nx, ny, nz, beta, cs) in enumerate(runs):
-        warm.append(srv.submit(r, chanfs.REQ_POISSON, fields[r][0], fields[r][1]))
-        for c in cs:
-            for loc in (chanfs.CENTER, chanfs.FACE):
-                warm.append(srv.submit(r, chanfs.REQ_HELMHOLTZ, fields[r][0], fields[r][1], c, loc))
-    for t in warm:
-        srv.wait(t)
+    for _ in range(slots):
+        warm = []
+        for r, (nx, ny, nz, beta, cs) in enumerate(runs):
+            warm.append(submit(r, chanfs.REQ_POISSON, 0, 0))
+            for ci in range(len(cs)):
+                for loc in (chanfs.CENTER, chanfs.FACE):
+                    warm.append(submit(r, chanfs.REQ_HELMHOLTZ, ci, loc))
+        for t in warm:
+            srv.wait(t)
     warm_s = time.perf_counter() - t0
-    before = srv.stats()
-    tickets = []
-    start = time.perf_counter()
-    for arrival, r, kind, ci, loc in reqs:
-        while True:
-            lag = start + arrival - time.perf_counter()
-            if lag <= 0:
-                break
-            if lag > 2e-4:
-                time.sleep(lag - 1e-4)
-        tickets.append(srv.submit(r, kind, fields[r][0], fields[r][1], runs[r][4][ci], loc))
-    lat, failed, statuses = [], 0, {}
-    for t in tickets:
-        status, l = srv.wait(t)
-        lat.append(l)
-        failed += status != 0
-        if status:
-            statuses[chanfs.status_string(status)] = statuses.get(chanfs.status_string(status), 0) + 1
-    span = time.perf_counter() - start
-    after = srv.stats()
-    # capacity: the first `ncap` requests submitted at once (saturated server)
+    pts = np.array([runs[r][0] * runs[r][1] * runs[r][2] for _, r, _, _, _ in reqs], dtype=np.float64)
+
+    def stream(rate):
+        scale = cfg["rate"] / rate
+        before = srv.stats()
+        tickets = []
+        start = time.perf_counter()
+        for arrival, r, kind, ci, loc in reqs:
+            due = start + arrival * scale
+            while True:
+                lag = due - time.perf_counter()
+                if lag <= 0:
+                    break
+                if lag > 2e-4:
+                    time.sleep(lag - 1e-4)
+            tickets.append(submit(r, kind, ci, loc))
+        lat, failed, statuses = [], 0, {}
+        for t in tickets:
+            status, l = srv.wait(t)
+            lat.append(l)
+            failed += status != 0
+            if status:
+                key = chanfs.status_string(status)
+                statuses[key] = statuses.get(key, 0) + 1
+        span = time.perf_counter() - start
+        after = srv.stats()
+        lat = np.array(lat)
+        nb = after["batches"] - before["batches"]
+        return {"offered_rate_per_s": rate, "arrival_span_s": reqs[-1][0] * scale,
+                "solves_per_s": len(reqs) / span, "wall_s": span,
+                "p50_latency_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_latency_ms": float(np.percentile(lat, 99) * 1e3),
+                "mean_latency_ms": float(lat.mean() * 1e3), "failed": int(failed),
+                "failures": statuses, "grid_points_per_s": float(pts.sum() / span),
+                "mean_batch": (after["completed"] - before["completed"]) / max(nb, 1)}
+
+    streams = [stream(rate) for rate in rates]
+    # capacity: the first `ncap` requests of the stream submitted at once
     ncap = min(4000, len(reqs))
     t0 = time.perf_counter()
-    cap_tickets = [srv.submit(r, kind, fields[r][0], fields[r][1], runs[r][4][ci], loc)
-                   for _, r, kind, ci, loc in reqs[:ncap]]
+    cap_tickets = [submit(r, kind, ci, loc) for _, r, kind, ci, loc in reqs[:ncap]]
     for t in cap_tickets:
         srv.wait(t)
     cap_s = time.perf_counter() - t0
+    after = srv.stats()
     srv.close()
     # the same requests as plain per-request FP64 solves, one after another
     plans64 = []
@@ -628,9 +686,9 @@ def run_serving(chanfs, torch, device, nreq: int = 0, workers: int = 4, max_batc
     def fp64(sub):
         for _, r, kind, ci, loc in sub:
             if kind == 0:
-                plans64[r].poisson_solve(fields[r][0], out=fields[r][1])
+                plans64[r].poisson_solve(fields[r][0], out=fields[r][1][0])
             else:
-                plans64[r].helmholtz_solve(runs[r][4][ci], fields[r][0], loc, out=fields[r][1])
+                plans64[r].helmholtz_solve(runs[r][4][ci], fields[r][0], loc, out=fields[r][1][0])
 
     fp64(reqs[:200])  # Helmholtz sets and warm-up
     torch.cuda.synchronize()
@@ -640,32 +698,26 @@ def run_serving(chanfs, torch, device, nreq: int = 0, workers: int = 4, max_batc
     f64_s = time.perf_counter() - t0
     for pl in plans64:
         pl.close()
-    lat = np.array(lat)
-    pts = np.array([runs[r][0] * runs[r][1] * runs[r][2] for _, r, _, _, _ in reqs], dtype=np.float64)
-    nb = after["batches"] - before["batches"]
-    return {"workload": cfg["name"], "requests": len(reqs), "runs": len(runs),
-            "offered_rate_per_s": cfg["rate"], "arrival_span_s": reqs[-1][0],
-            "poisson_requests": sum(1 for q in reqs if q[2] == 0),
-            "solves_per_s": len(reqs) / span, "wall_s": span,
-            "p50_latency_ms": float(np.percentile(lat, 50) * 1e3),
-            "p99_latency_ms": float(np.percentile(lat, 99) * 1e3),
-            "mean_latency_ms": float(lat.mean() * 1e3), "failed": int(failed),
-            "failures": statuses,
-            "grid_points_per_s": float(pts.sum() / span),
-            "mean_batch": (after["completed"] - before["completed"]) / max(nb, 1),
-            "max_batch": after["max_batch_seen"], "plans_created": after["plans_created"],
-            "plans_evicted": after["plans_evicted"], "plan_bytes": after["bytes_in_use"],
-            "workers": workers, "budget_gb": cfg["budget_gb"], "warm_s": round(warm_s, 1),
-            "capacity_solves_per_s": ncap / cap_s,
-            "per_request_f64_solves_per_s": ncap / f64_s,
-            "capacity_vs_per_request_f64": f64_s / cap_s,
-            "capacity_sample": f"first {ncap} requests of the stream submitted at once, against the "
-                               "same requests solved one after another by FP64 plans",
-            "precision": "Poisson: FP32 solves + FP64 refinement to 1e-10 (at most 4 FP32 "
-                         "solves); Helmholtz: per size the faster of that and FP64 Algorithm 2 "
-                         "(autotuner), both within 1e-10",
-            "latency": "host clock from submission (at the scheduled arrival) to completion; "
-                       "plans warmed before the stream"}
+    out = {"workload": cfg["name"], "requests": len(reqs), "runs": len(runs),
+           "poisson_requests": sum(1 for q in reqs if q[2] == 0)}
+    out.update(streams[0])
+    out["streams"] = streams
+    out.update({"max_batch": after["max_batch_seen"], "plans_created": after["plans_created"],
+                "plans_evicted": after["plans_evicted"], "plan_bytes": after["bytes_in_use"],
+                "workers": workers, "slots_per_run": slots, "budget_gb": cfg["budget_gb"],
+                "warm_s": round(warm_s, 1),
+                "capacity_solves_per_s": ncap / cap_s,
+                "per_request_f64_solves_per_s": ncap / f64_s,
+                "capacity_vs_per_request_f64": f64_s / cap_s,
+                "capacity_sample": f"first {ncap} requests of the stream submitted at once, against "
+                                   "the same requests solved one after another by FP64 plans",
+                "precision": "Poisson: FP32 solves + FP64 refinement to 1e-10 (at most 4 FP32 "
+                             "solves); Helmholtz: per size the faster of that and FP64 Algorithm 2 "
+                             "(autotuner), both within 1e-10",
+                "latency": "host clock from submission (at the scheduled arrival) to completion; "
+                           "plans warmed before the streams; the second stream is the same "
+                           "arrivals with their times scaled to the higher rate"})
+    return out
 
 
 # ----------------------------------------------------------------------------
@@ -681,6 +733,16 @@ def run_mixed_only(args):
     mixed = run_mixed(chanfs, torch, torch.device("cuda", 0), reps=args.steps, warmup=args.warmup,
                       nz=args.mixed_nz)
     print(json.dumps({"mixed": mixed}), flush=True)
+    return 0
+
+
+def run_probe_only(args):
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2502_06296_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2502_06296_gb300 import chanfs
+    print(json.dumps({"fma_probe": run_fma_probe(chanfs, 0, reps=args.steps)}), flush=True)
     return 0
 
 
@@ -839,8 +901,9 @@ def run_ours(args):
             "algorithmic_bytes_per_launch": nbytes,
             "hbm_gbs": nbytes / dur_s / 1e9,
             "hbm_frac": nbytes / dur_s / 1e9 / float(peaks.get("hbm_gbs", 6800.0)),
-            "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flops x 2070 MHz (1.26 TFLOP/s); "
-                           "HBM: MEASURED_PEAKS.json hbm_gbs"}
+            "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flops x 2070 MHz (1.26 TFLOP/s), the "
+                           "2 DFMA/clk/SM measured by cfs_probe_fma (line's fma_probe; "
+                           "profiles/fp64_fma_probe.md); HBM: MEASURED_PEAKS.json hbm_gbs"}
     line = {
         "metric": METRIC, "value": agg["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": agg["ms_per_step"], "higher_is_better": False,
@@ -860,10 +923,12 @@ def run_ours(args):
         "gpu_launches": 8 * args.steps,
         "roofline": roof,
         "stage_ms": {s: round(v, 4) for s, v in mean_ms.items()},
+        "stage_ms_min": {s: round(float(np.min(v)), 4) for s, v in stage_ms.items()},
         "kernel_ms_per_step": {k: round(v, 4) for k, v in per_kernel.items()},
         "clocks": clock,
         "device_status": status,
     }
+    line["fma_probe"] = run_fma_probe(chanfs, local)
     line["helmholtz3d"] = run_helmholtz3d(chanfs, torch, device, plan, rhs, us)
     line["ywalls"] = run_ywalls(chanfs, torch, device, f, dz)
     line["cufft_comparison"] = run_cufft_comparison(torch, f, mean_ms)
@@ -907,6 +972,8 @@ def main(argv=None):
                     help="wall-normal size of the mixed comparison (profiling captures only)")
     ap.add_argument("--mixed-only", action="store_true",
                     help="run only the FP32-refined vs FP64 comparison and print its object")
+    ap.add_argument("--probe-only", action="store_true",
+                    help="measure only the FP64 and FP32 FMA rates (--steps repetitions)")
     ap.add_argument("--nz", type=int, default=0,
                     help="override the wall-normal size (profiling captures only)")
     args = ap.parse_args(argv)
@@ -916,6 +983,8 @@ def main(argv=None):
         return run_reference(args)
     if args.mixed_only:
         return run_mixed_only(args)
+    if args.probe_only:
+        return run_probe_only(args)
     if args.extras_only:
         return run_extras_only(args)
     return run_ours(args)

@@ -47,7 +47,8 @@ typedef enum {
   CFS_EUNSUPPORTED = -3,   /* size outside what the kernels implement */
   CFS_ECUDA = -4,          /* a CUDA runtime call failed */
   CFS_ETIMEOUT = -5,       /* a device-side bounded wait ran out */
-  CFS_ENOTCONVERGED = -6   /* reserved for iterative refinement */
+  CFS_ENOTCONVERGED = -6,  /* iterative refinement missed its tolerance */
+  CFS_ECANCELED = -7       /* a served request was cancelled before it ran */
 } cfs_status;
 
 typedef enum { CFS_BC_NEUMANN = 0, CFS_BC_DIRICHLET = 1 } cfs_bc;   /* z walls */
@@ -350,17 +351,20 @@ int cfs_group_set_graphs(cfs_group_t group, int on);
  * Serving.  The paper has no counterpart.  A server takes Poisson and
  * Helmholtz solve requests from many concurrently running simulations
  * ("runs", one grid each) and answers them with FP32 + FP64-refined solves
- * (tolerance 1e-10, at most 4 FP32 solves).  Each run's plan stays resident in
- * device memory while the budget allows: it is created when a request first
- * needs it (and tuned with cfs_plan_autotune if `autotune`), and the plans of
- * idle runs are destroyed, least recently used first, when a new plan would
- * exceed hbm_budget_bytes.  `workers` threads, each with its own CUDA stream,
- * form batches continuously: a free worker takes the oldest request whose run
- * is idle, adds every pending request of the same kind for other idle runs (up
- * to max_batch), and solves them as one grouped solve; requests arriving
- * meanwhile join the next batch, and batches of different workers overlap on
- * the device.  A result is bit-identical to the refined solve of the run's
- * plan alone.
+ * (tolerance 1e-10, at most 4 FP32 solves).  A run has up to slots_per_run
+ * plans, so that as many of its requests can be solved at the same time;
+ * each plan stays resident in device memory while the budget allows: it is
+ * created when a request first needs it (and tuned with cfs_plan_autotune if
+ * `autotune`), and idle plans are destroyed, least recently used first, when
+ * a new plan would exceed hbm_budget_bytes.  `workers` threads, each with its
+ * own CUDA stream, form batches continuously: a free worker takes the oldest
+ * request whose run has a free plan slot, adds every pending request of the
+ * same kind that finds a free slot (up to max_batch), and solves them as one
+ * grouped solve; requests arriving meanwhile join the next batch, and batches
+ * of different workers overlap on the device.  A result is bit-identical to
+ * the refined solve of the run's plan alone.
+ *   cfs_server_create  CFS_ECUDA if no worker could start (its stream or
+ *       group); workers that cannot start leave, the others serve.
  *   cfs_server_add_run  a grid (as cfs_plan_create); nx % 4 == 0; returns the
  *       run index.  CFS_EUNSUPPORTED if its plan alone exceeds the budget.
  *   cfs_server_submit  kind CFS_REQ_POISSON (c, loc ignored) or
@@ -368,27 +372,45 @@ int cfs_group_set_graphs(cfs_group_t group, int on);
  *       of the run's size, distinct, owned by the caller and left untouched
  *       until the request completes.  Returns a ticket.
  *   cfs_server_wait  waits up to timeout_s seconds (< 0: no limit) for the
- *       ticket; CFS_ETIMEOUT if not done.  On success *status is the solve's
- *       status and *latency_s the time from submission to completion, and the
- *       ticket is retired.
- *   cfs_server_destroy  finishes the pending requests, stops the workers and
- *       destroys the plans.
+ *       ticket; CFS_ETIMEOUT if not done (the ticket stays valid).  On
+ *       success *status is the request's status (a solve's status, the
+ *       status of a plan creation that failed for it, CFS_ECANCELED) and
+ *       *latency_s the time from submission to completion, and the ticket is
+ *       retired.  A failure is the request's own: the others go on.
+ *   cfs_server_cancel  takes a request that no worker has taken yet off the
+ *       queue (it completes with CFS_ECANCELED); CFS_EINVAL if the ticket is
+ *       unknown, already running or done.
+ *   cfs_server_pause  paused != 0: workers form no new batches (running ones
+ *       finish; requests queue); 0 resumes.
+ *   cfs_server_destroy  resumes, finishes the pending requests, stops the
+ *       workers and destroys the plans; tickets never waited for are freed.
+ *   cfs_server_inject_fault  host-side fault injection for tests:
+ *       CFS_FAULT_PLAN_ALLOC makes the next `count` plan creations of server
+ *       S fail with CFS_ENOMEM, as a refused device allocation would;
+ *       CFS_FAULT_WORKER_START (S = NULL) makes the next `count` worker
+ *       start-ups of servers created afterwards fail.
  */
 typedef struct cfs_server* cfs_server_t;
 enum { CFS_REQ_POISSON = 0, CFS_REQ_HELMHOLTZ = 1 };
+enum { CFS_FAULT_PLAN_ALLOC = 1, CFS_FAULT_WORKER_START = 2 };
 typedef struct {
   unsigned long long submitted, completed, failed, batches;
   int max_batch_seen, plans_created, plans_evicted, plans_resident;
   size_t bytes_in_use;  /* plan bytes held (reserved estimates included) */
+  unsigned long long cancelled;
+  int workers_alive, pending;
 } cfs_server_stats_t;
 int cfs_server_create(cfs_server_t* server, size_t hbm_budget_bytes, int workers, int max_batch,
-                      int autotune);
+                      int slots_per_run, int autotune);
 int cfs_server_add_run(cfs_server_t server, int nx, int ny, int nz, double lx, double ly,
                        const double* dz, int poisson_bc, int* run);
 int cfs_server_submit(cfs_server_t server, int run, int kind, double c, int loc, const double* rhs,
                       double* out, unsigned long long* ticket);
 int cfs_server_wait(cfs_server_t server, unsigned long long ticket, double timeout_s, int* status,
                     double* latency_s);
+int cfs_server_cancel(cfs_server_t server, unsigned long long ticket);
+int cfs_server_pause(cfs_server_t server, int paused);
+int cfs_server_inject_fault(cfs_server_t server, int fault, int count);
 int cfs_server_stats(cfs_server_t server, cfs_server_stats_t* stats);
 int cfs_server_destroy(cfs_server_t server);
 
@@ -494,6 +516,20 @@ int cfs_selfcheck_conversions(unsigned long long samples, unsigned long long* mi
  * Waits for the device.
  */
 int cfs_probe_fma(int bits, long long iters, double* fma_per_s, double* ms);
+
+/*
+ * cfs_selftest_wait_timeout -- a test of the failure path, with no
+ * counterpart in the paper.  Every kernel that waits for asynchronous copies
+ * waits a bounded number of polls; when the bound runs out it records
+ * CFS_ETIMEOUT's bit in the status word, waits once more (bounded) for the
+ * copies still in flight and exits without storing.  This queues, on
+ * `stream`, 4 CTAs that go through that same path with `polls` polls
+ * (1 <= polls <= 2^20) on a barrier that no copy completes (no copy is
+ * issued).  The bit lands in the plan's status word (read by cfs_plan_check)
+ * when plan is given, else in the caller's device int `device_status`
+ * (exactly one of the two).  The device stays usable.
+ */
+int cfs_selftest_wait_timeout(cfs_plan_t plan, int* device_status, unsigned polls, void* stream);
 
 /*
  * cfs_plan_check -- wait for the device and report device-side failures

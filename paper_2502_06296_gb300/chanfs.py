@@ -36,9 +36,11 @@ class ServerStats(ctypes.Structure):
                 ("failed", ctypes.c_ulonglong), ("batches", ctypes.c_ulonglong),
                 ("max_batch_seen", ctypes.c_int), ("plans_created", ctypes.c_int),
                 ("plans_evicted", ctypes.c_int), ("plans_resident", ctypes.c_int),
-                ("bytes_in_use", ctypes.c_size_t)]
+                ("bytes_in_use", ctypes.c_size_t), ("cancelled", ctypes.c_ulonglong),
+                ("workers_alive", ctypes.c_int), ("pending", ctypes.c_int)]
 
-OK, EINVAL, ENOMEM, EUNSUPPORTED, ECUDA, ETIMEOUT, ENOTCONVERGED = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ENOMEM, EUNSUPPORTED, ECUDA, ETIMEOUT, ENOTCONVERGED, ECANCELED = 0, -1, -2, -3, -4, -5, -6, -7
+FAULT_PLAN_ALLOC, FAULT_WORKER_START = 1, 2
 
 _lib = None
 
@@ -78,6 +80,7 @@ def lib():
             "cfs_helmholtz_solve_noalloc": ([i, i, i, dp, d, i, i, vp, vp, vp, vp], i),
             "cfs_last_info": ([vp, ctypes.POINTER(i), ctypes.POINTER(d)], i),
             "cfs_probe_fma": ([i, ctypes.c_longlong, dp, dp], i),
+            "cfs_selftest_wait_timeout": ([vp, vp, ctypes.c_uint, vp], i),
             "cfs_group_create": ([ctypes.POINTER(vp), i, ctypes.POINTER(vp)], i),
             "cfs_group_destroy": ([vp], i),
             "cfs_group_size": ([vp, ctypes.POINTER(i)], i),
@@ -98,7 +101,10 @@ def lib():
             "cfs_selfcheck_conversions": ([ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_ulonglong)], i),
             "cfs_group_reserve": ([ctypes.POINTER(vp), i], i),
             "cfs_group_rebind": ([vp, i, ctypes.POINTER(vp), vp], i),
-            "cfs_server_create": ([ctypes.POINTER(vp), ctypes.c_size_t, i, i, i], i),
+            "cfs_server_create": ([ctypes.POINTER(vp), ctypes.c_size_t, i, i, i, i], i),
+            "cfs_server_cancel": ([vp, ctypes.c_ulonglong], i),
+            "cfs_server_pause": ([vp, i], i),
+            "cfs_server_inject_fault": ([vp, i, i], i),
             "cfs_server_add_run": ([vp, i, i, i, d, d, dp, i, ctypes.POINTER(i)], i),
             "cfs_server_submit": ([vp, i, i, d, i, vp, vp, ctypes.POINTER(ctypes.c_ulonglong)], i),
             "cfs_server_wait": ([vp, ctypes.c_ulonglong, d, ctypes.POINTER(i), ctypes.POINTER(d)], i),
@@ -429,10 +435,11 @@ class Server:
     with one CUDA stream each, FP32 + FP64-refined grouped solves."""
 
     def __init__(self, budget_bytes: int, workers: int = 2, max_batch: int = 16,
-                 autotune: bool = True):
+                 autotune: bool = True, slots_per_run: int = 1):
         h = ctypes.c_void_p()
         _check(lib().cfs_server_create(ctypes.byref(h), int(budget_bytes), int(workers),
-                                       int(max_batch), int(bool(autotune))), "cfs_server_create")
+                                       int(max_batch), int(slots_per_run), int(bool(autotune))),
+               "cfs_server_create")
         self._h = h
         self._shapes = []
         self._held = {}
@@ -489,6 +496,19 @@ class Server:
                                      ctypes.byref(lat)), "cfs_server_wait")
         self._held.pop(ticket, None)
         return status.value, lat.value
+
+    def cancel(self, ticket: int) -> None:
+        """Take a request no worker has started off the queue (it completes
+        with ECANCELED); raises if it is unknown, running or done."""
+        _check(lib().cfs_server_cancel(self._h, ticket), "cfs_server_cancel")
+
+    def pause(self, paused: bool = True) -> None:
+        _check(lib().cfs_server_pause(self._h, int(bool(paused))), "cfs_server_pause")
+
+    def inject_fault(self, fault: int, count: int) -> None:
+        """Host-side fault injection (FAULT_PLAN_ALLOC) for tests."""
+        _check(lib().cfs_server_inject_fault(self._h, int(fault), int(count)),
+               "cfs_server_inject_fault")
 
     def stats(self) -> dict:
         st = ServerStats()

@@ -127,6 +127,28 @@ struct PcrBoxT {  // one field of a grouped Algorithm 2 launch; maps 64-byte ali
 using PcrBox = PcrBoxT<float>;     // FP32 inner solves of refinement
 using PcrBox64 = PcrBoxT<double>;  // FP64 solves
 
+// The refined Helmholtz solve in one pass (pcr.cu, pcr_refine_kernel): FP32
+// Algorithm 2 solves and double-float residuals on tiles in shared memory.
+struct PcrRefineArgs {
+  double* u;            // output field (for the face wall row)
+  long long ncols;      // Nx * Ny
+  int n, nparts, nz, face, by, nbox;
+  int maxit;            // FP32 solves per tile at most
+  float tol;            // stop when max|r| <= tol max|rhs| over the tile
+  const float* rows;    // FP32 Algorithm 2 factors, alpha | beta | ib | ap | cp (5n)
+  const float* red;     // FP32 reduced LU, rl | rip | ripc (3 * 2p)
+  const double* abc;    // FP64 rows of I - c L_z: A' | B' | C' (n each)
+  unsigned int* words;  // [0] max |r|, [1] max |rhs| (float bits), [2] most FP32 solves
+};
+
+struct PcrRefineBox {  // one field of a grouped launch; maps 64-byte aligned
+  CUtensorMap in_map;
+  CUtensorMap out_map;
+  PcrRefineArgs a;
+  int* status;
+  int blocks;
+};
+
 #ifdef __CUDACC__
 
 // Box and box-local block of this block; false if the box is masked out.
@@ -164,6 +186,19 @@ cudaError_t launch_pcr_group64(const PcrBox64* boxes, GroupMap g, int total, int
                                size_t smem, cudaStream_t st);
 size_t pcr_group_box64(const cfs_plan* P, const HelmCoef& h, const double* rhs, double* u,
                        PcrBox64* box, int* blocks, int* threads);
+
+// The refined Helmholtz solve in one pass (FP32 Algorithm 2 solves and
+// double-float residuals in shared memory): whether plan P can take it for
+// set h (shared memory, FP32 Algorithm 2 inner solves), and the launches;
+// `words` receives max|r|, max|rhs| (float bits) and the most FP32 solves.
+bool pcr_refine_fits(const cfs_plan* P, const HelmCoef& h);
+size_t pcr_refine_smem(int n, int nparts);
+cudaError_t launch_pcr_refine(const cfs_plan* P, const HelmCoef& h, const double* rhs, double* u,
+                              unsigned int* words, cudaStream_t st);
+size_t pcr_refine_group_box(const cfs_plan* P, const HelmCoef& h, const double* rhs, double* u,
+                            unsigned int* words, PcrRefineBox* box, int* blocks, int* threads);
+cudaError_t launch_pcr_refine_group(const PcrRefineBox* boxes, GroupMap g, int total, int threads,
+                                    size_t smem, cudaStream_t st);
 
 // Thomas sweeps of the Helmholtz systems (helm_thomas.cu): `fp32` boxes are
 // the FP32 inner solves of refinement, the others FP64 solves on the call's

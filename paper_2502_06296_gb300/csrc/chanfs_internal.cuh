@@ -366,6 +366,36 @@ __device__ __forceinline__ void f64_split(double x, float* hi, float* lo) {
   *lo = __uint_as_float(lbits);
 }
 
+// Double-float accumulation on the FP32 units (the refinement residuals).
+struct DoubleFloat {
+  float s, e;
+};
+
+// s + t = a + b exactly (Knuth's TwoSum); the _rn intrinsics keep the
+// compiler from contracting or reassociating the steps.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// acc (+)= (chi + clo) * d; INIT: acc = the product.
+template <bool INIT = false>
+__device__ __forceinline__ void df_acc(DoubleFloat& acc, float chi, float clo, float d) {
+  const float p = __fmul_rn(chi, d);
+  float e = __fmaf_rn(chi, d, -p);  // chi * d - p, exact
+  e = __fmaf_rn(clo, d, e);
+  if (INIT) {
+    acc.s = p;
+    acc.e = e;
+  } else {
+    float s, t;
+    two_sum(acc.s, p, s, t);
+    acc.s = s;
+    acc.e = __fadd_rn(acc.e, __fadd_rn(t, e));
+  }
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }

@@ -2,9 +2,10 @@
 // bounded waits, Tensor Memory Accelerator (cp.async.bulk.tensor) loads and
 // stores, the driver's tensor-map encoder, and per-thread cp.async copies.
 //
-// Every wait is bounded: a wait that runs out returns false, and the caller
-// records kErrTmaTimeout in the plan's status word and leaves the kernel with
-// a CTA-uniform exit, so that no kernel can spin forever.
+// Every wait is bounded: a wait that runs out returns false; cta_wait then
+// records kErrTmaTimeout in the plan's status word, gives the copies still in
+// flight one more bounded wait, and the kernel leaves with a CTA-uniform
+// exit, so that no kernel can spin forever.
 #pragma once
 
 #include "chanfs_internal.cuh"
@@ -30,9 +31,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
 }
 
 // Bounded wait on phase `parity`; returns false if the bound ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          uint32_t polls = kWaitPolls) {
   const uint32_t addr = smem_u32(bar);
-  for (uint32_t it = 0; it < kWaitPolls; ++it) {
+  for (uint32_t it = 0; it < polls; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -43,6 +45,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     if (done) return true;
   }
+  return false;
+}
+
+// Every thread of the CTA waits (bounded) for phase `parity` of `bar`, and the
+// CTA agrees on one outcome.  If any wait ran out, thread 0 records
+// kErrTmaTimeout in *status, every thread waits once more (bounded) so that
+// copies of this phase still in flight land before the CTA's shared memory
+// is released, and false is returned: the caller then exits, CTA-uniformly,
+// storing nothing.  Must be reached by every thread of the CTA.
+__device__ __forceinline__ bool cta_wait(uint64_t* bar, uint32_t parity, int* status,
+                                         uint32_t polls = kWaitPolls) {
+  if (__syncthreads_and(mbar_wait(bar, parity, polls) ? 1 : 0)) return true;
+  if (threadIdx.x == 0) atomicOr(status, kErrTmaTimeout);
+  mbar_wait(bar, parity, polls);
+  __syncthreads();
   return false;
 }
 

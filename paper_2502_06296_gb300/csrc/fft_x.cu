@@ -62,11 +62,7 @@ __device__ __forceinline__ void rfft_x_body(const C* in, void* outv, long long n
   for (int e = threadIdx.x; e < npost; e += blockDim.x) post[e] = postg[e];
   if (!INV)  // the lines past the end of the field transform zeros
     for (int e = valid * M + threadIdx.x; e < lb * M; e += blockDim.x) buf0[e] = zero;
-  const int ok = __syncthreads_and(mbar_wait(bar, 0) ? 1 : 0);
-  if (!ok) {
-    if (threadIdx.x == 0) atomicOr(status, kErrTmaTimeout);
-    return;  // nothing is stored
-  }
+  if (!cta_wait(bar, 0, status)) return;  // nothing is stored
   // work item e of a line-major loop over (line l, index k < npost), stepped
   // by blockDim.x without a division per item
   const int sk = blockDim.x % npost, sl = blockDim.x / npost;

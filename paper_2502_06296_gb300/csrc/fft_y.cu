@@ -162,11 +162,7 @@ __device__ __forceinline__ void fft_y_body(const CUtensorMap* map, const FftDesc
     for (int e = threadIdx.x; e < d.ntw; e += blockDim.x) tw[e] = twg[e];
   // every thread waits (bounded); the CTA then agrees on one outcome, which
   // also publishes the twiddles
-  const int ok = __syncthreads_and(mbar_wait(bar, 0) ? 1 : 0);
-  if (!ok) {
-    if (threadIdx.x == 0) atomicOr(status, kErrTmaTimeout);
-    return;  // no pass ran; nothing is stored
-  }
+  if (!cta_wait(bar, 0, status)) return;  // no pass ran; nothing is stored
   const int ny = d.n;
   // Column kx = 0 of the first tile is the packed pair F(0,ky) + i F(Nx/2,ky)
   // (App. A).  Its y spectrum is stored untangled, App. A's packing applied

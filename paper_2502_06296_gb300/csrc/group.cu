@@ -117,6 +117,13 @@ struct cfs_group {
   int* d_spcr = nullptr;
   HThomasBox* d_hth = nullptr;  // boxes whose Helmholtz systems take Thomas sweeps
   HThomasBox* h_hth = nullptr;
+  PcrRefineBox* d_fus = nullptr;  // boxes refined in one pass (FP32 Algorithm 2 on tiles)
+  PcrRefineBox* h_fus = nullptr;
+  int* d_sfus = nullptr;
+  int* h_sfus = nullptr;
+  unsigned int* d_fwords = nullptr;  // per such box: max|r|, max|rhs|, FP32 solves
+  unsigned int* h_fwords = nullptr;
+  int* h_fused = nullptr;
   int* d_sth32 = nullptr;  // block offsets: FP32 inner Thomas sweeps
   int* d_sth64 = nullptr;  // FP64 direct Thomas sweeps
   int* h_sth32 = nullptr;
@@ -200,10 +207,11 @@ static void group_free(cfs_group* G) {
   void* ptrs[] = {G->d_tab,   G->d_active, G->d_mean, G->d_fmax, G->d_tol,  G->d_maxit,
                   G->d_iters, G->d_rho,    G->d_nactive, G->d_io, G->d_pcr, G->d_hres,
                   G->d_spcr, G->d_pcr64, G->d_spcr64, G->d_zero, G->d_elig, G->d_ctl,
-                  G->d_hth, G->d_sth32, G->d_sth64};
+                  G->d_hth, G->d_sth32, G->d_sth64, G->d_fus, G->d_sfus, G->d_fwords};
   for (void* p : ptrs) cudaFree(p);
-  void* hptrs[] = {G->h_tol, G->h_maxit, G->h_elig, G->h_spcr, G->h_spcr64,
-                   G->h_iters, G->h_rho, G->h_ctl, G->h_hth, G->h_sth32, G->h_sth64};
+  void* hptrs[] = {G->h_tol,   G->h_maxit, G->h_elig, G->h_spcr,  G->h_spcr64, G->h_iters,
+                   G->h_rho,   G->h_ctl,   G->h_hth,  G->h_sth32, G->h_sth64,  G->h_fus,
+                   G->h_sfus,  G->h_fwords, G->h_fused};
   for (void* p : hptrs)
     if (p) cudaFreeHost(p);
   if (G->cap_main) cudaStreamDestroy(G->cap_main);
@@ -257,6 +265,13 @@ static int group_alloc(cfs_group* G, int cap) {
   if (e == cudaSuccess) e = cudaMalloc(&G->d_sth64, sizeof(int) * (cap + 1));
   if (e == cudaSuccess) e = cudaMallocHost(&G->h_sth32, sizeof(int) * (cap + 1));
   if (e == cudaSuccess) e = cudaMallocHost(&G->h_sth64, sizeof(int) * (cap + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_fus, sizeof(PcrRefineBox) * cap);
+  if (e == cudaSuccess) e = cudaMallocHost(&G->h_fus, sizeof(PcrRefineBox) * cap);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_sfus, sizeof(int) * (cap + 1));
+  if (e == cudaSuccess) e = cudaMallocHost(&G->h_sfus, sizeof(int) * (cap + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_fwords, sizeof(unsigned int) * 3 * cap);
+  if (e == cudaSuccess) e = cudaMallocHost(&G->h_fwords, sizeof(unsigned int) * 3 * cap);
+  if (e == cudaSuccess) e = cudaMallocHost(&G->h_fused, sizeof(int) * cap);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&G->cap_main, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&G->cap_body, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G->io_copied, cudaEventDisableTiming);
@@ -667,7 +682,17 @@ static int finish_helm(cfs_group* G, cudaError_t e, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return rc_of(e);
   std::vector<int> fp64(G->nbox);
-  for (int b = 0; b < G->nbox; ++b) fp64[b] = !G->h_elig[b];
+  for (int b = 0; b < G->nbox; ++b) {
+    fp64[b] = !G->h_elig[b] && !G->h_fused[b];
+    if (G->h_fused[b]) {  // refined in one pass: the words its tiles left
+      const unsigned int* w = G->h_fwords + 3 * b;
+      float rmax, amax;
+      memcpy(&rmax, &w[0], sizeof(float));
+      memcpy(&amax, &w[1], sizeof(float));
+      G->h_iters[b] = (int)w[2];
+      G->h_rho[b] = amax > 0.0f ? (double)rmax / (double)amax : 0.0;
+    }
+  }
   return finish(G, fp64.data());
 }
 
@@ -687,9 +712,9 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
   // per-call descriptors.  Boxes whose plans take FP64 Algorithm 2 directly
   // (CFS_OPT_HELM_FP64) run in one FP64 launch; the others are refined
   // together.
-  std::vector<int> blocks(nb, 0), blocks64(nb, 0), bt32(nb, 0), bt64(nb, 0);
-  int threads = 0, threads64 = 0, nref = 0;
-  size_t smem = 0, smem64 = 0, smem_t32 = 0, smem_t64 = 0;
+  std::vector<int> blocks(nb, 0), blocks64(nb, 0), bt32(nb, 0), bt64(nb, 0), bfus(nb, 0);
+  int threads = 0, threads64 = 0, threads_f = 0, nref = 0;
+  size_t smem = 0, smem64 = 0, smem_t32 = 0, smem_t64 = 0, smem_f = 0;
   for (int b = 0; b < nb; ++b) {
     cfs_plan* P = G->plans[b];
     HelmCoef* h = nullptr;
@@ -697,9 +722,17 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
     if (rc) return rc;
     int th = 0;
     G->h_elig[b] = !P->helm_fp64;
+    G->h_fused[b] = G->h_elig[b] && pcr_refine_fits(P, *h);
+    if (G->h_fused[b]) G->h_elig[b] = 0;  // refined in one pass, outside the loop
     nref += G->h_elig[b];
     memset(&G->h_hth[b], 0, sizeof(HThomasBox));
-    if (G->h_elig[b] && P->helm_thomas32) {
+    if (G->h_fused[b]) {
+      const size_t sm = pcr_refine_group_box(P, *h, rhs[b], u[b], G->d_fwords + 3 * b,
+                                             &G->h_fus[b], &bfus[b], &th);
+      if (!sm) return CFS_ECUDA;
+      threads_f = std::max(threads_f, th);
+      smem_f = std::max(smem_f, sm);
+    } else if (G->h_elig[b] && P->helm_thomas32) {
       smem_t32 = std::max(smem_t32, helm_thomas_group_box(P, *h, true, &G->h_hth[b], &bt32[b]));
     } else if (G->h_elig[b]) {
       const size_t sm = pcr_group_box(P, *h, &G->h_pcr[b], &blocks[b], &th);
@@ -721,7 +754,9 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
     G->h_tol[b] = P->tol;
     G->h_maxit[b] = P->maxit;
   }
-  int tpcr = 0, tpcr64 = 0, tt32 = 0, tt64 = 0;
+  int tpcr = 0, tpcr64 = 0, tt32 = 0, tt64 = 0, tfus = 0;
+  const std::vector<int> sfus = offsets(bfus, &tfus);
+  memcpy(G->h_sfus, sfus.data(), sizeof(int) * (nb + 1));
   const std::vector<int> spcr = offsets(blocks, &tpcr), spcr64 = offsets(blocks64, &tpcr64);
   const std::vector<int> st32 = offsets(bt32, &tt32), st64 = offsets(bt64, &tt64);
   memcpy(G->h_spcr, spcr.data(), sizeof(int) * (nb + 1));
@@ -748,6 +783,18 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
       if (r == cudaSuccess)
         r = cudaMemcpyAsync(G->d_sth64, G->h_sth64, sizeof(int) * (nb + 1), kH2D, s);
     }
+    // the boxes refined in one pass: one launch, the result words copied out
+    if (r == cudaSuccess && tfus > 0)
+      r = cudaMemcpyAsync(G->d_fus, G->h_fus, sizeof(PcrRefineBox) * nb, kH2D, s);
+    if (r == cudaSuccess && tfus > 0)
+      r = cudaMemcpyAsync(G->d_sfus, G->h_sfus, sizeof(int) * (nb + 1), kH2D, s);
+    if (r == cudaSuccess && tfus > 0)
+      r = cudaMemsetAsync(G->d_fwords, 0, sizeof(unsigned int) * 3 * nb, s);
+    if (r == cudaSuccess && tfus > 0)
+      r = launch_pcr_refine_group(G->d_fus, GroupMap{G->d_sfus, nullptr, nb}, tfus, threads_f,
+                                  smem_f, s);
+    if (r == cudaSuccess && tfus > 0)
+      r = cudaMemcpyAsync(G->h_fwords, G->d_fwords, sizeof(unsigned int) * 3 * nb, kD2H, s);
     // the FP64 boxes: one launch per method, no refinement
     if (r == cudaSuccess && tpcr64 > 0)
       r = launch_pcr_group64(G->d_pcr64, GroupMap{G->d_spcr64, nullptr, nb}, tpcr64, threads64,
@@ -792,7 +839,7 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
     return r;
   };
 
-  if (nref == 0) {  // FP64 boxes only: no refinement loop
+  if (nref == 0) {  // no box needs the refinement loop (FP64 or one-pass boxes)
     e = head(st);
     for (int b = 0; b < nb; ++b) {
       G->h_iters[b] = 0;
@@ -804,7 +851,8 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
                                       tpcr64,   threads,  threads64,
                                       (long long)smem,    (long long)smem64,
                                       tt32,     tt64,     (long long)smem_t32,
-                                      (long long)smem_t64, G->tres, G->tsub};
+                                      (long long)smem_t64, G->tres, G->tsub,
+                                      tfus,     threads_f, (long long)smem_f};
   cudaGraphExec_t exec = G->graphs ? find_graph(G, sig) : nullptr;
   if (exec || (G->graphs && capture_now(G, sig))) {
     if (!exec) {

@@ -130,6 +130,7 @@ extern "C" const char* cfs_status_string(int s) {
     case CFS_ECUDA: return "CUDA runtime error";
     case CFS_ETIMEOUT: return "device-side wait timed out";
     case CFS_ENOTCONVERGED: return "not converged";
+    case CFS_ECANCELED: return "cancelled";
     default: return "unknown status";
   }
 }

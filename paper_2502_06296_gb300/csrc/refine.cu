@@ -49,36 +49,6 @@ __device__ __forceinline__ void block_sum_to(double v, double* slot) {
   }
 }
 
-// Double-float accumulation on the FP32 units (see the residual update below).
-struct DoubleFloat {
-  float s, e;
-};
-
-// s + t = a + b exactly (Knuth's TwoSum); the _rn intrinsics keep the
-// compiler from contracting or reassociating the steps.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-// acc (+)= (chi + clo) * d; INIT: acc = the product.
-template <bool INIT = false>
-__device__ __forceinline__ void df_acc(DoubleFloat& acc, float chi, float clo, float d) {
-  const float p = __fmul_rn(chi, d);
-  float e = __fmaf_rn(chi, d, -p);  // chi * d - p, exact
-  e = __fmaf_rn(clo, d, e);
-  if (INIT) {
-    acc.s = p;
-    acc.e = e;
-  } else {
-    float s, t;
-    two_sum(acc.s, p, s, t);
-    acc.s = s;
-    acc.e = __fadd_rn(acc.e, __fadd_rn(t, e));
-  }
-}
-
 // ----------------------------------------------------------------------------
 // Start of a refined Poisson solve, one pass over f: r_0 = f as FP32 (the
 // right-hand side of the first FP32 solve), the dz-weighted plane sums of f
@@ -942,8 +912,29 @@ int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st) {
   return (P->last_rho <= P->tol) ? CFS_OK : CFS_ENOTCONVERGED;
 }
 
+// The refined Helmholtz solve in one pass over the field (pcr.cu): one
+// launch, then one read of the three result words (one synchronisation).
+static int refine_helmholtz_fused(cfs_plan* P, const HelmCoef& h, const double* rhs, double* u,
+                                  cudaStream_t st) {
+  unsigned int* words = max_word(P);  // three words at the start of the plan's scratch
+  cudaError_t e = cudaMemsetAsync(words, 0, 3 * sizeof(unsigned int), st);
+  if (e == cudaSuccess) e = launch_pcr_refine(P, h, rhs, u, words, st);
+  unsigned int w[3] = {0u, 0u, 0u};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w, words, sizeof(w), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaErrorInvalidValue) return CFS_EINVAL;
+  if (e != cudaSuccess) return CFS_ECUDA;
+  float rmax, amax;
+  memcpy(&rmax, &w[0], sizeof(float));
+  memcpy(&amax, &w[1], sizeof(float));
+  P->last_iters = (int)w[2];
+  P->last_rho = amax > 0.0f ? (double)rmax / (double)amax : 0.0;
+  return (P->last_rho <= P->tol) ? CFS_OK : CFS_ENOTCONVERGED;
+}
+
 int refine_helmholtz(cfs_plan* P, const HelmCoef& h, const double* rhs, double* u,
                      cudaStream_t st) {
+  if (pcr_refine_fits(P, h)) return refine_helmholtz_fused(P, h, rhs, u, st);
   const long long ncols = (long long)P->nx * P->ny;
   const unsigned grid = (unsigned)((ncols + kResBlock - 1) / kResBlock);
   auto residual = [&](int mode) -> cudaError_t {

@@ -590,12 +590,8 @@ __global__ void __launch_bounds__(2 * TW) thomas_tile_kernel(const __grid_consta
       for (int b = 0; b < nbox; ++b)
         tma_load_3d(tile + (size_t)b * bz * NT, &map, bar, 2 * j0, ky, b * bz);
     }
-    const int ok = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0);
+    if (!cta_wait(bar, phase, status)) return;
     phase ^= 1u;
-    if (!ok) {
-      if (tid == 0) atomicOr(status, kErrTmaTimeout);
-      return;
-    }
     // Singular Neumann column (real part of column 0, slot 0): the
     // dz-weighted mean of its right-hand side (mu) and, through g^T E', that
     // of the pinned solution (nu), reduced over the loaded tile.

@@ -244,30 +244,30 @@ extern "C" int cfs_plan_autotune(cfs_plan_t P, void* stream) {
       const float tt64 = best_ms(st, [&]() { return launch_helm_thomas(P, hc, s64, s64, st); });
       best.helm_thomas = tt64 < tp64;
       t_direct64 = std::min(tp64, tt64);
-      if (fp32) {
-        const float tp32 = best_ms(st, [&]() { return launch_pcr32(P, hc, s32, s32, st); });
-        const float tt32 =
-            best_ms(st, [&]() { return launch_helm_thomas32(P, hc, s32, s32, st); });
-        best.helm_thomas32 = tt32 < tp32;
-      }
     }
     plan_helm_forget(P, kProbeC);
   }
-  // Refined plans: refined Helmholtz against the FP64 direct solve (both meet
+  // Refined plans: the whole refined Helmholtz solve with Algorithm 2 inner
+  // solves (one pass over the field where a tile fits in shared memory) and
+  // with Thomas inner solves, against the FP64 direct solve (all three meet
   // the refinement target), on a constant right-hand side
   best.helm_fp64 = 0;
   if (fp32 && P->nz <= kPcrMaxUnknowns) {
     double* u = nullptr;
     HelmCoef* h = nullptr;
-    P->helm_thomas32 = best.helm_thomas32;
     if (cudaMalloc(&u, sizeof(double) * npts) == cudaSuccess &&
         cudaMemsetAsync(s64, 0x3f, sizeof(double) * npts, st) == cudaSuccess &&
         plan_helm_prepare(P, kProbeC, CFS_LOC_CENTER, best.pcr_parts, &h) == CFS_OK) {
       const HelmCoef hc = *h;
-      const float t32 = best_ms(st, [&]() {
-        return refine_helmholtz(P, hc, s64, u, st) == CFS_OK ? cudaSuccess : cudaErrorUnknown;
-      });
-      best.helm_fp64 = t_direct64 < t32;
+      float t32[2] = {1e30f, 1e30f};
+      for (int th = 0; th < 2; ++th) {
+        P->helm_thomas32 = th;
+        t32[th] = best_ms(st, [&]() {
+          return refine_helmholtz(P, hc, s64, u, st) == CFS_OK ? cudaSuccess : cudaErrorUnknown;
+        });
+      }
+      best.helm_thomas32 = t32[1] < t32[0];
+      best.helm_fp64 = t_direct64 < std::min(t32[0], t32[1]);
     }
     cudaStreamSynchronize(st);
     cudaFree(u);

@@ -33,7 +33,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_version_and_status_strings(lib):
     assert lib.cfs_version() == 100
-    for s in range(-6, 1):
+    for s in range(-7, 1):
         assert chanfs.status_string(s) not in ("", "unknown status")
     assert chanfs.status_string(-99) == "unknown status"
 
@@ -104,3 +104,26 @@ def test_batch_host_entry_point_checks_its_arguments(lib):
     p = (ctypes.c_void_p * 1)(None)
     assert lib.cfs_solve_batch_host(None, 1, i3, None, None, p, p, None) == chanfs.EINVAL
     assert lib.cfs_solve_batch_host(None, -1, None, None, None, None, None, None) == chanfs.EINVAL
+
+
+def test_server_and_selftest_entry_points_check_their_arguments(lib):
+    h = ctypes.c_void_p()
+    assert lib.cfs_server_create(None, 1 << 30, 1, 1, 1, 0) == chanfs.EINVAL
+    assert lib.cfs_server_create(ctypes.byref(h), 1 << 30, 0, 1, 1, 0) == chanfs.EINVAL
+    assert lib.cfs_server_create(ctypes.byref(h), 1 << 30, 1, 1, 0, 0) == chanfs.EINVAL
+    assert lib.cfs_server_create(ctypes.byref(h), 1 << 30, 1, 1, 17, 0) == chanfs.EINVAL
+    assert lib.cfs_server_cancel(None, 1) == chanfs.EINVAL
+    assert lib.cfs_server_pause(None, 1) == chanfs.EINVAL
+    assert lib.cfs_server_inject_fault(None, chanfs.FAULT_PLAN_ALLOC, 1) == chanfs.EINVAL
+    assert lib.cfs_server_inject_fault(None, chanfs.FAULT_WORKER_START, -1) == chanfs.EINVAL
+    # exactly one of plan and device_status; polls within range
+    assert lib.cfs_selftest_wait_timeout(None, None, 100, None) == chanfs.EINVAL
+    assert lib.cfs_selftest_wait_timeout(None, ctypes.c_void_p(16), 0, None) == chanfs.EINVAL
+    assert lib.cfs_selftest_wait_timeout(None, ctypes.c_void_p(16), (1 << 20) + 1, None) == chanfs.EINVAL
+
+
+def test_probe_checks_its_arguments(lib):
+    rate = ctypes.c_double(0.0)
+    assert lib.cfs_probe_fma(16, 100, ctypes.byref(rate), None) == chanfs.EINVAL
+    assert lib.cfs_probe_fma(64, 0, ctypes.byref(rate), None) == chanfs.EINVAL
+    assert lib.cfs_probe_fma(64, 100, None, None) == chanfs.EINVAL

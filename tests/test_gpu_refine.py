@@ -192,6 +192,51 @@ def test_refined_helmholtz_matches_fp64_oracle(chanfs, nx, ny, nz, beta, loc, c)
         assert np.array_equal(host(t), u)
 
 
+# The refined Helmholtz solve runs in one pass (FP32 Algorithm 2 and
+# double-float residuals on tiles in shared memory) where a tile fits, else
+# as the loop of FP32 solves and FP64 residual passes (long columns, or FP32
+# Thomas inner solves).  Both against the oracle, with partition counts,
+# ragged tiles, both locations, a coefficient far from the identity, and
+# the outcome reported when the target is missed.
+ONE_PASS = [
+    (12, 9, 64, 2.2, 0, 1e-4, 0),     # ragged last tile (108 columns), c/h^2 large
+    (16, 12, 192, 1.2, 1, 1e-6, 6),
+    (32, 24, 384, 1.8, 0, 9.615e-9, 16),
+    (8, 4, 600, 1.8, 1, 3e-5, 24),
+    (12, 9, 100, 1.5, 0, 1e-2, 3),    # far from the identity: several FP32 solves
+    (8, 6, 900, 1.8, 0, 1e-5, 0),     # too long for one pass: the loop
+]
+
+
+@pytest.mark.parametrize("nx,ny,nz,beta,loc,c,nparts", ONE_PASS)
+def test_refined_helmholtz_one_pass_matches_oracle(chanfs, nx, ny, nz, beta, loc, c, nparts):
+    dz = synth.tanh_dz(nz, beta)
+    rhs = synth.normal(3 * nz + loc, (nz, ny, nx))
+    ref = oracle.helmholtz_solve(rhs, dz, c, loc)
+    with chanfs.Plan(nx, ny, nz, 1.0, 1.0, dz, 0, chanfs.F32_REFINED) as plan:
+        plan.set_option(chanfs.OPT_PCR_PARTS, nparts)
+        u = host(plan.helmholtz_solve(c, dev(rhs), loc))
+        iters, rho = plan.last_info()
+        assert rho <= TOL and 1 <= iters <= 4, (iters, rho)
+        assert rel(u, ref) < TOL, rel(u, ref)
+        # the reported residual against the oracle's operator
+        r = rhs - oracle.apply_helmholtz(u, dz, c, loc)
+        if loc == 1:
+            r[-1] = 0.0
+            assert np.all(u[-1] == 0.0)
+        assert np.max(np.abs(r)) / np.max(np.abs(rhs)) < 2 * TOL
+        # zero right-hand side, and a tolerance one FP32 solve cannot meet
+        z = host(plan.helmholtz_solve(c, torch.zeros_like(dev(rhs)), loc))
+        assert np.all(z == 0.0) and plan.last_info()[1] == 0.0
+        plan.set_refinement(1e-14, 1)
+        with pytest.raises(chanfs.ChanfsError) as err:
+            plan.helmholtz_solve(c, dev(rhs), loc)
+        assert err.value.status == chanfs.ENOTCONVERGED
+        iters, rho = plan.last_info()
+        assert iters == 1 and 1e-14 < rho < 1e-3
+        assert plan.check() == 0
+
+
 @pytest.mark.slow
 def test_refined_precision_workload_full_size(chanfs):
     """The 1024 x 768 x 512 uniform precision workload in the launch

@@ -61,8 +61,8 @@ def alone(chanfs, req):
         return host(out)
 
 
-def serve(chanfs, reqs, budget, workers=3, max_batch=8):
-    with chanfs.Server(budget, workers, max_batch, autotune=False) as srv:
+def serve(chanfs, reqs, budget, workers=3, max_batch=8, slots=1):
+    with chanfs.Server(budget, workers, max_batch, autotune=False, slots_per_run=slots) as srv:
         for nx, ny, nz, beta, bc in RUNS:
             srv.add_run(nx, ny, nz, 12.8, 6.4, synth.tanh_dz(nz, beta), bc)
         ins = [torch.from_numpy(q[4]).cuda() for q in reqs]
@@ -93,6 +93,21 @@ def test_server_results_are_the_same_in_the_mix_as_alone(chanfs):
         assert np.max(np.abs(g - ref)) / np.max(np.abs(ref)) < 1e-10
 
 
+def test_server_solves_several_requests_of_one_run_at_once(chanfs):
+    """With three plan slots per run, requests of the same run are solved in
+    one batch (or overlapping batches); every result is still bit-identical to
+    the run's plan alone."""
+    reqs = [q for q in requests(chanfs) if q[0] in (0, 2)]
+    reqs = reqs + [(r, k, c, loc, f[::-1].copy()) for r, k, c, loc, f in reqs]  # more per run
+    got, results, stats = serve(chanfs, reqs, budget=8 << 30, workers=2, max_batch=8, slots=3)
+    assert all(s == 0 for s, _ in results), results
+    assert stats["completed"] == len(reqs) and stats["failed"] == 0
+    assert stats["plans_created"] > 2  # more than one plan for a run
+    assert stats["plans_resident"] <= 6
+    for q, g in zip(reqs, got):
+        assert np.array_equal(g, alone(chanfs, q))
+
+
 def test_server_evicts_plans_under_a_small_budget(chanfs):
     reqs = requests(chanfs)
     # room for about two plans of these sizes at a time
@@ -120,6 +135,9 @@ def test_server_rejects_bad_requests(chanfs):
         assert lib.cfs_server_submit(srv._h, run, 1, 1e-5, 7, px, py, ctypes.byref(t)) == chanfs.EINVAL
         assert lib.cfs_server_submit(srv._h, run, 0, 0.0, 0, px, px, ctypes.byref(t)) == chanfs.EINVAL
         assert lib.cfs_server_submit(srv._h, run, 3, 0.0, 0, px, py, ctypes.byref(t)) == chanfs.EINVAL
+        assert lib.cfs_server_cancel(srv._h, 987654) == chanfs.EINVAL
+        assert lib.cfs_server_inject_fault(srv._h, 99, 1) == chanfs.EINVAL
+        assert lib.cfs_server_inject_fault(srv._h, chanfs.FAULT_WORKER_START, 1) == chanfs.EINVAL
         ticket = srv.submit(run, chanfs.REQ_POISSON, x, y)
         assert srv.wait(ticket, 60.0)[0] == 0
         assert np.all(host(y) == 0.0)  # zero right-hand side
