@@ -167,6 +167,48 @@ __host__ __device__ inline void alg2_reduced_factor(int J, const double* sub, co
   }
 }
 
+// The reduced system solved in parallel instead (Step 3 again): parallel
+// cyclic reduction.  At level l (stride s = 2^l) row j takes away s-away rows
+// j - s and j + s with the multipliers k1_j = sub_j / diag_{j-s} and
+// k2_j = sup_j / diag_{j+s} (zero where the neighbour lies outside), which
+// leaves it coupled to rows j -+ 2s only:
+//   sub'_j = -k1_j sub_{j-s},  sup'_j = -k2_j sup_{j+s},
+//   diag'_j = diag_j - k1_j sup_{j-s} - k2_j sub_{j+s};
+// after ceil(log2 J) levels every row is decoupled.  The multipliers depend
+// on the matrix only, so they are computed once: k1 at K1[l*J + j], k2 at
+// K2[l*J + j], and the final 1/diag_j at ib[j].  At run time a level is
+//   y_j <- y_j - k1_j y_{j-s} - k2_j y_{j+s}   (all j at once),
+// and x_j = ib_j y_j.  sub, diag, sup are overwritten.
+__host__ __device__ inline int alg2_pcr_levels(int J) {
+  int l = 0;
+  while ((1 << l) < J) ++l;
+  return l;
+}
+
+__host__ __device__ inline void alg2_reduced_pcr(int J, double* sub, double* diag, double* sup,
+                                                 double* na, double* nb, double* nc, double* K1,
+                                                 double* K2, double* ib) {
+  const int L = alg2_pcr_levels(J);
+  for (int l = 0, st = 1; l < L; ++l, st <<= 1) {
+    for (int j = 0; j < J; ++j) {
+      const bool lo = j - st >= 0, hi = j + st < J;
+      const double k1 = lo ? sub[j] / diag[j - st] : 0.0;
+      const double k2 = hi ? sup[j] / diag[j + st] : 0.0;
+      K1[l * J + j] = k1;
+      K2[l * J + j] = k2;
+      na[j] = lo ? -k1 * sub[j - st] : 0.0;
+      nc[j] = hi ? -k2 * sup[j + st] : 0.0;
+      nb[j] = diag[j] - (lo ? k1 * sup[j - st] : 0.0) - (hi ? k2 * sub[j + st] : 0.0);
+    }
+    for (int j = 0; j < J; ++j) {
+      sub[j] = na[j];
+      diag[j] = nb[j];
+      sup[j] = nc[j];
+    }
+  }
+  for (int j = 0; j < J; ++j) ib[j] = 1.0 / diag[j];
+}
+
 }  // namespace chanfs
 
 #endif  // CHANFS_ALG2_CUH

@@ -138,6 +138,8 @@ struct PcrRefineArgs {
   const float* rows;    // FP32 Algorithm 2 factors, alpha | beta | ib | ap | cp (5n)
   const float* red;     // FP32 reduced LU, rl | rip | ripc (3 * 2p)
   const double* abc;    // FP64 rows of I - c L_z: A' | B' | C' (n each)
+  const float* lv;      // reduced system by parallel cyclic reduction: K1 | K2 | 1/diag
+  int nlv;              // its levels, ceil(log2 2p)
   unsigned int* words;  // [0] max |r|, [1] max |rhs| (float bits), [2] most FP32 solves
 };
 
@@ -195,10 +197,17 @@ bool pcr_refine_fits(const cfs_plan* P, const HelmCoef& h);
 size_t pcr_refine_smem(int n, int nparts);
 cudaError_t launch_pcr_refine(const cfs_plan* P, const HelmCoef& h, const double* rhs, double* u,
                               unsigned int* words, cudaStream_t st);
+// Rows per thread of the kernel instance set h needs (8, 16, 24, 32; 0: none
+// fits), and the threads a CTA of that instance may have.  A grouped launch
+// runs one instance: `rows` (the largest of its boxes') selects it.
+constexpr int kPcrTileColumns = 16;  // columns of an Algorithm 2 tile (one half-warp)
+int pcr_refine_rows(const HelmCoef& h);
+int pcr_refine_thread_limit(int rows);
 size_t pcr_refine_group_box(const cfs_plan* P, const HelmCoef& h, const double* rhs, double* u,
-                            unsigned int* words, PcrRefineBox* box, int* blocks, int* threads);
+                            unsigned int* words, PcrRefineBox* box, int* blocks, int* threads,
+                            int* rows);
 cudaError_t launch_pcr_refine_group(const PcrRefineBox* boxes, GroupMap g, int total, int threads,
-                                    size_t smem, cudaStream_t st);
+                                    size_t smem, int rows, cudaStream_t st);
 
 // Thomas sweeps of the Helmholtz systems (helm_thomas.cu): `fp32` boxes are
 // the FP32 inner solves of refinement, the others FP64 solves on the call's

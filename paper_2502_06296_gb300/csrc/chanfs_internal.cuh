@@ -80,6 +80,8 @@ struct HelmCoef {
   double* d_abc;   // 3*n doubles: A' | B' | C' of I - c L_z (refinement residual)
   double* d_th;    // 3*n doubles: Thomas factors fs | fa | fc of I - c L_z
   float* d_th32;   // FP32 copies (refined plans)
+  float* d_lv32;   // refined plans: parallel reduction of the reduced system,
+                   // K1 (L x 2p) | K2 (L x 2p) | 1/diag (2p), L = ceil(log2 2p)
   unsigned long long stamp;
 };
 

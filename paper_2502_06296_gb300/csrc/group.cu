@@ -713,22 +713,33 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
   // (CFS_OPT_HELM_FP64) run in one FP64 launch; the others are refined
   // together.
   std::vector<int> blocks(nb, 0), blocks64(nb, 0), bt32(nb, 0), bt64(nb, 0), bfus(nb, 0);
-  int threads = 0, threads64 = 0, threads_f = 0, nref = 0;
+  int threads = 0, threads64 = 0, threads_f = 0, nref = 0, rows_f = 0;
   size_t smem = 0, smem64 = 0, smem_t32 = 0, smem_t64 = 0, smem_f = 0;
+  // boxes refined in one pass share one kernel instance: the most rows per
+  // thread any of them needs; a box with more threads than that instance
+  // allows takes the loop instead
+  std::vector<HelmCoef*> hs(nb, nullptr);
   for (int b = 0; b < nb; ++b) {
     cfs_plan* P = G->plans[b];
-    HelmCoef* h = nullptr;
-    int rc = plan_helm_prepare(P, c[b], loc[b], 0, &h);
+    int rc = plan_helm_prepare(P, c[b], loc[b], 0, &hs[b]);
     if (rc) return rc;
+    if (!P->helm_fp64 && pcr_refine_fits(P, *hs[b]))
+      rows_f = std::max(rows_f, pcr_refine_rows(*hs[b]));
+  }
+  for (int b = 0; b < nb; ++b) {
+    cfs_plan* P = G->plans[b];
+    HelmCoef* h = hs[b];
     int th = 0;
     G->h_elig[b] = !P->helm_fp64;
-    G->h_fused[b] = G->h_elig[b] && pcr_refine_fits(P, *h);
+    G->h_fused[b] = G->h_elig[b] && pcr_refine_fits(P, *h) &&
+                    kPcrTileColumns * h->nparts <= pcr_refine_thread_limit(rows_f);
     if (G->h_fused[b]) G->h_elig[b] = 0;  // refined in one pass, outside the loop
     nref += G->h_elig[b];
     memset(&G->h_hth[b], 0, sizeof(HThomasBox));
     if (G->h_fused[b]) {
+      int rows_b = 0;
       const size_t sm = pcr_refine_group_box(P, *h, rhs[b], u[b], G->d_fwords + 3 * b,
-                                             &G->h_fus[b], &bfus[b], &th);
+                                             &G->h_fus[b], &bfus[b], &th, &rows_b);
       if (!sm) return CFS_ECUDA;
       threads_f = std::max(threads_f, th);
       smem_f = std::max(smem_f, sm);
@@ -792,7 +803,7 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
       r = cudaMemsetAsync(G->d_fwords, 0, sizeof(unsigned int) * 3 * nb, s);
     if (r == cudaSuccess && tfus > 0)
       r = launch_pcr_refine_group(G->d_fus, GroupMap{G->d_sfus, nullptr, nb}, tfus, threads_f,
-                                  smem_f, s);
+                                  smem_f, rows_f, s);
     if (r == cudaSuccess && tfus > 0)
       r = cudaMemcpyAsync(G->h_fwords, G->d_fwords, sizeof(unsigned int) * 3 * nb, kD2H, s);
     // the FP64 boxes: one launch per method, no refinement
@@ -852,7 +863,7 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
                                       (long long)smem,    (long long)smem64,
                                       tt32,     tt64,     (long long)smem_t32,
                                       (long long)smem_t64, G->tres, G->tsub,
-                                      tfus,     threads_f, (long long)smem_f};
+                                      tfus,     threads_f, (long long)smem_f, rows_f};
   cudaGraphExec_t exec = G->graphs ? find_graph(G, sig) : nullptr;
   if (exec || (G->graphs && capture_now(G, sig))) {
     if (!exec) {

@@ -19,34 +19,28 @@
 // for every column, are staged once per CTA and read as broadcasts.  CTAs are
 // persistent over tiles; several CTAs per SM overlap one CTA's serial phases
 // (copies, the reduced solve) with another's arithmetic.
+#include "chanfs_alg2.cuh"
 #include "chanfs_tma.cuh"
 #include "chanfs_group.cuh"
 
 namespace chanfs {
 
-constexpr int kPcrCols = 16;  // columns per tile (one half-warp)
+constexpr int kPcrCols = kPcrTileColumns;  // columns per tile (one half-warp)
 
 
 // Steps 2-4 of Algorithm 2 on a tile T [rows][16] in shared memory, in place:
 // the thread of column threadIdx.x % 16 and partition q (rows s .. s+m-1;
 // `part` false for threads beyond the partitions) reduces its right-hand
-// side, 16 lanes solve the reduced systems, and every partition is
-// reconstructed.  s_x holds the 2p boundary values of each column.  Every
-// thread of the CTA calls it (it contains the CTA barriers).
+// side (Step 2), 16 lanes solve the reduced systems (Step 3), and every
+// partition is reconstructed (Step 4).  s_x holds the 2p boundary values of
+// each column, [2p][16].
 template <class R>
-__device__ __forceinline__ void pcr_steps(R* T, R* s_x, const R* s_rows, const R* s_red, int n,
-                                          int J, int q, bool part, int s, int m) {
+__device__ __forceinline__ void pcr_step2(R* T, R* s_x, const R* s_rows, int n, int q, bool part,
+                                          int s, int m) {
   const R* alpha = s_rows;
   const R* beta = s_rows + n;
-  const R* ib = s_rows + 2 * n;
-  const R* ap = s_rows + 3 * n;
-  const R* cp = s_rows + 4 * n;
-  const R* rl = s_red;
-  const R* rip = s_red + J;
-  const R* ripc = s_red + 2 * J;
   const int c = threadIdx.x % kPcrCols;
   R* col = T + c;  // element (row r) at col[r * 16]
-  // Step 2: forward then backward reduction of d only
   if (part) {
     R prev = col[(s + 1) * kPcrCols];
     for (int i = 2; i < m; ++i) {
@@ -63,8 +57,15 @@ __device__ __forceinline__ void pcr_steps(R* T, R* s_x, const R* s_rows, const R
     s_x[(2 * q) * kPcrCols + c] = col[s * kPcrCols];
     s_x[(2 * q + 1) * kPcrCols + c] = col[(s + m - 1) * kPcrCols];
   }
-  __syncthreads();
-  // Step 3: reduced system [x_0^0, x_{m-1}^0, x_0^1, ...], one lane per column
+}
+
+// Step 3 by the LU factors of the reduced system, one lane per column.
+template <class R>
+__device__ __forceinline__ void pcr_step3_lu(R* s_x, const R* s_red, int J) {
+  const R* rl = s_red;
+  const R* rip = s_red + J;
+  const R* ripc = s_red + 2 * J;
+  const int c = threadIdx.x % kPcrCols;
   if (threadIdx.x < kPcrCols) {
     R y = s_x[c];
     for (int jj = 1; jj < J; ++jj) {
@@ -78,8 +79,16 @@ __device__ __forceinline__ void pcr_steps(R* T, R* s_x, const R* s_rows, const R
       s_x[jj * kPcrCols + c] = x;
     }
   }
-  __syncthreads();
-  // Step 4: reconstruction in place
+}
+
+template <class R>
+__device__ __forceinline__ void pcr_step4(R* T, const R* s_x, const R* s_rows, int n, int q,
+                                          bool part, int s, int m) {
+  const R* ib = s_rows + 2 * n;
+  const R* ap = s_rows + 3 * n;
+  const R* cp = s_rows + 4 * n;
+  const int c = threadIdx.x % kPcrCols;
+  R* col = T + c;
   if (part) {
     const R x0 = s_x[(2 * q) * kPcrCols + c];
     const R xm = s_x[(2 * q + 1) * kPcrCols + c];
@@ -90,6 +99,45 @@ __device__ __forceinline__ void pcr_steps(R* T, R* s_x, const R* s_rows, const R
       col[r * kPcrCols] = fma(-cp[r], xm, fma(-ap[r], x0, ib[r] * col[r * kPcrCols]));
     }
   }
+}
+
+// Every thread of the CTA calls it (it contains the CTA barriers).
+template <class R>
+__device__ __forceinline__ void pcr_steps(R* T, R* s_x, const R* s_rows, const R* s_red, int n,
+                                          int J, int q, bool part, int s, int m) {
+  pcr_step2<R>(T, s_x, s_rows, n, q, part, s, m);
+  __syncthreads();
+  pcr_step3_lu<R>(s_x, s_red, J);
+  __syncthreads();
+  pcr_step4<R>(T, s_x, s_rows, n, q, part, s, m);
+}
+
+// Step 3 by parallel cyclic reduction with the precomputed multipliers
+// (K1 | K2 | 1/diag, see alg2_reduced_pcr), every thread of the CTA taking
+// (row, column) items of the 2p x 16 boundary values; ping-pong between s_x
+// and s_y.  The solution ends in s_x.  Contains CTA barriers.
+__device__ __forceinline__ void pcr_step3_pcr(float* s_x, float* s_y, const float* s_lv, int J,
+                                              int L) {
+  const float* K1 = s_lv;
+  const float* K2 = s_lv + L * J;
+  const float* ib = s_lv + 2 * L * J;
+  const int items = J * kPcrCols;
+  float* a = s_x;
+  float* b = s_y;
+  for (int l = 0, st = 1; l < L; ++l, st <<= 1) {
+    for (int e = threadIdx.x; e < items; e += blockDim.x) {
+      const int j = e / kPcrCols, c = e % kPcrCols;
+      float y = a[e];
+      if (j - st >= 0) y = fmaf(-K1[l * J + j], a[(j - st) * kPcrCols + c], y);
+      if (j + st < J) y = fmaf(-K2[l * J + j], a[(j + st) * kPcrCols + c], y);
+      b[e] = y;
+    }
+    __syncthreads();
+    float* t = a;
+    a = b;
+    b = t;
+  }
+  for (int e = threadIdx.x; e < items; e += blockDim.x) s_x[e] = ib[e / kPcrCols] * a[e];
 }
 
 // Tiles tile0, tile0 + tstride, ... of one field.  Threads beyond the
@@ -173,14 +221,20 @@ __global__ void __launch_bounds__(1024) pcr_group_kernel(const PcrBoxT<R>* boxes
 // ----------------------------------------------------------------------------
 // The refined Helmholtz solve in one pass over the field.  The z-implicit
 // operator couples only the rows of one (x, y) column, and a tile holds whole
-// columns, so iterative refinement runs entirely in shared memory: per tile
-//   W = fl32(rhs);  repeat { W = FP32 Algorithm 2 solve of W;  u += W;
-//                            r = r - (I - c L_z) W;  W = fl32(r) }
+// columns, so iterative refinement runs entirely on chip: per tile
+//   w = fl32(rhs);  repeat { w = FP32 Algorithm 2 solve of w;  u += w;
+//                            r = r - (I - c L_z) w;  w = fl32(r) }
 // with r (initially rhs) and u kept as double-float pairs and the operator's
 // FP64 rows split into hi + lo, until max|r| <= tol max|rhs| over the tile
 // (a bound at least as strict as the same test over the whole field) or
-// maxit FP32 solves.  HBM traffic is one FP64 read and one FP64 write per
-// point; the only FP64 instruction is the final hi + lo of each u.
+// maxit FP32 solves.  The thread of column c and partition q keeps its
+// partition's rows of w and u in registers (at most MM rows), so the
+// recurrences of Algorithm 2 run without shared-memory latency; r lives in
+// the FP64 tile the copies use (as a float pair per element), the reduced
+// system is solved by parallel cyclic reduction over the whole CTA, and the
+// residual's neighbours across a partition end are the reduced system's
+// solution itself.  HBM traffic is one FP64 read and one FP64 write per point;
+// the only FP64 instruction is the final hi + lo of each u.
 // ----------------------------------------------------------------------------
 
 // *slot = max(*slot, v) over the CTA (v >= 0; floats order like their bits).
@@ -198,6 +252,11 @@ __device__ __forceinline__ float2 df_sub(float bh, float bl, const DoubleFloat& 
   return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
 }
 
+// Threads per CTA of the one-pass kernel holding at most MM rows per thread
+// (three registers per row: the correction and u as a pair).
+template <int MM> struct refine_threads { static constexpr int value = MM <= 16 ? 512 : 256; };
+
+template <int MM>
 __device__ __forceinline__ void pcr_refine_body(const CUtensorMap* in_map,
                                                 const CUtensorMap* out_map,
                                                 const PcrRefineArgs& a, int* status,
@@ -210,19 +269,19 @@ __device__ __forceinline__ void pcr_refine_body(const CUtensorMap* in_map,
   // slot is cleared only after every thread has read it)
   unsigned int* s_max = reinterpret_cast<unsigned int*>(smem_raw + 16);
   double* Rt = reinterpret_cast<double*>(smem_raw + 128);  // [rows_alloc][16]: rhs, r, u
-  float2* U = reinterpret_cast<float2*>(Rt + rows_alloc * kPcrCols);  // [n][16] u (hi, lo)
-  float* W = reinterpret_cast<float*>(U + n * kPcrCols);             // [n][16] FP32 work
-  float* s_rows = W + n * kPcrCols;                                  // 5n
-  float* s_red = s_rows + 5 * n;                                     // 3J
-  float* s_op = s_red + 3 * J;                                       // 6n: A', B', C' hi, lo
-  float* s_x = s_op + 6 * n;                                         // J x 16
+  float2* Rp = reinterpret_cast<float2*>(Rt);               // the same slots as (hi, lo)
+  float* s_rows = reinterpret_cast<float*>(Rt + rows_alloc * kPcrCols);  // 5n
+  float* s_op = s_rows + 5 * n;                 // 6n: A', B', C' as (hi, lo)
+  float* s_x = s_op + 6 * n;                    // J x 16
+  float* s_y = s_x + J * kPcrCols;              // J x 16
+  float* s_lv = s_y + J * kPcrCols;             // (2L + 1) J
 
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     mbar_init_fence();
   }
   for (int e = threadIdx.x; e < 5 * n; e += blockDim.x) s_rows[e] = a.rows[e];
-  for (int e = threadIdx.x; e < 3 * J; e += blockDim.x) s_red[e] = a.red[e];
+  for (int e = threadIdx.x; e < (2 * a.nlv + 1) * J; e += blockDim.x) s_lv[e] = a.lv[e];
   for (int e = threadIdx.x; e < 3 * n; e += blockDim.x) {
     float hi, lo;
     f64_split(a.abc[e], &hi, &lo);
@@ -230,6 +289,11 @@ __device__ __forceinline__ void pcr_refine_body(const CUtensorMap* in_map,
     s_op[2 * e + 1] = lo;
   }
   __syncthreads();
+  const float* alpha = s_rows;
+  const float* beta = s_rows + n;
+  const float* ib = s_rows + 2 * n;
+  const float* ap = s_rows + 3 * n;
+  const float* cp = s_rows + 4 * n;
   const float* opA = s_op;
   const float* opB = s_op + 2 * n;
   const float* opC = s_op + 4 * n;
@@ -238,10 +302,11 @@ __device__ __forceinline__ void pcr_refine_body(const CUtensorMap* in_map,
   const int q = threadIdx.x / kPcrCols;
   const bool part = q < a.nparts;
   const int s = (int)(((long long)q * n) / a.nparts);
-  const int m = (int)(((long long)(q + 1) * n) / a.nparts) - s;
+  const int m = part ? (int)(((long long)(q + 1) * n) / a.nparts) - s : 0;
   const long long ntiles = (a.ncols + kPcrCols - 1) / kPcrCols;
   const uint32_t tile_bytes = (uint32_t)(a.nbox * a.by * kPcrCols * sizeof(double));
   uint32_t phase = 0;
+  float w[MM], uh[MM], ul[MM];
 
   for (long long tile = tile0; tile < ntiles; tile += tstride) {
     const int col0 = (int)(tile * kPcrCols);
@@ -255,73 +320,100 @@ __device__ __forceinline__ void pcr_refine_body(const CUtensorMap* in_map,
     phase ^= 1u;
     // the first FP32 right-hand side and the tile's max|rhs|
     float amax = 0.0f;
-    if (part)
-      for (int i = 0; i < m; ++i) {
-        const int e = (s + i) * kPcrCols + c;
-        const float h = f64_to_f32(Rt[e]);
-        W[e] = h;
-        amax = fmaxf(amax, fabsf(h));
+#pragma unroll
+    for (int i = 0; i < MM; ++i)
+      if (i < m) {
+        w[i] = f64_to_f32(Rt[(s + i) * kPcrCols + c]);
+        amax = fmaxf(amax, fabsf(w[i]));
       }
     cta_max_to(amax, s_max);
     int it = 0;
     for (;;) {
-      pcr_steps<float>(W, s_x, s_rows, s_red, n, J, q, part, s, m);
-      __syncthreads();  // every correction of the tile is in W
-      // u += delta and r -= (I - c L_z) delta in double-float (on the first
-      // pass u = delta and r = rhs - (I - c L_z) delta, rhs split from FP64)
+      // Step 2 in registers: the partition's two boundary values to s_x
+      if (m > 0) {
+        // (the last row's value is kept on the way: a select of w[m - 1] by
+        // a run-time index would move w to local memory)
+        float wl = w[0];
+#pragma unroll
+        for (int i = 2; i < MM; ++i)
+          if (i < m) {
+            w[i] = fmaf(-alpha[s + i], w[i - 1], w[i]);
+            wl = w[i];
+          }
+#pragma unroll
+        for (int i = MM - 3; i >= 0; --i)
+          if (i <= m - 3) w[i] = fmaf(-beta[s + i], w[i + 1], w[i]);
+        s_x[(2 * q) * kPcrCols + c] = w[0];
+        s_x[(2 * q + 1) * kPcrCols + c] = wl;
+      }
+      __syncthreads();
+      pcr_step3_pcr(s_x, s_y, s_lv, J, a.nlv);  // Step 3, the whole CTA
+      __syncthreads();
+      // Step 4 in registers, then u += w and r -= (I - c L_z) w in
+      // double-float; the neighbours beyond the partition's ends are the
+      // neighbouring partitions' end values, solved in Step 3
       float rmax = 0.0f;
-      if (part)
-        for (int i = 0; i < m; ++i) {
-          const int r = s + i, e = r * kPcrCols + c;
-          const float d = W[e];
-          DoubleFloat acc;
-          df_acc<true>(acc, opB[2 * r], opB[2 * r + 1], d);
-          if (r > 0) df_acc(acc, opA[2 * r], opA[2 * r + 1], W[e - kPcrCols]);
-          if (r < n - 1) df_acc(acc, opC[2 * r], opC[2 * r + 1], W[e + kPcrCols]);
-          float bh, bl;
-          if (it == 0) {
-            f64_split(Rt[e], &bh, &bl);
-          } else {
-            const float2 rb = reinterpret_cast<const float2*>(Rt)[e];
-            bh = rb.x;
-            bl = rb.y;
+      if (m > 0) {
+        const float x0 = s_x[(2 * q) * kPcrCols + c], xm = s_x[(2 * q + 1) * kPcrCols + c];
+        const float below = q > 0 ? s_x[(2 * q - 1) * kPcrCols + c] : 0.0f;
+        const float above = q + 1 < a.nparts ? s_x[(2 * q + 2) * kPcrCols + c] : 0.0f;
+#pragma unroll
+        for (int i = 0; i < MM; ++i)
+          if (i < m) {
+            const int r = s + i;
+            w[i] = (i == 0) ? x0
+                 : (i == m - 1) ? xm
+                 : fmaf(-cp[r], xm, fmaf(-ap[r], x0, ib[r] * w[i]));
           }
-          const float2 rn = df_sub(bh, bl, acc);
-          reinterpret_cast<float2*>(Rt)[e] = rn;
-          rmax = fmaxf(rmax, fabsf(rn.x));
-          if (it == 0) {
-            U[e] = make_float2(d, 0.0f);
-          } else {
-            const float2 uo = U[e];
-            float us, ut;
-            two_sum(uo.x, d, us, ut);
-            const float ue = __fadd_rn(uo.y, ut);
-            const float uh = __fadd_rn(us, ue);
-            U[e] = make_float2(uh, __fsub_rn(ue, __fsub_rn(uh, us)));
+        float dprev = below;
+#pragma unroll
+        for (int i = 0; i < MM; ++i)
+          if (i < m) {
+            const int r = s + i, e = r * kPcrCols + c;
+            const float d = w[i];
+            const float dnext = (i + 1 < m) ? w[i + 1 < MM ? i + 1 : MM - 1] : above;
+            DoubleFloat acc;
+            df_acc<true>(acc, opB[2 * r], opB[2 * r + 1], d);
+            df_acc(acc, opA[2 * r], opA[2 * r + 1], dprev);
+            df_acc(acc, opC[2 * r], opC[2 * r + 1], dnext);
+            float bh, bl;
+            if (it == 0) {
+              f64_split(Rt[e], &bh, &bl);
+            } else {
+              const float2 rb = Rp[e];
+              bh = rb.x;
+              bl = rb.y;
+            }
+            const float2 rn = df_sub(bh, bl, acc);
+            Rp[e] = rn;
+            rmax = fmaxf(rmax, fabsf(rn.x));
+            if (it == 0) {
+              uh[i] = d;
+              ul[i] = 0.0f;
+            } else {
+              float us, ut;
+              two_sum(uh[i], d, us, ut);
+              const float ue = __fadd_rn(ul[i], ut);
+              uh[i] = __fadd_rn(us, ue);
+              ul[i] = __fsub_rn(ue, __fsub_rn(uh[i], us));
+            }
+            dprev = d;
+            w[i] = rn.x;  // the next FP32 right-hand side
           }
-        }
+      }
       unsigned int* slot = s_max + 1 + (it & 1);
       cta_max_to(rmax, slot);
-      __syncthreads();  // the residual is complete; W is free
+      __syncthreads();  // the residual is complete; s_x may be rewritten
       ++it;
       const float rm = __uint_as_float(*slot), am = __uint_as_float(s_max[0]);
       if (rm <= a.tol * am || it >= a.maxit) break;  // the same outcome on every thread
-      if (part)
-        for (int i = 0; i < m; ++i) {
-          const int e = (s + i) * kPcrCols + c;
-          W[e] = reinterpret_cast<const float2*>(Rt)[e].x;
-        }
       // the next pass's slot was last read before this pass's barriers
       if (threadIdx.x == 0) s_max[1 + (it & 1)] = 0u;
-      __syncthreads();
     }
     // u = hi + lo in FP64, written over the tile for the store
-    if (part)
-      for (int i = 0; i < m; ++i) {
-        const int e = (s + i) * kPcrCols + c;
-        const float2 uo = U[e];
-        Rt[e] = f32_to_f64(uo.x) + f32_to_f64(uo.y);
-      }
+#pragma unroll
+    for (int i = 0; i < MM; ++i)
+      if (i < m) Rt[(s + i) * kPcrCols + c] = f32_to_f64(uh[i]) + f32_to_f64(ul[i]);
     if (threadIdx.x == 0) {
       atomicMax(a.words, s_max[1 + ((it - 1) & 1)]);
       atomicMax(a.words + 1, s_max[0]);
@@ -340,14 +432,16 @@ __device__ __forceinline__ void pcr_refine_body(const CUtensorMap* in_map,
   }
 }
 
-__global__ void __launch_bounds__(1024)
+template <int MM>
+__global__ void __launch_bounds__(refine_threads<MM>::value)
     pcr_refine_kernel(const __grid_constant__ CUtensorMap in_map,
                       const __grid_constant__ CUtensorMap out_map, PcrRefineArgs a, int* status) {
-  pcr_refine_body(&in_map, &out_map, a, status, blockIdx.x, gridDim.x);
+  pcr_refine_body<MM>(&in_map, &out_map, a, status, blockIdx.x, gridDim.x);
 }
 
-__global__ void __launch_bounds__(1024) pcr_refine_group_kernel(const PcrRefineBox* boxes,
-                                                                GroupMap g) {
+template <int MM>
+__global__ void __launch_bounds__(refine_threads<MM>::value)
+    pcr_refine_group_kernel(const PcrRefineBox* boxes, GroupMap g) {
   int b, blk;
   if (!group_block(g, &b, &blk)) return;
   const PcrRefineBox& x = boxes[b];
@@ -355,7 +449,7 @@ __global__ void __launch_bounds__(1024) pcr_refine_group_kernel(const PcrRefineB
     tensormap_acquire(&x.in_map);
     tensormap_acquire(&x.out_map);
   }
-  pcr_refine_body(&x.in_map, &x.out_map, x.a, x.status, blk, x.blocks);
+  pcr_refine_body<MM>(&x.in_map, &x.out_map, x.a, x.status, blk, x.blocks);
 }
 
 // 2-D map over the first n rows of a field: ncols reals per row.
@@ -492,15 +586,27 @@ cudaError_t launch_pcr_group64(const PcrBox64* boxes, GroupMap g, int total, int
 size_t pcr_refine_smem(int n, int nparts) {
   int nbox, by;
   pcr_boxes(n, sizeof(double), &nbox, &by);
-  const size_t J = 2 * (size_t)nparts;
+  const size_t J = 2 * (size_t)nparts, L = (size_t)alg2_pcr_levels((int)J);
   return 128 + sizeof(double) * (size_t)nbox * by * kPcrCols   // rhs, r, u tile
-         + sizeof(float2) * (size_t)n * kPcrCols               // u as (hi, lo)
-         + sizeof(float) * (size_t)n * kPcrCols                // FP32 work
-         + sizeof(float) * (5 * (size_t)n + 3 * J + 6 * (size_t)n + J * kPcrCols);
+         + sizeof(float) * (11 * (size_t)n + 2 * J * kPcrCols + (2 * L + 1) * J);
 }
 
+int pcr_refine_thread_limit(int rows) {
+  return rows <= 16 ? refine_threads<16>::value : refine_threads<32>::value;
+}
+
+// Rows per thread the one-pass kernel is compiled for (8, 16, 24 or 32) for
+// the largest partition of set h, or 0 if it has more rows or too many
+// partitions for the kernel's CTA.
+int pcr_refine_rows(const HelmCoef& h) {
+  const int mm = h.mmax <= 8 ? 8 : h.mmax <= 16 ? 16 : h.mmax <= 24 ? 24 : h.mmax <= 32 ? 32 : 0;
+  return (mm && kPcrCols * h.nparts <= pcr_refine_thread_limit(mm)) ? mm : 0;
+}
+static int refine_rows(const HelmCoef& h) { return pcr_refine_rows(h); }
+
 bool pcr_refine_fits(const cfs_plan* P, const HelmCoef& h) {
-  return h.d_rows32 && h.d_abc && !P->helm_thomas32 && pcr_refine_smem(h.n, h.nparts) <= 227 * 1024;
+  return h.d_rows32 && h.d_abc && h.d_lv32 && !P->helm_thomas32 && refine_rows(h) &&
+         pcr_refine_smem(h.n, h.nparts) <= 227 * 1024;
 }
 
 static PcrRefineArgs refine_args(const cfs_plan* P, const HelmCoef& h, double* u,
@@ -518,12 +624,35 @@ static PcrRefineArgs refine_args(const cfs_plan* P, const HelmCoef& h, double* u
   a.rows = h.d_rows32;
   a.red = h.d_red32;
   a.abc = h.d_abc;
+  a.lv = h.d_lv32;
+  a.nlv = alg2_pcr_levels(2 * h.nparts);
   a.words = words;
   return a;
 }
 
+template <int MM>
+static cudaError_t launch_refine_mm(const CUtensorMap& in_map, const CUtensorMap& out_map,
+                                    const PcrRefineArgs& a, int* status, size_t smem,
+                                    int threads, cudaStream_t st) {
+  auto kern = pcr_refine_kernel<MM>;
+  cudaError_t e = allow_max_smem(kern);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+  if (per_sm < 1) per_sm = 1;
+  const long long ntiles = (a.ncols + kPcrCols - 1) / kPcrCols;
+  long long grid = (long long)nsm * per_sm;
+  if (grid > ntiles) grid = ntiles;
+  kern<<<(unsigned)grid, threads, smem, st>>>(in_map, out_map, a, status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pcr_refine(const cfs_plan* P, const HelmCoef& h, const double* rhs, double* u,
                               unsigned int* words, cudaStream_t st) {
+  const int mm = refine_rows(h);
+  if (!mm) return cudaErrorInvalidValue;
   const PcrRefineArgs a = refine_args(P, h, u, words);
   CUtensorMap in_map, out_map;
   if (!pcr_map<double>(&in_map, rhs, a.ncols, h.n, a.by) ||
@@ -531,22 +660,19 @@ cudaError_t launch_pcr_refine(const cfs_plan* P, const HelmCoef& h, const double
     return cudaErrorInvalidValue;
   const size_t smem = pcr_refine_smem(h.n, h.nparts);
   const int threads = kPcrCols * h.nparts;
-  cudaError_t e = allow_max_smem(pcr_refine_kernel);
-  if (e != cudaSuccess) return e;
-  int dev = 0, nsm = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcr_refine_kernel, threads, smem);
-  if (per_sm < 1) per_sm = 1;
-  const long long ntiles = (a.ncols + kPcrCols - 1) / kPcrCols;
-  long long grid = (long long)nsm * per_sm;
-  if (grid > ntiles) grid = ntiles;
-  pcr_refine_kernel<<<(unsigned)grid, threads, smem, st>>>(in_map, out_map, a, P->d_status);
-  return cudaGetLastError();
+  switch (mm) {
+    case 8: return launch_refine_mm<8>(in_map, out_map, a, P->d_status, smem, threads, st);
+    case 16: return launch_refine_mm<16>(in_map, out_map, a, P->d_status, smem, threads, st);
+    case 24: return launch_refine_mm<24>(in_map, out_map, a, P->d_status, smem, threads, st);
+    default: return launch_refine_mm<32>(in_map, out_map, a, P->d_status, smem, threads, st);
+  }
 }
 
 size_t pcr_refine_group_box(const cfs_plan* P, const HelmCoef& h, const double* rhs, double* u,
-                            unsigned int* words, PcrRefineBox* box, int* blocks, int* threads) {
+                            unsigned int* words, PcrRefineBox* box, int* blocks, int* threads,
+                            int* rows) {
+  *rows = refine_rows(h);
+  if (!*rows) return 0;
   box->a = refine_args(P, h, u, words);
   if (!pcr_map<double>(&box->in_map, rhs, box->a.ncols, h.n, box->a.by) ||
       !pcr_map<double>(&box->out_map, u, box->a.ncols, h.n, box->a.by))
@@ -559,13 +685,26 @@ size_t pcr_refine_group_box(const cfs_plan* P, const HelmCoef& h, const double* 
   return pcr_refine_smem(h.n, h.nparts);
 }
 
-cudaError_t launch_pcr_refine_group(const PcrRefineBox* boxes, GroupMap g, int total, int threads,
-                                    size_t smem, cudaStream_t st) {
-  if (total <= 0) return cudaSuccess;
-  cudaError_t e = allow_max_smem(pcr_refine_group_kernel);
+template <int MM>
+static cudaError_t launch_refine_group_mm(const PcrRefineBox* boxes, GroupMap g, int total,
+                                          int threads, size_t smem, cudaStream_t st) {
+  auto kern = pcr_refine_group_kernel<MM>;
+  cudaError_t e = allow_max_smem(kern);
   if (e != cudaSuccess) return e;
-  pcr_refine_group_kernel<<<total, threads, smem, st>>>(boxes, g);
+  kern<<<total, threads, smem, st>>>(boxes, g);
   return cudaGetLastError();
+}
+
+cudaError_t launch_pcr_refine_group(const PcrRefineBox* boxes, GroupMap g, int total, int threads,
+                                    size_t smem, int rows, cudaStream_t st) {
+  if (total <= 0) return cudaSuccess;
+  switch (rows) {
+    case 8: return launch_refine_group_mm<8>(boxes, g, total, threads, smem, st);
+    case 16: return launch_refine_group_mm<16>(boxes, g, total, threads, smem, st);
+    case 24: return launch_refine_group_mm<24>(boxes, g, total, threads, smem, st);
+    case 32: return launch_refine_group_mm<32>(boxes, g, total, threads, smem, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace chanfs

@@ -544,6 +544,10 @@ static void helm_release(cfs_plan* P, HelmCoef& h) {
     cudaFree(h.d_th32);
     P->device_bytes -= sizeof(float) * (5 * n + 6 * p + 3 * n) + sizeof(double) * 3 * n;
   }
+  if (h.d_lv32) {
+    cudaFree(h.d_lv32);
+    P->device_bytes -= sizeof(float) * (2 * (size_t)alg2_pcr_levels(2 * (int)p) + 1) * 2 * p;
+  }
 }
 
 static int helm_prepare(cfs_plan* P, double c, int loc, int nparts, HelmCoef** res) {
@@ -636,6 +640,14 @@ static int helm_prepare(cfs_plan* P, double c, int loc, int nparts, HelmCoef** r
     if (!rcode) rcode = dev_upload(&h.d_abc, abc.data(), abc.size(), &P->device_bytes);
     std::vector<float> th32(th.begin(), th.end());
     if (!rcode) rcode = dev_upload(&h.d_th32, th32.data(), th32.size(), &P->device_bytes);
+    // the reduced system by parallel cyclic reduction (the one-pass refined solve)
+    const int L = alg2_pcr_levels(J);
+    std::vector<double> sub(ra), diag(rb), sup(rc), na(J), nb(J), nc(J);
+    std::vector<double> lv((2 * (size_t)L + 1) * J);
+    alg2_reduced_pcr(J, sub.data(), diag.data(), sup.data(), na.data(), nb.data(), nc.data(),
+                     lv.data(), lv.data() + (size_t)L * J, lv.data() + 2 * (size_t)L * J);
+    std::vector<float> lv32(lv.begin(), lv.end());
+    if (!rcode) rcode = dev_upload(&h.d_lv32, lv32.data(), lv32.size(), &P->device_bytes);
   }
   if (rcode) {
     cudaFree(h.d_rows);
@@ -645,6 +657,7 @@ static int helm_prepare(cfs_plan* P, double c, int loc, int nparts, HelmCoef** r
     cudaFree(h.d_red32);
     cudaFree(h.d_abc);
     cudaFree(h.d_th32);
+    cudaFree(h.d_lv32);
     return rcode;
   }
   // bounded cache: evict the least recently used entry
