@@ -415,6 +415,52 @@ int cfs_server_stats(cfs_server_t server, cfs_server_stats_t* stats);
 int cfs_server_destroy(cfs_server_t server);
 
 /*
+ * z-slabs over several GPUs: the paper's parallel tridiagonal solver
+ * (P-TDMA, Sec. 2.2.3) with one slab of whole x-y planes per rank
+ * (p_y = 1, p_z = nranks, the layout of its weak-scaling runs, Sec. 3).
+ * The x and y transforms of a rank's planes are local; along z each column's
+ * system is split over the ranks, each rank's planes one partition of
+ * Algorithm 2 (Sec. 2.2.4).  A solve is two calls around one exchange:
+ *   *_reduce  transforms (Poisson) and Step 2 on the rank's rows; writes the
+ *             rank's boundary buffer `bnd` (cfs_slab_boundary_doubles
+ *             doubles: the two boundary values of every column, plus for the
+ *             Poisson solve two partial sums of the Neumann (0, 0) column).
+ *   the caller gathers the buffers of all ranks into `bnd_all`, rank-major
+ *             (rank r's buffer at offset r * count; an NCCL all-gather).
+ *   *_finish  Step 3 (the reduced system of the 2 nranks boundary unknowns
+ *             of every column, solved by every rank) and Step 4 on the rank's
+ *             rows, then the inverse transforms (Poisson); writes the rank's
+ *             planes of the solution.
+ * The reduced systems' coefficients are computed by every rank for all
+ * ranks when the slab is created (Poisson) or a coefficient is first used
+ * (Helmholtz), so only right-hand-side data is exchanged.  Fields are the
+ * rank's planes: nx*ny*(z1 - z0) doubles, x fastest; `work` is a field of
+ * that size owned by the caller (work == p allowed for the Poisson solve;
+ * the Helmholtz solve keeps rhs, work and u distinct).  Results equal the
+ * single-GPU solve of the whole field up to rounding.  Periodic y only.
+ *   cfs_slab_partition  planes [z0, z1) of `rank` (host arithmetic only).
+ *   cfs_slab_create  the rank's slab of the global grid (dz: nz HOST
+ *       doubles of the whole grid); every slab needs at least 4 planes;
+ *       nranks <= 64.  Creates a plan for the rank's planes on the current
+ *       device.
+ */
+typedef struct cfs_slab* cfs_slab_t;
+int cfs_slab_partition(int nz, int nranks, int rank, int* z0, int* z1);
+int cfs_slab_create(cfs_slab_t* slab, int nx, int ny, int nz, double lx, double ly,
+                    const double* dz, int poisson_bc, int nranks, int rank);
+int cfs_slab_destroy(cfs_slab_t slab);
+int cfs_slab_extent(cfs_slab_t slab, int* z0, int* z1);
+int cfs_slab_boundary_doubles(cfs_slab_t slab, int kind, size_t* count);
+int cfs_slab_poisson_reduce(cfs_slab_t slab, const double* f, double* work, double* bnd,
+                            void* stream);
+int cfs_slab_poisson_finish(cfs_slab_t slab, const double* bnd_all, double* work, double* p,
+                            void* stream);
+int cfs_slab_helmholtz_reduce(cfs_slab_t slab, double c, int loc, const double* rhs,
+                              double* work, double* bnd, void* stream);
+int cfs_slab_helmholtz_finish(cfs_slab_t slab, double c, int loc, const double* bnd_all,
+                              const double* work, double* u, void* stream);
+
+/*
  * Kernel-shape options of a plan.  The paper has no counterpart: an option
  * chooses between launch shapes that compute the same thing (up to rounding
  * order), and defaults are picked per plan from the problem size.

@@ -21,7 +21,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
          "-Xcompiler", "-Wall"]
 SOURCES = ["plan.cu", "fft_x.cu", "fft_y.cu", "thomas.cu", "pcr.cu", "refine.cu", "group.cu",
-           "tune.cu", "noalloc.cu", "helm_thomas.cu", "probe.cu", "server.cpp"]
+           "tune.cu", "noalloc.cu", "helm_thomas.cu", "probe.cu", "slab.cu", "server.cpp"]
 
 
 def _nvcc() -> str:

@@ -81,6 +81,15 @@ def lib():
             "cfs_last_info": ([vp, ctypes.POINTER(i), ctypes.POINTER(d)], i),
             "cfs_probe_fma": ([i, ctypes.c_longlong, dp, dp], i),
             "cfs_selftest_wait_timeout": ([vp, vp, ctypes.c_uint, vp], i),
+            "cfs_slab_partition": ([i, i, i, ctypes.POINTER(i), ctypes.POINTER(i)], i),
+            "cfs_slab_create": ([ctypes.POINTER(vp), i, i, i, d, d, dp, i, i, i], i),
+            "cfs_slab_destroy": ([vp], i),
+            "cfs_slab_extent": ([vp, ctypes.POINTER(i), ctypes.POINTER(i)], i),
+            "cfs_slab_boundary_doubles": ([vp, i, ctypes.POINTER(ctypes.c_size_t)], i),
+            "cfs_slab_poisson_reduce": ([vp, vp, vp, vp, vp], i),
+            "cfs_slab_poisson_finish": ([vp, vp, vp, vp, vp], i),
+            "cfs_slab_helmholtz_reduce": ([vp, d, i, vp, vp, vp, vp], i),
+            "cfs_slab_helmholtz_finish": ([vp, d, i, vp, vp, vp, vp], i),
             "cfs_group_create": ([ctypes.POINTER(vp), i, ctypes.POINTER(vp)], i),
             "cfs_group_destroy": ([vp], i),
             "cfs_group_size": ([vp, ctypes.POINTER(i)], i),
@@ -340,6 +349,91 @@ def helmholtz_solve_noalloc(dz, c: float, rhs, loc: int = CENTER, nparts: int = 
                                              ctypes.c_void_p(status.data_ptr()), _stream_ptr(stream)),
            "cfs_helmholtz_solve_noalloc")
     return out, status
+
+
+def slab_partition(nz: int, nranks: int, rank: int):
+    """Planes [z0, z1) of `rank` among `nranks` z-slabs (host arithmetic)."""
+    z0, z1 = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().cfs_slab_partition(nz, nranks, rank, ctypes.byref(z0), ctypes.byref(z1)),
+           "cfs_slab_partition")
+    return z0.value, z1.value
+
+
+class Slab:
+    """One rank's z-slab of a grid distributed over several GPUs (see
+    cfs_slab_create): the rank's planes of the Poisson and Helmholtz solves,
+    reduce and finish around an exchange of boundary values."""
+
+    def __init__(self, nx: int, ny: int, nz: int, lx: float, ly: float, dz, bc: int = NEUMANN,
+                 nranks: int = 1, rank: int = 0):
+        dz = np.ascontiguousarray(dz, dtype=np.float64)
+        if dz.size != nz:
+            raise ValueError("dz must have nz entries (the whole grid)")
+        h = ctypes.c_void_p()
+        _check(lib().cfs_slab_create(ctypes.byref(h), nx, ny, nz, float(lx), float(ly),
+                                     dz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), bc,
+                                     nranks, rank), "cfs_slab_create")
+        self._h = h
+        z0, z1 = ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib().cfs_slab_extent(self._h, ctypes.byref(z0), ctypes.byref(z1)), "cfs_slab_extent")
+        self.z0, self.z1 = z0.value, z1.value
+        self.shape = (self.z1 - self.z0, ny, nx)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cfs_slab_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def boundary_doubles(self, kind: int) -> int:
+        n = ctypes.c_size_t(0)
+        _check(lib().cfs_slab_boundary_doubles(self._h, kind, ctypes.byref(n)),
+               "cfs_slab_boundary_doubles")
+        return n.value
+
+    def _field(self, t, name):
+        if t.dtype != _torch().float64 or not t.is_cuda or not t.is_contiguous() or \
+                tuple(t.shape) != self.shape:
+            raise TypeError(f"{name} must be a contiguous float64 CUDA tensor of shape {self.shape}")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def poisson_reduce(self, f, work, bnd, stream=None):
+        _check(lib().cfs_slab_poisson_reduce(self._h, self._field(f, "f"), self._field(work, "work"),
+                                             ctypes.c_void_p(bnd.data_ptr()), _stream_ptr(stream)),
+               "cfs_slab_poisson_reduce")
+
+    def poisson_finish(self, bnd_all, work, out, stream=None):
+        _check(lib().cfs_slab_poisson_finish(self._h, ctypes.c_void_p(bnd_all.data_ptr()),
+                                             self._field(work, "work"), self._field(out, "out"),
+                                             _stream_ptr(stream)), "cfs_slab_poisson_finish")
+
+    def helmholtz_reduce(self, c: float, loc: int, rhs, work, bnd, stream=None):
+        _check(lib().cfs_slab_helmholtz_reduce(self._h, float(c), loc, self._field(rhs, "rhs"),
+                                               self._field(work, "work"),
+                                               ctypes.c_void_p(bnd.data_ptr()), _stream_ptr(stream)),
+               "cfs_slab_helmholtz_reduce")
+
+    def helmholtz_finish(self, c: float, loc: int, bnd_all, work, out, stream=None):
+        _check(lib().cfs_slab_helmholtz_finish(self._h, float(c), loc,
+                                               ctypes.c_void_p(bnd_all.data_ptr()),
+                                               self._field(work, "work"), self._field(out, "out"),
+                                               _stream_ptr(stream)), "cfs_slab_helmholtz_finish")
+
+
+def _torch():
+    import torch
+    return torch
 
 
 class Group:
