@@ -56,6 +56,28 @@ SOURCE_OF_STAGE = {"x_forward": "fft_x.cu", "x_inverse": "fft_x.cu", "y_forward"
                    "helm_v": "pcr.cu", "helm_w": "pcr.cu"}
 
 
+class nvtx_range:
+    """An NVTX range (profilers can restrict a capture to it: ncu --nvtx
+    --nvtx-include "<name>/"); nothing if NVTX is unavailable."""
+
+    def __init__(self, name: str):
+        self.name = name
+
+    def __enter__(self):
+        try:
+            import torch
+            torch.cuda.nvtx.range_push(self.name)
+            self.on = True
+        except Exception:
+            self.on = False
+        return self
+
+    def __exit__(self, *exc):
+        if self.on:
+            import torch
+            torch.cuda.nvtx.range_pop()
+
+
 def set_helm_method(thomas: bool):
     """The Helmholtz stages run Algorithm 2 (pcr_kernel) or Thomas sweeps
     (helm_thomas_kernel), as the plan's option says."""
@@ -314,13 +336,14 @@ def run_mixed(chanfs, torch, device, reps: int = 5, warmup: int = 3, nz: int = 0
             torch.cuda.synchronize()
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
             iters = []
-            ev[0].record(stream)
-            for r in range(reps):
-                plan.poisson_solve(f, out=p)
-                ev[r + 1].record(stream)
-                if dtype == chanfs.F32_REFINED:
-                    iters.append(plan.last_info())
-            torch.cuda.synchronize()
+            with nvtx_range(f"solve_{name}"):
+                ev[0].record(stream)
+                for r in range(reps):
+                    plan.poisson_solve(f, out=p)
+                    ev[r + 1].record(stream)
+                    if dtype == chanfs.F32_REFINED:
+                        iters.append(plan.last_info())
+                torch.cuda.synchronize()
             ms = [ev[r].elapsed_time(ev[r + 1]) for r in range(reps)]
             entry = {"ms": round(statistics.median(ms), 4),
                      "ns_per_pt": statistics.median(ms) * 1e6 / npts,
@@ -465,9 +488,15 @@ def run_ensemble(chanfs, torch, device, reps: int = 3):
 
     grouped()  # a launch shape is captured as a graph at its second solve
     t_group = timed(grouped)
+    with nvtx_range("ensemble_grouped_step"):  # one more step, for profilers
+        grouped()
+        torch.cuda.synchronize()
     info = group.last_info()
     group.set_graphs(False)  # the same launches, refinement loop on the host
     t_group_host = timed(grouped)
+    with nvtx_range("ensemble_grouped_step_direct"):  # kernel by kernel, for profilers
+        grouped()
+        torch.cuda.synchronize()
     group.set_graphs(True)
     t64 = timed(per_box(plans64))
     t32 = timed(per_box(plans32))
@@ -764,6 +793,80 @@ def run_extras_only(args):
     return 0
 
 
+def run_slab(args):
+    """The paper's weak-scaling layout (Sec. 3: p_y = 1, p_z = number of GPUs):
+    one z-slab of 384 planes of a 512 x 384 x (384 N) tanh(1.8) channel per
+    GPU, the step (Poisson + three Helmholtz solves) by P-TDMA with one NCCL
+    all-gather of the boundary values per solve.  Each rank's fields are its
+    own seeded N(0,1) draws."""
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend="nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    from paper_2502_06296_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2502_06296_gb300 import chanfs, slab
+
+    nx, ny, nzl = CFG["nx"], CFG["ny"], CFG["nz"]
+    nz = nzl * world
+    dz = synth.tanh_dz(nz, CFG["beta"])
+    c = synth.CHANNEL_C
+    solver = slab.SlabSolver(nx, ny, nz, CFG["lx"], CFG["ly"], dz, chanfs.NEUMANN)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(CFG["seed"] + 1000 * rank)
+    shape = solver.shape
+    f = torch.randn(*shape, dtype=torch.float64, device=device, generator=gen)
+    rhs = [torch.randn(*shape, dtype=torch.float64, device=device, generator=gen) for _ in range(3)]
+    p = torch.empty_like(f)
+    us = [torch.empty_like(f) for _ in range(3)]
+    w = torch.empty_like(f)
+    locs = (chanfs.CENTER, chanfs.CENTER, chanfs.FACE)
+
+    def step():
+        solver.poisson_solve(f, out=p, work=p)
+        for i in range(3):
+            solver.helmholtz_solve(c, rhs[i], locs[i], out=us[i], work=w)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(device)
+    with ClockSampler(local) as clk:
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            step()
+        b.record()
+        torch.cuda.synchronize()
+    barrier(device)
+    max_ms = reduce_max(a.elapsed_time(b), device)
+    npts = nx * ny * shape[0]
+    agg = aggregate(max_ms, args.steps, nx * ny * nzl, world)
+    solver.close()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": agg["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": agg["ms_per_step"], "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"channel_zslab_{nx}x{ny}x{nz}_tanh1.8", "nx": nx, "ny": ny,
+                   "nz": nz, "planes_per_gpu": nzl, "parallelism": f"zslab{world}",
+                   "method": "P-TDMA: local x/y transforms, Algorithm 2 Step 2 per slab, NCCL "
+                             "all-gather of 2 values per column per rank, reduced solve and "
+                             "reconstruction per slab",
+                   "l2": f"inputs larger than L2 ({npts * 8 / 1e6:.0f} MB fields per GPU)"},
+        "e2e": None, "gpu_launches": None, "roofline": None, "cpu_baseline": None,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -835,7 +938,7 @@ def run_ours(args):
     events = [[torch.cuda.Event(enable_timing=True) for _ in range(9)] for _ in range(args.steps)]
     barrier(device)
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
+    with ClockSampler(local) as clk, nvtx_range("timed_steps"):
         start = torch.cuda.Event(enable_timing=True)
         stop = torch.cuda.Event(enable_timing=True)
         start.record(stream)
@@ -974,6 +1077,9 @@ def main(argv=None):
                     help="run only the FP32-refined vs FP64 comparison and print its object")
     ap.add_argument("--probe-only", action="store_true",
                     help="measure only the FP64 and FP32 FMA rates (--steps repetitions)")
+    ap.add_argument("--slab", action="store_true",
+                    help="N > 1: one z-slab of the channel per GPU, solved by P-TDMA with an "
+                         "NCCL all-gather (the default runs independent replicas)")
     ap.add_argument("--nz", type=int, default=0,
                     help="override the wall-normal size (profiling captures only)")
     args = ap.parse_args(argv)
@@ -985,6 +1091,8 @@ def main(argv=None):
         return run_mixed_only(args)
     if args.probe_only:
         return run_probe_only(args)
+    if args.slab:
+        return run_slab(args)
     if args.extras_only:
         return run_extras_only(args)
     return run_ours(args)

@@ -16,7 +16,7 @@ namespace chanfs {
 
 // Output modes of the FP32 inverse x transform: in place, FP64 result written
 // to the solution, or added to it (the correction step p += delta).
-enum { OUT_SAME = 0, OUT_SET = 1, OUT_ADD = 2 };
+enum { OUT_SAME = 0, OUT_SET = 1, OUT_ADD = 2, OUT_SUM = 3 };
 
 struct GroupMap {
   const int* start;   // nbox + 1 block offsets
@@ -42,6 +42,7 @@ struct XBox {  // packed real FFT along x (fft_x.cu)
   int* status;
   const double* msum;  // inverse, correction pass: the solution's weighted sum (may be null)
   double minv;         // 1 / (sum of the cell widths * Nx * Ny)
+  const void* add_src; // inverse, second pass (OUT_SUM): the first correction (FP32)
 };
 
 struct YBox {  // FFT along y on TMA tiles (fft_y.cu); the map is 64-byte aligned
@@ -77,7 +78,8 @@ struct ResBox {  // refinement residual and norms (refine.cu)
   double* mean;        // dz-weighted mean
   float* r32;          // FP32 residual / correction
   float* r32b;         // FP32 residual of the later iterations
-  float2* rdf;         // residual kept between iterations, double-float (hi, lo)
+  float* rlo;          // low part of the residual kept between iterations (high part: r32b)
+  float* dcopy;        // the first correction, kept for the second pass (OUT_SUM)
   const float4* zk;    // Poisson: packed double-float coefficients per plane (refine.cu)
   unsigned int* rmax;  // max |r| (float bits)
   int nx, ny, nz, n;   // n = Helmholtz unknowns per column
@@ -226,22 +228,26 @@ struct GroupCtl {  // device-side iteration state of a grouped refined solve
 };
 cudaError_t launch_group_start(const ResBox* boxes, int nbox, int keys, double* fmax,
                                const int* eligible, int* active, int* mean_on, int* zero,
-                               int* iters, double* rho, GroupCtl* ctl, cudaStream_t st);
+                               int* iters, double* rho, GroupCtl* ctl, cudaStream_t st,
+                               int* one = nullptr);
+// one (may be null): boxes still on their first correction, i.e. whose p is
+// written by the FIRST_ONLY stage if they stop there
 cudaError_t launch_group_iter_end(const ResBox* boxes, int nbox, const double* fmax,
                                   const double* tol, const int* maxit, int* active,
                                   int* mean_on, int* iters, double* rho, GroupCtl* ctl,
-                                  cudaGraphConditionalHandle cond, int set_cond, cudaStream_t st);
+                                  cudaGraphConditionalHandle cond, int set_cond, cudaStream_t st,
+                                  int* one = nullptr);
 cudaError_t launch_group_zero_max(const ResBox* boxes, int nbox, cudaStream_t st);
 enum {
   GSTAGE_MEAN_FINAL = 1,
   GSTAGE_RESIDUAL = 2,
-  GSTAGE_SUBTRACT = 3,
   GSTAGE_HELM_RESIDUAL = 4,  // flag = mode of helm_residual_kernel
   GSTAGE_UPDATE = 5,         // r -= L delta (double-float), r32b and max
   GSTAGE_ZERO = 6,           // zero solution (boxes with a zero right-hand side)
   GSTAGE_START = 7,          // r_0 = f as FP32, its extremes, plane sums (plane x chunk blocks)
   GSTAGE_MEAN_ACC = 8,       // running weighted sum of the solution += the correction's
-  GSTAGE_MEAN_FROM_NUM = 9   // the solution's weighted mean from the running sum
+  GSTAGE_MEAN_FROM_NUM = 9,  // the solution's weighted mean from the running sum
+  GSTAGE_FIRST_ONLY = 10     // p from the only correction (boxes stopped after one solve)
 };
 
 // Host-side descriptions of one plan's box for the grouped kernels.

@@ -156,8 +156,10 @@ struct cfs_plan {
   float* d_bwd32;
   int kx64, ky64;    // columns kx < kx64, min(ky, Ny-ky) < ky64 stay FP64
   float* d_r32;      // FP32 residual / correction field (in-place inner solve)
-  float* d_r32b;     // the FP32 residual of the later iterations (input of their solves)
-  float2* d_rdf;     // the residual kept between iterations, double-float (hi, lo)
+  float* d_r32b;     // the residual kept between iterations, high part (FP32 input of the
+                     // next solve)
+  float* d_rlo;      // its low part: the double-float residual is (d_r32b, d_rlo)
+  float* d_w2;       // the first correction, kept until the second pass writes p once
   float4* d_zk;      // per plane k, split hi + lo: (A_k, C_k), (B'_k, dz_k), (D_k, dz_k); then
                      // (1/dx^2, 1/dy^2).  D_k = A_k + B'_k + C_k + 2/dx^2 + 2/dy^2 (exact sum)
   double* d_mpart;   // per-block dz-weighted sums of a correction (residual grid blocks)
@@ -203,6 +205,11 @@ cudaError_t launch_rfft_x32(const cfs_plan* P, const float* in, float* out, bool
 // add: p += delta (less msum * inv_wn when msum is not null), else p = delta
 cudaError_t launch_rfft_x32_to64(const cfs_plan* P, const float* in, double* out, bool add,
                                  cudaStream_t st, const double* msum = nullptr);
+// the second correction pass: p = first + delta (less msum * inv_wn when msum
+// is not null), with delta left in `in`; p is not read
+cudaError_t launch_rfft_x32_sum(const cfs_plan* P, const float* in, double* out,
+                                const float* first, cudaStream_t st,
+                                const double* msum = nullptr);
 cudaError_t launch_fft_y32(const cfs_plan* P, float* data, bool inverse, cudaStream_t st);
 cudaError_t launch_thomas32(const cfs_plan* P, float* data, cudaStream_t st);
 // x-lines per CTA of the x transforms of complex element size csize.

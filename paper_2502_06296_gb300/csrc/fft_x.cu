@@ -31,7 +31,8 @@ __device__ __forceinline__ void rfft_x_body(const C* in, void* outv, long long n
                                             const FftDesc& d, const C* __restrict__ twg,
                                             const C* __restrict__ postg, int lb, double scale,
                                             int scaled, int* status, long long blk,
-                                            const double* msum = nullptr, double minv = 0.0) {
+                                            const double* msum = nullptr, double minv = 0.0,
+                                            const C* add_src = nullptr) {
   using T = typename cscal<C>::T;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int M = d.n;
@@ -147,7 +148,7 @@ __device__ __forceinline__ void rfft_x_body(const C* in, void* outv, long long n
         tma_store_commit_and_wait_read();
       }
     } else {
-      if (OUT == OUT_ADD && msum) {
+      if ((OUT == OUT_ADD || OUT == OUT_SUM) && msum) {
         // the correction less the solution's current weighted mean (msum *
         // minv), so that p keeps a zero mean without a pass of its own; the
         // correction stored for the residual update is this one
@@ -167,10 +168,15 @@ __device__ __forceinline__ void rfft_x_body(const C* in, void* outv, long long n
         }
       }
       double2* dst = reinterpret_cast<double2*>(outv) + line0 * M;
+      const C* first = add_src ? add_src + line0 * M : nullptr;
       for (int e = threadIdx.x; e < valid * M; e += blockDim.x) {
         const C r = res[e];
         if (OUT == OUT_SET) {
           dst[e] = make_double2(f32_to_f64(r.x), f32_to_f64(r.y));
+        } else if (OUT == OUT_SUM) {  // p = the first correction + this one, written once
+          const C a = first[e];
+          dst[e] = make_double2(f32_to_f64(a.x) + f32_to_f64(r.x),
+                                f32_to_f64(a.y) + f32_to_f64(r.y));
         } else {
           const double2 p = dst[e];
           dst[e] = make_double2(p.x + f32_to_f64(r.x), p.y + f32_to_f64(r.y));
@@ -186,9 +192,10 @@ __global__ void __launch_bounds__(128) rfft_x_kernel(const C* in, void* outv, lo
                                                      FftDesc d, const C* __restrict__ twg,
                                                      const C* __restrict__ postg, int lb,
                                                      double scale, int scaled, int* status,
-                                                     const double* msum, double minv) {
+                                                     const double* msum, double minv,
+                                                     const C* add_src) {
   rfft_x_body<INV, C, OUT>(in, outv, nlines, d, twg, postg, lb, scale, scaled, status,
-                           blockIdx.x, msum, minv);
+                           blockIdx.x, msum, minv, add_src);
 }
 
 // One launch for several boxes (FP32 inner solves of grouped refinement):
@@ -204,7 +211,7 @@ __global__ void __launch_bounds__(128) rfft_x_group_kernel(const XBox* boxes, Gr
   rfft_x_body<INV, float2, OUT>(in, out, x.nlines, x.d,
                                 static_cast<const float2*>(x.tw),
                                 static_cast<const float2*>(x.post), x.lb, 1.0, 0, x.status, blk,
-                                x.msum, x.minv);
+                                x.msum, x.minv, static_cast<const float2*>(x.add_src));
 }
 
 int x_lines_per_cta(const cfs_plan* P, size_t csize) {
@@ -222,7 +229,7 @@ size_t x_smem_bytes(const cfs_plan* P, int lines, size_t csize) {
 template <class C, int OUT>
 static cudaError_t launch_x(const cfs_plan* P, const void* in, void* out, bool inverse,
                             double scale, const C* tw, const C* post, cudaStream_t st,
-                            const double* msum = nullptr) {
+                            const double* msum = nullptr, const void* add_src = nullptr) {
   const long long nlines = (long long)P->ny * P->nz;
   const int lb = x_lines_per_cta(P, sizeof(C));
   const long long grid = (nlines + lb - 1) / lb;
@@ -233,12 +240,13 @@ static cudaError_t launch_x(const cfs_plan* P, const void* in, void* out, bool i
     auto k = rfft_x_kernel<false, C, OUT_SAME>;
     allow_max_smem(k);
     k<<<(unsigned)grid, 128, smem, st>>>(cin, out, nlines, P->fx, tw, post, lb, scale, scaled,
-                                         P->d_status, nullptr, 0.0);
+                                         P->d_status, nullptr, 0.0, nullptr);
   } else {
     auto k = rfft_x_kernel<true, C, OUT>;
     allow_max_smem(k);
     k<<<(unsigned)grid, 128, smem, st>>>(cin, out, nlines, P->fx, tw, post, lb, scale, scaled,
-                                         P->d_status, msum, P->inv_wn);
+                                         P->d_status, msum, P->inv_wn,
+                                         reinterpret_cast<const C*>(add_src));
   }
   return cudaGetLastError();
 }
@@ -260,12 +268,19 @@ cudaError_t launch_rfft_x32_to64(const cfs_plan* P, const float* in, double* out
   return launch_x<float2, OUT_SET>(P, in, out, true, 1.0, P->d_twx32, P->d_post32, st);
 }
 
+cudaError_t launch_rfft_x32_sum(const cfs_plan* P, const float* in, double* out,
+                                const float* first, cudaStream_t st, const double* msum) {
+  return launch_x<float2, OUT_SUM>(P, in, out, true, 1.0, P->d_twx32, P->d_post32, st, msum,
+                                   first);
+}
+
 size_t x_group_box(const cfs_plan* P, bool inverse, XBox* box, int* blocks) {
   const int lb = x_lines_per_cta(P, sizeof(float2));
   box->d = P->fx;
   box->in = P->d_r32;
   box->in2 = P->d_r32b;
-  box->out = inverse ? nullptr : P->d_r32;
+  box->out = P->d_r32;  // the FP32 result (forward, and the first inverse of refinement)
+  box->add_src = P->d_w2;
   box->tw = P->d_twx32;
   box->post = P->d_post32;
   box->nlines = (long long)P->ny * P->nz;
@@ -289,6 +304,14 @@ cudaError_t launch_rfft_x_group32(const XBox* boxes, GroupMap g, int total, size
     k<<<total, 128, smem, st>>>(boxes, g, io, alt_in);
   } else if (out_mode == OUT_ADD) {
     auto k = rfft_x_group_kernel<true, OUT_ADD>;
+    allow_max_smem(k);
+    k<<<total, 128, smem, st>>>(boxes, g, io, alt_in);
+  } else if (out_mode == OUT_SUM) {
+    auto k = rfft_x_group_kernel<true, OUT_SUM>;
+    allow_max_smem(k);
+    k<<<total, 128, smem, st>>>(boxes, g, io, alt_in);
+  } else if (out_mode == OUT_SAME) {
+    auto k = rfft_x_group_kernel<true, OUT_SAME>;
     allow_max_smem(k);
     k<<<total, 128, smem, st>>>(boxes, g, io, alt_in);
   } else {

@@ -95,6 +95,7 @@ struct cfs_group {
   // refinement state
   int* d_active = nullptr;  // boxes still iterating
   int* d_mean = nullptr;    // boxes whose mean is removed (Neumann, nonzero rhs)
+  int* d_one = nullptr;     // boxes on their first correction (p written at the end if they stop)
   int* d_zero = nullptr;    // boxes with a zero right-hand side (zero solution)
   int* d_elig = nullptr;    // Helmholtz: boxes that are refined (the others solve in FP64)
   GroupCtl* d_ctl = nullptr;
@@ -204,7 +205,7 @@ static void keep_graph(cfs_group* G, const std::vector<long long>& sig, cudaGrap
 
 static void group_free(cfs_group* G) {
   drop_graphs(G);
-  void* ptrs[] = {G->d_tab,   G->d_active, G->d_mean, G->d_fmax, G->d_tol,  G->d_maxit,
+  void* ptrs[] = {G->d_tab,   G->d_active, G->d_mean, G->d_one, G->d_fmax, G->d_tol,  G->d_maxit,
                   G->d_iters, G->d_rho,    G->d_nactive, G->d_io, G->d_pcr, G->d_hres,
                   G->d_spcr, G->d_pcr64, G->d_spcr64, G->d_zero, G->d_elig, G->d_ctl,
                   G->d_hth, G->d_sth32, G->d_sth64, G->d_fus, G->d_sfus, G->d_fwords};
@@ -232,6 +233,7 @@ static int group_alloc(cfs_group* G, int cap) {
   if (e == cudaSuccess) e = cudaMallocHost(&G->h_tab, G->tab.bytes);
   if (e == cudaSuccess) e = cudaMalloc(&G->d_active, sizeof(int) * cap);
   if (e == cudaSuccess) e = cudaMalloc(&G->d_mean, sizeof(int) * cap);
+  if (e == cudaSuccess) e = cudaMalloc(&G->d_one, sizeof(int) * cap);
   if (e == cudaSuccess) e = cudaMalloc(&G->d_fmax, sizeof(double) * cap);
   if (e == cudaSuccess) e = cudaMalloc(&G->d_tol, sizeof(double) * cap);
   if (e == cudaSuccess) e = cudaMalloc(&G->d_maxit, sizeof(int) * cap);
@@ -337,7 +339,8 @@ static int group_bind(cfs_group* G, int nplans, const cfs_plan_t* plans, cudaStr
     r.mean = P->d_red + 1;
     r.r32 = P->d_r32;
     r.r32b = P->d_r32b;
-    r.rdf = P->d_rdf;
+    r.rlo = P->d_rlo;
+    r.dcopy = P->d_w2;
     r.zk = P->d_zk;
     r.rmax = reinterpret_cast<unsigned int*>(P->d_red);
     r.nx = P->nx;
@@ -530,7 +533,7 @@ cudaError_t poisson_head(cfs_group* G, cudaStream_t st) {
     e = launch_group_refine_stage(GSTAGE_MEAN_FINAL, G->d_res, g, G->tone, G->d_io, 0, st);
   if (e == cudaSuccess)
     e = launch_group_start(G->d_res, nb, 1, G->d_fmax, nullptr, G->d_active, G->d_mean,
-                           G->d_zero, G->d_iters, G->d_rho, G->d_ctl, st);
+                           G->d_zero, G->d_iters, G->d_rho, G->d_ctl, st, G->d_one);
   g = GroupMap{G->d_ssub, G->d_zero, nb};
   if (e == cudaSuccess)
     e = launch_group_refine_stage(GSTAGE_ZERO, G->d_res, g, G->tsub, G->d_io, 0, st);
@@ -538,9 +541,10 @@ cudaError_t poisson_head(cfs_group* G, cudaStream_t st) {
 }
 
 // One iteration: FP32 solve of the current residual, correction of p, new
-// residual, stopping test.  kind 0: the first (p = delta, residual directly
-// in FP64); kind 1: the second (p += delta, double-float residual update);
-// kind 2: the later ones (as 1, the FP32 right-hand side read from r32b).
+// residual, stopping test.  kind 0: the first (the correction stays in FP32,
+// first residual by differences); kind 1: the second (p = both corrections,
+// double-float residual update); kind 2: the later ones (p += delta; as 1,
+// the FP32 right-hand side read from r32b).
 cudaError_t poisson_iteration(cfs_group* G, int kind, cudaGraphConditionalHandle cond,
                               int set_cond, cudaStream_t st) {
   const int nb = G->nbox;
@@ -561,8 +565,11 @@ cudaError_t poisson_iteration(cfs_group* G, int kind, cudaGraphConditionalHandle
   }
   if (e == cudaSuccess) {
     g.start = G->d_sx;
-    e = launch_rfft_x_group32(G->d_xi, g, G->tx, G->smem_x, true, kind == 0 ? OUT_SET : OUT_ADD,
-                              G->d_io, 0, st);
+    // the first correction stays in FP32; the second pass writes p = both;
+    // later passes add to p
+    e = launch_rfft_x_group32(G->d_xi, g, G->tx, G->smem_x, true,
+                              kind == 0 ? OUT_SAME : kind == 1 ? OUT_SUM : OUT_ADD, G->d_io, 0,
+                              st);
   }
   if (e == cudaSuccess) {
     g.start = G->d_sres;
@@ -575,22 +582,23 @@ cudaError_t poisson_iteration(cfs_group* G, int kind, cudaGraphConditionalHandle
   }
   if (e == cudaSuccess)
     e = launch_group_iter_end(G->d_res, nb, G->d_fmax, G->d_tol, G->d_maxit, G->d_active,
-                              G->d_mean, G->d_iters, G->d_rho, G->d_ctl, cond, set_cond, st);
+                              G->d_mean, G->d_iters, G->d_rho, G->d_ctl, cond, set_cond, st,
+                              G->d_one);
   return e;
 }
 
-// The zero dz-weighted mean of p restored (Neumann boxes that stopped after
-// one FP32 solve, as the single solve does: the mean from the running
-// weighted sum of the corrections), and the iteration counts and residuals
-// copied out.
+// Boxes that stopped after one FP32 solve: p from that correction, less the
+// solution's dz-weighted mean for Neumann boxes (from the running weighted
+// sum of the corrections), as the single solve does; then the iteration
+// counts and residuals copied out.
 cudaError_t poisson_tail(cfs_group* G, cudaStream_t st) {
   const int nb = G->nbox;
   GroupMap g{G->d_sone, G->d_mean, nb};
   cudaError_t e =
       launch_group_refine_stage(GSTAGE_MEAN_FROM_NUM, G->d_res, g, G->tone, G->d_io, 0, st);
-  g.start = G->d_ssub;
+  g = GroupMap{G->d_ssub, G->d_one, nb};
   if (e == cudaSuccess)
-    e = launch_group_refine_stage(GSTAGE_SUBTRACT, G->d_res, g, G->tsub, G->d_io, 0, st);
+    e = launch_group_refine_stage(GSTAGE_FIRST_ONLY, G->d_res, g, G->tsub, G->d_io, 0, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(G->h_iters, G->d_iters, sizeof(int) * nb, kD2H, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(G->h_rho, G->d_rho, sizeof(double) * nb, kD2H, st);
   return e;

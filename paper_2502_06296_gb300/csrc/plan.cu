@@ -160,7 +160,8 @@ static void plan_free(cfs_plan* P) {
   cudaFree(P->d_bwd32);
   cudaFree(P->d_r32);
   cudaFree(P->d_r32b);
-  cudaFree(P->d_rdf);
+  cudaFree(P->d_rlo);
+  cudaFree(P->d_w2);
   cudaFree(P->d_zk);
   cudaFree(P->d_mpart);
   cudaFree(P->d_red);
@@ -410,7 +411,8 @@ extern "C" int cfs_plan_create_walls(cfs_plan_t* out, int nx, int ny, int nz, do
       rc = dev_upload<double>(&P->d_mpart, nullptr, ((size_t)nx * ny + 127) / 128,
                               &P->device_bytes);
     if (!rc) rc = dev_upload<float>(&P->d_r32b, nullptr, (size_t)nx * ny * nz, &P->device_bytes);
-    if (!rc) rc = dev_upload<float2>(&P->d_rdf, nullptr, (size_t)nx * ny * nz, &P->device_bytes);
+    if (!rc) rc = dev_upload<float>(&P->d_rlo, nullptr, (size_t)nx * ny * nz, &P->device_bytes);
+    if (!rc) rc = dev_upload<float>(&P->d_w2, nullptr, (size_t)nx * ny * nz, &P->device_bytes);
   }
 
   if (!rc) rc = dev_upload(&dA, A.data(), A.size(), &scratch);

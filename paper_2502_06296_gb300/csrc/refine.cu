@@ -203,8 +203,8 @@ __host__ __device__ inline double start_norm(const unsigned int* words, double m
 // each pair as (hi, lo).
 template <class I>
 __device__ __forceinline__ void poisson_update_body(const float* __restrict__ dlt,
-                                                    float2* __restrict__ rdf,
-                                                    float* __restrict__ r32,
+                                                    float* __restrict__ rhi,
+                                                    float* __restrict__ rlo,
                                                     const float4* __restrict__ zk,
                                                     unsigned int* rmax, int nx, int ny, int nz,
                                                     int ybc, double* mpart, long long blk) {
@@ -233,14 +233,14 @@ __device__ __forceinline__ void poisson_update_body(const float* __restrict__ dl
     float dkm = 0.0f, dk = dlt[col];
     float dkp = (nz > 1) ? dlt[nxy + col] : 0.0f;
     float xp = dlt[ip], xm = dlt[im], yp = dlt[jp], ym = dlt[jm];
-    float2 rp = rdf[col];
+    float2 rp = make_float2(rhi[col], rlo[col]);
     for (int k = 0; k < nz; ++k) {
       const I o = (I)k * nxy;
       const bool more = k + 1 < nz;
       const I on = more ? o + nxy : o;  // plane k + 1 (clamped)
       const float dkp2 = (k + 2 < nz) ? dlt[on + nxy + col] : 0.0f;
       const float xpn = dlt[on + ip], xmn = dlt[on + im], ypn = dlt[on + jp], ymn = dlt[on + jm];
-      const float2 rpn = rdf[on + col];
+      const float2 rpn = make_float2(rhi[on + col], rlo[on + col]);
       const float4 ac = zk[3 * k], bw = zk[3 * k + 1];
       DoubleFloat acc;
       df_acc<true>(acc, bw.x, bw.y, dk);
@@ -256,10 +256,9 @@ __device__ __forceinline__ void poisson_update_body(const float* __restrict__ dl
       two_sum(rp.x, -acc.s, sh, se);
       se = __fadd_rn(se, __fsub_rn(rp.y, acc.e));
       two_sum(sh, se, hi, lo);
-      rdf[o + col] = make_float2(hi, lo);
-      const float rf = hi;
-      r32[o + col] = rf;
-      vmax = fmaxf(vmax, fabsf(rf));
+      rhi[o + col] = hi;  // also the next FP32 right-hand side
+      rlo[o + col] = lo;
+      vmax = fmaxf(vmax, fabsf(hi));
       if (mpart) df_acc<false>(macc, bw.z, bw.w, dk);
       dkm = dk;
       dk = dkp;
@@ -284,10 +283,10 @@ inline __host__ __device__ bool res_idx32(int nx, int ny, int nz) {
 
 template <class I>
 __global__ void __launch_bounds__(kResBlock) poisson_update_kernel(
-    const float* __restrict__ dlt, float2* __restrict__ rdf, float* __restrict__ r32,
+    const float* __restrict__ dlt, float* __restrict__ rhi, float* __restrict__ rlo,
     const float4* __restrict__ zk, unsigned int* rmax, int nx, int ny, int nz, int ybc,
     double* mpart) {
-  poisson_update_body<I>(dlt, rdf, r32, zk, rmax, nx, ny, nz, ybc, mpart, blockIdx.x);
+  poisson_update_body<I>(dlt, rhi, rlo, zk, rmax, nx, ny, nz, ybc, mpart, blockIdx.x);
 }
 
 // ----------------------------------------------------------------------------
@@ -337,8 +336,9 @@ __device__ __forceinline__ void diff_acc(DoubleFloat& acc, float ch, float cl, f
 template <class I>
 __device__ __forceinline__ void poisson_first_body(
     const double* __restrict__ f, const double* __restrict__ mean, const float* __restrict__ dlt,
-    float2* __restrict__ rdf, float* __restrict__ r32, const float4* __restrict__ zk,
-    unsigned int* rmax, int nx, int ny, int nz, int ybc, double* mpart, long long blk) {
+    float* __restrict__ rhi, float* __restrict__ rlo, const float4* __restrict__ zk,
+    unsigned int* rmax, int nx, int ny, int nz, int ybc, double* mpart, long long blk,
+    float* __restrict__ dcopy) {
   const I nxy = (I)nx * ny;
   const I col = (I)(blk * blockDim.x + threadIdx.x);
   float vmax = 0.0f;
@@ -387,8 +387,9 @@ __device__ __forceinline__ void poisson_first_body(
       two_sum(fh, -acc.s, sh, se);
       se = __fadd_rn(se, __fsub_rn(fl, acc.e));
       two_sum(sh, se, hi, lo);
-      rdf[o + col] = make_float2(hi, lo);
-      r32[o + col] = hi;
+      rhi[o + col] = hi;  // also the next FP32 right-hand side
+      rlo[o + col] = lo;
+      dcopy[o + col] = dk;  // the correction, for the pass that writes p
       vmax = fmaxf(vmax, fabsf(hi));
       if (mpart) df_acc<false>(macc, dw.z, dw.w, dk);
       dkm = dk;
@@ -408,9 +409,10 @@ __device__ __forceinline__ void poisson_first_body(
 template <class I>
 __global__ void __launch_bounds__(kResBlock) poisson_first_kernel(
     const double* __restrict__ f, const double* __restrict__ mean, const float* __restrict__ dlt,
-    float2* __restrict__ rdf, float* __restrict__ r32, const float4* __restrict__ zk,
-    unsigned int* rmax, int nx, int ny, int nz, int ybc, double* mpart) {
-  poisson_first_body<I>(f, mean, dlt, rdf, r32, zk, rmax, nx, ny, nz, ybc, mpart, blockIdx.x);
+    float* __restrict__ rhi, float* __restrict__ rlo, const float4* __restrict__ zk,
+    unsigned int* rmax, int nx, int ny, int nz, int ybc, double* mpart, float* __restrict__ dcopy) {
+  poisson_first_body<I>(f, mean, dlt, rhi, rlo, zk, rmax, nx, ny, nz, ybc, mpart, blockIdx.x,
+                        dcopy);
 }
 
 // The dz-weighted sum of a correction, from the per-block sums of the
@@ -493,17 +495,21 @@ __global__ void __launch_bounds__(kResBlock) helm_residual_kernel(
   helm_residual_body(rhs, u, r32, abc, rmax, ncols, n, nz, mode, blockIdx.x);
 }
 
-// p -= mean (the dz-weighted mean of p, from its running weighted sum).
-__device__ __forceinline__ void subtract_mean_body(double* __restrict__ p, long long n,
-                                                   const double* __restrict__ mean, long long blk,
-                                                   long long nblk) {
-  const double mu = *mean;
-  for (long long i = blk * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) p[i] -= mu;
+// A solve that stopped after its first FP32 solve: p is that correction (the
+// passes keep it in FP32 until a second one is added), less the solution's
+// dz-weighted mean (mean may be null: no null space).
+__device__ __forceinline__ void first_only_body(double* __restrict__ p,
+                                                const float* __restrict__ delta, long long n,
+                                                const double* __restrict__ mean, long long blk,
+                                                long long nblk) {
+  const double mu = mean ? *mean : 0.0;
+  for (long long i = blk * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x)
+    p[i] = f32_to_f64(delta[i]) - mu;
 }
 
-__global__ void subtract_mean_kernel(double* __restrict__ p, long long n,
-                                     const double* __restrict__ mean) {
-  subtract_mean_body(p, n, mean, blockIdx.x, gridDim.x);
+__global__ void first_only_kernel(double* __restrict__ p, const float* __restrict__ delta,
+                                  long long n, const double* __restrict__ mean) {
+  first_only_body(p, delta, n, mean, blockIdx.x, gridDim.x);
 }
 
 // ----------------------------------------------------------------------------
@@ -537,11 +543,11 @@ __global__ void __launch_bounds__(kResBlock) poisson_first_group_kernel(const Re
   const double* mean = r.neumann ? r.mean : nullptr;
   double* mpart = r.neumann ? r.mpart : nullptr;
   if (res_idx32(r.nx, r.ny, r.nz))
-    poisson_first_body<int>(io[b].f, mean, r.r32, r.rdf, r.r32b, r.zk, r.rmax, r.nx, r.ny, r.nz,
-                            r.ybc, mpart, blk);
+    poisson_first_body<int>(io[b].f, mean, r.r32, r.r32b, r.rlo, r.zk, r.rmax, r.nx, r.ny, r.nz,
+                            r.ybc, mpart, blk, r.dcopy);
   else
-    poisson_first_body<long long>(io[b].f, mean, r.r32, r.rdf, r.r32b, r.zk, r.rmax, r.nx, r.ny,
-                                  r.nz, r.ybc, mpart, blk);
+    poisson_first_body<long long>(io[b].f, mean, r.r32, r.r32b, r.rlo, r.zk, r.rmax, r.nx, r.ny,
+                                  r.nz, r.ybc, mpart, blk, r.dcopy);
 }
 
 // One block per box (Neumann boxes; the others have nothing to sum).
@@ -579,19 +585,19 @@ __global__ void __launch_bounds__(kResBlock) poisson_update_group_kernel(const R
   const ResBox& r = boxes[b];
   double* mpart = r.neumann ? r.mpart : nullptr;
   if (res_idx32(r.nx, r.ny, r.nz))
-    poisson_update_body<int>(r.r32, r.rdf, r.r32b, r.zk, r.rmax, r.nx, r.ny, r.nz, r.ybc, mpart,
+    poisson_update_body<int>(r.r32, r.r32b, r.rlo, r.zk, r.rmax, r.nx, r.ny, r.nz, r.ybc, mpart,
                              blk);
   else
-    poisson_update_body<long long>(r.r32, r.rdf, r.r32b, r.zk, r.rmax, r.nx, r.ny, r.nz, r.ybc,
+    poisson_update_body<long long>(r.r32, r.r32b, r.rlo, r.zk, r.rmax, r.nx, r.ny, r.nz, r.ybc,
                                    mpart, blk);
 }
 
-__global__ void subtract_mean_group_kernel(const ResBox* boxes, GroupMap g, const GroupIo* io) {
+__global__ void first_only_group_kernel(const ResBox* boxes, GroupMap g, const GroupIo* io) {
   int b, blk;
   if (!group_block(g, &b, &blk)) return;
   const ResBox& r = boxes[b];
   const long long n = (long long)r.nx * r.ny * r.nz;
-  subtract_mean_body(io[b].p, n, r.mean, blk, group_sub_blocks(n));
+  first_only_body(io[b].p, r.r32, n, r.neumann ? r.mean : nullptr, blk, group_sub_blocks(n));
 }
 
 // Zero solution of the boxes whose right-hand side is zero.
@@ -614,7 +620,7 @@ __global__ void zero_fill_group_kernel(const ResBox* boxes, GroupMap g, const Gr
 // solution mean is removed at the end.  Every box starts at 0 iterations.
 __global__ void group_start_kernel(const ResBox* boxes, int nbox, int keys, double* fmax,
                                    const int* eligible, int* active, int* mean_on, int* zero,
-                                   int* iters, double* rho, GroupCtl* ctl) {
+                                   int* iters, double* rho, GroupCtl* ctl, int* one) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b == 0) {
     ctl->it = 0;
@@ -630,6 +636,7 @@ __global__ void group_start_kernel(const ResBox* boxes, int nbox, int keys, doub
   const int on = elig && f != 0.0;
   active[b] = on;
   if (mean_on) mean_on[b] = on && boxes[b].neumann;
+  if (one) one[b] = on;
   if (boxes[b].mnum) *boxes[b].mnum = 0.0;
   zero[b] = elig && !on;
   iters[b] = 0;
@@ -646,7 +653,7 @@ __global__ void group_start_kernel(const ResBox* boxes, int nbox, int keys, doub
 __global__ void __launch_bounds__(1024) group_iter_end_kernel(
     const ResBox* boxes, int nbox, const double* fmax, const double* tol, const int* maxit,
     int* active, int* mean_on, int* iters, double* rho, GroupCtl* ctl,
-    cudaGraphConditionalHandle cond, int set_cond) {
+    cudaGraphConditionalHandle cond, int set_cond, int* one) {
   __shared__ int count;
   if (threadIdx.x == 0) count = 0;
   __syncthreads();
@@ -663,6 +670,7 @@ __global__ void __launch_bounds__(1024) group_iter_end_kernel(
     if (r <= tol[b] || it + 1 >= maxit[b]) {
       active[b] = 0;
       if (mean_on && it >= 1) mean_on[b] = 0;
+      if (one && it >= 1) one[b] = 0;  // more than one correction: p was written
     } else {
       ++mine;
     }
@@ -715,8 +723,8 @@ cudaError_t launch_group_refine_stage(int stage, const ResBox* boxes, GroupMap g
     case GSTAGE_MEAN_FROM_NUM:
       mean_from_num_group_kernel<<<total, 32, 0, st>>>(boxes, g);
       break;
-    default:
-      subtract_mean_group_kernel<<<total, 256, 0, st>>>(boxes, g, io);
+    default:  // GSTAGE_FIRST_ONLY
+      first_only_group_kernel<<<total, 256, 0, st>>>(boxes, g, io);
       break;
   }
   return cudaGetLastError();
@@ -724,18 +732,20 @@ cudaError_t launch_group_refine_stage(int stage, const ResBox* boxes, GroupMap g
 
 cudaError_t launch_group_start(const ResBox* boxes, int nbox, int keys, double* fmax,
                                const int* eligible, int* active, int* mean_on, int* zero,
-                               int* iters, double* rho, GroupCtl* ctl, cudaStream_t st) {
+                               int* iters, double* rho, GroupCtl* ctl, cudaStream_t st, int* one) {
   group_start_kernel<<<(nbox + 127) / 128, 128, 0, st>>>(boxes, nbox, keys, fmax, eligible,
-                                                         active, mean_on, zero, iters, rho, ctl);
+                                                         active, mean_on, zero, iters, rho, ctl,
+                                                         one);
   return cudaGetLastError();
 }
 
 cudaError_t launch_group_iter_end(const ResBox* boxes, int nbox, const double* fmax,
                                   const double* tol, const int* maxit, int* active,
                                   int* mean_on, int* iters, double* rho, GroupCtl* ctl,
-                                  cudaGraphConditionalHandle cond, int set_cond, cudaStream_t st) {
+                                  cudaGraphConditionalHandle cond, int set_cond, cudaStream_t st,
+                                  int* one) {
   group_iter_end_kernel<<<1, 1024, 0, st>>>(boxes, nbox, fmax, tol, maxit, active, mean_on,
-                                            iters, rho, ctl, cond, set_cond);
+                                            iters, rho, ctl, cond, set_cond, one);
   return cudaGetLastError();
 }
 
@@ -865,19 +875,25 @@ int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st) {
     if (e == cudaSuccess) e = launch_fft_y32(P, P->d_r32, false, st);
     if (e == cudaSuccess) e = launch_thomas32(P, P->d_r32, st);
     if (e == cudaSuccess) e = launch_fft_y32(P, P->d_r32, true, st);
-    if (e == cudaSuccess)
-      e = launch_rfft_x32_to64(P, P->d_r32, p, it > 0, st, P->has_null ? mean_num(P) : nullptr);
+    // the first correction stays in FP32 (the first residual keeps a copy in
+    // w2); the second pass writes p = both once, later passes add to p
+    const double* msum = P->has_null ? mean_num(P) : nullptr;
+    if (e == cudaSuccess) {
+      if (it == 0) e = launch_rfft_x32(P, P->d_r32, P->d_r32, true, st);
+      else if (it == 1) e = launch_rfft_x32_sum(P, P->d_r32, p, P->d_w2, st, msum);
+      else e = launch_rfft_x32_to64(P, P->d_r32, p, true, st, msum);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(P->d_red, 0, sizeof(unsigned int), st);
     // (Neumann: each kernel also sums its correction, dz-weighted, per block)
     double* mpart = P->has_null ? P->d_mpart : nullptr;
     if (e == cudaSuccess && it == 0) {  // r = (f - mean) - L delta, by differences
       auto k = idx32 ? poisson_first_kernel<int> : poisson_first_kernel<long long>;
-      k<<<grid, kResBlock, 0, st>>>(f, mean, P->d_r32, P->d_rdf, P->d_r32b, P->d_zk, max_word(P),
-                                    P->nx, P->ny, P->nz, P->ybc, mpart);
+      k<<<grid, kResBlock, 0, st>>>(f, mean, P->d_r32, P->d_r32b, P->d_rlo, P->d_zk, max_word(P),
+                                    P->nx, P->ny, P->nz, P->ybc, mpart, P->d_w2);
       e = cudaGetLastError();
     } else if (e == cudaSuccess) {  // r -= L delta
       auto k = idx32 ? poisson_update_kernel<int> : poisson_update_kernel<long long>;
-      k<<<grid, kResBlock, 0, st>>>(P->d_r32, P->d_rdf, P->d_r32b, P->d_zk, max_word(P), P->nx,
+      k<<<grid, kResBlock, 0, st>>>(P->d_r32, P->d_r32b, P->d_rlo, P->d_zk, max_word(P), P->nx,
                                     P->ny, P->nz, P->ybc, mpart);
       e = cudaGetLastError();
     }
@@ -893,19 +909,21 @@ int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st) {
     P->last_rho = (double)rmax / (double)fmax;
     if (P->last_rho <= P->tol) break;
   }
-  if (P->has_null && P->last_iters == 1) {
-    // The residual cannot see a constant, so the FP32 rounding of each
-    // correction's mean would accumulate unchecked.  p is the sum of the
-    // corrections (each added in FP64), so its dz-weighted sum is the sum of
-    // theirs, accumulated by the residual kernels that read every correction
+  if (P->last_iters == 1) {
+    // p is still the first correction, in FP32: written here.  The residual
+    // cannot see a constant, so the FP32 rounding of each correction's mean
+    // would accumulate unchecked.  p is the sum of the corrections (each
+    // added in FP64), so its dz-weighted sum is the sum of theirs,
+    // accumulated by the residual kernels that read every correction
     // (double-float per column, FP64 across columns, in a fixed order).  Each
     // correction pass after the first subtracts the mean so far from its
     // correction; what is left is the mean of the last correction, at the
     // FP32 rounding of a correction that is itself small.  A solve that
     // stopped after its first FP32 solve has the mean of that solve left:
-    // it is removed here.
-    mean_from_num_kernel<<<1, 32, 0, st>>>(mean_num(P), P->inv_wn, P->d_red + 1);
-    subtract_mean_kernel<<<1216, 256, 0, st>>>(p, nxy * P->nz, P->d_red + 1);
+    // it is removed here (Neumann).
+    if (P->has_null) mean_from_num_kernel<<<1, 32, 0, st>>>(mean_num(P), P->inv_wn, P->d_red + 1);
+    first_only_kernel<<<1216, 256, 0, st>>>(p, P->d_r32, nxy * P->nz,
+                                            P->has_null ? P->d_red + 1 : nullptr);
     rc = cuda_rc(cudaGetLastError());
     if (rc) return rc;
   }
