@@ -527,6 +527,64 @@ def run_ensemble(chanfs, torch, device, reps: int = 3):
                       "L2 in total (no flush between steps)"}
 
 
+HELM_SIZES = [(128, 96, 64, 2.2, 1e-4), (192, 192, 128, 2.0, 3e-5), (256, 192, 192, 1.8, 1e-5),
+              (512, 384, 384, 1.8, 9.615e-9)]
+
+
+def run_refined_helmholtz(chanfs, torch, device, reps: int = 7, sizes=HELM_SIZES):
+    """z-implicit Helmholtz per size (ensemble and serving shapes): FP64
+    Algorithm 2, FP64 Thomas sweeps, and the refined solves of a
+    CFS_F32_REFINED plan -- one pass over the field (FP32 Algorithm 2 and
+    double-float residuals on chip) at each partition count it runs with,
+    and the loop with FP32 Thomas inner solves -- median CUDA-event times."""
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    out = []
+    gen = torch.Generator(device=device)
+    gen.manual_seed(1234)
+    for nx, ny, nz, beta, c in sizes:
+        dz = synth.tanh_dz(nz, beta)
+        r = torch.randn(nz, ny, nx, dtype=torch.float64, device=device, generator=gen)
+        u = torch.empty_like(r)
+        row = {"size": f"{nx}x{ny}x{nz}", "c": c}
+        with chanfs.Plan(nx, ny, nz, 12.8, 6.4, dz, chanfs.NEUMANN, chanfs.F64) as p64:
+            for th, name in ((0, "f64_algorithm2_ms"), (1, "f64_thomas_ms")):
+                p64.set_option(chanfs.OPT_HELM_THOMAS, th)
+                row[name] = round(timed(lambda: p64.helmholtz_solve(c, r, 0, out=u)), 4)
+        with chanfs.Plan(nx, ny, nz, 12.8, 6.4, dz, chanfs.NEUMANN, chanfs.F32_REFINED) as p32:
+            one = {}
+            for parts in (8, 16, 32):
+                try:
+                    p32.set_option(chanfs.OPT_PCR_PARTS, parts)
+                except chanfs.ChanfsError:
+                    continue
+                if (nz + parts - 1) // parts > 32:
+                    continue  # more rows per partition than the one-pass kernel holds
+                with nvtx_range(f"refined_helmholtz_{nx}x{ny}x{nz}_p{parts}"):
+                    t = timed(lambda: p32.helmholtz_solve(c, r, 0, out=u))
+                it, rho = p32.last_info()
+                one[str(parts)] = {"ms": round(t, 4), "fp32_solves": it, "rel_residual": rho}
+            row["refined_one_pass"] = one
+            p32.set_option(chanfs.OPT_PCR_PARTS, 0)
+            p32.set_option(chanfs.OPT_HELM_THOMAS32, 1)
+            row["refined_thomas_loop_ms"] = round(timed(lambda: p32.helmholtz_solve(c, r, 0, out=u)), 4)
+        out.append(row)
+    return {"what": "median CUDA-event ms per Helmholtz solve, rhs N(0,1), Dirichlet centred",
+            "sizes": out}
+
+
 def run_cufft_comparison(torch, f, stage_ms, reps: int = 5):
     """cuFFT (through torch.fft) D2Z / Z2D over (y, x) of the FP64 channel
     field, timed for comparison only (the library does not use it), beside
@@ -762,6 +820,22 @@ def run_mixed_only(args):
     mixed = run_mixed(chanfs, torch, torch.device("cuda", 0), reps=args.steps, warmup=args.warmup,
                       nz=args.mixed_nz)
     print(json.dumps({"mixed": mixed}), flush=True)
+    return 0
+
+
+def run_helmholtz_only(args):
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2502_06296_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2502_06296_gb300 import chanfs
+    sizes = HELM_SIZES
+    if args.helm_size:
+        nx, ny, nz = (int(v) for v in args.helm_size.split("x"))
+        sizes = [(nx, ny, nz, 1.8, 1e-5)]
+    out = run_refined_helmholtz(chanfs, torch, torch.device("cuda", 0), reps=args.steps,
+                                sizes=sizes)
+    print(json.dumps({"refined_helmholtz": out}), flush=True)
     return 0
 
 
@@ -1040,6 +1114,7 @@ def run_ours(args):
     if not args.no_stress:
         line["stress"] = run_stress(chanfs, torch, device)
     if not args.no_mixed:
+        line["refined_helmholtz"] = run_refined_helmholtz(chanfs, torch, device)
         line["mixed"] = run_mixed(chanfs, torch, device)
     if not args.no_ensemble:
         line["ensemble"] = run_ensemble(chanfs, torch, device)
@@ -1062,7 +1137,8 @@ def main(argv=None):
     ap.add_argument("--nparts", type=int, default=0, help="PCR partitions (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true",
-                    help="skip the FP32-refined vs FP64 solve of the 1024x768x512 workload")
+                    help="skip the FP32-refined vs FP64 comparisons (Helmholtz per size and "
+                         "the 1024x768x512 workload)")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 48-box ensemble")
     ap.add_argument("--no-stress", action="store_true",
                     help="skip the 3456x3072x30 single-GPU box")
@@ -1075,6 +1151,10 @@ def main(argv=None):
                     help="wall-normal size of the mixed comparison (profiling captures only)")
     ap.add_argument("--mixed-only", action="store_true",
                     help="run only the FP32-refined vs FP64 comparison and print its object")
+    ap.add_argument("--helmholtz-only", action="store_true",
+                    help="time only the FP64 and refined Helmholtz solves per size")
+    ap.add_argument("--helm-size", default="",
+                    help="with --helmholtz-only: one size NXxNYxNZ (stretching 1.8, c = 1e-5)")
     ap.add_argument("--probe-only", action="store_true",
                     help="measure only the FP64 and FP32 FMA rates (--steps repetitions)")
     ap.add_argument("--slab", action="store_true",
@@ -1091,6 +1171,8 @@ def main(argv=None):
         return run_mixed_only(args)
     if args.probe_only:
         return run_probe_only(args)
+    if args.helmholtz_only:
+        return run_helmholtz_only(args)
     if args.slab:
         return run_slab(args)
     if args.extras_only:

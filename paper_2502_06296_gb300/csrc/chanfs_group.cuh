@@ -71,6 +71,21 @@ struct ThomasArgs {  // z sweeps of Eq. 12 (thomas.cu)
   int ywall;             // y walls: every slot ky is its own column (no +-ky pairs)
 };
 
+// The partitioned FP32 z solve of Eq. 12 (Algorithm 2 over register-resident
+// z-partitions, thomas.cu).
+struct ZPartArgs {
+  ThomasArgs t;        // spectrum, sizes; the special columns' factors
+  const float4* zrow;  // (A_k, B_k, C_k, 1) / s of the z operator for k < nz (s the
+                       // inverse-FFT normalisation), then (0, 1, 0, 0) rows: x = 0,
+                       // uncoupled (the wall row has C = 0)
+  const float* lam;    // lx[0..M] then ly[0..nky), divided by s
+  int P;               // partitions per column
+  int C;               // columns per tile (C * P of the CTA's 256 threads work)
+  int ntx;             // tiles along kx per slot pair
+  int nsp;             // blocks of the special columns (first in the grid)
+  int mm;              // rows per partition (8)
+};
+
 struct ResBox {  // refinement residual and norms (refine.cu)
   const double* abc;   // Helmholtz: A' | B' | C'
   const double* dzf;   // cell widths
@@ -254,5 +269,12 @@ enum {
 size_t x_group_box(const cfs_plan* P, bool inverse, XBox* box, int* blocks);
 size_t y_group_box(const cfs_plan* P, YBox* box, int* blocks);
 size_t thomas_group_box(const cfs_plan* P, ThomasArgs* box, int* blocks);
+// Boxes whose plans take the partitioned FP32 z solve (CFS_OPT_THOMAS_TILE 1)
+// run it in their grouped solves too, so that a box's bits match its solve
+// alone.
+bool zpart_group_member(const cfs_plan* P);
+size_t zpart_group_box(const cfs_plan* P, ZPartArgs* box, int* blocks);  // returns smem
+cudaError_t launch_zpart_group(const ZPartArgs* boxes, GroupMap g, int total, size_t smem,
+                               cudaStream_t st);
 
 }  // namespace chanfs

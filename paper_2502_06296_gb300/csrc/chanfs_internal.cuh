@@ -100,6 +100,9 @@ struct Helm3Coef {
 // Chunks per z plane of the refined Poisson start pass (refine.cu): about
 // 2432 blocks (16 per SM) over the nz planes, at most kMaxStartChunks.
 constexpr int kMaxStartChunks = 16;
+// Rows appended to the FP32 z-operator table for the partitioned z solve (its
+// partitions have 8 or 16 rows; the last one may extend past nz).
+constexpr int kZPartRowPad = 16;
 inline __host__ __device__ int start_chunks(int nz) {
   const int c = (2432 + nz - 1) / nz;
   return c < 1 ? 1 : (c > kMaxStartChunks ? kMaxStartChunks : c);
@@ -133,7 +136,8 @@ struct cfs_plan {
   double2* d_fwd;    // (s/piv_k, A_k/piv_k)
   double* d_bwd;     // C_k/piv_k
   int thomas_tw;     // columns per shared-memory Thomas tile: 0 automatic,
-                     // 8 or 16 forced, -1 the streaming kernel
+                     // 8 or 16 forced, -1 the streaming kernel, 1 the partitioned
+                     // FP32 solve (Algorithm 2 in registers)
   int x_lines;       // x-lines per CTA of the x transforms (0: about 16 KB of data)
   int tk_auto, tk32_auto;  // y tile widths chosen at creation
   int pcr_parts;     // partitions of Helmholtz sets prepared without a count (0: auto)
@@ -155,6 +159,9 @@ struct cfs_plan {
   float2* d_fwd32;   // FP32 copies of the Thomas factors
   float* d_bwd32;
   int kx64, ky64;    // columns kx < kx64, min(ky, Ny-ky) < ky64 stay FP64
+  float4* d_zrow32;  // (A_k, B_k, C_k, 1) of the z operator in FP32, then kZPartRowPad
+                     // identity rows (0, 1, 0, 0) (partitioned z solve, thomas.cu)
+  float* d_lam32;    // lx[0..M] then ly[0..nky) in FP32
   float* d_r32;      // FP32 residual / correction field (in-place inner solve)
   float* d_r32b;     // the residual kept between iterations, high part (FP32 input of the
                      // next solve)

@@ -54,12 +54,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
 // copies of this phase still in flight land before the CTA's shared memory
 // is released, and false is returned: the caller then exits, CTA-uniformly,
 // storing nothing.  Must be reached by every thread of the CTA.
-__device__ __forceinline__ bool cta_wait(uint64_t* bar, uint32_t parity, int* status,
-                                         uint32_t polls = kWaitPolls) {
-  if (__syncthreads_and(mbar_wait(bar, parity, polls) ? 1 : 0)) return true;
+// (The failure path is a call of its own: inlined into the x transform it
+// cost the FP64 inverse 13 % of its time.)
+static __device__ __noinline__ void cta_wait_failed(uint64_t* bar, uint32_t parity, int* status,
+                                                    uint32_t polls) {
   if (threadIdx.x == 0) atomicOr(status, kErrTmaTimeout);
   mbar_wait(bar, parity, polls);
   __syncthreads();
+}
+
+__device__ __forceinline__ bool cta_wait(uint64_t* bar, uint32_t parity, int* status,
+                                         uint32_t polls = kWaitPolls) {
+  if (__syncthreads_and(mbar_wait(bar, parity, polls) ? 1 : 0)) return true;
+  cta_wait_failed(bar, parity, status, polls);
   return false;
 }
 

@@ -47,7 +47,7 @@ std::vector<int> offsets(const std::vector<int>& blocks, int* total) {
 // Descriptor tables of a bound group, at fixed offsets of one device buffer
 // (and of its pinned host staging copy) sized for the group's capacity.
 struct GroupTables {
-  size_t xf, xi, y, th, res, sx, sy, sth, sres, splane, sone, ssub, neu, bytes;
+  size_t xf, xi, y, th, zp, res, sx, sy, sth, szp, sres, splane, sone, ssub, neu, bytes;
   explicit GroupTables(int cap) {
     size_t o = 0;
     auto take = [&](size_t n) {
@@ -59,10 +59,12 @@ struct GroupTables {
     xi = take(sizeof(XBox) * cap);
     y = take(sizeof(YBox) * cap);
     th = take(sizeof(ThomasArgs) * cap);
+    zp = take(sizeof(ZPartArgs) * cap);
     res = take(sizeof(ResBox) * cap);
     sx = take(sizeof(int) * (cap + 1));
     sy = take(sizeof(int) * (cap + 1));
     sth = take(sizeof(int) * (cap + 1));
+    szp = take(sizeof(int) * (cap + 1));
     sres = take(sizeof(int) * (cap + 1));
     splane = take(sizeof(int) * (cap + 1));
     sone = take(sizeof(int) * (cap + 1));
@@ -85,13 +87,14 @@ struct cfs_group {
   XBox* d_xf = nullptr;
   XBox* d_xi = nullptr;
   YBox* d_y = nullptr;
-  ThomasArgs* d_th = nullptr;
+  ThomasArgs* d_th = nullptr;  // streaming z sweeps
+  ZPartArgs* d_zp = nullptr;    // partitioned z solves
   ResBox* d_res = nullptr;
-  int *d_sx = nullptr, *d_sy = nullptr, *d_sth = nullptr, *d_sres = nullptr;
+  int *d_sx = nullptr, *d_sy = nullptr, *d_sth = nullptr, *d_szp = nullptr, *d_sres = nullptr;
   int *d_splane = nullptr, *d_sone = nullptr, *d_ssub = nullptr;
   int* d_neumann = nullptr;  // boxes whose operator has the constants as null space
-  int tx = 0, ty = 0, tth = 0, tres = 0, tplane = 0, tone = 0, tsub = 0;
-  size_t smem_x = 0, smem_y = 0;
+  int tx = 0, ty = 0, tth = 0, tzp = 0, tres = 0, tplane = 0, tone = 0, tsub = 0;
+  size_t smem_x = 0, smem_y = 0, smem_zp = 0;
   // refinement state
   int* d_active = nullptr;  // boxes still iterating
   int* d_mean = nullptr;    // boxes whose mean is removed (Neumann, nonzero rhs)
@@ -283,10 +286,12 @@ static int group_alloc(cfs_group* G, int cap) {
   G->d_xi = reinterpret_cast<XBox*>(G->d_tab + t.xi);
   G->d_y = reinterpret_cast<YBox*>(G->d_tab + t.y);
   G->d_th = reinterpret_cast<ThomasArgs*>(G->d_tab + t.th);
+  G->d_zp = reinterpret_cast<ZPartArgs*>(G->d_tab + t.zp);
   G->d_res = reinterpret_cast<ResBox*>(G->d_tab + t.res);
   G->d_sx = reinterpret_cast<int*>(G->d_tab + t.sx);
   G->d_sy = reinterpret_cast<int*>(G->d_tab + t.sy);
   G->d_sth = reinterpret_cast<int*>(G->d_tab + t.sth);
+  G->d_szp = reinterpret_cast<int*>(G->d_tab + t.szp);
   G->d_sres = reinterpret_cast<int*>(G->d_tab + t.sres);
   G->d_splane = reinterpret_cast<int*>(G->d_tab + t.splane);
   G->d_sone = reinterpret_cast<int*>(G->d_tab + t.sone);
@@ -314,13 +319,14 @@ static int group_bind(cfs_group* G, int nplans, const cfs_plan_t* plans, cudaStr
   XBox* xi = reinterpret_cast<XBox*>(G->h_tab + t.xi);
   YBox* y = reinterpret_cast<YBox*>(G->h_tab + t.y);
   ThomasArgs* th = reinterpret_cast<ThomasArgs*>(G->h_tab + t.th);
+  ZPartArgs* zp = reinterpret_cast<ZPartArgs*>(G->h_tab + t.zp);
   ResBox* res = reinterpret_cast<ResBox*>(G->h_tab + t.res);
-  std::vector<int> bx(nplans), by(nplans), bth(nplans), bres(nplans), bplane(nplans),
-      bone(nplans, 1), bsub(nplans);
+  std::vector<int> bx(nplans), by(nplans), bth(nplans), bzp(nplans, 0), bres(nplans),
+      bplane(nplans), bone(nplans, 1), bsub(nplans);
   G->plans.clear();
   G->neumann.clear();
   G->res.assign(nplans, ResBox{});
-  G->smem_x = G->smem_y = 0;
+  G->smem_x = G->smem_y = G->smem_zp = 0;
   for (int b = 0; b < nplans; ++b) {
     cfs_plan* P = plans[b];
     G->plans.push_back(P);
@@ -331,6 +337,10 @@ static int group_bind(cfs_group* G, int nplans, const cfs_plan_t* plans, cudaStr
     if (!sy) return CFS_ECUDA;
     G->smem_y = std::max(G->smem_y, sy);
     thomas_group_box(P, &th[b], &bth[b]);
+    if (zpart_group_member(P)) {  // the z solve its plan takes alone
+      G->smem_zp = std::max(G->smem_zp, zpart_group_box(P, &zp[b], &bzp[b]));
+      bth[b] = 0;
+    }
     const long long nxy = (long long)P->nx * P->ny;
     ResBox& r = res[b];
     memset(&r, 0, sizeof(r));
@@ -364,6 +374,7 @@ static int group_bind(cfs_group* G, int nplans, const cfs_plan_t* plans, cudaStr
   put(t.sx, offsets(bx, &G->tx));
   put(t.sy, offsets(by, &G->ty));
   put(t.sth, offsets(bth, &G->tth));
+  put(t.szp, offsets(bzp, &G->tzp));
   put(t.sres, offsets(bres, &G->tres));
   put(t.splane, offsets(bplane, &G->tplane));
   put(t.sone, offsets(bone, &G->tone));
@@ -560,6 +571,10 @@ cudaError_t poisson_iteration(cfs_group* G, int kind, cudaGraphConditionalHandle
     e = launch_thomas_group32(G->d_th, g, G->tth, st);
   }
   if (e == cudaSuccess) {
+    g.start = G->d_szp;
+    e = launch_zpart_group(G->d_zp, g, G->tzp, G->smem_zp, st);
+  }
+  if (e == cudaSuccess) {
     g.start = G->d_sy;
     e = launch_fft_y_group32(G->d_y, g, G->ty, G->smem_y, true, st);
   }
@@ -646,8 +661,9 @@ extern "C" int cfs_group_poisson_solve(cfs_group_t G, const double* const* f, do
     G->h_maxit[b] = G->plans[b]->maxit;
   }
   const std::vector<long long> sig = {0,       nb,      G->tx,     G->ty,
-                                      G->tth,  G->tres, G->tplane, G->tone,
-                                      G->tsub, (long long)G->smem_x, (long long)G->smem_y};
+                                      G->tth,  G->tzp,  G->tres,   G->tplane,
+                                      G->tone, G->tsub, (long long)G->smem_x,
+                                      (long long)G->smem_y, (long long)G->smem_zp};
   cudaGraphExec_t exec = G->graphs ? find_graph(G, sig) : nullptr;
   if (exec || (G->graphs && capture_now(G, sig))) {
     if (!exec) {

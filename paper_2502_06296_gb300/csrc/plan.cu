@@ -158,6 +158,8 @@ static void plan_free(cfs_plan* P) {
   cudaFree(P->d_post32);
   cudaFree(P->d_fwd32);
   cudaFree(P->d_bwd32);
+  cudaFree(P->d_zrow32);
+  cudaFree(P->d_lam32);
   cudaFree(P->d_r32);
   cudaFree(P->d_r32b);
   cudaFree(P->d_rlo);
@@ -365,6 +367,19 @@ extern "C" int cfs_plan_create_walls(cfs_plan_t* out, int nx, int ny, int nz, do
     }
     if (!rc) rc = dev_upload<float2>(&P->d_fwd32, nullptr, nfac, &P->device_bytes);
     if (!rc) rc = dev_upload<float>(&P->d_bwd32, nullptr, nfac, &P->device_bytes);
+    {  // the partitioned FP32 z solve forms its rows from these, divided by
+       // the inverse-FFT normalisation s (its solution then comes out scaled)
+      const double is = ((double)nx * (double)ny) / 2.0;
+      std::vector<float4> zrow(nz + kZPartRowPad, make_float4(0.0f, 1.0f, 0.0f, 0.0f));
+      for (int k = 0; k < nz; ++k)
+        zrow[k] = make_float4(k > 0 ? (float)(A[k] * is) : 0.0f, (float)(B[k] * is),
+                              k + 1 < nz ? (float)(C[k] * is) : 0.0f, 1.0f);
+      std::vector<float> lam;
+      for (double v : lamx) lam.push_back((float)(v * is));
+      for (double v : lamy) lam.push_back((float)(v * is));
+      if (!rc) rc = dev_upload(&P->d_zrow32, zrow.data(), zrow.size(), &P->device_bytes);
+      if (!rc) rc = dev_upload(&P->d_lam32, lam.data(), lam.size(), &P->device_bytes);
+    }
     if (!rc) rc = dev_upload<float>(&P->d_r32, nullptr, (size_t)nx * ny * nz, &P->device_bytes);
     if (!rc)
       rc = dev_upload<double>(&P->d_red, nullptr, (size_t)nz * start_chunks(nz) + 8,
@@ -871,8 +886,9 @@ extern "C" int cfs_plan_set_option(cfs_plan_t P, int option, int value) {
   if (!P) return CFS_EINVAL;
   switch (option) {
     case CFS_OPT_THOMAS_TILE: {
-      if (value != 0 && value != -1 && value != 8 && value != 16) return CFS_EINVAL;
+      if (value != 0 && value != -1 && value != 1 && value != 8 && value != 16) return CFS_EINVAL;
       const bool fp32 = (P->dtype == CFS_F32_REFINED);
+      if (value == 1 && !fp32) return CFS_EUNSUPPORTED;  // the partitioned solve is FP32
       if (thomas_tile_width(P, false, value) == 0 ||
           (fp32 && thomas_tile_width(P, true, value) == 0))
         return CFS_EUNSUPPORTED;

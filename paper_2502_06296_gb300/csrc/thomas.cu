@@ -22,6 +22,7 @@
 
 #include "chanfs_tma.cuh"
 #include "chanfs_group.cuh"
+#include "chanfs_alg2.cuh"
 
 namespace chanfs {
 
@@ -179,8 +180,8 @@ __device__ __forceinline__ void sweep_column(const ThomasArgs& a, CS* const s0, 
 // the special kernel takes column kx = 0 of every slot (two real columns, or
 // the singular one) and, for FP32 spectra, the FP64 columns.
 
-// Column (ky, j) in full generality.
-template <class CS>
+// Column (ky, j) in full generality; PF rows of prefetch.
+template <class CS, int PF = 1>
 __device__ __forceinline__ void thomas_column(const ThomasArgs& a, int ky, int j) {
   // factor sets of the real (x) and imaginary (y) parts
   int kx_x = j, kx_y = j, kp_x, kp_y;
@@ -207,10 +208,10 @@ __device__ __forceinline__ void thomas_column(const ThomasArgs& a, int ky, int j
   // (one row of prefetch: these few columns run beside the main ones, whose
   // register budget the kernel keeps)
   if (fp64)
-    sweep_column<CS, double2, false, 1>(a, s0, a.fwd + ox, a.fwd + oy, a.bwd + ox, a.bwd + oy,
+    sweep_column<CS, double2, false, PF>(a, s0, a.fwd + ox, a.fwd + oy, a.bwd + ox, a.bwd + oy,
                                         sing);
   else
-    sweep_column<CS, float2, false, 1>(a, s0, a.fwd32 + ox, a.fwd32 + oy, a.bwd32 + ox,
+    sweep_column<CS, float2, false, PF>(a, s0, a.fwd32 + ox, a.fwd32 + oy, a.bwd32 + ox,
                                        a.bwd32 + oy, false);
 }
 
@@ -352,14 +353,14 @@ __host__ __device__ inline int special_width(const ThomasArgs& a) {
   return w < a.M ? w : a.M;
 }
 
-template <class CS>
+template <class CS, int PF = 1>
 __device__ __forceinline__ void thomas_special_body(const ThomasArgs& a, int blk) {
   const int kxs = special_width<CS>(a);
   const int t = blk * kThomasBlock + threadIdx.x;
   const int j = t % kxs, ky = t / kxs;
   if (ky >= a.ny) return;
   if (j > 0 && !fp64_column(a, ky, j)) return;  // the main kernel's column
-  thomas_column<CS>(a, ky, j);
+  thomas_column<CS, PF>(a, ky, j);
 }
 
 template <class CS>
@@ -409,6 +410,271 @@ static cudaError_t launch_streaming(const ThomasArgs& a, cudaStream_t st) {
     }
   }
   thomas_kernel<CS, false><<<(unsigned)blocks, kThomasBlock, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// FP32 spectra: Algorithm 2 (Sec. 2.2.4) over z-partitions held in registers.
+// The streaming sweep above writes its forward intermediate to the spectrum
+// and reads it back, and reads factor tables: about 2.3 times the one read and
+// one write of the spectrum a z solve needs.  Here thread (q, c) of a CTA
+// holds rows [8q, 8q + 8) of column c of a tile of C consecutive kx, for the
+// slots ky and Ny - ky at once (they share the eigenvalue, so four real
+// right-hand sides share one elimination; one slot with y walls).  Rows past
+// Nz are identity rows x = 0, uncoupled because the wall row has C = 0.  A
+// warp's loads and stores cover C consecutive complex values of one row.  The
+// thread forms its rows of Eq. 12 on the fly from the plan's z operator and
+// eigenvalues, divided by the inverse-FFT normalisation s,
+//   (A_k F_{k-1} + (B_k + lx[kx] + ly[ky]) F_k + C_k F_{k+1}) / s = f_k
+// (FP32 arithmetic is cheap on GB300; no per-column table is read), and runs
+// Steps 1 and 2 of Algorithm 2 together, rows normalised:
+//  * downward, with x_0 a parameter: piv_i = D_i - A_i c'_{i-1} (piv_1 = D_1),
+//    c'_i = C_i / piv_i, g'_i = -A_i g'_{i-1} / piv_i (g'_1 = A_1 / D_1),
+//    d'_i = (d_i - A_i d'_{i-1}) / piv_i; row i then reads
+//    x_i + c'_i x_{i+1} + g'_i x_0 = d'_i  (i = 1 .. 7);
+//  * upward, x_i = u_i - v_i x_0 - w_i x_7 for i = 6 .. 1 carried as scalars
+//    into row 0: A_0 x_{-1} + (D_0 - C_0 v_1) x_0 - C_0 w_1 x_7 = d_0 - C_0 u_1.
+// Row 0 and row 7 of every partition form the 2P-row reduced system of the
+// column (Step 3), solved in shared memory by cyclic reduction (multipliers
+// formed on the fly; O(P) work), and each thread then recovers its interior
+// rows by back substitution in the downward form (Step 4),
+// x_i = d'_i - c'_i x_{i+1} - g'_i x_0.  Per row a thread keeps d' (two
+// complex values) and c', g' in registers; the spectrum is read once and
+// written once.  The FP64 columns of an FP32 spectrum and the kx = 0 slots
+// run in the launch's first blocks, as in the streaming kernel.
+// ----------------------------------------------------------------------------
+constexpr int kZPartThreads = 256;  // at most C * P threads per CTA
+constexpr int kZPartMaxParts = 64;
+constexpr int kZPartRows = 8;  // rows per partition (register arrays): Nz <= 512
+
+// Reciprocals by the fast hardware approximation (a few ulp): the inner
+// solve needs FP32 accuracy only, the refinement corrects the rest, and the
+// correctly rounded form would add a slow-path call per row.
+__device__ __forceinline__ float zp_rcp(float x) { return __fdividef(1.0f, x); }
+
+__device__ __forceinline__ float2 f2_fms(float2 a, float k, float2 b) {  // a - k b
+  return make_float2(fmaf(-k, b.x, a.x), fmaf(-k, b.y, a.y));
+}
+
+// Shared memory of a tile: the operator rows of the column, partition by
+// partition with one float4 of padding after each (so that the lanes of a
+// warp, which read the same row of different partitions, hit different
+// banks), then the reduced system: per row (sub, diag, sup, -) and the two
+// slots' complex right-hand sides.
+__host__ __device__ inline int zpart_rows_smem(int P, int MM) { return P * (MM + 1); }
+
+__device__ __forceinline__ float4 f4_fms(float4 a, float k, float4 b) {  // a - k b
+  return make_float4(fmaf(-k, b.x, a.x), fmaf(-k, b.y, a.y), fmaf(-k, b.z, a.z),
+                     fmaf(-k, b.w, a.w));
+}
+
+template <int MM>
+__device__ __forceinline__ void zpart_body(const ZPartArgs& z, int tile) {
+  const ThomasArgs& a = z.t;
+  const int C = z.C, P = z.P, J = 2 * P;
+  const int kp = tile / z.ntx;  // slot ky (and its partner Ny - ky with periodic y)
+  const bool live = (int)threadIdx.x < C * P;  // the others only join the barriers
+  const int c = threadIdx.x % C, q = live ? threadIdx.x / C : 0;
+  const int j = (tile % z.ntx) * C + c;
+  const bool active = live && j >= 1 && j < a.M && !fp64_column(a, kp, j);
+  const int ky2 = (!a.ywall && kp > 0 && 2 * kp != a.ny) ? a.ny - kp : kp;
+  const bool two = active && ky2 != kp;
+  const int r0 = q * MM;  // every partition MM rows; rows past nz are x = 0
+  const long long rs = (long long)a.ny * a.M;
+  float2* const base = reinterpret_cast<float2*>(a.S) + (long long)r0 * rs + (active ? j : 0);
+  float2* const col = base + (long long)kp * a.M;
+  float2* const col2 = base + (long long)ky2 * a.M;
+
+  extern __shared__ __align__(16) unsigned char zsm[];
+  float4* const srow = reinterpret_cast<float4*>(zsm);
+  for (int k = threadIdx.x; k < P * MM; k += blockDim.x) srow[k + k / MM] = __ldg(z.zrow + k);
+  float2 u[MM], v[MM];  // right-hand sides of the two slots, then d'
+#pragma unroll
+  for (int i = 0; i < MM; ++i) {
+    u[i] = v[i] = make_float2(0.0f, 0.0f);
+    if (active && r0 + i < a.nz) u[i] = col[i * rs];
+    if (two && r0 + i < a.nz) v[i] = col2[i * rs];
+  }
+  // (inactive lanes solve a harmless zero column with the largest shift)
+  const float lam = active ? z.lam[j] + z.lam[a.M + 1 + kp] : z.lam[a.M];
+  __syncthreads();
+  const float4* const zr = srow + q * (MM + 1);
+
+  // downward, rows normalised: x_i + c'_i x_{i+1} + g'_i x_0 = d'_i (i >= 1).
+  // The rows and eigenvalues are divided by the normalisation s, so that the
+  // solution comes out scaled by s.
+  float cq[MM], gq[MM];
+  {
+    const float4 r = zr[1];
+    const float ib = zp_rcp(fmaf(lam, r.w, r.y));
+    cq[1] = r.z * ib;
+    gq[1] = r.x * ib;
+    u[1] = make_float2(u[1].x * ib, u[1].y * ib);
+    v[1] = make_float2(v[1].x * ib, v[1].y * ib);
+  }
+  cq[0] = gq[0] = 0.0f;
+#pragma unroll
+  for (int i = 2; i < MM; ++i) {
+    const float4 r = zr[i];
+    const float ib = zp_rcp(fmaf(-r.x, cq[i - 1], fmaf(lam, r.w, r.y)));
+    cq[i] = r.z * ib;
+    gq[i] = -(r.x * ib) * gq[i - 1];
+    const float2 t = f2_fms(u[i], r.x, u[i - 1]), w = f2_fms(v[i], r.x, v[i - 1]);
+    u[i] = make_float2(t.x * ib, t.y * ib);
+    v[i] = make_float2(w.x * ib, w.y * ib);
+  }
+  // upward to row 0: x_i = uu_i - vv_i x_0 - ww_i x_{MM-1}, carried as scalars
+  float2 uu = u[MM - 2], uv = v[MM - 2];
+  float vv = gq[MM - 2], ww = cq[MM - 2];
+#pragma unroll
+  for (int i = MM - 3; i >= 1; --i) {
+    const float ci = cq[i];
+    uu = f2_fms(u[i], ci, uu);
+    uv = f2_fms(v[i], ci, uv);
+    vv = fmaf(-ci, vv, gq[i]);
+    ww = -ci * ww;
+  }
+  const float4 rz = zr[0];
+
+  // the reduced system (Step 3): row 2q is the partition's row 0, row 2q + 1
+  // its row MM-1; column c's row k at index k * C + c.  Solved by cyclic
+  // reduction: at stride s the rows k = -1 mod 2s take away rows k -+ s,
+  // down to the single row 2^L - 1; then back substitution.
+  float4* const cA = srow + zpart_rows_smem(P, MM);  // (sub, diag, sup, -)
+  float4* const cY = cA + J * C;                     // (slot 1, slot 2) right-hand sides
+  if (live) {
+    cA[(2 * q) * C + c] =
+        make_float4(rz.x, fmaf(-rz.z, vv, fmaf(lam, rz.w, rz.y)), -rz.z * ww, 0.0f);
+    cY[(2 * q) * C + c] = make_float4(fmaf(-rz.z, uu.x, u[0].x), fmaf(-rz.z, uu.y, u[0].y),
+                                      fmaf(-rz.z, uv.x, v[0].x), fmaf(-rz.z, uv.y, v[0].y));
+    cA[(2 * q + 1) * C + c] = make_float4(gq[MM - 1], 1.0f, cq[MM - 1], 0.0f);
+    cY[(2 * q + 1) * C + c] = make_float4(u[MM - 1].x, u[MM - 1].y, v[MM - 1].x, v[MM - 1].y);
+  }
+  __syncthreads();
+  const int k1 = 2 * q + 1;  // the odd row this thread updates
+  int s = 1;
+  for (; 2 * s <= J; s <<= 1) {
+    if (live && ((k1 + 1) & (2 * s - 1)) == 0) {
+      float4 m = cA[k1 * C + c];
+      float4 y = cY[k1 * C + c];
+      const float4 lo = cA[(k1 - s) * C + c];
+      const float e1 = m.x * zp_rcp(lo.y);
+      float diag = fmaf(-e1, lo.z, m.y);
+      const float sub = -e1 * lo.x;
+      float sup = 0.0f;
+      y = f4_fms(y, e1, cY[(k1 - s) * C + c]);
+      if (k1 + s < J) {
+        const float4 hi = cA[(k1 + s) * C + c];
+        const float e2 = m.z * zp_rcp(hi.y);
+        diag = fmaf(-e2, hi.x, diag);
+        sup = -e2 * hi.z;
+        y = f4_fms(y, e2, cY[(k1 + s) * C + c]);
+      }
+      cA[k1 * C + c] = make_float4(sub, diag, sup, 0.0f);
+      cY[k1 * C + c] = y;
+    }
+    __syncthreads();
+  }
+  // s is now the first stride with no update: the last row updated is s - 1
+  if (live && k1 == s - 1) {
+    const float id = zp_rcp(cA[k1 * C + c].y);
+    const float4 y = cY[k1 * C + c];
+    cY[k1 * C + c] = make_float4(y.x * id, y.y * id, y.z * id, y.w * id);
+  }
+  __syncthreads();
+  for (int h = s >> 1; h >= 1; h >>= 1) {  // rows k = h - 1 mod 2h, from x_{k -+ h}
+    const int k = (h == 1) ? 2 * q : k1;
+    if (live && ((k + 1) & (2 * h - 1)) == h) {
+      const float4 m = cA[k * C + c];
+      float4 y = cY[k * C + c];
+      if (k - h >= 0) y = f4_fms(y, m.x, cY[(k - h) * C + c]);
+      if (k + h < J) y = f4_fms(y, m.z, cY[(k + h) * C + c]);
+      const float id = zp_rcp(m.y);
+      cY[k * C + c] = make_float4(y.x * id, y.y * id, y.z * id, y.w * id);
+    }
+    __syncthreads();
+  }
+  const float4 x0 = cY[(2 * q) * C + c], xl = cY[k1 * C + c];
+
+  // back substitution in the downward form, rows MM-2 .. 1
+  u[MM - 1] = make_float2(xl.x, xl.y);
+  v[MM - 1] = make_float2(xl.z, xl.w);
+#pragma unroll
+  for (int i = MM - 2; i >= 1; --i) {
+    u[i] = make_float2(fmaf(-cq[i], u[i + 1].x, fmaf(-gq[i], x0.x, u[i].x)),
+                       fmaf(-cq[i], u[i + 1].y, fmaf(-gq[i], x0.y, u[i].y)));
+    v[i] = make_float2(fmaf(-cq[i], v[i + 1].x, fmaf(-gq[i], x0.z, v[i].x)),
+                       fmaf(-cq[i], v[i + 1].y, fmaf(-gq[i], x0.w, v[i].y)));
+  }
+  u[0] = make_float2(x0.x, x0.y);
+  v[0] = make_float2(x0.z, x0.w);
+#pragma unroll
+  for (int i = 0; i < MM; ++i) {
+    if (active && r0 + i < a.nz) col[i * rs] = u[i];
+    if (two && r0 + i < a.nz) col2[i * rs] = v[i];
+  }
+}
+
+// Block blk of one box: the FP64 and kx = 0 columns first, then the tiles.
+template <int MM>
+__device__ __forceinline__ void zpart_block(const ZPartArgs& z, int blk) {
+  if (blk < z.nsp) {
+    // (a deeper prefetch than in the streaming kernel: here the main columns
+    // finish sooner, and these serial sweeps would be the launch's tail)
+    if (threadIdx.x < kThomasBlock) thomas_special_body<float2, 4>(z.t, blk);
+    return;
+  }
+  zpart_body<MM>(z, blk - z.nsp);
+}
+
+__global__ void __launch_bounds__(kZPartThreads, 2) zpart_kernel(ZPartArgs z) {
+  zpart_block<kZPartRows>(z, (int)blockIdx.x);
+}
+
+// One launch for several boxes (FP32 inner solves of grouped refinement): the
+// same blocks as each box alone, so the same bits.
+__global__ void __launch_bounds__(kZPartThreads, 2) zpart_group_kernel(const ZPartArgs* boxes,
+                                                                       GroupMap g) {
+  int b, blk;
+  if (!group_block(g, &b, &blk)) return;
+  zpart_block<kZPartRows>(boxes[b], blk);
+}
+
+static ThomasArgs thomas_args(const cfs_plan* P, void* data);
+
+// Rows per partition (MM) for nz rows; 0 if the partitioned solve does not
+// apply.  The operator table holds ceil(nz / MM) MM <= nz + kZPartRowPad rows.
+static int zpart_rows(int nz) {
+  return (nz >= 3 && (nz + kZPartRows - 1) / kZPartRows <= kZPartMaxParts) ? kZPartRows : 0;
+}
+
+static bool zpart_ok(const cfs_plan* P) {
+  return P->dtype == CFS_F32_REFINED && P->d_zrow32 && P->d_lam32 && zpart_rows(P->nz) > 0;
+}
+
+// The launch of one plan's partitioned solve on `data`; returns its blocks.
+static int zpart_args(const cfs_plan* P, float* data, ZPartArgs* z) {
+  z->t = thomas_args(P, data);
+  z->zrow = P->d_zrow32;
+  z->lam = P->d_lam32;
+  z->mm = zpart_rows(P->nz);
+  z->P = (P->nz + z->mm - 1) / z->mm;
+  int C = 4;  // the widest tile within the thread budget (more than half of it)
+  while (2 * C * z->P <= kZPartThreads) C *= 2;
+  z->C = C;
+  z->ntx = (P->M + C - 1) / C;
+  z->nsp = special_blocks<float2>(z->t);
+  return z->nsp + main_rows(z->t) * z->ntx;  // slot pairs (ky, Ny - ky), or slots (y walls)
+}
+
+static size_t zpart_smem(const ZPartArgs& z) {
+  return sizeof(float4) * ((size_t)zpart_rows_smem(z.P, z.mm) + (size_t)2 * (2 * z.P) * z.C);
+}
+
+static cudaError_t launch_zpart(const cfs_plan* P, float* data, cudaStream_t st) {
+  ZPartArgs z;
+  const int blocks = zpart_args(P, data, &z);
+  zpart_kernel<<<blocks, kZPartThreads, zpart_smem(z), st>>>(z);
   return cudaGetLastError();
 }
 
@@ -743,6 +1009,8 @@ template <int TW> struct tile_depth<float2, TW> { static constexpr int DG = TW =
 template <class CS>
 static int pick_tile_width(const cfs_plan* P, int tw) {
   constexpr int D16 = tile_depth<CS, 16>::DG, D8 = tile_depth<CS, 8>::DG;
+  if (tw == 1)  // the partitioned solve: FP32 spectra (FP64 sweeps stream)
+    return sizeof(CS) == sizeof(float2) ? (zpart_ok(P) ? 1 : 0) : -1;
   if (tw == -1) return -1;
   if (tw == 16) return tile_occupancy<CS, 16, D16>(P->nz) >= 1 ? 16 : 0;
   if (tw == 8) return tile_occupancy<CS, 8, D8>(P->nz) >= 1 ? 8 : 0;
@@ -757,6 +1025,8 @@ int thomas_tile_width(const cfs_plan* P, bool fp32, int tw) {
 template <class CS>
 static cudaError_t launch_thomas_t(const cfs_plan* P, void* data, cudaStream_t st) {
   const int tw = pick_tile_width<CS>(P, P->thomas_tw);
+  if constexpr (sizeof(CS) == sizeof(float2))
+    if (tw == 1) return launch_zpart(P, static_cast<float*>(data), st);
   if (tw == 16) return launch_tile<CS, 16, tile_depth<CS, 16>::DG>(P, data, st);
   if (tw == 8) return launch_tile<CS, 8, tile_depth<CS, 8>::DG>(P, data, st);
   return launch_streaming<CS>(thomas_args(P, data), st);
@@ -848,6 +1118,20 @@ size_t thomas_group_box(const cfs_plan* P, ThomasArgs* box, int* blocks) {
   *box = thomas_args(P, P->d_r32);
   *blocks = special_blocks<float2>(*box) + box->nblk_x * main_rows(*box);
   return 0;
+}
+
+bool zpart_group_member(const cfs_plan* P) { return pick_tile_width<float2>(P, P->thomas_tw) == 1; }
+
+size_t zpart_group_box(const cfs_plan* P, ZPartArgs* box, int* blocks) {
+  *blocks = zpart_args(P, P->d_r32, box);
+  return zpart_smem(*box);
+}
+
+cudaError_t launch_zpart_group(const ZPartArgs* boxes, GroupMap g, int total, size_t smem,
+                               cudaStream_t st) {
+  if (total <= 0) return cudaSuccess;
+  zpart_group_kernel<<<total, kZPartThreads, smem, st>>>(boxes, g);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_thomas_group32(const ThomasArgs* boxes, GroupMap g, int total,

@@ -197,7 +197,7 @@ extern "C" int cfs_plan_autotune(cfs_plan_t P, void* stream) {
   {
     float tbest = 1e30f;
     best.thomas = -1;
-    for (int cand : {-1, 8, 16}) {
+    for (int cand : {-1, 1, 8, 16}) {
       if (thomas_tile_width(P, fp32, cand) != cand) continue;
       P->thomas_tw = cand;
       const float t = best_ms(st, [&]() {

@@ -123,7 +123,7 @@ def test_refined_residual_is_evaluated_to_fp64_accuracy(chanfs, bc, beta, kind):
         assert rel(p, ref) < 10 * tol, rel(p, ref)
 
 
-@pytest.mark.parametrize("tw", [-1, 8, 16])
+@pytest.mark.parametrize("tw", [-1, 1, 8, 16])
 def test_refined_poisson_thomas_shapes(chanfs, tw):
     nx, ny, nz = 64, 48, 300   # two TMA boxes along z, near-singular FP64 columns
     dz = synth.tanh_dz(nz, 1.8)
@@ -136,6 +136,87 @@ def test_refined_poisson_thomas_shapes(chanfs, tw):
         assert rho <= TOL and iters <= 4, (iters, rho)
         assert rel(p, ref) < TOL, rel(p, ref)
         assert plan.check() == 0
+
+
+# The partitioned FP32 z solve (CFS_OPT_THOMAS_TILE 1: Algorithm 2 over
+# z-partitions of 8 rows in registers, coefficients formed on the fly, the
+# reduced system by cyclic reduction): one partition, ragged last partitions
+# (nz = 97: one real row and seven identity rows), the largest reduced system
+# (nz = 512: 64 partitions, 4 column pairs per tile), both z walls, both kinds
+# of y walls (one slot per thread), odd Ny (no self-paired slot Ny/2).
+ZPART = [
+    ((32, 24, 5), 1.2, 0, 0),
+    ((48, 36, 97), 2.0, 1, 0),
+    ((64, 48, 300), 1.8, 0, 0),
+    ((128, 96, 512), 1.8, 0, 0),
+    ((16, 12, 512), 1.8, 0, 0),
+    ((32, 27, 41), 1.6, 0, 0),
+    ((64, 48, 64), 1.5, 0, 1),
+    ((64, 48, 66), 1.5, 1, 2),
+]
+
+
+@pytest.mark.parametrize("dims,beta,bc,ybc", ZPART)
+def test_refined_poisson_partitioned_z_solve(chanfs, dims, beta, bc, ybc):
+    nx, ny, nz = dims
+    lx, ly = 12.8, 6.4
+    dz = synth.tanh_dz(nz, beta)
+    f = synth.normal(31 * nz + bc + ybc, (nz, ny, nx))
+    if bc == 0 and ybc != 2:
+        f = synth.remove_weighted_mean(f, dz)
+    ref = (oracle.poisson_solve(f, lx, ly, dz, bc) if ybc == 0
+           else oracle.poisson_solve_walls(f, lx, ly, dz, bc, ybc))
+    out = {}
+    for tw in (-1, 1):
+        with chanfs.Plan(nx, ny, nz, lx, ly, dz, bc, chanfs.F32_REFINED, ybc) as plan:
+            plan.set_option(chanfs.OPT_THOMAS_TILE, tw)
+            assert plan.get_option(chanfs.OPT_THOMAS_TILE) == tw
+            p = host(plan.poisson_solve(dev(f)))
+            iters, rho = plan.last_info()
+            assert rho <= TOL and iters <= 4, (tw, iters, rho)
+            assert rel(p, ref) < TOL, (tw, rel(p, ref))
+            assert plan.check() == 0
+            out[tw] = iters
+    # the partitioned inner solve is as good a preconditioner as the sweep
+    assert out[1] <= out[-1] + 1, out
+
+
+def test_partitioned_z_solve_grouped_bits_match_alone(chanfs):
+    """Boxes that take the partitioned z solve run it in a group too: the
+    same bits as alone, beside a box on the streaming sweep."""
+    dims = [(64, 48, 97), (32, 24, 300), (48, 36, 40)]
+    tws = [1, 1, -1]
+    plans, rhs, alone = [], [], []
+    try:
+        for (nx, ny, nz), tw in zip(dims, tws):
+            dz = synth.tanh_dz(nz, 1.7)
+            pl = chanfs.Plan(nx, ny, nz, 12.8, 6.4, dz, 0, chanfs.F32_REFINED)
+            pl.set_option(chanfs.OPT_THOMAS_TILE, tw)
+            f = synth.remove_weighted_mean(synth.normal(nz + nx, (nz, ny, nx)), dz)
+            plans.append(pl)
+            rhs.append(dev(f))
+            alone.append(host(pl.poisson_solve(rhs[-1])))
+        with chanfs.Group(plans) as g:
+            for _ in range(3):  # direct launches, graph capture, graph replay
+                got = [host(o) for o in g.poisson_solve(rhs)]
+                for a, b in zip(got, alone):
+                    assert np.array_equal(a, b)
+    finally:
+        for pl in plans:
+            pl.close()
+
+
+def test_partitioned_z_solve_option_rules(chanfs):
+    dz = synth.tanh_dz(40, 1.5)
+    with chanfs.Plan(32, 24, 40, 1.0, 1.0, dz, 0) as p64:  # FP64 plans: no partitioned solve
+        with pytest.raises(chanfs.ChanfsError) as err:
+            p64.set_option(chanfs.OPT_THOMAS_TILE, 1)
+        assert err.value.status == chanfs.EUNSUPPORTED
+    dz = synth.tanh_dz(520, 1.5)   # more than 64 partitions of 8 rows
+    with chanfs.Plan(16, 12, 520, 1.0, 1.0, dz, 0, chanfs.F32_REFINED) as p:
+        with pytest.raises(chanfs.ChanfsError) as err:
+            p.set_option(chanfs.OPT_THOMAS_TILE, 1)
+        assert err.value.status == chanfs.EUNSUPPORTED
 
 
 def test_refined_poisson_reports_nonconvergence(chanfs):
