@@ -498,6 +498,21 @@ def run_ensemble(chanfs, torch, device, reps: int = 3):
         grouped()
         torch.cuda.synchronize()
     group.set_graphs(True)
+    # Idle time between a grouped step's nodes: the device time of each copy
+    # and kernel (direct launches, one event pair each), summed, against the
+    # graph-launched step.  Best of reps.
+    group.set_trace(True)
+    sums, launches = [], 0
+    for _ in range(reps):
+        traced = []
+        group.poisson_solve(f, p)
+        traced += group.trace()
+        for k in range(3):
+            group.helmholtz_solve(cs, [r[k] for r in rhs], [locs[k]] * len(boxes), [x[k] for x in u])
+            traced += group.trace()
+        sums.append(sum(traced))
+        launches = len(traced)
+    group.set_trace(False)
     t64 = timed(per_box(plans64))
     t32 = timed(per_box(plans32))
     group.close()
@@ -518,6 +533,13 @@ def run_ensemble(chanfs, torch, device, reps: int = 3):
             "per_box_refined_ms": round(t32, 3),
             "grouped_ns_per_pt": t_group * 1e6 / npts, "per_box_f64_ns_per_pt": t64 * 1e6 / npts,
             "speedup_vs_per_box_f64": t64 / t_group,
+            "launch_trace": {"copies_and_kernels": launches,
+                             "device_ms_sum": round(min(sums), 3),
+                             "graph_step_ms": round(t_group, 3),
+                             "idle_ms": round(t_group - min(sums), 3),
+                             "how": "cfs_group_set_trace: an event pair around every copy and "
+                                    "kernel of one step launched directly, summed (best of "
+                                    "reps); idle = graph-launched step - sum"},
             "max_fp32_solves_last_helmholtz": max(i for i, _ in info),
             "max_rel_residual_last_helmholtz": max(r for _, r in info),
             "autotuned": "per refined box size: x_lines, y_tile, thomas_tile, pcr_parts, "

@@ -346,6 +346,18 @@ int cfs_group_last_info(cfs_group_t group, int* iters, double* rel_residual);
  * refinement loop on the host (one wait per iteration); on != 0 (the
  * default): graphs as above.  Both give bit-identical results. */
 int cfs_group_set_graphs(cfs_group_t group, int on);
+/* Launch tracing, a measurement aid (the paper has no counterpart).  While
+ * on != 0, the group's solves run as direct launches (no graph) and every
+ * copy and kernel they issue on the caller's stream is bracketed by a pair
+ * of CUDA events (the first 512 of a solve; later ones run untraced).  The
+ * first call with on != 0 creates the events (CFS_ECUDA if that fails).
+ * cfs_group_trace waits for the last solve's events and writes the device
+ * time of each traced copy or kernel, in issue order, to ms[0 .. min(count,
+ * capacity)) in milliseconds; *count receives how many were traced.  Their
+ * sum against the time of the same solve as a graph bounds the idle time
+ * between a graph's nodes. */
+int cfs_group_set_trace(cfs_group_t group, int on);
+int cfs_group_trace(cfs_group_t group, float* ms, int capacity, int* count);
 
 /*
  * Serving.  The paper has no counterpart.  A server takes Poisson and

@@ -96,6 +96,8 @@ def lib():
             "cfs_group_poisson_solve": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp], i),
             "cfs_group_last_info": ([vp, ctypes.POINTER(i), ctypes.POINTER(d)], i),
             "cfs_group_set_graphs": ([vp, i], i),
+            "cfs_group_set_trace": ([vp, i], i),
+            "cfs_group_trace": ([vp, ctypes.POINTER(ctypes.c_float), i, ctypes.POINTER(i)], i),
             "cfs_solve_batch_host": ([vp, i, ctypes.POINTER(i), ctypes.POINTER(d),
                                       ctypes.POINTER(i), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                       vp], i),
@@ -513,6 +515,18 @@ class Group:
         """Graph-launched solves with the refinement loop on the device (the
         default), or direct launches with the loop on the host (on=False)."""
         _check(lib().cfs_group_set_graphs(self._h, int(bool(on))), "cfs_group_set_graphs")
+
+    def set_trace(self, on):
+        """Direct launches with an event pair around each copy and kernel
+        (cfs_group_set_trace); trace() then gives their device times."""
+        _check(lib().cfs_group_set_trace(self._h, int(bool(on))), "cfs_group_set_trace")
+
+    def trace(self, capacity: int = 512):
+        """Device time (ms) of each copy and kernel of the last traced solve."""
+        buf = (ctypes.c_float * capacity)()
+        n = ctypes.c_int(0)
+        _check(lib().cfs_group_trace(self._h, buf, capacity, ctypes.byref(n)), "cfs_group_trace")
+        return [float(buf[k]) for k in range(min(n.value, capacity))]
 
     def last_info(self):
         """Per plan: (FP32 solves, final relative residual) of the last solve."""

@@ -158,6 +158,11 @@ struct cfs_group {
   // run as direct launches and do not pay for a capture
   std::vector<std::vector<long long>> seen;
   cudaEvent_t io_copied = nullptr;  // staging buffers free again after this
+  // Launch tracing (cfs_group_set_trace): while on, solves run as direct
+  // launches with a pair of events around every copy and kernel they issue.
+  bool trace = false;
+  std::vector<cudaEvent_t> trace_ev;  // begin / end pairs, kTraceLaunches of them
+  int trace_n = 0;                    // pairs recorded by the last solve
   std::vector<ResBox> res;          // host copy of the bound boxes' residual records
   std::vector<int> last_iters;
   std::vector<double> last_rho;
@@ -206,8 +211,23 @@ static void keep_graph(cfs_group* G, const std::vector<long long>& sig, cudaGrap
   G->cache.push_back({sig, exec});
 }
 
+constexpr int kTraceLaunches = 512;
+
+// Runs f() (one copy or kernel launch on st), bracketed by a pair of trace
+// events while tracing is on; launches past the pool run untraced.
+template <class F>
+static cudaError_t traced(cfs_group* G, cudaStream_t st, F&& f) {
+  if (!G->trace || 2 * G->trace_n + 2 > (int)G->trace_ev.size()) return f();
+  cudaError_t e = cudaEventRecord(G->trace_ev[2 * G->trace_n], st);
+  if (e == cudaSuccess) e = f();
+  if (e == cudaSuccess) e = cudaEventRecord(G->trace_ev[2 * G->trace_n + 1], st);
+  if (e == cudaSuccess) ++G->trace_n;
+  return e;
+}
+
 static void group_free(cfs_group* G) {
   drop_graphs(G);
+  for (cudaEvent_t ev : G->trace_ev) cudaEventDestroy(ev);
   void* ptrs[] = {G->d_tab,   G->d_active, G->d_mean, G->d_one, G->d_fmax, G->d_tol,  G->d_maxit,
                   G->d_iters, G->d_rho,    G->d_nactive, G->d_io, G->d_pcr, G->d_hres,
                   G->d_spcr, G->d_pcr64, G->d_spcr64, G->d_zero, G->d_elig, G->d_ctl,
@@ -532,22 +552,38 @@ cudaError_t build_graph(cfs_group* G, Head head, Body body, Tail tail, cudaGraph
 // zero solution of boxes whose right-hand side is zero.
 cudaError_t poisson_head(cfs_group* G, cudaStream_t st) {
   const int nb = G->nbox;
-  cudaError_t e = cudaMemcpyAsync(G->d_io, G->h_io, sizeof(GroupIo) * nb, kH2D, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(G->d_tol, G->h_tol, sizeof(double) * nb, kH2D, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(G->d_maxit, G->h_maxit, sizeof(int) * nb, kH2D, st);
-  if (e == cudaSuccess) e = launch_group_zero_max(G->d_res, nb, st);
+  cudaError_t e = traced(G, st, [&] {
+    return cudaMemcpyAsync(G->d_io, G->h_io, sizeof(GroupIo) * nb, kH2D, st);
+  });
+  if (e == cudaSuccess)
+    e = traced(G, st, [&] {
+      return cudaMemcpyAsync(G->d_tol, G->h_tol, sizeof(double) * nb, kH2D, st);
+    });
+  if (e == cudaSuccess)
+    e = traced(G, st, [&] {
+      return cudaMemcpyAsync(G->d_maxit, G->h_maxit, sizeof(int) * nb, kH2D, st);
+    });
+  if (e == cudaSuccess) e = traced(G, st, [&] { return launch_group_zero_max(G->d_res, nb, st); });
   GroupMap g{G->d_splane, nullptr, nb};
   if (e == cudaSuccess)
-    e = launch_group_refine_stage(GSTAGE_START, G->d_res, g, G->tplane, G->d_io, 0, st);
+    e = traced(G, st, [&] {
+      return launch_group_refine_stage(GSTAGE_START, G->d_res, g, G->tplane, G->d_io, 0, st);
+    });
   g = GroupMap{G->d_sone, G->d_neumann, nb};
   if (e == cudaSuccess)
-    e = launch_group_refine_stage(GSTAGE_MEAN_FINAL, G->d_res, g, G->tone, G->d_io, 0, st);
+    e = traced(G, st, [&] {
+      return launch_group_refine_stage(GSTAGE_MEAN_FINAL, G->d_res, g, G->tone, G->d_io, 0, st);
+    });
   if (e == cudaSuccess)
-    e = launch_group_start(G->d_res, nb, 1, G->d_fmax, nullptr, G->d_active, G->d_mean,
-                           G->d_zero, G->d_iters, G->d_rho, G->d_ctl, st, G->d_one);
+    e = traced(G, st, [&] {
+      return launch_group_start(G->d_res, nb, 1, G->d_fmax, nullptr, G->d_active, G->d_mean,
+                                G->d_zero, G->d_iters, G->d_rho, G->d_ctl, st, G->d_one);
+    });
   g = GroupMap{G->d_ssub, G->d_zero, nb};
   if (e == cudaSuccess)
-    e = launch_group_refine_stage(GSTAGE_ZERO, G->d_res, g, G->tsub, G->d_io, 0, st);
+    e = traced(G, st, [&] {
+      return launch_group_refine_stage(GSTAGE_ZERO, G->d_res, g, G->tsub, G->d_io, 0, st);
+    });
   return e;
 }
 
@@ -560,45 +596,55 @@ cudaError_t poisson_iteration(cfs_group* G, int kind, cudaGraphConditionalHandle
                               int set_cond, cudaStream_t st) {
   const int nb = G->nbox;
   GroupMap g{G->d_sx, G->d_active, nb};
-  cudaError_t e = launch_rfft_x_group32(G->d_xf, g, G->tx, G->smem_x, false, OUT_SAME, G->d_io,
-                                        kind >= 1, st);
+  cudaError_t e = traced(G, st, [&] {
+    return launch_rfft_x_group32(G->d_xf, g, G->tx, G->smem_x, false, OUT_SAME, G->d_io,
+                                 kind >= 1, st);
+  });
   if (e == cudaSuccess) {
     g.start = G->d_sy;
-    e = launch_fft_y_group32(G->d_y, g, G->ty, G->smem_y, false, st);
+    e = traced(G, st, [&] { return launch_fft_y_group32(G->d_y, g, G->ty, G->smem_y, false, st); });
   }
   if (e == cudaSuccess) {
     g.start = G->d_sth;
-    e = launch_thomas_group32(G->d_th, g, G->tth, st);
+    e = traced(G, st, [&] { return launch_thomas_group32(G->d_th, g, G->tth, st); });
   }
   if (e == cudaSuccess) {
     g.start = G->d_szp;
-    e = launch_zpart_group(G->d_zp, g, G->tzp, G->smem_zp, st);
+    e = traced(G, st, [&] { return launch_zpart_group(G->d_zp, g, G->tzp, G->smem_zp, st); });
   }
   if (e == cudaSuccess) {
     g.start = G->d_sy;
-    e = launch_fft_y_group32(G->d_y, g, G->ty, G->smem_y, true, st);
+    e = traced(G, st, [&] { return launch_fft_y_group32(G->d_y, g, G->ty, G->smem_y, true, st); });
   }
   if (e == cudaSuccess) {
     g.start = G->d_sx;
     // the first correction stays in FP32; the second pass writes p = both;
     // later passes add to p
-    e = launch_rfft_x_group32(G->d_xi, g, G->tx, G->smem_x, true,
-                              kind == 0 ? OUT_SAME : kind == 1 ? OUT_SUM : OUT_ADD, G->d_io, 0,
-                              st);
+    e = traced(G, st, [&] {
+      return launch_rfft_x_group32(G->d_xi, g, G->tx, G->smem_x, true,
+                                   kind == 0 ? OUT_SAME : kind == 1 ? OUT_SUM : OUT_ADD, G->d_io, 0,
+                                   st);
+    });
   }
   if (e == cudaSuccess) {
     g.start = G->d_sres;
-    e = launch_group_refine_stage(kind == 0 ? GSTAGE_RESIDUAL : GSTAGE_UPDATE, G->d_res, g,
-                                  G->tres, G->d_io, 1, st);
+    e = traced(G, st, [&] {
+      return launch_group_refine_stage(kind == 0 ? GSTAGE_RESIDUAL : GSTAGE_UPDATE, G->d_res, g,
+                                       G->tres, G->d_io, 1, st);
+    });
   }
   if (e == cudaSuccess) {  // the weighted sum of p, correction by correction (Neumann boxes)
     g.start = G->d_sone;
-    e = launch_group_refine_stage(GSTAGE_MEAN_ACC, G->d_res, g, G->tone, G->d_io, 0, st);
+    e = traced(G, st, [&] {
+      return launch_group_refine_stage(GSTAGE_MEAN_ACC, G->d_res, g, G->tone, G->d_io, 0, st);
+    });
   }
   if (e == cudaSuccess)
-    e = launch_group_iter_end(G->d_res, nb, G->d_fmax, G->d_tol, G->d_maxit, G->d_active,
-                              G->d_mean, G->d_iters, G->d_rho, G->d_ctl, cond, set_cond, st,
-                              G->d_one);
+    e = traced(G, st, [&] {
+      return launch_group_iter_end(G->d_res, nb, G->d_fmax, G->d_tol, G->d_maxit, G->d_active,
+                                   G->d_mean, G->d_iters, G->d_rho, G->d_ctl, cond, set_cond, st,
+                                   G->d_one);
+    });
   return e;
 }
 
@@ -613,9 +659,17 @@ cudaError_t poisson_tail(cfs_group* G, cudaStream_t st) {
       launch_group_refine_stage(GSTAGE_MEAN_FROM_NUM, G->d_res, g, G->tone, G->d_io, 0, st);
   g = GroupMap{G->d_ssub, G->d_one, nb};
   if (e == cudaSuccess)
-    e = launch_group_refine_stage(GSTAGE_FIRST_ONLY, G->d_res, g, G->tsub, G->d_io, 0, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(G->h_iters, G->d_iters, sizeof(int) * nb, kD2H, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(G->h_rho, G->d_rho, sizeof(double) * nb, kD2H, st);
+    e = traced(G, st, [&] {
+      return launch_group_refine_stage(GSTAGE_FIRST_ONLY, G->d_res, g, G->tsub, G->d_io, 0, st);
+    });
+  if (e == cudaSuccess)
+    e = traced(G, st, [&] {
+      return cudaMemcpyAsync(G->h_iters, G->d_iters, sizeof(int) * nb, kD2H, st);
+    });
+  if (e == cudaSuccess)
+    e = traced(G, st, [&] {
+      return cudaMemcpyAsync(G->h_rho, G->d_rho, sizeof(double) * nb, kD2H, st);
+    });
   return e;
 }
 
@@ -660,12 +714,14 @@ extern "C" int cfs_group_poisson_solve(cfs_group_t G, const double* const* f, do
     G->h_tol[b] = G->plans[b]->tol;
     G->h_maxit[b] = G->plans[b]->maxit;
   }
+  G->trace_n = 0;
   const std::vector<long long> sig = {0,       nb,      G->tx,     G->ty,
                                       G->tth,  G->tzp,  G->tres,   G->tplane,
                                       G->tone, G->tsub, (long long)G->smem_x,
                                       (long long)G->smem_y, (long long)G->smem_zp};
-  cudaGraphExec_t exec = G->graphs ? find_graph(G, sig) : nullptr;
-  if (exec || (G->graphs && capture_now(G, sig))) {
+  const bool graphs = G->graphs && !G->trace;
+  cudaGraphExec_t exec = graphs ? find_graph(G, sig) : nullptr;
+  if (exec || (graphs && capture_now(G, sig))) {
     if (!exec) {
       e = build_graph(
           G,
@@ -732,6 +788,7 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaEventSynchronize(G->io_copied);  // staging of the previous call is free
   if (e != cudaSuccess) return CFS_ECUDA;
+  G->trace_n = 0;
   // Algorithm 2, Step 1 of every box (host, cached per plan), and the
   // per-call descriptors.  Boxes whose plans take FP64 Algorithm 2 directly
   // (CFS_OPT_HELM_FP64) run in one FP64 launch; the others are refined
@@ -800,77 +857,142 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
   memcpy(G->h_sth64, st64.data(), sizeof(int) * (nb + 1));
 
   auto head = [&](cudaStream_t s) {
-    cudaError_t r = cudaMemcpyAsync(G->d_pcr, G->h_pcr, sizeof(PcrBox) * nb, kH2D, s);
-    if (r == cudaSuccess) r = cudaMemcpyAsync(G->d_hres, G->h_hres, sizeof(ResBox) * nb, kH2D, s);
-    if (r == cudaSuccess && tpcr64 > 0)
-      r = cudaMemcpyAsync(G->d_pcr64, G->h_pcr64, sizeof(PcrBox64) * nb, kH2D, s);
-    if (r == cudaSuccess) r = cudaMemcpyAsync(G->d_io, G->h_io, sizeof(GroupIo) * nb, kH2D, s);
-    if (r == cudaSuccess) r = cudaMemcpyAsync(G->d_spcr, G->h_spcr, sizeof(int) * (nb + 1), kH2D, s);
+    cudaError_t r = traced(G, s, [&] {
+      return cudaMemcpyAsync(G->d_pcr, G->h_pcr, sizeof(PcrBox) * nb, kH2D, s);
+    });
     if (r == cudaSuccess)
-      r = cudaMemcpyAsync(G->d_spcr64, G->h_spcr64, sizeof(int) * (nb + 1), kH2D, s);
-    if (r == cudaSuccess) r = cudaMemcpyAsync(G->d_tol, G->h_tol, sizeof(double) * nb, kH2D, s);
-    if (r == cudaSuccess) r = cudaMemcpyAsync(G->d_maxit, G->h_maxit, sizeof(int) * nb, kH2D, s);
-    if (r == cudaSuccess) r = cudaMemcpyAsync(G->d_elig, G->h_elig, sizeof(int) * nb, kH2D, s);
+      r = traced(G, s, [&] {
+        return cudaMemcpyAsync(G->d_hres, G->h_hres, sizeof(ResBox) * nb, kH2D, s);
+      });
+    if (r == cudaSuccess && tpcr64 > 0)
+      r = traced(G, s, [&] {
+        return cudaMemcpyAsync(G->d_pcr64, G->h_pcr64, sizeof(PcrBox64) * nb, kH2D, s);
+      });
+    if (r == cudaSuccess)
+      r = traced(G, s, [&] {
+        return cudaMemcpyAsync(G->d_io, G->h_io, sizeof(GroupIo) * nb, kH2D, s);
+      });
+    if (r == cudaSuccess)
+      r = traced(G, s, [&] {
+        return cudaMemcpyAsync(G->d_spcr, G->h_spcr, sizeof(int) * (nb + 1), kH2D, s);
+      });
+    if (r == cudaSuccess)
+      r = traced(G, s, [&] {
+        return cudaMemcpyAsync(G->d_spcr64, G->h_spcr64, sizeof(int) * (nb + 1), kH2D, s);
+      });
+    if (r == cudaSuccess)
+      r = traced(G, s, [&] {
+        return cudaMemcpyAsync(G->d_tol, G->h_tol, sizeof(double) * nb, kH2D, s);
+      });
+    if (r == cudaSuccess)
+      r = traced(G, s, [&] {
+        return cudaMemcpyAsync(G->d_maxit, G->h_maxit, sizeof(int) * nb, kH2D, s);
+      });
+    if (r == cudaSuccess)
+      r = traced(G, s, [&] {
+        return cudaMemcpyAsync(G->d_elig, G->h_elig, sizeof(int) * nb, kH2D, s);
+      });
     if (r == cudaSuccess && tt32 + tt64 > 0) {
-      r = cudaMemcpyAsync(G->d_hth, G->h_hth, sizeof(HThomasBox) * nb, kH2D, s);
+      r = traced(G, s, [&] {
+        return cudaMemcpyAsync(G->d_hth, G->h_hth, sizeof(HThomasBox) * nb, kH2D, s);
+      });
       if (r == cudaSuccess)
-        r = cudaMemcpyAsync(G->d_sth32, G->h_sth32, sizeof(int) * (nb + 1), kH2D, s);
+        r = traced(G, s, [&] {
+          return cudaMemcpyAsync(G->d_sth32, G->h_sth32, sizeof(int) * (nb + 1), kH2D, s);
+        });
       if (r == cudaSuccess)
-        r = cudaMemcpyAsync(G->d_sth64, G->h_sth64, sizeof(int) * (nb + 1), kH2D, s);
+        r = traced(G, s, [&] {
+          return cudaMemcpyAsync(G->d_sth64, G->h_sth64, sizeof(int) * (nb + 1), kH2D, s);
+        });
     }
     // the boxes refined in one pass: one launch, the result words copied out
     if (r == cudaSuccess && tfus > 0)
-      r = cudaMemcpyAsync(G->d_fus, G->h_fus, sizeof(PcrRefineBox) * nb, kH2D, s);
+      r = traced(G, s, [&] {
+        return cudaMemcpyAsync(G->d_fus, G->h_fus, sizeof(PcrRefineBox) * nb, kH2D, s);
+      });
     if (r == cudaSuccess && tfus > 0)
-      r = cudaMemcpyAsync(G->d_sfus, G->h_sfus, sizeof(int) * (nb + 1), kH2D, s);
+      r = traced(G, s, [&] {
+        return cudaMemcpyAsync(G->d_sfus, G->h_sfus, sizeof(int) * (nb + 1), kH2D, s);
+      });
     if (r == cudaSuccess && tfus > 0)
-      r = cudaMemsetAsync(G->d_fwords, 0, sizeof(unsigned int) * 3 * nb, s);
+      r = traced(G, s, [&] {
+        return cudaMemsetAsync(G->d_fwords, 0, sizeof(unsigned int) * 3 * nb, s);
+      });
     if (r == cudaSuccess && tfus > 0)
-      r = launch_pcr_refine_group(G->d_fus, GroupMap{G->d_sfus, nullptr, nb}, tfus, threads_f,
-                                  smem_f, rows_f, s);
+      r = traced(G, s, [&] {
+        return launch_pcr_refine_group(G->d_fus, GroupMap{G->d_sfus, nullptr, nb}, tfus, threads_f,
+                                       smem_f, rows_f, s);
+      });
     if (r == cudaSuccess && tfus > 0)
-      r = cudaMemcpyAsync(G->h_fwords, G->d_fwords, sizeof(unsigned int) * 3 * nb, kD2H, s);
+      r = traced(G, s, [&] {
+        return cudaMemcpyAsync(G->h_fwords, G->d_fwords, sizeof(unsigned int) * 3 * nb, kD2H, s);
+      });
     // the FP64 boxes: one launch per method, no refinement
     if (r == cudaSuccess && tpcr64 > 0)
-      r = launch_pcr_group64(G->d_pcr64, GroupMap{G->d_spcr64, nullptr, nb}, tpcr64, threads64,
-                             smem64, s);
+      r = traced(G, s, [&] {
+        return launch_pcr_group64(G->d_pcr64, GroupMap{G->d_spcr64, nullptr, nb}, tpcr64, threads64,
+                                  smem64, s);
+      });
     if (r == cudaSuccess && tt64 > 0)
-      r = launch_helm_thomas_group(G->d_hth, GroupMap{G->d_sth64, nullptr, nb}, tt64, smem_t64,
-                                   false, G->d_io, s);
+      r = traced(G, s, [&] {
+        return launch_helm_thomas_group(G->d_hth, GroupMap{G->d_sth64, nullptr, nb}, tt64, smem_t64,
+                                        false, G->d_io, s);
+      });
     if (nref == 0) return r;
     // r_0 = rhs and its max-norm (refined boxes), the start state, zero
     // solutions of zero right-hand sides
     GroupMap g{G->d_sres, G->d_elig, nb};
-    if (r == cudaSuccess) r = launch_group_zero_max(G->d_hres, nb, s);
+    if (r == cudaSuccess) r = traced(G, s, [&] { return launch_group_zero_max(G->d_hres, nb, s); });
     if (r == cudaSuccess)
-      r = launch_group_refine_stage(GSTAGE_HELM_RESIDUAL, G->d_hres, g, G->tres, G->d_io, 0, s);
+      r = traced(G, s, [&] {
+        return launch_group_refine_stage(GSTAGE_HELM_RESIDUAL, G->d_hres, g, G->tres, G->d_io, 0,
+                                         s);
+      });
     if (r == cudaSuccess)
-      r = launch_group_start(G->d_hres, nb, 0, G->d_fmax, G->d_elig, G->d_active, nullptr,
-                             G->d_zero, G->d_iters, G->d_rho, G->d_ctl, s);
+      r = traced(G, s, [&] {
+        return launch_group_start(G->d_hres, nb, 0, G->d_fmax, G->d_elig, G->d_active, nullptr,
+                                  G->d_zero, G->d_iters, G->d_rho, G->d_ctl, s);
+      });
     g = GroupMap{G->d_ssub, G->d_zero, nb};
     if (r == cudaSuccess)
-      r = launch_group_refine_stage(GSTAGE_ZERO, G->d_hres, g, G->tsub, G->d_io, 0, s);
+      r = traced(G, s, [&] {
+        return launch_group_refine_stage(GSTAGE_ZERO, G->d_hres, g, G->tsub, G->d_io, 0, s);
+      });
     return r;
   };
   // one iteration: FP32 Algorithm 2 on the residual, u updated, new residual
   // (mode 1: u = delta, 2: u += delta), stopping test
   auto iteration = [&](int mode, cudaGraphConditionalHandle cond, int set_cond, cudaStream_t s) {
     GroupMap g{G->d_spcr, G->d_active, nb};
-    cudaError_t r = launch_pcr_group32(G->d_pcr, g, tpcr, threads, smem, s);
+    cudaError_t r = traced(G, s, [&] {
+      return launch_pcr_group32(G->d_pcr, g, tpcr, threads, smem, s);
+    });
     g.start = G->d_sth32;
     if (r == cudaSuccess)
-      r = launch_helm_thomas_group(G->d_hth, g, tt32, smem_t32, true, G->d_io, s);
+      r = traced(G, s, [&] {
+        return launch_helm_thomas_group(G->d_hth, g, tt32, smem_t32, true, G->d_io, s);
+      });
     g.start = G->d_sres;
     if (r == cudaSuccess)
-      r = launch_group_refine_stage(GSTAGE_HELM_RESIDUAL, G->d_hres, g, G->tres, G->d_io, mode, s);
+      r = traced(G, s, [&] {
+        return launch_group_refine_stage(GSTAGE_HELM_RESIDUAL, G->d_hres, g, G->tres, G->d_io, mode,
+                                         s);
+      });
     if (r == cudaSuccess)
-      r = launch_group_iter_end(G->d_hres, nb, G->d_fmax, G->d_tol, G->d_maxit, G->d_active,
-                                nullptr, G->d_iters, G->d_rho, G->d_ctl, cond, set_cond, s);
+      r = traced(G, s, [&] {
+        return launch_group_iter_end(G->d_hres, nb, G->d_fmax, G->d_tol, G->d_maxit, G->d_active,
+                                     nullptr, G->d_iters, G->d_rho, G->d_ctl, cond, set_cond, s);
+      });
     return r;
   };
   auto tail = [&](cudaStream_t s) {
-    cudaError_t r = cudaMemcpyAsync(G->h_iters, G->d_iters, sizeof(int) * nb, kD2H, s);
-    if (r == cudaSuccess) r = cudaMemcpyAsync(G->h_rho, G->d_rho, sizeof(double) * nb, kD2H, s);
+    cudaError_t r = traced(G, s, [&] {
+      return cudaMemcpyAsync(G->h_iters, G->d_iters, sizeof(int) * nb, kD2H, s);
+    });
+    if (r == cudaSuccess)
+      r = traced(G, s, [&] {
+        return cudaMemcpyAsync(G->h_rho, G->d_rho, sizeof(double) * nb, kD2H, s);
+      });
     return r;
   };
 
@@ -888,8 +1010,9 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
                                       tt32,     tt64,     (long long)smem_t32,
                                       (long long)smem_t64, G->tres, G->tsub,
                                       tfus,     threads_f, (long long)smem_f, rows_f};
-  cudaGraphExec_t exec = G->graphs ? find_graph(G, sig) : nullptr;
-  if (exec || (G->graphs && capture_now(G, sig))) {
+  const bool graphs = G->graphs && !G->trace;
+  cudaGraphExec_t exec = graphs ? find_graph(G, sig) : nullptr;
+  if (exec || (graphs && capture_now(G, sig))) {
     if (!exec) {
       e = build_graph(
           G,
@@ -921,6 +1044,36 @@ extern "C" int cfs_group_helmholtz_solve(cfs_group_t G, const double* c, const i
 extern "C" int cfs_group_set_graphs(cfs_group_t G, int on) {
   if (!G) return CFS_EINVAL;
   G->graphs = on != 0;
+  return CFS_OK;
+}
+
+extern "C" int cfs_group_set_trace(cfs_group_t G, int on) {
+  if (!G) return CFS_EINVAL;
+  if (on && G->trace_ev.empty()) {
+    G->trace_ev.assign(2 * kTraceLaunches, nullptr);
+    for (cudaEvent_t& ev : G->trace_ev) {
+      if (cudaEventCreate(&ev) != cudaSuccess) {
+        for (cudaEvent_t& x : G->trace_ev)
+          if (x) cudaEventDestroy(x);
+        G->trace_ev.clear();
+        return CFS_ECUDA;
+      }
+    }
+  }
+  G->trace = on != 0;
+  G->trace_n = 0;
+  return CFS_OK;
+}
+
+extern "C" int cfs_group_trace(cfs_group_t G, float* ms, int capacity, int* count) {
+  if (!G || !count || capacity < 0 || (capacity > 0 && !ms)) return CFS_EINVAL;
+  *count = G->trace_n;
+  for (int i = 0; i < G->trace_n && i < capacity; ++i) {
+    cudaError_t e = cudaEventSynchronize(G->trace_ev[2 * i + 1]);
+    if (e == cudaSuccess)
+      e = cudaEventElapsedTime(&ms[i], G->trace_ev[2 * i], G->trace_ev[2 * i + 1]);
+    if (e != cudaSuccess) return CFS_ECUDA;
+  }
   return CFS_OK;
 }
 

@@ -254,6 +254,37 @@ def test_graph_and_host_loop_give_the_same_bits(chanfs):
         p.close()
 
 
+def test_launch_trace(chanfs):
+    """Tracing runs a grouped solve as direct launches with an event pair
+    around every copy and kernel: the same bits as the graph-launched solve,
+    one positive device time per traced operation, and a reset per solve."""
+    boxes = [make_box(chanfs, i, s) for i, s in enumerate(BOXES[:3])]
+    plans = [b[0] for b in boxes]
+    fs = [dev(b[1]) for b in boxes]
+    with chanfs.Group(plans) as g:
+        ref = [[host(o) for o in g.poisson_solve(fs)] for _ in range(3)][-1]  # graph replay
+        info = g.last_info()
+        g.set_trace(True)
+        got = [host(o) for o in g.poisson_solve(fs)]
+        ms = g.trace()
+        iters = max(i for i, _ in g.last_info())
+        # start copies and kernels, at least one iteration's stages, the tail
+        assert len(ms) >= 8 + 6 * iters, (len(ms), iters)
+        assert all(t > 0.0 for t in ms) and sum(ms) < 1e3
+        assert g.last_info() == info
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b)
+        n_p = len(ms)
+        g.helmholtz_solve([1e-5] * 3, fs, [chanfs.CENTER] * 3)
+        assert 0 < len(g.trace()) < n_p + 40  # counted afresh
+        assert g.trace(capacity=2) == g.trace()[:2]
+        g.set_trace(False)
+        g.poisson_solve(fs)
+        assert len(g.trace()) == 0  # untraced solves record nothing
+    for p in plans:
+        p.close()
+
+
 def test_rebinding_reuses_or_captures_graphs(chanfs):
     """Rebinding to other boxes (a new launch shape) and back (a cached
     graph, now reading the re-uploaded tables) gives each box its own bits."""
