@@ -845,6 +845,47 @@ def run_mixed_only(args):
     return 0
 
 
+def run_zsolve_only(args):
+    """The refined Poisson solve of the 1024 x 768 x nz uniform workload with
+    each z-solve kernel of FP32 spectra: the partitioned solve
+    (CFS_OPT_THOMAS_TILE 1) and the streaming sweep (-1); median CUDA-event
+    ms per solve over --steps solves after one warm-up solve each."""
+    import torch
+    torch.cuda.set_device(0)
+    device = torch.device("cuda", 0)
+    from paper_2502_06296_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2502_06296_gb300 import chanfs
+    cfg = dict(synth.PRECISION)
+    if args.mixed_nz:
+        cfg.update(nz=args.mixed_nz)
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    f = torch.from_numpy(synth.precision_rhs(cfg)).to(device)
+    p = torch.empty_like(f)
+    out = {"workload": f"poisson_uniform_{nx}x{ny}x{nz}"}
+    with chanfs.Plan(nx, ny, nz, cfg["lx"], cfg["ly"], synth.grid_dz(cfg), chanfs.NEUMANN,
+                     chanfs.F32_REFINED) as plan:
+        for tw, name in ((1, "partitioned"), (-1, "streaming")):
+            plan.set_option(chanfs.OPT_THOMAS_TILE, tw)
+            plan.poisson_solve(f, out=p)
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(args.steps):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                with nvtx_range(f"refined_solve_{name}"):
+                    plan.poisson_solve(f, out=p)
+                b.record()
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            it, rho = plan.last_info()
+            out[name] = {"ms": round(statistics.median(ms), 4), "fp32_solves": it,
+                         "rel_residual": rho}
+    print(json.dumps({"zsolve": out}), flush=True)
+    return 0
+
+
 def run_helmholtz_only(args):
     import torch
     torch.cuda.set_device(0)
@@ -1173,6 +1214,9 @@ def main(argv=None):
                     help="wall-normal size of the mixed comparison (profiling captures only)")
     ap.add_argument("--mixed-only", action="store_true",
                     help="run only the FP32-refined vs FP64 comparison and print its object")
+    ap.add_argument("--zsolve-only", action="store_true",
+                    help="time the refined Poisson solve with each FP32 z-solve kernel "
+                         "(1024 x 768 x --mixed-nz, default 512)")
     ap.add_argument("--helmholtz-only", action="store_true",
                     help="time only the FP64 and refined Helmholtz solves per size")
     ap.add_argument("--helm-size", default="",
@@ -1195,6 +1239,8 @@ def main(argv=None):
         return run_probe_only(args)
     if args.helmholtz_only:
         return run_helmholtz_only(args)
+    if args.zsolve_only:
+        return run_zsolve_only(args)
     if args.slab:
         return run_slab(args)
     if args.extras_only:

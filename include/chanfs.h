@@ -48,7 +48,8 @@ typedef enum {
   CFS_ECUDA = -4,          /* a CUDA runtime call failed */
   CFS_ETIMEOUT = -5,       /* a device-side bounded wait ran out */
   CFS_ENOTCONVERGED = -6,  /* iterative refinement missed its tolerance */
-  CFS_ECANCELED = -7       /* a served request was cancelled before it ran */
+  CFS_ECANCELED = -7,      /* a served request was cancelled before it ran */
+  CFS_EGUARD = -8          /* guard words around a plan work buffer were overwritten */
 } cfs_status;
 
 typedef enum { CFS_BC_NEUMANN = 0, CFS_BC_DIRICHLET = 1 } cfs_bc;   /* z walls */
@@ -479,7 +480,12 @@ int cfs_slab_helmholtz_finish(cfs_slab_t slab, double c, int loc, const double* 
  *   CFS_OPT_THOMAS_TILE  columns per shared-memory tile of the z sweeps of
  *       Eq. 12: 0 automatic (the default), 8 or 16, or -1 for the streaming
  *       kernel (one thread per column, rows through registers, the forward
- *       sweep's intermediate written to the spectrum and read back).
+ *       sweep's intermediate written to the spectrum and read back), or, for
+ *       the FP32 solves of CFS_F32_REFINED plans with Nz <= 512, 1: Algorithm 2
+ *       (Sec. 2.2.4) over z-partitions of 8 rows in registers, the rows of
+ *       Eq. 12 formed on the fly (the spectrum read and written once; the
+ *       plan's FP64 sweeps then stream).  1 on an FP64 plan, or with Nz > 512,
+ *       is CFS_EUNSUPPORTED.
  *   CFS_OPT_X_LINES  x-lines per CTA of the x transforms: 0 automatic (about
  *       16 KB of data per buffer) or 1..64.
  *   CFS_OPT_Y_TILE  complex columns per y-transform tile (of the precision the
@@ -596,6 +602,22 @@ int cfs_selftest_wait_timeout(cfs_plan_t plan, int* device_status, unsigned poll
  * wait inside a kernel ran out, CFS_ECUDA if the device reported an error.
  */
 int cfs_plan_check(cfs_plan_t plan, int* device_error);
+
+/*
+ * cfs_plan_check_guards -- a stand-in for a device memory checker (no
+ * counterpart in the paper).  The work buffers of a plan that its kernels
+ * write (the factor tables of Eq. 12, the FP32 fields and the reduction
+ * scratch of refined plans) are allocated with 256 bytes of a fixed pattern
+ * before and after them.  This waits for the device and compares every
+ * pattern; *damaged (may be NULL) receives the number of buffers with an
+ * overwritten guard.  Returns CFS_EGUARD if there is one, else CFS_OK.
+ * cfs_plan_debug_guard_poke overwrites one byte of buffer `buffer`'s leading
+ * (tail = 0: the byte just before the buffer) or trailing (tail != 0: the
+ * byte just after it) guard with a host-side memset, for tests of the check;
+ * CFS_EINVAL if the plan has no such buffer.
+ */
+int cfs_plan_check_guards(cfs_plan_t plan, int* damaged);
+int cfs_plan_debug_guard_poke(cfs_plan_t plan, int buffer, int tail);
 
 #ifdef __cplusplus
 }

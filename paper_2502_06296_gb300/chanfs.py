@@ -40,6 +40,7 @@ class ServerStats(ctypes.Structure):
                 ("workers_alive", ctypes.c_int), ("pending", ctypes.c_int)]
 
 OK, EINVAL, ENOMEM, EUNSUPPORTED, ECUDA, ETIMEOUT, ENOTCONVERGED, ECANCELED = 0, -1, -2, -3, -4, -5, -6, -7
+EGUARD = -8
 FAULT_PLAN_ALLOC, FAULT_WORKER_START = 1, 2
 
 _lib = None
@@ -75,6 +76,8 @@ def lib():
             "cfs_poisson_solve_host": ([vp, vp, vp, vp], i),
             "cfs_helmholtz_solve_host": ([vp, d, i, vp, vp, vp], i),
             "cfs_plan_check": ([vp, ctypes.POINTER(i)], i),
+            "cfs_plan_check_guards": ([vp, ctypes.POINTER(i)], i),
+            "cfs_plan_debug_guard_poke": ([vp, i, i], i),
             "cfs_poisson_stage": ([vp, i, vp, vp, vp], i),
             "cfs_plan_set_refinement": ([vp, d, i], i),
             "cfs_helmholtz_solve_noalloc": ([i, i, i, dp, d, i, i, vp, vp, vp, vp], i),
@@ -323,6 +326,19 @@ class Plan:
         rc = lib().cfs_plan_check(self._h, ctypes.byref(bits))
         _check(rc, "cfs_plan_check")
         return bits.value
+
+    def check_guards(self) -> int:
+        """Synchronise and compare the guard words around the plan's work
+        buffers (cfs_plan_check_guards); raises ChanfsError(EGUARD) if any
+        was overwritten, else returns 0."""
+        n = ctypes.c_int(0)
+        _check(lib().cfs_plan_check_guards(self._h, ctypes.byref(n)), "cfs_plan_check_guards")
+        return n.value
+
+    def debug_guard_poke(self, buffer: int, tail: bool):
+        """Overwrite one byte of a work buffer's guard (tests of the check)."""
+        _check(lib().cfs_plan_debug_guard_poke(self._h, int(buffer), int(bool(tail))),
+               "cfs_plan_debug_guard_poke")
 
 
 def helmholtz_solve_noalloc(dz, c: float, rhs, loc: int = CENTER, nparts: int = 0, out=None,

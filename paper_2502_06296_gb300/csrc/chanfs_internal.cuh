@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
 #include <vector>
 
 #include "../../include/chanfs.h"
@@ -195,6 +196,8 @@ struct cfs_plan {
   cudaEvent_t ev_entry, ev_in[4], ev_done[4], ev_free[4];
   // device status word
   int* d_status;
+  // work buffers allocated with guard words: (allocation base, payload bytes)
+  std::vector<std::pair<unsigned char*, size_t>> guarded;
   size_t device_bytes;
 };
 

@@ -76,6 +76,30 @@ static int dev_upload(T** dst, const T* src, size_t count, size_t* acc) {
   return CFS_OK;
 }
 
+// Guard words around the work buffers that kernels write (factor tables, the
+// refinement's FP32 fields and reduction scratch): kGuardBytes of a fixed
+// pattern before and after each, compared by cfs_plan_check_guards, so that a
+// kernel storing past either end of its buffer is noticed at the next check.
+// (A stand-in for a device memory checker in runs that cannot use one.)
+constexpr size_t kGuardBytes = 256;   // keeps the buffer 256-byte aligned
+constexpr uint32_t kGuardWord = 0x6A09E667u;
+
+template <typename T>
+static int dev_alloc_guarded(cfs_plan* P, T** dst, size_t count) {
+  const size_t bytes = sizeof(T) * count;
+  unsigned char* base = nullptr;
+  if (cudaMalloc(&base, bytes + 2 * kGuardBytes) != cudaSuccess) return CFS_ENOMEM;
+  P->guarded.push_back({base, bytes});
+  P->device_bytes += bytes + 2 * kGuardBytes;
+  const std::vector<uint32_t> pat(kGuardBytes / sizeof(uint32_t), kGuardWord);
+  if (cudaMemcpy(base, pat.data(), kGuardBytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(base + kGuardBytes + bytes, pat.data(), kGuardBytes, cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+    return CFS_ECUDA;
+  *dst = reinterpret_cast<T*>(base + kGuardBytes);
+  return CFS_OK;
+}
+
 // z stencil of the staggered grid (Sec. 2.1, eta of Eq. 12), flux form:
 //   (L_z p)_k = [(p_{k+1}-p_k)/dzc_k - (p_k-p_{k-1})/dzc_{k-1}] / dzf_k,
 // centred unknowns with mirror ghosts at the walls (Neumann: p_{-1} = p_0;
@@ -131,17 +155,17 @@ extern "C" const char* cfs_status_string(int s) {
     case CFS_ETIMEOUT: return "device-side wait timed out";
     case CFS_ENOTCONVERGED: return "not converged";
     case CFS_ECANCELED: return "cancelled";
+    case CFS_EGUARD: return "guard words around a work buffer were overwritten";
     default: return "unknown status";
   }
 }
 
 static void plan_free(cfs_plan* P) {
   if (!P) return;
+  for (const auto& g : P->guarded) cudaFree(g.first);  // guarded work buffers
   cudaFree(P->d_twx);
   cudaFree(P->d_twy);
   cudaFree(P->d_post);
-  cudaFree(P->d_fwd);
-  cudaFree(P->d_bwd);
   cudaFree(P->d_dzf);
   cudaFree(P->d_sing);
   cudaFree(P->d_stage);
@@ -156,17 +180,9 @@ static void plan_free(cfs_plan* P) {
   cudaFree(P->d_twx32);
   cudaFree(P->d_twy32);
   cudaFree(P->d_post32);
-  cudaFree(P->d_fwd32);
-  cudaFree(P->d_bwd32);
   cudaFree(P->d_zrow32);
   cudaFree(P->d_lam32);
-  cudaFree(P->d_r32);
-  cudaFree(P->d_r32b);
-  cudaFree(P->d_rlo);
-  cudaFree(P->d_w2);
   cudaFree(P->d_zk);
-  cudaFree(P->d_mpart);
-  cudaFree(P->d_red);
   cudaFree(P->d_wy);
   cudaFree(P->d_wy32);
 
@@ -347,8 +363,8 @@ extern "C" int cfs_plan_create_walls(cfs_plan_t* out, int nx, int ny, int nz, do
   if (!rc) rc = dev_upload(&P->d_dzf, P->dzf.data(), (size_t)nz, &P->device_bytes);
   if (!rc) rc = dev_upload(&P->d_sing, sing.data(), sing.size(), &P->device_bytes);
   if (!rc && !wy.empty()) rc = dev_upload(&P->d_wy, wy.data(), wy.size(), &P->device_bytes);
-  if (!rc) rc = dev_upload<double2>(&P->d_fwd, nullptr, nfac, &P->device_bytes);
-  if (!rc) rc = dev_upload<double>(&P->d_bwd, nullptr, nfac, &P->device_bytes);
+  if (!rc) rc = dev_alloc_guarded(P, &P->d_fwd, nfac);
+  if (!rc) rc = dev_alloc_guarded(P, &P->d_bwd, nfac);
   if (!rc) rc = dev_upload<int>(&P->d_status, nullptr, 1, &P->device_bytes);
   if (!rc) rc = cuda_status(cudaMemset(P->d_status, 0, sizeof(int)));
   if (!rc && refined) {
@@ -365,8 +381,8 @@ extern "C" int cfs_plan_create_walls(cfs_plan_t* out, int nx, int ny, int nz, do
       const std::vector<float2> wy32 = f32(wy);
       rc = dev_upload(&P->d_wy32, wy32.data(), wy32.size(), &P->device_bytes);
     }
-    if (!rc) rc = dev_upload<float2>(&P->d_fwd32, nullptr, nfac, &P->device_bytes);
-    if (!rc) rc = dev_upload<float>(&P->d_bwd32, nullptr, nfac, &P->device_bytes);
+    if (!rc) rc = dev_alloc_guarded(P, &P->d_fwd32, nfac);
+    if (!rc) rc = dev_alloc_guarded(P, &P->d_bwd32, nfac);
     {  // the partitioned FP32 z solve forms its rows from these, divided by
        // the inverse-FFT normalisation s (its solution then comes out scaled)
       const double is = ((double)nx * (double)ny) / 2.0;
@@ -380,10 +396,9 @@ extern "C" int cfs_plan_create_walls(cfs_plan_t* out, int nx, int ny, int nz, do
       if (!rc) rc = dev_upload(&P->d_zrow32, zrow.data(), zrow.size(), &P->device_bytes);
       if (!rc) rc = dev_upload(&P->d_lam32, lam.data(), lam.size(), &P->device_bytes);
     }
-    if (!rc) rc = dev_upload<float>(&P->d_r32, nullptr, (size_t)nx * ny * nz, &P->device_bytes);
+    if (!rc) rc = dev_alloc_guarded(P, &P->d_r32, (size_t)nx * ny * nz);
     if (!rc)
-      rc = dev_upload<double>(&P->d_red, nullptr, (size_t)nz * start_chunks(nz) + 8,
-                              &P->device_bytes);
+      rc = dev_alloc_guarded(P, &P->d_red, (size_t)nz * start_chunks(nz) + 8);
     // The residual kernels' coefficients, each split as hi = fl32(v),
     // lo = fl32(v - hi), packed per plane (three float4: (A, C), (B', dz),
     // (D, dz)) and then (1/dx^2, 1/dy^2).  D_k = A_k + B'_k + C_k + 2/dx^2 +
@@ -423,11 +438,10 @@ extern "C" int cfs_plan_create_walls(cfs_plan_t* out, int nx, int ny, int nz, do
     if (!rc) rc = dev_upload(&P->d_zk, zk.data(), zk.size(), &P->device_bytes);
     P->inv_wn = 1.0 / (wsum * (double)nx * (double)ny);
     if (!rc)
-      rc = dev_upload<double>(&P->d_mpart, nullptr, ((size_t)nx * ny + 127) / 128,
-                              &P->device_bytes);
-    if (!rc) rc = dev_upload<float>(&P->d_r32b, nullptr, (size_t)nx * ny * nz, &P->device_bytes);
-    if (!rc) rc = dev_upload<float>(&P->d_rlo, nullptr, (size_t)nx * ny * nz, &P->device_bytes);
-    if (!rc) rc = dev_upload<float>(&P->d_w2, nullptr, (size_t)nx * ny * nz, &P->device_bytes);
+      rc = dev_alloc_guarded(P, &P->d_mpart, ((size_t)nx * ny + 127) / 128);
+    if (!rc) rc = dev_alloc_guarded(P, &P->d_r32b, (size_t)nx * ny * nz);
+    if (!rc) rc = dev_alloc_guarded(P, &P->d_rlo, (size_t)nx * ny * nz);
+    if (!rc) rc = dev_alloc_guarded(P, &P->d_w2, (size_t)nx * ny * nz);
   }
 
   if (!rc) rc = dev_upload(&dA, A.data(), A.size(), &scratch);
@@ -1136,6 +1150,34 @@ extern "C" int cfs_solve_batch_host(cfs_plan_t P, int n, const int* kind, const 
   if (rc != CFS_OK && rc != CFS_ENOTCONVERGED) return rc;
   if (e != cudaSuccess || ef != cudaSuccess) return CFS_ECUDA;
   return rc;
+}
+
+extern "C" int cfs_plan_check_guards(cfs_plan_t P, int* damaged) {
+  if (!P) return CFS_EINVAL;
+  CaptureLock lock(capture_mutex());
+  if (cudaDeviceSynchronize() != cudaSuccess) return CFS_ECUDA;
+  std::vector<uint32_t> got(kGuardBytes / sizeof(uint32_t));
+  int bad = 0;
+  for (const auto& g : P->guarded) {
+    unsigned char* ends[2] = {g.first, g.first + kGuardBytes + g.second};
+    bool ok = true;
+    for (unsigned char* at : ends) {
+      if (cudaMemcpy(got.data(), at, kGuardBytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return CFS_ECUDA;
+      for (uint32_t w : got) ok = ok && (w == kGuardWord);
+    }
+    bad += ok ? 0 : 1;
+  }
+  if (damaged) *damaged = bad;
+  return bad ? CFS_EGUARD : CFS_OK;
+}
+
+extern "C" int cfs_plan_debug_guard_poke(cfs_plan_t P, int buffer, int tail) {
+  if (!P || buffer < 0 || buffer >= (int)P->guarded.size()) return CFS_EINVAL;
+  CaptureLock lock(capture_mutex());
+  const auto& g = P->guarded[buffer];
+  unsigned char* at = tail ? g.first + kGuardBytes + g.second : g.first + kGuardBytes - 1;
+  return cudaMemset(at, 0x5A, 1) == cudaSuccess ? CFS_OK : CFS_ECUDA;
 }
 
 extern "C" int cfs_plan_check(cfs_plan_t P, int* device_error) {

@@ -33,7 +33,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_version_and_status_strings(lib):
     assert lib.cfs_version() == 100
-    for s in range(-7, 1):
+    for s in range(-8, 1):
         assert chanfs.status_string(s) not in ("", "unknown status")
     assert chanfs.status_string(-99) == "unknown status"
 
@@ -76,6 +76,10 @@ def test_null_handles_are_rejected(lib):
     assert lib.cfs_plan_check(None, None) == chanfs.EINVAL
     assert lib.cfs_spectral_forward(None, None, None, None) == chanfs.EINVAL
     assert lib.cfs_poisson_solve_host(None, None, None, None) == chanfs.EINVAL
+    assert lib.cfs_plan_check_guards(None, None) == chanfs.EINVAL
+    assert lib.cfs_plan_debug_guard_poke(None, 0, 0) == chanfs.EINVAL
+    assert lib.cfs_group_set_trace(None, 1) == chanfs.EINVAL
+    assert lib.cfs_group_trace(None, None, 0, None) == chanfs.EINVAL
 
 
 def test_product_package_does_not_import_the_oracle():

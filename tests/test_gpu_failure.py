@@ -104,6 +104,45 @@ def _poisson_ref(f):
     return oracle.poisson_solve(f, 12.8, 6.4, synth.tanh_dz(nz, beta), bc)
 
 
+@pytest.mark.parametrize("dtype,nbuf", [(0, 2), (1, 10)])
+def test_guard_words_around_work_buffers(chanfs, dtype, nbuf):
+    """The work buffers kernels write carry guard words: intact after every
+    kind of solve (no kernel stores past its buffer), and a byte overwritten
+    just before or just after a buffer (a host-side memset into the guard) is
+    reported as CFS_EGUARD with the number of damaged buffers."""
+    nx, ny, nz = 64, 48, 40
+    dz = synth.tanh_dz(nz, 1.6)
+    f = synth.remove_weighted_mean(synth.normal(61, (nz, ny, nx)), dz)
+    with chanfs.Plan(nx, ny, nz, 2.0, 1.0, dz, 0, dtype) as plan:
+        t = torch.from_numpy(f).cuda()
+        plan.poisson_solve(t)
+        for loc in (chanfs.CENTER, chanfs.FACE):
+            plan.helmholtz_solve(1e-4, t, loc)
+        plan.helmholtz3d_solve(1e-4, t)
+        if dtype == 1:
+            plan.set_option(chanfs.OPT_THOMAS_TILE, 1)
+            plan.poisson_solve(t)
+            with chanfs.Group([plan]) as g:
+                g.poisson_solve([t])
+                g.helmholtz_solve([1e-4], [t])
+        assert plan.check_guards() == 0
+        plan.debug_guard_poke(0, False)
+        with pytest.raises(chanfs.ChanfsError) as err:
+            plan.check_guards()
+        assert err.value.status == chanfs.EGUARD
+        plan.debug_guard_poke(nbuf - 1, True)
+        n = ctypes.c_int(0)
+        assert chanfs.lib().cfs_plan_check_guards(plan._h, ctypes.byref(n)) == chanfs.EGUARD
+        assert n.value == 2
+        with pytest.raises(chanfs.ChanfsError) as err:
+            plan.debug_guard_poke(nbuf, False)  # no such buffer
+        assert err.value.status == chanfs.EINVAL
+        # the plan still solves correctly (the guards are outside its data)
+        p = plan.poisson_solve(t).cpu().numpy()
+        ref = oracle.poisson_solve(f, 2.0, 1.0, dz, 0)
+        assert np.max(np.abs(p - ref)) / np.max(np.abs(ref)) < (1e-12 if dtype == 0 else 1e-10)
+
+
 def test_refused_plan_allocation_fails_only_its_request(chanfs):
     srv, run = _server(chanfs, workers=1)
     with srv:

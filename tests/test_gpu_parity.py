@@ -194,10 +194,13 @@ def test_thomas_shapes_match_oracle(chanfs, dims, beta, bc):
 
 def test_thomas_option_rejects_bad_values(chanfs):
     with chanfs.Plan(16, 12, 10, 1.0, 1.0, np.full(10, 0.2)) as plan:
-        for bad in (1, 4, 32, -2):
+        for bad in (2, 4, 32, -2):
             with pytest.raises(chanfs.ChanfsError) as err:
                 plan.set_option(chanfs.OPT_THOMAS_TILE, bad)
             assert err.value.status == chanfs.EINVAL
+        with pytest.raises(chanfs.ChanfsError) as err:  # the partitioned solve is FP32 only
+            plan.set_option(chanfs.OPT_THOMAS_TILE, 1)
+        assert err.value.status == chanfs.EUNSUPPORTED
         with pytest.raises(chanfs.ChanfsError) as err:
             plan.set_option(99, 0)
         assert err.value.status == chanfs.EINVAL
