@@ -35,11 +35,15 @@ constexpr int kThomasBlock = 64;
 template <class CA> struct prefetch_rows { static constexpr int value = 3; };
 template <> struct prefetch_rows<float2> { static constexpr int value = 6; };
 // The same for a thread that sweeps two columns (sweep_pair): two rows per
-// step.  DEEP: the launch fits in one wave at 8 blocks per SM (FP64 plans of
-// moderate size), so each thread may keep a deeper queue.
-template <class CA, bool DEEP> struct pair_prefetch_rows { static constexpr int value = 2; };
-template <> struct pair_prefetch_rows<double2, true> { static constexpr int value = 4; };
-template <bool DEEP> struct pair_prefetch_rows<float2, DEEP> { static constexpr int value = 3; };
+// step.  DEEP (FP64 plans of moderate size): the launch fits in one wave at
+// 6 (DEEP = 6) or 8 (DEEP = 4) blocks per SM, so each thread may keep a
+// queue of DEEP rows; the sweep is bound by memory latency at the few warps
+// per SM such a launch has (the channel's FP64 spectrum: 772 blocks, 6 rows
+// measured 5 % faster than 4).
+template <class CA, int DEEP> struct pair_prefetch_rows {
+  static constexpr int value = DEEP ? DEEP : 2;
+};
+template <int DEEP> struct pair_prefetch_rows<float2, DEEP> { static constexpr int value = 3; };
 
 template <class C> struct cplx_traits;
 template <> struct cplx_traits<double2> {
@@ -315,7 +319,7 @@ __device__ __forceinline__ bool fp64_column(const ThomasArgs& a, int ky, int j) 
   return j < a.kx64 && kp < a.ky64;
 }
 
-template <class CS, bool DEEP>
+template <class CS, int DEEP>
 __device__ __forceinline__ void thomas_body(const ThomasArgs& a, int blk) {
   const int ky = blk / a.nblk_x;  // (the pair index kp for periodic y)
   const int j = (blk % a.nblk_x) * kThomasBlock + threadIdx.x;
@@ -370,17 +374,19 @@ __host__ __device__ inline int special_blocks(const ThomasArgs& a) {
 
 // One launch: the special columns' blocks first (their sweeps are the
 // longest-latency ones and overlap the main columns), then the main blocks.
-template <class CS, bool DEEP>
+template <class CS, int DEEP>
 __device__ __forceinline__ void thomas_launch_body(const ThomasArgs& a, int blk) {
   const int nsp = special_blocks<CS>(a);
   if (blk < nsp) thomas_special_body<CS>(a, blk);
   else thomas_body<CS, DEEP>(a, blk - nsp);
 }
 
-// Resident blocks the register budget is sized for: 14 per SM, or 8 with
-// deeper prefetch queues (DEEP) for launches that fit in one wave of those.
-template <class CS, bool DEEP>
-__global__ void __launch_bounds__(kThomasBlock, DEEP ? 8 : 14) thomas_kernel(ThomasArgs a) {
+// Resident blocks the register budget is sized for: 14 per SM, or 8 / 6
+// with deeper prefetch queues (DEEP 4 / 6) for launches that fit in one wave
+// of those.
+template <class CS, int DEEP>
+__global__ void __launch_bounds__(kThomasBlock, DEEP == 6 ? 6 : (DEEP == 4 ? 8 : 14))
+    thomas_kernel(ThomasArgs a) {
   thomas_launch_body<CS, DEEP>(a, blockIdx.x);
 }
 
@@ -389,7 +395,7 @@ __global__ void __launch_bounds__(kThomasBlock, 14) thomas_group_kernel(const Th
                                                                         GroupMap g) {
   int b, blk;
   if (!group_block(g, &b, &blk)) return;
-  thomas_launch_body<float2, false>(boxes[b], blk);
+  thomas_launch_body<float2, 0>(boxes[b], blk);
 }
 
 template <class CS>
@@ -404,12 +410,16 @@ static cudaError_t launch_streaming(const ThomasArgs& a, cudaStream_t st) {
     sms.store(nsm, std::memory_order_relaxed);
   }
   if constexpr (sizeof(CS) == sizeof(double2)) {
+    if (blocks <= 6LL * nsm) {
+      thomas_kernel<CS, 6><<<(unsigned)blocks, kThomasBlock, 0, st>>>(a);
+      return cudaGetLastError();
+    }
     if (blocks <= 8LL * nsm) {
-      thomas_kernel<CS, true><<<(unsigned)blocks, kThomasBlock, 0, st>>>(a);
+      thomas_kernel<CS, 4><<<(unsigned)blocks, kThomasBlock, 0, st>>>(a);
       return cudaGetLastError();
     }
   }
-  thomas_kernel<CS, false><<<(unsigned)blocks, kThomasBlock, 0, st>>>(a);
+  thomas_kernel<CS, 0><<<(unsigned)blocks, kThomasBlock, 0, st>>>(a);
   return cudaGetLastError();
 }
 
