@@ -201,3 +201,116 @@ def test_auto_partitions(h):
         assert 1 <= p <= 64
         assert all((q + 1) * n // p - q * n // p >= 3 for q in range(p))
         assert p == max(1, min(64, (n + 31) // 32)) or n // ((n + 31) // 32) < 3
+
+
+# ---------------------------------------------------------------------------
+# The partitioned z solve of FP32 spectra (thomas.cu, zpart_kernel), restated
+# in numpy: 8-row partitions with identity rows past the last row, the
+# normalised downward elimination with x_0 a parameter, the upward
+# elimination into row 0, cyclic reduction of the 2P-row reduced system, and
+# back substitution in the downward form.  The restatement must solve the
+# system (against numpy.linalg.solve): this checks the derivation the kernel
+# implements; the kernel itself is checked against the oracle on the GPU.
+# ---------------------------------------------------------------------------
+
+def _zpart_solve(A, D, C, d, mm=8):
+    n = D.size
+    P = (n + mm - 1) // mm
+    N = P * mm
+    A_, D_, C_ = np.zeros(N), np.ones(N), np.zeros(N)
+    A_[:n], D_[:n], C_[:n] = A, D, C
+    A_[0] = 0.0
+    C_[n - 1] = 0.0
+    rhs = np.zeros(N, dtype=d.dtype)
+    rhs[:n] = d
+    red = np.zeros((2 * P, 3))
+    ry = np.zeros(2 * P, dtype=d.dtype)
+    keep = []
+    for q in range(P):
+        o = q * mm
+        a, b, c, u = A_[o:o + mm], D_[o:o + mm], C_[o:o + mm], rhs[o:o + mm].copy()
+        cq, gq = np.zeros(mm), np.zeros(mm)
+        ib = 1.0 / b[1]
+        cq[1], gq[1], u[1] = c[1] * ib, a[1] * ib, u[1] * ib
+        for i in range(2, mm):
+            ib = 1.0 / (b[i] - a[i] * cq[i - 1])
+            cq[i] = c[i] * ib
+            gq[i] = -a[i] * ib * gq[i - 1]
+            u[i] = (u[i] - a[i] * u[i - 1]) * ib
+        uu, vv, ww = u[mm - 2], gq[mm - 2], cq[mm - 2]
+        for i in range(mm - 3, 0, -1):
+            uu, vv, ww = u[i] - cq[i] * uu, gq[i] - cq[i] * vv, -cq[i] * ww
+        red[2 * q] = (a[0], b[0] - c[0] * vv, -c[0] * ww)
+        ry[2 * q] = u[0] - c[0] * uu
+        red[2 * q + 1] = (gq[mm - 1], 1.0, cq[mm - 1])
+        ry[2 * q + 1] = u[mm - 1]
+        keep.append((cq, gq, u))
+    # cyclic reduction: at stride s the rows k = -1 mod 2s take away k -+ s
+    J = 2 * P
+    s = 1
+    while 2 * s <= J:
+        for k in range(2 * s - 1, J, 2 * s):
+            sub, dia, sup = red[k]
+            y = ry[k]
+            lo = red[k - s]
+            e1 = sub / lo[1]
+            dia -= e1 * lo[2]
+            y -= e1 * ry[k - s]
+            sub = -e1 * lo[0]
+            new_sup = 0.0
+            if k + s < J:
+                hi = red[k + s]
+                e2 = sup / hi[1]
+                dia -= e2 * hi[0]
+                y -= e2 * ry[k + s]
+                new_sup = -e2 * hi[2]
+            red[k] = (sub, dia, new_sup)
+            ry[k] = y
+        s *= 2
+    x = np.zeros(J, dtype=d.dtype)
+    top = s - 1
+    x[top] = ry[top] / red[top][1]
+    h = s // 2
+    while h >= 1:
+        for k in range(h - 1, J, 2 * h):
+            if k == top:
+                continue
+            y = ry[k]
+            if k - h >= 0:
+                y = y - red[k][0] * x[k - h]
+            if k + h < J:
+                y = y - red[k][2] * x[k + h]
+            x[k] = y / red[k][1]
+        h //= 2
+    out = np.zeros(N, dtype=d.dtype)
+    for q in range(P):
+        cq, gq, u = keep[q]
+        o = q * mm
+        xs = np.zeros(mm, dtype=d.dtype)
+        xs[0], xs[mm - 1] = x[2 * q], x[2 * q + 1]
+        for i in range(mm - 2, 0, -1):
+            xs[i] = u[i] - cq[i] * xs[i + 1] - gq[i] * xs[0]
+        out[o:o + mm] = xs
+    return out[:n]
+
+
+@pytest.mark.parametrize("n", [3, 5, 8, 9, 17, 40, 97, 128, 300, 512])
+@pytest.mark.parametrize("lam", [-1e-3, -5.0])
+def test_partitioned_z_solve_algebra(n, lam):
+    """Eq. 12 rows (the z operator of a stretched grid shifted by an
+    eigenvalue), complex right-hand side, against a dense solve."""
+    dz = synth.tanh_dz(n, 1.8)
+    zf = np.concatenate(([0.0], np.cumsum(dz)))
+    zc = 0.5 * (zf[:-1] + zf[1:])
+    h = np.diff(zc)
+    A, C = np.zeros(n), np.zeros(n)
+    A[1:] = 1.0 / (dz[1:] * h)
+    C[:-1] = 1.0 / (dz[:-1] * h)
+    B = -(A + C)  # Neumann walls: the wall couplings fold into the diagonal
+    D = B + lam
+    rng = np.random.default_rng(n)
+    d = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    T = np.diag(D) + np.diag(A[1:], -1) + np.diag(C[:-1], 1)
+    ref = np.linalg.solve(T, d)
+    got = _zpart_solve(A, D, C, d)
+    assert np.max(np.abs(got - ref)) <= 1e-9 * np.max(np.abs(ref))
