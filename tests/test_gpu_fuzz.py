@@ -1,0 +1,111 @@
+"""GPU: a seeded sweep over many small plan shapes against the oracle.
+
+Each case draws a grid (x and y lengths with prime factors 2 and 3 only, as
+the transforms require; 3..80 cells in z, uniform or tanh-stretched), the
+wall conditions (z: Neumann or Dirichlet; y: periodic, Neumann or Dirichlet
+walls), the precision (FP64, or FP32 solves with FP64 refinement) and kernel
+shapes (z-solve kernel, Algorithm 2 partitions, Thomas or Algorithm 2 for
+Helmholtz), then checks a Poisson and a Helmholtz solve element by element
+against the oracle: relative max-norm 1e-12 for FP64 plans, 1e-10 for
+refined ones.  Shapes the library declines (CFS_EUNSUPPORTED) are skipped
+and counted; most must be accepted.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2502_06296_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+def _smooth(n):
+    """True when n has no prime factors other than 2 and 3."""
+    for p in (2, 3):
+        while n % p == 0:
+            n //= p
+    return n == 1
+
+
+SMOOTH = [n for n in range(1, 97) if _smooth(n)]
+
+
+@pytest.fixture(scope="module")
+def chanfs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_06296_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2502_06296_gb300 import chanfs as c
+    c.lib()
+    return c
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def draw(rng, chanfs):
+    refined = bool(rng.integers(2))
+    while True:
+        m = int(rng.choice([k for k in SMOOTH if 2 <= k <= 48]))
+        nx = 2 * m
+        if not refined or nx % 4 == 0:
+            break
+    ny = int(rng.choice([k for k in SMOOTH if k <= 96]))
+    nz = int(rng.integers(4, 81))
+    beta = float(rng.choice([0.0, 1.2, 1.8, 2.4]))
+    bc = int(rng.integers(2))
+    ybc = int(rng.choice([0, 0, 1, 2]))
+    c = float(10.0 ** rng.uniform(-6, -2))
+    loc = int(rng.integers(2))
+    opts = {"thomas": int(rng.choice([0, -1, 8, 16] + ([1] if refined else []))),
+            "parts": int(rng.choice([0, 0, 2, 4, 8])),
+            "helm_thomas": int(rng.integers(2))}
+    return dict(refined=refined, nx=nx, ny=ny, nz=nz, beta=beta, bc=bc, ybc=ybc, c=c, loc=loc,
+                opts=opts)
+
+
+def test_random_plans_match_the_oracle(chanfs):
+    rng = np.random.default_rng(2502)
+    ran = skipped = 0
+    for case in range(96):
+        d = draw(rng, chanfs)
+        nx, ny, nz = d["nx"], d["ny"], d["nz"]
+        lx, ly = 2.0 + nx / 64.0, 1.0 + ny / 64.0
+        dz = synth.uniform_dz(nz) if d["beta"] == 0.0 else synth.tanh_dz(nz, d["beta"])
+        dtype = chanfs.F32_REFINED if d["refined"] else chanfs.F64
+        try:
+            plan = chanfs.Plan(nx, ny, nz, lx, ly, dz, d["bc"], dtype, d["ybc"])
+        except chanfs.ChanfsError as e:
+            assert e.status == chanfs.EUNSUPPORTED, (d, e)
+            skipped += 1
+            continue
+        with plan:
+            for opt, key in ((chanfs.OPT_THOMAS_TILE, "thomas"), (chanfs.OPT_PCR_PARTS, "parts"),
+                             (chanfs.OPT_HELM_THOMAS, "helm_thomas")):
+                try:
+                    plan.set_option(opt, d["opts"][key])
+                except chanfs.ChanfsError as e:
+                    assert e.status == chanfs.EUNSUPPORTED, (d, key, e)
+            tol = 1e-10 if d["refined"] else 1e-12
+            f = synth.normal(1000 + case, (nz, ny, nx))
+            if d["bc"] == 0 and d["ybc"] != 2:  # the constants are the null space
+                f = synth.remove_weighted_mean(f, dz)
+            ref = (oracle.poisson_solve(f, lx, ly, dz, d["bc"]) if d["ybc"] == 0 else
+                   oracle.poisson_solve_walls(f, lx, ly, dz, d["bc"], d["ybc"]))
+            p = plan.poisson_solve(dev(f)).cpu().numpy()
+            assert rel(p, ref) < tol, (case, d, rel(p, ref))
+            rhs = synth.normal(2000 + case, (nz, ny, nx))
+            uref = oracle.helmholtz_solve(rhs, dz, d["c"], d["loc"])
+            u = plan.helmholtz_solve(d["c"], dev(rhs), d["loc"]).cpu().numpy()
+            assert rel(u, uref) < tol, (case, d, rel(u, uref))
+            assert plan.check() == 0
+            assert plan.check_guards() == 0
+            ran += 1
+    assert ran >= 72, (ran, skipped)
