@@ -480,7 +480,10 @@ int cfs_slab_helmholtz_finish(cfs_slab_t slab, double c, int loc, const double* 
  *   CFS_OPT_THOMAS_TILE  columns per shared-memory tile of the z sweeps of
  *       Eq. 12: 0 automatic (the default), 8 or 16, or -1 for the streaming
  *       kernel (one thread per column, rows through registers, the forward
- *       sweep's intermediate written to the spectrum and read back), or, for
+ *       sweep's intermediate written to the spectrum and read back).  Tiles
+ *       apply to FP64 sweeps only: the FP32 sweeps of refined plans stream
+ *       (grouped solves have no tile variant, and a box gives the same bits
+ *       grouped as alone), and get_option reports their shape.  Or, for
  *       the FP32 solves of CFS_F32_REFINED plans with Nz <= 512, 1: Algorithm 2
  *       (Sec. 2.2.4) over z-partitions of 8 rows in registers, the rows of
  *       Eq. 12 formed on the fly (the spectrum read and written once; the

@@ -1012,7 +1012,6 @@ static cudaError_t launch_tile(const cfs_plan* P, void* data, cudaStream_t st) {
 // spends longer per row, so fewer rows in flight cover the same latency; the
 // narrow tile leaves shared memory for a deeper ring.
 template <class CS, int TW> struct tile_depth { static constexpr int DG = TW == 8 ? 6 : 2; };
-template <int TW> struct tile_depth<float2, TW> { static constexpr int DG = TW == 8 ? 12 : 4; };
 
 // Tile width for this plan: the forced one, or the one that keeps more
 // threads resident per SM (the wider tile on a tie); -1 = streaming kernel.
@@ -1021,11 +1020,17 @@ static int pick_tile_width(const cfs_plan* P, int tw) {
   constexpr int D16 = tile_depth<CS, 16>::DG, D8 = tile_depth<CS, 8>::DG;
   if (tw == 1)  // the partitioned solve: FP32 spectra (FP64 sweeps stream)
     return sizeof(CS) == sizeof(float2) ? (zpart_ok(P) ? 1 : 0) : -1;
-  if (tw == -1) return -1;
-  if (tw == 16) return tile_occupancy<CS, 16, D16>(P->nz) >= 1 ? 16 : 0;
-  if (tw == 8) return tile_occupancy<CS, 8, D8>(P->nz) >= 1 ? 8 : 0;
-  if (tw != 0) return 0;
-  return -1;  // measured fastest at the workload sizes so far
+  // FP32 spectra take no tiles: their grouped solves have no tile variant,
+  // and a box must give the same bits grouped as alone
+  if constexpr (sizeof(CS) == sizeof(float2)) {
+    return (tw == -1 || tw == 0 || tw == 8 || tw == 16) ? -1 : 0;
+  } else {
+    if (tw == -1) return -1;
+    if (tw == 16) return tile_occupancy<CS, 16, D16>(P->nz) >= 1 ? 16 : 0;
+    if (tw == 8) return tile_occupancy<CS, 8, D8>(P->nz) >= 1 ? 8 : 0;
+    if (tw != 0) return 0;
+    return -1;  // measured fastest at the workload sizes so far
+  }
 }
 
 int thomas_tile_width(const cfs_plan* P, bool fp32, int tw) {
@@ -1037,8 +1042,10 @@ static cudaError_t launch_thomas_t(const cfs_plan* P, void* data, cudaStream_t s
   const int tw = pick_tile_width<CS>(P, P->thomas_tw);
   if constexpr (sizeof(CS) == sizeof(float2))
     if (tw == 1) return launch_zpart(P, static_cast<float*>(data), st);
-  if (tw == 16) return launch_tile<CS, 16, tile_depth<CS, 16>::DG>(P, data, st);
-  if (tw == 8) return launch_tile<CS, 8, tile_depth<CS, 8>::DG>(P, data, st);
+  if constexpr (sizeof(CS) == sizeof(double2)) {
+    if (tw == 16) return launch_tile<CS, 16, tile_depth<CS, 16>::DG>(P, data, st);
+    if (tw == 8) return launch_tile<CS, 8, tile_depth<CS, 8>::DG>(P, data, st);
+  }
   return launch_streaming<CS>(thomas_args(P, data), st);
 }
 

@@ -109,3 +109,58 @@ def test_random_plans_match_the_oracle(chanfs):
             assert plan.check_guards() == 0
             ran += 1
     assert ran >= 72, (ran, skipped)
+
+
+def test_random_groups_give_the_bits_of_solves_alone(chanfs):
+    """Groups of 2 to 5 random refined plans (sizes, walls, kernel options
+    drawn as above): every box's grouped Poisson and Helmholtz results equal
+    its results alone, bit for bit, through direct launches, a graph capture
+    and a replay."""
+    rng = np.random.default_rng(602)
+    groups = 0
+    for g in range(12):
+        plans, fs, rhs, alone_p, alone_u, cs, locs = [], [], [], [], [], [], []
+        try:
+            for b in range(int(rng.integers(2, 6))):
+                d = draw(rng, chanfs)
+                if not d["refined"]:
+                    continue
+                nx, ny, nz = d["nx"], d["ny"], d["nz"]
+                dz = synth.uniform_dz(nz) if d["beta"] == 0.0 else synth.tanh_dz(nz, d["beta"])
+                try:
+                    pl = chanfs.Plan(nx, ny, nz, 2.0, 1.0, dz, d["bc"], chanfs.F32_REFINED,
+                                     d["ybc"])
+                except chanfs.ChanfsError as e:
+                    assert e.status == chanfs.EUNSUPPORTED
+                    continue
+                plans.append(pl)
+                for opt, key in ((chanfs.OPT_THOMAS_TILE, "thomas"),
+                                 (chanfs.OPT_PCR_PARTS, "parts")):
+                    try:
+                        pl.set_option(opt, d["opts"][key])
+                    except chanfs.ChanfsError as e:
+                        assert e.status == chanfs.EUNSUPPORTED
+                f = synth.normal(3000 + 10 * g + b, (nz, ny, nx))
+                if d["bc"] == 0 and d["ybc"] != 2:
+                    f = synth.remove_weighted_mean(f, dz)
+                fs.append(dev(f))
+                rhs.append(dev(synth.normal(4000 + 10 * g + b, (nz, ny, nx))))
+                cs.append(d["c"])
+                locs.append(d["loc"])
+                alone_p.append(pl.poisson_solve(fs[-1]).cpu().numpy())
+                alone_u.append(pl.helmholtz_solve(cs[-1], rhs[-1], locs[-1]).cpu().numpy())
+            if len(plans) < 2:
+                continue
+            with chanfs.Group(plans) as grp:
+                for _ in range(3):
+                    got_p = [o.cpu().numpy() for o in grp.poisson_solve(fs)]
+                    got_u = [o.cpu().numpy() for o in grp.helmholtz_solve(cs, rhs, locs)]
+                    for a, b in zip(got_p, alone_p):
+                        assert np.array_equal(a, b), g
+                    for a, b in zip(got_u, alone_u):
+                        assert np.array_equal(a, b), g
+            groups += 1
+        finally:
+            for pl in plans:
+                pl.close()
+    assert groups >= 4, groups
