@@ -66,7 +66,9 @@ def draw(rng, chanfs):
     loc = int(rng.integers(2))
     opts = {"thomas": int(rng.choice([0, -1, 8, 16] + ([1] if refined else []))),
             "parts": int(rng.choice([0, 0, 2, 4, 8])),
-            "helm_thomas": int(rng.integers(2))}
+            "helm_thomas": int(rng.integers(2)),
+            "helm_fp64": int(rng.integers(2)) if refined else 0,
+            "helm_thomas32": int(rng.integers(2)) if refined else 0}
     return dict(refined=refined, nx=nx, ny=ny, nz=nz, beta=beta, bc=bc, ybc=ybc, c=c, loc=loc,
                 opts=opts)
 
@@ -101,6 +103,10 @@ def test_random_plans_match_the_oracle(chanfs):
                    oracle.poisson_solve_walls(f, lx, ly, dz, d["bc"], d["ybc"]))
             p = plan.poisson_solve(dev(f)).cpu().numpy()
             assert rel(p, ref) < tol, (case, d, rel(p, ref))
+            if case % 4 == 0:  # the host-buffer entry point: the same bits
+                ph = np.empty_like(f)
+                plan.poisson_solve_host(np.ascontiguousarray(f), ph)
+                assert np.array_equal(ph, p), case
             rhs = synth.normal(2000 + case, (nz, ny, nx))
             uref = oracle.helmholtz_solve(rhs, dz, d["c"], d["loc"])
             u = plan.helmholtz_solve(d["c"], dev(rhs), d["loc"]).cpu().numpy()
@@ -112,10 +118,11 @@ def test_random_plans_match_the_oracle(chanfs):
 
 
 def test_random_groups_give_the_bits_of_solves_alone(chanfs):
-    """Groups of 2 to 5 random refined plans (sizes, walls, kernel options
-    drawn as above): every box's grouped Poisson and Helmholtz results equal
-    its results alone, bit for bit, through direct launches, a graph capture
-    and a replay."""
+    """Groups of 2 to 5 random refined plans (sizes, walls, kernel options,
+    Helmholtz by FP64 Algorithm 2 or Thomas, refined in one pass or by the
+    loop with FP32 Algorithm 2 or Thomas inner solves): every box's grouped
+    Poisson and Helmholtz results equal its results alone, bit for bit,
+    through direct launches, a graph capture and a replay."""
     rng = np.random.default_rng(602)
     groups = 0
     for g in range(12):
@@ -135,7 +142,10 @@ def test_random_groups_give_the_bits_of_solves_alone(chanfs):
                     continue
                 plans.append(pl)
                 for opt, key in ((chanfs.OPT_THOMAS_TILE, "thomas"),
-                                 (chanfs.OPT_PCR_PARTS, "parts")):
+                                 (chanfs.OPT_PCR_PARTS, "parts"),
+                                 (chanfs.OPT_HELM_THOMAS, "helm_thomas"),
+                                 (chanfs.OPT_HELM_FP64, "helm_fp64"),
+                                 (chanfs.OPT_HELM_THOMAS32, "helm_thomas32")):
                     try:
                         pl.set_option(opt, d["opts"][key])
                     except chanfs.ChanfsError as e:
