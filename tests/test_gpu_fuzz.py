@@ -174,3 +174,59 @@ def test_random_groups_give_the_bits_of_solves_alone(chanfs):
             for pl in plans:
                 pl.close()
     assert groups >= 4, groups
+
+
+def test_random_slab_splits_match_the_oracle(chanfs):
+    """z-slab solves (P-TDMA) of random grids split over 1 to 4 slabs on one
+    GPU (the boundary buffers concatenated as the all-gather delivers them):
+    Poisson and Helmholtz against the oracle at 1e-12."""
+    rng = np.random.default_rng(2206)
+    ran = 0
+    for case in range(16):
+        m = int(rng.choice([k for k in SMOOTH if 2 <= k <= 32]))
+        nx, ny = 2 * m, int(rng.choice([k for k in SMOOTH if k <= 48]))
+        R = int(rng.integers(1, 5))
+        nz = int(rng.integers(6 * R, 90))
+        bc = int(rng.integers(2))
+        dz = synth.tanh_dz(nz, float(rng.uniform(1.0, 2.4)))
+        lx, ly = 2.0, 1.5
+        try:
+            ss = [chanfs.Slab(nx, ny, nz, lx, ly, dz, bc, R, r) for r in range(R)]
+        except chanfs.ChanfsError as e:
+            assert e.status == chanfs.EUNSUPPORTED, (nx, ny, nz, R, e)
+            continue
+        try:
+            f = synth.normal(5000 + case, (nz, ny, nx))
+            if bc == 0:
+                f = synth.remove_weighted_mean(f, dz)
+            ref = oracle.poisson_solve(f, lx, ly, dz, bc)
+            fl = [dev(f[s.z0:s.z1]) for s in ss]
+            work = [torch.empty_like(x) for x in fl]
+            bnd = [torch.empty(s.boundary_doubles(chanfs.REQ_POISSON), dtype=torch.float64,
+                               device="cuda") for s in ss]
+            for s, x, w, b in zip(ss, fl, work, bnd):
+                s.poisson_reduce(x, w, b)
+            outs = [torch.empty_like(x) for x in fl]
+            for s, w, o in zip(ss, work, outs):
+                s.poisson_finish(torch.cat(bnd), w, o)
+            p = np.concatenate([o.cpu().numpy() for o in outs])
+            assert rel(p, ref) < 1e-12, (case, nx, ny, nz, R, bc, rel(p, ref))
+            c, loc = float(10.0 ** rng.uniform(-6, -2)), int(rng.integers(2))
+            rhs = synth.normal(6000 + case, (nz, ny, nx))
+            uref = oracle.helmholtz_solve(rhs, dz, c, loc)
+            rl = [dev(rhs[s.z0:s.z1]) for s in ss]
+            work = [torch.empty_like(x) for x in rl]
+            bnd = [torch.empty(s.boundary_doubles(chanfs.REQ_HELMHOLTZ), dtype=torch.float64,
+                               device="cuda") for s in ss]
+            for s, x, w, b in zip(ss, rl, work, bnd):
+                s.helmholtz_reduce(c, loc, x, w, b)
+            outs = [torch.empty_like(x) for x in rl]
+            for s, w, o in zip(ss, work, outs):
+                s.helmholtz_finish(c, loc, torch.cat(bnd), w, o)
+            u = np.concatenate([o.cpu().numpy() for o in outs])
+            assert rel(u, uref) < 1e-12, (case, nx, ny, nz, R, loc, rel(u, uref))
+            ran += 1
+        finally:
+            for s in ss:
+                s.close()
+    assert ran >= 12, ran
