@@ -5,9 +5,10 @@ the transforms require; 3..80 cells in z, uniform or tanh-stretched), the
 wall conditions (z: Neumann or Dirichlet; y: periodic, Neumann or Dirichlet
 walls), the precision (FP64, or FP32 solves with FP64 refinement) and kernel
 shapes (z-solve kernel, Algorithm 2 partitions, Thomas or Algorithm 2 for
-Helmholtz), then checks a Poisson and a Helmholtz solve element by element
-against the oracle: relative max-norm 1e-12 for FP64 plans, 1e-10 for
-refined ones.  Shapes the library declines (CFS_EUNSUPPORTED) are skipped
+Helmholtz), then checks a Poisson and a Helmholtz solve (and for some a
+fully implicit Helmholtz solve) element by element against the oracle:
+relative max-norm 1e-12 for FP64 plans, 1e-10 for refined ones; the
+host-buffer and stage-by-stage entry points must give the solve's bits.  Shapes the library declines (CFS_EUNSUPPORTED) are skipped
 and counted; most must be accepted.
 """
 
@@ -107,6 +108,18 @@ def test_random_plans_match_the_oracle(chanfs):
                 ph = np.empty_like(f)
                 plan.poisson_solve_host(np.ascontiguousarray(f), ph)
                 assert np.array_equal(ph, p), case
+            if not d["refined"]:  # stage by stage: the same bits as the solve
+                x = dev(f)
+                t = torch.empty_like(x)
+                plan.poisson_stage(chanfs.X_FORWARD, x, out=t)
+                for st in (chanfs.Y_FORWARD, chanfs.Z_SOLVE, chanfs.Y_INVERSE, chanfs.X_INVERSE):
+                    plan.poisson_stage(st, t, out=t)
+                assert np.array_equal(t.cpu().numpy(), p), case
+            if d["ybc"] == 0 and case % 3 == 0:  # the fully implicit Helmholtz solve (Eq. 8)
+                r3 = synth.normal(3000 + case, (nz, ny, nx))
+                u3ref = oracle.helmholtz3d_solve(r3, lx, ly, dz, d["c"], d["loc"])
+                u3 = plan.helmholtz3d_solve(d["c"], dev(r3), d["loc"]).cpu().numpy()
+                assert rel(u3, u3ref) < tol, (case, d, rel(u3, u3ref))
             rhs = synth.normal(2000 + case, (nz, ny, nx))
             uref = oracle.helmholtz_solve(rhs, dz, d["c"], d["loc"])
             u = plan.helmholtz_solve(d["c"], dev(rhs), d["loc"]).cpu().numpy()
