@@ -55,6 +55,20 @@ __host__ __device__ inline void helm_row(int k, int nz, const double* dzf, int l
   *hi = -c * h;
 }
 
+// The rows of a partition starting at row o, from arrays of the operator's
+// (sub, diag, super) coefficients: a row function for alg2_factor_partition.
+struct ArrayRows {
+  const double* lo;
+  const double* diag;
+  const double* hi;
+  int o;
+  __host__ __device__ void operator()(int i, double* l, double* d, double* h) const {
+    *l = lo[o + i];
+    *d = diag[o + i];
+    *h = hi[o + i];
+  }
+};
+
 // Partition q of p over n rows: [start(q), start(q + 1)).
 __host__ __device__ inline int alg2_part_start(int q, int n, int p) {
   return (int)(((long long)q * n) / p);

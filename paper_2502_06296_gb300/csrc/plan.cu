@@ -625,11 +625,7 @@ static int helm_prepare(cfs_plan* P, double c, int loc, int nparts, HelmCoef** r
   for (int q = 0; q < np; ++q) {
     const int o = h.start[q], m = h.start[q + 1] - o;
     // Step 1 of Algorithm 2, and the partition's two rows of the reduced system
-    auto row = [&](int i, double* lo, double* diag, double* hi) {
-      *lo = A[o + i];
-      *diag = B[o + i];
-      *hi = C[o + i];
-    };
+    const ArrayRows row{A.data(), B.data(), C.data(), o};
     double first[3], last[3];
     alg2_factor_partition(m, row, alpha + o, beta + o, ib + o, ap + o, cpv + o, first, last);
     ra[2 * q] = first[0];

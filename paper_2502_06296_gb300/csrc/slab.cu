@@ -98,11 +98,7 @@ void slab_factors(int n, const double* L, const double* D, const double* U, cons
     const int o = start[q], m = start[q + 1] - o;
     tmp.assign(5 * (size_t)m, 0.0);
     double* dst = (q == own) ? own_rows : tmp.data();
-    auto row = [&](int i, double* lo, double* diag, double* hi) {
-      *lo = L[o + i];
-      *diag = D[o + i];
-      *hi = U[o + i];
-    };
+    const ArrayRows row{L, D, U, o};
     double first[3], last[3];
     alg2_factor_partition(m, row, dst, dst + m, dst + 2 * m, dst + 3 * m, dst + 4 * m, first, last);
     ra[2 * q] = first[0];
