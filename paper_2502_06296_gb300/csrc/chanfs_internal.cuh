@@ -167,7 +167,8 @@ struct cfs_plan {
   float* d_r32b;     // the residual kept between iterations, high part (FP32 input of the
                      // next solve)
   float* d_rlo;      // its low part: the double-float residual is (d_r32b, d_rlo)
-  float* d_w2;       // the first correction, kept until the second pass writes p once
+  float* d_w2;       // single solves: the second FP32 solve's workspace (the first correction
+                     // stays in d_r32); grouped solves: a copy of the first correction
   float4* d_zk;      // per plane k, split hi + lo: (A_k, C_k), (B'_k, dz_k), (D_k, dz_k); then
                      // (1/dx^2, 1/dy^2).  D_k = A_k + B'_k + C_k + 2/dx^2 + 2/dy^2 (exact sum)
   double* d_mpart;   // per-block dz-weighted sums of a correction (residual grid blocks)

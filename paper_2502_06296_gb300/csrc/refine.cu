@@ -389,7 +389,7 @@ __device__ __forceinline__ void poisson_first_body(
       two_sum(sh, se, hi, lo);
       rhi[o + col] = hi;  // also the next FP32 right-hand side
       rlo[o + col] = lo;
-      dcopy[o + col] = dk;  // the correction, for the pass that writes p
+      if (dcopy) dcopy[o + col] = dk;  // the correction, for the pass that writes p
       vmax = fmaxf(vmax, fabsf(hi));
       if (mpart) df_acc<false>(macc, dw.z, dw.w, dk);
       dkm = dk;
@@ -868,33 +868,36 @@ int refine_poisson(cfs_plan* P, const double* f, double* p, cudaStream_t st) {
     return cuda_rc(cudaMemsetAsync(p, 0, sizeof(double) * (size_t)nxy * P->nz, st));
   }
   for (int it = 0; it < P->maxit; ++it) {
-    // delta = solve32(r) in r32 (the right-hand side of the later iterations
-    // comes from r32b); p (+)= delta fused into the last pass, which also
-    // leaves delta in r32 for the residual update
-    e = launch_rfft_x32(P, it >= 1 ? P->d_r32b : P->d_r32, P->d_r32, false, st);
-    if (e == cudaSuccess) e = launch_fft_y32(P, P->d_r32, false, st);
-    if (e == cudaSuccess) e = launch_thomas32(P, P->d_r32, st);
-    if (e == cudaSuccess) e = launch_fft_y32(P, P->d_r32, true, st);
-    // the first correction stays in FP32 (the first residual keeps a copy in
-    // w2); the second pass writes p = both once, later passes add to p
+    // delta = solve32(r) in the workspace W (the right-hand side of the later
+    // iterations comes from r32b); p (+)= delta fused into the last pass,
+    // which also leaves delta in W for the residual update.  The second
+    // solve works in w2, so that the first correction stays in r32 for the
+    // pass that writes p = both corrections once.
+    float* const W = (it == 1) ? P->d_w2 : P->d_r32;
+    e = launch_rfft_x32(P, it >= 1 ? P->d_r32b : P->d_r32, W, false, st);
+    if (e == cudaSuccess) e = launch_fft_y32(P, W, false, st);
+    if (e == cudaSuccess) e = launch_thomas32(P, W, st);
+    if (e == cudaSuccess) e = launch_fft_y32(P, W, true, st);
+    // the first correction stays in FP32; the second pass writes p = both
+    // once, later passes add to p
     const double* msum = P->has_null ? mean_num(P) : nullptr;
     if (e == cudaSuccess) {
-      if (it == 0) e = launch_rfft_x32(P, P->d_r32, P->d_r32, true, st);
-      else if (it == 1) e = launch_rfft_x32_sum(P, P->d_r32, p, P->d_w2, st, msum);
-      else e = launch_rfft_x32_to64(P, P->d_r32, p, true, st, msum);
+      if (it == 0) e = launch_rfft_x32(P, W, W, true, st);
+      else if (it == 1) e = launch_rfft_x32_sum(P, W, p, P->d_r32, st, msum);
+      else e = launch_rfft_x32_to64(P, W, p, true, st, msum);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(P->d_red, 0, sizeof(unsigned int), st);
     // (Neumann: each kernel also sums its correction, dz-weighted, per block)
     double* mpart = P->has_null ? P->d_mpart : nullptr;
     if (e == cudaSuccess && it == 0) {  // r = (f - mean) - L delta, by differences
       auto k = idx32 ? poisson_first_kernel<int> : poisson_first_kernel<long long>;
-      k<<<grid, kResBlock, 0, st>>>(f, mean, P->d_r32, P->d_r32b, P->d_rlo, P->d_zk, max_word(P),
-                                    P->nx, P->ny, P->nz, P->ybc, mpart, P->d_w2);
+      k<<<grid, kResBlock, 0, st>>>(f, mean, W, P->d_r32b, P->d_rlo, P->d_zk, max_word(P),
+                                    P->nx, P->ny, P->nz, P->ybc, mpart, nullptr);
       e = cudaGetLastError();
     } else if (e == cudaSuccess) {  // r -= L delta
       auto k = idx32 ? poisson_update_kernel<int> : poisson_update_kernel<long long>;
-      k<<<grid, kResBlock, 0, st>>>(P->d_r32, P->d_r32b, P->d_rlo, P->d_zk, max_word(P), P->nx,
-                                    P->ny, P->nz, P->ybc, mpart);
+      k<<<grid, kResBlock, 0, st>>>(W, P->d_r32b, P->d_rlo, P->d_zk, max_word(P), P->nx, P->ny,
+                                    P->nz, P->ybc, mpart);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess && mpart) {  // the weighted sum of p, correction by correction
