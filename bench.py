@@ -912,6 +912,64 @@ def run_probe_only(args):
     return 0
 
 
+def run_f64_adds_sweep(args):
+    """The FP64 transforms of the channel Poisson solve with each level of
+    integer-unit butterfly additions (CFS_OPT_F64_ADDS_X / _Y): median
+    CUDA-event ms per stage over --steps solves (stage by stage, both options
+    at the level), the bits of each solve against level 0's, and the pair
+    rates of the FP64 pipe and of the integer-unit additions."""
+    import torch
+    torch.cuda.set_device(0)
+    device = torch.device("cuda", 0)
+    from paper_2502_06296_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2502_06296_gb300 import chanfs
+    cfg = dict(CFG)
+    if args.nz:
+        cfg.update(nz=args.nz)
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    f_h, _ = synth.channel_fields(cfg)
+    f = torch.from_numpy(f_h).to(device)
+    p = torch.empty_like(f)
+    stream = torch.cuda.current_stream(device)
+    out = {"workload": f"channel_{nx}x{ny}x{nz}_tanh1.8", "levels": {}}
+    order = (chanfs.X_FORWARD, chanfs.Y_FORWARD, chanfs.Z_SOLVE, chanfs.Y_INVERSE,
+             chanfs.X_INVERSE)
+    names = ("x_forward", "y_forward", "z_thomas", "y_inverse", "x_inverse")
+    with chanfs.Plan(nx, ny, nz, CFG["lx"], CFG["ly"], synth.grid_dz(cfg), chanfs.NEUMANN) as plan:
+        ref = None
+        for level in range(5):
+            plan.set_option(chanfs.OPT_F64_ADDS_X, level)
+            plan.set_option(chanfs.OPT_F64_ADDS_Y, level)
+            times = {n: [] for n in names}
+            for rep in range(args.warmup + args.steps):
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+                ev[0].record(stream)
+                src = f
+                for i, st in enumerate(order):
+                    plan.poisson_stage(st, src, out=p)
+                    src = p
+                    ev[i + 1].record(stream)
+                torch.cuda.synchronize()
+                if rep >= args.warmup:
+                    for i, n in enumerate(names):
+                        times[n].append(ev[i].elapsed_time(ev[i + 1]))
+            if ref is None:
+                ref = p.clone()
+            out["levels"][str(level)] = {
+                "stage_ms": {n: round(statistics.median(v), 4) for n, v in times.items()},
+                "stage_ms_min": {n: round(min(v), 4) for n, v in times.items()},
+                "bits_equal_level0": bool(torch.equal(p, ref))}
+        out["device_status"] = plan.check()
+    for emu in (False, True):
+        r = [chanfs.probe_addsub(emu, 1 << 14) for _ in range(3)]
+        out["pairs_per_s_" + ("integer" if emu else "fp64_pipe")] = statistics.median(
+            v for v, _ in r)
+    out["selfcheck_mismatches"] = chanfs.selfcheck_f64_addsub(1 << 24)
+    print(json.dumps({"f64_adds_sweep": out}), flush=True)
+    return 0
+
+
 def run_extras_only(args):
     import torch
     torch.cuda.set_device(0)
@@ -1223,6 +1281,9 @@ def main(argv=None):
                     help="with --helmholtz-only: one size NXxNYxNZ (stretching 1.8, c = 1e-5)")
     ap.add_argument("--probe-only", action="store_true",
                     help="measure only the FP64 and FP32 FMA rates (--steps repetitions)")
+    ap.add_argument("--f64-adds-sweep", action="store_true",
+                    help="time the FP64 transforms at each level of integer-unit butterfly "
+                         "additions (CFS_OPT_F64_ADDS_X / _Y) and check their bits")
     ap.add_argument("--slab", action="store_true",
                     help="N > 1: one z-slab of the channel per GPU, solved by P-TDMA with an "
                          "NCCL all-gather (the default runs independent replicas)")
@@ -1237,6 +1298,8 @@ def main(argv=None):
         return run_mixed_only(args)
     if args.probe_only:
         return run_probe_only(args)
+    if args.f64_adds_sweep:
+        return run_f64_adds_sweep(args)
     if args.helmholtz_only:
         return run_helmholtz_only(args)
     if args.zsolve_only:

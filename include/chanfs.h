@@ -513,6 +513,15 @@ int cfs_slab_helmholtz_finish(cfs_slab_t slab, double c, int loc, const double* 
  *       4 (radix-4 passes, then 2, 3s).  Setting it rebuilds the twiddle
  *       tables (it waits for the device); groups bound to the plan must be
  *       rebound.
+ *   CFS_OPT_F64_ADDS_X, CFS_OPT_F64_ADDS_Y  how many kinds of butterfly
+ *       additions of the FP64 x / y transforms run on the integer units
+ *       instead of the FP64 pipe, 0..4 (cumulative: 1 the second level of
+ *       every radix-4 core, 2 also the radix-2 combination of each DFT8,
+ *       3 also the first level of the untwiddled passes, 4 also the real-FFT
+ *       untangle of the x transform).  Those additions are exact IEEE-754
+ *       binary64 round-to-nearest-even additions done in integer
+ *       arithmetic, so every level gives the same bits; on GPUs whose FP64
+ *       pipe is narrow it lets the integer units share the FP64 work.
  * cfs_plan_set_option returns CFS_EINVAL for an unknown option or value, and
  * CFS_EUNSUPPORTED if the value cannot run at this plan's size (a tile that
  * does not fit in shared memory).  cfs_plan_get_option reports the value in
@@ -527,7 +536,9 @@ enum {
   CFS_OPT_HELM_FP64 = 5,
   CFS_OPT_HELM_THOMAS = 6,
   CFS_OPT_HELM_THOMAS32 = 7,
-  CFS_OPT_FFT_RADIX = 8
+  CFS_OPT_FFT_RADIX = 8,
+  CFS_OPT_F64_ADDS_X = 9,
+  CFS_OPT_F64_ADDS_Y = 10
 };
 int cfs_plan_set_option(cfs_plan_t plan, int option, int value);
 int cfs_plan_get_option(cfs_plan_t plan, int option, int* value);
@@ -572,6 +583,22 @@ int cfs_autotune_clear(void);
 int cfs_selfcheck_conversions(unsigned long long samples, unsigned long long* mismatches);
 
 /*
+ * cfs_selfcheck_f64_addsub -- a diagnostic with no counterpart in the paper.
+ * The FP64 x and y transforms may run part of their butterfly additions in
+ * integer arithmetic (CFS_OPT_F64_ADDS_X / _Y): an exact IEEE-754 binary64
+ * round-to-nearest-even a + b and a - b, with zeros, subnormals, operands
+ * below 2^-959 or from 2^1023 up, infinities and NaNs left to the FP64
+ * pipe.  This runs `samples` hashed operand pairs (any two bit patterns,
+ * close and distant exponents, cancellation, exact rounding ties, the ends
+ * of the integer range, equal magnitudes, FFT-sized values) through both on
+ * the GPU (on_device = 1) or on the host CPU (on_device = 0, no GPU needed)
+ * and reports in *mismatches how many of the 2 * samples results differ in
+ * any bit (0 expected; NaN results compare equal whatever their payload).
+ */
+int cfs_selfcheck_f64_addsub(unsigned long long samples, int on_device,
+                             unsigned long long* mismatches);
+
+/*
  * cfs_probe_fma -- a measurement with no counterpart in the paper: the FMA
  * rate of the current GPU in FP64 (bits = 64) or FP32 (bits = 32), the
  * roofline peak of kernels bound by those instructions.  Every thread of one
@@ -583,6 +610,17 @@ int cfs_selfcheck_conversions(unsigned long long samples, unsigned long long* mi
  * Waits for the device.
  */
 int cfs_probe_fma(int bits, long long iters, double* fma_per_s, double* ms);
+
+/*
+ * cfs_probe_addsub -- a measurement with no counterpart in the paper: the
+ * rate of FP64 butterfly pairs (a + b, a - b) on the FP64 pipe
+ * (on_integer_units = 0) or by the integer-unit additions of the transforms
+ * (1).  Every thread of one full wave of 256-thread blocks runs 8
+ * independent pair chains for `iters` steps (rounded up to a multiple of
+ * 256; 1 <= iters <= 2^40), timed as cfs_probe_fma.  *pairs_per_s receives
+ * pairs per second, *ms (may be NULL) the launch time.  Waits for the device.
+ */
+int cfs_probe_addsub(int on_integer_units, long long iters, double* pairs_per_s, double* ms);
 
 /*
  * cfs_selftest_wait_timeout -- a test of the failure path, with no

@@ -25,6 +25,7 @@ X_FORWARD, Y_FORWARD, Z_SOLVE, Y_INVERSE, X_INVERSE = 0, 1, 2, 3, 4
 
 OPT_THOMAS_TILE, OPT_X_LINES, OPT_Y_TILE, OPT_PCR_PARTS, OPT_HELM_FP64 = 1, 2, 3, 4, 5
 OPT_HELM_THOMAS, OPT_HELM_THOMAS32, OPT_FFT_RADIX = 6, 7, 8
+OPT_F64_ADDS_X, OPT_F64_ADDS_Y = 9, 10
 
 REQ_POISSON, REQ_HELMHOLTZ = 0, 1
 
@@ -113,6 +114,9 @@ def lib():
             "cfs_helmholtz3d_solve": ([vp, d, i, vp, vp, vp], i),
             "cfs_plan_set_option": ([vp, i, i], i),
             "cfs_selfcheck_conversions": ([ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_ulonglong)], i),
+            "cfs_selfcheck_f64_addsub": ([ctypes.c_ulonglong, i,
+                                          ctypes.POINTER(ctypes.c_ulonglong)], i),
+            "cfs_probe_addsub": ([i, ctypes.c_longlong, dp, dp], i),
             "cfs_group_reserve": ([ctypes.POINTER(vp), i], i),
             "cfs_group_rebind": ([vp, i, ctypes.POINTER(vp), vp], i),
             "cfs_server_create": ([ctypes.POINTER(vp), ctypes.c_size_t, i, i, i, i], i),
@@ -306,7 +310,8 @@ class Plan:
                 (("x_lines", OPT_X_LINES), ("y_tile", OPT_Y_TILE),
                  ("thomas_tile", OPT_THOMAS_TILE), ("pcr_parts", OPT_PCR_PARTS),
                  ("helm_fp64", OPT_HELM_FP64), ("helm_thomas", OPT_HELM_THOMAS),
-                 ("helm_thomas32", OPT_HELM_THOMAS32), ("fft_radix", OPT_FFT_RADIX))}
+                 ("helm_thomas32", OPT_HELM_THOMAS32), ("fft_radix", OPT_FFT_RADIX),
+                 ("f64_adds_x", OPT_F64_ADDS_X), ("f64_adds_y", OPT_F64_ADDS_Y))}
 
     def get_option(self, option: int) -> int:
         """The kernel shape in effect, automatic choices resolved."""
@@ -674,6 +679,26 @@ def selfcheck_conversions(samples: int = 1 << 22) -> int:
     _check(lib().cfs_selfcheck_conversions(int(samples), ctypes.byref(bad)),
            "cfs_selfcheck_conversions")
     return bad.value
+
+
+def selfcheck_f64_addsub(samples: int = 1 << 22, on_device: bool = True) -> int:
+    """Bit mismatches of the library's integer-unit FP64 additions and
+    subtractions against the FP64 hardware's over `samples` hashed operand
+    pairs, on the GPU or, with on_device=False, on the host CPU
+    (cfs_selfcheck_f64_addsub)."""
+    bad = ctypes.c_ulonglong(0)
+    _check(lib().cfs_selfcheck_f64_addsub(int(samples), 1 if on_device else 0, ctypes.byref(bad)),
+           "cfs_selfcheck_f64_addsub")
+    return bad.value
+
+
+def probe_addsub(on_integer_units: bool, iters: int = 1 << 14):
+    """(butterfly pairs per second, launch ms) of (a + b, a - b) in FP64 on the
+    FP64 pipe or on the integer units (cfs_probe_addsub)."""
+    rate, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib().cfs_probe_addsub(1 if on_integer_units else 0, int(iters), ctypes.byref(rate),
+                                  ctypes.byref(ms)), "cfs_probe_addsub")
+    return rate.value, ms.value
 
 
 def _host_ptr(a, shape):

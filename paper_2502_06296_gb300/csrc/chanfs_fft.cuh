@@ -3,6 +3,7 @@
 // (the FP64 path) and float2 (the FP32 inner solves of iterative refinement).
 #pragma once
 
+#include "chanfs_f64emu.cuh"
 #include "chanfs_internal.cuh"
 
 namespace chanfs {
@@ -28,6 +29,25 @@ template <class C> __device__ __forceinline__ C cmul(C a, C w) {
 template <class C> __device__ __forceinline__ C cmulc(C a, C w) {
   return mkc<C>(fma(a.x, w.x, a.y * w.y), fma(a.y, w.x, -a.x * w.y));
 }
+// Which butterfly additions of the FP64 transforms run on the integer units
+// (f64_addsub, bit for bit the FP64 pipe's results), as a mask of template
+// parameter EMU; FP32 transforms ignore it.
+constexpr int kEmuCore = 1;   // the second level of every radix-4 core (t0 +- t2, t1 +- t3)
+constexpr int kEmuComb = 2;   // the radix-2 combination of a DFT8 (E0 +- O0, E2 +- i O2)
+constexpr int kEmuFirst = 4;  // the first level of untwiddled DFT8/4/2 and DFT3's b +- c
+constexpr int kEmuPost = 8;   // the real-FFT untangle of the x transform
+
+// (a + b, a - b); EMU: the FP64 additions by f64_addsub.
+template <bool EMU, class C> __device__ __forceinline__ void cpair(C a, C b, C& p, C& m) {
+  if constexpr (EMU && sizeof(C) == sizeof(double2)) {
+    f64_addsub(a.x, b.x, p.x, m.x);
+    f64_addsub(a.y, b.y, p.y, m.y);
+  } else {
+    p = cadd(a, b);
+    m = csub(a, b);
+  }
+}
+
 // Multiply by -i (forward) or +i (inverse): a swap and a sign, no arithmetic.
 template <bool INV, class C> __device__ __forceinline__ C mul_mi(C a) {
   return INV ? mkc<C>(-a.y, a.x) : mkc<C>(a.y, -a.x);
@@ -54,10 +74,8 @@ template <class C> __device__ __forceinline__ C ctwice_minus(C a, C s) {
 // (r >= 1) and fold each twiddle product into the first butterfly level:
 //   (a + w x, a - w x) = (s, 2a - s) with s = a + w x by four FMAs,
 // 6 instructions per pair instead of 8.
-template <bool INV, class C> __device__ __forceinline__ void dft2(C& a, C& b) {
-  C t = a;
-  a = cadd(t, b);
-  b = csub(t, b);
+template <bool INV, class C, int EMU = 0> __device__ __forceinline__ void dft2(C& a, C& b) {
+  cpair<(EMU & kEmuFirst) != 0>(C(a), C(b), a, b);
 }
 
 template <bool INV, class C> __device__ __forceinline__ void dft2_tw(C* v, const C* w) {
@@ -78,8 +96,10 @@ __device__ __forceinline__ void dft3_core(C& a, C& b, C& c, C s, C d) {
   c = mkc<C>(fma(-sx, d.y, t.x), fma(sx, d.x, t.y));
 }
 
-template <bool INV, class C> __device__ __forceinline__ void dft3(C& a, C& b, C& c) {
-  dft3_core<INV>(a, b, c, cadd(b, c), csub(b, c));
+template <bool INV, class C, int EMU = 0> __device__ __forceinline__ void dft3(C& a, C& b, C& c) {
+  C s, d;
+  cpair<(EMU & kEmuFirst) != 0>(b, c, s, d);
+  dft3_core<INV>(a, b, c, s, d);
 }
 
 template <bool INV, class C> __device__ __forceinline__ void dft3_tw(C* v, const C* w) {
@@ -91,48 +111,47 @@ template <bool INV, class C> __device__ __forceinline__ void dft3_tw(C* v, const
 
 // Radix-4 second level from t0 = a0 + a2, t1 = a0 - a2, t2 = a1 + a3,
 // d = a1 - a3.
-template <bool INV, class C>
+template <bool INV, class C, int EMU = 0>
 __device__ __forceinline__ void dft4_core(C* y, C t0, C t1, C t2, C d) {
   C t3 = mul_mi<INV>(d);
-  y[0] = cadd(t0, t2);
-  y[2] = csub(t0, t2);
-  y[1] = cadd(t1, t3);
-  y[3] = csub(t1, t3);
+  cpair<(EMU & kEmuCore) != 0>(t0, t2, y[0], y[2]);
+  cpair<(EMU & kEmuCore) != 0>(t1, t3, y[1], y[3]);
 }
 
-template <bool INV, class C> __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
-  C y[4];
-  dft4_core<INV>(y, cadd(a0, a2), csub(a0, a2), cadd(a1, a3), csub(a1, a3));
+template <bool INV, class C, int EMU = 0>
+__device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
+  C y[4], t0, t1, t2, d;
+  cpair<(EMU & kEmuFirst) != 0>(a0, a2, t0, t1);
+  cpair<(EMU & kEmuFirst) != 0>(a1, a3, t2, d);
+  dft4_core<INV, C, EMU>(y, t0, t1, t2, d);
   a0 = y[0]; a1 = y[1]; a2 = y[2]; a3 = y[3];
 }
 
 // DFT4 of (x0, w1 x1, w2 x2, w3 x3) given x0..x3 and w1..w3 (x0 untwiddled).
-template <bool INV, class C>
+template <bool INV, class C, int EMU = 0>
 __device__ __forceinline__ void dft4_tw4(C* y, C x0, C x1, C x2, C x3, C w1, C w2, C w3) {
   C t0 = cfma<INV>(w2, x2, x0);
   C t1 = ctwice_minus(x0, t0);
   C u = ctw<INV>(x1, w1);
   C t2 = cfma<INV>(w3, x3, u);
-  dft4_core<INV>(y, t0, t1, t2, ctwice_minus(u, t2));
+  dft4_core<INV, C, EMU>(y, t0, t1, t2, ctwice_minus(u, t2));
 }
 
-template <bool INV, class C> __device__ __forceinline__ void dft4_tw(C* v, const C* w) {
+template <bool INV, class C, int EMU = 0> __device__ __forceinline__ void dft4_tw(C* v, const C* w) {
   C y[4];
-  dft4_tw4<INV>(y, v[0], v[1], v[2], v[3], w[0], w[1], w[2]);
+  dft4_tw4<INV, C, EMU>(y, v[0], v[1], v[2], v[3], w[0], w[1], w[2]);
   v[0] = y[0]; v[1] = y[1]; v[2] = y[2]; v[3] = y[3];
 }
 
 // Radix-2 combination of the even (E) and odd (O) half-DFTs of a DFT8, with
 // the W8 factors folded into fused multiply-adds.
-template <bool INV, class C>
+template <bool INV, class C, int EMU = 0>
 __device__ __forceinline__ void dft8_combine(C* v, const C* E, const C* O) {
   using T = typename cscal<C>::T;
   const T r = T(0.7071067811865475244008443621048490);  // 1/sqrt(2)
-  v[0] = cadd(E[0], O[0]);
-  v[4] = csub(E[0], O[0]);
+  cpair<(EMU & kEmuComb) != 0>(E[0], O[0], v[0], v[4]);
   C m2 = mul_mi<INV>(O[2]);
-  v[2] = cadd(E[2], m2);
-  v[6] = csub(E[2], m2);
+  cpair<(EMU & kEmuComb) != 0>(E[2], m2, v[2], v[6]);
   if (!INV) {
     // W8 O = r (O.x + O.y, O.y - O.x);  W8^3 O = r (O.y - O.x, -(O.x + O.y))
     T p1 = O[1].x + O[1].y, q1 = O[1].y - O[1].x;
@@ -152,46 +171,52 @@ __device__ __forceinline__ void dft8_combine(C* v, const C* E, const C* O) {
   }
 }
 
-template <bool INV, class C> __device__ __forceinline__ void dft8(C* v) {
-  C E[4], O[4];
-  dft4_core<INV>(E, cadd(v[0], v[4]), csub(v[0], v[4]), cadd(v[2], v[6]), csub(v[2], v[6]));
-  dft4_core<INV>(O, cadd(v[1], v[5]), csub(v[1], v[5]), cadd(v[3], v[7]), csub(v[3], v[7]));
-  dft8_combine<INV>(v, E, O);
+template <bool INV, class C, int EMU = 0> __device__ __forceinline__ void dft8(C* v) {
+  constexpr bool F = (EMU & kEmuFirst) != 0;
+  C E[4], O[4], p[8];
+  cpair<F>(v[0], v[4], p[0], p[1]);
+  cpair<F>(v[2], v[6], p[2], p[3]);
+  cpair<F>(v[1], v[5], p[4], p[5]);
+  cpair<F>(v[3], v[7], p[6], p[7]);
+  dft4_core<INV, C, EMU>(E, p[0], p[1], p[2], p[3]);
+  dft4_core<INV, C, EMU>(O, p[4], p[5], p[6], p[7]);
+  dft8_combine<INV, C, EMU>(v, E, O);
 }
 
-template <bool INV, class C> __device__ __forceinline__ void dft8_tw(C* v, const C* w) {
+template <bool INV, class C, int EMU = 0> __device__ __forceinline__ void dft8_tw(C* v, const C* w) {
   C E[4], O[4];
   // even half: (v0, w2 v2, w4 v4, w6 v6)
-  dft4_tw4<INV>(E, v[0], v[2], v[4], v[6], w[1], w[3], w[5]);
+  dft4_tw4<INV, C, EMU>(E, v[0], v[2], v[4], v[6], w[1], w[3], w[5]);
   // odd half: all four twiddled
   C a = ctw<INV>(v[1], w[0]);
   C t0 = cfma<INV>(w[4], v[5], a);
   C t1 = ctwice_minus(a, t0);
   C b = ctw<INV>(v[3], w[2]);
   C t2 = cfma<INV>(w[6], v[7], b);
-  dft4_core<INV>(O, t0, t1, t2, ctwice_minus(b, t2));
-  dft8_combine<INV>(v, E, O);
+  dft4_core<INV, C, EMU>(O, t0, t1, t2, ctwice_minus(b, t2));
+  dft8_combine<INV, C, EMU>(v, E, O);
 }
 
-template <int R, bool INV, class C> __device__ __forceinline__ void dft(C* v) {
-  if constexpr (R == 2) dft2<INV>(v[0], v[1]);
-  else if constexpr (R == 3) dft3<INV>(v[0], v[1], v[2]);
-  else if constexpr (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
-  else if constexpr (R == 8) dft8<INV>(v);
+template <int R, bool INV, class C, int EMU = 0> __device__ __forceinline__ void dft(C* v) {
+  if constexpr (R == 2) dft2<INV, C, EMU>(v[0], v[1]);
+  else if constexpr (R == 3) dft3<INV, C, EMU>(v[0], v[1], v[2]);
+  else if constexpr (R == 4) dft4<INV, C, EMU>(v[0], v[1], v[2], v[3]);
+  else if constexpr (R == 8) dft8<INV, C, EMU>(v);
 }
 
-template <int R, bool INV, class C> __device__ __forceinline__ void dft_tw(C* v, const C* w) {
+template <int R, bool INV, class C, int EMU = 0>
+__device__ __forceinline__ void dft_tw(C* v, const C* w) {
   if constexpr (R == 2) dft2_tw<INV>(v, w);
   else if constexpr (R == 3) dft3_tw<INV>(v, w);
-  else if constexpr (R == 4) dft4_tw<INV>(v, w);
-  else if constexpr (R == 8) dft8_tw<INV>(v, w);
+  else if constexpr (R == 4) dft4_tw<INV, C, EMU>(v, w);
+  else if constexpr (R == 8) dft8_tw<INV, C, EMU>(v, w);
 }
 
 // One Stockham radix-R butterfly: reads R points j + r*n/R of one batch from
 // `in`, applies the twiddles of pass (L, R), transforms, and writes them to
 // positions (j - k)*R + k + r*L of `out` (k = j mod L, by a mask when L is a
 // power of two: lmask = L - 1, else -1).  es = element stride.
-template <int R, bool INV, class C>
+template <int R, bool INV, class C, int EMU = 0>
 __device__ __forceinline__ void stockham_bfly(const C* __restrict__ in, C* __restrict__ out, int j,
                                               int L, int lmask, int n, int es,
                                               const C* __restrict__ tw) {
@@ -204,9 +229,9 @@ __device__ __forceinline__ void stockham_bfly(const C* __restrict__ in, C* __res
     C w[R - 1];
 #pragma unroll
     for (int r = 0; r < R - 1; ++r) w[r] = tw[k * (R - 1) + r];
-    dft_tw<R, INV>(v, w);
+    dft_tw<R, INV, C, EMU>(v, w);
   } else {
-    dft<R, INV>(v);
+    dft<R, INV, C, EMU>(v);
   }
   const int o = (j - k) * R + k;
 #pragma unroll
@@ -217,7 +242,7 @@ __device__ __forceinline__ void stockham_bfly(const C* __restrict__ in, C* __res
 // batch b lives at buf[b*bs + e*es].  Ping-pongs between a and b; returns the
 // buffer holding the result.  BATCH_FAST: consecutive threads take consecutive
 // batches (columns of a y tile) instead of consecutive butterflies.
-template <bool INV, bool BATCH_FAST, class C>
+template <bool INV, bool BATCH_FAST, class C, int EMU = 0>
 __device__ C* stockham_smem(C* a, C* b, const FftDesc& d, int nb, int es, int bs,
                             const C* __restrict__ tw) {
   const int n = d.n;
@@ -245,10 +270,10 @@ __device__ C* stockham_smem(C* a, C* b, const FftDesc& d, int nb, int es, int bs
       const C* in = a + bat * bs;
       C* out = b + bat * bs;
       switch (R) {
-        case 8: stockham_bfly<8, INV>(in, out, j, L, lmask, n, es, twp); break;
-        case 4: stockham_bfly<4, INV>(in, out, j, L, lmask, n, es, twp); break;
-        case 3: stockham_bfly<3, INV>(in, out, j, L, lmask, n, es, twp); break;
-        default: stockham_bfly<2, INV>(in, out, j, L, lmask, n, es, twp); break;
+        case 8: stockham_bfly<8, INV, C, EMU>(in, out, j, L, lmask, n, es, twp); break;
+        case 4: stockham_bfly<4, INV, C, EMU>(in, out, j, L, lmask, n, es, twp); break;
+        case 3: stockham_bfly<3, INV, C, EMU>(in, out, j, L, lmask, n, es, twp); break;
+        default: stockham_bfly<2, INV, C, EMU>(in, out, j, L, lmask, n, es, twp); break;
       }
     }
     __syncthreads();
@@ -334,7 +359,7 @@ __host__ __device__ inline int xbuf_elems(int lines, int m, bool fp32) {
 // output, fixed_padded(N) between passes): the same butterflies and twiddles
 // as stockham_smem with every radix, span, stride and offset a constant.
 // Returns the buffer holding the result.
-template <bool INV, int N, int P, class C>
+template <bool INV, int N, int P, class C, int EMU = 0>
 __device__ __forceinline__ C* stockham_fixed(C* a, C* b, int nb, const C* __restrict__ tw) {
   if constexpr (fixed_radix(N, P) == 0) {
     return a;
@@ -357,16 +382,16 @@ __device__ __forceinline__ C* stockham_fixed(C* a, C* b, int nb, const C* __rest
         C w[R - 1];
 #pragma unroll
         for (int r = 0; r < R - 1; ++r) w[r] = tw[TO + k * (R - 1) + r];
-        dft_tw<R, INV>(v, w);
+        dft_tw<R, INV, C, EMU>(v, w);
       } else {
-        dft<R, INV>(v);
+        dft<R, INV, C, EMU>(v);
       }
       const int o = (j - k) * R + k;
 #pragma unroll
       for (int r = 0; r < R; ++r) out[POUT ? pad16(o + r * L) : o + r * L] = v[r];
     }
     __syncthreads();
-    return stockham_fixed<INV, N, P + 1>(b, a, nb, tw);
+    return stockham_fixed<INV, N, P + 1, C, EMU>(b, a, nb, tw);
   }
 }
 
@@ -427,7 +452,7 @@ __host__ __device__ inline bool tile_fixed_len(const FftDesc& d) {
 }
 
 // All passes of a y tile (FP32: the compile-time path for common lengths).
-template <bool INV, class C>
+template <bool INV, class C, int EMU = 0>
 __device__ __forceinline__ C* stockham_tile(C* a, C* b, const FftDesc& d, int tk,
                                             const C* __restrict__ tw) {
   if constexpr (sizeof(C) == sizeof(float2)) {
@@ -460,7 +485,7 @@ __device__ __forceinline__ C* stockham_tile(C* a, C* b, const FftDesc& d, int tk
         break;
     }
   }
-  return stockham_smem<INV, true>(a, b, d, tk, tk, 1, tw);
+  return stockham_smem<INV, true, C, EMU>(a, b, d, tk, tk, 1, tw);
 }
 
 // All passes over `nb` contiguous batches of length d.n (the x transform's
@@ -468,7 +493,7 @@ __device__ __forceinline__ C* stockham_tile(C* a, C* b, const FftDesc& d, int tk
 // common lengths take a compile-time path (about a third fewer instructions
 // at n = 512); FP64 transforms are bound by the FP64 pipe and keep the
 // general one.
-template <bool INV, class C>
+template <bool INV, class C, int EMU = 0>
 __device__ __forceinline__ C* stockham_lines(C* a, C* b, const FftDesc& d, int nb,
                                              const C* __restrict__ tw) {
   if constexpr (sizeof(C) == sizeof(float2)) {
@@ -507,7 +532,7 @@ __device__ __forceinline__ C* stockham_lines(C* a, C* b, const FftDesc& d, int n
         break;
     }
   }
-  return stockham_smem<INV, false>(a, b, d, nb, 1, d.n, tw);
+  return stockham_smem<INV, false, C, EMU>(a, b, d, nb, 1, d.n, tw);
 }
 
 }  // namespace chanfs

@@ -35,6 +35,10 @@ constexpr int kPcrMaxUnknowns = 1024;  // rows of a PCR tile in shared memory
 
 constexpr int kMaxGroup = 4096;     // plans of one grouped solve
 constexpr int kBatchSlots = 4;      // device slots of a batch of host-buffer solves
+// Default levels of CFS_OPT_F64_ADDS_X / _Y (FP64 butterfly additions on the
+// integer units).
+constexpr int kEmuDefaultX = 0;
+constexpr int kEmuDefaultY = 0;
 
 // Device status bits (plan->d_status)
 constexpr int kErrTmaTimeout = 1;
@@ -146,6 +150,8 @@ struct cfs_plan {
   int helm_thomas;   // FP64 Helmholtz solves by Thomas sweeps instead of Algorithm 2
   int helm_thomas32; // FP32 inner Helmholtz solves of refinement by Thomas sweeps
   int fft_radix;     // largest radix of the x and y FFT passes (8 or 4)
+  int emu_x, emu_y;  // FP64 x / y transforms: levels 0..4 of butterfly additions
+                     // on the integer units (CFS_OPT_F64_ADDS_X / _Y)
   double* d_dzf;     // cell widths (weights of the Neumann mean)
   // Neumann (0,0) column: wn = w/sum(w), gn = g/sum(w) with g = T'^{-T} w,
   // hs = sc * T'^{-1} (0,1,..,1), T' the pinned operator; 3*nz doubles

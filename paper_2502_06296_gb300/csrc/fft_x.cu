@@ -10,6 +10,9 @@
 // The inverse runs the same steps backwards.  Consecutive lines (y, z) are
 // contiguous, so a CTA's block of `lb` lines is one contiguous span.
 // in and out may alias (the inverse runs in place): no __restrict__ on them.
+// EMU (FP64 only) chooses the butterfly additions that run on the integer
+// units instead of the FP64 pipe (kEmu* in chanfs_fft.cuh): the results are
+// the same bits, the FP64 pipe that bounds these kernels does less.
 //
 // C = double2 is the FP64 solve.  C = float2 is the inner solve of iterative
 // refinement; its inverse can write the FP64 result directly (OUT_SET) or add
@@ -26,7 +29,7 @@ namespace chanfs {
 // memory and another writes the result back, so the global traffic is two
 // large asynchronous transfers per block and no thread computes an address
 // per element.
-template <bool INV, class C, int OUT>
+template <bool INV, class C, int OUT, int EMU = 0>
 __device__ __forceinline__ void rfft_x_body(const C* in, void* outv, long long nlines,
                                             const FftDesc& d, const C* __restrict__ twg,
                                             const C* __restrict__ postg, int lb, double scale,
@@ -69,7 +72,7 @@ __device__ __forceinline__ void rfft_x_body(const C* in, void* outv, long long n
   const int sk = blockDim.x % npost, sl = blockDim.x / npost;
 
   if (!INV) {
-    C* Z = stockham_lines<false>(buf0, buf1, d, lb, tw);
+    C* Z = stockham_lines<false, C, EMU>(buf0, buf1, d, lb, tw);
     C* ob = (Z == buf0) ? buf1 : buf0;
     // untangle the half-length spectrum into the packed real spectrum
     int l = threadIdx.x / npost, k = threadIdx.x % npost;
@@ -81,8 +84,10 @@ __device__ __forceinline__ void rfft_x_body(const C* in, void* outv, long long n
         o[0] = mkc<C>(z0.x + z0.y, z0.x - z0.y);  // (X_0, X_M)
       } else {
         const C zk = z[k], zm = z[M - k];
-        const C E = mkc<C>(zk.x + zm.x, zk.y - zm.y);
-        const C O = mkc<C>(zk.x - zm.x, zk.y + zm.y);
+        C p, m;
+        cpair<(EMU & kEmuPost) != 0>(zk, zm, p, m);
+        const C E = mkc<C>(p.x, m.y);  // (zk.x + zm.x, zk.y - zm.y)
+        const C O = mkc<C>(m.x, p.y);  // (zk.x - zm.x, zk.y + zm.y)
         const C u = cmul(O, post[k]);  // (W^k/2) O
         const C t = mkc<C>(u.y, -u.x);  // -i (W^k/2) O
         o[k] = mkc<C>(fma(h, E.x, t.x), fma(h, E.y, t.y));
@@ -116,8 +121,10 @@ __device__ __forceinline__ void rfft_x_body(const C* in, void* outv, long long n
       } else {
         const C* x = buf1 + l * bs;
         const C xk = x[k], xm = x[M - k];
-        const C E = mkc<C>(xk.x + xm.x, xk.y - xm.y);
-        const C Tt = mkc<C>(xk.x - xm.x, xk.y + xm.y);
+        C p, m;
+        cpair<(EMU & kEmuPost) != 0>(xk, xm, p, m);
+        const C E = mkc<C>(p.x, m.y);   // (xk.x + xm.x, xk.y - xm.y)
+        const C Tt = mkc<C>(m.x, p.y);  // (xk.x - xm.x, xk.y + xm.y)
         const C u = cmulc(Tt, post[k]);  // conj(W^k/2) T
         zk = mkc<C>(fma(h, E.x, -u.y), fma(h, E.y, u.x));
         zm = mkc<C>(fma(h, E.x, u.y), fma(-h, E.y, u.x));
@@ -139,7 +146,7 @@ __device__ __forceinline__ void rfft_x_body(const C* in, void* outv, long long n
       }
     }
     __syncthreads();
-    C* res = stockham_lines<true>(buf0, buf1, d, lb, tw);
+    C* res = stockham_lines<true, C, EMU>(buf0, buf1, d, lb, tw);
     if (OUT == OUT_SAME) {
       fence_proxy_async();
       __syncthreads();
@@ -187,15 +194,15 @@ __device__ __forceinline__ void rfft_x_body(const C* in, void* outv, long long n
   }
 }
 
-template <bool INV, class C, int OUT>
+template <bool INV, class C, int OUT, int EMU = 0>
 __global__ void __launch_bounds__(128) rfft_x_kernel(const C* in, void* outv, long long nlines,
                                                      FftDesc d, const C* __restrict__ twg,
                                                      const C* __restrict__ postg, int lb,
                                                      double scale, int scaled, int* status,
                                                      const double* msum, double minv,
                                                      const C* add_src) {
-  rfft_x_body<INV, C, OUT>(in, outv, nlines, d, twg, postg, lb, scale, scaled, status,
-                           blockIdx.x, msum, minv, add_src);
+  rfft_x_body<INV, C, OUT, EMU>(in, outv, nlines, d, twg, postg, lb, scale, scaled, status,
+                                blockIdx.x, msum, minv, add_src);
 }
 
 // One launch for several boxes (FP32 inner solves of grouped refinement):
@@ -226,7 +233,7 @@ size_t x_smem_bytes(const cfs_plan* P, int lines, size_t csize) {
   return 128 + csize * (2 * cap + (size_t)P->fx.ntw + P->M / 2 + 1);
 }
 
-template <class C, int OUT>
+template <class C, int OUT, int EMU = 0>
 static cudaError_t launch_x(const cfs_plan* P, const void* in, void* out, bool inverse,
                             double scale, const C* tw, const C* post, cudaStream_t st,
                             const double* msum = nullptr, const void* add_src = nullptr) {
@@ -237,12 +244,12 @@ static cudaError_t launch_x(const cfs_plan* P, const void* in, void* out, bool i
   const int scaled = (scale != 1.0);
   const C* cin = reinterpret_cast<const C*>(in);
   if (!inverse) {
-    auto k = rfft_x_kernel<false, C, OUT_SAME>;
+    auto k = rfft_x_kernel<false, C, OUT_SAME, EMU>;
     allow_max_smem(k);
     k<<<(unsigned)grid, 128, smem, st>>>(cin, out, nlines, P->fx, tw, post, lb, scale, scaled,
                                          P->d_status, nullptr, 0.0, nullptr);
   } else {
-    auto k = rfft_x_kernel<true, C, OUT>;
+    auto k = rfft_x_kernel<true, C, OUT, EMU>;
     allow_max_smem(k);
     k<<<(unsigned)grid, 128, smem, st>>>(cin, out, nlines, P->fx, tw, post, lb, scale, scaled,
                                          P->d_status, msum, P->inv_wn,
@@ -253,7 +260,19 @@ static cudaError_t launch_x(const cfs_plan* P, const void* in, void* out, bool i
 
 cudaError_t launch_rfft_x(const cfs_plan* P, const double* in, double* out, bool inverse,
                           double scale, cudaStream_t st) {
-  return launch_x<double2, OUT_SAME>(P, in, out, inverse, scale, P->d_twx, P->d_post, st);
+  // the plan's level L of integer-unit additions: kEmu* bits 0 .. L-1
+  switch (P->emu_x) {
+    case 1:
+      return launch_x<double2, OUT_SAME, 1>(P, in, out, inverse, scale, P->d_twx, P->d_post, st);
+    case 2:
+      return launch_x<double2, OUT_SAME, 3>(P, in, out, inverse, scale, P->d_twx, P->d_post, st);
+    case 3:
+      return launch_x<double2, OUT_SAME, 7>(P, in, out, inverse, scale, P->d_twx, P->d_post, st);
+    case 4:
+      return launch_x<double2, OUT_SAME, 15>(P, in, out, inverse, scale, P->d_twx, P->d_post, st);
+    default:
+      return launch_x<double2, OUT_SAME, 0>(P, in, out, inverse, scale, P->d_twx, P->d_post, st);
+  }
 }
 
 cudaError_t launch_rfft_x32(const cfs_plan* P, const float* in, float* out, bool inverse,

@@ -132,7 +132,7 @@ __device__ __forceinline__ void y_wall_transform(C* buf0, C* buf1, const FftDesc
 
 // Tile bx (columns [bx * tk, bx * tk + tk)) of z plane z; ytype is Y_FFT for
 // periodic y, else the wall transform, with wy[k] = exp(-i pi k / 2N).
-template <bool INV, class C>
+template <bool INV, class C, int EMU = 0>
 __device__ __forceinline__ void fft_y_body(const CUtensorMap* map, const FftDesc& d,
                                            const C* __restrict__ twg, int tk, int by, int nbox,
                                            int* status, int bx, int z, int ytype,
@@ -182,7 +182,7 @@ __device__ __forceinline__ void fft_y_body(const CUtensorMap* map, const FftDesc
     __syncthreads();
   }
   // element (y, c) of the tile sits at y*tk + c: element stride tk, batch stride 1
-  C* res = stockham_tile<INV>(buf0, buf1, d, tk, gtw ? twg : tw);
+  C* res = stockham_tile<INV, C, EMU>(buf0, buf1, d, tk, gtw ? twg : tw);
   if (!INV && bx == 0) {  // untangle after the forward transform
     for (int ky = 1 + threadIdx.x; 2 * ky < ny; ky += blockDim.x) {
       const C zz = res[ky * tk], zm = res[(ny - ky) * tk];
@@ -201,12 +201,15 @@ __device__ __forceinline__ void fft_y_body(const CUtensorMap* map, const FftDesc
   }
 }
 
-template <bool INV, class C>
+// EMU (FP64 only): the butterfly additions that run on the integer units
+// (kEmu* in chanfs_fft.cuh; the same bits as the FP64 pipe's).
+template <bool INV, class C, int EMU = 0>
 __global__ void __launch_bounds__(256) fft_y_kernel(const __grid_constant__ CUtensorMap map,
                                                     FftDesc d, const C* __restrict__ twg,
                                                     int tk, int by, int nbox, int* status,
                                                     int ytype, const C* __restrict__ wy) {
-  fft_y_body<INV, C>(&map, d, twg, tk, by, nbox, status, blockIdx.x, blockIdx.y, ytype, wy);
+  fft_y_body<INV, C, EMU>(&map, d, twg, tk, by, nbox, status, blockIdx.x, blockIdx.y, ytype,
+                          wy);
 }
 
 // One launch for several boxes (FP32 inner solves of grouped refinement).
@@ -221,7 +224,7 @@ __global__ void __launch_bounds__(256, 1) fft_y_group_kernel(const YBox* boxes, 
                           static_cast<const float2*>(y.wy));
 }
 
-template <class C>
+template <class C, int EMU = 0>
 static cudaError_t launch_y(const cfs_plan* P, void* data, bool inverse, int tk, const C* tw,
                             const C* wy, cudaStream_t st) {
   if (P->ny == 1) return cudaSuccess;  // length-1 transform is the identity
@@ -235,12 +238,12 @@ static cudaError_t launch_y(const cfs_plan* P, void* data, bool inverse, int tk,
   const size_t smem = y_smem_of(P, tk, sizeof(C) == sizeof(float2));
   dim3 grid((P->M + tk - 1) / tk, P->nz);
   if (!inverse) {
-    auto k = fft_y_kernel<false, C>;
+    auto k = fft_y_kernel<false, C, EMU>;
     allow_max_smem(k);
     k<<<grid, y_threads<C>(), smem, st>>>(map, P->fy, tw, tk, P->by, P->nbox, P->d_status,
                                           P->ybc, wy);
   } else {
-    auto k = fft_y_kernel<true, C>;
+    auto k = fft_y_kernel<true, C, EMU>;
     allow_max_smem(k);
     k<<<grid, y_threads<C>(), smem, st>>>(map, P->fy, tw, tk, P->by, P->nbox, P->d_status,
                                           P->ybc, wy);
@@ -256,7 +259,19 @@ bool y_tile_ok(const cfs_plan* P, int tk, bool fp32) {
 }
 
 cudaError_t launch_fft_y(const cfs_plan* P, double* data, bool inverse, cudaStream_t st) {
-  return launch_y<double2>(P, data, inverse, P->tk, P->d_twy, P->d_wy, st);
+  // the plan's level L of integer-unit additions: kEmu* bits 0 .. L-1 (the
+  // x transform's untangle bit has no work here)
+  switch (P->emu_y) {
+    case 1:
+      return launch_y<double2, 1>(P, data, inverse, P->tk, P->d_twy, P->d_wy, st);
+    case 2:
+      return launch_y<double2, 3>(P, data, inverse, P->tk, P->d_twy, P->d_wy, st);
+    case 3:
+    case 4:
+      return launch_y<double2, 7>(P, data, inverse, P->tk, P->d_twy, P->d_wy, st);
+    default:
+      return launch_y<double2, 0>(P, data, inverse, P->tk, P->d_twy, P->d_wy, st);
+  }
 }
 
 cudaError_t launch_fft_y32(const cfs_plan* P, float* data, bool inverse, cudaStream_t st) {

@@ -274,6 +274,8 @@ extern "C" int cfs_plan_create_walls(cfs_plan_t* out, int nx, int ny, int nz, do
 
   std::vector<double2> twx, twy;
   P->fft_radix = 8;
+  P->emu_x = kEmuDefaultX;
+  P->emu_y = kEmuDefaultY;
   if (!make_fft_desc(P->M, &P->fx, &twx, 8) || !make_fft_desc(ny, &P->fy, &twy, 8)) {
     plan_free(P);
     return CFS_EUNSUPPORTED;
@@ -936,6 +938,11 @@ extern "C" int cfs_plan_set_option(cfs_plan_t P, int option, int value) {
       if (value && P->dtype != CFS_F32_REFINED) return CFS_EUNSUPPORTED;
       P->helm_thomas32 = value;
       return CFS_OK;
+    case CFS_OPT_F64_ADDS_X:
+    case CFS_OPT_F64_ADDS_Y:
+      if (value < 0 || value > 4) return CFS_EINVAL;
+      (option == CFS_OPT_F64_ADDS_X ? P->emu_x : P->emu_y) = value;
+      return CFS_OK;
     case CFS_OPT_PCR_PARTS: {
       if (value < 0 || value > kPcrMaxParts) return CFS_EINVAL;
       for (int n = P->nz - 1; value > 0 && n <= P->nz; ++n)  // face and centred fields
@@ -974,6 +981,12 @@ extern "C" int cfs_plan_get_option(cfs_plan_t P, int option, int* value) {
       return CFS_OK;
     case CFS_OPT_HELM_THOMAS32:
       *value = P->helm_thomas32;
+      return CFS_OK;
+    case CFS_OPT_F64_ADDS_X:
+      *value = P->emu_x;
+      return CFS_OK;
+    case CFS_OPT_F64_ADDS_Y:
+      *value = P->emu_y;
       return CFS_OK;
     default:
       return CFS_EINVAL;
