@@ -1174,6 +1174,19 @@ def run_ours(args):
     barrier(device)
     e2e = aggregate(e2e_ms, e2e_steps, npts, world)
     field_bytes = npts * 8
+    # the same calls with whole fields per copy (no streaming in chunks), for comparison
+    stream_chunks = plan.get_option(chanfs.OPT_STREAM_CHUNKS)
+    plan.set_option(chanfs.OPT_STREAM_CHUNKS, 1)
+    e2e_step()
+    barrier(device)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    whole_ms = reduce_max((time.perf_counter() - t0) * 1e3, device)
+    barrier(device)
+    plan.set_option(chanfs.OPT_STREAM_CHUNKS, 0)
+    e2e_whole = aggregate(whole_ms, e2e_steps, npts, world)
 
     if rank != 0:
         plan.close()
@@ -1217,7 +1230,13 @@ def run_ours(args):
         "e2e": {"value": e2e["value"], "unit": UNIT, "h2d_bytes_per_step": 4 * field_bytes,
                 "d2h_bytes_per_step": 4 * field_bytes, "steps": e2e_steps,
                 "api": "cfs_solve_batch_host (Poisson + 3 Helmholtz, host<->device copies "
-                       "overlapped with the solves), pinned host buffers"},
+                       "overlapped with the solves), pinned host buffers",
+                "stream_chunks": stream_chunks,
+                "ms_per_step": e2e["ms_per_step"],
+                "whole_fields": {"value": e2e_whole["value"],
+                                 "ms_per_step": e2e_whole["ms_per_step"],
+                                 "how": "the same calls with CFS_OPT_STREAM_CHUNKS 1 (each "
+                                        "field copied and solved whole)"}},
         "gpu_launches": 8 * args.steps,
         "roofline": roof,
         "stage_ms": {s: round(v, 4) for s, v in mean_ms.items()},

@@ -207,8 +207,15 @@ int cfs_helmholtz_solve_host(cfs_plan_t plan, double c, int loc,
  * copy-in stream and a copy-out stream per compute stream.  The solves run
  * after the work already on `stream`: Poisson solves on `stream`, and on
  * CFS_F64 plans the Helmholtz solves on a second stream beside them (they
- * share no plan scratch; refined solves all run on `stream`).  Host buffers
- * should be pinned for the copies to overlap.  Returns when every result has
+ * share no plan scratch; refined solves all run on `stream`).  On CFS_F64
+ * plans each field moves in chunks (CFS_OPT_STREAM_CHUNKS): a Poisson field
+ * in ranges of z planes, transformed along x range by range as it lands and
+ * copied out range by range as its inverse x transform finishes; a Helmholtz
+ * field solved by Algorithm 2 in ranges of y rows, each solved and copied
+ * out on its own; and the batch's first Helmholtz solve is taken first when
+ * the batch also holds Poisson solves.  The results are the same bits as
+ * whole-field solves.  Host buffers should be pinned for the copies to
+ * overlap.  Returns when every result has
  * arrived: CFS_OK, the first error, or CFS_ENOTCONVERGED if a refined solve
  * missed its tolerance (every output is still written).  A step of the
  * channel workload is one call: the Poisson solve and the three Helmholtz
@@ -522,6 +529,13 @@ int cfs_slab_helmholtz_finish(cfs_slab_t slab, double c, int loc, const double* 
  *       binary64 round-to-nearest-even additions done in integer
  *       arithmetic, so every level gives the same bits; on GPUs whose FP64
  *       pipe is narrow it lets the integer units share the FP64 work.
+ *   CFS_OPT_STREAM_CHUNKS  chunks in which cfs_solve_batch_host moves each
+ *       field of an FP64 plan: 0 automatic (about 128 MB per chunk, at most
+ *       8), 1 whole fields, or 2..8.  A Poisson field moves in ranges of z
+ *       planes (its x transforms run range by range as the data lands and
+ *       leaves), a Helmholtz field solved by Algorithm 2 in ranges of y rows;
+ *       the results are the same bits for every value.  get_option reports
+ *       the count a Poisson field of the plan takes.
  * cfs_plan_set_option returns CFS_EINVAL for an unknown option or value, and
  * CFS_EUNSUPPORTED if the value cannot run at this plan's size (a tile that
  * does not fit in shared memory).  cfs_plan_get_option reports the value in
@@ -538,7 +552,8 @@ enum {
   CFS_OPT_HELM_THOMAS32 = 7,
   CFS_OPT_FFT_RADIX = 8,
   CFS_OPT_F64_ADDS_X = 9,
-  CFS_OPT_F64_ADDS_Y = 10
+  CFS_OPT_F64_ADDS_Y = 10,
+  CFS_OPT_STREAM_CHUNKS = 11
 };
 int cfs_plan_set_option(cfs_plan_t plan, int option, int value);
 int cfs_plan_get_option(cfs_plan_t plan, int option, int* value);

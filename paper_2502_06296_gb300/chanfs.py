@@ -25,7 +25,7 @@ X_FORWARD, Y_FORWARD, Z_SOLVE, Y_INVERSE, X_INVERSE = 0, 1, 2, 3, 4
 
 OPT_THOMAS_TILE, OPT_X_LINES, OPT_Y_TILE, OPT_PCR_PARTS, OPT_HELM_FP64 = 1, 2, 3, 4, 5
 OPT_HELM_THOMAS, OPT_HELM_THOMAS32, OPT_FFT_RADIX = 6, 7, 8
-OPT_F64_ADDS_X, OPT_F64_ADDS_Y = 9, 10
+OPT_F64_ADDS_X, OPT_F64_ADDS_Y, OPT_STREAM_CHUNKS = 9, 10, 11
 
 REQ_POISSON, REQ_HELMHOLTZ = 0, 1
 

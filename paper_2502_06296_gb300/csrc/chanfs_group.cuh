@@ -123,7 +123,8 @@ struct HThomasBox {  // Helmholtz Thomas sweep of one box (helm_thomas.cu)
 template <class R>
 struct PcrArgs {  // Algorithm 2 runtime (pcr.cu)
   R* u;                // output field (for the face wall row)
-  long long ncols;     // Nx * Ny
+  long long ncols;     // columns solved: Nx * Ny, or a range of them
+  long long zstride;   // elements between z rows (Nx * Ny)
   int n;               // unknowns per column
   int nparts;
   int face;            // face-located field: slot nz-1 is the wall, written 0

@@ -35,6 +35,7 @@ constexpr int kPcrMaxUnknowns = 1024;  // rows of a PCR tile in shared memory
 
 constexpr int kMaxGroup = 4096;     // plans of one grouped solve
 constexpr int kBatchSlots = 4;      // device slots of a batch of host-buffer solves
+constexpr int kMaxStreamChunks = 8; // chunks a field of a streamed batch moves in
 // Default levels of CFS_OPT_F64_ADDS_X / _Y (FP64 butterfly additions on the
 // integer units).
 constexpr int kEmuDefaultX = 0;
@@ -200,7 +201,10 @@ struct cfs_plan {
   double* d_batch;
   int batch_slots;
   cudaStream_t copy_in, copy_out, copy_out2, compute2;
-  cudaEvent_t ev_entry, ev_in[4], ev_done[4], ev_free[4];
+  cudaEvent_t ev_entry, ev_done[4], ev_free[4];
+  // streamed FP64 batches: per slot, a chunk's input landed / its result is ready
+  cudaEvent_t ev_cin[4][8], ev_cdone[4][8];
+  int stream_chunks;  // CFS_OPT_STREAM_CHUNKS (0 automatic)
   // device status word
   int* d_status;
   // work buffers allocated with guard words: (allocation base, payload bytes)
@@ -213,8 +217,10 @@ namespace chanfs {
 // ----------------------------------------------------------------------------
 // Kernel launchers (one per translation unit)
 // ----------------------------------------------------------------------------
+// nlines >= 0: only the first nlines x lines of in / out (a range of z planes
+// when in and out point at its first plane); -1: every line of the field.
 cudaError_t launch_rfft_x(const cfs_plan* P, const double* in, double* out, bool inverse,
-                          double scale, cudaStream_t st);
+                          double scale, cudaStream_t st, long long nlines = -1);
 cudaError_t launch_fft_y(const cfs_plan* P, double* data, bool inverse, cudaStream_t st);
 cudaError_t launch_thomas(const cfs_plan* P, double* data, cudaStream_t st);
 cudaError_t launch_rfft_x32(const cfs_plan* P, const float* in, float* out, bool inverse,
@@ -250,6 +256,9 @@ cudaError_t launch_thomas_factor(cfs_plan* P, const double* dA, const double* dB
                                  cudaStream_t st);
 cudaError_t launch_pcr(const cfs_plan* P, const HelmCoef& h, const double* rhs, double* u,
                        cudaStream_t st);
+// The columns [col0, col0 + ncols) of the (x, y) plane only (col0 even).
+cudaError_t launch_pcr_cols(const cfs_plan* P, const HelmCoef& h, const double* rhs, double* u,
+                            long long col0, long long ncols, cudaStream_t st);
 size_t pcr_smem_bytes(int n, int nparts);
 cudaError_t launch_pcr_raw(long long ncols, int nz, int n, int nparts, int loc, const double* rows,
                            const double* red, const double* rhs, double* u, int* status,

@@ -236,8 +236,10 @@ size_t x_smem_bytes(const cfs_plan* P, int lines, size_t csize) {
 template <class C, int OUT, int EMU = 0>
 static cudaError_t launch_x(const cfs_plan* P, const void* in, void* out, bool inverse,
                             double scale, const C* tw, const C* post, cudaStream_t st,
-                            const double* msum = nullptr, const void* add_src = nullptr) {
-  const long long nlines = (long long)P->ny * P->nz;
+                            const double* msum = nullptr, const void* add_src = nullptr,
+                            long long nlines = -1) {
+  if (nlines < 0) nlines = (long long)P->ny * P->nz;
+  if (nlines == 0) return cudaSuccess;
   const int lb = x_lines_per_cta(P, sizeof(C));
   const long long grid = (nlines + lb - 1) / lb;
   const size_t smem = x_smem_bytes(P, lb, sizeof(C));
@@ -259,19 +261,26 @@ static cudaError_t launch_x(const cfs_plan* P, const void* in, void* out, bool i
 }
 
 cudaError_t launch_rfft_x(const cfs_plan* P, const double* in, double* out, bool inverse,
-                          double scale, cudaStream_t st) {
+                          double scale, cudaStream_t st, long long nlines) {
+  const double2* tw = P->d_twx;
+  const double2* post = P->d_post;
   // the plan's level L of integer-unit additions: kEmu* bits 0 .. L-1
   switch (P->emu_x) {
     case 1:
-      return launch_x<double2, OUT_SAME, 1>(P, in, out, inverse, scale, P->d_twx, P->d_post, st);
+      return launch_x<double2, OUT_SAME, 1>(P, in, out, inverse, scale, tw, post, st, nullptr,
+                                            nullptr, nlines);
     case 2:
-      return launch_x<double2, OUT_SAME, 3>(P, in, out, inverse, scale, P->d_twx, P->d_post, st);
+      return launch_x<double2, OUT_SAME, 3>(P, in, out, inverse, scale, tw, post, st, nullptr,
+                                            nullptr, nlines);
     case 3:
-      return launch_x<double2, OUT_SAME, 7>(P, in, out, inverse, scale, P->d_twx, P->d_post, st);
+      return launch_x<double2, OUT_SAME, 7>(P, in, out, inverse, scale, tw, post, st, nullptr,
+                                            nullptr, nlines);
     case 4:
-      return launch_x<double2, OUT_SAME, 15>(P, in, out, inverse, scale, P->d_twx, P->d_post, st);
+      return launch_x<double2, OUT_SAME, 15>(P, in, out, inverse, scale, tw, post, st, nullptr,
+                                             nullptr, nlines);
     default:
-      return launch_x<double2, OUT_SAME, 0>(P, in, out, inverse, scale, P->d_twx, P->d_post, st);
+      return launch_x<double2, OUT_SAME, 0>(P, in, out, inverse, scale, tw, post, st, nullptr,
+                                            nullptr, nlines);
   }
 }
 

@@ -192,7 +192,7 @@ __device__ __forceinline__ void pcr_body(const CUtensorMap* in_map, const CUtens
       tma_store_commit_and_wait_read();  // the tile may be reused
     }
     if (a.face && threadIdx.x < kPcrCols && col0 + c < a.ncols)
-      a.u[(long long)(a.nz - 1) * a.ncols + col0 + c] = R(0);
+      a.u[(long long)(a.nz - 1) * a.zstride + col0 + c] = R(0);
     __syncthreads();
   }
 }
@@ -452,11 +452,13 @@ __global__ void __launch_bounds__(refine_threads<MM>::value)
   pcr_refine_body<MM>(&x.in_map, &x.out_map, x.a, x.status, blk, x.blocks);
 }
 
-// 2-D map over the first n rows of a field: ncols reals per row.
+// 2-D map over the first n rows of a field: ncols reals per row, rows
+// zstride reals apart (0: ncols).
 template <class R>
-static bool pcr_map(CUtensorMap* map, const void* base, long long ncols, int n, int by) {
+static bool pcr_map(CUtensorMap* map, const void* base, long long ncols, int n, int by,
+                    long long zstride = 0) {
   const cuuint64_t gdim[2] = {(cuuint64_t)ncols, (cuuint64_t)n};
-  const cuuint64_t gstride[1] = {(cuuint64_t)ncols * sizeof(R)};
+  const cuuint64_t gstride[1] = {(cuuint64_t)(zstride ? zstride : ncols) * sizeof(R)};
   const cuuint32_t box[2] = {(cuuint32_t)kPcrCols, (cuuint32_t)by};
   return encode_map(map, sizeof(R), 2, base, gdim, gstride, box);
 }
@@ -479,12 +481,20 @@ static size_t pcr_smem_t(int n, int nparts) {
 
 size_t pcr_smem_bytes(int n, int nparts) { return pcr_smem_t<double>(n, nparts); }
 
+// Columns [col0, col0 + ncols) of the field (ncols < 0: all of them).
 template <class R>
 static cudaError_t launch_pcr_t(const cfs_plan* P, const HelmCoef& h, const R* rows, const R* red,
-                                const R* rhs, R* u, cudaStream_t st) {
+                                const R* rhs, R* u, cudaStream_t st, long long col0 = 0,
+                                long long ncols = -1) {
+  const long long plane = (long long)P->nx * P->ny;
+  if (ncols < 0) ncols = plane;
+  if (ncols == 0) return cudaSuccess;
+  rhs += col0;
+  u += col0;
   PcrArgs<R> a;
   a.u = u;
-  a.ncols = (long long)P->nx * P->ny;
+  a.ncols = ncols;
+  a.zstride = plane;
   a.n = h.n;
   a.nparts = h.nparts;
   a.face = (h.loc == CFS_LOC_FACE);
@@ -493,7 +503,8 @@ static cudaError_t launch_pcr_t(const cfs_plan* P, const HelmCoef& h, const R* r
   a.rows = rows;
   a.red = red;
   CUtensorMap in_map, out_map;
-  if (!pcr_map<R>(&in_map, rhs, a.ncols, h.n, a.by) || !pcr_map<R>(&out_map, u, a.ncols, h.n, a.by))
+  if (!pcr_map<R>(&in_map, rhs, a.ncols, h.n, a.by, plane) ||
+      !pcr_map<R>(&out_map, u, a.ncols, h.n, a.by, plane))
     return cudaErrorInvalidValue;
   const size_t smem = pcr_smem_t<R>(h.n, h.nparts);
   const int threads = kPcrCols * h.nparts;
@@ -516,6 +527,13 @@ cudaError_t launch_pcr(const cfs_plan* P, const HelmCoef& h, const double* rhs, 
   return launch_pcr_t<double>(P, h, h.d_rows, h.d_red, rhs, u, st);
 }
 
+cudaError_t launch_pcr_cols(const cfs_plan* P, const HelmCoef& h, const double* rhs, double* u,
+                            long long col0, long long ncols, cudaStream_t st) {
+  if (col0 < 0 || (col0 & 1) || ncols < 0 || col0 + ncols > (long long)P->nx * P->ny)
+    return cudaErrorInvalidValue;  // (16-byte aligned TMA bases)
+  return launch_pcr_t<double>(P, h, h.d_rows, h.d_red, rhs, u, st, col0, ncols);
+}
+
 cudaError_t launch_pcr32(const cfs_plan* P, const HelmCoef& h, const float* rhs, float* u,
                          cudaStream_t st) {
   if (!h.d_rows32) return cudaErrorInvalidValue;
@@ -532,6 +550,7 @@ static size_t pcr_group_box_t(const cfs_plan* P, const HelmCoef& h, const R* row
   PcrArgs<R>& a = box->a;
   a.u = u;
   a.ncols = (long long)P->nx * P->ny;
+  a.zstride = a.ncols;
   a.n = h.n;
   a.nparts = h.nparts;
   a.face = (h.loc == CFS_LOC_FACE);
@@ -719,6 +738,7 @@ cudaError_t launch_pcr_raw(long long ncols, int nz, int n, int nparts, int loc, 
   PcrArgs<double> a;
   a.u = u;
   a.ncols = ncols;
+  a.zstride = ncols;
   a.n = n;
   a.nparts = nparts;
   a.face = (loc == CFS_LOC_FACE);

@@ -173,9 +173,13 @@ static void plan_free(cfs_plan* P) {
   for (cudaStream_t q : {P->copy_in, P->copy_out, P->copy_out2, P->compute2})
     if (q) cudaStreamDestroy(q);
   if (P->ev_entry) cudaEventDestroy(P->ev_entry);
-  for (int k = 0; k < kBatchSlots; ++k)
-    for (cudaEvent_t e : {P->ev_in[k], P->ev_done[k], P->ev_free[k]})
+  for (int k = 0; k < kBatchSlots; ++k) {
+    for (cudaEvent_t e : {P->ev_done[k], P->ev_free[k]})
       if (e) cudaEventDestroy(e);
+    for (int c = 0; c < kMaxStreamChunks; ++c)
+      for (cudaEvent_t e : {P->ev_cin[k][c], P->ev_cdone[k][c]})
+        if (e) cudaEventDestroy(e);
+  }
   cudaFree(P->d_status);
   cudaFree(P->d_twx32);
   cudaFree(P->d_twy32);
@@ -894,6 +898,21 @@ int chanfs::plan_set_radix(cfs_plan* P, int max_radix) {
   return CFS_OK;
 }
 
+// Chunks of a streamed FP64 batch field (CFS_OPT_STREAM_CHUNKS): z-plane
+// ranges of a Poisson field, (x, y)-column ranges (whole y rows) of a
+// Helmholtz field solved by Algorithm 2; 1 for the solves that take the whole
+// field at once.  Automatic: about 128 MB per chunk, at most kMaxStreamChunks.
+static int batch_chunks(const cfs_plan* P, int kind) {
+  const size_t plane = (size_t)P->nx * P->ny;
+  if (P->dtype != CFS_F64 || (P->nx & 1)) return 1;
+  if (kind == CFS_REQ_HELMHOLTZ && (P->helm_thomas || sizeof(double) * plane > (1u << 30)))
+    return 1;  // (Thomas sweeps take the field whole; 2-D copy pitches stay modest)
+  const int extent = (kind == CFS_REQ_POISSON) ? P->nz : P->ny;
+  int k = P->stream_chunks;
+  if (k == 0) k = (int)std::min<size_t>(kMaxStreamChunks, sizeof(double) * plane * P->nz >> 27);
+  return std::max(1, std::min(k, extent));
+}
+
 extern "C" int cfs_plan_set_option(cfs_plan_t P, int option, int value) {
   if (!P) return CFS_EINVAL;
   switch (option) {
@@ -943,6 +962,10 @@ extern "C" int cfs_plan_set_option(cfs_plan_t P, int option, int value) {
       if (value < 0 || value > 4) return CFS_EINVAL;
       (option == CFS_OPT_F64_ADDS_X ? P->emu_x : P->emu_y) = value;
       return CFS_OK;
+    case CFS_OPT_STREAM_CHUNKS:
+      if (value < 0 || value > kMaxStreamChunks) return CFS_EINVAL;
+      P->stream_chunks = value;
+      return CFS_OK;
     case CFS_OPT_PCR_PARTS: {
       if (value < 0 || value > kPcrMaxParts) return CFS_EINVAL;
       for (int n = P->nz - 1; value > 0 && n <= P->nz; ++n)  // face and centred fields
@@ -987,6 +1010,9 @@ extern "C" int cfs_plan_get_option(cfs_plan_t P, int option, int* value) {
       return CFS_OK;
     case CFS_OPT_F64_ADDS_Y:
       *value = P->emu_y;
+      return CFS_OK;
+    case CFS_OPT_STREAM_CHUNKS:
+      *value = batch_chunks(P, CFS_REQ_POISSON);
       return CFS_OK;
     default:
       return CFS_EINVAL;
@@ -1070,22 +1096,38 @@ static int ensure_batch(cfs_plan* P, int slots) {
   for (cudaStream_t* q : {&P->copy_in, &P->copy_out, &P->copy_out2, &P->compute2})
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(q, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev_entry, cudaEventDisableTiming);
-  for (int k = 0; k < kBatchSlots && e == cudaSuccess; ++k)
-    for (cudaEvent_t* v : {&P->ev_in[k], &P->ev_done[k], &P->ev_free[k]})
+  for (int k = 0; k < kBatchSlots && e == cudaSuccess; ++k) {
+    for (cudaEvent_t* v : {&P->ev_done[k], &P->ev_free[k]})
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(v, cudaEventDisableTiming);
+    for (int c = 0; c < kMaxStreamChunks; ++c)
+      for (cudaEvent_t* v : {&P->ev_cin[k][c], &P->ev_cdone[k][c]})
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(v, cudaEventDisableTiming);
+  }
   return e == cudaSuccess ? CFS_OK : CFS_ECUDA;
 }
 
 // n solves through host buffers, pipelined over up to kBatchSlots device
-// slots (job i in slot i mod K): the inputs are copied in back to back on one
-// copy stream as their slots free up; each solve starts when its input has
-// arrived and its slot's previous output has been copied out; each result is
-// copied out as soon as its solve ends.  On FP64 plans the Helmholtz solves
-// run on a second compute stream, beside the Poisson solves (the two kinds
-// share no plan scratch; refined solves share the FP32 work fields and stay
-// on the caller's stream), each compute stream with its own copy-out stream.
-// The copy of the next input is enqueued before solve i starts, so that it
-// proceeds even while a refined solve waits on the host.
+// slots (the job at position p of the processing order in slot p mod K): the
+// inputs are copied in back to back on one copy stream as their slots free
+// up; each solve starts when its input has arrived and its slot's previous
+// output has been copied out; each result is copied out as soon as it is
+// ready.  On FP64 plans the Helmholtz solves run on a second compute stream,
+// beside the Poisson solves (the two kinds share no plan scratch; refined
+// solves share the FP32 work fields and stay on the caller's stream), each
+// compute stream with its own copy-out stream.  The copy of the next input is
+// enqueued before solve p starts, so that it proceeds even while a refined
+// solve waits on the host.
+//
+// FP64 plans stream their fields in chunks (batch_chunks): a Poisson field in
+// ranges of z planes, whose forward x transforms start as each range lands and
+// whose inverse x transforms hand each range to the copy-out stream as it is
+// done; a Helmholtz field solved by Algorithm 2 in ranges of y rows (2-D
+// copies), each solved and copied out on its own.  The host link then carries
+// inputs and results at once from the first chunk on, instead of waiting for
+// whole fields.  Every chunk is computed by the same kernels on the same
+// columns or lines as a whole-field solve, so the results are the same bits.
+// The first Helmholtz job of a batch that also holds Poisson jobs is taken
+// first: its chunks come back while the Poisson input is still arriving.
 extern "C" int cfs_solve_batch_host(cfs_plan_t P, int n, const int* kind, const double* c,
                                     const int* loc, const double* const* in, double* const* out,
                                     void* stream) {
@@ -1105,8 +1147,22 @@ extern "C" int cfs_solve_batch_host(cfs_plan_t P, int n, const int* kind, const 
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const bool two = (P->dtype == CFS_F64);  // Helmholtz beside Poisson
-  const size_t nf = (size_t)P->nx * P->ny * P->nz;
+  const size_t plane = (size_t)P->nx * P->ny;
+  const size_t nf = plane * P->nz;
   const size_t bytes = sizeof(double) * nf;
+  // processing order: the first Helmholtz job ahead when Poisson jobs are streamed too
+  std::vector<int> ord(n);
+  for (int i = 0; i < n; ++i) ord[i] = i;
+  if (two) {
+    int first_h = -1;
+    bool any_p = false;
+    for (int i = 0; i < n; ++i) {
+      if (kind[i] == CFS_REQ_HELMHOLTZ && first_h < 0) first_h = i;
+      any_p = any_p || kind[i] == CFS_REQ_POISSON;
+    }
+    if (first_h > 0 && any_p && batch_chunks(P, CFS_REQ_HELMHOLTZ) > 1)
+      std::rotate(ord.begin(), ord.begin() + first_h, ord.begin() + first_h + 1);
+  }
   auto din = [&](int s) { return P->d_batch + (size_t)(2 * s) * nf; };
   auto dout = [&](int s) { return P->d_batch + (size_t)(2 * s + 1) * nf; };
   auto cstream = [&](int i) {
@@ -1115,41 +1171,98 @@ extern "C" int cfs_solve_batch_host(cfs_plan_t P, int n, const int* kind, const 
   auto ostream = [&](int i) {
     return (two && kind[i] == CFS_REQ_HELMHOLTZ) ? P->copy_out2 : P->copy_out;
   };
+  // chunk q of job i: element offset, and the 2-D shape (rows x width
+  // elements, rows nf / nz apart) for column ranges
+  struct Chunk {
+    size_t off, rows, width;
+  };
+  auto chunk = [&](int i, int q, int nq) {
+    if (nq == 1) return Chunk{0, 1, nf};
+    if (kind[i] == CFS_REQ_POISSON) {  // z planes [z0, z1)
+      const size_t z0 = (size_t)P->nz * q / nq, z1 = (size_t)P->nz * (q + 1) / nq;
+      return Chunk{z0 * plane, 1, (z1 - z0) * plane};
+    }
+    const size_t y0 = (size_t)P->ny * q / nq, y1 = (size_t)P->ny * (q + 1) / nq;  // y rows
+    return Chunk{y0 * P->nx, (size_t)P->nz, (y1 - y0) * P->nx};
+  };
+  auto copy = [&](double* dst, const double* src, const Chunk& k, cudaMemcpyKind dir,
+                  cudaStream_t q) {
+    if (k.rows == 1)
+      return cudaMemcpyAsync(dst + k.off, src + k.off, sizeof(double) * k.width, dir, q);
+    return cudaMemcpy2DAsync(dst + k.off, sizeof(double) * plane, src + k.off,
+                             sizeof(double) * plane, sizeof(double) * k.width, k.rows, dir, q);
+  };
   // everything starts after the work already on the caller's stream
   cudaError_t e = cudaEventRecord(P->ev_entry, st);
   for (cudaStream_t q : {P->copy_in, P->copy_out, P->copy_out2, P->compute2})
     if (e == cudaSuccess) e = cudaStreamWaitEvent(q, P->ev_entry, 0);
-  auto copy_in = [&](int i) {
-    const int s = i % K;
+  auto copy_in = [&](int p) {
+    const int i = ord[p], s = p % K, nq = batch_chunks(P, kind[i]);
     cudaError_t r = cudaSuccess;
-    if (i >= K) r = cudaStreamWaitEvent(P->copy_in, P->ev_done[s], 0);  // solve i-K read it
-    if (r == cudaSuccess)
-      r = cudaMemcpyAsync(din(s), in[i], bytes, cudaMemcpyHostToDevice, P->copy_in);
-    if (r == cudaSuccess) r = cudaEventRecord(P->ev_in[s], P->copy_in);
+    if (p >= K) r = cudaStreamWaitEvent(P->copy_in, P->ev_done[s], 0);  // solve p-K read it
+    for (int q = 0; q < nq && r == cudaSuccess; ++q) {
+      r = copy(din(s), in[i], chunk(i, q, nq), cudaMemcpyHostToDevice, P->copy_in);
+      if (r == cudaSuccess) r = cudaEventRecord(P->ev_cin[s][q], P->copy_in);
+    }
     return r;
   };
   if (e == cudaSuccess) e = copy_in(0);
-  for (int i = 0; i < n && e == cudaSuccess; ++i) {
-    const int s = i % K;
+  for (int p = 0; p < n && e == cudaSuccess; ++p) {
+    const int i = ord[p], s = p % K, nq = batch_chunks(P, kind[i]);
     cudaStream_t cs = cstream(i);
-    if (i + 1 < n) e = copy_in(i + 1);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, P->ev_in[s], 0);
-    if (e == cudaSuccess && i >= K)  // the output of solve i-K has been copied out
+    if (p + 1 < n) e = copy_in(p + 1);
+    if (e == cudaSuccess && p >= K)  // the output of solve p-K has been copied out
       e = cudaStreamWaitEvent(cs, P->ev_free[s], 0);
     if (e != cudaSuccess) break;
-    const int r = (kind[i] == CFS_REQ_POISSON)
-                      ? cfs_poisson_solve(P, din(s), dout(s), cs)
-                      : cfs_helmholtz_solve(P, c[i], loc[i], din(s), dout(s), cs);
+    int r = CFS_OK;
+    if (nq == 1) {
+      e = cudaStreamWaitEvent(cs, P->ev_cin[s][0], 0);
+      if (e != cudaSuccess) break;
+      r = (kind[i] == CFS_REQ_POISSON)
+              ? cfs_poisson_solve(P, din(s), dout(s), cs)
+              : cfs_helmholtz_solve(P, c[i], loc[i], din(s), dout(s), cs);
+      if (r == CFS_OK || r == CFS_ENOTCONVERGED) e = cudaEventRecord(P->ev_cdone[s][0], cs);
+    } else if (kind[i] == CFS_REQ_POISSON) {  // the stages of cfs_poisson_solve, x by z ranges
+      for (int q = 0; q < nq && e == cudaSuccess; ++q) {
+        const Chunk k = chunk(i, q, nq);
+        e = cudaStreamWaitEvent(cs, P->ev_cin[s][q], 0);
+        if (e == cudaSuccess)
+          e = launch_rfft_x(P, din(s) + k.off, dout(s) + k.off, false, 1.0, cs,
+                            (long long)(k.width / P->nx));
+      }
+      if (e == cudaSuccess) e = launch_fft_y(P, dout(s), false, cs);
+      if (e == cudaSuccess) e = launch_thomas(P, dout(s), cs);
+      if (e == cudaSuccess) e = launch_fft_y(P, dout(s), true, cs);
+      for (int q = 0; q < nq && e == cudaSuccess; ++q) {
+        const Chunk k = chunk(i, q, nq);
+        e = launch_rfft_x(P, dout(s) + k.off, dout(s) + k.off, true, 1.0, cs,
+                          (long long)(k.width / P->nx));
+        if (e == cudaSuccess) e = cudaEventRecord(P->ev_cdone[s][q], cs);
+      }
+    } else {  // Algorithm 2 by y-row ranges of columns
+      HelmCoef* h = nullptr;
+      r = helm_prepare(P, c[i], loc[i], P->pcr_parts, &h);
+      for (int q = 0; q < nq && r == CFS_OK && e == cudaSuccess; ++q) {
+        const Chunk k = chunk(i, q, nq);
+        e = cudaStreamWaitEvent(cs, P->ev_cin[s][q], 0);
+        if (e == cudaSuccess)
+          e = launch_pcr_cols(P, *h, din(s), dout(s), (long long)k.off, (long long)k.width, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(P->ev_cdone[s][q], cs);
+      }
+    }
     if (r != CFS_OK && r != CFS_ENOTCONVERGED) {
       rc = r;
       break;
     }
+    if (e != cudaSuccess) break;
     if (r == CFS_ENOTCONVERGED && rc == CFS_OK) rc = r;
     cudaStream_t os = ostream(i);
     e = cudaEventRecord(P->ev_done[s], cs);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(os, P->ev_done[s], 0);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(out[i], dout(s), bytes, cudaMemcpyDeviceToHost, os);
+    for (int q = 0; q < nq && e == cudaSuccess; ++q) {
+      e = cudaStreamWaitEvent(os, P->ev_cdone[s][q], 0);
+      if (e == cudaSuccess)
+        e = copy(out[i], dout(s), chunk(i, q, nq), cudaMemcpyDeviceToHost, os);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(P->ev_free[s], os);
   }
   // every copy has landed (or the work stops here) before returning
@@ -1157,6 +1270,7 @@ extern "C" int cfs_solve_batch_host(cfs_plan_t P, int n, const int* kind, const 
   for (cudaStream_t q : {P->copy_in, P->compute2, P->copy_out, P->copy_out2, st})
     if (cudaStreamSynchronize(q) != cudaSuccess) ef = cudaErrorUnknown;
   if (rc != CFS_OK && rc != CFS_ENOTCONVERGED) return rc;
+  if (e == cudaErrorInvalidValue) return CFS_EINVAL;
   if (e != cudaSuccess || ef != cudaSuccess) return CFS_ECUDA;
   return rc;
 }

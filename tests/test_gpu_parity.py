@@ -661,3 +661,44 @@ def test_batch_of_host_solves_matches_single_solves(chanfs, dtype):
             for got, w in zip(outs, want):
                 assert np.array_equal(got.numpy(), w)
         assert plan.check() == 0
+
+
+@pytest.mark.parametrize("dims,chunks,ybc,thomas", [
+    ((64, 48, 40), 2, 0, 0), ((64, 48, 40), 3, 0, 0), ((64, 48, 40), 8, 0, 0),
+    ((96, 36, 27), 5, 0, 0), ((32, 6, 17), 8, 0, 0), ((64, 48, 40), 3, 1, 0),
+    ((64, 48, 40), 3, 0, 1), ((48, 2, 9), 4, 2, 0),
+])
+def test_streamed_batch_matches_single_solves(chanfs, dims, chunks, ybc, thomas):
+    """FP64 batches streamed in chunks (CFS_OPT_STREAM_CHUNKS: z-plane ranges
+    of Poisson fields, y-row ranges of Helmholtz fields, more chunks than y
+    rows or z planes, y walls, Thomas Helmholtz solves taking whole fields)
+    give the bits of the device solves, for job orders that move the first
+    Helmholtz solve ahead and batches larger than the plan's four slots."""
+    nx, ny, nz = dims
+    dz = make_dz(nz, 1.5)
+    f = [synth.normal(71 + i, (nz, ny, nx)) for i in range(2)]
+    if ybc != 2:
+        f = [synth.remove_weighted_mean(x, dz) for x in f]
+    rhs = [synth.normal(75 + i, (nz, ny, nx)) for i in range(4)]
+    c = 3e-5
+    with chanfs.Plan(nx, ny, nz, 2.0, 1.0, dz, 0, 0, ybc) as plan:
+        plan.set_option(chanfs.OPT_HELM_THOMAS, thomas)
+        plan.set_option(chanfs.OPT_STREAM_CHUNKS, chunks)
+        assert plan.get_option(chanfs.OPT_STREAM_CHUNKS) == min(chunks, nz)
+        P = lambda k: (chanfs.REQ_POISSON, 0.0, 0, f[k])
+        H = lambda k, loc: (chanfs.REQ_HELMHOLTZ, c, loc, rhs[k])
+        for order in ([P(0), H(0, 0), H(1, 0), H(2, 1)],
+                      [H(0, 1), P(0), P(1), H(1, 0), H(2, 0), H(3, 1)],
+                      [P(1), P(0)], [H(3, 0)]):
+            want = []
+            for kind, cc, loc, x in order:
+                d = dev(x)
+                want.append(host(plan.poisson_solve(d) if kind == chanfs.REQ_POISSON
+                                 else plan.helmholtz_solve(cc, d, loc)))
+            ins = [torch.from_numpy(x).pin_memory() for *_, x in order]
+            outs = [torch.full_like(x, float("nan")).pin_memory() for x in ins]
+            plan.solve_batch_host([(k, cc, loc, a, b) for (k, cc, loc, _), a, b
+                                   in zip(order, ins, outs)])
+            for got, w in zip(outs, want):
+                assert np.array_equal(got.numpy(), w)
+        assert plan.check() == 0
