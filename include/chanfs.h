@@ -530,7 +530,7 @@ int cfs_slab_helmholtz_finish(cfs_slab_t slab, double c, int loc, const double* 
  *       arithmetic, so every level gives the same bits; on GPUs whose FP64
  *       pipe is narrow it lets the integer units share the FP64 work.
  *   CFS_OPT_STREAM_CHUNKS  chunks in which cfs_solve_batch_host moves each
- *       field of an FP64 plan: 0 automatic (about 128 MB per chunk, at most
+ *       field of an FP64 plan: 0 automatic (about 200 MB per chunk, at most
  *       8), 1 whole fields, or 2..8.  A Poisson field moves in ranges of z
  *       planes (its x transforms run range by range as the data lands and
  *       leaves), a Helmholtz field solved by Algorithm 2 in ranges of y rows;

@@ -901,7 +901,10 @@ int chanfs::plan_set_radix(cfs_plan* P, int max_radix) {
 // Chunks of a streamed FP64 batch field (CFS_OPT_STREAM_CHUNKS): z-plane
 // ranges of a Poisson field, (x, y)-column ranges (whole y rows) of a
 // Helmholtz field solved by Algorithm 2; 1 for the solves that take the whole
-// field at once.  Automatic: about 128 MB per chunk, at most kMaxStreamChunks.
+// field at once.  Automatic: about 200 MB per chunk (3 for a 604 MB channel
+// field; on GB300 2, 3, 4 and 6 chunks gave 19.4, 19.0, 20.0 and 19.9 ms per
+// channel step against 20.8 ms whole, and 8 chunks 23.2 ms), at most
+// kMaxStreamChunks.
 static int batch_chunks(const cfs_plan* P, int kind) {
   const size_t plane = (size_t)P->nx * P->ny;
   if (P->dtype != CFS_F64 || (P->nx & 1)) return 1;
@@ -909,7 +912,8 @@ static int batch_chunks(const cfs_plan* P, int kind) {
     return 1;  // (Thomas sweeps take the field whole; 2-D copy pitches stay modest)
   const int extent = (kind == CFS_REQ_POISSON) ? P->nz : P->ny;
   int k = P->stream_chunks;
-  if (k == 0) k = (int)std::min<size_t>(kMaxStreamChunks, sizeof(double) * plane * P->nz >> 27);
+  if (k == 0)
+    k = (int)std::min<size_t>(kMaxStreamChunks, sizeof(double) * plane * P->nz / (192u << 20));
   return std::max(1, std::min(k, extent));
 }
 
