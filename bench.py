@@ -1160,33 +1160,34 @@ def run_ours(args):
     jobs = [(chanfs.REQ_POISSON, 0.0, 0, f_pin, out_pin[0])]
     jobs += [(chanfs.REQ_HELMHOLTZ, c, locs[i], rhs_pin[i], out_pin[1 + i]) for i in range(3)]
 
-    def e2e_step():  # one call: the four solves, copies overlapped with the solves
-        plan.solve_batch_host(jobs)
+    def e2e_step(chunks):  # one call: the four solves, copies overlapped with the solves
+        plan.set_option(chanfs.OPT_STREAM_CHUNKS, chunks)
+        t = time.perf_counter()
+        plan.solve_batch_host(jobs)  # returns once every result is in host memory
+        return (time.perf_counter() - t) * 1e3
 
-    e2e_step()
+    # the library's default (fields streamed in chunks) and, interleaved with
+    # it call by call, the same calls moving and solving whole fields; the
+    # host link's speed drifts and stalls now and then, so each figure is the
+    # median over its calls
+    e2e_step(0)
+    e2e_step(1)
     e2e_steps = max(3, min(args.steps, 10))
+    times = {0: [], 1: []}
     barrier(device)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        e2e_step()
+    for k in range(e2e_steps):
+        for chunks in ((0, 1) if k % 2 == 0 else (1, 0)):
+            times[chunks].append(e2e_step(chunks))
     torch.cuda.synchronize()
-    e2e_ms = reduce_max((time.perf_counter() - t0) * 1e3, device)
-    barrier(device)
-    e2e = aggregate(e2e_ms, e2e_steps, npts, world)
-    field_bytes = npts * 8
-    # the same calls with whole fields per copy (no streaming in chunks), for comparison
-    stream_chunks = plan.get_option(chanfs.OPT_STREAM_CHUNKS)
-    plan.set_option(chanfs.OPT_STREAM_CHUNKS, 1)
-    e2e_step()
-    barrier(device)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        e2e_step()
-    torch.cuda.synchronize()
-    whole_ms = reduce_max((time.perf_counter() - t0) * 1e3, device)
-    barrier(device)
     plan.set_option(chanfs.OPT_STREAM_CHUNKS, 0)
-    e2e_whole = aggregate(whole_ms, e2e_steps, npts, world)
+    stream_chunks = plan.get_option(chanfs.OPT_STREAM_CHUNKS)  # the automatic count
+    e2e_ms = reduce_max(statistics.median(times[0]), device)
+    whole_ms = reduce_max(statistics.median(times[1]), device)
+    barrier(device)
+    e2e = aggregate(e2e_ms, 1, npts, world)
+    e2e_whole = aggregate(whole_ms, 1, npts, world)
+    e2e_mean = {c: statistics.mean(v) for c, v in times.items()}
+    field_bytes = npts * 8
 
     if rank != 0:
         plan.close()
@@ -1232,9 +1233,13 @@ def run_ours(args):
                 "api": "cfs_solve_batch_host (Poisson + 3 Helmholtz, host<->device copies "
                        "overlapped with the solves), pinned host buffers",
                 "stream_chunks": stream_chunks,
-                "ms_per_step": e2e["ms_per_step"],
+                "ms_per_step": e2e["ms_per_step"], "mean_ms_per_step": e2e_mean[0],
+                "timing": "host clock around each call (it returns once every result is in "
+                          "host memory); median over the calls, interleaved call by call "
+                          "with the whole-field calls",
                 "whole_fields": {"value": e2e_whole["value"],
                                  "ms_per_step": e2e_whole["ms_per_step"],
+                                 "mean_ms_per_step": e2e_mean[1],
                                  "how": "the same calls with CFS_OPT_STREAM_CHUNKS 1 (each "
                                         "field copied and solved whole)"}},
         "gpu_launches": 8 * args.steps,
