@@ -201,9 +201,10 @@ struct cfs_plan {
   double* d_batch;
   int batch_slots;
   cudaStream_t copy_in, copy_out, copy_out2, compute2;
-  cudaEvent_t ev_entry, ev_done[4], ev_free[4];
+  cudaEvent_t ev_entry, ev_done[chanfs::kBatchSlots], ev_free[chanfs::kBatchSlots];
   // streamed FP64 batches: per slot, a chunk's input landed / its result is ready
-  cudaEvent_t ev_cin[4][8], ev_cdone[4][8];
+  cudaEvent_t ev_cin[chanfs::kBatchSlots][chanfs::kMaxStreamChunks];
+  cudaEvent_t ev_cdone[chanfs::kBatchSlots][chanfs::kMaxStreamChunks];
   int stream_chunks;  // CFS_OPT_STREAM_CHUNKS (0 automatic)
   // device status word
   int* d_status;
