@@ -614,6 +614,15 @@ int cfs_selfcheck_f64_addsub(unsigned long long samples, int on_device,
                              unsigned long long* mismatches);
 
 /*
+ * cfs_f64_addsub_host -- a diagnostic with no counterpart in the paper: the
+ * same integer-unit FP64 addition and subtraction, evaluated on the host CPU
+ * for caller-chosen operands, s[i] = a[i] + b[i] and d[i] = a[i] - b[i]
+ * (i < n).  All four pointers are HOST arrays of n doubles (s, d written);
+ * n = 0 does nothing.  No GPU is needed.
+ */
+int cfs_f64_addsub_host(long long n, const double* a, const double* b, double* s, double* d);
+
+/*
  * cfs_probe_fma -- a measurement with no counterpart in the paper: the FMA
  * rate of the current GPU in FP64 (bits = 64) or FP32 (bits = 32), the
  * roofline peak of kernels bound by those instructions.  Every thread of one

@@ -117,6 +117,7 @@ def lib():
             "cfs_selfcheck_f64_addsub": ([ctypes.c_ulonglong, i,
                                           ctypes.POINTER(ctypes.c_ulonglong)], i),
             "cfs_probe_addsub": ([i, ctypes.c_longlong, dp, dp], i),
+            "cfs_f64_addsub_host": ([ctypes.c_longlong, dp, dp, dp, dp], i),
             "cfs_group_reserve": ([ctypes.POINTER(vp), i], i),
             "cfs_group_rebind": ([vp, i, ctypes.POINTER(vp), vp], i),
             "cfs_server_create": ([ctypes.POINTER(vp), ctypes.c_size_t, i, i, i, i], i),
@@ -690,6 +691,20 @@ def selfcheck_f64_addsub(samples: int = 1 << 22, on_device: bool = True) -> int:
     _check(lib().cfs_selfcheck_f64_addsub(int(samples), 1 if on_device else 0, ctypes.byref(bad)),
            "cfs_selfcheck_f64_addsub")
     return bad.value
+
+
+def f64_addsub_host(a, b):
+    """(a + b, a - b) elementwise by the library's integer-unit FP64 additions,
+    run on the host CPU (cfs_f64_addsub_host); a and b are float64 arrays of
+    one shape."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    if a.shape != b.shape:
+        raise ValueError("a and b must have the same shape")
+    s, d = np.empty_like(a), np.empty_like(a)
+    p = lambda x: x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    _check(lib().cfs_f64_addsub_host(a.size, p(a), p(b), p(s), p(d)), "cfs_f64_addsub_host")
+    return s, d
 
 
 def probe_addsub(on_integer_units: bool, iters: int = 1 << 14):

@@ -306,6 +306,13 @@ extern "C" int cfs_selfcheck_f64_addsub(unsigned long long samples, int on_devic
   return e == cudaSuccess ? CFS_OK : CFS_ECUDA;
 }
 
+extern "C" int cfs_f64_addsub_host(long long n, const double* a, const double* b, double* s,
+                                   double* d) {
+  if (n < 0 || (n > 0 && (!a || !b || !s || !d))) return CFS_EINVAL;
+  for (long long i = 0; i < n; ++i) chanfs::f64_addsub(a[i], b[i], s[i], d[i]);
+  return CFS_OK;
+}
+
 extern "C" int cfs_probe_addsub(int on_integer_units, long long iters, double* pairs_per_s,
                                 double* ms) {
   if (!pairs_per_s || iters < 1 || iters > (1ll << 40) ||
