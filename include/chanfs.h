@@ -208,13 +208,15 @@ int cfs_helmholtz_solve_host(cfs_plan_t plan, double c, int loc,
  * after the work already on `stream`: Poisson solves on `stream`, and on
  * CFS_F64 plans the Helmholtz solves on a second stream beside them (they
  * share no plan scratch; refined solves all run on `stream`).  On CFS_F64
- * plans each field moves in chunks (CFS_OPT_STREAM_CHUNKS): a Poisson field
- * in ranges of z planes, transformed along x range by range as it lands and
+ * plans whose fields are larger than about 200 MB (or with
+ * CFS_OPT_STREAM_CHUNKS set) each field moves in chunks: a Poisson field in
+ * ranges of z planes, transformed along x range by range as it lands and
  * copied out range by range as its inverse x transform finishes; a Helmholtz
  * field solved by Algorithm 2 in ranges of y rows, each solved and copied
- * out on its own; and the batch's first Helmholtz solve is taken first when
- * the batch also holds Poisson solves.  The results are the same bits as
- * whole-field solves.  Host buffers should be pinned for the copies to
+ * out on its own (Thomas-sweep Helmholtz solves take the field whole); and
+ * the batch's first Helmholtz solve is taken first when the batch also holds
+ * Poisson solves and its fields move in chunks.  The results are the same
+ * bits as whole-field solves.  Host buffers should be pinned for the copies to
  * overlap.  Returns when every result has
  * arrived: CFS_OK, the first error, or CFS_ENOTCONVERGED if a refined solve
  * missed its tolerance (every output is still written).  A step of the
